@@ -1,0 +1,164 @@
+/*
+ * burgers.h -- C ABI of libburgers, the B300 (sm_103a) implementation of the
+ * 1D viscous Burgers solvers of arXiv 2601.12204:
+ *
+ *     u_t + u u_x = nu u_xx                                   (Eq. 1)
+ *
+ * advanced either by the explicit forward-Euler upwind/central step (Eq. 21,
+ * upwind side chosen by the sign of u_i as in Sec. 2.2, time step from the CFL
+ * limits of Eq. 7-8) or by the implicit BTCS step (Sec. 2.4, Eq. 23) with the
+ * convecting velocity lagged from u^n (one Picard linearisation per step),
+ * whose tridiagonal system is solved directly under Dirichlet BCs (Eq. 16-17)
+ * and through Sherman-Morrison under periodic BCs (Eq. 18).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  * Device pointers are CUDA device addresses of the context's device; the
+ *    caller owns them and the stream. Work is enqueued on `stream` (NULL = the
+ *    legacy default stream) and the call returns without waiting unless its
+ *    comment says "blocking".
+ *  * A batch is a packed buffer of `count` independent rows. Row b occupies
+ *    elements [inst[b].offset, inst[b].offset + inst[b].n) of the buffer, in
+ *    the batch dtype (FP32 or FP64). Rows must not overlap. `inst` is a host
+ *    array; it is read during the call only.
+ *  * Grid: periodic rows have n distinct nodes (node n is node 0, Eq. 18), so
+ *    dx = L/n; Dirichlet rows have n nodes including both ends, dx = L/(n-1),
+ *    and u[0], u[n-1] carry the boundary values a, b, which stay fixed.
+ *  * r = dt/dx and s = nu*dt/dx^2 are formed in FP64 on the host and rounded
+ *    once to the batch dtype.
+ *  * Errors: every function returns a status and never aborts or throws.
+ *    BURGERS_EINVAL: n < 3, dx <= 0, nu < 0, dt <= 0, nsteps < 0, a NULL
+ *    pointer, a bad enum, overlapping rows. BURGERS_ENOMEM: the context
+ *    could not grow its workspace. BURGERS_ECUDA: a CUDA call failed (the
+ *    message is in burgers_last_error()). The buffers are unchanged on
+ *    EINVAL; after ECUDA their contents are unspecified.
+ *  * A context owns its workspace, tuning table and graph cache; it is not
+ *    thread-safe and its calls must be ordered on one stream at a time.
+ */
+#ifndef BURGERS_H
+#define BURGERS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* burgers_stream; /* identical to cudaStream_t */
+
+typedef enum {
+  BURGERS_OK = 0,
+  BURGERS_EINVAL = 1,
+  BURGERS_ENOMEM = 2,
+  BURGERS_ECUDA = 3,
+  BURGERS_EAGAIN = 4,    /* serving: request still pending */
+  BURGERS_ETIMEOUT = 5,  /* a bounded wait gave up */
+  BURGERS_ECANCELED = 6, /* serving: request cancelled */
+  BURGERS_ENOTFOUND = 7  /* serving: unknown ticket */
+} burgers_status;
+
+typedef enum { BURGERS_F32 = 0, BURGERS_F64 = 1 } burgers_dtype;
+typedef enum { BURGERS_PERIODIC = 0, BURGERS_DIRICHLET = 1 } burgers_bc;
+typedef enum { BURGERS_EXPLICIT = 0, BURGERS_BTCS = 1 } burgers_scheme;
+
+/* One row of a batch (see the conventions above). */
+typedef struct {
+  int64_t offset; /* first element of the row in the packed buffer */
+  int32_t n;      /* nodes, >= 3 */
+  int32_t bc;     /* burgers_bc */
+  double dx;      /* grid spacing, > 0 */
+  double nu;      /* viscosity, >= 0 */
+  double dt;      /* time step, > 0 */
+  int64_t nsteps; /* steps to advance, >= 0 */
+} burgers_instance;
+
+typedef struct {
+  int32_t dtype; /* burgers_dtype of the buffers */
+  int32_t reserved;
+  int64_t count;                /* number of rows */
+  const burgers_instance* inst; /* host array of `count` rows */
+} burgers_batch;
+
+typedef struct burgers_ctx burgers_ctx;
+
+/* ---- context ------------------------------------------------------------ */
+
+/* Creates a context on CUDA device `device` (made current on the calling
+ * thread). Queries the SM count and shared-memory limits used for launch
+ * shapes. *out receives the context; destroy it with burgers_ctx_destroy. */
+burgers_status burgers_ctx_create(int device, burgers_ctx** out);
+
+/* Synchronises the context's device work and frees everything it owns. */
+void burgers_ctx_destroy(burgers_ctx* ctx);
+
+/* Message of the last failure on the calling thread ("" if none). The string
+ * stays valid until the next call on this thread. */
+const char* burgers_last_error(void);
+
+/* Tunables (see burgers_option). Returns EINVAL for an unknown key or a value
+ * out of range. */
+typedef enum {
+  BURGERS_OPT_GRAPHS = 0,        /* 1: replay multi-launch sequences as CUDA graphs (default 1) */
+  BURGERS_OPT_PLAIN = 1,         /* 1: one launch per row per call, no batching (baseline) */
+  BURGERS_OPT_STREAM_K = 2,      /* steps per HBM pass of the streaming explicit kernel, 1..64;
+                                    0 = tuned (default 0) */
+  BURGERS_OPT_RESIDENT_MAX = 3,  /* rows longer than this use the streaming explicit kernel and
+                                    the multi-level BTCS solver; 0 = device limit (default 0) */
+  BURGERS_OPT_AUTOTUNE = 4,      /* 1: time candidate launch shapes on first use (default 0) */
+  BURGERS_OPT_LAUNCH_COUNT = 5   /* write-only reset of the launch counter (value ignored) */
+} burgers_option;
+burgers_status burgers_ctx_set(burgers_ctx* ctx, int32_t option, int64_t value);
+
+/* Number of kernel launches this context has issued (graph replays count the
+ * kernels they contain). */
+int64_t burgers_launch_count(const burgers_ctx* ctx);
+
+/* ---- time step (Eq. 7-8) ------------------------------------------------- */
+
+/* Blocking. For every row b of `batch`, dt_host[b] = cfl * min(dx / max|u|,
+ * dx^2 / (2 nu)), the max taken over all n nodes of the row in `u_dev` on the
+ * device; the formula is evaluated in FP64 on the device. The rows' dt and
+ * nsteps fields are ignored. A row with max|u| == 0 and nu == 0 has no finite
+ * limit: dt_host[b] = -1 and the call returns EINVAL after filling the rest. */
+burgers_status burgers_cfl_dt(burgers_ctx* ctx, const burgers_batch* batch, const void* u_dev,
+                              double cfl, double* dt_host, burgers_stream stream);
+
+/* ---- solvers ------------------------------------------------------------- */
+
+/* Explicit forward-Euler upwind/central solve (Eq. 21, Sec. 2.2). In place:
+ * u_dev holds u(0) of every row on entry and u(nsteps*dt) on exit. Each row
+ * advances its own nsteps with its own dt. No CFL check is made. */
+burgers_status burgers_explicit_advance(burgers_ctx* ctx, const burgers_batch* batch,
+                                        void* u_dev, burgers_stream stream);
+
+/* Lagged-coefficient upwind BTCS solve (Sec. 2.4, Eq. 23). In place, as
+ * above. Step n solves A(u^n) u^{n+1} = u^n with
+ *   l_i = -r a_i^+ - s,  d_i = 1 + r|a_i| + 2s,  c_i = r a_i^- - s,  a = u^n,
+ * cyclically (periodic, Sherman-Morrison with an FP64 correction) or with the
+ * boundary nodes held (Dirichlet). */
+burgers_status burgers_btcs_advance(burgers_ctx* ctx, const burgers_batch* batch,
+                                    void* u_dev, burgers_stream stream);
+
+/* End-to-end variant through host memory: copies every row from u_host to a
+ * context-owned device buffer, advances it with `scheme` (burgers_scheme),
+ * copies the rows back into u_host. Blocking. u_host should be pinned for
+ * full copy bandwidth. */
+burgers_status burgers_solve_host(burgers_ctx* ctx, int32_t scheme, const burgers_batch* batch,
+                                  void* u_host, burgers_stream stream);
+
+/* ---- norms (Nomenclature "L2", Sec. 2.7.4) ------------------------------- */
+
+/* Blocking. out_host[b] = ||u_b - ref_b||_2 / ||ref_b||_2 over the n nodes of
+ * row b, accumulated in FP64 in a fixed order (deterministic). `u_dev` has the
+ * batch dtype, `ref_dev` has dtype `ref_dtype` and the same row offsets.
+ * ||ref_b|| == 0 gives 0 if u_b == ref_b, else +inf. If rms_host is not NULL,
+ * rms_host[b] = ||u_b - ref_b||_2 / sqrt(n). */
+burgers_status burgers_rel_l2(burgers_ctx* ctx, const burgers_batch* batch, const void* u_dev,
+                              const void* ref_dev, int32_t ref_dtype, double* out_host,
+                              double* rms_host, burgers_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BURGERS_H */

@@ -1,0 +1,177 @@
+"""Python front end of libburgers: batches, a context wrapper, torch tensors.
+
+PyTorch provides device memory and streams; every solver step runs in the
+library's CUDA kernels. Tensors are passed by pointer on the current torch
+stream of their device.
+"""
+from __future__ import annotations
+
+import ctypes
+from typing import Optional
+
+import numpy as np
+
+from . import _lib as L
+
+DTYPES = {L.BURGERS_F32: np.float32, L.BURGERS_F64: np.float64}
+
+
+def _torch():
+    import torch
+    return torch
+
+
+class Batch:
+    """A packed batch of rows (mirror of burgers_batch)."""
+
+    def __init__(self, dtype: int, offsets, ns, bcs, dxs, nus, dts, nsteps):
+        offsets = np.asarray(offsets, dtype=np.int64).ravel()
+        count = offsets.size
+        arr = np.zeros(count, dtype=L.INSTANCE_DTYPE)
+        arr["offset"] = offsets
+        arr["n"] = np.broadcast_to(np.asarray(ns, dtype=np.int32), (count,))
+        arr["bc"] = np.broadcast_to(np.asarray(bcs, dtype=np.int32), (count,))
+        arr["dx"] = np.broadcast_to(np.asarray(dxs, dtype=np.float64), (count,))
+        arr["nu"] = np.broadcast_to(np.asarray(nus, dtype=np.float64), (count,))
+        arr["dt"] = np.broadcast_to(np.asarray(dts, dtype=np.float64), (count,))
+        arr["nsteps"] = np.broadcast_to(np.asarray(nsteps, dtype=np.int64), (count,))
+        self.arr = np.ascontiguousarray(arr)
+        self.dtype = int(dtype)
+        self._c = L.burgers_batch(self.dtype, 0, count, self.arr.ctypes.data)
+
+    @classmethod
+    def from_ensemble(cls, ens, dts, nsteps, dtype: int = L.BURGERS_F32) -> "Batch":
+        return cls(dtype, ens.offsets, ens.ns, ens.bcs, ens.dxs, ens.nus, dts, nsteps)
+
+    @property
+    def count(self) -> int:
+        return int(self.arr.size)
+
+    @property
+    def span(self) -> int:
+        if self.count == 0:
+            return 0
+        return int(np.max(self.arr["offset"] + self.arr["n"]))
+
+    def ref(self):
+        return ctypes.byref(self._c)
+
+    def with_fields(self, **kw) -> "Batch":
+        a = self.arr
+        f = {k: a[k] for k in ("offset", "n", "bc", "dx", "nu", "dt", "nsteps")}
+        f.update(kw)
+        return Batch(kw.get("dtype", self.dtype), f["offset"], f["n"], f["bc"], f["dx"], f["nu"],
+                     f["dt"], f["nsteps"])
+
+
+class Context:
+    """Owns a burgers_ctx on one CUDA device."""
+
+    def __init__(self, device: int = 0):
+        self._lib = L.load()
+        h = ctypes.c_void_p()
+        L.check(self._lib.burgers_ctx_create(int(device), ctypes.byref(h)), "burgers_ctx_create")
+        self.h = h
+        self.device = int(device)
+
+    def close(self) -> None:
+        if getattr(self, "h", None) is not None and self.h.value:
+            self._lib.burgers_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- helpers ----------------------------------------------------------
+    def _stream(self, stream, t=None):
+        if stream is not None:
+            return ctypes.c_void_p(int(stream))
+        torch = _torch()
+        dev = t.device if t is not None else torch.device("cuda", self.device)
+        return ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream)
+
+    def _check_tensor(self, t, batch: Batch, dtype: Optional[int] = None):
+        torch = _torch()
+        want = {L.BURGERS_F32: torch.float32, L.BURGERS_F64: torch.float64}[
+            batch.dtype if dtype is None else dtype]
+        if not t.is_cuda or t.device.index != self.device:
+            raise ValueError("tensor must live on the context's CUDA device")
+        if t.dtype != want:
+            raise ValueError(f"tensor dtype {t.dtype} does not match batch dtype {want}")
+        if not t.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        if t.numel() < batch.span:
+            raise ValueError("tensor is smaller than the batch span")
+        return ctypes.c_void_p(t.data_ptr())
+
+    # -- entry points -------------------------------------------------------
+    def set(self, option: int, value: int) -> None:
+        L.check(self._lib.burgers_ctx_set(self.h, int(option), int(value)), "burgers_ctx_set")
+
+    def launch_count(self) -> int:
+        return int(self._lib.burgers_launch_count(self.h))
+
+    def explicit_advance(self, batch: Batch, u, stream=None) -> None:
+        p = self._check_tensor(u, batch)
+        L.check(self._lib.burgers_explicit_advance(self.h, batch.ref(), p, self._stream(stream, u)),
+                "burgers_explicit_advance")
+
+    def btcs_advance(self, batch: Batch, u, stream=None) -> None:
+        p = self._check_tensor(u, batch)
+        L.check(self._lib.burgers_btcs_advance(self.h, batch.ref(), p, self._stream(stream, u)),
+                "burgers_btcs_advance")
+
+    def advance(self, scheme: int, batch: Batch, u, stream=None) -> None:
+        if scheme == L.BURGERS_EXPLICIT:
+            self.explicit_advance(batch, u, stream)
+        else:
+            self.btcs_advance(batch, u, stream)
+
+    def cfl_dt(self, batch: Batch, u, cfl: float = 0.4, stream=None) -> np.ndarray:
+        p = self._check_tensor(u, batch)
+        out = np.zeros(batch.count, dtype=np.float64)
+        L.check(self._lib.burgers_cfl_dt(self.h, batch.ref(), p, float(cfl),
+                                         out.ctypes.data_as(ctypes.c_void_p),
+                                         self._stream(stream, u)), "burgers_cfl_dt")
+        return out
+
+    def rel_l2(self, batch: Batch, u, ref, stream=None):
+        torch = _torch()
+        p = self._check_tensor(u, batch)
+        rdt = L.BURGERS_F64 if ref.dtype == torch.float64 else L.BURGERS_F32
+        q = self._check_tensor(ref, batch, rdt)
+        rel = np.zeros(batch.count)
+        rms = np.zeros(batch.count)
+        L.check(self._lib.burgers_rel_l2(self.h, batch.ref(), p, q, rdt,
+                                         rel.ctypes.data_as(ctypes.c_void_p),
+                                         rms.ctypes.data_as(ctypes.c_void_p),
+                                         self._stream(stream, u)), "burgers_rel_l2")
+        return rel, rms
+
+    def solve_host(self, scheme: int, batch: Batch, u_host, stream=None) -> None:
+        """In-place solve of a host buffer (numpy array or CPU tensor)."""
+        if isinstance(u_host, np.ndarray):
+            if u_host.dtype != DTYPES[batch.dtype] or not u_host.flags.c_contiguous:
+                raise ValueError("host array dtype/contiguity mismatch")
+            ptr = u_host.ctypes.data
+            n = u_host.size
+        else:
+            torch = _torch()
+            want = torch.float32 if batch.dtype == L.BURGERS_F32 else torch.float64
+            if u_host.is_cuda or u_host.dtype != want or not u_host.is_contiguous():
+                raise ValueError("host tensor dtype/device/contiguity mismatch")
+            ptr = u_host.data_ptr()
+            n = u_host.numel()
+        if n < batch.span:
+            raise ValueError("host buffer is smaller than the batch span")
+        L.check(self._lib.burgers_solve_host(self.h, int(scheme), batch.ref(), ctypes.c_void_p(ptr),
+                                             self._stream(stream)), "burgers_solve_host")

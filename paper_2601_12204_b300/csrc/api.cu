@@ -1,0 +1,799 @@
+// api.cu -- the C ABI of libburgers (include/burgers.h): context, argument
+// checks, launch planning, plan and CUDA-graph caches, dispatch.
+//
+// A call turns its batch into a Plan: rows short enough to stay resident are
+// grouped by kernel shape (smallest register capacity >= n), each group sorted
+// by cost (n * nsteps, longest first) so the persistent CTAs of one launch
+// drain it with little tail; longer rows become tiled work items of the
+// streaming explicit kernel or of the multi-level BTCS solver. The packed
+// descriptors live in device memory owned by the plan, so a repeated batch
+// costs no host-to-device copy, and a plan with several launches is captured
+// once into a CUDA graph and replayed.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <atomic>
+#include <list>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/burgers.h"
+#include "api_internal.h"
+#include "kernels.h"
+#include "norms.h"
+
+using namespace burgers;
+
+namespace burgers {
+
+thread_local std::string g_last_error;
+
+burgers_status set_error(burgers_status st, const std::string& msg) {
+  g_last_error = msg;
+  return st;
+}
+
+burgers_status cuda_error(cudaError_t e, const char* where) {
+  return set_error(BURGERS_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+// ---------------------------------------------------------------------------
+// device buffers
+// ---------------------------------------------------------------------------
+DevBuf::~DevBuf() {
+  if (ptr) cudaFree(ptr);
+}
+
+cudaError_t DevBuf::ensure(size_t need) {
+  if (need <= bytes) return cudaSuccess;
+  if (ptr) {
+    cudaError_t e = cudaDeviceSynchronize();  // the old buffer may still be in use
+    if (e != cudaSuccess) return e;
+    cudaFree(ptr);
+    ptr = nullptr;
+    bytes = 0;
+  }
+  size_t want = std::max(need, size_t(1) << 16);
+  cudaError_t e = cudaMalloc(&ptr, want);
+  if (e != cudaSuccess) {
+    ptr = nullptr;
+    return e;
+  }
+  bytes = want;
+  ++generation;
+  return cudaSuccess;
+}
+
+// ---------------------------------------------------------------------------
+// shapes
+// ---------------------------------------------------------------------------
+struct Shape {
+  int nt, c;
+};
+
+// Default resident shapes per (kind, dtype), ascending capacity; the first
+// entry of a capacity is the default, later entries are autotuning
+// alternatives of the same capacity.
+static const std::vector<Shape>& resident_shapes(int kind, int dtype) {
+  static const std::vector<Shape> ex32 = {{32, 1},   {32, 2},    {32, 4},   {32, 8},  {64, 8},
+                                          {128, 8},  {64, 16},   {128, 16}, {256, 8}, {256, 16},
+                                          {128, 32}, {512, 16},  {256, 32}, {512, 8}, {1024, 16},
+                                          {1024, 32}};
+  static const std::vector<Shape> ex64 = {{32, 1},  {32, 2},   {32, 4},  {32, 8},   {64, 8},
+                                          {128, 8}, {256, 8},  {128, 16}, {512, 8}, {256, 16},
+                                          {1024, 8}, {512, 16}};
+  static const std::vector<Shape> bt32 = {{32, 1},  {32, 2},   {32, 4},   {32, 8},  {64, 8},
+                                          {128, 8}, {256, 8},  {128, 16}, {256, 16}, {512, 8},
+                                          {512, 16}, {1024, 8}};
+  static const std::vector<Shape> bt64 = {{32, 1},  {32, 2},  {32, 4},  {32, 8},  {64, 8},
+                                          {128, 8}, {256, 8}, {512, 8}, {256, 16}};
+  if (kind == K_EXPLICIT_RESIDENT) return dtype == 0 ? ex32 : ex64;
+  return dtype == 0 ? bt32 : bt64;
+}
+
+static int64_t max_resident(int kind, int dtype) {
+  int64_t m = 0;
+  for (const Shape& s : resident_shapes(kind, dtype)) m = std::max<int64_t>(m, int64_t(s.nt) * s.c);
+  return m;
+}
+
+}  // namespace burgers
+
+// ---------------------------------------------------------------------------
+// context
+// ---------------------------------------------------------------------------
+burgers_ctx::burgers_ctx() = default;
+burgers_ctx::~burgers_ctx() = default;
+
+namespace burgers {
+
+static int64_t resident_limit(const burgers_ctx* ctx, int kind, int dtype) {
+  int64_t m = max_resident(kind, dtype);
+  if (ctx->resident_max > 0) m = std::min<int64_t>(m, ctx->resident_max);
+  return m;
+}
+
+// Shape for a resident row of n nodes: the tuned choice for its capacity class
+// if there is one, else the default (first smallest capacity >= n).
+static Shape pick_resident(const burgers_ctx* ctx, int kind, int dtype, int64_t n) {
+  const auto& list = resident_shapes(kind, dtype);
+  int64_t cap = -1;
+  Shape best{0, 0};
+  for (const Shape& s : list) {
+    int64_t c = int64_t(s.nt) * s.c;
+    if (c >= n && s.c < n && (cap < 0 || c < cap)) {
+      cap = c;
+      best = s;
+    }
+  }
+  if (cap > 0) {
+    auto it = ctx->tuned.find(tune_key(kind, dtype, cap, cap == n));
+    if (it != ctx->tuned.end()) return Shape{it->second.nt, it->second.c};
+  }
+  return best;
+}
+
+static uint64_t fnv1a(const void* data, size_t len, uint64_t h = 1469598103934665603ull) {
+  const unsigned char* p = static_cast<const unsigned char*>(data);
+  for (size_t i = 0; i < len; ++i) {
+    h ^= p[i];
+    h *= 1099511628211ull;
+  }
+  return h;
+}
+
+burgers_status validate_batch(const burgers_batch* batch, bool allow_empty) {
+  if (!batch) return set_error(BURGERS_EINVAL, "batch is NULL");
+  if (batch->dtype != BURGERS_F32 && batch->dtype != BURGERS_F64)
+    return set_error(BURGERS_EINVAL, "bad dtype");
+  if (batch->count < 0) return set_error(BURGERS_EINVAL, "negative count");
+  if (batch->count > 0 && !batch->inst) return set_error(BURGERS_EINVAL, "inst is NULL");
+  if (batch->count == 0 && !allow_empty) return BURGERS_OK;
+  if (batch->count > (int64_t(1) << 30)) return set_error(BURGERS_EINVAL, "count too large");
+  std::vector<std::pair<int64_t, int64_t>> spans;
+  spans.reserve(size_t(batch->count));
+  for (int64_t b = 0; b < batch->count; ++b) {
+    const burgers_instance& in = batch->inst[b];
+    char msg[160];
+    if (in.n < 3) {
+      snprintf(msg, sizeof msg, "row %lld: n = %d < 3", (long long)b, in.n);
+      return set_error(BURGERS_EINVAL, msg);
+    }
+    if (in.bc != BURGERS_PERIODIC && in.bc != BURGERS_DIRICHLET) {
+      snprintf(msg, sizeof msg, "row %lld: bad bc %d", (long long)b, in.bc);
+      return set_error(BURGERS_EINVAL, msg);
+    }
+    if (!(in.dx > 0.0) || !(in.nu >= 0.0) || !(in.dt > 0.0) || in.nsteps < 0 ||
+        in.offset < 0) {
+      snprintf(msg, sizeof msg, "row %lld: need dx > 0, nu >= 0, dt > 0, nsteps >= 0, offset >= 0",
+               (long long)b);
+      return set_error(BURGERS_EINVAL, msg);
+    }
+    spans.emplace_back(in.offset, in.offset + in.n);
+  }
+  std::sort(spans.begin(), spans.end());
+  for (size_t i = 1; i < spans.size(); ++i)
+    if (spans[i].first < spans[i - 1].second)
+      return set_error(BURGERS_EINVAL, "rows overlap");
+  return BURGERS_OK;
+}
+
+static RowDesc make_row(const burgers_instance& in) {
+  RowDesc d;
+  d.offset = in.offset;
+  d.nsteps = in.nsteps;
+  d.r = in.dt / in.dx;
+  d.s = in.nu * in.dt / (in.dx * in.dx);
+  d.ds_dnu = in.dt / (in.dx * in.dx);
+  d.n = in.n;
+  d.bc = in.bc;
+  return d;
+}
+
+static int blocks_per_sm(const KernelEntry* k) {
+  int b = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k->fn, k->nt, k->dyn_smem) != cudaSuccess ||
+      b < 1)
+    b = 1;
+  return b;
+}
+
+// Streaming shape for a long explicit row: the largest registered window that
+// fits the row, with K = min(requested, W/4).
+static bool pick_stream(const burgers_ctx* ctx, int dtype, int64_t n_min, Shape* sh, int* K) {
+  static const Shape s32[] = {{256, 16}, {128, 16}, {32, 4}};
+  static const Shape s64[] = {{256, 8}, {128, 8}, {32, 4}};
+  const Shape* list = dtype == 0 ? s32 : s64;
+  for (int i = 0; i < 3; ++i) {
+    int64_t W = int64_t(list[i].nt) * list[i].c;
+    if (W <= n_min) {
+      *sh = list[i];
+      int k = ctx->stream_k > 0 ? ctx->stream_k : (dtype == 0 ? 32 : 16);
+      *K = int(std::min<int64_t>(k, W / 4));
+      auto it = ctx->tuned.find(tune_key(K_EXPLICIT_STREAM, dtype, W, 0));
+      if (ctx->stream_k == 0 && it != ctx->tuned.end()) {
+        *sh = Shape{it->second.nt, it->second.c};
+        *K = int(std::min<int64_t>(it->second.k, int64_t(sh->nt) * sh->c / 4));
+      }
+      return true;
+    }
+  }
+  return false;
+}
+
+// Builds the plan of one advance call.
+static burgers_status build_plan(burgers_ctx* ctx, int scheme, const burgers_batch* batch,
+                                 Plan* p) {
+  const int dtype = batch->dtype;
+  p->dtype = dtype;
+  p->scheme = scheme;
+  const int rkind = scheme == BURGERS_EXPLICIT ? K_EXPLICIT_RESIDENT : K_BTCS_RESIDENT;
+  const int64_t rlim = resident_limit(ctx, rkind, dtype);
+  struct Grp {
+    Shape sh;
+    int exact;
+    std::vector<std::pair<double, int64_t>> rows;  // (cost, index)
+  };
+  std::vector<Grp> groups;
+  std::vector<int64_t> longs;
+  for (int64_t b = 0; b < batch->count; ++b) {
+    const burgers_instance& in = batch->inst[b];
+    if (in.nsteps == 0) continue;
+    if (in.n > rlim) {
+      longs.push_back(b);
+      continue;
+    }
+    Shape sh = pick_resident(ctx, rkind, dtype, in.n);
+    if (sh.nt == 0) return set_error(BURGERS_EINVAL, "no resident kernel shape fits the row");
+    int exact = int64_t(sh.nt) * sh.c == in.n ? 1 : 0;
+    Grp* g = nullptr;
+    for (Grp& x : groups)
+      if (x.sh.nt == sh.nt && x.sh.c == sh.c && x.exact == exact) g = &x;
+    if (!g) {
+      groups.push_back(Grp{sh, exact, {}});
+      g = &groups.back();
+    }
+    g->rows.emplace_back(double(in.n) * double(in.nsteps), b);
+  }
+  // resident groups
+  for (Grp& g : groups) {
+    std::stable_sort(g.rows.begin(), g.rows.end(),
+                     [](const auto& a, const auto& b) { return a.first > b.first; });
+    const KernelEntry* k = find_kernel(rkind, dtype, g.sh.nt, g.sh.c, g.exact);
+    if (!k) return set_error(BURGERS_EINVAL, "kernel shape not instantiated");
+    int begin = int(p->rows.size());
+    for (auto& pr : g.rows) p->rows.push_back(make_row(batch->inst[pr.second]));
+    int cnt = int(g.rows.size());
+    if (ctx->plain) {
+      for (int i = 0; i < cnt; ++i) {
+        Launch L;
+        L.k = k;
+        L.type = LAUNCH_RESIDENT;
+        L.grid = 1;
+        L.row_begin = begin + i;
+        L.row_count = 1;
+        L.counter = p->ncounters++;
+        p->launches.push_back(L);
+      }
+    } else {
+      Launch L;
+      L.k = k;
+      L.type = LAUNCH_RESIDENT;
+      L.grid = std::min(cnt, ctx->sm_count * blocks_per_sm(k));
+      L.row_begin = begin;
+      L.row_count = cnt;
+      L.counter = p->ncounters++;
+      p->launches.push_back(L);
+    }
+  }
+  if (!longs.empty()) {
+    if (scheme == BURGERS_EXPLICIT) {
+      int64_t nmin = INT64_MAX, smax = 0, span = 0;
+      for (int64_t b : longs) {
+        nmin = std::min<int64_t>(nmin, batch->inst[b].n);
+        smax = std::max<int64_t>(smax, batch->inst[b].nsteps);
+        span = std::max<int64_t>(span, batch->inst[b].offset + batch->inst[b].n);
+      }
+      Shape sh;
+      int K;
+      if (!pick_stream(ctx, dtype, nmin, &sh, &K))
+        return set_error(BURGERS_EINVAL, "row too short for the streaming kernel");
+      const KernelEntry* k = find_kernel(K_EXPLICIT_STREAM, dtype, sh.nt, sh.c, 0);
+      if (!k) return set_error(BURGERS_EINVAL, "streaming shape not instantiated");
+      const int64_t W = int64_t(sh.nt) * sh.c, O = W - 2 * K;
+      int rbegin = int(p->rows.size());
+      int ibegin = int(p->items.size());
+      for (size_t q = 0; q < longs.size(); ++q) {
+        const burgers_instance& in = batch->inst[longs[q]];
+        p->rows.push_back(make_row(in));
+        int64_t tiles = (in.n + O - 1) / O;
+        for (int64_t t = 0; t < tiles; ++t)
+          p->items.push_back(TileItem{int32_t(q), int32_t(t)});
+      }
+      int nitems = int(p->items.size()) - ibegin;
+      int grid = std::min(nitems, ctx->sm_count * blocks_per_sm(k));
+      int64_t passes = (smax + K - 1) / K;
+      for (int64_t ps = 0; ps < passes; ++ps) {
+        Launch L;
+        L.k = k;
+        L.type = LAUNCH_STREAM;
+        L.grid = grid;
+        L.row_begin = rbegin;
+        L.row_count = int(longs.size());
+        L.item_begin = ibegin;
+        L.item_count = nitems;
+        L.K = K;
+        L.step_base = ps * K;
+        L.to_scratch = (ps % 2) == 0;
+        p->launches.push_back(L);
+      }
+      if (passes % 2 == 1) {  // result sits in the scratch buffer: copy it back
+        Launch L;
+        L.k = k;
+        L.type = LAUNCH_STREAM;
+        L.grid = grid;
+        L.row_begin = rbegin;
+        L.row_count = int(longs.size());
+        L.item_begin = ibegin;
+        L.item_count = nitems;
+        L.K = K;
+        L.step_base = smax;  // every row done: copy-through
+        L.to_scratch = false;
+        p->launches.push_back(L);
+      }
+      p->scratch_elems = span;
+    } else {
+      burgers_status st = plan_multilevel(ctx, batch, longs, p);
+      if (st != BURGERS_OK) return st;
+    }
+  }
+  // device image: rows | items | counters (+ multilevel descriptors)
+  size_t off = 0;
+  auto align = [](size_t x) { return (x + 255) & ~size_t(255); };
+  p->rows_off = off;
+  off = align(off + p->rows.size() * sizeof(RowDesc));
+  p->items_off = off;
+  off = align(off + p->items.size() * sizeof(TileItem));
+  p->counters_off = off;
+  off = align(off + size_t(p->ncounters) * sizeof(int));
+  p->ml_off = off;
+  off = align(off + p->ml_bytes.size());
+  p->dev_bytes = off;
+  if (off > 0) {
+    cudaError_t e = cudaMalloc(&p->dev, off);
+    if (e != cudaSuccess) return set_error(BURGERS_ENOMEM, "plan descriptors: out of device memory");
+    std::vector<unsigned char> img(off, 0);
+    if (!p->rows.empty()) memcpy(img.data() + p->rows_off, p->rows.data(), p->rows.size() * sizeof(RowDesc));
+    if (!p->items.empty())
+      memcpy(img.data() + p->items_off, p->items.data(), p->items.size() * sizeof(TileItem));
+    if (!p->ml_bytes.empty()) memcpy(img.data() + p->ml_off, p->ml_bytes.data(), p->ml_bytes.size());
+    e = cudaMemcpy(p->dev, img.data(), off, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_error(e, "plan upload");
+  }
+  for (const Launch& L : p->launches)
+    if (L.k) ++p->kernel_launches;
+  return BURGERS_OK;
+}
+
+Plan::~Plan() {
+  if (gexec) cudaGraphExecDestroy(gexec);
+  if (dev) cudaFree(dev);
+}
+
+static cudaError_t enqueue_plan(burgers_ctx* ctx, Plan* p, void* u, cudaStream_t st) {
+  char* base = static_cast<char*>(p->dev);
+  RowDesc* rows = reinterpret_cast<RowDesc*>(base + p->rows_off);
+  TileItem* items = reinterpret_cast<TileItem*>(base + p->items_off);
+  int* counters = reinterpret_cast<int*>(base + p->counters_off);
+  const size_t esz = p->dtype == 0 ? 4 : 8;
+  if (p->ncounters > 0) {
+    cudaError_t e = cudaMemsetAsync(counters, 0, sizeof(int) * size_t(p->ncounters), st);
+    if (e != cudaSuccess) return e;
+  }
+  void* scratch = ctx->scratch.ptr;
+  for (const Launch& L : p->launches) {
+    cudaError_t e = cudaSuccess;
+    if (L.type == LAUNCH_RESIDENT) {
+      RowDesc* r = rows + L.row_begin;
+      int cnt = L.row_count;
+      int* ctr = counters + L.counter;
+      void* args[] = {&u, &r, &cnt, &ctr};
+      e = cudaLaunchKernel(L.k->fn, dim3(L.grid), dim3(L.k->nt), args, L.k->dyn_smem, st);
+    } else if (L.type == LAUNCH_STREAM) {
+      const void* src = L.to_scratch ? u : scratch;
+      void* dst = L.to_scratch ? scratch : u;
+      RowDesc* r = rows + L.row_begin;
+      TileItem* it = items + L.item_begin;
+      int ni = L.item_count, K = L.K;
+      int64_t sb = L.step_base;
+      void* args[] = {&src, &dst, &r, &it, &ni, &K, &sb};
+      e = cudaLaunchKernel(L.k->fn, dim3(L.grid), dim3(L.k->nt), args, L.k->dyn_smem, st);
+    } else {
+      e = enqueue_multilevel_launch(ctx, p, L, u, st);
+    }
+    if (e != cudaSuccess) return e;
+  }
+  (void)esz;
+  return cudaSuccess;
+}
+
+static burgers_status run_plan(burgers_ctx* ctx, Plan* p, void* u, cudaStream_t st) {
+  if (p->scratch_elems > 0) {
+    cudaError_t e = ctx->scratch.ensure(size_t(p->scratch_elems) * (p->dtype == 0 ? 4 : 8));
+    if (e != cudaSuccess) return set_error(BURGERS_ENOMEM, "streaming scratch: out of device memory");
+  }
+  if (p->ml_ws_elems > 0) {
+    cudaError_t e = ctx->mlws.ensure(size_t(p->ml_ws_elems) * (p->dtype == 0 ? 4 : 8));
+    if (e != cudaSuccess) return set_error(BURGERS_ENOMEM, "multi-level workspace: out of device memory");
+  }
+  const bool use_graph = ctx->graphs && !ctx->plain && p->launches.size() > 1;
+  if (use_graph) {
+    const bool valid = p->gexec && p->g_u == u && p->g_scratch_gen == ctx->scratch.generation &&
+                       p->g_ml_gen == ctx->mlws.generation;
+    if (!valid) {
+      if (p->gexec) {
+        cudaGraphExecDestroy(p->gexec);
+        p->gexec = nullptr;
+      }
+      cudaError_t e = cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeThreadLocal);
+      if (e != cudaSuccess) return cuda_error(e, "begin capture");
+      cudaError_t e1 = enqueue_plan(ctx, p, u, ctx->capture_stream);
+      cudaGraph_t g = nullptr;
+      cudaError_t e2 = cudaStreamEndCapture(ctx->capture_stream, &g);
+      if (e1 != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return cuda_error(e1, "capture enqueue");
+      }
+      if (e2 != cudaSuccess) return cuda_error(e2, "end capture");
+      e = cudaGraphInstantiate(&p->gexec, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) {
+        p->gexec = nullptr;
+        return cuda_error(e, "graph instantiate");
+      }
+      p->g_u = u;
+      p->g_scratch_gen = ctx->scratch.generation;
+      p->g_ml_gen = ctx->mlws.generation;
+    }
+    cudaError_t e = cudaGraphLaunch(p->gexec, st);
+    if (e != cudaSuccess) return cuda_error(e, "graph launch");
+  } else {
+    cudaError_t e = enqueue_plan(ctx, p, u, st);
+    if (e != cudaSuccess) return cuda_error(e, "kernel launch");
+  }
+  ctx->launches += p->kernel_launches;
+  return BURGERS_OK;
+}
+
+static uint64_t plan_key(const burgers_ctx* ctx, int scheme, const burgers_batch* b) {
+  uint64_t h = fnv1a(b->inst, sizeof(burgers_instance) * size_t(b->count));
+  int32_t hdr[8] = {scheme, b->dtype, ctx->plain ? 1 : 0, ctx->stream_k, int32_t(ctx->resident_max),
+                    int32_t(ctx->tune_version), 0, 0};
+  return fnv1a(hdr, sizeof hdr, h);
+}
+
+Plan* get_plan(burgers_ctx* ctx, int scheme, const burgers_batch* batch, burgers_status* st) {
+  const uint64_t key = plan_key(ctx, scheme, batch);
+  for (auto it = ctx->plans.begin(); it != ctx->plans.end(); ++it) {
+    if ((*it)->key == key && (*it)->count == batch->count) {
+      ctx->plans.splice(ctx->plans.begin(), ctx->plans, it);  // most recent first
+      *st = BURGERS_OK;
+      return ctx->plans.front().get();
+    }
+  }
+  auto p = std::make_unique<Plan>();
+  p->key = key;
+  p->count = batch->count;
+  *st = build_plan(ctx, scheme, batch, p.get());
+  if (*st != BURGERS_OK) return nullptr;
+  ctx->plans.push_front(std::move(p));
+  while (ctx->plans.size() > 64) {
+    cudaDeviceSynchronize();
+    ctx->plans.pop_back();
+  }
+  return ctx->plans.front().get();
+}
+
+burgers_status advance(burgers_ctx* ctx, int scheme, const burgers_batch* batch, void* u_dev,
+                       cudaStream_t stream) {
+  if (!ctx) return set_error(BURGERS_EINVAL, "ctx is NULL");
+  burgers_status st = validate_batch(batch, false);
+  if (st != BURGERS_OK) return st;
+  if (batch->count == 0) return BURGERS_OK;
+  if (!u_dev) return set_error(BURGERS_EINVAL, "u_dev is NULL");
+  cudaError_t e = cudaSetDevice(ctx->device);
+  if (e != cudaSuccess) return cuda_error(e, "cudaSetDevice");
+  Plan* p = get_plan(ctx, scheme, batch, &st);
+  if (!p) return st;
+  return run_plan(ctx, p, u_dev, stream);
+}
+
+}  // namespace burgers
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+burgers_status burgers_ctx_create(int device, burgers_ctx** out) {
+  if (!out) return set_error(BURGERS_EINVAL, "out is NULL");
+  *out = nullptr;
+  int ndev = 0;
+  cudaError_t e = cudaGetDeviceCount(&ndev);
+  if (e != cudaSuccess) return cuda_error(e, "cudaGetDeviceCount");
+  if (device < 0 || device >= ndev) return set_error(BURGERS_EINVAL, "bad device index");
+  e = cudaSetDevice(device);
+  if (e != cudaSuccess) return cuda_error(e, "cudaSetDevice");
+  auto ctx = std::make_unique<burgers_ctx>();
+  ctx->device = device;
+  cudaDeviceProp prop;
+  e = cudaGetDeviceProperties(&prop, device);
+  if (e != cudaSuccess) return cuda_error(e, "cudaGetDeviceProperties");
+  ctx->sm_count = prop.multiProcessorCount;
+  ctx->smem_optin = prop.sharedMemPerBlockOptin;
+  e = prepare_kernels();
+  if (e != cudaSuccess) return cuda_error(e, "kernel attributes");
+  e = cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return cuda_error(e, "cudaStreamCreate");
+  *out = ctx.release();
+  return BURGERS_OK;
+}
+
+void burgers_ctx_destroy(burgers_ctx* ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  cudaDeviceSynchronize();
+  ctx->plans.clear();
+  if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
+  delete ctx;
+}
+
+const char* burgers_last_error(void) { return g_last_error.c_str(); }
+
+burgers_status burgers_ctx_set(burgers_ctx* ctx, int32_t option, int64_t value) {
+  if (!ctx) return set_error(BURGERS_EINVAL, "ctx is NULL");
+  switch (option) {
+    case BURGERS_OPT_GRAPHS: ctx->graphs = value != 0; return BURGERS_OK;
+    case BURGERS_OPT_PLAIN: ctx->plain = value != 0; return BURGERS_OK;
+    case BURGERS_OPT_STREAM_K:
+      if (value < 0 || value > 64) return set_error(BURGERS_EINVAL, "stream K out of range");
+      ctx->stream_k = int(value);
+      return BURGERS_OK;
+    case BURGERS_OPT_RESIDENT_MAX:
+      if (value < 0 || value > (int64_t(1) << 30)) return set_error(BURGERS_EINVAL, "bad resident max");
+      ctx->resident_max = value;
+      return BURGERS_OK;
+    case BURGERS_OPT_AUTOTUNE: ctx->autotune = value != 0; return BURGERS_OK;
+    case BURGERS_OPT_LAUNCH_COUNT: ctx->launches = 0; return BURGERS_OK;
+    default: return set_error(BURGERS_EINVAL, "unknown option");
+  }
+}
+
+int64_t burgers_launch_count(const burgers_ctx* ctx) { return ctx ? ctx->launches.load() : 0; }
+
+burgers_status burgers_explicit_advance(burgers_ctx* ctx, const burgers_batch* batch, void* u_dev,
+                                        burgers_stream stream) {
+  return advance(ctx, BURGERS_EXPLICIT, batch, u_dev, reinterpret_cast<cudaStream_t>(stream));
+}
+
+burgers_status burgers_btcs_advance(burgers_ctx* ctx, const burgers_batch* batch, void* u_dev,
+                                    burgers_stream stream) {
+  return advance(ctx, BURGERS_BTCS, batch, u_dev, reinterpret_cast<cudaStream_t>(stream));
+}
+
+}  // extern "C"
+
+namespace burgers {
+
+// Reduction plan: one item per (row, chunk of NORM_CHUNK nodes).
+static burgers_status reduction_setup(burgers_ctx* ctx, const burgers_batch* batch,
+                                      std::vector<RowDesc>* rows, std::vector<TileItem>* items,
+                                      std::vector<int32_t>* first) {
+  rows->clear();
+  items->clear();
+  first->assign(size_t(batch->count) + 1, 0);
+  for (int64_t b = 0; b < batch->count; ++b) {
+    rows->push_back(make_row(batch->inst[b]));
+    (*first)[size_t(b)] = int32_t(items->size());
+    int64_t chunks = (batch->inst[b].n + NORM_CHUNK - 1) / NORM_CHUNK;
+    for (int64_t c = 0; c < chunks; ++c) items->push_back(TileItem{int32_t(b), int32_t(c)});
+  }
+  (*first)[size_t(batch->count)] = int32_t(items->size());
+  (void)ctx;
+  return BURGERS_OK;
+}
+
+// Uploads a reduction plan into the context's reduction workspace.
+static burgers_status reduction_upload(burgers_ctx* ctx, const std::vector<RowDesc>& rows,
+                                       const std::vector<TileItem>& items,
+                                       const std::vector<int32_t>& first, size_t extra_bytes,
+                                       const void* extra, cudaStream_t st, char** base_out) {
+  auto align = [](size_t x) { return (x + 255) & ~size_t(255); };
+  size_t o_rows = 0;
+  size_t o_items = align(rows.size() * sizeof(RowDesc));
+  size_t o_first = align(o_items + items.size() * sizeof(TileItem));
+  size_t o_extra = align(o_first + first.size() * sizeof(int32_t));
+  size_t o_partial = align(o_extra + extra_bytes);
+  size_t o_out = align(o_partial + items.size() * sizeof(double2));
+  size_t total = align(o_out + 2 * rows.size() * sizeof(double));
+  cudaError_t e = ctx->redws.ensure(total);
+  if (e != cudaSuccess) return set_error(BURGERS_ENOMEM, "reduction workspace");
+  e = ctx->redhost.ensure_host(o_partial);
+  if (e != cudaSuccess) return set_error(BURGERS_ENOMEM, "pinned staging");
+  char* h = static_cast<char*>(ctx->redhost.hptr);
+  memcpy(h + o_rows, rows.data(), rows.size() * sizeof(RowDesc));
+  memcpy(h + o_items, items.data(), items.size() * sizeof(TileItem));
+  memcpy(h + o_first, first.data(), first.size() * sizeof(int32_t));
+  if (extra_bytes) memcpy(h + o_extra, extra, extra_bytes);
+  e = cudaMemcpyAsync(ctx->redws.ptr, h, o_partial, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return cuda_error(e, "reduction upload");
+  *base_out = static_cast<char*>(ctx->redws.ptr);
+  ctx->red_offsets[0] = o_rows;
+  ctx->red_offsets[1] = o_items;
+  ctx->red_offsets[2] = o_first;
+  ctx->red_offsets[3] = o_extra;
+  ctx->red_offsets[4] = o_partial;
+  ctx->red_offsets[5] = o_out;
+  return BURGERS_OK;
+}
+
+cudaError_t HostBuf::ensure_host(size_t need) {
+  if (need <= bytes) return cudaSuccess;
+  if (hptr) cudaFreeHost(hptr);
+  hptr = nullptr;
+  bytes = 0;
+  size_t want = std::max(need, size_t(1) << 16);
+  cudaError_t e = cudaMallocHost(&hptr, want);
+  if (e != cudaSuccess) {
+    hptr = nullptr;
+    return e;
+  }
+  bytes = want;
+  return cudaSuccess;
+}
+
+HostBuf::~HostBuf() {
+  if (hptr) cudaFreeHost(hptr);
+}
+
+}  // namespace burgers
+
+extern "C" {
+
+burgers_status burgers_rel_l2(burgers_ctx* ctx, const burgers_batch* batch, const void* u_dev,
+                              const void* ref_dev, int32_t ref_dtype, double* out_host,
+                              double* rms_host, burgers_stream stream) {
+  if (!ctx) return set_error(BURGERS_EINVAL, "ctx is NULL");
+  burgers_status st = validate_batch(batch, false);
+  if (st != BURGERS_OK) return st;
+  if (batch->count == 0) return BURGERS_OK;
+  if (!u_dev || !ref_dev || !out_host) return set_error(BURGERS_EINVAL, "NULL pointer");
+  if (ref_dtype != BURGERS_F32 && ref_dtype != BURGERS_F64) return set_error(BURGERS_EINVAL, "bad ref dtype");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaSetDevice(ctx->device);
+  if (e != cudaSuccess) return cuda_error(e, "cudaSetDevice");
+  std::vector<RowDesc> rows;
+  std::vector<TileItem> items;
+  std::vector<int32_t> first;
+  reduction_setup(ctx, batch, &rows, &items, &first);
+  char* base = nullptr;
+  st = reduction_upload(ctx, rows, items, first, 0, nullptr, s, &base);
+  if (st != BURGERS_OK) return st;
+  auto* o = ctx->red_offsets;
+  double* rel_d = reinterpret_cast<double*>(base + o[5]);
+  double* rms_d = rel_d + rows.size();
+  e = launch_rel_l2(batch->dtype, ref_dtype, u_dev, ref_dev,
+                    reinterpret_cast<RowDesc*>(base + o[0]), reinterpret_cast<TileItem*>(base + o[1]),
+                    int(items.size()), reinterpret_cast<int32_t*>(base + o[2]), int(rows.size()),
+                    NORM_CHUNK, reinterpret_cast<double2*>(base + o[4]), rel_d, rms_d, s);
+  if (e != cudaSuccess) return cuda_error(e, "rel_l2 launch");
+  ctx->launches += 2;
+  std::vector<double> tmp(2 * rows.size());
+  e = cudaMemcpyAsync(tmp.data(), rel_d, 2 * rows.size() * sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_error(e, "rel_l2");
+  memcpy(out_host, tmp.data(), rows.size() * sizeof(double));
+  if (rms_host) memcpy(rms_host, tmp.data() + rows.size(), rows.size() * sizeof(double));
+  return BURGERS_OK;
+}
+
+burgers_status burgers_cfl_dt(burgers_ctx* ctx, const burgers_batch* batch, const void* u_dev,
+                              double cfl, double* dt_host, burgers_stream stream) {
+  if (!ctx) return set_error(BURGERS_EINVAL, "ctx is NULL");
+  if (!batch || batch->count < 0 || (batch->count > 0 && !batch->inst))
+    return set_error(BURGERS_EINVAL, "bad batch");
+  if (batch->count == 0) return BURGERS_OK;
+  if (!u_dev || !dt_host) return set_error(BURGERS_EINVAL, "NULL pointer");
+  if (!(cfl > 0.0)) return set_error(BURGERS_EINVAL, "cfl must be > 0");
+  // dt and nsteps of the rows are ignored: check the rest with placeholders
+  std::vector<burgers_instance> tmp(batch->inst, batch->inst + batch->count);
+  for (auto& in : tmp) {
+    in.dt = 1.0;
+    in.nsteps = 0;
+  }
+  burgers_batch b2 = *batch;
+  b2.inst = tmp.data();
+  burgers_status st = validate_batch(&b2, false);
+  if (st != BURGERS_OK) return st;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaSetDevice(ctx->device);
+  if (e != cudaSuccess) return cuda_error(e, "cudaSetDevice");
+  std::vector<RowDesc> rows;
+  std::vector<TileItem> items;
+  std::vector<int32_t> first;
+  reduction_setup(ctx, &b2, &rows, &items, &first);
+  std::vector<double2> dxnu(size_t(batch->count));
+  for (int64_t b = 0; b < batch->count; ++b) dxnu[size_t(b)] = make_double2(tmp[b].dx, tmp[b].nu);
+  char* base = nullptr;
+  st = reduction_upload(ctx, rows, items, first, dxnu.size() * sizeof(double2), dxnu.data(), s, &base);
+  if (st != BURGERS_OK) return st;
+  auto* o = ctx->red_offsets;
+  double* dt_d = reinterpret_cast<double*>(base + o[5]);
+  e = launch_cfl(batch->dtype, u_dev, reinterpret_cast<RowDesc*>(base + o[0]),
+                 reinterpret_cast<TileItem*>(base + o[1]), int(items.size()),
+                 reinterpret_cast<int32_t*>(base + o[2]), reinterpret_cast<double2*>(base + o[3]),
+                 int(rows.size()), NORM_CHUNK, cfl, reinterpret_cast<double*>(base + o[4]), dt_d, s);
+  if (e != cudaSuccess) return cuda_error(e, "cfl launch");
+  ctx->launches += 2;
+  e = cudaMemcpyAsync(dt_host, dt_d, rows.size() * sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_error(e, "cfl_dt");
+  for (size_t b = 0; b < rows.size(); ++b)
+    if (dt_host[b] < 0) return set_error(BURGERS_EINVAL, "a row has no finite CFL limit");
+  return BURGERS_OK;
+}
+
+burgers_status burgers_solve_host(burgers_ctx* ctx, int32_t scheme, const burgers_batch* batch,
+                                  void* u_host, burgers_stream stream) {
+  if (!ctx) return set_error(BURGERS_EINVAL, "ctx is NULL");
+  if (scheme != BURGERS_EXPLICIT && scheme != BURGERS_BTCS) return set_error(BURGERS_EINVAL, "bad scheme");
+  burgers_status st = validate_batch(batch, false);
+  if (st != BURGERS_OK) return st;
+  if (batch->count == 0) return BURGERS_OK;
+  if (!u_host) return set_error(BURGERS_EINVAL, "u_host is NULL");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaSetDevice(ctx->device);
+  if (e != cudaSuccess) return cuda_error(e, "cudaSetDevice");
+  const size_t esz = batch->dtype == BURGERS_F32 ? 4 : 8;
+  int64_t lo = INT64_MAX, hi = 0;
+  std::vector<std::pair<int64_t, int64_t>> spans;
+  for (int64_t b = 0; b < batch->count; ++b) {
+    lo = std::min<int64_t>(lo, batch->inst[b].offset);
+    hi = std::max<int64_t>(hi, batch->inst[b].offset + batch->inst[b].n);
+    spans.emplace_back(batch->inst[b].offset, batch->inst[b].offset + batch->inst[b].n);
+  }
+  std::sort(spans.begin(), spans.end());
+  std::vector<std::pair<int64_t, int64_t>> runs;  // merged contiguous spans
+  for (auto& sp : spans) {
+    if (!runs.empty() && runs.back().second == sp.first) runs.back().second = sp.second;
+    else runs.push_back(sp);
+  }
+  e = ctx->iobuf.ensure(size_t(hi - lo) * esz);
+  if (e != cudaSuccess) return set_error(BURGERS_ENOMEM, "host-solve buffer: out of device memory");
+  std::vector<burgers_instance> shifted(batch->inst, batch->inst + batch->count);
+  for (auto& in : shifted) in.offset -= lo;
+  burgers_batch b2 = *batch;
+  b2.inst = shifted.data();
+  char* dbase = static_cast<char*>(ctx->iobuf.ptr);
+  char* hbase = static_cast<char*>(u_host);
+  for (auto& rn : runs) {
+    e = cudaMemcpyAsync(dbase + (rn.first - lo) * esz, hbase + rn.first * esz,
+                        size_t(rn.second - rn.first) * esz, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_error(e, "solve_host H2D");
+  }
+  st = advance(ctx, scheme, &b2, dbase, s);
+  if (st != BURGERS_OK) return st;
+  for (auto& rn : runs) {
+    e = cudaMemcpyAsync(hbase + rn.first * esz, dbase + (rn.first - lo) * esz,
+                        size_t(rn.second - rn.first) * esz, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return cuda_error(e, "solve_host D2H");
+  }
+  e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_error(e, "solve_host sync");
+  return BURGERS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,119 @@
+// api_internal.h -- host-side state of libburgers shared by its translation
+// units (context, plans, workspaces).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+#include <list>
+#include <map>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/burgers.h"
+#include "kernels.h"
+
+namespace burgers {
+
+burgers_status set_error(burgers_status st, const std::string& msg);
+burgers_status cuda_error(cudaError_t e, const char* where);
+burgers_status validate_batch(const burgers_batch* batch, bool allow_empty);
+
+// Growable device allocation; `generation` changes whenever the pointer does.
+struct DevBuf {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+  uint64_t generation = 0;
+  cudaError_t ensure(size_t need);
+  ~DevBuf();
+};
+
+// Growable pinned host allocation.
+struct HostBuf {
+  void* hptr = nullptr;
+  size_t bytes = 0;
+  cudaError_t ensure_host(size_t need);
+  ~HostBuf();
+};
+
+enum LaunchType : int { LAUNCH_RESIDENT = 0, LAUNCH_STREAM = 1, LAUNCH_ML = 2 };
+
+struct Launch {
+  const KernelEntry* k = nullptr;
+  int type = LAUNCH_RESIDENT;
+  int grid = 1;
+  int row_begin = 0, row_count = 0;
+  int counter = -1;
+  int item_begin = 0, item_count = 0;
+  int K = 0;
+  int64_t step_base = 0;
+  bool to_scratch = false;
+  int level = 0;   // multi-level: level of a reduce/recover launch
+  int ml_phase = 0;
+};
+
+struct Plan {
+  uint64_t key = 0;
+  int64_t count = 0;
+  int dtype = 0, scheme = 0;
+  std::vector<RowDesc> rows;
+  std::vector<TileItem> items;
+  std::vector<unsigned char> ml_bytes;  // multi-level row descriptors
+  int ml_rows = 0;
+  std::vector<Launch> launches;
+  int ncounters = 0;
+  int64_t kernel_launches = 0;
+  int64_t scratch_elems = 0;  // streaming ping-pong buffer, elements
+  int64_t ml_ws_elems = 0;    // multi-level workspace, elements
+  void* dev = nullptr;
+  size_t rows_off = 0, items_off = 0, counters_off = 0, ml_off = 0, dev_bytes = 0;
+  cudaGraphExec_t gexec = nullptr;
+  void* g_u = nullptr;
+  uint64_t g_scratch_gen = 0, g_ml_gen = 0;
+  ~Plan();
+};
+
+struct TuneVal {
+  int nt = 0, c = 0, k = 0;
+};
+
+inline uint64_t tune_key(int kind, int dtype, int64_t cap, int exact) {
+  return (uint64_t(kind) << 56) ^ (uint64_t(dtype) << 52) ^ (uint64_t(exact) << 48) ^ uint64_t(cap);
+}
+
+}  // namespace burgers
+
+struct burgers_ctx {
+  int device = 0;
+  int sm_count = 1;
+  size_t smem_optin = 0;
+  bool graphs = true;
+  bool plain = false;
+  bool autotune = false;
+  int stream_k = 0;
+  int64_t resident_max = 0;
+  int tune_version = 0;
+  std::atomic<int64_t> launches{0};
+  cudaStream_t capture_stream = nullptr;
+  std::list<std::unique_ptr<burgers::Plan>> plans;
+  std::map<uint64_t, burgers::TuneVal> tuned;
+  burgers::DevBuf scratch;  // streaming ping-pong
+  burgers::DevBuf mlws;     // multi-level reduced systems
+  burgers::DevBuf redws;    // reductions
+  burgers::DevBuf iobuf;    // burgers_solve_host
+  burgers::HostBuf redhost;
+  size_t red_offsets[6] = {0, 0, 0, 0, 0, 0};
+  burgers_ctx();
+  ~burgers_ctx();
+};
+
+namespace burgers {
+burgers_status plan_multilevel(burgers_ctx* ctx, const burgers_batch* batch,
+                               const std::vector<int64_t>& longs, Plan* p);
+cudaError_t enqueue_multilevel_launch(burgers_ctx* ctx, Plan* p, const Launch& L, void* u,
+                                      cudaStream_t st);
+burgers_status advance(burgers_ctx* ctx, int scheme, const burgers_batch* batch, void* u_dev,
+                       cudaStream_t stream);
+}  // namespace burgers

@@ -1,0 +1,76 @@
+// common.cuh -- device-side types and helpers shared by the libburgers kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace burgers {
+
+constexpr unsigned FULL_MASK = 0xffffffffu;
+
+// Per-row launch record, packed on the host from burgers_instance.
+// r = dt/dx and s = nu dt/dx^2 are formed in FP64 on the host.
+struct RowDesc {
+  int64_t offset;  // first element of the row
+  int64_t nsteps;  // steps to advance
+  double r;        // dt / dx
+  double s;        // nu dt / dx^2
+  double ds_dnu;   // dt / dx^2 (derivative of s with respect to nu)
+  int32_t n;       // nodes
+  int32_t bc;      // 0 periodic, 1 Dirichlet
+};
+
+enum : int32_t { BC_PERIODIC = 0, BC_DIRICHLET = 1 };
+
+__device__ __forceinline__ float tfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double tfma(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float tabs(float x) { return fabsf(x); }
+__device__ __forceinline__ double tabs(double x) { return fabs(x); }
+__device__ __forceinline__ float tmax(float a, float b) { return fmaxf(a, b); }
+__device__ __forceinline__ double tmax(double a, double b) { return fmax(a, b); }
+__device__ __forceinline__ float tmin(float a, float b) { return fminf(a, b); }
+__device__ __forceinline__ double tmin(double a, double b) { return fmin(a, b); }
+
+// Reciprocal used in the tridiagonal eliminations. Every pivot there is >= 1
+// (the BTCS matrices are diagonally dominant by a margin of one, and so are
+// their Schur complements), so the FP32 hardware approximation (relative error
+// about 2^-23 on normal inputs) is safe; FP64 uses the IEEE division.
+__device__ __forceinline__ float recip(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ double recip(double x) { return 1.0 / x; }
+
+template <typename T>
+__device__ __forceinline__ T shfl(T v, int src) {
+  return __shfl_sync(FULL_MASK, v, src);
+}
+template <typename T>
+__device__ __forceinline__ T shfl_up(T v, int d) {
+  return __shfl_up_sync(FULL_MASK, v, d);
+}
+template <typename T>
+__device__ __forceinline__ T shfl_down(T v, int d) {
+  return __shfl_down_sync(FULL_MASK, v, d);
+}
+
+// One explicit forward-Euler upwind/central update of node value u with left
+// and right neighbours ul, ur (Eq. 21 with the upwind side of Sec. 2.2):
+//   u' = u - r (u+ (u - ul) + u- (ur - u)) + s (ur - 2u + ul).
+// Using u+ = (u + |u|)/2 and u- = (u - |u|)/2 this is
+//   u' = u - h u (ur - ul) + (s + h |u|) (ur - 2u + ul),   h = r/2,
+// seven FP instructions per node (|u| is an operand modifier, and dl of node
+// i is dr of node i-1).
+template <typename T>
+__device__ __forceinline__ T explicit_update(T u, T ul, T ur, T h, T s) {
+  T dr = ur - u;
+  T dl = u - ul;
+  T d2 = dr - dl;
+  T d1 = dr + dl;
+  T c = tfma(h, tabs(u), s);
+  T w = tfma(-h * u, d1, u);
+  return tfma(c, d2, w);
+}
+
+}  // namespace burgers

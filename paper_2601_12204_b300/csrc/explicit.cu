@@ -1,0 +1,255 @@
+// explicit.cu -- explicit forward-Euler upwind/central kernels (Eq. 21,
+// upwind side by the sign of u_i as in Sec. 2.2).
+//
+// Layout: thread t of a CTA holds C consecutive nodes of a row in registers.
+// Neighbour values cross lanes by warp shuffles and cross warps through a
+// double-buffered shared-memory slot per warp, so one step costs one
+// __syncthreads (none for single-warp rows) and seven FP instructions per node.
+//
+//  * k_explicit_resident: the whole row lives in registers for all of its
+//    steps (the paper's time loop runs inside the kernel). CTAs are
+//    persistent and take rows from an atomic counter over a host list sorted
+//    by cost, so one launch drains thousands of uneven rows.
+//  * k_explicit_stream: rows too long to stay resident. A CTA loads a window
+//    of W = NT*C nodes, advances it K steps (the valid region shrinks by one
+//    node per side per step: trapezoidal temporal blocking) and writes the
+//    central W - 2K nodes, so a pass costs about 2*sizeof(T) bytes of HBM per
+//    node for K steps.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace burgers {
+
+enum : int { MODE_EXACT = 0, MODE_RAGGED = 1, MODE_WINDOW = 2, MODE_WINDOW_DIR = 3 };
+
+// Advances the C nodes held by this thread `nsteps` steps.
+//   MODE_EXACT      row length n == NT*C; periodic wrap through the halo slots.
+//   MODE_RAGGED     n < NT*C; nodes >= n are inert padding, the periodic wrap
+//                   pairs node 0 with node n-1 explicitly.
+//   MODE_WINDOW     streaming window; its two edges go stale one node per step.
+//   MODE_WINDOW_DIR streaming window that contains a Dirichlet end node.
+// gbase is the row index of this thread's first node.
+template <typename T, int NT, int C, int MODE, int BCT>
+__device__ __forceinline__ void explicit_steps(T (&v)[C], int64_t nsteps, T h, T s, int n,
+                                               int64_t gbase, T* sh_last, T* sh_first,
+                                               T* sh_wrap) {
+  constexpr int NW = NT / 32;
+  constexpr bool WRAPX = (MODE == MODE_RAGGED && BCT == BC_PERIODIC);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int jstar = int(n - 1 - gbase);  // local index of node n-1 (resident modes)
+  for (int64_t k = 0; k < nsteps; ++k) {
+    const int p = int(k & 1);
+    const T first = v[0], last = v[C - 1];
+    T left = shfl(last, (lane + 31) & 31);
+    T right = shfl(first, (lane + 1) & 31);
+    if constexpr (NW > 1) {
+      if (lane == 31) sh_last[p * NW + warp] = last;
+      if (lane == 0) sh_first[p * NW + warp] = first;
+    }
+    if constexpr (WRAPX) {
+      if (jstar >= 0 && jstar < C) {
+        T sel = v[0];
+#pragma unroll
+        for (int j = 1; j < C; ++j)
+          if (j == jstar) sel = v[j];
+        sh_wrap[p * 2 + 0] = sel;
+      }
+      if (tid == 0) sh_wrap[p * 2 + 1] = first;
+    }
+    if constexpr (NW > 1 || WRAPX) __syncthreads();
+    if constexpr (NW > 1) {
+      if (lane == 0) left = sh_last[p * NW + (warp + NW - 1) % NW];
+      if (lane == 31) right = sh_first[p * NW + (warp + 1) % NW];
+    }
+    T wrapL = T(0), wrapR = T(0);
+    if constexpr (WRAPX) {
+      wrapL = sh_wrap[p * 2 + 0];
+      wrapR = sh_wrap[p * 2 + 1];
+    }
+    T prev = left;
+#pragma unroll
+    for (int j = 0; j < C; ++j) {
+      const T cur = v[j];
+      T ul = prev;
+      T ur = (j + 1 < C) ? v[j + 1] : right;
+      if constexpr (WRAPX) {
+        if (j == 0 && tid == 0) ul = wrapL;
+        if (j == jstar) ur = wrapR;
+      }
+      T nv = explicit_update(cur, ul, ur, h, s);
+      if constexpr (MODE == MODE_EXACT && BCT == BC_DIRICHLET) {
+        if (j == 0 && tid == 0) nv = cur;
+        if (j == C - 1 && tid == NT - 1) nv = cur;
+      } else if constexpr (MODE == MODE_RAGGED) {
+        bool keep = j > jstar;  // padding
+        if constexpr (BCT == BC_DIRICHLET) keep = keep || j == jstar || (j == 0 && tid == 0);
+        if (keep) nv = cur;
+      } else if constexpr (MODE == MODE_WINDOW_DIR) {
+        const int64_t gi = gbase + j;
+        if (gi == 0 || gi == n - 1) nv = cur;
+      }
+      prev = cur;
+      v[j] = nv;
+    }
+  }
+}
+
+template <typename T, int NT, int C, bool EXACT>
+__global__ void __launch_bounds__(NT) k_explicit_resident(T* __restrict__ u,
+                                                          const RowDesc* __restrict__ rows,
+                                                          int count, int* __restrict__ counter) {
+  constexpr int NW = NT / 32;
+  __shared__ T sh_last[2 * NW], sh_first[2 * NW], sh_wrap[4];
+  __shared__ int s_item;
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
+    __syncthreads();
+    const int item = s_item;
+    if (item >= count) return;
+    const RowDesc rd = rows[item];
+    T* row = u + rd.offset;
+    const int base = threadIdx.x * C;
+    T v[C];
+#pragma unroll
+    for (int j = 0; j < C; ++j) v[j] = (EXACT || base + j < rd.n) ? row[base + j] : T(0);
+    const T h = T(0.5 * rd.r), s = T(rd.s);
+    constexpr int M = EXACT ? MODE_EXACT : MODE_RAGGED;
+    if (rd.bc == BC_PERIODIC)
+      explicit_steps<T, NT, C, M, BC_PERIODIC>(v, rd.nsteps, h, s, rd.n, base, sh_last, sh_first,
+                                               sh_wrap);
+    else
+      explicit_steps<T, NT, C, M, BC_DIRICHLET>(v, rd.nsteps, h, s, rd.n, base, sh_last,
+                                                sh_first, sh_wrap);
+#pragma unroll
+    for (int j = 0; j < C; ++j)
+      if (EXACT || base + j < rd.n) row[base + j] = v[j];
+    __syncthreads();
+  }
+}
+
+template <typename T>
+struct Vec2;
+template <>
+struct Vec2<float> {
+  using type = float4;
+  static constexpr int width = 4;
+};
+template <>
+struct Vec2<double> {
+  using type = double2;
+  static constexpr int width = 2;
+};
+
+template <typename T, int C>
+__device__ __forceinline__ void load_vec(T (&v)[C], const T* p) {
+  using V = typename Vec2<T>::type;
+  constexpr int Wd = Vec2<T>::width;
+  static_assert(C % Wd == 0, "C must be a multiple of the vector width");
+#pragma unroll
+  for (int q = 0; q < C / Wd; ++q) {
+    V x = __ldg(reinterpret_cast<const V*>(p) + q);
+    if constexpr (Wd == 4) {
+      v[4 * q + 0] = x.x; v[4 * q + 1] = x.y; v[4 * q + 2] = x.z; v[4 * q + 3] = x.w;
+    } else {
+      v[2 * q + 0] = x.x; v[2 * q + 1] = x.y;
+    }
+  }
+}
+
+// Streaming window kernel. Pass `step_base` advances every row by
+// min(K, nsteps - step_base) steps from src into dst (rows already done are
+// copied through, so src/dst stay consistent for the ping-pong).
+template <typename T, int NT, int C>
+__global__ void __launch_bounds__(NT) k_explicit_stream(const T* __restrict__ src,
+                                                        T* __restrict__ dst,
+                                                        const RowDesc* __restrict__ rows,
+                                                        const TileItem* __restrict__ items,
+                                                        int nitems, int K, int64_t step_base) {
+  constexpr int NW = NT / 32;
+  constexpr int W = NT * C;
+  __shared__ T sh_last[2 * NW], sh_first[2 * NW], sh_wrap[4];
+  const int O = W - 2 * K;
+  const int base = threadIdx.x * C;
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const TileItem ti = items[it];
+    const RowDesc rd = rows[ti.row];
+    const int64_t n = rd.n;
+    const int64_t out_lo = int64_t(ti.tile) * O;
+    const int64_t out_hi = min(out_lo + O, n);
+    const int64_t ws = out_lo - K;
+    const int64_t rem = rd.nsteps - step_base;
+    const int kk = rem <= 0 ? 0 : (rem < K ? int(rem) : K);
+    const T* srow = src + rd.offset;
+    T* drow = dst + rd.offset;
+    if (kk == 0) {
+      for (int64_t g = out_lo + threadIdx.x; g < out_hi; g += NT) drow[g] = srow[g];
+      continue;
+    }
+    T v[C];
+    const int64_t g0 = ws + base;
+    const bool interior = ws >= 0 && ws + W <= n;
+    const bool aligned = (reinterpret_cast<uintptr_t>(srow + ws) & 15) == 0;
+    if (interior && aligned && (C % Vec2<T>::width == 0)) {
+      load_vec<T, C>(v, srow + g0);
+    } else {
+#pragma unroll
+      for (int j = 0; j < C; ++j) {
+        int64_t gi = g0 + j;
+        if (rd.bc == BC_PERIODIC) {
+          gi %= n;
+          if (gi < 0) gi += n;
+        } else {
+          gi = gi < 0 ? 0 : (gi >= n ? n - 1 : gi);
+        }
+        v[j] = srow[gi];
+      }
+    }
+    const T h = T(0.5 * rd.r), s = T(rd.s);
+    const bool has_end = rd.bc == BC_DIRICHLET && ((ws <= 0 && ws + W > 0) ||
+                                                   (ws <= n - 1 && ws + W > n - 1));
+    if (has_end)
+      explicit_steps<T, NT, C, MODE_WINDOW_DIR, BC_DIRICHLET>(v, kk, h, s, int(n), g0, sh_last,
+                                                              sh_first, sh_wrap);
+    else
+      explicit_steps<T, NT, C, MODE_WINDOW, BC_PERIODIC>(v, kk, h, s, int(n), g0, sh_last,
+                                                         sh_first, sh_wrap);
+#pragma unroll
+    for (int j = 0; j < C; ++j) {
+      const int w = base + j;
+      const int64_t gi = ws + w;
+      if (w >= K && w < K + O && gi < out_hi) drow[gi] = v[j];
+    }
+    __syncthreads();
+  }
+}
+
+#define REG_RES(T, DT, NT, C)                                                               \
+  reg.push_back({K_EXPLICIT_RESIDENT, DT, NT, C, 1,                                         \
+                 reinterpret_cast<const void*>(&k_explicit_resident<T, NT, C, true>), 0});  \
+  reg.push_back({K_EXPLICIT_RESIDENT, DT, NT, C, 0,                                         \
+                 reinterpret_cast<const void*>(&k_explicit_resident<T, NT, C, false>), 0});
+#define REG_STREAM(T, DT, NT, C)        \
+  reg.push_back({K_EXPLICIT_STREAM, DT, NT, C, 0, \
+                 reinterpret_cast<const void*>(&k_explicit_stream<T, NT, C>), 0});
+
+void register_explicit(std::vector<KernelEntry>& reg) {
+  // FP32 resident shapes (capacity NT*C nodes)
+  REG_RES(float, 0, 32, 1) REG_RES(float, 0, 32, 2) REG_RES(float, 0, 32, 4)
+  REG_RES(float, 0, 32, 8) REG_RES(float, 0, 64, 8) REG_RES(float, 0, 128, 8)
+  REG_RES(float, 0, 64, 16) REG_RES(float, 0, 128, 16) REG_RES(float, 0, 256, 8)
+  REG_RES(float, 0, 256, 16) REG_RES(float, 0, 128, 32) REG_RES(float, 0, 512, 8)
+  REG_RES(float, 0, 512, 16) REG_RES(float, 0, 256, 32) REG_RES(float, 0, 1024, 16)
+  REG_RES(float, 0, 1024, 32)
+  // FP64 resident shapes
+  REG_RES(double, 1, 32, 1) REG_RES(double, 1, 32, 2) REG_RES(double, 1, 32, 4)
+  REG_RES(double, 1, 32, 8) REG_RES(double, 1, 64, 8) REG_RES(double, 1, 128, 8)
+  REG_RES(double, 1, 256, 8) REG_RES(double, 1, 128, 16) REG_RES(double, 1, 512, 8)
+  REG_RES(double, 1, 256, 16) REG_RES(double, 1, 1024, 8) REG_RES(double, 1, 512, 16)
+  // streaming window shapes
+  REG_STREAM(float, 0, 32, 4) REG_STREAM(float, 0, 128, 16) REG_STREAM(float, 0, 256, 16)
+  REG_STREAM(float, 0, 512, 16) REG_STREAM(float, 0, 256, 32)
+  REG_STREAM(double, 1, 32, 4) REG_STREAM(double, 1, 128, 8) REG_STREAM(double, 1, 256, 8)
+  REG_STREAM(double, 1, 256, 16)
+}
+
+}  // namespace burgers

@@ -1,0 +1,302 @@
+"""GPU parity: the CUDA path against the FP64 oracle on the same seeded inputs."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from gpu_helpers import (BTCS, EXPLICIT, F32, F64, assert_parity, oracle_dts, run_gpu,
+                         run_oracle)
+from paper_2601_12204_b300 import _lib as L
+from paper_2601_12204_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+SCHEMES = [EXPLICIT, BTCS]
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2601_12204_b300.api import Context
+    c = Context(0)
+    yield c
+    c.close()
+
+
+def _fresh(ctx):
+    for opt, val in ((L.BURGERS_OPT_RESIDENT_MAX, 0), (L.BURGERS_OPT_PLAIN, 0),
+                     (L.BURGERS_OPT_GRAPHS, 1), (L.BURGERS_OPT_STREAM_K, 0)):
+        ctx.set(opt, val)
+
+
+@pytest.mark.parametrize("scheme", SCHEMES)
+@pytest.mark.parametrize("dtype", [F64, F32])
+def test_config1_plain_sine(ctx, scheme, dtype):
+    """N = 256 Dirichlet, u0 = -sin(pi x), nu = 0.01/pi, t_f = 1/pi, 102 steps."""
+    _fresh(ctx)
+    e = W.plain_sine(256)
+    dt0 = oracle.cfl_dt(e.u0, e.dxs[0], e.nus[0], 0.4)
+    n = math.ceil(e.meta["t_final"] / dt0)
+    dts = np.array([e.meta["t_final"] / n])
+    assert n == 102
+    got = run_gpu(ctx, scheme, e, dts, n, dtype)
+    ref = run_oracle(scheme, e, dts, n)
+    assert_parity(e, got, ref, dtype, "cfg1")
+    # the odd initial condition stays odd on the GPU too
+    assert np.max(np.abs(got + got[::-1])) <= (1e-13 if dtype == F64 else 1e-6)
+
+
+@pytest.mark.parametrize("scheme", SCHEMES)
+@pytest.mark.parametrize("dtype", [F64, F32])
+@pytest.mark.parametrize("bc", [W.PERIODIC, W.DIRICHLET])
+def test_exact_shapes(ctx, scheme, dtype, bc):
+    """Row lengths equal to every resident register capacity (no padding)."""
+    _fresh(ctx)
+    ns = [32, 64, 128, 256, 512, 1024, 2048, 4096]
+    if scheme == EXPLICIT:
+        ns += [8192, 16384] if dtype == F64 else [8192, 16384, 32768]
+    else:
+        ns += [8192] if dtype == F32 else []
+    rows = []
+    for n in ns:
+        e = W.fourier_ensemble(2, n, seed=n)
+        e.bcs[:] = bc
+        rows.append(e)
+    ens = _concat(rows)
+    dts = oracle_dts(ens, 1.0 if scheme == EXPLICIT else 10.0)
+    steps = np.where(ens.ns > 4096, 40, 150)
+    got = run_gpu(ctx, scheme, ens, dts, steps, dtype)
+    ref = run_oracle(scheme, ens, dts, steps)
+    assert_parity(ens, got, ref, dtype, f"exact s{scheme} bc{bc}")
+
+
+@pytest.mark.parametrize("scheme", SCHEMES)
+@pytest.mark.parametrize("dtype", [F64, F32])
+def test_ragged_mixed_batch(ctx, scheme, dtype):
+    """Uneven rows (n from 3 to several thousand, both BCs, ragged step counts)
+    in one call, including lengths just above and below shape capacities."""
+    _fresh(ctx)
+    nmax = 6000 if (scheme == EXPLICIT or dtype == F32) else 4000
+    ens = W.mixed_ensemble(60, 3, nmax, seed=77)
+    extra = [3, 4, 5, 31, 33, 63, 65, 255, 257, 1023, 1025, 4095, 4097 if nmax > 4097 else 3999]
+    ens = _concat([ens] + [_one(n, bc, seed=n + bc) for n in extra for bc in (0, 1)])
+    dts = oracle_dts(ens, 1.0 if scheme == EXPLICIT else 7.0)
+    g = np.random.default_rng(5)
+    steps = g.integers(0, 300, ens.count)
+    got = run_gpu(ctx, scheme, ens, dts, steps, dtype)
+    ref = run_oracle(scheme, ens, dts, steps)
+    assert_parity(ens, got, ref, dtype, f"ragged s{scheme}")
+
+
+@pytest.mark.parametrize("dtype", [F64, F32])
+@pytest.mark.parametrize("K", [1, 7, 32])
+def test_streaming_explicit(ctx, dtype, K):
+    """Long rows through the temporally blocked streaming kernel (several
+    windows per row, a ragged last window, both BCs, odd and even passes)."""
+    _fresh(ctx)
+    ctx.set(L.BURGERS_OPT_RESIDENT_MAX, 1024)
+    ctx.set(L.BURGERS_OPT_STREAM_K, K)
+    try:
+        ens = _concat([_one(n, bc, seed=n) for n in (5000, 9001, 70001) for bc in (0, 1)])
+        dts = oracle_dts(ens)
+        steps = np.array([3 * K + 1, 2 * K, 97, 64, 150, K])
+        got = run_gpu(ctx, EXPLICIT, ens, dts, steps, dtype)
+        ref = run_oracle(EXPLICIT, ens, dts, steps)
+        assert_parity(ens, got, ref, dtype, f"stream K{K}")
+    finally:
+        _fresh(ctx)
+
+
+def test_gaps_between_rows_untouched(ctx):
+    """Elements outside every row keep their values (streaming and resident)."""
+    import torch
+    _fresh(ctx)
+    ctx.set(L.BURGERS_OPT_RESIDENT_MAX, 1024)
+    try:
+        from paper_2601_12204_b300.api import Batch
+        e = _concat([_one(3000, 0, 1), _one(500, 1, 2)])
+        offs = np.array([10, 3100])
+        buf = np.full(3700, 7.5)
+        for b in range(2):
+            buf[offs[b]:offs[b] + e.ns[b]] = e.row(b)
+        dts = oracle_dts(e)
+        bt = Batch(F64, offs, e.ns, e.bcs, e.dxs, e.nus, dts, [33, 20])
+        u = torch.tensor(buf, device="cuda")
+        ctx.explicit_advance(bt, u)
+        out = u.cpu().numpy()
+        mask = np.ones(buf.size, bool)
+        for b in range(2):
+            mask[offs[b]:offs[b] + e.ns[b]] = False
+        assert np.all(out[mask] == 7.5)
+    finally:
+        _fresh(ctx)
+
+
+@pytest.mark.parametrize("scheme", SCHEMES)
+def test_config2_full_size_sampled(ctx, scheme):
+    """4096 periodic rows x 4096 nodes, FP32 and FP64, 2000 explicit steps at
+    CFL 0.4 or 200 BTCS steps at 10x that dt: sampled rows against the oracle,
+    and every FP32 row against the GPU FP64 result (the FP32 error per row)."""
+    import torch
+    _fresh(ctx)
+    ens = W.fourier_ensemble(4096, 4096, seed=W.DEFAULT_SEED)
+    dts = oracle_dts(ens, 1.0 if scheme == EXPLICIT else 10.0)
+    steps = 2000 if scheme == EXPLICIT else 200
+    g32 = run_gpu(ctx, scheme, ens, dts, steps, F32)
+    g64 = run_gpu(ctx, scheme, ens, dts, steps, F64)
+    ids = np.array([0, 1, 777, 2048, 4095])
+    sub = ens.subset(ids)
+    ref = run_oracle(scheme, sub, dts[ids], steps)
+    for j, b in enumerate(ids):
+        o = int(ens.offsets[b])
+        so = int(sub.offsets[j])
+        r = ref[so:so + 4096]
+        assert oracle.rel_l2(g64[o:o + 4096], r) <= 1e-12
+        assert oracle.rel_l2(g32[o:o + 4096], r) <= 1e-5
+    # FP32 vs FP64 on every row, through the GPU norm kernel
+    from paper_2601_12204_b300.api import Batch
+    b32 = Batch.from_ensemble(ens, dts, steps, F32)
+    rel, _ = ctx.rel_l2(b32, torch.tensor(g32, dtype=torch.float32, device="cuda"),
+                        torch.tensor(g64, device="cuda"))
+    assert float(np.max(rel)) <= 1e-5
+
+
+@pytest.mark.parametrize("scheme", SCHEMES)
+@pytest.mark.parametrize("dtype", [F64, F32])
+def test_degenerate_cases(ctx, scheme, dtype):
+    _fresh(ctx)
+    rows = [_one(3, 0, 1), _one(3, 1, 2), _one(4, 0, 3), _one(700, 0, 4)]
+    ens = _concat(rows)
+    # constant state rows
+    for b, cval in ((2, 1.25),):
+        o = ens.offsets[b]
+        ens.u0[o:o + ens.ns[b]] = cval
+    dts = oracle_dts(ens, 3.0 if scheme == BTCS else 1.0)
+    steps = [5, 5, 9, 0]
+    got = run_gpu(ctx, scheme, ens, dts, steps, dtype)
+    ref = run_oracle(scheme, ens, dts, steps)
+    assert_parity(ens, got, ref, dtype, "degenerate")
+    o = ens.offsets[3]
+    assert np.array_equal(got[o:o + 700], ens.u0[o:o + 700].astype(
+        np.float32 if dtype == F32 else np.float64).astype(np.float64))
+
+
+@pytest.mark.parametrize("scheme", SCHEMES)
+def test_inviscid_rows(ctx, scheme):
+    """nu = 0: pure upwind convection (s = 0)."""
+    _fresh(ctx)
+    ens = _concat([_one(n, bc, seed=n) for n in (100, 1000) for bc in (0, 1)])
+    ens.nus[:] = 0.0
+    dts = oracle_dts(ens, 1.0 if scheme == EXPLICIT else 5.0)
+    got = run_gpu(ctx, scheme, ens, dts, 120, F64)
+    ref = run_oracle(scheme, ens, dts, 120)
+    assert_parity(ens, got, ref, F64, "inviscid")
+
+
+def test_cfl_dt_matches_oracle(ctx):
+    import torch
+    from paper_2601_12204_b300.api import Batch
+    _fresh(ctx)
+    ens = W.mixed_ensemble(40, 3, 40000, seed=9)
+    ens.nus[::3] = 0.0
+    b = Batch.from_ensemble(ens, 1.0, 0, F64)
+    dt = ctx.cfl_dt(b, torch.tensor(ens.u0, device="cuda"), 0.4)
+    ref = np.array([oracle.cfl_dt(ens.row(i), ens.dxs[i], ens.nus[i], 0.4) for i in range(ens.count)])
+    assert np.array_equal(dt, ref)
+
+
+def test_rel_l2_matches_oracle(ctx):
+    import torch
+    from paper_2601_12204_b300.api import Batch
+    _fresh(ctx)
+    ens = W.mixed_ensemble(30, 3, 50000, seed=10)
+    g = np.random.default_rng(0)
+    other = ens.u0 + 1e-3 * g.normal(size=ens.u0.size)
+    b = Batch.from_ensemble(ens, 1.0, 0, F64)
+    rel, rms = ctx.rel_l2(b, torch.tensor(other, device="cuda"), torch.tensor(ens.u0, device="cuda"))
+    for i in range(ens.count):
+        o, n = ens.offsets[i], ens.ns[i]
+        assert rel[i] == pytest.approx(oracle.rel_l2(other[o:o + n], ens.u0[o:o + n]), rel=1e-13)
+        assert rms[i] == pytest.approx(oracle.rms(other[o:o + n], ens.u0[o:o + n]), rel=1e-13)
+    b32 = Batch.from_ensemble(ens, 1.0, 0, F32)
+    rel32, _ = ctx.rel_l2(b32, torch.tensor(other, dtype=torch.float32, device="cuda"),
+                          torch.tensor(ens.u0, device="cuda"))
+    assert np.all(np.abs(rel32 - rel) <= 1e-6 + 1e-3 * rel)
+
+
+@pytest.mark.parametrize("scheme", SCHEMES)
+def test_plain_graphs_and_determinism_are_bitwise(ctx, scheme):
+    """Batched, one-row-per-launch, graph and no-graph runs and repeated runs
+    give bitwise identical results (same kernel shape per row)."""
+    _fresh(ctx)
+    ens = W.mixed_ensemble(25, 3, 3000, seed=12)
+    dts = oracle_dts(ens, 1.0 if scheme == EXPLICIT else 4.0)
+    a = run_gpu(ctx, scheme, ens, dts, 80, F32)
+    b = run_gpu(ctx, scheme, ens, dts, 80, F32)
+    ctx.set(L.BURGERS_OPT_PLAIN, 1)
+    c = run_gpu(ctx, scheme, ens, dts, 80, F32)
+    ctx.set(L.BURGERS_OPT_PLAIN, 0)
+    ctx.set(L.BURGERS_OPT_GRAPHS, 0)
+    d = run_gpu(ctx, scheme, ens, dts, 80, F32)
+    _fresh(ctx)
+    assert np.array_equal(a, b) and np.array_equal(a, c) and np.array_equal(a, d)
+
+
+def test_solve_host_matches_device(ctx):
+    _fresh(ctx)
+    from paper_2601_12204_b300.api import Batch
+    ens = W.mixed_ensemble(12, 10, 2000, seed=13)
+    dts = oracle_dts(ens)
+    dev = run_gpu(ctx, EXPLICIT, ens, dts, 50, F64)
+    host = ens.u0.copy()
+    ctx.solve_host(EXPLICIT, Batch.from_ensemble(ens, dts, 50, F64), host)
+    assert np.array_equal(host, dev)
+
+
+def test_invalid_arguments_rejected(ctx):
+    import torch
+    from paper_2601_12204_b300.api import Batch
+    _fresh(ctx)
+    u = torch.zeros(100, dtype=torch.float64, device="cuda")
+    lib = L.load()
+    bad = [
+        Batch(F64, [0], [2], [0], [0.1], [0.1], [0.01], [1]),        # n < 3
+        Batch(F64, [0], [10], [5], [0.1], [0.1], [0.01], [1]),       # bad bc
+        Batch(F64, [0], [10], [0], [0.0], [0.1], [0.01], [1]),       # dx = 0
+        Batch(F64, [0], [10], [0], [0.1], [-1.0], [0.01], [1]),      # nu < 0
+        Batch(F64, [0], [10], [0], [0.1], [0.1], [0.0], [1]),        # dt = 0
+        Batch(F64, [0], [10], [0], [0.1], [0.1], [0.01], [-1]),      # nsteps < 0
+        Batch(F64, [0, 5], [10, 10], [0, 0], [0.1] * 2, [0.1] * 2, [0.01] * 2, [1, 1]),  # overlap
+    ]
+    before = u.clone()
+    for b in bad:
+        st = lib.burgers_explicit_advance(ctx.h, b.ref(), u.data_ptr(), None)
+        assert st == L.BURGERS_EINVAL, L.last_error()
+        st = lib.burgers_btcs_advance(ctx.h, b.ref(), u.data_ptr(), None)
+        assert st == L.BURGERS_EINVAL
+    ok = Batch(F64, [0], [10], [0], [0.1], [0.1], [0.01], [1])
+    assert lib.burgers_explicit_advance(ctx.h, ok.ref(), None, None) == L.BURGERS_EINVAL
+    assert lib.burgers_explicit_advance(None, ok.ref(), u.data_ptr(), None) == L.BURGERS_EINVAL
+    torch.cuda.synchronize()
+    assert torch.equal(u, before)
+
+
+# ---------------------------------------------------------------------------
+def _one(n, bc, seed):
+    x, dx = W.grid(n, bc, 0.0, W.TWO_PI)
+    a, phi, nu = W.fourier_coeffs(seed, 99)
+    u0 = W.fourier_field(x, a, phi)
+    return W.Ensemble(u0, np.zeros(1, np.int64), np.array([n], np.int32), np.array([bc], np.int32),
+                      np.array([dx]), np.array([nu]), np.zeros(1), np.array([W.TWO_PI]))
+
+
+def _concat(parts):
+    u0 = np.concatenate([p.u0 for p in parts])
+    ns = np.concatenate([p.ns for p in parts])
+    offs = np.zeros(ns.size, np.int64)
+    offs[1:] = np.cumsum(ns[:-1])
+    cat = lambda k: np.concatenate([getattr(p, k) for p in parts])  # noqa: E731
+    return W.Ensemble(u0, offs, ns, cat("bcs"), cat("dxs"), cat("nus"), cat("x0"), cat("length"))
