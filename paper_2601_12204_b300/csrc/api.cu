@@ -242,7 +242,10 @@ static burgers_status build_plan(burgers_ctx* ctx, int scheme, const burgers_bat
   for (int64_t b = 0; b < batch->count; ++b) {
     const burgers_instance& in = batch->inst[b];
     if (in.nsteps == 0) continue;
-    if (in.n > rlim) {
+    // long rows: streaming explicit windows / multi-level BTCS (which needs at
+    // least a few chunks; shorter rows stay resident whatever the limit)
+    const int64_t min_long = scheme == BURGERS_EXPLICIT ? 128 : 64;
+    if (in.n > rlim && in.n >= min_long && in.n > 0) {
       longs.push_back(b);
       continue;
     }

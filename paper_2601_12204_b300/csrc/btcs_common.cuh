@@ -1,0 +1,176 @@
+// btcs_common.cuh -- pieces of the partitioned tridiagonal elimination shared
+// by the resident BTCS kernel and the multi-level solver: the shared-memory
+// layout of a CTA's reduced system and its warp-0 solver (Sherman-Morrison
+// split of the cyclic corners with an FP64 correction, per-lane elimination,
+// parallel cyclic reduction over warp shuffles).
+#pragma once
+
+#include "common.cuh"
+
+namespace burgers {
+
+__device__ __forceinline__ int sk(int i) { return i + (i >> 5); }  // bank skew
+
+template <typename T, int NT>
+struct BtcsShared {
+  static constexpr int SK = NT + NT / 32;
+  T rd[NT], ra[NT], rg[NT];              // first-row relation per chunk; reused for z
+  T A[SK], B[SK], Cc[SK], D[SK], U[SK];  // reduced rows (skewed)
+  T X[NT];                               // chunk-end solution
+};
+
+// Solves the reduced system held in sm (rows 0..NT-1, rows beyond tl are
+// decoupled identities) with warp 0; leaves the solution in sm.X.
+template <typename T, int NT, bool CYC>
+__device__ __forceinline__ void reduced_solve(BtcsShared<T, NT>& sm, int tl, int lane) {
+  constexpr int Q = NT / 32;
+  double fad = 0.0;  // A_0 / gamma of the Sherman-Morrison split, FP64
+  if constexpr (CYC) {
+    const T A0 = sm.A[sk(0)], B0 = sm.B[sk(0)], Ct = sm.Cc[sk(tl)], Bt = sm.B[sk(tl)];
+    const T gam = -B0;
+    fad = double(A0) / double(gam);
+    __syncwarp();
+    if (lane == 0) {
+      sm.B[sk(0)] = B0 - gam;
+      sm.A[sk(0)] = T(0);
+      sm.U[sk(0)] = gam;
+      sm.B[sk(tl)] = Bt - Ct * T(fad);
+      sm.Cc[sk(tl)] = T(0);
+      sm.U[sk(tl)] = Ct;
+    }
+    __syncwarp();
+  }
+  const int r0 = lane * Q;
+  // forward sweep over this lane's Q reduced rows
+  T chp = T(0), ahp = T(-1), dhp = T(0), uhp = T(0);
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    const int i = sk(r0 + q);
+    const T a = sm.A[i], b = sm.B[i], c = sm.Cc[i], d = sm.D[i];
+    const T inv = recip(tfma(-a, chp, b));
+    const T ai = a * inv;
+    chp = c * inv;
+    ahp = -ai * ahp;
+    dhp = tfma(-ai, dhp, d * inv);
+    sm.Cc[i] = chp;
+    sm.A[i] = ahp;
+    sm.D[i] = dhp;
+    if constexpr (CYC) {
+      uhp = tfma(-ai, uhp, sm.U[i] * inv);
+      sm.U[i] = uhp;
+    }
+  }
+  const T e_ch = chp, e_ah = ahp, e_dh = dhp, e_uh = uhp;
+  // backward sweep: rows before the lane's end row, relation to (L, X_end)
+  T cd = T(0), ca = T(0), cg = T(-1), cu = T(0);
+#pragma unroll
+  for (int q = Q - 2; q >= 0; --q) {
+    const int i = sk(r0 + q);
+    const T ch = sm.Cc[i];
+    cd = tfma(-ch, cd, sm.D[i]);
+    ca = tfma(-ch, ca, sm.A[i]);
+    cg = -ch * cg;
+    sm.D[i] = cd;
+    sm.A[i] = ca;
+    sm.Cc[i] = cg;
+    if constexpr (CYC) {
+      cu = tfma(-ch, cu, sm.U[i]);
+      sm.U[i] = cu;
+    }
+  }
+  // next lane's first-row relation
+  T nd = shfl_down(cd, 1), na = shfl_down(ca, 1), ng = shfl_down(cg, 1), nu = shfl_down(cu, 1);
+  if (lane == 31) { nd = T(0); na = T(0); ng = T(0); nu = T(0); }
+  T a32 = e_ah, b32 = T(1) - e_ch * na, c32 = -e_ch * ng;
+  T d32 = tfma(-e_ch, nd, e_dh), u32 = tfma(-e_ch, nu, e_uh);
+  {
+    const T inv = recip(b32);
+    a32 *= inv; c32 *= inv; d32 *= inv; u32 *= inv;
+  }
+  // parallel cyclic reduction over the 32 lanes (non-cyclic after the split)
+#pragma unroll
+  for (int k = 1; k < 32; k <<= 1) {
+    T am = shfl_up(a32, k), cm = shfl_up(c32, k), dm = shfl_up(d32, k);
+    T ap = shfl_down(a32, k), cp = shfl_down(c32, k), dp = shfl_down(d32, k);
+    T um = T(0), up = T(0);
+    if constexpr (CYC) { um = shfl_up(u32, k); up = shfl_down(u32, k); }
+    if (lane < k) { am = T(0); cm = T(0); dm = T(0); um = T(0); }
+    if (lane + k > 31) { ap = T(0); cp = T(0); dp = T(0); up = T(0); }
+    const T inv = recip(T(1) - a32 * cm - c32 * ap);
+    const T na2 = -a32 * am * inv, nc2 = -c32 * cp * inv;
+    const T nd2 = (d32 - a32 * dm - c32 * dp) * inv;
+    if constexpr (CYC) u32 = (u32 - a32 * um - c32 * up) * inv;
+    a32 = na2; c32 = nc2; d32 = nd2;
+  }
+  const T Ye = d32, Ze = u32;
+  T YL = shfl_up(Ye, 1), ZL = shfl_up(Ze, 1);
+  if (lane == 0) { YL = T(0); ZL = T(0); }
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    const int i = sk(r0 + q);
+    T y = Ye, z = Ze;
+    if (q < Q - 1) {
+      y = tfma(-sm.Cc[i], Ye, tfma(-sm.A[i], YL, sm.D[i]));
+      if constexpr (CYC) z = tfma(-sm.Cc[i], Ze, tfma(-sm.A[i], ZL, sm.U[i]));
+    }
+    sm.X[r0 + q] = y;
+    if constexpr (CYC) sm.rd[r0 + q] = z;
+  }
+  if constexpr (CYC) {
+    __syncwarp();
+    // x = y - (v.y)/(1 + v.z) z,  v = e_0 + (A_0/gamma) e_tl
+    const double y0 = double(sm.X[0]), yt = double(sm.X[tl]);
+    const double z0 = double(sm.rd[0]), zt = double(sm.rd[tl]);
+    const double fac = (y0 + fad * yt) / (1.0 + z0 + fad * zt);
+    __syncwarp();
+#pragma unroll
+    for (int q = 0; q < Q; ++q)
+      sm.X[r0 + q] = T(double(sm.X[r0 + q]) - fac * double(sm.rd[r0 + q]));
+  }
+}
+
+// Forward sweep over the C rows of one chunk; rows j > je are inert padding.
+// row(j, l, d, c, rhs) supplies row j. Leaves ch, ah, v = dh per row and the
+// forward outputs of the end row je in e_ch, e_ah, e_dh (zero if je < 0).
+template <typename T, int C, typename RowFn>
+__device__ __forceinline__ void chunk_forward(T (&v)[C], T (&ah)[C], T (&ch)[C], int je, RowFn&& row,
+                                              T& e_ch, T& e_ah, T& e_dh) {
+  T chp = T(0), ahp = T(-1), dhp = T(0);
+  e_ch = T(0); e_ah = T(0); e_dh = T(0);
+#pragma unroll
+  for (int j = 0; j < C; ++j) {
+    T l, d, c, rhs;
+    row(j, l, d, c, rhs);
+    if (j > je) { l = T(0); c = T(0); d = T(1); rhs = T(0); }
+    const T inv = recip(tfma(-l, chp, d));
+    const T li = l * inv;
+    chp = c * inv;
+    ahp = -li * ahp;
+    dhp = tfma(-li, dhp, rhs * inv);
+    ch[j] = chp;
+    ah[j] = ahp;
+    v[j] = dhp;
+    if (j == je) { e_ch = chp; e_ah = ahp; e_dh = dhp; }
+  }
+}
+
+// Backward sweep: rows before the end row je become x_j = v_j - ah_j L - ch_j X
+// (delta, alpha, gamma); the end row is x = X; padding rows become 0.
+template <typename T, int C>
+__device__ __forceinline__ void chunk_backward(T (&v)[C], T (&ah)[C], T (&ch)[C], int je) {
+  T cd = T(0), ca = T(0), cg = T(-1);
+#pragma unroll
+  for (int j = C - 1; j >= 0; --j) {
+    const T cj = ch[j];
+    T nd = tfma(-cj, cd, v[j]);
+    T na = tfma(-cj, ca, ah[j]);
+    T ng = -cj * cg;
+    const bool past = j > je, at = j == je;
+    if (past || at) { nd = T(0); na = T(0); ng = at ? T(-1) : T(0); }
+    v[j] = nd; ah[j] = na; ch[j] = ng;
+    if (past || at) { cd = T(0); ca = T(0); cg = T(-1); }
+    else { cd = nd; ca = na; cg = ng; }
+  }
+}
+
+}  // namespace burgers

@@ -1,22 +1,360 @@
-// multilevel.cu -- multi-level partitioned BTCS solver for rows too long to
-// stay resident in one CTA (filled in below).
+// multilevel.cu -- BTCS (Sec. 2.4, Eq. 23) for rows too long to stay resident
+// in one CTA, e.g. the N = 2^24 periodic grid.
+//
+// The partitioned elimination of btcs.cu applied recursively through global
+// memory. Level 0 holds the n nodes; every chunk of C consecutive rows of
+// level l is eliminated by one thread and leaves six numbers: the forward
+// outputs of its end row (ch, ah, dh) and the relation of its first row
+// (delta, alpha, gamma). Chunk k of level l is row k of level l+1:
+//     A_k = ah_k,  B_k = 1 - ch_k alpha_{k+1},  C_k = -ch_k gamma_{k+1},
+//     D_k = dh_k - ch_k delta_{k+1}               (k+1 taken cyclically),
+// so level l+1 has ceil(m_l / C) rows and is again (cyclic) tridiagonal. Once
+// a level fits one CTA, k_ml_top solves it like the resident kernel
+// (Sherman-Morrison split of the cyclic corners, FP64 correction). The
+// recover sweeps then walk back down: each chunk repeats its elimination
+// (nothing per row is stored, which halves the memory traffic) and forms
+//     x_j = delta_j - alpha_j X_{k-1} - gamma_j X_k
+// from the two solved chunk-end values. Level 0 reads u^n and writes u^{n+1}
+// in place: each thread reads and writes only its own nodes.
+//
+// Per step: L reduce launches, one top launch per top shape, L recover
+// launches; the host captures the whole step sequence in a CUDA graph.
+#include <algorithm>
+
 #include "api_internal.h"
+#include "btcs_common.cuh"
+#include "common.cuh"
 #include "kernels.h"
 
 namespace burgers {
 
-void register_multilevel(std::vector<KernelEntry>& reg) { (void)reg; }
+constexpr int ML_MAXL = 6;
+
+struct MLRow {
+  int64_t offset;
+  int64_t nsteps;
+  double r, s;
+  int32_t n, bc, levels, pad;
+  int64_t m[ML_MAXL + 1];   // rows per level, m[0] = n
+  int64_t ef[ML_MAXL];      // workspace offset of the six chunk arrays of level l
+  int64_t x[ML_MAXL + 1];   // workspace offset of the solution of level l >= 1
+};
+
+// Row j of level `level` (>= 1) from the chunk arrays of the level below.
+template <typename T>
+struct UpperRows {
+  const T* E;
+  int64_t M;
+  int64_t base;
+  int je;
+  __device__ __forceinline__ void operator()(int j, T& l, T& d, T& c, T& rhs) const {
+    if (j > je) { l = T(0); d = T(1); c = T(0); rhs = T(0); return; }
+    const int64_t i = base + j;
+    const int64_t i1 = (i + 1 == M) ? 0 : i + 1;
+    const T ech = E[i], eah = E[M + i], edh = E[2 * M + i];
+    const T fd = E[3 * M + i1], fa = E[4 * M + i1], fg = E[5 * M + i1];
+    l = eah;
+    d = T(1) - ech * fa;
+    c = -ech * fg;
+    rhs = tfma(-ech, fd, edh);
+  }
+};
+
+// Level-0 rows: lagged upwind BTCS coefficients assembled from u^n.
+template <typename T>
+struct NodeRows {
+  const T* row;
+  int64_t n;
+  int64_t base;
+  int je;
+  T r, s, ds1;
+  bool dir;
+  __device__ __forceinline__ void operator()(int j, T& l, T& d, T& c, T& rhs) const {
+    const int64_t gi = base + j;
+    const T a = (j <= je) ? row[gi] : T(0);
+    const T ra = r * a;
+    l = -s - tmax(ra, T(0));
+    c = tmin(ra, T(0)) - s;
+    d = ds1 + tabs(ra);
+    rhs = a;
+    if (dir && (gi == 0 || gi == n - 1)) { l = T(0); c = T(0); d = T(1); }
+  }
+};
+
+template <typename T, int NT, int C, bool LVL0, bool RECOVER>
+__global__ void __launch_bounds__(NT) k_ml_sweep(T* __restrict__ u, T* __restrict__ ws,
+                                                 const MLRow* __restrict__ rows,
+                                                 const TileItem* __restrict__ items, int nitems,
+                                                 int level, int64_t step) {
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const TileItem ti = items[it];
+    const MLRow& R = rows[ti.row];
+    if (step >= R.nsteps) continue;
+    const int64_t M = R.m[level];
+    const int64_t base = int64_t(ti.tile) * (NT * C) + int64_t(threadIdx.x) * C;
+    if (base >= M) continue;
+    const int je = int(M - 1 - base < int64_t(C - 1) ? M - 1 - base : int64_t(C - 1));
+    T v[C], ah[C], ch[C];
+    T e_ch, e_ah, e_dh;
+    if constexpr (LVL0) {
+      const T s = T(R.s);
+      NodeRows<T> src{u + R.offset, M, base, je, T(R.r), s, T(1) + T(2) * s,
+                      R.bc == BC_DIRICHLET};
+      chunk_forward<T, C>(v, ah, ch, je, src, e_ch, e_ah, e_dh);
+    } else {
+      UpperRows<T> src{ws + R.ef[level - 1], M, base, je};
+      chunk_forward<T, C>(v, ah, ch, je, src, e_ch, e_ah, e_dh);
+    }
+    chunk_backward<T, C>(v, ah, ch, je);
+    const int64_t k = base / C;
+    const int64_t Mn = R.m[level + 1];
+    if constexpr (!RECOVER) {
+      T* Eo = ws + R.ef[level];
+      Eo[k] = e_ch;
+      Eo[Mn + k] = e_ah;
+      Eo[2 * Mn + k] = e_dh;
+      Eo[3 * Mn + k] = v[0];
+      Eo[4 * Mn + k] = ah[0];
+      Eo[5 * Mn + k] = ch[0];
+    } else {
+      const T* Xn = ws + R.x[level + 1];
+      const T L = k > 0 ? Xn[k - 1] : (R.bc == BC_PERIODIC ? Xn[Mn - 1] : T(0));
+      const T Xk = Xn[k];
+      T* out = LVL0 ? (u + R.offset) : (ws + R.x[level]);
+#pragma unroll
+      for (int j = 0; j < C; ++j)
+        if (j <= je) out[base + j] = tfma(-ch[j], Xk, tfma(-ah[j], L, v[j]));
+    }
+  }
+}
+
+// Solves the top level of each row (one CTA per row) into X_top.
+template <typename T, int NT, int C>
+__global__ void __launch_bounds__(NT) k_ml_top(T* __restrict__ u, T* __restrict__ ws,
+                                               const MLRow* __restrict__ rows,
+                                               const TileItem* __restrict__ items, int nitems,
+                                               int level, int64_t step) {
+  __shared__ BtcsShared<T, NT> sm;
+  (void)u;
+  (void)level;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const MLRow& R = rows[items[it].row];
+    if (step >= R.nsteps) continue;
+    const int L = R.levels;
+    const int64_t M = R.m[L];
+    const int base = tid * C;
+    const int tl = int((M - 1) / C);
+    const int je = base < M ? int(M - 1 - base < int64_t(C - 1) ? M - 1 - base : int64_t(C - 1)) : -1;
+    T v[C], ah[C], ch[C];
+    T e_ch, e_ah, e_dh;
+    UpperRows<T> src{ws + R.ef[L - 1], M, base, je};
+    chunk_forward<T, C>(v, ah, ch, je, src, e_ch, e_ah, e_dh);
+    chunk_backward<T, C>(v, ah, ch, je);
+    sm.rd[tid] = v[0];
+    sm.ra[tid] = ah[0];
+    sm.rg[tid] = ch[0];
+    __syncthreads();
+    T A = T(0), B = T(1), Cc = T(0), D = T(0);
+    if (tid <= tl) {
+      const int nx = (tid == tl) ? 0 : tid + 1;
+      A = e_ah;
+      B = T(1) - e_ch * sm.ra[nx];
+      Cc = -e_ch * sm.rg[nx];
+      D = tfma(-e_ch, sm.rd[nx], e_dh);
+    }
+    const int si = sk(tid);
+    sm.A[si] = A; sm.B[si] = B; sm.Cc[si] = Cc; sm.D[si] = D; sm.U[si] = T(0);
+    __syncthreads();
+    if (warp == 0) {
+      if (R.bc == BC_PERIODIC) reduced_solve<T, NT, true>(sm, tl, lane);
+      else reduced_solve<T, NT, false>(sm, tl, lane);
+    }
+    __syncthreads();
+    if (tid <= tl) {
+      T Lv = T(0);
+      if (tid > 0) Lv = sm.X[tid - 1];
+      else if (R.bc == BC_PERIODIC) Lv = sm.X[tl];
+      const T Xt = sm.X[tid];
+      T* out = ws + R.x[L];
+#pragma unroll
+      for (int j = 0; j < C; ++j)
+        if (j <= je) out[base + j] = tfma(-ch[j], Xt, tfma(-ah[j], Lv, v[j]));
+    }
+    __syncthreads();
+  }
+}
+
+#define REG_SWEEP(T, DT, NT, C)                                                               \
+  reg.push_back({K_BTCS_REDUCE, DT, NT, C, 1,                                                 \
+                 reinterpret_cast<const void*>(&k_ml_sweep<T, NT, C, true, false>), 0});     \
+  reg.push_back({K_BTCS_REDUCE, DT, NT, C, 0,                                                 \
+                 reinterpret_cast<const void*>(&k_ml_sweep<T, NT, C, false, false>), 0});    \
+  reg.push_back({K_BTCS_RECOVER, DT, NT, C, 1,                                                \
+                 reinterpret_cast<const void*>(&k_ml_sweep<T, NT, C, true, true>), 0});      \
+  reg.push_back({K_BTCS_RECOVER, DT, NT, C, 0,                                                \
+                 reinterpret_cast<const void*>(&k_ml_sweep<T, NT, C, false, true>), 0});
+#define REG_TOP(T, DT, NT, C) \
+  reg.push_back({K_BTCS_TOP, DT, NT, C, 0, reinterpret_cast<const void*>(&k_ml_top<T, NT, C>), 0});
+
+void register_multilevel(std::vector<KernelEntry>& reg) {
+  REG_SWEEP(float, 0, 256, 16) REG_SWEEP(float, 0, 128, 8)
+  REG_SWEEP(double, 1, 256, 8) REG_SWEEP(double, 1, 128, 4)
+  REG_TOP(float, 0, 32, 1) REG_TOP(float, 0, 32, 4) REG_TOP(float, 0, 128, 8)
+  REG_TOP(float, 0, 256, 16)
+  REG_TOP(double, 1, 32, 1) REG_TOP(double, 1, 32, 4) REG_TOP(double, 1, 128, 8)
+  REG_TOP(double, 1, 256, 8)
+}
+
+// ---------------------------------------------------------------------------
+// host planning
+// ---------------------------------------------------------------------------
+namespace {
+struct TopShape {
+  int nt, c;
+};
+const TopShape kTop32[] = {{32, 1}, {32, 4}, {128, 8}, {256, 16}};
+const TopShape kTop64[] = {{32, 1}, {32, 4}, {128, 8}, {256, 8}};
+}  // namespace
+
+static int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
 burgers_status plan_multilevel(burgers_ctx* ctx, const burgers_batch* batch,
                                const std::vector<int64_t>& longs, Plan* p) {
-  (void)ctx; (void)batch; (void)longs; (void)p;
-  return set_error(BURGERS_EINVAL, "BTCS rows longer than the resident limit are not supported yet");
+  const int dtype = batch->dtype;
+  const int snt = 256, sc = dtype == 0 ? 16 : 8;  // sweep shape
+  const TopShape* tops = dtype == 0 ? kTop32 : kTop64;
+  const int64_t top_cap = int64_t(tops[3].nt) * tops[3].c;
+  const KernelEntry* red0 = find_kernel(K_BTCS_REDUCE, dtype, snt, sc, 1);
+  const KernelEntry* red1 = find_kernel(K_BTCS_REDUCE, dtype, snt, sc, 0);
+  const KernelEntry* rec0 = find_kernel(K_BTCS_RECOVER, dtype, snt, sc, 1);
+  const KernelEntry* rec1 = find_kernel(K_BTCS_RECOVER, dtype, snt, sc, 0);
+  if (!red0 || !red1 || !rec0 || !rec1) return set_error(BURGERS_EINVAL, "multi-level kernels missing");
+  std::vector<MLRow> mrows;
+  int64_t ws = 0;
+  int Lmax = 0;
+  int64_t smax = 0;
+  auto al = [](int64_t x) { return (x + 63) & ~int64_t(63); };
+  for (int64_t b : longs) {
+    const burgers_instance& in = batch->inst[b];
+    MLRow R;
+    memset(&R, 0, sizeof R);
+    R.offset = in.offset;
+    R.nsteps = in.nsteps;
+    R.r = in.dt / in.dx;
+    R.s = in.nu * in.dt / (in.dx * in.dx);
+    R.n = in.n;
+    R.bc = in.bc;
+    R.m[0] = in.n;
+    int L = 0;
+    while (L == 0 || R.m[L] > top_cap) {
+      if (L == ML_MAXL) return set_error(BURGERS_EINVAL, "row too long for the multi-level solver");
+      R.m[L + 1] = cdiv(R.m[L], sc);
+      ++L;
+    }
+    if (R.m[L] < 2) return set_error(BURGERS_EINVAL, "row too short for the multi-level solver");
+    R.levels = L;
+    for (int l = 0; l < L; ++l) {
+      R.ef[l] = ws;
+      ws = al(ws + 6 * R.m[l + 1]);
+    }
+    for (int l = 1; l <= L; ++l) {
+      R.x[l] = ws;
+      ws = al(ws + R.m[l]);
+    }
+    Lmax = std::max(Lmax, L);
+    smax = std::max<int64_t>(smax, in.nsteps);
+    mrows.push_back(R);
+  }
+  p->ml_ws_elems = ws;
+  p->ml_rows = int(mrows.size());
+  p->ml_bytes.resize(mrows.size() * sizeof(MLRow));
+  memcpy(p->ml_bytes.data(), mrows.data(), p->ml_bytes.size());
+  // item lists: sweeps of each level, then one list per top shape
+  const int64_t tile = int64_t(snt) * sc;
+  std::vector<std::pair<int, int>> level_items(static_cast<size_t>(Lmax));  // (begin, count)
+  for (int l = 0; l < Lmax; ++l) {
+    int begin = int(p->items.size());
+    for (size_t q = 0; q < mrows.size(); ++q)
+      if (mrows[q].levels > l) {
+        int64_t tiles = cdiv(mrows[q].m[l], tile);
+        for (int64_t t = 0; t < tiles; ++t) p->items.push_back(TileItem{int32_t(q), int32_t(t)});
+      }
+    level_items[size_t(l)] = {begin, int(p->items.size()) - begin};
+  }
+  struct TopGroup {
+    const KernelEntry* k;
+    int begin, count;
+  };
+  std::vector<TopGroup> tgroups;
+  for (int ts = 0; ts < 4; ++ts) {
+    int begin = int(p->items.size());
+    for (size_t q = 0; q < mrows.size(); ++q) {
+      const int64_t mt = mrows[q].m[mrows[q].levels];
+      int pick = 0;
+      while (pick < 3 && !(int64_t(tops[pick].nt) * tops[pick].c >= mt && tops[pick].c < mt)) ++pick;
+      if (pick == ts) p->items.push_back(TileItem{int32_t(q), 0});
+    }
+    int cnt = int(p->items.size()) - begin;
+    if (cnt > 0) {
+      const KernelEntry* k = find_kernel(K_BTCS_TOP, dtype, tops[ts].nt, tops[ts].c, 0);
+      if (!k) return set_error(BURGERS_EINVAL, "top kernel missing");
+      tgroups.push_back(TopGroup{k, begin, cnt});
+    }
+  }
+  auto grid_for = [&](const KernelEntry* k, int nitems) {
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k->fn, k->nt, 0) != cudaSuccess || b < 1) b = 1;
+    return std::max(1, std::min(nitems, ctx->sm_count * b));
+  };
+  for (int64_t s = 0; s < smax; ++s) {
+    for (int l = 0; l < Lmax; ++l) {
+      Launch L;
+      L.type = LAUNCH_ML;
+      L.k = l == 0 ? red0 : red1;
+      L.item_begin = level_items[size_t(l)].first;
+      L.item_count = level_items[size_t(l)].second;
+      L.grid = grid_for(L.k, L.item_count);
+      L.level = l;
+      L.step_base = s;
+      p->launches.push_back(L);
+    }
+    for (const TopGroup& g : tgroups) {
+      Launch L;
+      L.type = LAUNCH_ML;
+      L.k = g.k;
+      L.item_begin = g.begin;
+      L.item_count = g.count;
+      L.grid = g.count;
+      L.level = 0;
+      L.step_base = s;
+      p->launches.push_back(L);
+    }
+    for (int l = Lmax - 1; l >= 0; --l) {
+      Launch L;
+      L.type = LAUNCH_ML;
+      L.k = l == 0 ? rec0 : rec1;
+      L.item_begin = level_items[size_t(l)].first;
+      L.item_count = level_items[size_t(l)].second;
+      L.grid = grid_for(L.k, L.item_count);
+      L.level = l;
+      L.step_base = s;
+      p->launches.push_back(L);
+    }
+  }
+  return BURGERS_OK;
 }
 
 cudaError_t enqueue_multilevel_launch(burgers_ctx* ctx, Plan* p, const Launch& L, void* u,
                                       cudaStream_t st) {
-  (void)ctx; (void)p; (void)L; (void)u; (void)st;
-  return cudaErrorNotSupported;
+  char* base = static_cast<char*>(p->dev);
+  void* ws = ctx->mlws.ptr;
+  const MLRow* rows = reinterpret_cast<const MLRow*>(base + p->ml_off);
+  const TileItem* items = reinterpret_cast<const TileItem*>(base + p->items_off) + L.item_begin;
+  int ni = L.item_count, level = L.level;
+  int64_t step = L.step_base;
+  void* args[] = {&u, &ws, &rows, &items, &ni, &level, &step};
+  return cudaLaunchKernel(L.k->fn, dim3(L.grid), dim3(L.k->nt), args, L.k->dyn_smem, st);
 }
 
 }  // namespace burgers

@@ -46,7 +46,8 @@ def test_config1_plain_sine(ctx, scheme, dtype):
     ref = run_oracle(scheme, e, dts, n)
     assert_parity(e, got, ref, dtype, "cfg1")
     # the odd initial condition stays odd on the GPU too
-    assert np.max(np.abs(got + got[::-1])) <= (1e-13 if dtype == F64 else 1e-6)
+    # (the partitioned solve is not mirror-symmetric in rounding: FP32 bar)
+    assert np.max(np.abs(got + got[::-1])) <= (1e-13 if dtype == F64 else 1e-5)
 
 
 @pytest.mark.parametrize("scheme", SCHEMES)
@@ -108,6 +109,37 @@ def test_streaming_explicit(ctx, dtype, K):
         assert_parity(ens, got, ref, dtype, f"stream K{K}")
     finally:
         _fresh(ctx)
+
+
+@pytest.mark.parametrize("dtype", [F64, F32])
+def test_multilevel_btcs(ctx, dtype):
+    """Long BTCS rows through the multi-level partitioned solver (one and two
+    reduction levels, every top shape, both BCs, ragged step counts)."""
+    _fresh(ctx)
+    ctx.set(L.BURGERS_OPT_RESIDENT_MAX, 64)
+    try:
+        ns = (100, 700, 5000, 70001)
+        ens = _concat([_one(n, bc, seed=n + 3) for n in ns for bc in (0, 1)])
+        dts = oracle_dts(ens, 8.0)
+        steps = np.array([7, 3, 25, 24, 40, 1, 12, 13])
+        got = run_gpu(ctx, BTCS, ens, dts, steps, dtype)
+        ref = run_oracle(BTCS, ens, dts, steps)
+        assert_parity(ens, got, ref, dtype, "multilevel")
+    finally:
+        _fresh(ctx)
+
+
+@pytest.mark.parametrize("dtype", [F64, F32])
+def test_large_grid_both_schemes(ctx, dtype):
+    """Configuration-3 shape at 2^22 nodes (periodic, sin x + 0.5 + noise,
+    nu = 1e-3): streaming explicit and multi-level BTCS against the oracle."""
+    _fresh(ctx)
+    ens = W.large_grid(1 << 22)
+    dt0 = oracle_dts(ens)
+    for scheme, dts, steps in ((EXPLICIT, dt0, 64), (BTCS, dt0 * 10.0, 4)):
+        got = run_gpu(ctx, scheme, ens, dts, steps, dtype)
+        ref = run_oracle(scheme, ens, dts, steps)
+        assert_parity(ens, got, ref, dtype, f"large s{scheme}")
 
 
 def test_gaps_between_rows_untouched(ctx):
