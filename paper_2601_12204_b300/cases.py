@@ -1,0 +1,65 @@
+"""Single-launch workload cases for kernel profiling (ncu) and quick timing.
+
+    python -m paper_2601_12204_b300.cases --case explicit --rows 4096 --n 4096 --steps 200
+
+Each case builds one seeded batch on the device, runs the CFL reduction, then
+exactly one advance call of the named scheme (one resident kernel launch, or
+the streaming / multi-level launch sequence for long rows), and prints its
+CUDA-event time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+
+import numpy as np
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--case", choices=["explicit", "btcs"], default="explicit")
+    ap.add_argument("--rows", type=int, default=4096)
+    ap.add_argument("--n", type=int, default=4096)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--dtype", choices=["f32", "f64"], default="f32")
+    ap.add_argument("--dt-factor", type=float, default=None)
+    ap.add_argument("--large", action="store_true", help="one row: sin x + 0.5 + noise")
+    ap.add_argument("--stream-k", type=int, default=0)
+    ap.add_argument("--repeat", type=int, default=1)
+    a = ap.parse_args()
+
+    import torch
+
+    from . import _lib as L
+    from . import workloads as W
+    from .api import Batch, Context
+
+    dt_code = L.BURGERS_F32 if a.dtype == "f32" else L.BURGERS_F64
+    tdt = torch.float32 if a.dtype == "f32" else torch.float64
+    ens = W.large_grid(a.n) if a.large else W.fourier_ensemble(a.rows, a.n)
+    ctx = Context(0)
+    if a.stream_k:
+        ctx.set(L.BURGERS_OPT_STREAM_K, a.stream_k)
+    u0 = torch.tensor(ens.u0, dtype=tdt, device="cuda")
+    dt = ctx.cfl_dt(Batch.from_ensemble(ens, 1.0, 0, dt_code), u0, 0.4)
+    fac = a.dt_factor if a.dt_factor is not None else (1.0 if a.case == "explicit" else 10.0)
+    b = Batch.from_ensemble(ens, dt * fac, a.steps, dt_code)
+    scheme = L.BURGERS_EXPLICIT if a.case == "explicit" else L.BURGERS_BTCS
+    times = []
+    for _ in range(a.repeat):
+        u = u0.clone()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        ctx.advance(scheme, b, u)
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    cells = float(np.sum(ens.ns)) * a.steps
+    print(json.dumps({"case": a.case, "rows": int(ens.count), "n": int(ens.ns[0]),
+                      "steps": a.steps, "dtype": a.dtype, "ms": times,
+                      "cups": cells / (min(times) / 1e3)}))
+    ctx.close()
+
+
+if __name__ == "__main__":
+    main()
