@@ -114,6 +114,25 @@ burgers_status burgers_ctx_set(burgers_ctx* ctx, int32_t option, int64_t value);
  * kernels they contain). */
 int64_t burgers_launch_count(const burgers_ctx* ctx);
 
+/* Launch-shape autotuner. Blocking. For every capacity class of the rows of
+ * `batch` (rows grouped by the smallest register capacity that holds them)
+ * it times each registered kernel shape of that class on a private copy of up
+ * to 512 of the caller's rows from u_dev (not modified), each row advanced
+ * min(nsteps, probe_steps) steps, and records the fastest shape in the
+ * context's table; for explicit rows longer than the resident limit it times
+ * the streaming window shapes and steps-per-pass K. Later calls of the
+ * advance functions use the table. *tuned (may be NULL) receives the number
+ * of classes tuned. */
+burgers_status burgers_autotune(burgers_ctx* ctx, int32_t scheme, const burgers_batch* batch,
+                                const void* u_dev, int64_t probe_steps, int32_t* tuned,
+                                burgers_stream stream);
+
+/* Writes / reads the context's tuning table as text at `path`. Loading checks
+ * that every entry names a registered kernel shape (else EINVAL, table
+ * unchanged). */
+burgers_status burgers_tune_save(const burgers_ctx* ctx, const char* path);
+burgers_status burgers_tune_load(burgers_ctx* ctx, const char* path);
+
 /* ---- time step (Eq. 7-8) ------------------------------------------------- */
 
 /* Blocking. For every row b of `batch`, dt_host[b] = cfl * min(dx / max|u|,
@@ -146,6 +165,23 @@ burgers_status burgers_btcs_advance(burgers_ctx* ctx, const burgers_batch* batch
  * full copy bandwidth. */
 burgers_status burgers_solve_host(burgers_ctx* ctx, int32_t scheme, const burgers_batch* batch,
                                   void* u_host, burgers_stream stream);
+
+/* ---- adjoints (reverse-mode differentiation, Sec. 2.7.1 / 2.7.3) ---------- */
+
+/* Discrete adjoint of burgers_explicit_advance (scheme = BURGERS_EXPLICIT) or
+ * burgers_btcs_advance (BURGERS_BTCS) for every row of `batch`: given
+ * gT_dev = dJ/du(T) (batch dtype, row layout of the batch) it writes
+ * gu0_dev = dJ/du(0) (same layout; may alias gT_dev) and gnu_dev[b] = dJ/dnu_b
+ * (one FP64 device value per row, batch order), holding dt, dx and nsteps
+ * fixed. u0_dev holds u(0) and is not modified. At u_i = 0 the derivative of
+ * u+ is taken as 0 and that of u- as 1. The forward states are recomputed
+ * from checkpoints every `ckpt_stride` steps (0 = ceil(sqrt(nsteps))), with
+ * (ceil(nsteps/stride) + stride + 1) * n values of context-owned workspace per
+ * row; the nu gradient is accumulated in FP64. Rows longer than 4096 (FP32)
+ * or 2048 (FP64) nodes: EINVAL. Asynchronous on `stream`. */
+burgers_status burgers_adjoint(burgers_ctx* ctx, int32_t scheme, const burgers_batch* batch,
+                               const void* u0_dev, const void* gT_dev, void* gu0_dev,
+                               double* gnu_dev, int64_t ckpt_stride, burgers_stream stream);
 
 /* ---- norms (Nomenclature "L2", Sec. 2.7.4) ------------------------------- */
 

@@ -75,6 +75,10 @@ SIGNATURES = {
     "burgers_btcs_advance": (_ST, [_P, _P, _P, _P]),
     "burgers_solve_host": (_ST, [_P, _I32, _P, _P, _P]),
     "burgers_rel_l2": (_ST, [_P, _P, _P, _P, _I32, _P, _P, _P]),
+    "burgers_adjoint": (_ST, [_P, _I32, _P, _P, _P, _P, _P, _I64, _P]),
+    "burgers_autotune": (_ST, [_P, _I32, _P, _P, _I64, _P, _P]),
+    "burgers_tune_save": (_ST, [_P, ctypes.c_char_p]),
+    "burgers_tune_load": (_ST, [_P, ctypes.c_char_p]),
 }
 
 _lock = threading.Lock()

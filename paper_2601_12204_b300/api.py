@@ -157,6 +157,36 @@ class Context:
                                          self._stream(stream, u)), "burgers_rel_l2")
         return rel, rms
 
+    def adjoint(self, scheme: int, batch: Batch, u0, gT, gu0, gnu, ckpt_stride: int = 0,
+                stream=None) -> None:
+        """dJ/du0 into gu0 and dJ/dnu (FP64, one per row) into gnu, given gT = dJ/du(T)."""
+        torch = _torch()
+        a = self._check_tensor(u0, batch)
+        g = self._check_tensor(gT, batch)
+        o = self._check_tensor(gu0, batch)
+        if (not gnu.is_cuda or gnu.dtype != torch.float64 or gnu.numel() < batch.count
+                or not gnu.is_contiguous()):
+            raise ValueError("gnu must be a contiguous CUDA float64 tensor with one entry per row")
+        L.check(self._lib.burgers_adjoint(self.h, int(scheme), batch.ref(), a, g, o,
+                                          ctypes.c_void_p(gnu.data_ptr()), int(ckpt_stride),
+                                          self._stream(stream, u0)), "burgers_adjoint")
+
+    def autotune(self, scheme: int, batch: Batch, u, probe_steps: int = 50, stream=None) -> int:
+        """Times the kernel shapes of the batch's capacity classes on a copy of
+        its rows and keeps the fastest; returns the number of classes tuned."""
+        p = self._check_tensor(u, batch)
+        n = ctypes.c_int32(0)
+        L.check(self._lib.burgers_autotune(self.h, int(scheme), batch.ref(), p, int(probe_steps),
+                                           ctypes.byref(n), self._stream(stream, u)),
+                "burgers_autotune")
+        return int(n.value)
+
+    def tune_save(self, path: str) -> None:
+        L.check(self._lib.burgers_tune_save(self.h, str(path).encode()), "burgers_tune_save")
+
+    def tune_load(self, path: str) -> None:
+        L.check(self._lib.burgers_tune_load(self.h, str(path).encode()), "burgers_tune_load")
+
     def solve_host(self, scheme: int, batch: Batch, u_host, stream=None) -> None:
         """In-place solve of a host buffer (numpy array or CPU tensor)."""
         if isinstance(u_host, np.ndarray):

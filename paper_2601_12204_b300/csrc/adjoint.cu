@@ -1,0 +1,489 @@
+// adjoint.cu -- hand-written discrete adjoints of the explicit and BTCS solves
+// (reverse-mode differentiation of the solution with respect to the initial
+// state and the viscosity, Sec. 2.7.1 / 2.7.3).
+//
+// Given gT = dJ/du(T) the kernels return dJ/du(0) and dJ/dnu, holding dt, dx
+// and the step count fixed. One CTA owns one row (the resident register
+// layout of the forward kernels: thread t holds C consecutive nodes).
+//
+// Checkpointing: the forward pass stores u every k steps (k = ceil(sqrt(nsteps))
+// by default); the reverse pass walks the segments backwards, recomputes the
+// k+1 states of a segment into a per-row buffer and applies the transposed
+// step Jacobians to lambda, held in registers, from the last state to the first.
+// Memory per row: (ceil(nsteps/k) + k + 1) * n values.
+//
+// Explicit step (Eq. 21, upwind side by sign, H(0) = 0):
+//   lambda_i <- (1 - 2s - r (H_i dl_i + (1-H_i) dr_i + |u_i|)) lambda_i
+//             + (s + r u_{i+1}^+) lambda_{i+1} + (s - r u_{i-1}^-) lambda_{i-1}
+//   dJ/dnu  += (dt/dx^2) sum_i lambda_i (u_{i+1} - 2u_i + u_{i-1})
+// BTCS step A(u^n) u^{n+1} = u^n:
+//   mu = A^{-T} lambda   (transposed rows: sub c_{i-1}, diag d_i, super l_{i+1},
+//                         corners c_{n-1}, l_0; the same partitioned cyclic solver)
+//   lambda_i <- mu_i - mu_i r (-H_i x_{i-1} + (2H_i - 1) x_i + (1 - H_i) x_{i+1}),
+//   dJ/dnu  += (dt/dx^2) sum_i mu_i (x_{i+1} - 2x_i + x_{i-1}),   x = u^{n+1}.
+// Dirichlet end nodes are identity rows: they pass lambda through (plus what
+// their neighbours' updates send them) and add nothing to dJ/dnu.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+
+#include "adjoint.h"
+#include "btcs_common.cuh"
+#include "common.cuh"
+#include "kernels.h"
+#include "api_internal.h"
+
+namespace burgers {
+
+template <typename T, int NT>
+struct Xch {
+  T first[2][NT], last[2][NT], wl[2], wr[2];
+};
+
+// Publishes this thread's end nodes of v; after the barrier, returns the
+// value left of node `base` (wrap: node n-1 for thread 0), right of node
+// base+C-1 and the periodic right neighbour of node n-1 (node 0).
+template <typename T, int NT, int C>
+__device__ __forceinline__ void xch_publish(const T (&v)[C], int jstar, Xch<T, NT>& x, int p) {
+  const int tid = threadIdx.x;
+  x.first[p][tid] = v[0];
+  x.last[p][tid] = v[C - 1];
+  if (jstar >= 0 && jstar < C) {
+    T sel = v[0];
+#pragma unroll
+    for (int j = 1; j < C; ++j)
+      if (j == jstar) sel = v[j];
+    x.wl[p] = sel;
+  }
+  if (tid == 0) x.wr[p] = v[0];
+}
+template <typename T, int NT>
+__device__ __forceinline__ void xch_read(const Xch<T, NT>& x, int p, T& left, T& right, T& wrapR) {
+  const int tid = threadIdx.x;
+  left = tid > 0 ? x.last[p][tid - 1] : x.wl[p];
+  right = tid + 1 < NT ? x.first[p][tid + 1] : x.wr[p];
+  wrapR = x.wr[p];
+}
+
+// neighbours of node j of this thread: ul, ur (periodic wrap at node n-1)
+template <typename T, int C>
+__device__ __forceinline__ void nbrs(const T (&v)[C], int j, int jstar, T left, T right, T wrapR,
+                                     T& ul, T& ur) {
+  ul = j > 0 ? v[j - 1] : left;
+  ur = j + 1 < C ? v[j + 1] : right;
+  if (j == jstar) ur = wrapR;
+}
+
+// one explicit forward step of the resident layout (generic, padding aware)
+template <typename T, int NT, int C>
+__device__ __forceinline__ void fwd_explicit_step(T (&v)[C], T (&lo)[C], int n, int base, bool per,
+                                                  T h, T s, Xch<T, NT>& xs, int& p) {
+  const int jstar = n - 1 - base;
+  xch_publish<T, NT, C>(v, jstar, xs, p);
+  __syncthreads();
+  T left, right, wr;
+  xch_read<T, NT>(xs, p, left, right, wr);
+  p ^= 1;
+  T prev = left;
+#pragma unroll
+  for (int j = 0; j < C; ++j) {
+    const int gi = base + j;
+    T ul = prev, ur = j + 1 < C ? v[j + 1] : right;
+    if (j == jstar) ur = wr;
+    const T cur = v[j];
+    const T lo0 = lo[j];
+    T nv = explicit_update(cur, ul, ur, h, s, lo[j]);
+    const bool keep = gi >= n || (!per && (gi == 0 || gi == n - 1));
+    if (keep) { nv = cur; lo[j] = lo0; }
+    prev = cur;
+    v[j] = nv;
+  }
+}
+
+// BTCS rows (lagged coefficients of node values a) and their transpose.
+template <typename T>
+__device__ __forceinline__ void btcs_coef(T a, T r, T s, T& l, T& d, T& c) {
+  const T ra = r * a;
+  l = -s - tmax(ra, T(0));
+  c = tmin(ra, T(0)) - s;
+  d = T(1) + T(2) * s + tabs(ra);
+}
+
+// generic resident cyclic / plain tridiagonal solve of this CTA's row: rows
+// from rowfn(j, l, d, c, rhs); solution into x. Uses sm (three barriers).
+template <typename T, int NT, int C, typename RowFn>
+__device__ __forceinline__ void resident_solve(T (&x)[C], T (&ah)[C], T (&ch)[C], RowFn&& rowfn,
+                                               int n, bool cyc, BtcsShared<T, NT>& sm) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int base = tid * C;
+  const int tl = (n - 1) / C;
+  const int je = base < n ? (n - 1 - base < C - 1 ? n - 1 - base : C - 1) : -1;
+  T e_ch, e_ah, e_dh;
+  chunk_forward<T, C>(x, ah, ch, je, rowfn, e_ch, e_ah, e_dh);
+  chunk_backward<T, C>(x, ah, ch, je);
+  sm.rd[tid] = x[0];
+  sm.ra[tid] = ah[0];
+  sm.rg[tid] = ch[0];
+  __syncthreads();
+  T A = T(0), B = T(1), Cc = T(0), D = T(0);
+  if (tid <= tl) {
+    const int nx = (tid == tl) ? 0 : tid + 1;
+    A = e_ah;
+    B = T(1) - e_ch * sm.ra[nx];
+    Cc = -e_ch * sm.rg[nx];
+    D = tfma(-e_ch, sm.rd[nx], e_dh);
+  }
+  const int si = sk(tid);
+  sm.A[si] = A; sm.B[si] = B; sm.Cc[si] = Cc; sm.D[si] = D; sm.U[si] = T(0);
+  __syncthreads();
+  if (warp == 0) {
+    if (cyc) reduced_solve<T, NT, true>(sm, tl, lane);
+    else reduced_solve<T, NT, false>(sm, tl, lane);
+  }
+  __syncthreads();
+  if (tid <= tl) {
+    T L = T(0);
+    if (tid > 0) L = sm.X[tid - 1];
+    else if (cyc) L = sm.X[tl];
+    const T Xt = sm.X[tid];
+#pragma unroll
+    for (int j = 0; j < C; ++j) x[j] = tfma(-ch[j], Xt, tfma(-ah[j], L, x[j]));
+  }
+}
+
+// one BTCS forward step of the resident layout (generic), in the increment
+// form of the forward kernel: A(u^n) delta = Delta(u^n), u += delta.
+template <typename T, int NT, int C>
+__device__ __forceinline__ void fwd_btcs_step(T (&v)[C], T (&lo)[C], int n, int base, bool per,
+                                              T r, T h, T s, BtcsShared<T, NT>& sm,
+                                              Xch<T, NT>& xs, int& p) {
+  const int jstar = n - 1 - base;
+  xch_publish<T, NT, C>(v, jstar, xs, p);
+  __syncthreads();
+  T left, right, wr;
+  xch_read<T, NT>(xs, p, left, right, wr);
+  p ^= 1;
+  T ah[C], ch[C], x[C];
+  auto rows = [&](int j, T& l, T& d, T& c, T& rhs) {
+    const int gi = base + j;
+    T ul, ur;
+    nbrs<T, C>(v, j, jstar, left, right, wr, ul, ur);
+    btcs_coef(v[j], r, s, l, d, c);
+    rhs = explicit_increment(v[j], ul, ur, h, s, T(0));
+    if (!per && (gi == 0 || gi == n - 1)) { l = T(0); c = T(0); d = T(1); rhs = T(0); }
+  };
+  resident_solve<T, NT, C>(x, ah, ch, rows, n, per, sm);
+#pragma unroll
+  for (int j = 0; j < C; ++j)
+    if (base + j < n) v[j] = comp_add(v[j], x[j], lo[j]);
+}
+
+template <typename T, int NT>
+struct AdjShared {
+  BtcsShared<T, NT> bt;
+  Xch<T, NT> xa, xb;
+  double red[NT / 32];
+};
+
+template <typename T, int NT, int C, int SCHEME>
+__global__ void __launch_bounds__(NT) k_adjoint(const T* __restrict__ u0, const T* gT,
+                                                T* gu0, double* __restrict__ gnu,
+                                                const RowDesc* __restrict__ rows,
+                                                const AdjRow* __restrict__ arows, int count,
+                                                int* __restrict__ counter, T* __restrict__ ws) {
+  __shared__ AdjShared<T, NT> sm;
+  __shared__ int s_item;
+  const int tid = threadIdx.x;
+  for (;;) {
+    if (tid == 0) s_item = atomicAdd(counter, 1);
+    __syncthreads();
+    const int item = s_item;
+    if (item >= count) return;
+    const RowDesc rd = rows[item];
+    const AdjRow ar = arows[item];
+    const int n = rd.n, base = tid * C, jstar = n - 1 - base;
+    const bool per = rd.bc == BC_PERIODIC;
+    const T r = T(rd.r), s = T(rd.s), h = T(0.5 * rd.r);
+    const int64_t ns = rd.nsteps, k = ar.stride;
+    // checkpoints: ar.nckpt states of n values (FP32: followed by the n Kahan terms)
+    constexpr int CKW = Kahan<T>::on ? 2 : 1;
+    T* ck = ws + ar.ckpt;
+    T* sg = ws + ar.seg;  // segment states, k + 1 of n values
+    int p = 0;
+    T v[C], lo[C];
+#pragma unroll
+    for (int j = 0; j < C; ++j) {
+      v[j] = base + j < n ? u0[rd.offset + base + j] : T(0);
+      lo[j] = T(0);
+    }
+    // ---- forward pass with checkpoints every k steps
+    for (int64_t st = 0; st < ns; ++st) {
+      if (st % k == 0) {
+        T* dst = ck + (st / k) * n * CKW;
+#pragma unroll
+        for (int j = 0; j < C; ++j)
+          if (base + j < n) {
+            dst[base + j] = v[j];
+            if constexpr (Kahan<T>::on) dst[n + base + j] = lo[j];
+          }
+      }
+      if (st + 1 == ns) break;  // the last state is not needed
+      if constexpr (SCHEME == 0) fwd_explicit_step<T, NT, C>(v, lo, n, base, per, h, s, sm.xa, p);
+      else fwd_btcs_step<T, NT, C>(v, lo, n, base, per, r, h, s, sm.bt, sm.xa, p);
+    }
+    // ---- reverse pass
+    T lam[C];
+#pragma unroll
+    for (int j = 0; j < C; ++j) lam[j] = base + j < n ? gT[rd.offset + base + j] : T(0);
+    double gacc = 0.0;
+    const int64_t nseg = ns > 0 ? (ns + k - 1) / k : 0;
+    for (int64_t sgi = nseg - 1; sgi >= 0; --sgi) {
+      const int64_t s0 = sgi * k;
+      const int64_t s1 = (s0 + k < ns) ? s0 + k : ns;
+      // recompute the states s0 .. s1 (BTCS needs u^{s+1}; explicit only u^s)
+#pragma unroll
+      for (int j = 0; j < C; ++j) {
+        v[j] = base + j < n ? ck[sgi * n * CKW + base + j] : T(0);
+        if constexpr (Kahan<T>::on) lo[j] = base + j < n ? ck[sgi * n * CKW + n + base + j] : T(0);
+      }
+      const int64_t last = SCHEME == 0 ? s1 - 1 : s1;
+      for (int64_t st = s0; st <= last; ++st) {
+        T* dst = sg + (st - s0) * n;
+#pragma unroll
+        for (int j = 0; j < C; ++j)
+          if (base + j < n) dst[base + j] = v[j];
+        if (st == last) break;
+        if constexpr (SCHEME == 0) fwd_explicit_step<T, NT, C>(v, lo, n, base, per, h, s, sm.xa, p);
+        else fwd_btcs_step<T, NT, C>(v, lo, n, base, per, r, h, s, sm.bt, sm.xa, p);
+      }
+      for (int64_t st = s1 - 1; st >= s0; --st) {
+        const T* us = sg + (st - s0) * n;
+#pragma unroll
+        for (int j = 0; j < C; ++j) v[j] = base + j < n ? us[base + j] : T(0);
+        T part = T(0);
+        if constexpr (SCHEME == 0) {
+          // transposed explicit step
+          xch_publish<T, NT, C>(v, jstar, sm.xa, p);
+          xch_publish<T, NT, C>(lam, jstar, sm.xb, p);
+          __syncthreads();
+          T ul0, ur0, uw, ll0, lr0, lw;
+          xch_read<T, NT>(sm.xa, p, ul0, ur0, uw);
+          xch_read<T, NT>(sm.xb, p, ll0, lr0, lw);
+          p ^= 1;
+          T nl[C];
+#pragma unroll
+          for (int j = 0; j < C; ++j) {
+            const int gi = base + j;
+            T ul, ur, ll, lr;
+            nbrs<T, C>(v, j, jstar, ul0, ur0, uw, ul, ur);
+            nbrs<T, C>(lam, j, jstar, ll0, lr0, lw, ll, lr);
+            const T u = v[j];
+            const bool upI = per || (gi > 0 && gi < n - 1);
+            const bool upR = per || (gi + 1 < n - 1);
+            const bool upL = per || (gi - 1 > 0);
+            const T dl = u - ul, dr = ur - u;
+            const T dii = upI ? T(1) - T(2) * s - r * ((u > T(0) ? dl : dr) + tabs(u)) : T(1);
+            T acc = dii * lam[j];
+            if (upR) acc = tfma(tfma(r, tmax(ur, T(0)), s), lr, acc);
+            if (upL) acc = tfma(tfma(-r, tmin(ul, T(0)), s), ll, acc);
+            if (upI) part = tfma(lam[j], dr - dl, part);
+            nl[j] = gi < n ? acc : T(0);
+          }
+#pragma unroll
+          for (int j = 0; j < C; ++j) lam[j] = nl[j];
+        } else {
+          // transposed BTCS step: mu = A(u^s)^{-T} lam, then the coefficient term
+          xch_publish<T, NT, C>(v, jstar, sm.xa, p);
+          __syncthreads();
+          T ul0, ur0, uw;
+          xch_read<T, NT>(sm.xa, p, ul0, ur0, uw);
+          p ^= 1;
+          T mu[C], ah[C], ch[C];
+          auto trows = [&](int j, T& l, T& d, T& c, T& rhs) {
+            const int gi = base + j;
+            T ul, ur;
+            nbrs<T, C>(v, j, jstar, ul0, ur0, uw, ul, ur);
+            T l0, d0, c0, lm, dm, cm, lp, dp, cp;
+            btcs_coef(v[j], r, s, l0, d0, c0);
+            btcs_coef(ul, r, s, lm, dm, cm);
+            btcs_coef(ur, r, s, lp, dp, cp);
+            const bool bI = !per && (gi == 0 || gi == n - 1);
+            const bool bL = !per && (gi - 1 == 0);       // row i-1 is an identity row
+            const bool bR = !per && (gi + 1 == n - 1);   // row i+1 is an identity row
+            l = (bL || (!per && gi == 0)) ? T(0) : cm;   // sub-diagonal: c_{i-1}
+            c = (bR || (!per && gi == n - 1)) ? T(0) : lp;  // super-diagonal: l_{i+1}
+            d = bI ? T(1) : d0;
+            rhs = lam[j];
+          };
+          resident_solve<T, NT, C>(mu, ah, ch, trows, n, per, sm.bt);
+          const T* ux = sg + (st + 1 - s0) * n;  // x = u^{s+1}
+          T xv[C];
+#pragma unroll
+          for (int j = 0; j < C; ++j) xv[j] = base + j < n ? ux[base + j] : T(0);
+          xch_publish<T, NT, C>(xv, jstar, sm.xb, p);
+          __syncthreads();
+          T xl0, xr0, xw;
+          xch_read<T, NT>(sm.xb, p, xl0, xr0, xw);
+          p ^= 1;
+#pragma unroll
+          for (int j = 0; j < C; ++j) {
+            const int gi = base + j;
+            T xl, xr;
+            nbrs<T, C>(xv, j, jstar, xl0, xr0, xw, xl, xr);
+            const bool bI = !per && (gi == 0 || gi == n - 1);
+            const T H = v[j] > T(0) ? T(1) : T(0);
+            const T drow = r * (-H * xl + (T(2) * H - T(1)) * xv[j] + (T(1) - H) * xr);
+            T out = bI ? mu[j] : mu[j] - mu[j] * drow;
+            if (!bI && gi < n) part = tfma(mu[j], xr - T(2) * xv[j] + xl, part);
+            lam[j] = gi < n ? out : T(0);
+          }
+        }
+        gacc += double(part);
+      }
+    }
+    // ---- outputs
+#pragma unroll
+    for (int j = 0; j < C; ++j)
+      if (base + j < n) gu0[rd.offset + base + j] = lam[j];
+    // block reduction of the nu gradient (FP64)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) gacc += __shfl_xor_sync(FULL_MASK, gacc, o);
+    if ((tid & 31) == 0) sm.red[tid >> 5] = gacc;
+    __syncthreads();
+    if (tid == 0) {
+      double t = 0.0;
+      for (int w = 0; w < NT / 32; ++w) t += sm.red[w];
+      gnu[ar.out_index] = t * rd.ds_dnu;
+    }
+    __syncthreads();
+  }
+}
+
+#define REG_ADJ(T, DT, NT, C)                                                                      \
+  reg.push_back({K_ADJ_EXPLICIT, DT, NT, C, 0, reinterpret_cast<const void*>(&k_adjoint<T, NT, C, 0>), \
+                 0});                                                                              \
+  reg.push_back({K_ADJ_BTCS, DT, NT, C, 0, reinterpret_cast<const void*>(&k_adjoint<T, NT, C, 1>), 0});
+
+void register_adjoint(std::vector<KernelEntry>& reg) {
+  REG_ADJ(float, 0, 32, 1) REG_ADJ(float, 0, 32, 4) REG_ADJ(float, 0, 64, 8)
+  REG_ADJ(float, 0, 128, 8) REG_ADJ(float, 0, 128, 16) REG_ADJ(float, 0, 256, 16)
+  REG_ADJ(double, 1, 32, 1) REG_ADJ(double, 1, 32, 4) REG_ADJ(double, 1, 64, 8)
+  REG_ADJ(double, 1, 128, 8) REG_ADJ(double, 1, 256, 8)
+}
+
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+namespace {
+struct AShape {
+  int nt, c;
+};
+const AShape kAdj32[] = {{32, 1}, {32, 4}, {64, 8}, {128, 8}, {128, 16}, {256, 16}};
+const AShape kAdj64[] = {{32, 1}, {32, 4}, {64, 8}, {128, 8}, {256, 8}};
+}  // namespace
+
+int64_t adjoint_max_n(int dtype) { return dtype == 0 ? 256 * 16 : 256 * 8; }
+
+burgers_status adjoint_run(burgers_ctx* ctx, int scheme, const burgers_batch* batch,
+                           const void* u0, const void* gT, void* gu0, double* gnu,
+                           int64_t stride, cudaStream_t st) {
+  const int dtype = batch->dtype;
+  const AShape* shapes = dtype == 0 ? kAdj32 : kAdj64;
+  const int nshapes = dtype == 0 ? 6 : 5;
+  const int kind = scheme == BURGERS_EXPLICIT ? K_ADJ_EXPLICIT : K_ADJ_BTCS;
+  const size_t esz = dtype == 0 ? 4 : 8;
+  std::vector<std::vector<std::pair<double, int64_t>>> groups(static_cast<size_t>(nshapes));
+  for (int64_t b = 0; b < batch->count; ++b) {
+    const burgers_instance& in = batch->inst[b];
+    if (in.n > adjoint_max_n(dtype))
+      return set_error(BURGERS_EINVAL, "adjoint: row longer than the resident limit");
+    int pick = -1;
+    for (int i = 0; i < nshapes && pick < 0; ++i)
+      if (int64_t(shapes[i].nt) * shapes[i].c >= in.n && shapes[i].c < in.n) pick = i;
+    if (pick < 0) return set_error(BURGERS_EINVAL, "adjoint: no kernel shape fits the row");
+    groups[size_t(pick)].emplace_back(double(in.n) * double(in.nsteps + 1), b);
+  }
+  std::vector<RowDesc> rows;
+  std::vector<AdjRow> arows;
+  std::vector<std::pair<int, int>> ranges;  // (shape, count)
+  int64_t ws = 0;
+  for (int g = 0; g < nshapes; ++g) {
+    auto& G = groups[size_t(g)];
+    if (G.empty()) continue;
+    std::stable_sort(G.begin(), G.end(), [](const auto& a, const auto& b) { return a.first > b.first; });
+    for (auto& pr : G) {
+      const burgers_instance& in = batch->inst[pr.second];
+      RowDesc d;
+      d.offset = in.offset;
+      d.nsteps = in.nsteps;
+      d.r = in.dt / in.dx;
+      d.s = in.nu * in.dt / (in.dx * in.dx);
+      d.ds_dnu = in.dt / (in.dx * in.dx);
+      d.n = in.n;
+      d.bc = in.bc;
+      AdjRow a;
+      int64_t k = stride > 0 ? stride : int64_t(ceil(sqrt(double(std::max<int64_t>(in.nsteps, 1)))));
+      if (k < 1) k = 1;
+      a.stride = k;
+      a.nckpt = in.nsteps > 0 ? (in.nsteps + k - 1) / k : 0;
+      a.ckpt = ws;
+      ws += ((a.nckpt * in.n * (dtype == 0 ? 2 : 1) + 63) / 64) * 64;
+      a.seg = ws;
+      ws += (((k + 1) * in.n + 63) / 64) * 64;
+      a.out_index = int32_t(pr.second);
+      a.pad = 0;
+      rows.push_back(d);
+      arows.push_back(a);
+    }
+    ranges.emplace_back(g, int(G.size()));
+  }
+  cudaError_t e = ctx->adjws.ensure(size_t(std::max<int64_t>(ws, 1)) * esz);
+  if (e != cudaSuccess) return set_error(BURGERS_ENOMEM, "adjoint workspace: out of device memory");
+  auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
+  const size_t o_rows = 0, o_arows = al(rows.size() * sizeof(RowDesc));
+  const size_t o_ctr = al(o_arows + arows.size() * sizeof(AdjRow));
+  const size_t total = al(o_ctr + ranges.size() * sizeof(int));
+  e = ctx->adjdesc.ensure(total);
+  if (e == cudaSuccess) e = ctx->adjhost.ensure_host(total);
+  if (e != cudaSuccess) return set_error(BURGERS_ENOMEM, "adjoint descriptors");
+  if (ctx->adj_event) {  // the previous upload must have left the staging buffer
+    e = cudaEventSynchronize(ctx->adj_event);
+    if (e != cudaSuccess) return cuda_error(e, "adjoint staging");
+  } else {
+    e = cudaEventCreateWithFlags(&ctx->adj_event, cudaEventDisableTiming);
+    if (e != cudaSuccess) return cuda_error(e, "cudaEventCreate");
+  }
+  char* h = static_cast<char*>(ctx->adjhost.hptr);
+  memcpy(h + o_rows, rows.data(), rows.size() * sizeof(RowDesc));
+  memcpy(h + o_arows, arows.data(), arows.size() * sizeof(AdjRow));
+  memset(h + o_ctr, 0, ranges.size() * sizeof(int));
+  char* dbase = static_cast<char*>(ctx->adjdesc.ptr);
+  e = cudaMemcpyAsync(dbase, h, total, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaEventRecord(ctx->adj_event, st);
+  if (e != cudaSuccess) return cuda_error(e, "adjoint upload");
+  int begin = 0;
+  for (size_t q = 0; q < ranges.size(); ++q) {
+    const AShape sh = shapes[ranges[q].first];
+    const KernelEntry* k = find_kernel(kind, dtype, sh.nt, sh.c, 0);
+    if (!k) return set_error(BURGERS_EINVAL, "adjoint kernel shape missing");
+    int cnt = ranges[q].second;
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k->fn, k->nt, 0) != cudaSuccess || occ < 1)
+      occ = 1;
+    int grid = std::min(cnt, ctx->sm_count * occ);
+    const RowDesc* rp = reinterpret_cast<const RowDesc*>(dbase + o_rows) + begin;
+    const AdjRow* ap = reinterpret_cast<const AdjRow*>(dbase + o_arows) + begin;
+    int* ctr = reinterpret_cast<int*>(dbase + o_ctr) + q;
+    void* wsp = ctx->adjws.ptr;
+    void* args[] = {(void*)&u0, (void*)&gT, &gu0, &gnu, &rp, &ap, &cnt, &ctr, &wsp};
+    e = cudaLaunchKernel(k->fn, dim3(grid), dim3(k->nt), args, 0, st);
+    if (e != cudaSuccess) return cuda_error(e, "adjoint launch");
+    ctx->launches += 1;
+    begin += cnt;
+  }
+  return BURGERS_OK;
+}
+
+}  // namespace burgers

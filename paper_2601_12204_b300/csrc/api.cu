@@ -113,7 +113,27 @@ namespace burgers {
 static int64_t resident_limit(const burgers_ctx* ctx, int kind, int dtype) {
   int64_t m = max_resident(kind, dtype);
   if (ctx->resident_max > 0) m = std::min<int64_t>(m, ctx->resident_max);
+  if (ctx->resident_override) m = 0;
   return m;
+}
+
+int64_t resident_capacity(const burgers_ctx* ctx, int kind, int dtype) {
+  return resident_limit(ctx, kind, dtype);
+}
+
+int64_t resident_class(int kind, int dtype, int64_t n) {
+  int64_t cap = -1;
+  for (const Shape& s : resident_shapes(kind, dtype)) {
+    int64_t c = int64_t(s.nt) * s.c;
+    if (c >= n && s.c < n && (cap < 0 || c < cap)) cap = c;
+  }
+  return cap;
+}
+
+std::vector<std::pair<int, int>> resident_shape_list(int kind, int dtype) {
+  std::vector<std::pair<int, int>> out;
+  for (const Shape& s : resident_shapes(kind, dtype)) out.emplace_back(s.nt, s.c);
+  return out;
 }
 
 // Shape for a resident row of n nodes: the tuned choice for its capacity class
@@ -207,17 +227,19 @@ static bool pick_stream(const burgers_ctx* ctx, int dtype, int64_t n_min, Shape*
   static const Shape s32[] = {{256, 16}, {128, 16}, {32, 4}};
   static const Shape s64[] = {{256, 8}, {128, 8}, {32, 4}};
   const Shape* list = dtype == 0 ? s32 : s64;
+  auto it = ctx->tuned.find(tune_key(K_EXPLICIT_STREAM, dtype, 0, 0));
+  if (ctx->stream_k == 0 && it != ctx->tuned.end() &&
+      int64_t(it->second.nt) * it->second.c <= n_min) {
+    *sh = Shape{it->second.nt, it->second.c};
+    *K = int(std::min<int64_t>(it->second.k, int64_t(sh->nt) * sh->c / 4));
+    return true;
+  }
   for (int i = 0; i < 3; ++i) {
     int64_t W = int64_t(list[i].nt) * list[i].c;
     if (W <= n_min) {
       *sh = list[i];
       int k = ctx->stream_k > 0 ? ctx->stream_k : (dtype == 0 ? 32 : 16);
       *K = int(std::min<int64_t>(k, W / 4));
-      auto it = ctx->tuned.find(tune_key(K_EXPLICIT_STREAM, dtype, W, 0));
-      if (ctx->stream_k == 0 && it != ctx->tuned.end()) {
-        *sh = Shape{it->second.nt, it->second.c};
-        *K = int(std::min<int64_t>(it->second.k, int64_t(sh->nt) * sh->c / 4));
-      }
       return true;
     }
   }
@@ -347,7 +369,9 @@ static burgers_status build_plan(burgers_ctx* ctx, int scheme, const burgers_bat
         L.to_scratch = false;
         p->launches.push_back(L);
       }
-      p->scratch_elems = span;
+      p->stream_span = span;
+      // ping-pong copy of the rows, plus two Kahan compensation buffers (FP32)
+      p->scratch_elems = dtype == 0 ? 3 * span : span;
     } else {
       burgers_status st = plan_multilevel(ctx, batch, longs, p);
       if (st != BURGERS_OK) return st;
@@ -397,6 +421,19 @@ static cudaError_t enqueue_plan(burgers_ctx* ctx, Plan* p, void* u, cudaStream_t
     if (e != cudaSuccess) return e;
   }
   void* scratch = ctx->scratch.ptr;
+  void* lo_a = nullptr;
+  void* lo_b = nullptr;
+  if (p->stream_span > 0 && p->dtype == 0) {
+    lo_a = static_cast<char*>(scratch) + size_t(p->stream_span) * esz;
+    lo_b = static_cast<char*>(lo_a) + size_t(p->stream_span) * esz;
+    cudaError_t e = cudaMemsetAsync(lo_a, 0, size_t(p->stream_span) * esz, st);
+    if (e != cudaSuccess) return e;
+  }
+  if (p->ml_span > 0 && p->dtype == 0) {  // multi-level Kahan terms start at zero
+    cudaError_t e = cudaMemsetAsync(static_cast<char*>(scratch) + size_t(p->ml_span) * esz, 0,
+                                    size_t(p->ml_span) * esz, st);
+    if (e != cudaSuccess) return e;
+  }
   for (const Launch& L : p->launches) {
     cudaError_t e = cudaSuccess;
     if (L.type == LAUNCH_RESIDENT) {
@@ -408,18 +445,19 @@ static cudaError_t enqueue_plan(burgers_ctx* ctx, Plan* p, void* u, cudaStream_t
     } else if (L.type == LAUNCH_STREAM) {
       const void* src = L.to_scratch ? u : scratch;
       void* dst = L.to_scratch ? scratch : u;
+      const void* lsrc = L.to_scratch ? lo_a : lo_b;
+      void* ldst = L.to_scratch ? lo_b : lo_a;
       RowDesc* r = rows + L.row_begin;
       TileItem* it = items + L.item_begin;
       int ni = L.item_count, K = L.K;
       int64_t sb = L.step_base;
-      void* args[] = {&src, &dst, &r, &it, &ni, &K, &sb};
+      void* args[] = {&src, &dst, &lsrc, &ldst, &r, &it, &ni, &K, &sb};
       e = cudaLaunchKernel(L.k->fn, dim3(L.grid), dim3(L.k->nt), args, L.k->dyn_smem, st);
     } else {
       e = enqueue_multilevel_launch(ctx, p, L, u, st);
     }
     if (e != cudaSuccess) return e;
   }
-  (void)esz;
   return cudaSuccess;
 }
 
@@ -474,7 +512,7 @@ static burgers_status run_plan(burgers_ctx* ctx, Plan* p, void* u, cudaStream_t 
 static uint64_t plan_key(const burgers_ctx* ctx, int scheme, const burgers_batch* b) {
   uint64_t h = fnv1a(b->inst, sizeof(burgers_instance) * size_t(b->count));
   int32_t hdr[8] = {scheme, b->dtype, ctx->plain ? 1 : 0, ctx->stream_k, int32_t(ctx->resident_max),
-                    int32_t(ctx->tune_version), 0, 0};
+                    int32_t(ctx->tune_version), ctx->resident_override, 0};
   return fnv1a(hdr, sizeof hdr, h);
 }
 
@@ -551,6 +589,7 @@ void burgers_ctx_destroy(burgers_ctx* ctx) {
   cudaDeviceSynchronize();
   ctx->plans.clear();
   if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
+  if (ctx->adj_event) cudaEventDestroy(ctx->adj_event);
   delete ctx;
 }
 
@@ -585,6 +624,22 @@ burgers_status burgers_explicit_advance(burgers_ctx* ctx, const burgers_batch* b
 burgers_status burgers_btcs_advance(burgers_ctx* ctx, const burgers_batch* batch, void* u_dev,
                                     burgers_stream stream) {
   return advance(ctx, BURGERS_BTCS, batch, u_dev, reinterpret_cast<cudaStream_t>(stream));
+}
+
+burgers_status burgers_adjoint(burgers_ctx* ctx, int32_t scheme, const burgers_batch* batch,
+                               const void* u0_dev, const void* gT_dev, void* gu0_dev,
+                               double* gnu_dev, int64_t ckpt_stride, burgers_stream stream) {
+  if (!ctx) return set_error(BURGERS_EINVAL, "ctx is NULL");
+  if (scheme != BURGERS_EXPLICIT && scheme != BURGERS_BTCS) return set_error(BURGERS_EINVAL, "bad scheme");
+  if (ckpt_stride < 0) return set_error(BURGERS_EINVAL, "negative checkpoint stride");
+  burgers_status st = validate_batch(batch, false);
+  if (st != BURGERS_OK) return st;
+  if (batch->count == 0) return BURGERS_OK;
+  if (!u0_dev || !gT_dev || !gu0_dev || !gnu_dev) return set_error(BURGERS_EINVAL, "NULL pointer");
+  cudaError_t e = cudaSetDevice(ctx->device);
+  if (e != cudaSuccess) return cuda_error(e, "cudaSetDevice");
+  return adjoint_run(ctx, scheme, batch, u0_dev, gT_dev, gu0_dev, gnu_dev, ckpt_stride,
+                     reinterpret_cast<cudaStream_t>(stream));
 }
 
 }  // extern "C"

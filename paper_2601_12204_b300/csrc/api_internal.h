@@ -65,7 +65,9 @@ struct Plan {
   std::vector<Launch> launches;
   int ncounters = 0;
   int64_t kernel_launches = 0;
-  int64_t scratch_elems = 0;  // streaming ping-pong buffer, elements
+  int64_t scratch_elems = 0;  // streaming ping-pong (+ compensation) buffers, elements
+  int64_t stream_span = 0;    // elements covered by the streaming rows
+  int64_t ml_span = 0;        // elements covered by the multi-level rows
   int64_t ml_ws_elems = 0;    // multi-level workspace, elements
   void* dev = nullptr;
   size_t rows_off = 0, items_off = 0, counters_off = 0, ml_off = 0, dev_bytes = 0;
@@ -103,7 +105,14 @@ struct burgers_ctx {
   burgers::DevBuf mlws;     // multi-level reduced systems
   burgers::DevBuf redws;    // reductions
   burgers::DevBuf iobuf;    // burgers_solve_host
+  burgers::DevBuf tunews;   // autotuner descriptors
+  burgers::DevBuf tunebuf;  // autotuner row copies
+  int resident_override = 0;  // autotuner: send every long-enough row to the long-row path
   burgers::HostBuf redhost;
+  burgers::DevBuf adjws;    // adjoint checkpoints and segment states
+  burgers::DevBuf adjdesc;  // adjoint descriptors
+  burgers::HostBuf adjhost;
+  cudaEvent_t adj_event = nullptr;
   size_t red_offsets[6] = {0, 0, 0, 0, 0, 0};
   burgers_ctx();
   ~burgers_ctx();
@@ -116,4 +125,13 @@ cudaError_t enqueue_multilevel_launch(burgers_ctx* ctx, Plan* p, const Launch& L
                                       cudaStream_t st);
 burgers_status advance(burgers_ctx* ctx, int scheme, const burgers_batch* batch, void* u_dev,
                        cudaStream_t stream);
+int64_t adjoint_max_n(int dtype);
+int64_t resident_capacity(const burgers_ctx* ctx, int kind, int dtype);
+int64_t resident_class(int kind, int dtype, int64_t n);
+std::vector<std::pair<int, int>> resident_shape_list(int kind, int dtype);
+burgers_status autotune(burgers_ctx* ctx, int scheme, const burgers_batch* batch,
+                        const void* u_dev, int64_t probe_steps, cudaStream_t st, int* tuned_out);
+burgers_status adjoint_run(burgers_ctx* ctx, int scheme, const burgers_batch* batch,
+                           const void* u0, const void* gT, void* gu0, double* gnu,
+                           int64_t stride, cudaStream_t st);
 }  // namespace burgers

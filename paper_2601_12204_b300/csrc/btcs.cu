@@ -29,27 +29,78 @@
 namespace burgers {
 
 // Advances the C nodes held by this thread `nsteps` BTCS steps.
+//
+// Increment form: with a = u^n, A(u^n) u^n = u^n - Delta(u^n) where Delta is the
+// explicit forward-Euler increment of the same r, s (Eq. 21), so the step is
+//     A(u^n) delta = Delta(u^n),   u^{n+1} = u^n + delta,
+// the same solution as A u^{n+1} = u^n in exact arithmetic. Solving for the
+// small increment instead of the full state keeps the FP32 solve error
+// proportional to |delta| rather than |u|, and the FP32 addition is Kahan-
+// compensated like the explicit kernel. Dirichlet end rows and padding rows
+// are identity rows with a zero increment.
 template <typename T, int NT, int C, bool EXACT, int BCT>
-__device__ __forceinline__ void btcs_steps(T (&v)[C], int64_t nsteps, T r, T s, int n,
-                                           BtcsShared<T, NT>& sm) {
+__device__ __forceinline__ void btcs_steps(T (&v)[C], int64_t nsteps, T r, T h, T s, int n,
+                                           BtcsShared<T, NT>& sm, T* sh_last, T* sh_first,
+                                           T* sh_wrap) {
+  constexpr int NW = NT / 32;
+  constexpr bool WRAPX = (!EXACT && BCT == BC_PERIODIC);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int base = tid * C;
   const int tl = EXACT ? NT - 1 : (n - 1) / C;  // chunk holding node n-1
   const int jstar = n - 1 - base;                // local index of node n-1
   const int je = EXACT ? C - 1 : (jstar < C ? jstar : C - 1);  // chunk end row (<0: none)
   const T ds1 = T(1) + T(2) * s;
-  T ch[C], ah[C];
+  T ch[C], ah[C], dd[C], lo[C];
+#pragma unroll
+  for (int j = 0; j < C; ++j) lo[j] = T(0);
   for (int64_t step = 0; step < nsteps; ++step) {
-    // ---- assembly fused with the forward sweep
+    // ---- neighbour values of u^n across threads (as in the explicit kernel)
+    const int p = int(step & 1);
+    const T first = v[0], last = v[C - 1];
+    T left = shfl(last, (lane + 31) & 31);
+    T right = shfl(first, (lane + 1) & 31);
+    if constexpr (NW > 1) {
+      if (lane == 31) sh_last[p * NW + warp] = last;
+      if (lane == 0) sh_first[p * NW + warp] = first;
+    }
+    if constexpr (WRAPX) {
+      if (jstar >= 0 && jstar < C) {
+        T sel = v[0];
+#pragma unroll
+        for (int j = 1; j < C; ++j)
+          if (j == jstar) sel = v[j];
+        sh_wrap[p * 2 + 0] = sel;
+      }
+      if (tid == 0) sh_wrap[p * 2 + 1] = first;
+    }
+    if constexpr (NW > 1 || WRAPX) __syncthreads();
+    if constexpr (NW > 1) {
+      if (lane == 0) left = sh_last[p * NW + (warp + NW - 1) % NW];
+      if (lane == 31) right = sh_first[p * NW + (warp + 1) % NW];
+    }
+    T wrapL = T(0), wrapR = T(0);
+    if constexpr (WRAPX) {
+      wrapL = sh_wrap[p * 2 + 0];
+      wrapR = sh_wrap[p * 2 + 1];
+    }
+    // ---- assembly of rows and right-hand sides fused with the forward sweep
     T chp = T(0), ahp = T(-1), dhp = T(0);
+    T prev = left;
 #pragma unroll
     for (int j = 0; j < C; ++j) {
       const T a = v[j];
+      T ul = prev;
+      T ur = (j + 1 < C) ? v[j + 1] : right;
+      if constexpr (WRAPX) {
+        if (j == 0 && tid == 0) ul = wrapL;
+        if (j == jstar) ur = wrapR;
+      }
+      prev = a;
       const T ra = r * a;
       T l = -s - tmax(ra, T(0));
       T c = tmin(ra, T(0)) - s;
       T d = ds1 + tabs(ra);
-      T rhs = a;
+      T rhs = explicit_increment(a, ul, ur, h, s, T(0));
       bool ident = false;
       if constexpr (BCT == BC_DIRICHLET) {
         if constexpr (EXACT)
@@ -58,9 +109,9 @@ __device__ __forceinline__ void btcs_steps(T (&v)[C], int64_t nsteps, T r, T s, 
           ident = (j == 0 && tid == 0) || j == jstar;
       }
       if constexpr (!EXACT) {
-        if (j > jstar) { ident = true; rhs = T(0); }
+        if (j > jstar) ident = true;
       }
-      if (ident) { l = T(0); c = T(0); d = T(1); }
+      if (ident) { l = T(0); c = T(0); d = T(1); rhs = T(0); }
       const T inv = recip(tfma(-l, chp, d));
       const T li = l * inv;
       chp = c * inv;
@@ -68,44 +119,44 @@ __device__ __forceinline__ void btcs_steps(T (&v)[C], int64_t nsteps, T r, T s, 
       dhp = tfma(-li, dhp, rhs * inv);
       ch[j] = chp;
       ah[j] = ahp;
-      v[j] = dhp;
+      dd[j] = dhp;
     }
     T e_ch = T(0), e_ah = T(0), e_dh = T(0);
     if constexpr (EXACT) {
-      e_ch = ch[C - 1]; e_ah = ah[C - 1]; e_dh = v[C - 1];
+      e_ch = ch[C - 1]; e_ah = ah[C - 1]; e_dh = dd[C - 1];
     } else {
 #pragma unroll
       for (int j = 0; j < C; ++j)
-        if (j == je) { e_ch = ch[j]; e_ah = ah[j]; e_dh = v[j]; }
+        if (j == je) { e_ch = ch[j]; e_ah = ah[j]; e_dh = dd[j]; }
     }
-    // ---- backward sweep: (delta, alpha, gamma) into (v, ah, ch)
+    // ---- backward sweep: (delta, alpha, gamma) into (dd, ah, ch)
     T cd = T(0), ca = T(0), cg = T(-1);
     if constexpr (EXACT) {
-      v[C - 1] = T(0); ah[C - 1] = T(0); ch[C - 1] = T(-1);
+      dd[C - 1] = T(0); ah[C - 1] = T(0); ch[C - 1] = T(-1);
 #pragma unroll
       for (int j = C - 2; j >= 0; --j) {
         const T cj = ch[j];
-        cd = tfma(-cj, cd, v[j]);
+        cd = tfma(-cj, cd, dd[j]);
         ca = tfma(-cj, ca, ah[j]);
         cg = -cj * cg;
-        v[j] = cd; ah[j] = ca; ch[j] = cg;
+        dd[j] = cd; ah[j] = ca; ch[j] = cg;
       }
     } else {
 #pragma unroll
       for (int j = C - 1; j >= 0; --j) {
         const T cj = ch[j];
-        T nd = tfma(-cj, cd, v[j]);
+        T nd = tfma(-cj, cd, dd[j]);
         T na = tfma(-cj, ca, ah[j]);
         T ng = -cj * cg;
         const bool past = j > je, at = j == je;
         if (past || at) { nd = T(0); na = T(0); ng = at ? T(-1) : T(0); }
-        v[j] = nd; ah[j] = na; ch[j] = ng;
+        dd[j] = nd; ah[j] = na; ch[j] = ng;
         if (past || at) { cd = T(0); ca = T(0); cg = T(-1); }
         else { cd = nd; ca = na; cg = ng; }
       }
     }
     // ---- reduced row of this chunk
-    sm.rd[tid] = v[0];
+    sm.rd[tid] = dd[0];
     sm.ra[tid] = ah[0];
     sm.rg[tid] = ch[0];
     __syncthreads();
@@ -123,14 +174,17 @@ __device__ __forceinline__ void btcs_steps(T (&v)[C], int64_t nsteps, T r, T s, 
     __syncthreads();
     if (warp == 0) reduced_solve<T, NT, BCT == BC_PERIODIC>(sm, tl, lane);
     __syncthreads();
-    // ---- back-substitution
+    // ---- back-substitution of the increment and the compensated update
     if (tid <= tl) {
       T L = T(0);
       if (tid > 0) L = sm.X[tid - 1];
       else if constexpr (BCT == BC_PERIODIC) L = sm.X[tl];
       const T Xt = sm.X[tid];
 #pragma unroll
-      for (int j = 0; j < C; ++j) v[j] = tfma(-ch[j], Xt, tfma(-ah[j], L, v[j]));
+      for (int j = 0; j < C; ++j) {
+        const T delta = tfma(-ch[j], Xt, tfma(-ah[j], L, dd[j]));
+        v[j] = comp_add(v[j], delta, lo[j]);
+      }
     }
   }
 }
@@ -139,7 +193,9 @@ template <typename T, int NT, int C, bool EXACT>
 __global__ void __launch_bounds__(NT) k_btcs_resident(T* __restrict__ u,
                                                       const RowDesc* __restrict__ rows, int count,
                                                       int* __restrict__ counter) {
+  constexpr int NW = NT / 32;
   __shared__ BtcsShared<T, NT> sm;
+  __shared__ T sh_last[2 * NW], sh_first[2 * NW], sh_wrap[4];
   __shared__ int s_item;
   for (;;) {
     if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
@@ -152,11 +208,13 @@ __global__ void __launch_bounds__(NT) k_btcs_resident(T* __restrict__ u,
     T v[C];
 #pragma unroll
     for (int j = 0; j < C; ++j) v[j] = (EXACT || base + j < rd.n) ? row[base + j] : T(0);
-    const T r = T(rd.r), s = T(rd.s);
+    const T r = T(rd.r), h = T(0.5 * rd.r), s = T(rd.s);
     if (rd.bc == BC_PERIODIC)
-      btcs_steps<T, NT, C, EXACT, BC_PERIODIC>(v, rd.nsteps, r, s, rd.n, sm);
+      btcs_steps<T, NT, C, EXACT, BC_PERIODIC>(v, rd.nsteps, r, h, s, rd.n, sm, sh_last, sh_first,
+                                               sh_wrap);
     else
-      btcs_steps<T, NT, C, EXACT, BC_DIRICHLET>(v, rd.nsteps, r, s, rd.n, sm);
+      btcs_steps<T, NT, C, EXACT, BC_DIRICHLET>(v, rd.nsteps, r, h, s, rd.n, sm, sh_last,
+                                                sh_first, sh_wrap);
 #pragma unroll
     for (int j = 0; j < C; ++j)
       if (EXACT || base + j < rd.n) row[base + j] = v[j];

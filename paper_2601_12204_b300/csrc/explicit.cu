@@ -30,8 +30,8 @@ enum : int { MODE_EXACT = 0, MODE_RAGGED = 1, MODE_WINDOW = 2, MODE_WINDOW_DIR =
 //   MODE_WINDOW_DIR streaming window that contains a Dirichlet end node.
 // gbase is the row index of this thread's first node.
 template <typename T, int NT, int C, int MODE, int BCT>
-__device__ __forceinline__ void explicit_steps(T (&v)[C], int64_t nsteps, T h, T s, int n,
-                                               int64_t gbase, T* sh_last, T* sh_first,
+__device__ __forceinline__ void explicit_steps(T (&v)[C], T (&lo)[C], int64_t nsteps, T h, T s,
+                                               int n, int64_t gbase, T* sh_last, T* sh_first,
                                                T* sh_wrap) {
   constexpr int NW = NT / 32;
   constexpr bool WRAPX = (MODE == MODE_RAGGED && BCT == BC_PERIODIC);
@@ -76,18 +76,19 @@ __device__ __forceinline__ void explicit_steps(T (&v)[C], int64_t nsteps, T h, T
         if (j == 0 && tid == 0) ul = wrapL;
         if (j == jstar) ur = wrapR;
       }
-      T nv = explicit_update(cur, ul, ur, h, s);
+      const T lo0 = lo[j];
+      T nv = explicit_update(cur, ul, ur, h, s, lo[j]);
+      bool keep = false;
       if constexpr (MODE == MODE_EXACT && BCT == BC_DIRICHLET) {
-        if (j == 0 && tid == 0) nv = cur;
-        if (j == C - 1 && tid == NT - 1) nv = cur;
+        keep = (j == 0 && tid == 0) || (j == C - 1 && tid == NT - 1);
       } else if constexpr (MODE == MODE_RAGGED) {
-        bool keep = j > jstar;  // padding
+        keep = j > jstar;  // padding
         if constexpr (BCT == BC_DIRICHLET) keep = keep || j == jstar || (j == 0 && tid == 0);
-        if (keep) nv = cur;
       } else if constexpr (MODE == MODE_WINDOW_DIR) {
         const int64_t gi = gbase + j;
-        if (gi == 0 || gi == n - 1) nv = cur;
+        keep = gi == 0 || gi == n - 1;
       }
+      if (keep) { nv = cur; lo[j] = lo0; }
       prev = cur;
       v[j] = nv;
     }
@@ -109,16 +110,19 @@ __global__ void __launch_bounds__(NT) k_explicit_resident(T* __restrict__ u,
     const RowDesc rd = rows[item];
     T* row = u + rd.offset;
     const int base = threadIdx.x * C;
-    T v[C];
+    T v[C], lo[C];
 #pragma unroll
-    for (int j = 0; j < C; ++j) v[j] = (EXACT || base + j < rd.n) ? row[base + j] : T(0);
+    for (int j = 0; j < C; ++j) {
+      v[j] = (EXACT || base + j < rd.n) ? row[base + j] : T(0);
+      lo[j] = T(0);
+    }
     const T h = T(0.5 * rd.r), s = T(rd.s);
     constexpr int M = EXACT ? MODE_EXACT : MODE_RAGGED;
     if (rd.bc == BC_PERIODIC)
-      explicit_steps<T, NT, C, M, BC_PERIODIC>(v, rd.nsteps, h, s, rd.n, base, sh_last, sh_first,
-                                               sh_wrap);
+      explicit_steps<T, NT, C, M, BC_PERIODIC>(v, lo, rd.nsteps, h, s, rd.n, base, sh_last,
+                                               sh_first, sh_wrap);
     else
-      explicit_steps<T, NT, C, M, BC_DIRICHLET>(v, rd.nsteps, h, s, rd.n, base, sh_last,
+      explicit_steps<T, NT, C, M, BC_DIRICHLET>(v, lo, rd.nsteps, h, s, rd.n, base, sh_last,
                                                 sh_first, sh_wrap);
 #pragma unroll
     for (int j = 0; j < C; ++j)
@@ -156,17 +160,28 @@ __device__ __forceinline__ void load_vec(T (&v)[C], const T* p) {
   }
 }
 
+__device__ __forceinline__ int skew32(int i) { return i + (i >> 5); }
+
 // Streaming window kernel. Pass `step_base` advances every row by
 // min(K, nsteps - step_base) steps from src into dst (rows already done are
-// copied through, so src/dst stay consistent for the ping-pong).
+// copied through, so src/dst stay consistent for the ping-pong). FP32 passes
+// carry the Kahan compensation term through lo_src / lo_dst (same layout as
+// the rows); FP64 passes get null pointers. Results leave through a skewed
+// shared-memory stage so the stores of the W - 2K output nodes are coalesced.
 template <typename T, int NT, int C>
 __global__ void __launch_bounds__(NT) k_explicit_stream(const T* __restrict__ src,
                                                         T* __restrict__ dst,
+                                                        const T* __restrict__ lo_src,
+                                                        T* __restrict__ lo_dst,
                                                         const RowDesc* __restrict__ rows,
                                                         const TileItem* __restrict__ items,
                                                         int nitems, int K, int64_t step_base) {
   constexpr int NW = NT / 32;
   constexpr int W = NT * C;
+  constexpr int WS = W + W / 32;
+  extern __shared__ __align__(16) unsigned char dsm[];
+  T* stage = reinterpret_cast<T*>(dsm);   // WS values
+  T* stage_lo = stage + WS;                 // WS values (FP32 only)
   __shared__ T sh_last[2 * NW], sh_first[2 * NW], sh_wrap[4];
   const int O = W - 2 * K;
   const int base = threadIdx.x * C;
@@ -182,15 +197,23 @@ __global__ void __launch_bounds__(NT) k_explicit_stream(const T* __restrict__ sr
     const T* srow = src + rd.offset;
     T* drow = dst + rd.offset;
     if (kk == 0) {
-      for (int64_t g = out_lo + threadIdx.x; g < out_hi; g += NT) drow[g] = srow[g];
+      for (int64_t g = out_lo + threadIdx.x; g < out_hi; g += NT) {
+        drow[g] = srow[g];
+        if constexpr (Kahan<T>::on) lo_dst[rd.offset + g] = lo_src[rd.offset + g];
+      }
       continue;
     }
-    T v[C];
+    T v[C], lo[C];
     const int64_t g0 = ws + base;
     const bool interior = ws >= 0 && ws + W <= n;
     const bool aligned = (reinterpret_cast<uintptr_t>(srow + ws) & 15) == 0;
     if (interior && aligned && (C % Vec2<T>::width == 0)) {
       load_vec<T, C>(v, srow + g0);
+      if constexpr (Kahan<T>::on) load_vec<T, C>(lo, lo_src + rd.offset + g0);
+      else {
+#pragma unroll
+        for (int j = 0; j < C; ++j) lo[j] = T(0);
+      }
     } else {
 #pragma unroll
       for (int j = 0; j < C; ++j) {
@@ -202,22 +225,31 @@ __global__ void __launch_bounds__(NT) k_explicit_stream(const T* __restrict__ sr
           gi = gi < 0 ? 0 : (gi >= n ? n - 1 : gi);
         }
         v[j] = srow[gi];
+        if constexpr (Kahan<T>::on) lo[j] = lo_src[rd.offset + gi];
+        else lo[j] = T(0);
       }
     }
     const T h = T(0.5 * rd.r), s = T(rd.s);
     const bool has_end = rd.bc == BC_DIRICHLET && ((ws <= 0 && ws + W > 0) ||
                                                    (ws <= n - 1 && ws + W > n - 1));
     if (has_end)
-      explicit_steps<T, NT, C, MODE_WINDOW_DIR, BC_DIRICHLET>(v, kk, h, s, int(n), g0, sh_last,
-                                                              sh_first, sh_wrap);
+      explicit_steps<T, NT, C, MODE_WINDOW_DIR, BC_DIRICHLET>(v, lo, kk, h, s, int(n), g0,
+                                                              sh_last, sh_first, sh_wrap);
     else
-      explicit_steps<T, NT, C, MODE_WINDOW, BC_PERIODIC>(v, kk, h, s, int(n), g0, sh_last,
+      explicit_steps<T, NT, C, MODE_WINDOW, BC_PERIODIC>(v, lo, kk, h, s, int(n), g0, sh_last,
                                                          sh_first, sh_wrap);
 #pragma unroll
     for (int j = 0; j < C; ++j) {
-      const int w = base + j;
-      const int64_t gi = ws + w;
-      if (w >= K && w < K + O && gi < out_hi) drow[gi] = v[j];
+      stage[skew32(base + j)] = v[j];
+      if constexpr (Kahan<T>::on) stage_lo[skew32(base + j)] = lo[j];
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < O; i += NT) {
+      const int64_t gi = out_lo + i;
+      if (gi < out_hi) {
+        drow[gi] = stage[skew32(K + i)];
+        if constexpr (Kahan<T>::on) lo_dst[rd.offset + gi] = stage_lo[skew32(K + i)];
+      }
     }
     __syncthreads();
   }
@@ -228,9 +260,10 @@ __global__ void __launch_bounds__(NT) k_explicit_stream(const T* __restrict__ sr
                  reinterpret_cast<const void*>(&k_explicit_resident<T, NT, C, true>), 0});  \
   reg.push_back({K_EXPLICIT_RESIDENT, DT, NT, C, 0,                                         \
                  reinterpret_cast<const void*>(&k_explicit_resident<T, NT, C, false>), 0});
-#define REG_STREAM(T, DT, NT, C)        \
-  reg.push_back({K_EXPLICIT_STREAM, DT, NT, C, 0, \
-                 reinterpret_cast<const void*>(&k_explicit_stream<T, NT, C>), 0});
+#define REG_STREAM(T, DT, NT, C)                                                            \
+  reg.push_back({K_EXPLICIT_STREAM, DT, NT, C, 0,                                          \
+                 reinterpret_cast<const void*>(&k_explicit_stream<T, NT, C>),             \
+                 sizeof(T) * size_t(NT * C + NT * C / 32) * (Kahan<T>::on ? 2 : 1)});
 
 void register_explicit(std::vector<KernelEntry>& reg) {
   // FP32 resident shapes (capacity NT*C nodes)

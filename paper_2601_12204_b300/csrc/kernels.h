@@ -21,6 +21,8 @@ enum KernelKind : int32_t {
   K_BTCS_REDUCE = 3,        // multi-level BTCS: chunk elimination of one level
   K_BTCS_RECOVER = 4,       // multi-level BTCS: back-substitution of one level
   K_BTCS_TOP = 5,           // multi-level BTCS: resident solve of the top level
+  K_ADJ_EXPLICIT = 6,       // adjoint of the explicit solve (resident rows)
+  K_ADJ_BTCS = 7,           // adjoint of the BTCS solve (resident rows)
   K_KIND_COUNT
 };
 

@@ -60,50 +60,69 @@ struct UpperRows {
   }
 };
 
-// Level-0 rows: lagged upwind BTCS coefficients assembled from u^n.
+// Level-0 rows in increment form: lagged upwind BTCS coefficients of u^n and
+// the explicit increment Delta(u^n) as right-hand side (A delta = Delta).
 template <typename T>
 struct NodeRows {
   const T* row;
   int64_t n;
   int64_t base;
   int je;
-  T r, s, ds1;
+  T r, h, s, ds1;
   bool dir;
   __device__ __forceinline__ void operator()(int j, T& l, T& d, T& c, T& rhs) const {
     const int64_t gi = base + j;
-    const T a = (j <= je) ? row[gi] : T(0);
+    if (j > je) { l = T(0); d = T(1); c = T(0); rhs = T(0); return; }
+    const T a = row[gi];
+    const T ul = row[gi == 0 ? n - 1 : gi - 1];
+    const T ur = row[gi == n - 1 ? 0 : gi + 1];
     const T ra = r * a;
     l = -s - tmax(ra, T(0));
     c = tmin(ra, T(0)) - s;
     d = ds1 + tabs(ra);
-    rhs = a;
-    if (dir && (gi == 0 || gi == n - 1)) { l = T(0); c = T(0); d = T(1); }
+    rhs = explicit_increment(a, ul, ur, h, s, T(0));
+    if (dir && (gi == 0 || gi == n - 1)) { l = T(0); c = T(0); d = T(1); rhs = T(0); }
   }
 };
 
+// One sweep of one level. Level 0 reads u^n from the buffer of the step's
+// parity (u for even steps, u2 for odd ones); its recover sweep writes
+// u^{n+1} = u^n + delta into the other buffer (FP32: Kahan term lo in place)
+// and copies rows whose steps are done straight through, so every row
+// alternates buffers in lockstep.
 template <typename T, int NT, int C, bool LVL0, bool RECOVER>
-__global__ void __launch_bounds__(NT) k_ml_sweep(T* __restrict__ u, T* __restrict__ ws,
+__global__ void __launch_bounds__(NT) k_ml_sweep(T* __restrict__ u, T* __restrict__ u2,
+                                                 T* __restrict__ lo, T* __restrict__ ws,
                                                  const MLRow* __restrict__ rows,
                                                  const TileItem* __restrict__ items, int nitems,
                                                  int level, int64_t step) {
+  T* src = (step & 1) ? u2 : u;
+  T* dst = (step & 1) ? u : u2;
   for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
     const TileItem ti = items[it];
     const MLRow& R = rows[ti.row];
-    if (step >= R.nsteps) continue;
     const int64_t M = R.m[level];
     const int64_t base = int64_t(ti.tile) * (NT * C) + int64_t(threadIdx.x) * C;
     if (base >= M) continue;
     const int je = int(M - 1 - base < int64_t(C - 1) ? M - 1 - base : int64_t(C - 1));
+    if (step >= R.nsteps) {
+      if constexpr (LVL0 && RECOVER) {
+#pragma unroll
+        for (int j = 0; j < C; ++j)
+          if (j <= je) dst[R.offset + base + j] = src[R.offset + base + j];
+      }
+      continue;
+    }
     T v[C], ah[C], ch[C];
     T e_ch, e_ah, e_dh;
     if constexpr (LVL0) {
       const T s = T(R.s);
-      NodeRows<T> src{u + R.offset, M, base, je, T(R.r), s, T(1) + T(2) * s,
-                      R.bc == BC_DIRICHLET};
-      chunk_forward<T, C>(v, ah, ch, je, src, e_ch, e_ah, e_dh);
+      NodeRows<T> rsrc{src + R.offset, M, base, je, T(R.r), T(0.5 * R.r), s, T(1) + T(2) * s,
+                       R.bc == BC_DIRICHLET};
+      chunk_forward<T, C>(v, ah, ch, je, rsrc, e_ch, e_ah, e_dh);
     } else {
-      UpperRows<T> src{ws + R.ef[level - 1], M, base, je};
-      chunk_forward<T, C>(v, ah, ch, je, src, e_ch, e_ah, e_dh);
+      UpperRows<T> rsrc{ws + R.ef[level - 1], M, base, je};
+      chunk_forward<T, C>(v, ah, ch, je, rsrc, e_ch, e_ah, e_dh);
     }
     chunk_backward<T, C>(v, ah, ch, je);
     const int64_t k = base / C;
@@ -120,22 +139,54 @@ __global__ void __launch_bounds__(NT) k_ml_sweep(T* __restrict__ u, T* __restric
       const T* Xn = ws + R.x[level + 1];
       const T L = k > 0 ? Xn[k - 1] : (R.bc == BC_PERIODIC ? Xn[Mn - 1] : T(0));
       const T Xk = Xn[k];
-      T* out = LVL0 ? (u + R.offset) : (ws + R.x[level]);
+      if constexpr (LVL0) {
+        const int64_t o = R.offset + base;
 #pragma unroll
-      for (int j = 0; j < C; ++j)
-        if (j <= je) out[base + j] = tfma(-ch[j], Xk, tfma(-ah[j], L, v[j]));
+        for (int j = 0; j < C; ++j)
+          if (j <= je) {
+            const T delta = tfma(-ch[j], Xk, tfma(-ah[j], L, v[j]));
+            T l0 = T(0);
+            if constexpr (Kahan<T>::on) l0 = lo[o + j];
+            dst[o + j] = comp_add(src[o + j], delta, l0);
+            if constexpr (Kahan<T>::on) lo[o + j] = l0;
+          }
+      } else {
+        T* out = ws + R.x[level];
+#pragma unroll
+        for (int j = 0; j < C; ++j)
+          if (j <= je) out[base + j] = tfma(-ch[j], Xk, tfma(-ah[j], L, v[j]));
+      }
     }
+  }
+}
+
+// Copies the rows of the level-0 items from u2 back into u (after an odd
+// number of steps).
+template <typename T, int NT, int C>
+__global__ void __launch_bounds__(NT) k_ml_copy(T* __restrict__ u, T* __restrict__ u2,
+                                                T* __restrict__ lo, T* __restrict__ ws,
+                                                const MLRow* __restrict__ rows,
+                                                const TileItem* __restrict__ items, int nitems,
+                                                int level, int64_t step) {
+  (void)lo; (void)ws; (void)level; (void)step;
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const TileItem ti = items[it];
+    const MLRow& R = rows[ti.row];
+    const int64_t lo_i = int64_t(ti.tile) * (NT * C);
+    const int64_t hi_i = min(lo_i + NT * C, R.m[0]);
+    for (int64_t g = lo_i + threadIdx.x; g < hi_i; g += NT) u[R.offset + g] = u2[R.offset + g];
   }
 }
 
 // Solves the top level of each row (one CTA per row) into X_top.
 template <typename T, int NT, int C>
-__global__ void __launch_bounds__(NT) k_ml_top(T* __restrict__ u, T* __restrict__ ws,
+__global__ void __launch_bounds__(NT) k_ml_top(T* __restrict__ u, T* __restrict__ u2,
+                                               T* __restrict__ lo, T* __restrict__ ws,
                                                const MLRow* __restrict__ rows,
                                                const TileItem* __restrict__ items, int nitems,
                                                int level, int64_t step) {
   __shared__ BtcsShared<T, NT> sm;
-  (void)u;
+  (void)u; (void)u2; (void)lo;
   (void)level;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
@@ -196,6 +247,8 @@ __global__ void __launch_bounds__(NT) k_ml_top(T* __restrict__ u, T* __restrict_
                  reinterpret_cast<const void*>(&k_ml_sweep<T, NT, C, false, true>), 0});
 #define REG_TOP(T, DT, NT, C) \
   reg.push_back({K_BTCS_TOP, DT, NT, C, 0, reinterpret_cast<const void*>(&k_ml_top<T, NT, C>), 0});
+#define REG_COPY(T, DT, NT, C) \
+  reg.push_back({K_BTCS_TOP, DT, NT, C, 1, reinterpret_cast<const void*>(&k_ml_copy<T, NT, C>), 0});
 
 void register_multilevel(std::vector<KernelEntry>& reg) {
   REG_SWEEP(float, 0, 256, 16) REG_SWEEP(float, 0, 128, 8)
@@ -204,6 +257,7 @@ void register_multilevel(std::vector<KernelEntry>& reg) {
   REG_TOP(float, 0, 256, 16)
   REG_TOP(double, 1, 32, 1) REG_TOP(double, 1, 32, 4) REG_TOP(double, 1, 128, 8)
   REG_TOP(double, 1, 256, 8)
+  REG_COPY(float, 0, 256, 16) REG_COPY(double, 1, 256, 8)
 }
 
 // ---------------------------------------------------------------------------
@@ -268,6 +322,11 @@ burgers_status plan_multilevel(burgers_ctx* ctx, const burgers_batch* batch,
   }
   p->ml_ws_elems = ws;
   p->ml_rows = int(mrows.size());
+  int64_t span = 0;
+  for (const MLRow& R : mrows) span = std::max<int64_t>(span, R.offset + R.n);
+  p->ml_span = span;
+  // ping-pong copy of the rows (+ the Kahan terms for FP32)
+  p->scratch_elems = std::max<int64_t>(p->scratch_elems, dtype == 0 ? 2 * span : span);
   p->ml_bytes.resize(mrows.size() * sizeof(MLRow));
   memcpy(p->ml_bytes.data(), mrows.data(), p->ml_bytes.size());
   // item lists: sweeps of each level, then one list per top shape
@@ -342,6 +401,18 @@ burgers_status plan_multilevel(burgers_ctx* ctx, const burgers_batch* batch,
       p->launches.push_back(L);
     }
   }
+  if (smax % 2 == 1) {  // the result is in the scratch copy
+    Launch L;
+    L.type = LAUNCH_ML;
+    L.k = find_kernel(K_BTCS_TOP, dtype, snt, sc, 1);
+    if (!L.k) return set_error(BURGERS_EINVAL, "copy kernel missing");
+    L.item_begin = level_items[0].first;
+    L.item_count = level_items[0].second;
+    L.grid = grid_for(L.k, L.item_count);
+    L.level = 0;
+    L.step_base = smax;
+    p->launches.push_back(L);
+  }
   return BURGERS_OK;
 }
 
@@ -349,11 +420,14 @@ cudaError_t enqueue_multilevel_launch(burgers_ctx* ctx, Plan* p, const Launch& L
                                       cudaStream_t st) {
   char* base = static_cast<char*>(p->dev);
   void* ws = ctx->mlws.ptr;
+  const size_t esz = p->dtype == 0 ? 4 : 8;
+  void* u2 = ctx->scratch.ptr;
+  void* lo = p->dtype == 0 ? static_cast<char*>(ctx->scratch.ptr) + size_t(p->ml_span) * esz : nullptr;
   const MLRow* rows = reinterpret_cast<const MLRow*>(base + p->ml_off);
   const TileItem* items = reinterpret_cast<const TileItem*>(base + p->items_off) + L.item_begin;
   int ni = L.item_count, level = L.level;
   int64_t step = L.step_base;
-  void* args[] = {&u, &ws, &rows, &items, &ni, &level, &step};
+  void* args[] = {&u, &u2, &lo, &ws, &rows, &items, &ni, &level, &step};
   return cudaLaunchKernel(L.k->fn, dim3(L.grid), dim3(L.k->nt), args, L.k->dyn_smem, st);
 }
 

@@ -9,6 +9,7 @@ namespace burgers {
 void register_explicit(std::vector<KernelEntry>& reg);
 void register_btcs(std::vector<KernelEntry>& reg);
 void register_multilevel(std::vector<KernelEntry>& reg);
+void register_adjoint(std::vector<KernelEntry>& reg);
 
 const std::vector<KernelEntry>& kernel_registry() {
   static std::vector<KernelEntry> reg;
@@ -17,6 +18,7 @@ const std::vector<KernelEntry>& kernel_registry() {
     register_explicit(reg);
     register_btcs(reg);
     register_multilevel(reg);
+    register_adjoint(reg);
   });
   return reg;
 }

@@ -332,3 +332,36 @@ def _concat(parts):
     offs[1:] = np.cumsum(ns[:-1])
     cat = lambda k: np.concatenate([getattr(p, k) for p in parts])  # noqa: E731
     return W.Ensemble(u0, offs, ns, cat("bcs"), cat("dxs"), cat("nus"), cat("x0"), cat("length"))
+
+
+@pytest.mark.parametrize("scheme", SCHEMES)
+def test_autotune_then_parity(ctx, scheme, tmp_path):
+    """The autotuner picks shapes per capacity class; results with the tuned
+    table still match the oracle, and the table survives a save/load."""
+    import torch
+    from paper_2601_12204_b300.api import Batch, Context
+    _fresh(ctx)
+    ens = _concat([W.fourier_ensemble(40, 4096, seed=3), W.fourier_ensemble(40, 2048, seed=4),
+                   _one(70001, 0, 5)])
+    dts = oracle_dts(ens, 1.0 if scheme == EXPLICIT else 8.0)
+    steps = 60 if scheme == EXPLICIT else 12
+    b = Batch.from_ensemble(ens, dts, steps, F64)
+    c2 = Context(0)
+    try:
+        ntuned = c2.autotune(scheme, b, torch.tensor(ens.u0, device="cuda"), probe_steps=20)
+        assert ntuned >= 1
+        got = run_gpu(c2, scheme, ens, dts, steps, F64)
+        ref = run_oracle(scheme, ens, dts, steps)
+        assert_parity(ens, got, ref, F64, "tuned")
+        path = str(tmp_path / "tune.txt")
+        c2.tune_save(path)
+        c3 = Context(0)
+        c3.tune_load(path)
+        assert np.array_equal(run_gpu(c3, scheme, ens, dts, steps, F64), got)
+        c3.close()
+        bad = tmp_path / "bad.txt"
+        bad.write_text("123 7 7 7\n")
+        with pytest.raises(Exception):
+            c2.tune_load(str(bad))
+    finally:
+        c2.close()
