@@ -440,7 +440,7 @@ def extras(args, ctx, ens, u0, batches, probe, dev, world, rank):
         z.record(stream)
         torch.cuda.synchronize()
         t = a.elapsed_time(z) / 1000.0
-        cups = lg.ns[0] * steps / t
+        cups = float(lg.ns[0]) * steps / t
         if K == 0:
             large["explicit_cups"] = cups
             large["explicit_steps"] = steps

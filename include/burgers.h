@@ -194,6 +194,86 @@ burgers_status burgers_rel_l2(burgers_ctx* ctx, const burgers_batch* batch, cons
                               const void* ref_dev, int32_t ref_dtype, double* out_host,
                               double* rms_host, burgers_stream stream);
 
+/* ---- serving: continuous batching of mixed requests ----------------------- */
+
+/* A server owns a device memory pool and a worker thread. Requests of mixed
+ * scheme, BC, n and step count are admitted in arrival order as soon as their
+ * state fits the pool (admission by free HBM), advance together in slices of
+ * `slice_steps` steps per request (requests arriving meanwhile join at the
+ * next slice boundary), and are copied back to the host when done, which
+ * frees their slot for the next arrivals. Slice boundaries sit at fixed
+ * multiples of slice_steps of each request, so a result does not depend on
+ * the other requests in flight. */
+typedef struct burgers_server burgers_server;
+
+typedef struct {
+  int32_t dtype;          /* burgers_dtype of every request's state */
+  int32_t reserved;
+  int64_t max_active;     /* cap on concurrently active requests (0 = none) */
+  int64_t hbm_budget;     /* device bytes for pool + scratch (0 = half the free HBM) */
+  int64_t slice_steps;    /* steps per request per slice (0 = 256) */
+  double slice_timeout_s; /* deadline of one slice; exceeded: ETIMEOUT (0 = 60 s) */
+} burgers_serve_cfg;
+
+typedef struct {
+  int32_t scheme; /* burgers_scheme */
+  int32_t bc;     /* burgers_bc */
+  int32_t n;      /* nodes, >= 3 */
+  int32_t reserved;
+  double dx, nu, dt;
+  int64_t nsteps;
+  const void* u0_host; /* n values of the server dtype, copied during submit */
+} burgers_request;
+
+typedef struct {
+  double t_submit, t_admit, t_done; /* seconds on the server clock (CLOCK_MONOTONIC since create) */
+  int64_t slices;                   /* slices the request took part in */
+  int32_t status;                   /* burgers_status of the request */
+  int32_t reserved;
+} burgers_req_stats;
+
+typedef struct {
+  int64_t submitted, completed, slices, active_max, pool_used_max;
+  double cell_updates; /* of completed requests */
+  int64_t pending, active, pool_bytes, pool_used;
+  double now_s; /* server clock */
+} burgers_serve_stats;
+
+/* Creates a server on ctx (cfg may be NULL for defaults). The pool is half
+ * the budget; a quarter of it holds rows longer than the resident limit, and
+ * the context reserves three times that quarter as long-row scratch. The
+ * context must outlive the server and must not be used by other threads
+ * while the server runs. */
+burgers_status burgers_serve_create(burgers_ctx* ctx, const burgers_serve_cfg* cfg,
+                                    burgers_server** out);
+
+/* Queues a request; copies u0 before returning. *ticket identifies it.
+ * EINVAL for bad fields, ENOMEM if its state can never fit the pool, the
+ * server's fault status if the worker has failed. */
+burgers_status burgers_serve_submit(burgers_server* sv, const burgers_request* rq,
+                                    uint64_t* ticket);
+
+/* Non-blocking: EAGAIN while the request is pending or running; otherwise
+ * copies the result (n values) to out_host (may be NULL), fills *stats (may
+ * be NULL), forgets the ticket and returns the request's status (OK,
+ * ECANCELED, ETIMEOUT, ECUDA). ENOTFOUND for an unknown ticket. */
+burgers_status burgers_serve_poll(burgers_server* sv, uint64_t ticket, void* out_host,
+                                  burgers_req_stats* stats);
+
+/* Blocking poll with a timeout in seconds: ETIMEOUT if still unfinished
+ * (the request stays queued and can be waited for again). */
+burgers_status burgers_serve_wait(burgers_server* sv, uint64_t ticket, double timeout_s,
+                                  void* out_host, burgers_req_stats* stats);
+
+/* Cancels a request: removed from the queue, or from the device at the next
+ * slice boundary; its poll then returns ECANCELED. */
+burgers_status burgers_serve_cancel(burgers_server* sv, uint64_t ticket);
+
+burgers_status burgers_serve_get_stats(burgers_server* sv, burgers_serve_stats* out);
+
+/* Stops the worker (requests still queued are dropped), frees the pool. */
+burgers_status burgers_serve_destroy(burgers_server* sv);
+
 #ifdef __cplusplus
 }
 #endif

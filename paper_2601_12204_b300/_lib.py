@@ -81,6 +81,43 @@ SIGNATURES = {
     "burgers_tune_load": (_ST, [_P, ctypes.c_char_p]),
 }
 
+class burgers_serve_cfg(ctypes.Structure):
+    _fields_ = [("dtype", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("max_active", ctypes.c_int64), ("hbm_budget", ctypes.c_int64),
+                ("slice_steps", ctypes.c_int64), ("slice_timeout_s", ctypes.c_double)]
+
+
+class burgers_request(ctypes.Structure):
+    _fields_ = [("scheme", ctypes.c_int32), ("bc", ctypes.c_int32), ("n", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("dx", ctypes.c_double), ("nu", ctypes.c_double),
+                ("dt", ctypes.c_double), ("nsteps", ctypes.c_int64), ("u0_host", ctypes.c_void_p)]
+
+
+class burgers_req_stats(ctypes.Structure):
+    _fields_ = [("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double),
+                ("t_done", ctypes.c_double), ("slices", ctypes.c_int64),
+                ("status", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class burgers_serve_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64),
+                ("slices", ctypes.c_int64), ("active_max", ctypes.c_int64),
+                ("pool_used_max", ctypes.c_int64), ("cell_updates", ctypes.c_double),
+                ("pending", ctypes.c_int64), ("active", ctypes.c_int64),
+                ("pool_bytes", ctypes.c_int64), ("pool_used", ctypes.c_int64),
+                ("now_s", ctypes.c_double)]
+
+
+SIGNATURES.update({
+    "burgers_serve_create": (_ST, [_P, _P, ctypes.POINTER(_P)]),
+    "burgers_serve_submit": (_ST, [_P, _P, ctypes.POINTER(ctypes.c_uint64)]),
+    "burgers_serve_poll": (_ST, [_P, ctypes.c_uint64, _P, _P]),
+    "burgers_serve_wait": (_ST, [_P, ctypes.c_uint64, _D, _P, _P]),
+    "burgers_serve_cancel": (_ST, [_P, ctypes.c_uint64]),
+    "burgers_serve_get_stats": (_ST, [_P, _P]),
+    "burgers_serve_destroy": (_ST, [_P]),
+})
+
 _lock = threading.Lock()
 _lib = None
 

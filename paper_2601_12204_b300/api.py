@@ -205,3 +205,66 @@ class Context:
             raise ValueError("host buffer is smaller than the batch span")
         L.check(self._lib.burgers_solve_host(self.h, int(scheme), batch.ref(), ctypes.c_void_p(ptr),
                                              self._stream(stream)), "burgers_solve_host")
+
+
+class Server:
+    """Continuous-batching server over a Context (burgers_serve_*)."""
+
+    def __init__(self, ctx: Context, dtype: int = L.BURGERS_F32, hbm_budget: int = 0,
+                 slice_steps: int = 256, max_active: int = 0, slice_timeout_s: float = 60.0):
+        self._lib = ctx._lib
+        self.ctx = ctx
+        self.dtype = int(dtype)
+        self.np_dtype = DTYPES[self.dtype]
+        cfg = L.burgers_serve_cfg(self.dtype, 0, int(max_active), int(hbm_budget),
+                                  int(slice_steps), float(slice_timeout_s))
+        h = ctypes.c_void_p()
+        L.check(self._lib.burgers_serve_create(ctx.h, ctypes.byref(cfg), ctypes.byref(h)),
+                "burgers_serve_create")
+        self.h = h
+
+    def submit(self, scheme: int, bc: int, u0, dx: float, nu: float, dt: float, nsteps: int) -> int:
+        a = np.ascontiguousarray(u0, dtype=self.np_dtype)
+        rq = L.burgers_request(int(scheme), int(bc), int(a.size), 0, float(dx), float(nu), float(dt),
+                               int(nsteps), a.ctypes.data)
+        t = ctypes.c_uint64(0)
+        L.check(self._lib.burgers_serve_submit(self.h, ctypes.byref(rq), ctypes.byref(t)),
+                "burgers_serve_submit")
+        return int(t.value)
+
+    def _result(self, fn, ticket, n, *extra):
+        out = np.empty(n, dtype=self.np_dtype)
+        st = L.burgers_req_stats()
+        rc = fn(self.h, ctypes.c_uint64(ticket), *extra, out.ctypes.data, ctypes.byref(st))
+        return rc, out, st
+
+    def poll(self, ticket: int, n: int):
+        """(status, result or None, stats); status EAGAIN while running."""
+        rc, out, st = self._result(self._lib.burgers_serve_poll, ticket, n)
+        return rc, (out if rc == L.BURGERS_OK else None), st
+
+    def wait(self, ticket: int, n: int, timeout_s: float = 60.0):
+        rc, out, st = self._result(self._lib.burgers_serve_wait, ticket, n,
+                                   ctypes.c_double(timeout_s))
+        return rc, (out if rc == L.BURGERS_OK else None), st
+
+    def cancel(self, ticket: int) -> int:
+        return int(self._lib.burgers_serve_cancel(self.h, ctypes.c_uint64(ticket)))
+
+    def stats(self) -> dict:
+        s = L.burgers_serve_stats()
+        L.check(self._lib.burgers_serve_get_stats(self.h, ctypes.byref(s)), "burgers_serve_get_stats")
+        return {k: getattr(s, k) for k, _ in s._fields_}
+
+    def close(self) -> int:
+        if getattr(self, "h", None) is not None and self.h.value:
+            rc = int(self._lib.burgers_serve_destroy(self.h))
+            self.h = None
+            return rc
+        return 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

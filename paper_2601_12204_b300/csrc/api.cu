@@ -248,7 +248,7 @@ static bool pick_stream(const burgers_ctx* ctx, int dtype, int64_t n_min, Shape*
 
 // Builds the plan of one advance call.
 static burgers_status build_plan(burgers_ctx* ctx, int scheme, const burgers_batch* batch,
-                                 Plan* p) {
+                                 Plan* p, PlanScratch* ext, cudaStream_t ext_stream) {
   const int dtype = batch->dtype;
   p->dtype = dtype;
   p->scheme = scheme;
@@ -390,14 +390,28 @@ static burgers_status build_plan(burgers_ctx* ctx, int scheme, const burgers_bat
   off = align(off + p->ml_bytes.size());
   p->dev_bytes = off;
   if (off > 0) {
-    cudaError_t e = cudaMalloc(&p->dev, off);
-    if (e != cudaSuccess) return set_error(BURGERS_ENOMEM, "plan descriptors: out of device memory");
-    std::vector<unsigned char> img(off, 0);
-    if (!p->rows.empty()) memcpy(img.data() + p->rows_off, p->rows.data(), p->rows.size() * sizeof(RowDesc));
+    unsigned char* img = nullptr;
+    std::vector<unsigned char> tmp;
+    if (ext) {  // reusable buffers of the caller (serving): no allocation per plan
+      cudaError_t e = ext->dev.ensure(off);
+      if (e == cudaSuccess) e = ext->host.ensure_host(off);
+      if (e != cudaSuccess) return set_error(BURGERS_ENOMEM, "plan descriptors: out of memory");
+      img = static_cast<unsigned char*>(ext->host.hptr);
+      memset(img, 0, off);
+      p->dev = ext->dev.ptr;
+      p->dev_external = true;
+    } else {
+      cudaError_t e = cudaMalloc(&p->dev, off);
+      if (e != cudaSuccess) return set_error(BURGERS_ENOMEM, "plan descriptors: out of device memory");
+      tmp.assign(off, 0);
+      img = tmp.data();
+    }
+    if (!p->rows.empty()) memcpy(img + p->rows_off, p->rows.data(), p->rows.size() * sizeof(RowDesc));
     if (!p->items.empty())
-      memcpy(img.data() + p->items_off, p->items.data(), p->items.size() * sizeof(TileItem));
-    if (!p->ml_bytes.empty()) memcpy(img.data() + p->ml_off, p->ml_bytes.data(), p->ml_bytes.size());
-    e = cudaMemcpy(p->dev, img.data(), off, cudaMemcpyHostToDevice);
+      memcpy(img + p->items_off, p->items.data(), p->items.size() * sizeof(TileItem));
+    if (!p->ml_bytes.empty()) memcpy(img + p->ml_off, p->ml_bytes.data(), p->ml_bytes.size());
+    cudaError_t e = ext ? cudaMemcpyAsync(p->dev, img, off, cudaMemcpyHostToDevice, ext_stream)
+                        : cudaMemcpy(p->dev, img, off, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_error(e, "plan upload");
   }
   for (const Launch& L : p->launches)
@@ -407,7 +421,7 @@ static burgers_status build_plan(burgers_ctx* ctx, int scheme, const burgers_bat
 
 Plan::~Plan() {
   if (gexec) cudaGraphExecDestroy(gexec);
-  if (dev) cudaFree(dev);
+  if (dev && !dev_external) cudaFree(dev);
 }
 
 static cudaError_t enqueue_plan(burgers_ctx* ctx, Plan* p, void* u, cudaStream_t st) {
@@ -461,7 +475,8 @@ static cudaError_t enqueue_plan(burgers_ctx* ctx, Plan* p, void* u, cudaStream_t
   return cudaSuccess;
 }
 
-static burgers_status run_plan(burgers_ctx* ctx, Plan* p, void* u, cudaStream_t st) {
+static burgers_status run_plan(burgers_ctx* ctx, Plan* p, void* u, cudaStream_t st,
+                               bool allow_graph = true) {
   if (p->scratch_elems > 0) {
     cudaError_t e = ctx->scratch.ensure(size_t(p->scratch_elems) * (p->dtype == 0 ? 4 : 8));
     if (e != cudaSuccess) return set_error(BURGERS_ENOMEM, "streaming scratch: out of device memory");
@@ -470,7 +485,8 @@ static burgers_status run_plan(burgers_ctx* ctx, Plan* p, void* u, cudaStream_t 
     cudaError_t e = ctx->mlws.ensure(size_t(p->ml_ws_elems) * (p->dtype == 0 ? 4 : 8));
     if (e != cudaSuccess) return set_error(BURGERS_ENOMEM, "multi-level workspace: out of device memory");
   }
-  const bool use_graph = ctx->graphs && !ctx->plain && p->launches.size() > 1;
+  const bool use_graph = allow_graph && ctx->graphs && !ctx->plain && p->launches.size() > 1 &&
+                         p->launches.size() <= 20000;
   if (use_graph) {
     const bool valid = p->gexec && p->g_u == u && p->g_scratch_gen == ctx->scratch.generation &&
                        p->g_ml_gen == ctx->mlws.generation;
@@ -528,7 +544,7 @@ Plan* get_plan(burgers_ctx* ctx, int scheme, const burgers_batch* batch, burgers
   auto p = std::make_unique<Plan>();
   p->key = key;
   p->count = batch->count;
-  *st = build_plan(ctx, scheme, batch, p.get());
+  *st = build_plan(ctx, scheme, batch, p.get(), nullptr, nullptr);
   if (*st != BURGERS_OK) return nullptr;
   ctx->plans.push_front(std::move(p));
   while (ctx->plans.size() > 64) {
@@ -550,6 +566,20 @@ burgers_status advance(burgers_ctx* ctx, int scheme, const burgers_batch* batch,
   Plan* p = get_plan(ctx, scheme, batch, &st);
   if (!p) return st;
   return run_plan(ctx, p, u_dev, stream);
+}
+
+// One-off plan through caller-owned descriptor buffers (no cache, no graph):
+// the serving loop, whose batch changes every slice. The caller must not
+// reuse `ps` before the work enqueued here has consumed the upload.
+burgers_status advance_uncached(burgers_ctx* ctx, int scheme, const burgers_batch* batch,
+                                void* u_dev, cudaStream_t stream, PlanScratch* ps) {
+  burgers_status st = validate_batch(batch, false);
+  if (st != BURGERS_OK) return st;
+  if (batch->count == 0) return BURGERS_OK;
+  Plan p;
+  st = build_plan(ctx, scheme, batch, &p, ps, stream);
+  if (st != BURGERS_OK) return st;
+  return run_plan(ctx, &p, u_dev, stream, false);
 }
 
 }  // namespace burgers

@@ -70,11 +70,18 @@ struct Plan {
   int64_t ml_span = 0;        // elements covered by the multi-level rows
   int64_t ml_ws_elems = 0;    // multi-level workspace, elements
   void* dev = nullptr;
+  bool dev_external = false;
   size_t rows_off = 0, items_off = 0, counters_off = 0, ml_off = 0, dev_bytes = 0;
   cudaGraphExec_t gexec = nullptr;
   void* g_u = nullptr;
   uint64_t g_scratch_gen = 0, g_ml_gen = 0;
   ~Plan();
+};
+
+// Descriptor buffers owned by a caller of advance_uncached().
+struct PlanScratch {
+  DevBuf dev;
+  HostBuf host;
 };
 
 struct TuneVal {
@@ -125,6 +132,8 @@ cudaError_t enqueue_multilevel_launch(burgers_ctx* ctx, Plan* p, const Launch& L
                                       cudaStream_t st);
 burgers_status advance(burgers_ctx* ctx, int scheme, const burgers_batch* batch, void* u_dev,
                        cudaStream_t stream);
+burgers_status advance_uncached(burgers_ctx* ctx, int scheme, const burgers_batch* batch,
+                                void* u_dev, cudaStream_t stream, PlanScratch* ps);
 int64_t adjoint_max_n(int dtype);
 int64_t resident_capacity(const burgers_ctx* ctx, int kind, int dtype);
 int64_t resident_class(int kind, int dtype, int64_t n);

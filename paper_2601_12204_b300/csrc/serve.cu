@@ -1,0 +1,500 @@
+// serve.cu -- continuous-batching server for mixed Burgers requests.
+//
+// Requests (scheme, BC, n, dx, nu, dt, nsteps, u0) arrive from any thread and
+// wait in a FIFO. A worker thread owns one CUDA stream and a device memory
+// pool sized by the HBM budget; it repeats:
+//   1. admission: pending requests whose state fits the pool (a first-fit free
+//      list; long rows use their own region so the long-row scratch buffers
+//      stay bounded) become active, and their u0 is copied into their slot;
+//   2. slice: every active request advances min(S, remaining) steps, the
+//      explicit ones in one batched call and the BTCS ones in another, all
+//      through the same kernels as burgers_*_advance (the pool is the packed
+//      buffer, slot offsets are the row offsets);
+//   3. completion: finished requests are copied back to host memory and their
+//      slots return to the free list, which is what lets the next arrivals in.
+// Requests that arrive while a slice runs join at the next slice boundary.
+// Slices start at fixed multiples of S steps of each request, so a request's
+// result does not depend on what else is in the mix (same kernel shape, same
+// slice boundaries): the result alone and in the mix is bitwise the same.
+//
+// Every wait is bounded: the worker polls its event with a deadline and
+// records BURGERS_ETIMEOUT on the affected requests instead of hanging, and
+// burgers_serve_wait takes a timeout.
+#include <string.h>
+#include <time.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/burgers.h"
+#include "api_internal.h"
+
+namespace burgers {
+
+static double now_s() {
+  struct timespec ts;
+  clock_gettime(CLOCK_MONOTONIC, &ts);
+  return double(ts.tv_sec) + 1e-9 * double(ts.tv_nsec);
+}
+
+// First-fit allocator over [base, base + size) with coalescing.
+class Region {
+ public:
+  void init(int64_t base, int64_t size) {
+    free_.clear();
+    if (size > 0) free_[base] = size;
+    total_ = size;
+    used_ = 0;
+  }
+  bool alloc(int64_t bytes, int64_t* off) {
+    bytes = (bytes + 255) & ~int64_t(255);
+    for (auto it = free_.begin(); it != free_.end(); ++it) {
+      if (it->second >= bytes) {
+        *off = it->first;
+        const int64_t rest = it->second - bytes;
+        const int64_t start = it->first + bytes;
+        free_.erase(it);
+        if (rest > 0) free_[start] = rest;
+        used_ += bytes;
+        return true;
+      }
+    }
+    return false;
+  }
+  void release(int64_t off, int64_t bytes) {
+    bytes = (bytes + 255) & ~int64_t(255);
+    used_ -= bytes;
+    auto it = free_.emplace(off, bytes).first;
+    auto nx = std::next(it);
+    if (nx != free_.end() && it->first + it->second == nx->first) {
+      it->second += nx->second;
+      free_.erase(nx);
+    }
+    if (it != free_.begin()) {
+      auto pv = std::prev(it);
+      if (pv->first + pv->second == it->first) {
+        pv->second += it->second;
+        free_.erase(it);
+      }
+    }
+  }
+  int64_t total() const { return total_; }
+  int64_t used() const { return used_; }
+
+ private:
+  std::map<int64_t, int64_t> free_;
+  int64_t total_ = 0, used_ = 0;
+};
+
+enum ReqState : int { RQ_PENDING = 0, RQ_ACTIVE = 1, RQ_DONE = 2, RQ_CANCELED = 3, RQ_FAILED = 4 };
+
+struct Req {
+  uint64_t ticket = 0;
+  burgers_request r{};
+  std::vector<unsigned char> u0;
+  std::vector<unsigned char> out;
+  int state = RQ_PENDING;
+  burgers_status status = BURGERS_OK;
+  bool long_row = false;
+  bool cancel = false;
+  int64_t off = 0, bytes = 0, done_steps = 0, slices = 0;
+  double t_submit = 0, t_admit = 0, t_done = 0;
+};
+
+}  // namespace burgers
+
+struct burgers_server {
+  burgers_ctx* ctx = nullptr;
+  burgers_serve_cfg cfg{};
+  size_t esz = 4;
+  void* pool = nullptr;
+  int64_t pool_bytes = 0;
+  burgers::Region short_region, long_region;
+  cudaStream_t stream = nullptr;
+  cudaEvent_t ev = nullptr;
+  std::thread worker;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::deque<burgers::Req*> pending;
+  std::vector<burgers::Req*> active;
+  std::unordered_map<uint64_t, std::unique_ptr<burgers::Req>> reqs;
+  uint64_t next_ticket = 1;
+  bool stop = false;
+  burgers_status fault = BURGERS_OK;
+  std::string fault_msg;
+  burgers::PlanScratch ps_explicit, ps_btcs;
+  burgers::HostBuf staging;
+  burgers_serve_stats stats{};
+  double t0 = 0;
+};
+
+namespace burgers {
+
+static int64_t long_limit(burgers_server* sv, int scheme) {
+  const int kind = scheme == BURGERS_EXPLICIT ? K_EXPLICIT_RESIDENT : K_BTCS_RESIDENT;
+  return resident_capacity(sv->ctx, kind, sv->cfg.dtype);
+}
+
+// Admits pending requests in arrival order while their state fits the pool
+// (a request that does not fit blocks the ones behind it: no overtaking).
+static void admit(burgers_server* sv, std::vector<Req*>* admitted) {
+  while (!sv->pending.empty()) {
+    Req* q = sv->pending.front();
+    if (q->cancel) {
+      sv->pending.pop_front();
+      q->state = RQ_CANCELED;
+      q->status = BURGERS_ECANCELED;
+      q->t_done = now_s() - sv->t0;
+      sv->cv_done.notify_all();
+      continue;
+    }
+    if (sv->cfg.max_active > 0 && int64_t(sv->active.size()) >= sv->cfg.max_active) break;
+    Region& rg = q->long_row ? sv->long_region : sv->short_region;
+    int64_t off = 0;
+    if (!rg.alloc(q->bytes, &off)) break;
+    q->off = off;
+    q->state = RQ_ACTIVE;
+    q->t_admit = now_s() - sv->t0;
+    sv->pending.pop_front();
+    sv->active.push_back(q);
+    admitted->push_back(q);
+  }
+}
+
+static void fail_all(burgers_server* sv, burgers_status st, const std::string& msg) {
+  std::lock_guard<std::mutex> lk(sv->mu);
+  sv->fault = st;
+  sv->fault_msg = msg;
+  for (Req* q : sv->active) {
+    q->state = RQ_FAILED;
+    q->status = st;
+  }
+  for (Req* q : sv->pending) {
+    q->state = RQ_FAILED;
+    q->status = st;
+  }
+  sv->active.clear();
+  sv->pending.clear();
+  sv->cv_done.notify_all();
+}
+
+// Waits for the worker's event with a deadline (never spins unbounded).
+static burgers_status wait_event(burgers_server* sv, double timeout_s) {
+  const double end = now_s() + timeout_s;
+  for (;;) {
+    cudaError_t e = cudaEventQuery(sv->ev);
+    if (e == cudaSuccess) return BURGERS_OK;
+    if (e != cudaErrorNotReady) return cuda_error(e, "serve slice");
+    if (now_s() > end) return set_error(BURGERS_ETIMEOUT, "serve slice exceeded its deadline");
+    std::this_thread::sleep_for(std::chrono::microseconds(50));
+  }
+}
+
+static void worker_loop(burgers_server* sv) {
+  cudaSetDevice(sv->ctx->device);
+  const int64_t S = sv->cfg.slice_steps;
+  std::vector<burgers_instance> ie, ib;
+  std::vector<Req*> admitted, in_e, in_b, finished;
+  for (;;) {
+    admitted.clear();
+    {
+      std::unique_lock<std::mutex> lk(sv->mu);
+      for (;;) {
+        if (sv->stop) return;
+        // drop cancelled active requests at the slice boundary
+        for (size_t i = 0; i < sv->active.size();) {
+          Req* q = sv->active[i];
+          if (q->cancel) {
+            (q->long_row ? sv->long_region : sv->short_region).release(q->off, q->bytes);
+            q->state = RQ_CANCELED;
+            q->status = BURGERS_ECANCELED;
+            q->t_done = now_s() - sv->t0;
+            sv->active[i] = sv->active.back();
+            sv->active.pop_back();
+            sv->cv_done.notify_all();
+          } else {
+            ++i;
+          }
+        }
+        admit(sv, &admitted);
+        if (!sv->active.empty()) break;
+        sv->cv_work.wait_for(lk, std::chrono::milliseconds(2));
+      }
+      // host copies of the admitted u0 (their vectors are not touched again)
+    }
+    // ---- copy the new requests' u0 into their slots
+    cudaError_t e = cudaSuccess;
+    for (Req* q : admitted) {
+      e = cudaMemcpyAsync(static_cast<char*>(sv->pool) + q->off, q->u0.data(), q->u0.size(),
+                          cudaMemcpyHostToDevice, sv->stream);
+      if (e != cudaSuccess) break;
+    }
+    if (e != cudaSuccess) {
+      fail_all(sv, cuda_error(e, "serve admission copy"), burgers_last_error());
+      return;
+    }
+    // ---- one slice over every active request
+    ie.clear(); ib.clear(); in_e.clear(); in_b.clear();
+    {
+      std::lock_guard<std::mutex> lk(sv->mu);
+      for (Req* q : sv->active) {
+        burgers_instance in;
+        in.offset = q->off / int64_t(sv->esz);
+        in.n = q->r.n;
+        in.bc = q->r.bc;
+        in.dx = q->r.dx;
+        in.nu = q->r.nu;
+        in.dt = q->r.dt;
+        in.nsteps = std::min<int64_t>(S, q->r.nsteps - q->done_steps);
+        if (q->r.scheme == BURGERS_EXPLICIT) { ie.push_back(in); in_e.push_back(q); }
+        else { ib.push_back(in); in_b.push_back(q); }
+      }
+    }
+    burgers_batch be{sv->cfg.dtype, 0, int64_t(ie.size()), ie.data()};
+    burgers_batch bb{sv->cfg.dtype, 0, int64_t(ib.size()), ib.data()};
+    burgers_status st = BURGERS_OK;
+    if (!ie.empty()) st = advance_uncached(sv->ctx, BURGERS_EXPLICIT, &be, sv->pool, sv->stream, &sv->ps_explicit);
+    if (st == BURGERS_OK && !ib.empty())
+      st = advance_uncached(sv->ctx, BURGERS_BTCS, &bb, sv->pool, sv->stream, &sv->ps_btcs);
+    if (st == BURGERS_OK) {
+      e = cudaEventRecord(sv->ev, sv->stream);
+      if (e != cudaSuccess) st = cuda_error(e, "serve record");
+    }
+    if (st == BURGERS_OK) st = wait_event(sv, sv->cfg.slice_timeout_s);
+    if (st != BURGERS_OK) {
+      fail_all(sv, st, burgers_last_error());
+      return;
+    }
+    // ---- completions
+    finished.clear();
+    {
+      std::lock_guard<std::mutex> lk(sv->mu);
+      for (Req* q : sv->active) {
+        q->done_steps += std::min<int64_t>(S, q->r.nsteps - q->done_steps);
+        q->slices += 1;
+        if (q->done_steps >= q->r.nsteps) finished.push_back(q);
+      }
+      sv->stats.slices += 1;
+      sv->stats.active_max = std::max<int64_t>(sv->stats.active_max, int64_t(sv->active.size()));
+      sv->stats.pool_used_max = std::max<int64_t>(
+          sv->stats.pool_used_max, sv->short_region.used() + sv->long_region.used());
+    }
+    for (Req* q : finished) {
+      q->out.resize(q->u0.size());
+      e = cudaMemcpyAsync(q->out.data(), static_cast<char*>(sv->pool) + q->off, q->out.size(),
+                          cudaMemcpyDeviceToHost, sv->stream);
+      if (e != cudaSuccess) break;
+    }
+    if (e == cudaSuccess && !finished.empty()) {
+      e = cudaEventRecord(sv->ev, sv->stream);
+      if (e == cudaSuccess) st = wait_event(sv, sv->cfg.slice_timeout_s);
+      else st = cuda_error(e, "serve record");
+    } else if (e != cudaSuccess) {
+      st = cuda_error(e, "serve result copy");
+    }
+    if (st != BURGERS_OK) {
+      fail_all(sv, st, burgers_last_error());
+      return;
+    }
+    {
+      std::lock_guard<std::mutex> lk(sv->mu);
+      const double t = now_s() - sv->t0;
+      for (Req* q : finished) {
+        (q->long_row ? sv->long_region : sv->short_region).release(q->off, q->bytes);
+        q->state = RQ_DONE;
+        q->t_done = t;
+        sv->stats.completed += 1;
+        sv->stats.cell_updates += double(q->r.n) * double(q->r.nsteps);
+        std::vector<unsigned char>().swap(q->u0);
+      }
+      if (!finished.empty()) {
+        auto& act = sv->active;
+        act.erase(std::remove_if(act.begin(), act.end(),
+                                 [](Req* q) { return q->state == RQ_DONE; }),
+                  act.end());
+        sv->cv_done.notify_all();
+      }
+    }
+  }
+}
+
+}  // namespace burgers
+
+using namespace burgers;
+
+extern "C" {
+
+burgers_status burgers_serve_create(burgers_ctx* ctx, const burgers_serve_cfg* cfg,
+                                    burgers_server** out) {
+  if (!ctx || !out) return set_error(BURGERS_EINVAL, "NULL argument");
+  *out = nullptr;
+  burgers_serve_cfg c{};
+  if (cfg) c = *cfg;
+  if (c.dtype != BURGERS_F32 && c.dtype != BURGERS_F64) return set_error(BURGERS_EINVAL, "bad dtype");
+  if (c.slice_steps <= 0) c.slice_steps = 256;
+  if (c.slice_timeout_s <= 0) c.slice_timeout_s = 60.0;
+  if (c.max_active < 0 || c.hbm_budget < 0) return set_error(BURGERS_EINVAL, "negative limit");
+  cudaError_t e = cudaSetDevice(ctx->device);
+  if (e != cudaSuccess) return cuda_error(e, "cudaSetDevice");
+  if (c.hbm_budget == 0) {
+    size_t fr = 0, tot = 0;
+    e = cudaMemGetInfo(&fr, &tot);
+    if (e != cudaSuccess) return cuda_error(e, "cudaMemGetInfo");
+    c.hbm_budget = int64_t(fr / 2);
+  }
+  auto sv = std::make_unique<burgers_server>();
+  sv->ctx = ctx;
+  sv->cfg = c;
+  sv->esz = c.dtype == BURGERS_F32 ? 4 : 8;
+  // budget: pool (short + long regions) plus the long-row scratch and
+  // multi-level workspace the kernels need for the long region
+  const int64_t pool = (c.hbm_budget / 2) & ~int64_t(255);
+  const int64_t long_bytes = (pool / 4) & ~int64_t(255);
+  if (pool < (int64_t(1) << 20)) return set_error(BURGERS_EINVAL, "HBM budget too small (< 2 MiB)");
+  e = cudaMalloc(&sv->pool, size_t(pool));
+  if (e != cudaSuccess) return set_error(BURGERS_ENOMEM, "serve pool: out of device memory");
+  sv->pool_bytes = pool;
+  sv->long_region.init(0, long_bytes);
+  sv->short_region.init(long_bytes, pool - long_bytes);
+  e = ctx->scratch.ensure(size_t(3 * long_bytes));
+  if (e == cudaSuccess) e = ctx->mlws.ensure(size_t(long_bytes));
+  if (e != cudaSuccess) {
+    cudaFree(sv->pool);
+    return set_error(BURGERS_ENOMEM, "serve scratch: out of device memory");
+  }
+  e = cudaStreamCreateWithFlags(&sv->stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sv->ev, cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    cudaFree(sv->pool);
+    return cuda_error(e, "serve stream");
+  }
+  sv->t0 = now_s();
+  burgers_server* raw = sv.release();
+  raw->worker = std::thread(worker_loop, raw);
+  *out = raw;
+  return BURGERS_OK;
+}
+
+burgers_status burgers_serve_submit(burgers_server* sv, const burgers_request* rq, uint64_t* ticket) {
+  if (!sv || !rq || !ticket) return set_error(BURGERS_EINVAL, "NULL argument");
+  if (rq->scheme != BURGERS_EXPLICIT && rq->scheme != BURGERS_BTCS) return set_error(BURGERS_EINVAL, "bad scheme");
+  if (!rq->u0_host) return set_error(BURGERS_EINVAL, "u0_host is NULL");
+  burgers_instance in{0, rq->n, rq->bc, rq->dx, rq->nu, rq->dt, rq->nsteps};
+  burgers_batch b{sv->cfg.dtype, 0, 1, &in};
+  burgers_status st = validate_batch(&b, false);
+  if (st != BURGERS_OK) return st;
+  auto q = std::make_unique<Req>();
+  q->r = *rq;
+  q->r.u0_host = nullptr;
+  q->bytes = int64_t(rq->n) * int64_t(sv->esz);
+  q->long_row = rq->n > long_limit(sv, rq->scheme);
+  const Region& rg = q->long_row ? sv->long_region : sv->short_region;
+  if (q->bytes > rg.total()) return set_error(BURGERS_ENOMEM, "request larger than the pool region");
+  q->u0.assign(static_cast<const unsigned char*>(rq->u0_host),
+               static_cast<const unsigned char*>(rq->u0_host) + q->bytes);
+  std::lock_guard<std::mutex> lk(sv->mu);
+  if (sv->fault != BURGERS_OK) return set_error(sv->fault, "server failed: " + sv->fault_msg);
+  q->t_submit = now_s() - sv->t0;
+  q->ticket = sv->next_ticket++;
+  *ticket = q->ticket;
+  sv->pending.push_back(q.get());
+  sv->reqs[q->ticket] = std::move(q);
+  sv->stats.submitted += 1;
+  sv->cv_work.notify_one();
+  return BURGERS_OK;
+}
+
+static burgers_status take_result(burgers_server* sv, Req* q, void* out_host,
+                                  burgers_req_stats* rs) {
+  if (rs) {
+    rs->t_submit = q->t_submit;
+    rs->t_admit = q->t_admit;
+    rs->t_done = q->t_done;
+    rs->slices = q->slices;
+    rs->status = q->status;
+  }
+  burgers_status st = q->status;
+  if (q->state == RQ_DONE && out_host) memcpy(out_host, q->out.data(), q->out.size());
+  sv->reqs.erase(q->ticket);
+  if (st != BURGERS_OK) return set_error(st, "request did not complete");
+  return BURGERS_OK;
+}
+
+burgers_status burgers_serve_poll(burgers_server* sv, uint64_t ticket, void* out_host,
+                                  burgers_req_stats* rs) {
+  if (!sv) return set_error(BURGERS_EINVAL, "NULL server");
+  std::lock_guard<std::mutex> lk(sv->mu);
+  auto it = sv->reqs.find(ticket);
+  if (it == sv->reqs.end()) return set_error(BURGERS_ENOTFOUND, "unknown ticket");
+  Req* q = it->second.get();
+  if (q->state == RQ_PENDING || q->state == RQ_ACTIVE) return BURGERS_EAGAIN;
+  return take_result(sv, q, out_host, rs);
+}
+
+burgers_status burgers_serve_wait(burgers_server* sv, uint64_t ticket, double timeout_s,
+                                  void* out_host, burgers_req_stats* rs) {
+  if (!sv) return set_error(BURGERS_EINVAL, "NULL server");
+  std::unique_lock<std::mutex> lk(sv->mu);
+  auto it = sv->reqs.find(ticket);
+  if (it == sv->reqs.end()) return set_error(BURGERS_ENOTFOUND, "unknown ticket");
+  Req* q = it->second.get();
+  const auto deadline = std::chrono::steady_clock::now() +
+                        std::chrono::microseconds(int64_t(std::max(0.0, timeout_s) * 1e6));
+  while (q->state == RQ_PENDING || q->state == RQ_ACTIVE) {
+    if (sv->cv_done.wait_until(lk, deadline) == std::cv_status::timeout &&
+        (q->state == RQ_PENDING || q->state == RQ_ACTIVE))
+      return set_error(BURGERS_ETIMEOUT, "request not finished before the timeout");
+  }
+  return take_result(sv, q, out_host, rs);
+}
+
+burgers_status burgers_serve_cancel(burgers_server* sv, uint64_t ticket) {
+  if (!sv) return set_error(BURGERS_EINVAL, "NULL server");
+  std::lock_guard<std::mutex> lk(sv->mu);
+  auto it = sv->reqs.find(ticket);
+  if (it == sv->reqs.end()) return set_error(BURGERS_ENOTFOUND, "unknown ticket");
+  it->second->cancel = true;
+  sv->cv_work.notify_one();
+  return BURGERS_OK;
+}
+
+burgers_status burgers_serve_get_stats(burgers_server* sv, burgers_serve_stats* out) {
+  if (!sv || !out) return set_error(BURGERS_EINVAL, "NULL argument");
+  std::lock_guard<std::mutex> lk(sv->mu);
+  *out = sv->stats;
+  out->pending = int64_t(sv->pending.size());
+  out->active = int64_t(sv->active.size());
+  out->pool_bytes = sv->pool_bytes;
+  out->pool_used = sv->short_region.used() + sv->long_region.used();
+  out->now_s = now_s() - sv->t0;
+  return BURGERS_OK;
+}
+
+burgers_status burgers_serve_destroy(burgers_server* sv) {
+  if (!sv) return set_error(BURGERS_EINVAL, "NULL server");
+  {
+    std::lock_guard<std::mutex> lk(sv->mu);
+    sv->stop = true;
+  }
+  sv->cv_work.notify_all();
+  if (sv->worker.joinable()) sv->worker.join();
+  cudaSetDevice(sv->ctx->device);
+  if (sv->stream) cudaStreamSynchronize(sv->stream);
+  if (sv->ev) cudaEventDestroy(sv->ev);
+  if (sv->stream) cudaStreamDestroy(sv->stream);
+  if (sv->pool) cudaFree(sv->pool);
+  burgers_status st = sv->fault;
+  delete sv;
+  return st == BURGERS_OK ? BURGERS_OK : st;
+}
+
+}  // extern "C"

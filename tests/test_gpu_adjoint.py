@@ -10,8 +10,11 @@ from paper_2601_12204_b300 import workloads as W
 pytestmark = pytest.mark.gpu
 
 # gradient bars: FP64 rel-L2 <= 1e-11 (dJ/du0), rel <= 1e-10 (dJ/dnu); FP32
-# rel-L2 <= 1e-4 and rel <= 1e-3 against the FP64 oracle gradient.
-GTOL = {F64: (1e-11, 1e-10), F32: (1e-4, 1e-3)}
+# rel-L2 <= 1e-4 and rel <= 1e-3 against the FP64 oracle gradient. dJ/dnu is
+# a sum over all steps and nodes that can cancel to far below its terms, so
+# its bar also has an absolute floor at (FP64: 1e-13, FP32: 1e-6) times the
+# largest |dJ/dnu| of the batch.
+GTOL = {F64: (1e-11, 1e-10, 1e-13), F32: (1e-4, 1e-3, 1e-6)}
 
 
 @pytest.fixture(scope="module")
@@ -64,12 +67,13 @@ def _gpu_grads(ctx, scheme, ens, dts, steps, gT, dtype, stride=0):
 
 
 def _check(ens, got, ref, gnu, gnu_ref, dtype, what):
-    tu, tn = GTOL[dtype]
+    tu, tn, tf = GTOL[dtype]
+    floor = tf * float(np.max(np.abs(gnu_ref)))
     for b in range(ens.count):
         o, n = ens.offsets[b], ens.ns[b]
         rel = oracle.rel_l2(got[o:o + n], ref[o:o + n])
         assert rel <= tu, f"{what} row {b} (n={n}, bc={ens.bcs[b]}): dJ/du0 rel L2 {rel:.3e}"
-        assert abs(gnu[b] - gnu_ref[b]) <= tn * max(abs(gnu_ref[b]), 1e-30), \
+        assert abs(gnu[b] - gnu_ref[b]) <= tn * abs(gnu_ref[b]) + floor, \
             f"{what} row {b}: dJ/dnu {gnu[b]!r} vs {gnu_ref[b]!r}"
 
 
@@ -174,4 +178,4 @@ def test_config5_sampled(ctx, scheme):
         o = ens.offsets[b]
         rel = oracle.rel_l2(got[o:o + N], ref[j * N:(j + 1) * N])
         assert rel <= 1e-4, f"row {b}: {rel}"
-        assert abs(gnu[b] - gnu_ref[j]) <= 1e-3 * abs(gnu_ref[j])
+        assert abs(gnu[b] - gnu_ref[j]) <= 1e-3 * abs(gnu_ref[j]) + 1e-6 * np.max(np.abs(gnu_ref))
