@@ -369,6 +369,9 @@ static burgers_status build_plan(burgers_ctx* ctx, int scheme, const burgers_bat
         L.to_scratch = false;
         p->launches.push_back(L);
       }
+      // the compensation buffers follow the row copy; keep every buffer start
+      // 256-byte aligned (the kernel's vector loads need 16-byte alignment)
+      span = (span + 63) & ~int64_t(63);
       p->stream_span = span;
       // ping-pong copy of the rows, plus two Kahan compensation buffers (FP32)
       p->scratch_elems = dtype == 0 ? 3 * span : span;

@@ -38,10 +38,13 @@ namespace burgers {
 // proportional to |delta| rather than |u|, and the FP32 addition is Kahan-
 // compensated like the explicit kernel. Dirichlet end rows and padding rows
 // are identity rows with a zero increment.
+// u^n and (FP32) the Kahan terms wait in shared memory, laid out [j][thread]
+// so a warp's accesses are conflict-free, while the elimination holds only its
+// three coefficient arrays in registers.
 template <typename T, int NT, int C, bool EXACT, int BCT>
 __device__ __forceinline__ void btcs_steps(T (&v)[C], int64_t nsteps, T r, T h, T s, int n,
                                            BtcsShared<T, NT>& sm, T* sh_last, T* sh_first,
-                                           T* sh_wrap) {
+                                           T* sh_wrap, T* un, T* lo) {
   constexpr int NW = NT / 32;
   constexpr bool WRAPX = (!EXACT && BCT == BC_PERIODIC);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -50,9 +53,11 @@ __device__ __forceinline__ void btcs_steps(T (&v)[C], int64_t nsteps, T r, T h, 
   const int jstar = n - 1 - base;                // local index of node n-1
   const int je = EXACT ? C - 1 : (jstar < C ? jstar : C - 1);  // chunk end row (<0: none)
   const T ds1 = T(1) + T(2) * s;
-  T ch[C], ah[C], dd[C], lo[C];
+  T ch[C], ah[C], dd[C];
+  if constexpr (Kahan<T>::on) {
 #pragma unroll
-  for (int j = 0; j < C; ++j) lo[j] = T(0);
+    for (int j = 0; j < C; ++j) lo[j * NT + tid] = T(0);
+  }
   for (int64_t step = 0; step < nsteps; ++step) {
     // ---- neighbour values of u^n across threads (as in the explicit kernel)
     const int p = int(step & 1);
@@ -89,6 +94,7 @@ __device__ __forceinline__ void btcs_steps(T (&v)[C], int64_t nsteps, T r, T h, 
 #pragma unroll
     for (int j = 0; j < C; ++j) {
       const T a = v[j];
+      un[j * NT + tid] = a;
       T ul = prev;
       T ur = (j + 1 < C) ? v[j + 1] : right;
       if constexpr (WRAPX) {
@@ -183,8 +189,14 @@ __device__ __forceinline__ void btcs_steps(T (&v)[C], int64_t nsteps, T r, T h, 
 #pragma unroll
       for (int j = 0; j < C; ++j) {
         const T delta = tfma(-ch[j], Xt, tfma(-ah[j], L, dd[j]));
-        v[j] = comp_add(v[j], delta, lo[j]);
+        T l0 = T(0);
+        if constexpr (Kahan<T>::on) l0 = lo[j * NT + tid];
+        v[j] = comp_add(un[j * NT + tid], delta, l0);
+        if constexpr (Kahan<T>::on) lo[j * NT + tid] = l0;
       }
+    } else {
+#pragma unroll
+      for (int j = 0; j < C; ++j) v[j] = un[j * NT + tid];
     }
   }
 }
@@ -197,6 +209,9 @@ __global__ void __launch_bounds__(NT) k_btcs_resident(T* __restrict__ u,
   __shared__ BtcsShared<T, NT> sm;
   __shared__ T sh_last[2 * NW], sh_first[2 * NW], sh_wrap[4];
   __shared__ int s_item;
+  extern __shared__ __align__(16) unsigned char dsm[];
+  T* un = reinterpret_cast<T*>(dsm);  // C * NT values
+  T* lo = un + C * NT;                // C * NT values (FP32)
   for (;;) {
     if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
     __syncthreads();
@@ -211,10 +226,10 @@ __global__ void __launch_bounds__(NT) k_btcs_resident(T* __restrict__ u,
     const T r = T(rd.r), h = T(0.5 * rd.r), s = T(rd.s);
     if (rd.bc == BC_PERIODIC)
       btcs_steps<T, NT, C, EXACT, BC_PERIODIC>(v, rd.nsteps, r, h, s, rd.n, sm, sh_last, sh_first,
-                                               sh_wrap);
+                                               sh_wrap, un, lo);
     else
       btcs_steps<T, NT, C, EXACT, BC_DIRICHLET>(v, rd.nsteps, r, h, s, rd.n, sm, sh_last,
-                                                sh_first, sh_wrap);
+                                                sh_first, sh_wrap, un, lo);
 #pragma unroll
     for (int j = 0; j < C; ++j)
       if (EXACT || base + j < rd.n) row[base + j] = v[j];
@@ -222,11 +237,14 @@ __global__ void __launch_bounds__(NT) k_btcs_resident(T* __restrict__ u,
   }
 }
 
-#define REG_BTCS(T, DT, NT, C)                                                           \
-  reg.push_back({K_BTCS_RESIDENT, DT, NT, C, 1,                                          \
-                 reinterpret_cast<const void*>(&k_btcs_resident<T, NT, C, true>), 0});  \
-  reg.push_back({K_BTCS_RESIDENT, DT, NT, C, 0,                                          \
-                 reinterpret_cast<const void*>(&k_btcs_resident<T, NT, C, false>), 0});
+#define BTCS_DSM(T, NT, C) (sizeof(T) * size_t(NT) * size_t(C) * (Kahan<T>::on ? 2 : 1))
+#define REG_BTCS(T, DT, NT, C)                                                                  \
+  reg.push_back({K_BTCS_RESIDENT, DT, NT, C, 1,                                                 \
+                 reinterpret_cast<const void*>(&k_btcs_resident<T, NT, C, true>),              \
+                 BTCS_DSM(T, NT, C)});                                                          \
+  reg.push_back({K_BTCS_RESIDENT, DT, NT, C, 0,                                                 \
+                 reinterpret_cast<const void*>(&k_btcs_resident<T, NT, C, false>),             \
+                 BTCS_DSM(T, NT, C)});
 
 void register_btcs(std::vector<KernelEntry>& reg) {
   REG_BTCS(float, 0, 32, 1) REG_BTCS(float, 0, 32, 2) REG_BTCS(float, 0, 32, 4)

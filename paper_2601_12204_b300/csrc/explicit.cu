@@ -206,7 +206,9 @@ __global__ void __launch_bounds__(NT) k_explicit_stream(const T* __restrict__ sr
     T v[C], lo[C];
     const int64_t g0 = ws + base;
     const bool interior = ws >= 0 && ws + W <= n;
-    const bool aligned = (reinterpret_cast<uintptr_t>(srow + ws) & 15) == 0;
+    bool aligned = (reinterpret_cast<uintptr_t>(srow + ws) & 15) == 0;
+    if constexpr (Kahan<T>::on)
+      aligned = aligned && (reinterpret_cast<uintptr_t>(lo_src + rd.offset + ws) & 15) == 0;
     if (interior && aligned && (C % Vec2<T>::width == 0)) {
       load_vec<T, C>(v, srow + g0);
       if constexpr (Kahan<T>::on) load_vec<T, C>(lo, lo_src + rd.offset + g0);

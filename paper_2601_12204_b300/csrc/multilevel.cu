@@ -324,6 +324,7 @@ burgers_status plan_multilevel(burgers_ctx* ctx, const burgers_batch* batch,
   p->ml_rows = int(mrows.size());
   int64_t span = 0;
   for (const MLRow& R : mrows) span = std::max<int64_t>(span, R.offset + R.n);
+  span = (span + 63) & ~int64_t(63);  // aligned start of the Kahan buffer
   p->ml_span = span;
   // ping-pong copy of the rows (+ the Kahan terms for FP32)
   p->scratch_elems = std::max<int64_t>(p->scratch_elems, dtype == 0 ? 2 * span : span);
