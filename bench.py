@@ -123,12 +123,20 @@ def dist_setup():
     return world, rank, local
 
 
+def shard_ids(rank: int, world: int, rows: int = B_ROWS) -> np.ndarray:
+    """Rows of the ensemble owned by `rank`: each rank solves its own `rows`
+    instances (weak scaling), instance ids rank*rows .. (rank+1)*rows - 1."""
+    return np.arange(rank * rows, (rank + 1) * rows, dtype=np.int64)
+
+
 def allreduce_max(x: float, world: int) -> float:
+    """Max over ranks (the slowest rank sets the job time)."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
@@ -244,7 +252,7 @@ def run_ours(args):
     F32, F64 = L.BURGERS_F32, L.BURGERS_F64
 
     t0 = time.perf_counter()
-    ids = np.arange(rank * B_ROWS, (rank + 1) * B_ROWS)
+    ids = shard_ids(rank, world)
     ens = W.fourier_ensemble(B_ROWS, N_NODES, ids=ids)
     log(f"[rank {rank}] ensemble generated in {time.perf_counter() - t0:.1f} s")
     u0 = torch.tensor(ens.u0, dtype=torch.float32, device=dev)

@@ -26,6 +26,7 @@ def main():
     ap.add_argument("--large", action="store_true", help="one row: sin x + 0.5 + noise")
     ap.add_argument("--stream-k", type=int, default=0)
     ap.add_argument("--repeat", type=int, default=1)
+    ap.add_argument("--autotune", action="store_true", help="tune launch shapes first and print the table")
     a = ap.parse_args()
 
     import torch
@@ -45,6 +46,13 @@ def main():
     fac = a.dt_factor if a.dt_factor is not None else (1.0 if a.case == "explicit" else 10.0)
     b = Batch.from_ensemble(ens, dt * fac, a.steps, dt_code)
     scheme = L.BURGERS_EXPLICIT if a.case == "explicit" else L.BURGERS_BTCS
+    if a.autotune:
+        import os
+        import tempfile
+        ntuned = ctx.autotune(scheme, b, u0, probe_steps=min(a.steps, 100))
+        path = os.path.join(tempfile.mkdtemp(), "tune.txt")
+        ctx.tune_save(path)
+        print(json.dumps({"tuned_classes": ntuned, "table": open(path).read().splitlines()[1:]}))
     times = []
     for _ in range(a.repeat):
         u = u0.clone()
