@@ -159,6 +159,23 @@ burgers_status burgers_explicit_advance(burgers_ctx* ctx, const burgers_batch* b
 burgers_status burgers_btcs_advance(burgers_ctx* ctx, const burgers_batch* batch,
                                     void* u_dev, burgers_stream stream);
 
+/* burgers_explicit_advance for one row, without allocating device memory.
+ * The paper has no counterpart: this exists for callers that cannot allocate
+ * device memory while they run (an arena that already owns the GPU's memory,
+ * a service with a fixed footprint, code called under another allocator's
+ * lock). The streaming kernel's working buffers sit in a 16 MiB file-scope
+ * device array that every GPU loading this library holds until exit; the
+ * caller passes the row. `inst` describes the row (its offset is applied to
+ * u_dev); `dtype` is BURGERS_F32 or BURGERS_F64. Limits: 128 <= n <= 1048576
+ * (EINVAL beyond, u untouched). The first call on a device looks up the
+ * array's device address with that device current; make that first call
+ * before any stream capture. Every call shares the array and leaves its
+ * contents behind (each call clears what must start at zero), so calls whose
+ * work overlaps on the GPU race and must be serialised by the caller.
+ * Asynchronous on `stream`; calls no cudaMalloc or cudaFree. */
+burgers_status burgers_explicit_advance_noalloc(const burgers_instance* inst, int32_t dtype,
+                                                void* u_dev, burgers_stream stream);
+
 /* End-to-end variant through host memory: copies every row from u_host to a
  * context-owned device buffer, advances it with `scheme` (burgers_scheme),
  * copies the rows back into u_host. Blocking. u_host should be pinned for

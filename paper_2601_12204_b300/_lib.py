@@ -77,6 +77,7 @@ SIGNATURES = {
     "burgers_rel_l2": (_ST, [_P, _P, _P, _P, _I32, _P, _P, _P]),
     "burgers_adjoint": (_ST, [_P, _I32, _P, _P, _P, _P, _P, _I64, _P]),
     "burgers_autotune": (_ST, [_P, _I32, _P, _P, _I64, _P, _P]),
+    "burgers_explicit_advance_noalloc": (_ST, [_P, _I32, _P, _P]),
     "burgers_tune_save": (_ST, [_P, ctypes.c_char_p]),
     "burgers_tune_load": (_ST, [_P, ctypes.c_char_p]),
 }
