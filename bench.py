@@ -336,6 +336,9 @@ def run_ours(args):
 
     if not args.quick:
         res.update(extras(args, ctx, ens, u0, batches, probe, dev, world, rank))
+        if args.serve_seconds > 0 and world == 1:
+            log("serving ...")
+            res["serve"] = serve_bench(ctx, dev, args.serve_seconds)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         log("cpu baseline ...")
         res["cpu_baseline"] = cpu_baseline_sample()
@@ -465,6 +468,119 @@ def extras(args, ctx, ens, u0, batches, probe, dev, world, rank):
     return out
 
 
+def serve_bench(ctx, dev, duration: float, rate: float = 20000.0, plain_seconds: float = 5.0):
+    """Configuration 4: Poisson arrivals at `rate` for `duration` s of mixed
+    requests through the continuous-batching server; latency = done - submit
+    on the server clock. Also the plain path: the same trace served one
+    request per launch, in arrival order, for at most `plain_seconds`."""
+    import torch
+
+    from paper_2601_12204_b300 import _lib as L
+    from paper_2601_12204_b300 import workloads as W
+    from paper_2601_12204_b300.api import Batch, Server
+
+    t0 = time.perf_counter()
+    trace = W.serving_trace(rate=rate, duration=duration, with_u0=False)
+    u0d, offs = W.fourier_rows_torch(trace, dev, torch.float32)
+    ns = np.array([q.n for q in trace])
+    probe = Batch(L.BURGERS_F32, offs, ns, [q.bc for q in trace], [q.dx for q in trace],
+                  [q.nu for q in trace], 1.0, 0)
+    dt0 = ctx.cfl_dt(probe, u0d, CFL)
+    dts = np.where(np.array([q.scheme for q in trace]) == L.BURGERS_BTCS, BTCS_DT_FACTOR, 1.0) * dt0
+    host = u0d.cpu().pin_memory()
+    base = host.data_ptr()
+    del u0d
+    log(f"serving trace: {len(trace)} requests generated in {time.perf_counter() - t0:.1f} s")
+    cells = ns.astype(np.float64) * np.array([q.nsteps for q in trace])
+
+    sv = Server(ctx, L.BURGERS_F32, slice_steps=256)
+    # warm-up: a handful of requests of each kind
+    for q, o, dt in list(zip(trace, offs, dts))[:32]:
+        t = sv._submit_ptr(q.scheme, q.bc, q.n, base + 4 * int(o), q.dx, q.nu, dt, 50)
+        sv.wait(t, q.n, timeout_s=60)
+    import threading
+    done = {}
+    lock = threading.Lock()
+    finished = threading.Event()
+
+    def collector(expected):
+        got = 0
+        deadline = time.perf_counter() + duration + 600
+        while got < expected and time.perf_counter() < deadline:
+            tk = sv.wait_any(1.0)
+            if tk is None:
+                continue
+            n = tickets_n[tk]
+            rc, _, st = sv.poll(tk, n)
+            with lock:
+                done[tk] = (rc, st.t_submit, st.t_admit, st.t_done)
+            got += 1
+        finished.set()
+
+    tickets_n = {}
+    order = []
+    th = threading.Thread(target=collector, args=(len(trace),), daemon=True)
+    start = time.perf_counter()
+    th.start()
+    late = 0.0
+    for q, o, dt in zip(trace, offs, dts):
+        wait = start + q.t_arrive - time.perf_counter()
+        if wait > 0:
+            time.sleep(wait)
+        else:
+            late = max(late, -wait)
+        tk = sv._submit_ptr(q.scheme, q.bc, q.n, base + 4 * int(o), q.dx, q.nu, dt, q.nsteps)
+        tickets_n[tk] = q.n
+        order.append(tk)
+    finished.wait(duration + 600)
+    stats = sv.stats()
+    sv.close()
+    lat = np.array([done[t][3] - done[t][1] for t in order if t in done and done[t][0] == 0])
+    t_first = min(done[t][1] for t in order if t in done)
+    t_last = max(done[t][3] for t in order if t in done)
+    ok = [i for i, t in enumerate(order) if t in done and done[t][0] == 0]
+    res = {"requests": len(trace), "completed": len(ok), "rate_req_s": rate,
+           "trace_seconds": duration,
+           "p50_ms": 1e3 * float(np.percentile(lat, 50)), "p99_ms": 1e3 * float(np.percentile(lat, 99)),
+           "p999_ms": 1e3 * float(np.percentile(lat, 99.9)),
+           "throughput_cups": float(cells[ok].sum()) / (t_last - t_first),
+           "offered_cups": float(cells.sum()) / duration,
+           "max_submit_lag_ms": 1e3 * late, "slices": stats["slices"],
+           "active_max": stats["active_max"], "pool_bytes": stats["pool_bytes"],
+           "pool_used_max": stats["pool_used_max"], "slice_steps": 256, "dtype": "f32"}
+    # plain path: one request per launch, FIFO in arrival order
+    ctx.set(L.BURGERS_OPT_PLAIN, 1)
+    buf = torch.empty(int(ns.max()), dtype=torch.float32, device=dev)
+    lat_p, t_end = [], None
+    start = time.perf_counter()
+    k = 0
+    for q, o, dt in zip(trace, offs, dts):
+        now = time.perf_counter() - start
+        if now > plain_seconds:
+            break
+        if q.t_arrive > now:
+            time.sleep(q.t_arrive - now)
+        buf[:q.n].copy_(host[int(o):int(o) + q.n], non_blocking=False)
+        b = Batch(L.BURGERS_F32, [0], [q.n], [q.bc], [q.dx], [q.nu], [dt], [q.nsteps])
+        ctx.advance(q.scheme, b, buf)
+        out = buf[:q.n].cpu()
+        del out
+        lat_p.append(time.perf_counter() - start - q.t_arrive)
+        k += 1
+    t_end = time.perf_counter() - start
+    ctx.set(L.BURGERS_OPT_PLAIN, 0)
+    # requests that had arrived but were still waiting when the plain run stopped
+    backlog = [t_end - q.t_arrive for q in trace[k:] if q.t_arrive < t_end]
+    allp = np.array(lat_p + backlog)
+    res["plain"] = {"completed": k, "seconds": t_end, "backlog_at_stop": len(backlog),
+                    "p50_ms_lower_bound": 1e3 * float(np.percentile(allp, 50)),
+                    "p99_ms_lower_bound": 1e3 * float(np.percentile(allp, 99)),
+                    "throughput_cups": float(cells[:k].sum()) / t_end,
+                    "note": "same trace, one request per kernel launch in arrival order; waiting "
+                            "requests at the stop count with their wait so far (lower bounds)"}
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -473,6 +589,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--quick", action="store_true", help="skip the side measurements")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve-seconds", type=float, default=1.0,
+                    help="length of the Poisson trace of the serving measurement (0 = skip)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -282,6 +282,12 @@ burgers_status burgers_serve_poll(burgers_server* sv, uint64_t ticket, void* out
 burgers_status burgers_serve_wait(burgers_server* sv, uint64_t ticket, double timeout_s,
                                   void* out_host, burgers_req_stats* stats);
 
+/* Blocks until some request has finished (done, cancelled or failed) that
+ * this call has not reported before and that poll/wait have not taken yet;
+ * writes its ticket (then poll it to take the result). ETIMEOUT if none
+ * finishes within timeout_s seconds. */
+burgers_status burgers_serve_wait_any(burgers_server* sv, double timeout_s, uint64_t* ticket);
+
 /* Cancels a request: removed from the queue, or from the device at the next
  * slice boundary; its poll then returns ECANCELED. */
 burgers_status burgers_serve_cancel(burgers_server* sv, uint64_t ticket);

@@ -115,6 +115,7 @@ SIGNATURES.update({
     "burgers_serve_poll": (_ST, [_P, ctypes.c_uint64, _P, _P]),
     "burgers_serve_wait": (_ST, [_P, ctypes.c_uint64, _D, _P, _P]),
     "burgers_serve_cancel": (_ST, [_P, ctypes.c_uint64]),
+    "burgers_serve_wait_any": (_ST, [_P, _D, ctypes.POINTER(ctypes.c_uint64)]),
     "burgers_serve_get_stats": (_ST, [_P, _P]),
     "burgers_serve_destroy": (_ST, [_P]),
 })

@@ -232,6 +232,16 @@ class Server:
                 "burgers_serve_submit")
         return int(t.value)
 
+    def _submit_ptr(self, scheme: int, bc: int, n: int, u0_ptr: int, dx: float, nu: float,
+                    dt: float, nsteps: int) -> int:
+        """submit() from a raw host pointer to n values of the server dtype."""
+        rq = L.burgers_request(int(scheme), int(bc), int(n), 0, float(dx), float(nu), float(dt),
+                               int(nsteps), int(u0_ptr))
+        t = ctypes.c_uint64(0)
+        L.check(self._lib.burgers_serve_submit(self.h, ctypes.byref(rq), ctypes.byref(t)),
+                "burgers_serve_submit")
+        return int(t.value)
+
     def _result(self, fn, ticket, n, *extra):
         out = np.empty(n, dtype=self.np_dtype)
         st = L.burgers_req_stats()
@@ -247,6 +257,12 @@ class Server:
         rc, out, st = self._result(self._lib.burgers_serve_wait, ticket, n,
                                    ctypes.c_double(timeout_s))
         return rc, (out if rc == L.BURGERS_OK else None), st
+
+    def wait_any(self, timeout_s: float = 1.0):
+        """Ticket of the next finished request, or None on timeout."""
+        t = ctypes.c_uint64(0)
+        rc = self._lib.burgers_serve_wait_any(self.h, float(timeout_s), ctypes.byref(t))
+        return int(t.value) if rc == L.BURGERS_OK else None
 
     def cancel(self, ticket: int) -> int:
         return int(self._lib.burgers_serve_cancel(self.h, ctypes.c_uint64(ticket)))

@@ -24,17 +24,20 @@ struct BtcsShared {
 template <typename T, int NT, bool CYC>
 __device__ __forceinline__ void reduced_solve(BtcsShared<T, NT>& sm, int tl, int lane) {
   constexpr int Q = NT / 32;
-  double fad = 0.0;  // A_0 / gamma of the Sherman-Morrison split, FP64
+  // Sherman-Morrison split: gamma = -B_0, v = e_0 + (A_0/gamma) e_tl. The ratio
+  // is rounded once to T and used both in the modified diagonal and in v, so
+  // T~ + u v^T reproduces the cyclic matrix.
+  T fa = T(0);
   if constexpr (CYC) {
     const T A0 = sm.A[sk(0)], B0 = sm.B[sk(0)], Ct = sm.Cc[sk(tl)], Bt = sm.B[sk(tl)];
     const T gam = -B0;
-    fad = double(A0) / double(gam);
+    fa = A0 / gam;
     __syncwarp();
     if (lane == 0) {
       sm.B[sk(0)] = B0 - gam;
       sm.A[sk(0)] = T(0);
       sm.U[sk(0)] = gam;
-      sm.B[sk(tl)] = Bt - Ct * T(fad);
+      sm.B[sk(tl)] = Bt - Ct * fa;
       sm.Cc[sk(tl)] = T(0);
       sm.U[sk(tl)] = Ct;
     }
@@ -118,14 +121,18 @@ __device__ __forceinline__ void reduced_solve(BtcsShared<T, NT>& sm, int tl, int
   }
   if constexpr (CYC) {
     __syncwarp();
-    // x = y - (v.y)/(1 + v.z) z,  v = e_0 + (A_0/gamma) e_tl
-    const double y0 = double(sm.X[0]), yt = double(sm.X[tl]);
-    const double z0 = double(sm.rd[0]), zt = double(sm.rd[tl]);
-    const double fac = (y0 + fad * yt) / (1.0 + z0 + fad * zt);
-    __syncwarp();
+    // x = y - (v.y)/(1 + v.z) z: dot products and denominator in FP64, on one
+    // lane (the FP64 pipe is narrow), the factor broadcast in T.
+    T fac = T(0);
+    if (lane == 0) {
+      const double fd = double(fa);
+      const double vy = double(sm.X[0]) + fd * double(sm.X[tl]);
+      const double vz = double(sm.rd[0]) + fd * double(sm.rd[tl]);
+      fac = T(vy / (1.0 + vz));
+    }
+    fac = shfl(fac, 0);
 #pragma unroll
-    for (int q = 0; q < Q; ++q)
-      sm.X[r0 + q] = T(double(sm.X[r0 + q]) - fac * double(sm.rd[r0 + q]));
+    for (int q = 0; q < Q; ++q) sm.X[r0 + q] = tfma(-fac, sm.rd[r0 + q], sm.X[r0 + q]);
   }
 }
 

@@ -127,6 +127,7 @@ struct burgers_server {
   std::deque<burgers::Req*> pending;
   std::vector<burgers::Req*> active;
   std::unordered_map<uint64_t, std::unique_ptr<burgers::Req>> reqs;
+  std::deque<uint64_t> done_q;  // finished tickets not yet reported by wait_any
   uint64_t next_ticket = 1;
   bool stop = false;
   burgers_status fault = BURGERS_OK;
@@ -154,6 +155,7 @@ static void admit(burgers_server* sv, std::vector<Req*>* admitted) {
       q->state = RQ_CANCELED;
       q->status = BURGERS_ECANCELED;
       q->t_done = now_s() - sv->t0;
+      sv->done_q.push_back(q->ticket);
       sv->cv_done.notify_all();
       continue;
     }
@@ -177,10 +179,12 @@ static void fail_all(burgers_server* sv, burgers_status st, const std::string& m
   for (Req* q : sv->active) {
     q->state = RQ_FAILED;
     q->status = st;
+    sv->done_q.push_back(q->ticket);
   }
   for (Req* q : sv->pending) {
     q->state = RQ_FAILED;
     q->status = st;
+    sv->done_q.push_back(q->ticket);
   }
   sv->active.clear();
   sv->pending.clear();
@@ -218,6 +222,7 @@ static void worker_loop(burgers_server* sv) {
             q->state = RQ_CANCELED;
             q->status = BURGERS_ECANCELED;
             q->t_done = now_s() - sv->t0;
+            sv->done_q.push_back(q->ticket);
             sv->active[i] = sv->active.back();
             sv->active.pop_back();
             sv->cv_done.notify_all();
@@ -312,6 +317,7 @@ static void worker_loop(burgers_server* sv) {
         (q->long_row ? sv->long_region : sv->short_region).release(q->off, q->bytes);
         q->state = RQ_DONE;
         q->t_done = t;
+        sv->done_q.push_back(q->ticket);
         sv->stats.completed += 1;
         sv->stats.cell_updates += double(q->r.n) * double(q->r.nsteps);
         std::vector<unsigned char>().swap(q->u0);
@@ -455,6 +461,25 @@ burgers_status burgers_serve_wait(burgers_server* sv, uint64_t ticket, double ti
       return set_error(BURGERS_ETIMEOUT, "request not finished before the timeout");
   }
   return take_result(sv, q, out_host, rs);
+}
+
+burgers_status burgers_serve_wait_any(burgers_server* sv, double timeout_s, uint64_t* ticket) {
+  if (!sv || !ticket) return set_error(BURGERS_EINVAL, "NULL argument");
+  std::unique_lock<std::mutex> lk(sv->mu);
+  const auto deadline = std::chrono::steady_clock::now() +
+                        std::chrono::microseconds(int64_t(std::max(0.0, timeout_s) * 1e6));
+  for (;;) {
+    while (!sv->done_q.empty()) {
+      const uint64_t t = sv->done_q.front();
+      sv->done_q.pop_front();
+      if (sv->reqs.count(t)) {  // skip tickets already taken by poll / wait
+        *ticket = t;
+        return BURGERS_OK;
+      }
+    }
+    if (sv->cv_done.wait_until(lk, deadline) == std::cv_status::timeout && sv->done_q.empty())
+      return set_error(BURGERS_ETIMEOUT, "no request finished before the timeout");
+  }
 }
 
 burgers_status burgers_serve_cancel(burgers_server* sv, uint64_t ticket) {

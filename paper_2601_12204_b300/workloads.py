@@ -188,6 +188,8 @@ class Request:
     nu: float
     dx: float
     u0: np.ndarray
+    a: np.ndarray = None
+    phi: np.ndarray = None
 
 
 def serving_trace(rate: float = 20000.0, duration: float = 10.0, seed: int = DEFAULT_SEED,
@@ -211,6 +213,34 @@ def serving_trace(rate: float = 20000.0, duration: float = 10.0, seed: int = DEF
         a, phi, nu = fourier_coeffs(seed, (1 << 34) + rid)
         x, dx = grid(n, bc, 0.0, TWO_PI)
         u0 = fourier_field(x, a, phi) if with_u0 else None
-        out.append(Request(rid, t, scheme, bc, n, nsteps, nu, dx, u0))
+        out.append(Request(rid, t, scheme, bc, n, nsteps, nu, dx, u0, a, phi))
         rid += 1
     return out
+
+
+def fourier_rows_torch(reqs, device, dtype, chunk: int = 1 << 24):
+    """Packs the random-Fourier initial fields of `reqs` (Requests with their
+    coefficients) into one device tensor, evaluated with torch on `device`.
+    Returns (tensor, offsets). Same recipe as fourier_field on each request's
+    grid (periodic: dx = 2 pi/n, Dirichlet: dx = 2 pi/(n-1))."""
+    import torch
+    ns = np.array([q.n for q in reqs], dtype=np.int64)
+    offs = np.zeros(ns.size, dtype=np.int64)
+    offs[1:] = np.cumsum(ns[:-1])
+    total = int(ns.sum())
+    out = torch.empty(total, dtype=dtype, device=device)
+    A = torch.tensor(np.stack([q.a for q in reqs]), dtype=torch.float64, device=device)
+    P = torch.tensor(np.stack([q.phi for q in reqs]), dtype=torch.float64, device=device)
+    dxs = torch.tensor([q.dx for q in reqs], dtype=torch.float64, device=device)
+    row_of = torch.repeat_interleave(torch.arange(ns.size, device=device),
+                                     torch.tensor(ns, device=device))
+    start = torch.tensor(offs, device=device)
+    k = torch.arange(1, A.shape[1] + 1, dtype=torch.float64, device=device)
+    for lo in range(0, total, chunk):
+        hi = min(total, lo + chunk)
+        r = row_of[lo:hi]
+        i = torch.arange(lo, hi, device=device) - start[r]
+        x = i.to(torch.float64) * dxs[r]
+        u = torch.sum(A[r] * torch.sin(k[None, :] * x[:, None] + P[r]), dim=1)
+        out[lo:hi] = u.to(dtype)
+    return out, offs

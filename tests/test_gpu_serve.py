@@ -23,8 +23,8 @@ def ctx():
     c.close()
 
 
-def _requests(count, seed, nmax=20000, smax=300):
-    reqs = W.serving_trace(rate=1e6, duration=1.0, seed=seed, nmin=3, nmax=nmax, smin=0,
+def _requests(count, seed, nmax=20000, smax=300, nmin=3):
+    reqs = W.serving_trace(rate=1e6, duration=1.0, seed=seed, nmin=nmin, nmax=nmax, smin=0,
                            smax=smax, max_requests=count)
     out = []
     for q in reqs:
@@ -72,8 +72,7 @@ def test_serve_admission_by_free_memory(ctx):
     refused at submission."""
     from paper_2601_12204_b300.api import Server
     sv = Server(ctx, F32, hbm_budget=4 << 20, slice_steps=32)  # 2 MiB pool
-    reqs = _requests(40, seed=6, nmax=30000, smax=120)
-    reqs = [(q, dt) for q, dt in reqs if q.n * 4 <= (3 << 19)]
+    reqs = _requests(24, seed=6, nmin=20000, nmax=60000, smax=120)
     tickets = [sv.submit(q.scheme, q.bc, q.u0, q.dx, q.nu, dt, q.nsteps) for q, dt in reqs]
     total = sum(q.n * 4 for q, _ in reqs)
     assert total > sv.stats()["pool_bytes"]
