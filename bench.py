@@ -38,12 +38,14 @@ CELLS_PER_STEP = B_ROWS * N_NODES * (EXPLICIT_STEPS + BTCS_STEPS)
 WORKLOAD = (f"batched ensemble: {B_ROWS} periodic rows x {N_NODES} nodes, random-Fourier u0, "
             f"nu log-U[1e-3,1e-1]; CFL dt on device; {EXPLICIT_STEPS} explicit steps at CFL 0.4 + "
             f"{BTCS_STEPS} BTCS steps at 10x dt, both from u0")
-# FP32 lane-instructions per cell-update issued by the explicit kernel (Eq. 21 as
-# u + (s + h|u|)(ur - 2u + ul) - h u (ur - ul), with dl_i = dr_{i-1} shared)
-EXPLICIT_OPS = 7
-# BTCS per cell-update: assembly 5, forward elimination 7 (+1 reciprocal on the
-# MUFU pipe), backward 3, back-substitution 2
-BTCS_OPS = 17
+# FMA-pipe FP32 lane-instructions per cell-update of the explicit kernel: the
+# increment (s - r u-)(ur - u) - (s + r u+)(u - ul) costs one difference (the
+# other is the neighbour's), two FMA for the coefficients and two FMA, plus three
+# for the Kahan-compensated addition; its two min/max run on the ALU pipe.
+EXPLICIT_OPS = 8
+# BTCS: assembly 4 + right-hand side 3 + forward elimination 6 (+1 MUFU rcp) +
+# backward 3 + back-substitution 2 + compensated addition 4 (+2 min/max on ALU)
+BTCS_OPS = 22
 SMS, FP32_LANES = 148, 128
 
 
@@ -323,14 +325,15 @@ def run_ours(args):
         "bound": "alu", "kernel": "k_explicit_resident<float,256,16,exact>",
         "achieved": ach, "peak": peak_ops, "unit": "Tops/s (FP32 lane-instructions)",
         "frac": ach / peak_ops, "traffic": traffic_record("explicit_resident_f32_4096"),
-        "per_unit": f"{EXPLICIT_OPS} FP32 instr per cell-update; 16 MiB rows x 2000 steps per launch",
+        "per_unit": f"{EXPLICIT_OPS} FMA-pipe FP32 instr per cell-update (+2 ALU min/max); "
+                    f"4096 rows x 4096 nodes x 2000 steps per launch",
         "peak_note": "148 SMs x 128 FP32 lanes x 2032 MHz (max SM clock)",
         "kernel_ms": t_expl}
     achb = BTCS_OPS * B_ROWS * N_NODES * BTCS_STEPS / (t_btcs / 1000.0) / 1e12
     res["roofline_btcs"] = {"bound": "alu", "kernel": "k_btcs_resident<float,256,16,exact>",
                             "achieved": achb, "peak": peak_ops, "unit": "Tops/s (FP32 lane-instructions)",
                             "frac": achb / peak_ops, "kernel_ms": t_btcs,
-                            "per_unit": f"{BTCS_OPS} FP32 instr + 1 MUFU rcp per cell-update"}
+                            "per_unit": f"{BTCS_OPS} FMA-pipe FP32 instr + 1 MUFU rcp + 2 ALU per cell-update"}
     res["explicit_cups"] = B_ROWS * N_NODES * EXPLICIT_STEPS / (t_expl / 1000.0)
     res["btcs_cups"] = B_ROWS * N_NODES * BTCS_STEPS / (t_btcs / 1000.0)
 
@@ -456,7 +459,7 @@ def extras(args, ctx, ens, u0, batches, probe, dev, world, rank):
             large["explicit_cups"] = cups
             large["explicit_steps"] = steps
         else:
-            gbs = 8.0 * lg.ns[0] * steps / t / 1e9
+            gbs = 16.0 * float(lg.ns[0]) * steps / t / 1e9
             large["stream_k1_cups"] = cups
             large["stream_k1_gbs"] = gbs
             large["stream_k1_hbm_frac"] = gbs / 6502.8

@@ -42,7 +42,7 @@ namespace burgers {
 // so a warp's accesses are conflict-free, while the elimination holds only its
 // three coefficient arrays in registers.
 template <typename T, int NT, int C, bool EXACT, int BCT>
-__device__ __forceinline__ void btcs_steps(T (&v)[C], int64_t nsteps, T r, T h, T s, int n,
+__device__ __forceinline__ void btcs_steps(T (&v)[C], int64_t nsteps, T r, T s, int n,
                                            BtcsShared<T, NT>& sm, T* sh_last, T* sh_first,
                                            T* sh_wrap, T* un, T* lo) {
   constexpr int NW = NT / 32;
@@ -106,7 +106,8 @@ __device__ __forceinline__ void btcs_steps(T (&v)[C], int64_t nsteps, T r, T h, 
       T l = -s - tmax(ra, T(0));
       T c = tmin(ra, T(0)) - s;
       T d = ds1 + tabs(ra);
-      T rhs = explicit_increment(a, ul, ur, h, s, T(0));
+      // explicit increment (Eq. 21) from the same coefficients: -c (ur - a) + l (a - ul)
+      T rhs = tfma(l, a - ul, -c * (ur - a));
       bool ident = false;
       if constexpr (BCT == BC_DIRICHLET) {
         if constexpr (EXACT)
@@ -223,12 +224,12 @@ __global__ void __launch_bounds__(NT) k_btcs_resident(T* __restrict__ u,
     T v[C];
 #pragma unroll
     for (int j = 0; j < C; ++j) v[j] = (EXACT || base + j < rd.n) ? row[base + j] : T(0);
-    const T r = T(rd.r), h = T(0.5 * rd.r), s = T(rd.s);
+    const T r = T(rd.r), s = T(rd.s);
     if (rd.bc == BC_PERIODIC)
-      btcs_steps<T, NT, C, EXACT, BC_PERIODIC>(v, rd.nsteps, r, h, s, rd.n, sm, sh_last, sh_first,
+      btcs_steps<T, NT, C, EXACT, BC_PERIODIC>(v, rd.nsteps, r, s, rd.n, sm, sh_last, sh_first,
                                                sh_wrap, un, lo);
     else
-      btcs_steps<T, NT, C, EXACT, BC_DIRICHLET>(v, rd.nsteps, r, h, s, rd.n, sm, sh_last,
+      btcs_steps<T, NT, C, EXACT, BC_DIRICHLET>(v, rd.nsteps, r, s, rd.n, sm, sh_last,
                                                 sh_first, sh_wrap, un, lo);
 #pragma unroll
     for (int j = 0; j < C; ++j)

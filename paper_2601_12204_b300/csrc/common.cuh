@@ -57,19 +57,17 @@ __device__ __forceinline__ T shfl_down(T v, int d) {
 
 // Explicit forward-Euler upwind/central increment of node value u with left
 // and right neighbours ul, ur (Eq. 21 with the upwind side of Sec. 2.2):
-//   u' - u = -r (u+ (u - ul) + u- (ur - u)) + s (ur - 2u + ul).
-// Using u+ = (u + |u|)/2 and u- = (u - |u|)/2 this is
-//   u' - u = (s + h |u|) (ur - 2u + ul) - h u (ur - ul),   h = r/2,
-// returned plus `add`. Six FP instructions (|u| is an operand modifier and
-// dl of node i is dr of node i-1, so five when inlined in a sweep).
+//   u' - u = -r (u+ (u - ul) + u- (ur - u)) + s (ur - 2u + ul)
+//          = (s - r u-) (ur - u) - (s + r u+) (u - ul),
+// returned plus `add`. Per node: one difference (u - ul is the previous
+// node's ur - u), two min/max (ALU pipe), four FMA-pipe operations.
 template <typename T>
-__device__ __forceinline__ T explicit_increment(T u, T ul, T ur, T h, T s, T add) {
+__device__ __forceinline__ T explicit_increment(T u, T ul, T ur, T r, T s, T add) {
   const T dr = ur - u;
   const T dl = u - ul;
-  const T d2 = dr - dl;
-  const T d1 = dr + dl;
-  const T c = tfma(h, tabs(u), s);
-  return tfma(c, d2, tfma(-h * u, d1, add));
+  const T p = tfma(-r, tmin(u, T(0)), s);
+  const T q = tfma(r, tmax(u, T(0)), s);
+  return tfma(p, dr, tfma(-q, dl, add));
 }
 
 // u' = u + increment. FP64 adds directly (one rounding per step is far below
@@ -89,15 +87,15 @@ struct Kahan<float> {
 };
 
 template <typename T>
-__device__ __forceinline__ T explicit_update(T u, T ul, T ur, T h, T s, T& lo) {
+__device__ __forceinline__ T explicit_update(T u, T ul, T ur, T r, T s, T& lo) {
   if constexpr (Kahan<T>::on) {
-    const T y = explicit_increment(u, ul, ur, h, s, -lo);
+    const T y = explicit_increment(u, ul, ur, r, s, -lo);
     const T t = u + y;
     lo = (t - u) - y;
     return t;
   } else {
     (void)lo;
-    return explicit_increment(u, ul, ur, h, s, u);
+    return explicit_increment(u, ul, ur, r, s, u);
   }
 }
 

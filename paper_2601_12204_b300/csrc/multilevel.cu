@@ -68,7 +68,7 @@ struct NodeRows {
   int64_t n;
   int64_t base;
   int je;
-  T r, h, s, ds1;
+  T r, s, ds1;
   bool dir;
   __device__ __forceinline__ void operator()(int j, T& l, T& d, T& c, T& rhs) const {
     const int64_t gi = base + j;
@@ -80,7 +80,7 @@ struct NodeRows {
     l = -s - tmax(ra, T(0));
     c = tmin(ra, T(0)) - s;
     d = ds1 + tabs(ra);
-    rhs = explicit_increment(a, ul, ur, h, s, T(0));
+    rhs = tfma(l, a - ul, -c * (ur - a));  // explicit increment from the same coefficients
     if (dir && (gi == 0 || gi == n - 1)) { l = T(0); c = T(0); d = T(1); rhs = T(0); }
   }
 };
@@ -117,7 +117,7 @@ __global__ void __launch_bounds__(NT) k_ml_sweep(T* __restrict__ u, T* __restric
     T e_ch, e_ah, e_dh;
     if constexpr (LVL0) {
       const T s = T(R.s);
-      NodeRows<T> rsrc{src + R.offset, M, base, je, T(R.r), T(0.5 * R.r), s, T(1) + T(2) * s,
+      NodeRows<T> rsrc{src + R.offset, M, base, je, T(R.r), s, T(1) + T(2) * s,
                        R.bc == BC_DIRICHLET};
       chunk_forward<T, C>(v, ah, ch, je, rsrc, e_ch, e_ah, e_dh);
     } else {
