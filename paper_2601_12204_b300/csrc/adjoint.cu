@@ -78,7 +78,7 @@ __device__ __forceinline__ void nbrs(const T (&v)[C], int j, int jstar, T left, 
 // one explicit forward step of the resident layout (generic, padding aware)
 template <typename T, int NT, int C>
 __device__ __forceinline__ void fwd_explicit_step(T (&v)[C], T (&lo)[C], int n, int base, bool per,
-                                                  T r, T s, Xch<T, NT>& xs, int& p) {
+                                                  T r, T h, T s, Xch<T, NT>& xs, int& p) {
   const int jstar = n - 1 - base;
   xch_publish<T, NT, C>(v, jstar, xs, p);
   __syncthreads();
@@ -93,7 +93,7 @@ __device__ __forceinline__ void fwd_explicit_step(T (&v)[C], T (&lo)[C], int n, 
     if (j == jstar) ur = wr;
     const T cur = v[j];
     const T lo0 = lo[j];
-    T nv = explicit_update(cur, ul, ur, r, s, lo[j]);
+    T nv = explicit_update(cur, ul, ur, r, h, s, lo[j]);
     const bool keep = gi >= n || (!per && (gi == 0 || gi == n - 1));
     if (keep) { nv = cur; lo[j] = lo0; }
     prev = cur;
@@ -204,7 +204,7 @@ __global__ void __launch_bounds__(NT) k_adjoint(const T* __restrict__ u0, const 
     const AdjRow ar = arows[item];
     const int n = rd.n, base = tid * C, jstar = n - 1 - base;
     const bool per = rd.bc == BC_PERIODIC;
-    const T r = T(rd.r), s = T(rd.s);
+    const T r = T(rd.r), s = T(rd.s), h = T(0.5 * rd.r);
     const int64_t ns = rd.nsteps, k = ar.stride;
     // checkpoints: ar.nckpt states of n values (FP32: followed by the n Kahan terms)
     constexpr int CKW = Kahan<T>::on ? 2 : 1;
@@ -229,7 +229,7 @@ __global__ void __launch_bounds__(NT) k_adjoint(const T* __restrict__ u0, const 
           }
       }
       if (st + 1 == ns) break;  // the last state is not needed
-      if constexpr (SCHEME == 0) fwd_explicit_step<T, NT, C>(v, lo, n, base, per, r, s, sm.xa, p);
+      if constexpr (SCHEME == 0) fwd_explicit_step<T, NT, C>(v, lo, n, base, per, r, h, s, sm.xa, p);
       else fwd_btcs_step<T, NT, C>(v, lo, n, base, per, r, s, sm.bt, sm.xa, p);
     }
     // ---- reverse pass
@@ -254,7 +254,7 @@ __global__ void __launch_bounds__(NT) k_adjoint(const T* __restrict__ u0, const 
         for (int j = 0; j < C; ++j)
           if (base + j < n) dst[base + j] = v[j];
         if (st == last) break;
-        if constexpr (SCHEME == 0) fwd_explicit_step<T, NT, C>(v, lo, n, base, per, r, s, sm.xa, p);
+        if constexpr (SCHEME == 0) fwd_explicit_step<T, NT, C>(v, lo, n, base, per, r, h, s, sm.xa, p);
         else fwd_btcs_step<T, NT, C>(v, lo, n, base, per, r, s, sm.bt, sm.xa, p);
       }
       for (int64_t st = s1 - 1; st >= s0; --st) {

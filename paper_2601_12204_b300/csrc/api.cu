@@ -85,11 +85,11 @@ static const std::vector<Shape>& resident_shapes(int kind, int dtype) {
   static const std::vector<Shape> ex64 = {{32, 1},  {32, 2},   {32, 4},  {32, 8},   {64, 8},
                                           {128, 8}, {256, 8},  {128, 16}, {512, 8}, {256, 16},
                                           {1024, 8}, {512, 16}};
-  static const std::vector<Shape> bt32 = {{32, 1},  {32, 2},   {32, 4},   {32, 8},  {64, 8},
-                                          {128, 8}, {256, 8},  {128, 16}, {256, 16}, {512, 8},
-                                          {512, 16}, {1024, 8}};
-  static const std::vector<Shape> bt64 = {{32, 1},  {32, 2},  {32, 4},  {32, 8},  {64, 8},
-                                          {128, 8}, {256, 8}, {512, 8}, {256, 16}};
+  static const std::vector<Shape> bt32 = {{32, 1},   {32, 2},   {32, 4},   {32, 8},  {64, 8},
+                                          {128, 8},  {256, 8},  {128, 16}, {64, 32}, {256, 16},
+                                          {512, 8},  {128, 32}, {512, 16}, {1024, 8}, {256, 32}};
+  static const std::vector<Shape> bt64 = {{32, 1},  {32, 2},  {32, 4},   {32, 8},   {64, 8},
+                                          {128, 8}, {256, 8}, {128, 16}, {512, 8}, {256, 16}};
   if (kind == K_EXPLICIT_RESIDENT) return dtype == 0 ? ex32 : ex64;
   return dtype == 0 ? bt32 : bt64;
 }

@@ -252,9 +252,11 @@ void register_btcs(std::vector<KernelEntry>& reg) {
   REG_BTCS(float, 0, 32, 8) REG_BTCS(float, 0, 64, 8) REG_BTCS(float, 0, 128, 8)
   REG_BTCS(float, 0, 256, 8) REG_BTCS(float, 0, 128, 16) REG_BTCS(float, 0, 256, 16)
   REG_BTCS(float, 0, 512, 8) REG_BTCS(float, 0, 512, 16) REG_BTCS(float, 0, 1024, 8)
+  REG_BTCS(float, 0, 64, 32) REG_BTCS(float, 0, 128, 32) REG_BTCS(float, 0, 256, 32)
   REG_BTCS(double, 1, 32, 1) REG_BTCS(double, 1, 32, 2) REG_BTCS(double, 1, 32, 4)
   REG_BTCS(double, 1, 32, 8) REG_BTCS(double, 1, 64, 8) REG_BTCS(double, 1, 128, 8)
   REG_BTCS(double, 1, 256, 8) REG_BTCS(double, 1, 512, 8) REG_BTCS(double, 1, 256, 16)
+  REG_BTCS(double, 1, 128, 16)
 }
 
 }  // namespace burgers

@@ -58,15 +58,16 @@ __device__ __forceinline__ T shfl_down(T v, int d) {
 // Explicit forward-Euler upwind/central increment of node value u with left
 // and right neighbours ul, ur (Eq. 21 with the upwind side of Sec. 2.2):
 //   u' - u = -r (u+ (u - ul) + u- (ur - u)) + s (ur - 2u + ul)
-//          = (s - r u-) (ur - u) - (s + r u+) (u - ul),
+//          = p (ur - u) - q (u - ul),
+//   p = s - r u- = s + h (|u| - u),   q = s + r u+ = p + r u,   h = r/2,
 // returned plus `add`. Per node: one difference (u - ul is the previous
-// node's ur - u), two min/max (ALU pipe), four FMA-pipe operations.
+// node's ur - u) and five FMA-pipe operations, no min/max.
 template <typename T>
-__device__ __forceinline__ T explicit_increment(T u, T ul, T ur, T r, T s, T add) {
+__device__ __forceinline__ T explicit_increment(T u, T ul, T ur, T r, T h, T s, T add) {
   const T dr = ur - u;
   const T dl = u - ul;
-  const T p = tfma(-r, tmin(u, T(0)), s);
-  const T q = tfma(r, tmax(u, T(0)), s);
+  const T p = tfma(h, tabs(u) - u, s);
+  const T q = tfma(r, u, p);
   return tfma(p, dr, tfma(-q, dl, add));
 }
 
@@ -87,15 +88,15 @@ struct Kahan<float> {
 };
 
 template <typename T>
-__device__ __forceinline__ T explicit_update(T u, T ul, T ur, T r, T s, T& lo) {
+__device__ __forceinline__ T explicit_update(T u, T ul, T ur, T r, T h, T s, T& lo) {
   if constexpr (Kahan<T>::on) {
-    const T y = explicit_increment(u, ul, ur, r, s, -lo);
+    const T y = explicit_increment(u, ul, ur, r, h, s, -lo);
     const T t = u + y;
     lo = (t - u) - y;
     return t;
   } else {
     (void)lo;
-    return explicit_increment(u, ul, ur, r, s, u);
+    return explicit_increment(u, ul, ur, r, h, s, u);
   }
 }
 

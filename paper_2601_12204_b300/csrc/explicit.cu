@@ -4,8 +4,8 @@
 // Layout: thread t of a CTA holds C consecutive nodes of a row in registers.
 // Neighbour values cross lanes by warp shuffles and cross warps through a
 // double-buffered shared-memory slot per warp, so one step costs one
-// __syncthreads (none for single-warp rows) and, per node, five FMA-pipe and
-// two min/max instructions (plus three for the FP32 compensation).
+// __syncthreads (none for single-warp rows) and, per node, six FMA-pipe
+// instructions (plus three for the FP32 compensation).
 //
 //  * k_explicit_resident: the whole row lives in registers for all of its
 //    steps (the paper's time loop runs inside the kernel). CTAs are
@@ -31,7 +31,7 @@ enum : int { MODE_EXACT = 0, MODE_RAGGED = 1, MODE_WINDOW = 2, MODE_WINDOW_DIR =
 //   MODE_WINDOW_DIR streaming window that contains a Dirichlet end node.
 // gbase is the row index of this thread's first node.
 template <typename T, int NT, int C, int MODE, int BCT>
-__device__ __forceinline__ void explicit_steps(T (&v)[C], T (&lo)[C], int64_t nsteps, T r, T s,
+__device__ __forceinline__ void explicit_steps(T (&v)[C], T (&lo)[C], int64_t nsteps, T r, T h, T s,
                                                int n, int64_t gbase, T* sh_last, T* sh_first,
                                                T* sh_wrap) {
   constexpr int NW = NT / 32;
@@ -78,7 +78,7 @@ __device__ __forceinline__ void explicit_steps(T (&v)[C], T (&lo)[C], int64_t ns
         if (j == jstar) ur = wrapR;
       }
       const T lo0 = lo[j];
-      T nv = explicit_update(cur, ul, ur, r, s, lo[j]);
+      T nv = explicit_update(cur, ul, ur, r, h, s, lo[j]);
       bool keep = false;
       if constexpr (MODE == MODE_EXACT && BCT == BC_DIRICHLET) {
         keep = (j == 0 && tid == 0) || (j == C - 1 && tid == NT - 1);
@@ -117,13 +117,13 @@ __global__ void __launch_bounds__(NT) k_explicit_resident(T* __restrict__ u,
       v[j] = (EXACT || base + j < rd.n) ? row[base + j] : T(0);
       lo[j] = T(0);
     }
-    const T r = T(rd.r), s = T(rd.s);
+    const T r = T(rd.r), h = T(0.5 * rd.r), s = T(rd.s);
     constexpr int M = EXACT ? MODE_EXACT : MODE_RAGGED;
     if (rd.bc == BC_PERIODIC)
-      explicit_steps<T, NT, C, M, BC_PERIODIC>(v, lo, rd.nsteps, r, s, rd.n, base, sh_last,
+      explicit_steps<T, NT, C, M, BC_PERIODIC>(v, lo, rd.nsteps, r, h, s, rd.n, base, sh_last,
                                                sh_first, sh_wrap);
     else
-      explicit_steps<T, NT, C, M, BC_DIRICHLET>(v, lo, rd.nsteps, r, s, rd.n, base, sh_last,
+      explicit_steps<T, NT, C, M, BC_DIRICHLET>(v, lo, rd.nsteps, r, h, s, rd.n, base, sh_last,
                                                 sh_first, sh_wrap);
 #pragma unroll
     for (int j = 0; j < C; ++j)
@@ -232,14 +232,14 @@ __global__ void __launch_bounds__(NT) k_explicit_stream(const T* __restrict__ sr
         else lo[j] = T(0);
       }
     }
-    const T r = T(rd.r), s = T(rd.s);
+    const T r = T(rd.r), h = T(0.5 * rd.r), s = T(rd.s);
     const bool has_end = rd.bc == BC_DIRICHLET && ((ws <= 0 && ws + W > 0) ||
                                                    (ws <= n - 1 && ws + W > n - 1));
     if (has_end)
-      explicit_steps<T, NT, C, MODE_WINDOW_DIR, BC_DIRICHLET>(v, lo, kk, r, s, int(n), g0,
+      explicit_steps<T, NT, C, MODE_WINDOW_DIR, BC_DIRICHLET>(v, lo, kk, r, h, s, int(n), g0,
                                                               sh_last, sh_first, sh_wrap);
     else
-      explicit_steps<T, NT, C, MODE_WINDOW, BC_PERIODIC>(v, lo, kk, r, s, int(n), g0, sh_last,
+      explicit_steps<T, NT, C, MODE_WINDOW, BC_PERIODIC>(v, lo, kk, r, h, s, int(n), g0, sh_last,
                                                          sh_first, sh_wrap);
 #pragma unroll
     for (int j = 0; j < C; ++j) {
