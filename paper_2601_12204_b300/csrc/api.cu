@@ -80,8 +80,7 @@ struct Shape {
 static const std::vector<Shape>& resident_shapes(int kind, int dtype) {
   static const std::vector<Shape> ex32 = {{32, 1},   {32, 2},    {32, 4},   {32, 8},  {64, 8},
                                           {128, 8},  {64, 16},   {128, 16}, {256, 8}, {256, 16},
-                                          {128, 32}, {512, 16},  {256, 32}, {512, 8}, {1024, 16},
-                                          {1024, 32}};
+                                          {128, 32}, {512, 16},  {256, 32}, {512, 8}, {1024, 16}};
   static const std::vector<Shape> ex64 = {{32, 1},  {32, 2},   {32, 4},  {32, 8},   {64, 8},
                                           {128, 8}, {256, 8},  {128, 16}, {512, 8}, {256, 16},
                                           {1024, 8}, {512, 16}};
