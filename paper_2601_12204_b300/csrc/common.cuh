@@ -87,6 +87,18 @@ struct Kahan<float> {
   static constexpr bool on = true;
 };
 
+// The 16-byte vector type of T (four floats or two doubles).
+template <typename T>
+struct Vec16;
+template <>
+struct Vec16<float> {
+  using type = float4;
+};
+template <>
+struct Vec16<double> {
+  using type = double2;
+};
+
 template <typename T>
 __device__ __forceinline__ T explicit_update(T u, T ul, T ur, T r, T h, T s, T& lo) {
   if constexpr (Kahan<T>::on) {

@@ -160,6 +160,307 @@ __global__ void __launch_bounds__(NT) k_ml_sweep(T* __restrict__ u, T* __restric
   }
 }
 
+// ---------------------------------------------------------------------------
+// Level-0 sweeps with staged tiles. A CTA's tile of NT*C nodes and its two
+// halo nodes (and, for the recover sweep in FP32, the tile's Kahan terms) are
+// copied into shared memory with cp.async while the previous tile is being
+// eliminated (two buffers), so the sweep streams instead of waiting on each
+// thread's strided loads. Rows whose start is 16-byte aligned move in 16-byte
+// vectors (the last one zero-filled past the row end); others move element
+// by element. The buffer inserts 16 bytes after every 128, which keeps the
+// threads' reads of their C consecutive nodes spread over the banks while
+// leaving every vector slot 16-byte aligned. The recover sweep writes its
+// results back into its own slots and stores the tile contiguously.
+//
+// Local index L of node t0 + i is VE + i (VE elements per vector); the slot
+// L = VE - 1 holds the left neighbour of node t0 (periodic image for t0 = 0)
+// and L = VE + TILE the right neighbour of the tile's last node (row[0] when
+// that node is the row's last).
+// ---------------------------------------------------------------------------
+template <typename T, int NT, int C>
+struct Sweep0Smem {
+  static constexpr int TILE = NT * C;
+  static constexpr int VE = 16 / int(sizeof(T));
+  static constexpr int GRP = 128 / int(sizeof(T));
+  __device__ __host__ static constexpr int idx(int L) { return L + VE * (L / GRP); }
+  static constexpr int SSK = (idx(TILE + VE) / VE + 1) * VE;  // one buffer, elements
+  static constexpr size_t bytes(bool recover) {
+    return sizeof(T) * size_t(SSK) * 2 * ((recover && Kahan<T>::on) ? 2 : 1);
+  }
+};
+
+template <typename T>
+__device__ __forceinline__ unsigned smem_addr(const T* p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+// One element; src_bytes 0 zero-fills the slot without reading.
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T* smem, const T* gmem, bool valid) {
+  const int nb = valid ? int(sizeof(T)) : 0;
+  if constexpr (sizeof(T) == 4)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(smem_addr(smem)),
+                 "l"(gmem), "r"(nb)
+                 : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(smem_addr(smem)),
+                 "l"(gmem), "r"(nb)
+                 : "memory");
+}
+// One 16-byte vector, of which the first nb bytes are read (rest zero-filled).
+__device__ __forceinline__ void cp_async_vec(void* smem, const void* gmem, int nb) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(smem_addr(smem)),
+               "l"(gmem), "r"(nb)
+               : "memory");
+}
+// A 16-byte shared-memory load the compiler may not merge with an earlier
+// load of the same slot (so a value need not stay live in registers).
+__device__ __forceinline__ float4 lds_fresh(const float* p) {
+  float4 w;
+  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];\n"
+               : "=f"(w.x), "=f"(w.y), "=f"(w.z), "=f"(w.w)
+               : "r"(smem_addr(p)));
+  return w;
+}
+__device__ __forceinline__ double2 lds_fresh(const double* p) {
+  double2 w;
+  asm volatile("ld.shared.v2.f64 {%0, %1}, [%2];\n" : "=d"(w.x), "=d"(w.y) : "r"(smem_addr(p)));
+  return w;
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Copies nodes [t0, min(t0 + TILE, n)) of `row` to slots VE.. of `buf`.
+template <typename T, int NT, int C>
+__device__ __forceinline__ void stage_tile(T* buf, const T* row, int64_t t0, int64_t n) {
+  using SM = Sweep0Smem<T, NT, C>;
+  constexpr int VE = SM::VE;
+  const int tid = threadIdx.x;
+  const int64_t rem = n - t0;  // nodes left in the row from t0 (> 0)
+  const int cnt = rem < SM::TILE ? int(rem) : SM::TILE;
+  if ((reinterpret_cast<uintptr_t>(row) & 15) == 0) {
+    const T* src = row + t0;
+    for (int q = tid; q * VE < cnt; q += NT) {
+      const int e = q * VE;
+      const int left = cnt - e;
+      cp_async_vec(buf + SM::idx(VE + e), src + e, (left < VE ? left : VE) * int(sizeof(T)));
+    }
+  } else {
+    const T* src = row + t0;
+    for (int i = tid; i < cnt; i += NT) cp_async_elem(buf + SM::idx(VE + i), src + i, true);
+  }
+}
+
+// The CTA handles items blockIdx.x + k * gridDim.x, k = 0, 1, ... Their
+// (row, tile, row offset, row length) are gathered into shared memory KC at a
+// time, so staging the next tile needs no dependent global loads; the row's
+// record travels with the tile (cp.async into a per-buffer copy).
+template <typename T, int NT, int C, bool RECOVER>
+__global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? 768 : 512) / NT)
+    k_ml_sweep0(T* __restrict__ u, T* __restrict__ u2, T* __restrict__ lo, T* __restrict__ ws,
+                const MLRow* __restrict__ rows, const TileItem* __restrict__ items, int nitems,
+                int level, int64_t step) {
+  using SM = Sweep0Smem<T, NT, C>;
+  constexpr int TILE = SM::TILE, VE = SM::VE, SSK = SM::SSK;
+  constexpr bool KL = RECOVER && Kahan<T>::on;
+  constexpr int RV = int(sizeof(MLRow) / 16);
+  static_assert(sizeof(MLRow) % 16 == 0, "row record moves in 16-byte pieces");
+  extern __shared__ __align__(16) unsigned char dsm[];
+  __shared__ __align__(16) MLRow srow[2];
+  __shared__ int stile[2];
+  constexpr int KC = 64;  // cached item descriptors
+  static_assert(NT >= KC, "one thread per cached descriptor");
+  __shared__ int64_t coff[KC];
+  __shared__ int crow[KC], ctile[KC], cn[KC];
+  T* sbase = reinterpret_cast<T*>(dsm);
+  (void)level;
+  T* src = (step & 1) ? u2 : u;
+  T* dst = (step & 1) ? u : u2;
+  const int tid = threadIdx.x;
+  const int G = gridDim.x;
+  const int nk = int(blockIdx.x) < nitems ? (nitems - int(blockIdx.x) + G - 1) / G : 0;
+  if (nk == 0) return;
+
+  auto fill = [&](int k0) {  // descriptors of items k0 .. k0 + KC - 1
+    const int k = k0 + tid;
+    if (tid < KC && k < nk) {
+      const TileItem ti = items[int(blockIdx.x) + k * G];
+      crow[tid] = ti.row;
+      ctile[tid] = ti.tile;
+      coff[tid] = rows[ti.row].offset;
+      cn[tid] = rows[ti.row].n;
+    }
+  };
+  auto prefetch = [&](int k, int b) {
+    const int slot = k % KC;
+    const int rowi = crow[slot];
+    const int64_t n = cn[slot];
+    const int64_t t0 = int64_t(ctile[slot]) * TILE;
+    const T* row = src + coff[slot];
+    T* su = sbase + b * SSK;
+    stage_tile<T, NT, C>(su, row, t0, n);
+    if (tid == 0) {
+      cp_async_elem(su + SM::idx(VE - 1), row + (t0 == 0 ? n - 1 : t0 - 1), true);
+      stile[b] = ctile[slot];
+    }
+    if (tid == NT - 1) {
+      const int64_t gr = t0 + TILE < n ? t0 + TILE : 0;
+      cp_async_elem(su + SM::idx(VE + TILE), row + gr, true);
+    }
+    if (tid >= 32 && tid < 32 + RV)
+      cp_async_vec(reinterpret_cast<char*>(&srow[b]) + 16 * (tid - 32),
+                   reinterpret_cast<const char*>(rows + rowi) + 16 * (tid - 32), 16);
+    if constexpr (KL) stage_tile<T, NT, C>(sbase + (2 + b) * SSK, lo + coff[slot], t0, n);
+    cp_async_commit();
+  };
+
+  fill(0);
+  __syncthreads();
+  prefetch(0, 0);
+  int b = 0;
+  for (int k = 0; k < nk; ++k, b ^= 1) {
+    if (k + 1 < nk) {
+      if ((k + 1) % KC == 0) {
+        __syncthreads();  // every thread is past its last read of the cache
+        fill(k + 1);
+        __syncthreads();
+      }
+      prefetch(k + 1, b ^ 1);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncthreads();
+    const MLRow& R = srow[b];
+    const int64_t M = R.m[0];
+    const int64_t t0 = int64_t(stile[b]) * TILE;
+    const int64_t base = t0 + int64_t(tid) * C;
+    T* su = sbase + b * SSK;
+    T* sl = sbase + (2 + b) * SSK;
+    const int lb = VE + tid * C;  // local index of this thread's first node
+    using V = typename Vec16<T>::type;
+    constexpr int NV = C / VE;
+    static_assert(C % VE == 0, "a chunk is whole vectors");
+    if (base < M) {
+      const bool active = step < R.nsteps;
+      // the chunk and its two neighbours: a[0] = u_{base-1}, a[1 + j] = u_{base+j}
+      T a[C + 2];
+      a[0] = su[SM::idx(lb - 1)];
+#pragma unroll
+      for (int q = 0; q < NV; ++q) {
+        const V w = *reinterpret_cast<const V*>(su + SM::idx(lb + q * VE));
+        const T* wp = reinterpret_cast<const T*>(&w);
+#pragma unroll
+        for (int e = 0; e < VE; ++e) a[1 + q * VE + e] = wp[e];
+      }
+      a[C + 1] = su[SM::idx(lb + C)];
+      const int64_t kk = base / C;
+      const int64_t Mn = R.m[1];
+      T L = T(0), Xk = T(0);
+      if constexpr (RECOVER) {  // issue the coarse solution loads before the sweep
+        if (active) {
+          const T* Xn = ws + R.x[1];
+          L = kk > 0 ? Xn[kk - 1] : (R.bc == BC_PERIODIC ? Xn[Mn - 1] : T(0));
+          Xk = Xn[kk];
+        }
+      }
+      const T r = T(R.r), s = T(R.s), ds1 = T(1) + T(2) * s;
+      const bool dir = R.bc == BC_DIRICHLET;
+      T v[C], ah[C], ch[C];
+      T e_ch = T(0), e_ah = T(0), e_dh = T(0);
+      int je = C - 1;
+      if (!active) {
+        // rows already done: copied through by the recover sweep only
+      } else if (base + C < M && !(dir && base == 0)) {
+        // interior chunk: no row end, no Dirichlet end row
+        auto rowsrc = [&](int j, T& l, T& d, T& c, T& rhs) {
+          const T ra = r * a[j + 1];
+          l = -s - tmax(ra, T(0));
+          c = tmin(ra, T(0)) - s;
+          d = ds1 + tabs(ra);
+          rhs = tfma(l, a[j + 1] - a[j], -c * (a[j + 2] - a[j + 1]));
+        };
+        chunk_forward<T, C>(v, ah, ch, C - 1, rowsrc, e_ch, e_ah, e_dh);
+        chunk_backward<T, C>(v, ah, ch, C - 1);
+      } else {
+        je = int(M - 1 - base < int64_t(C - 1) ? M - 1 - base : int64_t(C - 1));
+        const int jend = int(M - 1 - base);  // local index of the row's last node, if here
+        const T hr = su[SM::idx(VE + TILE)];  // right neighbour of the row's last node
+        auto rowsrc = [&](int j, T& l, T& d, T& c, T& rhs) {
+          const int64_t gi = base + j;
+          if (j > je) { l = T(0); d = T(1); c = T(0); rhs = T(0); return; }
+          const T ur = j == jend ? hr : a[j + 2];
+          const T ra = r * a[j + 1];
+          l = -s - tmax(ra, T(0));
+          c = tmin(ra, T(0)) - s;
+          d = ds1 + tabs(ra);
+          rhs = tfma(l, a[j + 1] - a[j], -c * (ur - a[j + 1]));
+          if (dir && (gi == 0 || gi == M - 1)) { l = T(0); c = T(0); d = T(1); rhs = T(0); }
+        };
+        chunk_forward<T, C>(v, ah, ch, je, rowsrc, e_ch, e_ah, e_dh);
+        chunk_backward<T, C>(v, ah, ch, je);
+      }
+      if constexpr (!RECOVER) {
+        if (active) {
+          T* Eo = ws + R.ef[0];
+          Eo[kk] = e_ch;
+          Eo[Mn + kk] = e_ah;
+          Eo[2 * Mn + kk] = e_dh;
+          Eo[3 * Mn + kk] = v[0];
+          Eo[4 * Mn + kk] = ah[0];
+          Eo[5 * Mn + kk] = ch[0];
+        }
+      } else {
+        // u^{n+1} = u^n + delta (FP32: compensated), one vector at a time, stored
+        // straight from registers; rows already done are copied through
+        T* drow = dst + R.offset + base;
+        T* lrow = lo + R.offset + base;
+        const int cnt = M - base < C ? int(M - base) : C;
+        const bool vec = cnt == C && (reinterpret_cast<uintptr_t>(drow) & 15) == 0 &&
+                         (!KL || (reinterpret_cast<uintptr_t>(lrow) & 15) == 0);
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+          V w = lds_fresh(su + SM::idx(lb + q * VE));  // u^n again, not kept live
+          V wl;
+          if constexpr (KL) wl = lds_fresh(sl + SM::idx(lb + q * VE));
+          T* wp = reinterpret_cast<T*>(&w);
+          T* wlp = reinterpret_cast<T*>(&wl);
+          if (active) {
+#pragma unroll
+            for (int e = 0; e < VE; ++e) {
+              const int j = q * VE + e;
+              if (j <= je) {
+                const T delta = tfma(-ch[j], Xk, tfma(-ah[j], L, v[j]));
+                if constexpr (KL) {
+                  wp[e] = comp_add(wp[e], delta, wlp[e]);
+                } else {
+                  wp[e] = wp[e] + delta;
+                }
+              }
+            }
+          }
+          if (vec) {
+            *reinterpret_cast<V*>(drow + q * VE) = w;
+            if constexpr (KL) *reinterpret_cast<V*>(lrow + q * VE) = wl;
+          } else {
+#pragma unroll
+            for (int e = 0; e < VE; ++e)
+              if (q * VE + e < cnt) {
+                drow[q * VE + e] = wp[e];
+                if constexpr (KL) lrow[q * VE + e] = wlp[e];
+              }
+          }
+        }
+      }
+    }
+    __syncthreads();  // buffer b is refilled two iterations later
+  }
+}
+
 // Copies the rows of the level-0 items from u2 back into u (after an odd
 // number of steps).
 template <typename T, int NT, int C>
@@ -238,11 +539,13 @@ __global__ void __launch_bounds__(NT) k_ml_top(T* __restrict__ u, T* __restrict_
 
 #define REG_SWEEP(T, DT, NT, C)                                                               \
   reg.push_back({K_BTCS_REDUCE, DT, NT, C, 1,                                                 \
-                 reinterpret_cast<const void*>(&k_ml_sweep<T, NT, C, true, false>), 0});     \
+                 reinterpret_cast<const void*>(&k_ml_sweep0<T, NT, C, false>),               \
+                 Sweep0Smem<T, NT, C>::bytes(false)});                                        \
   reg.push_back({K_BTCS_REDUCE, DT, NT, C, 0,                                                 \
                  reinterpret_cast<const void*>(&k_ml_sweep<T, NT, C, false, false>), 0});    \
   reg.push_back({K_BTCS_RECOVER, DT, NT, C, 1,                                                \
-                 reinterpret_cast<const void*>(&k_ml_sweep<T, NT, C, true, true>), 0});      \
+                 reinterpret_cast<const void*>(&k_ml_sweep0<T, NT, C, true>),                \
+                 Sweep0Smem<T, NT, C>::bytes(true)});                                         \
   reg.push_back({K_BTCS_RECOVER, DT, NT, C, 0,                                                \
                  reinterpret_cast<const void*>(&k_ml_sweep<T, NT, C, false, true>), 0});
 #define REG_TOP(T, DT, NT, C) \
@@ -364,7 +667,9 @@ burgers_status plan_multilevel(burgers_ctx* ctx, const burgers_batch* batch,
   }
   auto grid_for = [&](const KernelEntry* k, int nitems) {
     int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k->fn, k->nt, 0) != cudaSuccess || b < 1) b = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k->fn, k->nt, k->dyn_smem) != cudaSuccess ||
+        b < 1)
+      b = 1;
     return std::max(1, std::min(nitems, ctx->sm_count * b));
   };
   for (int64_t s = 0; s < smax; ++s) {
@@ -426,6 +731,8 @@ cudaError_t enqueue_multilevel_launch(burgers_ctx* ctx, Plan* p, const Launch& L
   void* lo = p->dtype == 0 ? static_cast<char*>(ctx->scratch.ptr) + size_t(p->ml_span) * esz : nullptr;
   const MLRow* rows = reinterpret_cast<const MLRow*>(base + p->ml_off);
   const TileItem* items = reinterpret_cast<const TileItem*>(base + p->items_off) + L.item_begin;
+  // the staged sweeps copy row records in 16-byte pieces
+  if (reinterpret_cast<uintptr_t>(rows) & 15) return cudaErrorMisalignedAddress;
   int ni = L.item_count, level = L.level;
   int64_t step = L.step_base;
   void* args[] = {&u, &u2, &lo, &ws, &rows, &items, &ni, &level, &step};
