@@ -11,6 +11,8 @@ from __future__ import annotations
 
 import argparse
 import json
+import os
+import tempfile
 
 import numpy as np
 
@@ -27,6 +29,8 @@ def main():
     ap.add_argument("--stream-k", type=int, default=0)
     ap.add_argument("--repeat", type=int, default=1)
     ap.add_argument("--autotune", action="store_true", help="tune launch shapes first and print the table")
+    ap.add_argument("--tune-file", default=None,
+                    help="launch-shape table: loaded if it exists, else written after --autotune")
     a = ap.parse_args()
 
     import torch
@@ -46,11 +50,11 @@ def main():
     fac = a.dt_factor if a.dt_factor is not None else (1.0 if a.case == "explicit" else 10.0)
     b = Batch.from_ensemble(ens, dt * fac, a.steps, dt_code)
     scheme = L.BURGERS_EXPLICIT if a.case == "explicit" else L.BURGERS_BTCS
-    if a.autotune:
-        import os
-        import tempfile
+    if a.tune_file and os.path.exists(a.tune_file):
+        ctx.tune_load(a.tune_file)
+    elif a.autotune:
         ntuned = ctx.autotune(scheme, b, u0, probe_steps=min(a.steps, 100))
-        path = os.path.join(tempfile.mkdtemp(), "tune.txt")
+        path = a.tune_file or os.path.join(tempfile.mkdtemp(), "tune.txt")
         ctx.tune_save(path)
         print(json.dumps({"tuned_classes": ntuned, "table": open(path).read().splitlines()[1:]}))
     times = []

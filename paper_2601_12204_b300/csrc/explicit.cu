@@ -5,7 +5,8 @@
 // Neighbour values cross lanes by warp shuffles and cross warps through a
 // double-buffered shared-memory slot per warp, so one step costs one
 // __syncthreads (none for single-warp rows) and, per node, six FMA-pipe
-// instructions (plus three for the FP32 compensation).
+// instructions; FP32 adds one to evaluate its split state (value at the last
+// fold plus the increments since) and three every 32 steps to fold it.
 //
 //  * k_explicit_resident: the whole row lives in registers for all of its
 //    steps (the paper's time loop runs inside the kernel). CTAs are
@@ -30,68 +31,169 @@ enum : int { MODE_EXACT = 0, MODE_RAGGED = 1, MODE_WINDOW = 2, MODE_WINDOW_DIR =
 //   MODE_WINDOW     streaming window; its two edges go stale one node per step.
 //   MODE_WINDOW_DIR streaming window that contains a Dirichlet end node.
 // gbase is the row index of this thread's first node.
+// Exchanges this thread's edge values for its neighbours' (left = value of
+// the node before its first, right = after its last). Periodic rows wrap
+// through the slots of the first and last warp; WRAPX rows (ragged periodic)
+// also publish node n-1 and node 0 (wrap_sel, first of thread 0).
+template <typename T, int NT, bool WRAPX>
+__device__ __forceinline__ void halo_exchange(T first, T last, T wrap_sel, bool has_wrap, int p,
+                                              T* sh_last, T* sh_first, T* sh_wrap, T& left,
+                                              T& right, T& wrapL, T& wrapR) {
+  constexpr int NW = NT / 32;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  left = shfl(last, (lane + 31) & 31);
+  right = shfl(first, (lane + 1) & 31);
+  if constexpr (NW > 1) {
+    if (lane == 31) sh_last[p * NW + warp] = last;
+    if (lane == 0) sh_first[p * NW + warp] = first;
+  }
+  if constexpr (WRAPX) {
+    if (has_wrap) sh_wrap[p * 2 + 0] = wrap_sel;
+    if (tid == 0) sh_wrap[p * 2 + 1] = first;
+  }
+  if constexpr (NW > 1 || WRAPX) __syncthreads();
+  if constexpr (NW > 1) {
+    if (lane == 0) left = sh_last[p * NW + (warp + NW - 1) % NW];
+    if (lane == 31) right = sh_first[p * NW + (warp + 1) % NW];
+  }
+  if constexpr (WRAPX) {
+    wrapL = sh_wrap[p * 2 + 0];
+    wrapR = sh_wrap[p * 2 + 1];
+  }
+}
+
+// Whether node j of this thread keeps its value (end rows, padding).
+template <int NT, int C, int MODE, int BCT>
+__device__ __forceinline__ bool keep_node(int j, int jstar, int64_t gbase, int n) {
+  const int tid = threadIdx.x;
+  if constexpr (MODE == MODE_EXACT && BCT == BC_DIRICHLET) {
+    return (j == 0 && tid == 0) || (j == C - 1 && tid == NT - 1);
+  } else if constexpr (MODE == MODE_RAGGED) {
+    bool keep = j > jstar;  // padding
+    if constexpr (BCT == BC_DIRICHLET) keep = keep || j == jstar || (j == 0 && tid == 0);
+    return keep;
+  } else if constexpr (MODE == MODE_WINDOW_DIR) {
+    const int64_t gi = gbase + j;
+    return gi == 0 || gi == n - 1;
+  } else {
+    return false;
+  }
+}
+
+// FP32 steps with a split state: each node carries uh (its value at the last
+// fold) and d (the increments summed since), and a step evaluates the stencil
+// on u = uh + d and adds the increment to d. Every FOLD steps, and after the
+// last one, d is folded into uh with its rounding error kept in d (the same
+// two-sum as compensated summation), so increments are never rounded against
+// the full magnitude of u between folds. On entry and exit the state is
+// (v, lo) with the true value v - lo, as in Kahan summation.
+constexpr int FOLD = 32;
+
+template <int NT, int C, int MODE, int BCT>
+__device__ __forceinline__ void explicit_steps_split(float (&v)[C], float (&lo)[C], int64_t nsteps,
+                                                     float r, float h, float s, int n,
+                                                     int64_t gbase, float* sh_last,
+                                                     float* sh_first, float* sh_wrap) {
+  constexpr bool WRAPX = (MODE == MODE_RAGGED && BCT == BC_PERIODIC);
+  const int tid = threadIdx.x;
+  const int jstar = int(n - 1 - gbase);  // local index of node n-1 (resident modes)
+  // lo becomes d = -lo
+#pragma unroll
+  for (int j = 0; j < C; ++j) lo[j] = -lo[j];
+  for (int64_t k = 0; k < nsteps; ++k) {
+    const int p = int(k & 1);
+    const float first = v[0] + lo[0];
+    const float last = v[C - 1] + lo[C - 1];
+    float wsel = 0.f;
+    bool has_wrap = false;
+    if constexpr (WRAPX) {
+      has_wrap = jstar >= 0 && jstar < C;
+      float sv = v[0], sd = lo[0];
+#pragma unroll
+      for (int j = 1; j < C; ++j)
+        if (j == jstar) { sv = v[j]; sd = lo[j]; }
+      wsel = sv + sd;
+    }
+    float left, right, wrapL = 0.f, wrapR = 0.f;
+    halo_exchange<float, NT, WRAPX>(first, last, wsel, has_wrap, p, sh_last, sh_first, sh_wrap,
+                                    left, right, wrapL, wrapR);
+    float wl = left, wc = first;
+    if constexpr (WRAPX) {
+      if (tid == 0) wl = wrapL;
+    }
+#pragma unroll
+    for (int j = 0; j < C; ++j) {
+      float wr = (j + 1 < C) ? v[j + 1] + lo[j + 1] : right;
+      if constexpr (WRAPX) {
+        if (j == jstar) wr = wrapR;
+      }
+      const float dn = explicit_increment(wc, wl, wr, r, h, s, lo[j]);
+      if (!keep_node<NT, C, MODE, BCT>(j, jstar, gbase, n)) lo[j] = dn;
+      wl = wc;
+      wc = wr;
+    }
+    if (((k + 1) & (FOLD - 1)) == 0 || k + 1 == nsteps) {
+#pragma unroll
+      for (int j = 0; j < C; ++j) {
+        const float t = v[j] + lo[j];
+        lo[j] = lo[j] - (t - v[j]);
+        v[j] = t;
+      }
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < C; ++j) lo[j] = -lo[j];
+}
+
+// Advances the C nodes held by this thread `nsteps` steps.
+//   MODE_EXACT      row length n == NT*C; periodic wrap through the halo slots.
+//   MODE_RAGGED     n < NT*C; nodes >= n are inert padding, the periodic wrap
+//                   pairs node 0 with node n-1 explicitly.
+//   MODE_WINDOW     streaming window; its two edges go stale one node per step.
+//   MODE_WINDOW_DIR streaming window that contains a Dirichlet end node.
+// gbase is the row index of this thread's first node. FP32 runs the split
+// state above; FP64 updates the values in place.
 template <typename T, int NT, int C, int MODE, int BCT>
 __device__ __forceinline__ void explicit_steps(T (&v)[C], T (&lo)[C], int64_t nsteps, T r, T h, T s,
                                                int n, int64_t gbase, T* sh_last, T* sh_first,
                                                T* sh_wrap) {
-  constexpr int NW = NT / 32;
-  constexpr bool WRAPX = (MODE == MODE_RAGGED && BCT == BC_PERIODIC);
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int jstar = int(n - 1 - gbase);  // local index of node n-1 (resident modes)
-  for (int64_t k = 0; k < nsteps; ++k) {
-    const int p = int(k & 1);
-    const T first = v[0], last = v[C - 1];
-    T left = shfl(last, (lane + 31) & 31);
-    T right = shfl(first, (lane + 1) & 31);
-    if constexpr (NW > 1) {
-      if (lane == 31) sh_last[p * NW + warp] = last;
-      if (lane == 0) sh_first[p * NW + warp] = first;
-    }
-    if constexpr (WRAPX) {
-      if (jstar >= 0 && jstar < C) {
-        T sel = v[0];
+  if constexpr (Kahan<T>::on) {
+    explicit_steps_split<NT, C, MODE, BCT>(v, lo, nsteps, r, h, s, n, gbase, sh_last, sh_first,
+                                           sh_wrap);
+  } else {
+    constexpr bool WRAPX = (MODE == MODE_RAGGED && BCT == BC_PERIODIC);
+    const int tid = threadIdx.x;
+    const int jstar = int(n - 1 - gbase);
+    for (int64_t k = 0; k < nsteps; ++k) {
+      const int p = int(k & 1);
+      const T first = v[0], last = v[C - 1];
+      T wsel = T(0);
+      bool has_wrap = false;
+      if constexpr (WRAPX) {
+        has_wrap = jstar >= 0 && jstar < C;
+        wsel = v[0];
 #pragma unroll
         for (int j = 1; j < C; ++j)
-          if (j == jstar) sel = v[j];
-        sh_wrap[p * 2 + 0] = sel;
+          if (j == jstar) wsel = v[j];
       }
-      if (tid == 0) sh_wrap[p * 2 + 1] = first;
-    }
-    if constexpr (NW > 1 || WRAPX) __syncthreads();
-    if constexpr (NW > 1) {
-      if (lane == 0) left = sh_last[p * NW + (warp + NW - 1) % NW];
-      if (lane == 31) right = sh_first[p * NW + (warp + 1) % NW];
-    }
-    T wrapL = T(0), wrapR = T(0);
-    if constexpr (WRAPX) {
-      wrapL = sh_wrap[p * 2 + 0];
-      wrapR = sh_wrap[p * 2 + 1];
-    }
-    T prev = left;
-#pragma unroll
-    for (int j = 0; j < C; ++j) {
-      const T cur = v[j];
-      T ul = prev;
-      T ur = (j + 1 < C) ? v[j + 1] : right;
+      T left, right, wrapL = T(0), wrapR = T(0);
+      halo_exchange<T, NT, WRAPX>(first, last, wsel, has_wrap, p, sh_last, sh_first, sh_wrap, left,
+                                  right, wrapL, wrapR);
+      T prev = left;
       if constexpr (WRAPX) {
-        if (j == 0 && tid == 0) ul = wrapL;
-        if (j == jstar) ur = wrapR;
+        if (tid == 0) prev = wrapL;
       }
-      const T lo0 = lo[j];
-      T nv = explicit_update(cur, ul, ur, r, h, s, lo[j]);
-      bool keep = false;
-      if constexpr (MODE == MODE_EXACT && BCT == BC_DIRICHLET) {
-        keep = (j == 0 && tid == 0) || (j == C - 1 && tid == NT - 1);
-      } else if constexpr (MODE == MODE_RAGGED) {
-        keep = j > jstar;  // padding
-        if constexpr (BCT == BC_DIRICHLET) keep = keep || j == jstar || (j == 0 && tid == 0);
-      } else if constexpr (MODE == MODE_WINDOW_DIR) {
-        const int64_t gi = gbase + j;
-        keep = gi == 0 || gi == n - 1;
+#pragma unroll
+      for (int j = 0; j < C; ++j) {
+        const T cur = v[j];
+        T ur = (j + 1 < C) ? v[j + 1] : right;
+        if constexpr (WRAPX) {
+          if (j == jstar) ur = wrapR;
+        }
+        const T nv = explicit_update(cur, prev, ur, r, h, s, lo[j]);
+        if (!keep_node<NT, C, MODE, BCT>(j, jstar, gbase, n)) v[j] = nv;
+        prev = cur;
       }
-      if (keep) { nv = cur; lo[j] = lo0; }
-      prev = cur;
-      v[j] = nv;
     }
   }
 }
