@@ -71,13 +71,22 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits", "-lms",
-                 "200", "-i", str(self.index)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                 "50", "-i", str(self.index)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
                 text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
         except Exception as e:  # noqa: BLE001
             log("clock sampling unavailable:", e)
             self.proc = None
+        return self
+
+    def ready(self, timeout: float = 5.0):
+        """Waits for the first sample (the tool's start-up), then counts only
+        the samples taken from here on."""
+        t0 = time.perf_counter()
+        while self.proc is not None and not self.lines and time.perf_counter() - t0 < timeout:
+            time.sleep(0.01)
+        self.mark = len(self.lines)
         return self
 
     def _read(self):
@@ -94,7 +103,7 @@ class ClockSampler:
             self.proc.kill()
         sm, mx, reasons, pw = [], [], set(), []
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for ln in self.lines[getattr(self, "mark", 0):]:
             f = [x.strip() for x in ln.split(",")]
             if len(f) < 9:
                 continue
@@ -303,7 +312,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     barrier(world)
     torch.cuda.synchronize()
-    clocks = ClockSampler(local).start()
+    clocks = ClockSampler(local).start().ready()
     lc0 = ctx.launch_count()
     timing = []
     for _ in range(args.steps):
@@ -599,7 +608,7 @@ def serve_bench(ctx, dev, duration: float, rate: float = 20000.0, plain_seconds:
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--quick", action="store_true", help="skip the side measurements")
