@@ -28,80 +28,62 @@
 
 namespace burgers {
 
-// Advances the C nodes held by this thread `nsteps` BTCS steps.
+// Advances the row held by this CTA `nsteps` BTCS steps; thread t owns nodes
+// [tC, tC + C).
 //
 // Increment form: with a = u^n, A(u^n) u^n = u^n - Delta(u^n) where Delta is the
 // explicit forward-Euler increment of the same r, s (Eq. 21), so the step is
 //     A(u^n) delta = Delta(u^n),   u^{n+1} = u^n + delta,
 // the same solution as A u^{n+1} = u^n in exact arithmetic. Solving for the
 // small increment instead of the full state keeps the FP32 solve error
-// proportional to |delta| rather than |u|, and the FP32 addition is Kahan-
-// compensated like the explicit kernel. Dirichlet end rows and padding rows
+// proportional to |delta| rather than |u|. Dirichlet end rows and padding rows
 // are identity rows with a zero increment.
-// u^n and (FP32) the Kahan terms wait in shared memory, laid out [j][thread]
-// so a warp's accesses are conflict-free, while the elimination holds only its
-// three coefficient arrays in registers.
+//
+// The row state lives in shared memory, laid out [j][thread] so a warp's
+// accesses are conflict-free, and the elimination holds only its three
+// coefficient arrays in registers. FP32 adds u + delta with Kahan compensation
+// (the term lo per node, also in shared memory): BTCS steps are long, so an
+// increment can be a sizeable part of u and must be compensated every step.
+//
+// Two barriers per step. Each thread publishes the reduced-system data of its
+// chunk; warp 0 forms the reduced rows, solves them, and also computes the
+// next step's value of every chunk's first and last node (the owner computes
+// the same numbers from the same operands), so the neighbour values of the
+// next step need no exchange of their own.
 template <typename T, int NT, int C, bool EXACT, int BCT>
-__device__ __forceinline__ void btcs_steps(T (&v)[C], int64_t nsteps, T r, T s, int n,
-                                           BtcsShared<T, NT>& sm, T* sh_last, T* sh_first,
-                                           T* sh_wrap, T* un, T* lo) {
-  constexpr int NW = NT / 32;
-  constexpr bool WRAPX = (!EXACT && BCT == BC_PERIODIC);
+__device__ __forceinline__ void btcs_steps(int64_t nsteps, T r, T s, int n, BtcsShared<T, NT>& sm,
+                                           T* hfirst, T* hlast, T* us, T* lo) {
+  constexpr bool PER = BCT == BC_PERIODIC;
+  constexpr int Q = NT / 32;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int base = tid * C;
   const int tl = EXACT ? NT - 1 : (n - 1) / C;  // chunk holding node n-1
-  const int jstar = n - 1 - base;                // local index of node n-1
-  const int je = EXACT ? C - 1 : (jstar < C ? jstar : C - 1);  // chunk end row (<0: none)
+  const int jstar = n - 1 - tid * C;              // local index of node n-1
+  const int je = EXACT ? C - 1 : (jstar < C ? jstar : C - 1);  // chunk end row
   const T ds1 = T(1) + T(2) * s;
+  auto uval = [&](int j, int t) -> T { return us[j * NT + t]; };
+  // u^{n+1} of node j of chunk t from its increment (the owner's arithmetic)
+  auto next_u = [&](int j, int t, T delta) -> T {
+    T l0 = T(0);
+    if constexpr (Kahan<T>::on) l0 = lo[j * NT + t];
+    return comp_add(us[j * NT + t], delta, l0);
+  };
   T ch[C], ah[C], dd[C];
-  if constexpr (Kahan<T>::on) {
-#pragma unroll
-    for (int j = 0; j < C; ++j) lo[j * NT + tid] = T(0);
-  }
   for (int64_t step = 0; step < nsteps; ++step) {
-    // ---- neighbour values of u^n across threads (as in the explicit kernel)
-    const int p = int(step & 1);
-    const T first = v[0], last = v[C - 1];
-    T left = shfl(last, (lane + 31) & 31);
-    T right = shfl(first, (lane + 1) & 31);
-    if constexpr (NW > 1) {
-      if (lane == 31) sh_last[p * NW + warp] = last;
-      if (lane == 0) sh_first[p * NW + warp] = first;
-    }
-    if constexpr (WRAPX) {
-      if (jstar >= 0 && jstar < C) {
-        T sel = v[0];
-#pragma unroll
-        for (int j = 1; j < C; ++j)
-          if (j == jstar) sel = v[j];
-        sh_wrap[p * 2 + 0] = sel;
-      }
-      if (tid == 0) sh_wrap[p * 2 + 1] = first;
-    }
-    if constexpr (NW > 1 || WRAPX) __syncthreads();
-    if constexpr (NW > 1) {
-      if (lane == 0) left = sh_last[p * NW + (warp + NW - 1) % NW];
-      if (lane == 31) right = sh_first[p * NW + (warp + 1) % NW];
-    }
-    T wrapL = T(0), wrapR = T(0);
-    if constexpr (WRAPX) {
-      wrapL = sh_wrap[p * 2 + 0];
-      wrapR = sh_wrap[p * 2 + 1];
-    }
+    T left = T(0), right = T(0);
+    if (tid > 0) left = hlast[tid - 1];
+    else if constexpr (PER) left = hlast[tl];
+    if (tid < tl) right = hfirst[tid + 1];
+    else if constexpr (PER) right = hfirst[0];
     // ---- assembly of rows and right-hand sides fused with the forward sweep
     T chp = T(0), ahp = T(-1), dhp = T(0);
-    T prev = left;
+    T ul = left, a = uval(0, tid);
 #pragma unroll
     for (int j = 0; j < C; ++j) {
-      const T a = v[j];
-      un[j * NT + tid] = a;
-      T ul = prev;
-      T ur = (j + 1 < C) ? v[j + 1] : right;
-      if constexpr (WRAPX) {
-        if (j == 0 && tid == 0) ul = wrapL;
-        if (j == jstar) ur = wrapR;
+      const T an = (j + 1 < C) ? uval(j + 1, tid) : right;
+      T ur = an;
+      if constexpr (!EXACT) {
+        if (j == jstar) ur = right;
       }
-      prev = a;
       const T ra = r * a;
       T l = -s - tmax(ra, T(0));
       T c = tmin(ra, T(0)) - s;
@@ -127,6 +109,8 @@ __device__ __forceinline__ void btcs_steps(T (&v)[C], int64_t nsteps, T r, T s, 
       ch[j] = chp;
       ah[j] = ahp;
       dd[j] = dhp;
+      ul = a;
+      a = an;
     }
     T e_ch = T(0), e_ah = T(0), e_dh = T(0);
     if constexpr (EXACT) {
@@ -162,42 +146,71 @@ __device__ __forceinline__ void btcs_steps(T (&v)[C], int64_t nsteps, T r, T s, 
         else { cd = nd; ca = na; cg = ng; }
       }
     }
-    // ---- reduced row of this chunk
+    // ---- this chunk's first-row and end-row relations
     sm.rd[tid] = dd[0];
     sm.ra[tid] = ah[0];
     sm.rg[tid] = ch[0];
-    __syncthreads();
-    T A = T(0), B = T(1), Cc = T(0), D = T(0);
-    if (tid <= tl) {
-      const int nx = (tid == tl) ? 0 : tid + 1;
-      const T dn = sm.rd[nx], an = sm.ra[nx], gn = sm.rg[nx];
-      A = e_ah;
-      B = T(1) - e_ch * an;
-      Cc = -e_ch * gn;
-      D = tfma(-e_ch, dn, e_dh);
+    {
+      const int si = sk(tid);
+      sm.A[si] = e_ah;
+      sm.Cc[si] = e_ch;
+      sm.D[si] = e_dh;
     }
-    const int si = sk(tid);
-    sm.A[si] = A; sm.B[si] = B; sm.Cc[si] = Cc; sm.D[si] = D; sm.U[si] = T(0);
     __syncthreads();
-    if (warp == 0) reduced_solve<T, NT, BCT == BC_PERIODIC>(sm, tl, lane);
+    if (warp == 0) {
+      // reduced row of each of this lane's chunks: end row of chunk t with the
+      // first-row relation of chunk t + 1 substituted (chunk 0 after the last)
+#pragma unroll
+      for (int q = 0; q < Q; ++q) {
+        const int t = lane * Q + q, i = sk(t);
+        T A = T(0), B = T(1), Cc = T(0), D = T(0);
+        if (t <= tl) {
+          const int nx = (t == tl) ? 0 : t + 1;
+          const T ech = sm.Cc[i];
+          A = sm.A[i];
+          B = T(1) - ech * sm.ra[nx];
+          Cc = -ech * sm.rg[nx];
+          D = tfma(-ech, sm.rd[nx], sm.D[i]);
+        }
+        sm.A[i] = A; sm.B[i] = B; sm.Cc[i] = Cc; sm.D[i] = D; sm.U[i] = T(0);
+      }
+      __syncwarp();
+      reduced_solve<T, NT, PER>(sm, tl, lane);
+      __syncwarp();
+      // next step's first and last node of each chunk
+#pragma unroll
+      for (int q = 0; q < Q; ++q) {
+        const int t = lane * Q + q;
+        if (t <= tl) {
+          const T Xt = sm.X[t];
+          T L = T(0);
+          if (t > 0) L = sm.X[t - 1];
+          else if constexpr (PER) L = sm.X[tl];
+          const int jt = (t == tl) ? (n - 1) - t * C : C - 1;  // end row of chunk t
+          const T d0 = jt == 0 ? Xt : tfma(-sm.rg[t], Xt, tfma(-sm.ra[t], L, sm.rd[t]));
+          hfirst[t] = next_u(0, t, d0);
+          hlast[t] = next_u(jt, t, Xt);
+        }
+      }
+    }
     __syncthreads();
-    // ---- back-substitution of the increment and the compensated update
+    // ---- back-substitution of the increment and the update of the state
     if (tid <= tl) {
       T L = T(0);
       if (tid > 0) L = sm.X[tid - 1];
-      else if constexpr (BCT == BC_PERIODIC) L = sm.X[tl];
+      else if constexpr (PER) L = sm.X[tl];
       const T Xt = sm.X[tid];
 #pragma unroll
       for (int j = 0; j < C; ++j) {
-        const T delta = tfma(-ch[j], Xt, tfma(-ah[j], L, dd[j]));
-        T l0 = T(0);
-        if constexpr (Kahan<T>::on) l0 = lo[j * NT + tid];
-        v[j] = comp_add(un[j * NT + tid], delta, l0);
-        if constexpr (Kahan<T>::on) lo[j * NT + tid] = l0;
+        if (EXACT || j <= je) {
+          const T delta = (j == je) ? Xt : tfma(-ch[j], Xt, tfma(-ah[j], L, dd[j]));
+          const int o = j * NT + tid;
+          T l0 = T(0);
+          if constexpr (Kahan<T>::on) l0 = lo[o];
+          us[o] = comp_add(us[o], delta, l0);
+          if constexpr (Kahan<T>::on) lo[o] = l0;
+        }
       }
-    } else {
-#pragma unroll
-      for (int j = 0; j < C; ++j) v[j] = un[j * NT + tid];
     }
   }
 }
@@ -206,34 +219,41 @@ template <typename T, int NT, int C, bool EXACT>
 __global__ void __launch_bounds__(NT) k_btcs_resident(T* __restrict__ u,
                                                       const RowDesc* __restrict__ rows, int count,
                                                       int* __restrict__ counter) {
-  constexpr int NW = NT / 32;
   __shared__ BtcsShared<T, NT> sm;
-  __shared__ T sh_last[2 * NW], sh_first[2 * NW], sh_wrap[4];
+  __shared__ T hfirst[NT], hlast[NT];
   __shared__ int s_item;
   extern __shared__ __align__(16) unsigned char dsm[];
-  T* un = reinterpret_cast<T*>(dsm);  // C * NT values
-  T* lo = un + C * NT;                // C * NT values (FP32)
+  T* us = reinterpret_cast<T*>(dsm);  // C * NT values
+  T* lo = us + C * NT;                // C * NT values (FP32)
+  const int tid = threadIdx.x;
   for (;;) {
-    if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
+    if (tid == 0) s_item = atomicAdd(counter, 1);
     __syncthreads();
     const int item = s_item;
     if (item >= count) return;
     const RowDesc rd = rows[item];
     T* row = u + rd.offset;
-    const int base = threadIdx.x * C;
-    T v[C];
+    const int base = tid * C;
+    const int n = rd.n;
+    const int tl = EXACT ? NT - 1 : (n - 1) / C;
+    const int jt = (tid == tl) ? (n - 1) - base : C - 1;
 #pragma unroll
-    for (int j = 0; j < C; ++j) v[j] = (EXACT || base + j < rd.n) ? row[base + j] : T(0);
+    for (int j = 0; j < C; ++j) {
+      const T x = (EXACT || base + j < n) ? row[base + j] : T(0);
+      us[j * NT + tid] = x;
+      if constexpr (Kahan<T>::on) lo[j * NT + tid] = T(0);
+      if (j == 0) hfirst[tid] = x;
+      if (j == jt) hlast[tid] = x;
+    }
+    __syncthreads();
     const T r = T(rd.r), s = T(rd.s);
     if (rd.bc == BC_PERIODIC)
-      btcs_steps<T, NT, C, EXACT, BC_PERIODIC>(v, rd.nsteps, r, s, rd.n, sm, sh_last, sh_first,
-                                               sh_wrap, un, lo);
+      btcs_steps<T, NT, C, EXACT, BC_PERIODIC>(rd.nsteps, r, s, n, sm, hfirst, hlast, us, lo);
     else
-      btcs_steps<T, NT, C, EXACT, BC_DIRICHLET>(v, rd.nsteps, r, s, rd.n, sm, sh_last,
-                                                sh_first, sh_wrap, un, lo);
+      btcs_steps<T, NT, C, EXACT, BC_DIRICHLET>(rd.nsteps, r, s, n, sm, hfirst, hlast, us, lo);
 #pragma unroll
     for (int j = 0; j < C; ++j)
-      if (EXACT || base + j < rd.n) row[base + j] = v[j];
+      if (EXACT || base + j < n) row[base + j] = us[j * NT + tid];
     __syncthreads();
   }
 }

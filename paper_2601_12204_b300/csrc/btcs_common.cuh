@@ -14,9 +14,10 @@ __device__ __forceinline__ int sk(int i) { return i + (i >> 5); }  // bank skew
 template <typename T, int NT>
 struct BtcsShared {
   static constexpr int SK = NT + NT / 32;
-  T rd[NT], ra[NT], rg[NT];              // first-row relation per chunk; reused for z
+  T rd[NT], ra[NT], rg[NT];              // first-row relation per chunk
   T A[SK], B[SK], Cc[SK], D[SK], U[SK];  // reduced rows (skewed)
   T X[NT];                               // chunk-end solution
+  T Z[NT];                               // cyclic case: solution for the correction vector
 };
 
 // Solves the reduced system held in sm (rows 0..NT-1, rows beyond tl are
@@ -117,7 +118,7 @@ __device__ __forceinline__ void reduced_solve(BtcsShared<T, NT>& sm, int tl, int
       if constexpr (CYC) z = tfma(-sm.Cc[i], Ze, tfma(-sm.A[i], ZL, sm.U[i]));
     }
     sm.X[r0 + q] = y;
-    if constexpr (CYC) sm.rd[r0 + q] = z;
+    if constexpr (CYC) sm.Z[r0 + q] = z;
   }
   if constexpr (CYC) {
     __syncwarp();
@@ -127,12 +128,12 @@ __device__ __forceinline__ void reduced_solve(BtcsShared<T, NT>& sm, int tl, int
     if (lane == 0) {
       const double fd = double(fa);
       const double vy = double(sm.X[0]) + fd * double(sm.X[tl]);
-      const double vz = double(sm.rd[0]) + fd * double(sm.rd[tl]);
+      const double vz = double(sm.Z[0]) + fd * double(sm.Z[tl]);
       fac = T(vy / (1.0 + vz));
     }
     fac = shfl(fac, 0);
 #pragma unroll
-    for (int q = 0; q < Q; ++q) sm.X[r0 + q] = tfma(-fac, sm.rd[r0 + q], sm.X[r0 + q]);
+    for (int q = 0; q < Q; ++q) sm.X[r0 + q] = tfma(-fac, sm.Z[r0 + q], sm.X[r0 + q]);
   }
 }
 

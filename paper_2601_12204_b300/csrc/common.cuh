@@ -87,6 +87,10 @@ struct Kahan<float> {
   static constexpr bool on = true;
 };
 
+// Steps between folds of the FP32 split state (value at the last fold plus
+// the increments summed since) of the explicit kernels.
+constexpr int SPLIT_FOLD = 32;
+
 // The 16-byte vector type of T (four floats or two doubles).
 template <typename T>
 struct Vec16;

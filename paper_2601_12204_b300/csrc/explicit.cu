@@ -82,13 +82,11 @@ __device__ __forceinline__ bool keep_node(int j, int jstar, int64_t gbase, int n
 
 // FP32 steps with a split state: each node carries uh (its value at the last
 // fold) and d (the increments summed since), and a step evaluates the stencil
-// on u = uh + d and adds the increment to d. Every FOLD steps, and after the
+// on u = uh + d and adds the increment to d. Every SPLIT_FOLD steps, and after the
 // last one, d is folded into uh with its rounding error kept in d (the same
 // two-sum as compensated summation), so increments are never rounded against
 // the full magnitude of u between folds. On entry and exit the state is
 // (v, lo) with the true value v - lo, as in Kahan summation.
-constexpr int FOLD = 32;
-
 template <int NT, int C, int MODE, int BCT>
 __device__ __forceinline__ void explicit_steps_split(float (&v)[C], float (&lo)[C], int64_t nsteps,
                                                      float r, float h, float s, int n,
@@ -132,7 +130,7 @@ __device__ __forceinline__ void explicit_steps_split(float (&v)[C], float (&lo)[
       wl = wc;
       wc = wr;
     }
-    if (((k + 1) & (FOLD - 1)) == 0 || k + 1 == nsteps) {
+    if (((k + 1) & (SPLIT_FOLD - 1)) == 0 || k + 1 == nsteps) {
 #pragma unroll
       for (int j = 0; j < C; ++j) {
         const float t = v[j] + lo[j];
