@@ -122,17 +122,17 @@ __device__ __forceinline__ void resident_solve(T (&x)[C], T (&ah)[C], T (&ch)[C]
   T e_ch, e_ah, e_dh;
   chunk_forward<T, C>(x, ah, ch, je, rowfn, e_ch, e_ah, e_dh);
   chunk_backward<T, C>(x, ah, ch, je);
-  sm.rd[tid] = x[0];
-  sm.ra[tid] = ah[0];
-  sm.rg[tid] = ch[0];
+  sm.rd[sk(tid)] = x[0];
+  sm.ra[sk(tid)] = ah[0];
+  sm.rg[sk(tid)] = ch[0];
   __syncthreads();
   T A = T(0), B = T(1), Cc = T(0), D = T(0);
   if (tid <= tl) {
     const int nx = (tid == tl) ? 0 : tid + 1;
     A = e_ah;
-    B = T(1) - e_ch * sm.ra[nx];
-    Cc = -e_ch * sm.rg[nx];
-    D = tfma(-e_ch, sm.rd[nx], e_dh);
+    B = T(1) - e_ch * sm.ra[sk(nx)];
+    Cc = -e_ch * sm.rg[sk(nx)];
+    D = tfma(-e_ch, sm.rd[sk(nx)], e_dh);
   }
   const int si = sk(tid);
   sm.A[si] = A; sm.B[si] = B; sm.Cc[si] = Cc; sm.D[si] = D; sm.U[si] = T(0);
@@ -144,9 +144,9 @@ __device__ __forceinline__ void resident_solve(T (&x)[C], T (&ah)[C], T (&ch)[C]
   __syncthreads();
   if (tid <= tl) {
     T L = T(0);
-    if (tid > 0) L = sm.X[tid - 1];
-    else if (cyc) L = sm.X[tl];
-    const T Xt = sm.X[tid];
+    if (tid > 0) L = sm.X[sk(tid - 1)];
+    else if (cyc) L = sm.X[sk(tl)];
+    const T Xt = sm.X[sk(tid)];
 #pragma unroll
     for (int j = 0; j < C; ++j) x[j] = tfma(-ch[j], Xt, tfma(-ah[j], L, x[j]));
   }

@@ -14,7 +14,7 @@
 // tridiagonal row per chunk in the unknowns X_{t-1}, X_t, X_{t+1}: a reduced
 // system of NT rows (cyclic for periodic rows). Warp 0 solves it: the
 // cyclic corners are split off by Sherman-Morrison (gamma = -B_0, correction
-// factor (v.y)/(1 + v.z) evaluated in FP64), each lane eliminates Q = NT/32
+// factor (v.y)/(1 + v.z)), each lane eliminates Q = NT/32
 // reduced rows the same way, and the remaining 32-row system is solved by
 // parallel cyclic reduction over warp shuffles. Back-substitution then
 // recovers every node from delta, alpha, gamma and the chunk-end values.
@@ -147,9 +147,9 @@ __device__ __forceinline__ void btcs_steps(int64_t nsteps, T r, T s, int n, Btcs
       }
     }
     // ---- this chunk's first-row and end-row relations
-    sm.rd[tid] = dd[0];
-    sm.ra[tid] = ah[0];
-    sm.rg[tid] = ch[0];
+    sm.rd[sk(tid)] = dd[0];
+    sm.ra[sk(tid)] = ah[0];
+    sm.rg[sk(tid)] = ch[0];
     {
       const int si = sk(tid);
       sm.A[si] = e_ah;
@@ -168,9 +168,9 @@ __device__ __forceinline__ void btcs_steps(int64_t nsteps, T r, T s, int n, Btcs
           const int nx = (t == tl) ? 0 : t + 1;
           const T ech = sm.Cc[i];
           A = sm.A[i];
-          B = T(1) - ech * sm.ra[nx];
-          Cc = -ech * sm.rg[nx];
-          D = tfma(-ech, sm.rd[nx], sm.D[i]);
+          B = T(1) - ech * sm.ra[sk(nx)];
+          Cc = -ech * sm.rg[sk(nx)];
+          D = tfma(-ech, sm.rd[sk(nx)], sm.D[i]);
         }
         sm.A[i] = A; sm.B[i] = B; sm.Cc[i] = Cc; sm.D[i] = D; sm.U[i] = T(0);
       }
@@ -182,12 +182,12 @@ __device__ __forceinline__ void btcs_steps(int64_t nsteps, T r, T s, int n, Btcs
       for (int q = 0; q < Q; ++q) {
         const int t = lane * Q + q;
         if (t <= tl) {
-          const T Xt = sm.X[t];
+          const T Xt = sm.X[sk(t)];
           T L = T(0);
-          if (t > 0) L = sm.X[t - 1];
-          else if constexpr (PER) L = sm.X[tl];
+          if (t > 0) L = sm.X[sk(t - 1)];
+          else if constexpr (PER) L = sm.X[sk(tl)];
           const int jt = (t == tl) ? (n - 1) - t * C : C - 1;  // end row of chunk t
-          const T d0 = jt == 0 ? Xt : tfma(-sm.rg[t], Xt, tfma(-sm.ra[t], L, sm.rd[t]));
+          const T d0 = jt == 0 ? Xt : tfma(-sm.rg[sk(t)], Xt, tfma(-sm.ra[sk(t)], L, sm.rd[sk(t)]));
           hfirst[t] = next_u(0, t, d0);
           hlast[t] = next_u(jt, t, Xt);
         }
@@ -197,9 +197,9 @@ __device__ __forceinline__ void btcs_steps(int64_t nsteps, T r, T s, int n, Btcs
     // ---- back-substitution of the increment and the update of the state
     if (tid <= tl) {
       T L = T(0);
-      if (tid > 0) L = sm.X[tid - 1];
-      else if constexpr (PER) L = sm.X[tl];
-      const T Xt = sm.X[tid];
+      if (tid > 0) L = sm.X[sk(tid - 1)];
+      else if constexpr (PER) L = sm.X[sk(tl)];
+      const T Xt = sm.X[sk(tid)];
 #pragma unroll
       for (int j = 0; j < C; ++j) {
         if (EXACT || j <= je) {

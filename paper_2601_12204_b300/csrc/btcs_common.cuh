@@ -1,7 +1,7 @@
 // btcs_common.cuh -- pieces of the partitioned tridiagonal elimination shared
 // by the resident BTCS kernel and the multi-level solver: the shared-memory
 // layout of a CTA's reduced system and its warp-0 solver (Sherman-Morrison
-// split of the cyclic corners with an FP64 correction, per-lane elimination,
+// split of the cyclic corners, per-lane elimination,
 // parallel cyclic reduction over warp shuffles).
 #pragma once
 
@@ -14,10 +14,12 @@ __device__ __forceinline__ int sk(int i) { return i + (i >> 5); }  // bank skew
 template <typename T, int NT>
 struct BtcsShared {
   static constexpr int SK = NT + NT / 32;
-  T rd[NT], ra[NT], rg[NT];              // first-row relation per chunk
-  T A[SK], B[SK], Cc[SK], D[SK], U[SK];  // reduced rows (skewed)
-  T X[NT];                               // chunk-end solution
-  T Z[NT];                               // cyclic case: solution for the correction vector
+  // indexed through sk(): lane l of warp 0 handles rows lQ..lQ+Q-1, and the
+  // skew keeps those strided accesses free of bank conflicts
+  T rd[SK], ra[SK], rg[SK];              // first-row relation per chunk
+  T A[SK], B[SK], Cc[SK], D[SK], U[SK];  // reduced rows
+  T X[SK];                               // chunk-end solution
+  T Z[SK];                               // cyclic case: solution for the correction vector
 };
 
 // Solves the reduced system held in sm (rows 0..NT-1, rows beyond tl are
@@ -117,23 +119,20 @@ __device__ __forceinline__ void reduced_solve(BtcsShared<T, NT>& sm, int tl, int
       y = tfma(-sm.Cc[i], Ye, tfma(-sm.A[i], YL, sm.D[i]));
       if constexpr (CYC) z = tfma(-sm.Cc[i], Ze, tfma(-sm.A[i], ZL, sm.U[i]));
     }
-    sm.X[r0 + q] = y;
-    if constexpr (CYC) sm.Z[r0 + q] = z;
+    sm.X[sk(r0 + q)] = y;
+    if constexpr (CYC) sm.Z[sk(r0 + q)] = z;
   }
   if constexpr (CYC) {
     __syncwarp();
-    // x = y - (v.y)/(1 + v.z) z: dot products and denominator in FP64, on one
-    // lane (the FP64 pipe is narrow), the factor broadcast in T.
-    T fac = T(0);
-    if (lane == 0) {
-      const double fd = double(fa);
-      const double vy = double(sm.X[0]) + fd * double(sm.X[tl]);
-      const double vz = double(sm.Z[0]) + fd * double(sm.Z[tl]);
-      fac = T(vy / (1.0 + vz));
-    }
-    fac = shfl(fac, 0);
+    // x = y - (v.y)/(1 + v.z) z. v has two nonzeros, so each dot product is
+    // one FMA. By the matrix determinant lemma 1 + v.z is the ratio of the
+    // determinants of the cyclic and the split matrix, both nonsingular
+    // M-matrices, so it is positive and the division is well conditioned.
+    const T vy = tfma(fa, sm.X[sk(tl)], sm.X[sk(0)]);
+    const T vz = tfma(fa, sm.Z[sk(tl)], sm.Z[sk(0)]);
+    const T fac = vy / (T(1) + vz);
 #pragma unroll
-    for (int q = 0; q < Q; ++q) sm.X[r0 + q] = tfma(-fac, sm.Z[r0 + q], sm.X[r0 + q]);
+    for (int q = 0; q < Q; ++q) sm.X[sk(r0 + q)] = tfma(-fac, sm.Z[sk(r0 + q)], sm.X[sk(r0 + q)]);
   }
 }
 

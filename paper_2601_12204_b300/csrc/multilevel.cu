@@ -503,17 +503,17 @@ __global__ void __launch_bounds__(NT) k_ml_top(T* __restrict__ u, T* __restrict_
     UpperRows<T> src{ws + R.ef[L - 1], M, base, je};
     chunk_forward<T, C>(v, ah, ch, je, src, e_ch, e_ah, e_dh);
     chunk_backward<T, C>(v, ah, ch, je);
-    sm.rd[tid] = v[0];
-    sm.ra[tid] = ah[0];
-    sm.rg[tid] = ch[0];
+    sm.rd[sk(tid)] = v[0];
+    sm.ra[sk(tid)] = ah[0];
+    sm.rg[sk(tid)] = ch[0];
     __syncthreads();
     T A = T(0), B = T(1), Cc = T(0), D = T(0);
     if (tid <= tl) {
       const int nx = (tid == tl) ? 0 : tid + 1;
       A = e_ah;
-      B = T(1) - e_ch * sm.ra[nx];
-      Cc = -e_ch * sm.rg[nx];
-      D = tfma(-e_ch, sm.rd[nx], e_dh);
+      B = T(1) - e_ch * sm.ra[sk(nx)];
+      Cc = -e_ch * sm.rg[sk(nx)];
+      D = tfma(-e_ch, sm.rd[sk(nx)], e_dh);
     }
     const int si = sk(tid);
     sm.A[si] = A; sm.B[si] = B; sm.Cc[si] = Cc; sm.D[si] = D; sm.U[si] = T(0);
@@ -525,9 +525,9 @@ __global__ void __launch_bounds__(NT) k_ml_top(T* __restrict__ u, T* __restrict_
     __syncthreads();
     if (tid <= tl) {
       T Lv = T(0);
-      if (tid > 0) Lv = sm.X[tid - 1];
-      else if (R.bc == BC_PERIODIC) Lv = sm.X[tl];
-      const T Xt = sm.X[tid];
+      if (tid > 0) Lv = sm.X[sk(tid - 1)];
+      else if (R.bc == BC_PERIODIC) Lv = sm.X[sk(tl)];
+      const T Xt = sm.X[sk(tid)];
       T* out = ws + R.x[L];
 #pragma unroll
       for (int j = 0; j < C; ++j)
