@@ -1,7 +1,7 @@
 // btcs_common.cuh -- pieces of the partitioned tridiagonal elimination shared
 // by the resident BTCS kernel and the multi-level solver: the shared-memory
 // layout of a CTA's reduced system and its warp-0 solver (Sherman-Morrison
-// split of the cyclic corners, per-lane elimination,
+// split of the cyclic corners with an FP64 correction, per-lane elimination,
 // parallel cyclic reduction over warp shuffles).
 #pragma once
 
@@ -124,13 +124,16 @@ __device__ __forceinline__ void reduced_solve(BtcsShared<T, NT>& sm, int tl, int
   }
   if constexpr (CYC) {
     __syncwarp();
-    // x = y - (v.y)/(1 + v.z) z. v has two nonzeros, so each dot product is
-    // one FMA. By the matrix determinant lemma 1 + v.z is the ratio of the
-    // determinants of the cyclic and the split matrix, both nonsingular
-    // M-matrices, so it is positive and the division is well conditioned.
-    const T vy = tfma(fa, sm.X[sk(tl)], sm.X[sk(0)]);
-    const T vz = tfma(fa, sm.Z[sk(tl)], sm.Z[sk(0)]);
-    const T fac = vy / (T(1) + vz);
+    // x = y - (v.y)/(1 + v.z) z: dot products and denominator in FP64, on one
+    // lane (the FP64 pipe is narrow), the factor broadcast in T.
+    T fac = T(0);
+    if (lane == 0) {
+      const double fd = double(fa);
+      const double vy = double(sm.X[sk(0)]) + fd * double(sm.X[sk(tl)]);
+      const double vz = double(sm.Z[sk(0)]) + fd * double(sm.Z[sk(tl)]);
+      fac = T(vy / (1.0 + vz));
+    }
+    fac = shfl(fac, 0);
 #pragma unroll
     for (int q = 0; q < Q; ++q) sm.X[sk(r0 + q)] = tfma(-fac, sm.Z[sk(r0 + q)], sm.X[sk(r0 + q)]);
   }
