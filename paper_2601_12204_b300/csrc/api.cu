@@ -325,9 +325,15 @@ static burgers_status build_plan(burgers_ctx* ctx, int scheme, const burgers_bat
       int K;
       if (!pick_stream(ctx, dtype, nmin, &sh, &K))
         return set_error(BURGERS_EINVAL, "row too short for the streaming kernel");
-      const KernelEntry* k = find_kernel(K_EXPLICIT_STREAM, dtype, sh.nt, sh.c, 0);
+      const KernelEntry* k = nullptr;
+      if (K == 1) {  // one step per pass: the bandwidth-bound single-step kernel
+        k = find_kernel(K_EXPLICIT_STEP1, dtype, 256, dtype == 0 ? 8 : 4, 0);
+        sh = Shape{256, dtype == 0 ? 8 : 4};
+      } else {
+        k = find_kernel(K_EXPLICIT_STREAM, dtype, sh.nt, sh.c, 0);
+      }
       if (!k) return set_error(BURGERS_EINVAL, "streaming shape not instantiated");
-      const int64_t W = int64_t(sh.nt) * sh.c, O = W - 2 * K;
+      const int64_t W = int64_t(sh.nt) * sh.c, O = K == 1 ? W : W - 2 * K;
       int rbegin = int(p->rows.size());
       int ibegin = int(p->items.size());
       for (size_t q = 0; q < longs.size(); ++q) {
@@ -338,7 +344,10 @@ static burgers_status build_plan(burgers_ctx* ctx, int scheme, const burgers_bat
           p->items.push_back(TileItem{int32_t(q), int32_t(t)});
       }
       int nitems = int(p->items.size()) - ibegin;
-      int grid = std::min(nitems, ctx->sm_count * blocks_per_sm(k));
+      // the single-step kernel streams: one CTA per tile lets the scheduler
+      // overlap the tiles' memory traffic
+      int grid = K == 1 ? std::min(nitems, 1 << 20)
+                        : std::min(nitems, ctx->sm_count * blocks_per_sm(k));
       int64_t passes = (smax + K - 1) / K;
       for (int64_t ps = 0; ps < passes; ++ps) {
         Launch L;

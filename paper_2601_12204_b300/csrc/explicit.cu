@@ -358,6 +358,113 @@ __global__ void __launch_bounds__(NT) k_explicit_stream(const T* __restrict__ sr
   }
 }
 
+// One step per HBM pass (streaming with K = 1): the bandwidth-bound form of
+// the explicit step. Item `it` is tile ti.tile of row ti.row, NT*C nodes; a
+// thread updates C consecutive nodes read and written as 16-byte vectors when
+// the row's start allows it. The two neighbours of a thread's nodes come from
+// the adjacent lanes by shuffle, and from memory at warp and row edges. Same
+// arguments as k_explicit_stream (K is 1 here).
+template <typename T, int NT, int C>
+__global__ void __launch_bounds__(NT) k_explicit_step1(const T* __restrict__ src,
+                                                       T* __restrict__ dst,
+                                                       const T* __restrict__ lo_src,
+                                                       T* __restrict__ lo_dst,
+                                                       const RowDesc* __restrict__ rows,
+                                                       const TileItem* __restrict__ items,
+                                                       int nitems, int K, int64_t step_base) {
+  (void)K;
+  using V = typename Vec16<T>::type;
+  constexpr int VE = 16 / int(sizeof(T));
+  static_assert(C % VE == 0, "whole vectors per thread");
+  constexpr bool KL = Kahan<T>::on;
+  const int lane = threadIdx.x & 31;
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const TileItem ti = items[it];
+    const RowDesc rd = rows[ti.row];
+    const int64_t n = rd.n;
+    const int64_t g0 = int64_t(ti.tile) * (NT * C) + int64_t(threadIdx.x) * C;
+    const int cnt = g0 >= n ? 0 : (n - g0 < C ? int(n - g0) : C);
+    const T* srow = src + rd.offset;
+    T* drow = dst + rd.offset;
+    const T* lsrc = KL ? lo_src + rd.offset : nullptr;
+    T* ldst = KL ? lo_dst + rd.offset : nullptr;
+    const bool vec = cnt == C && (reinterpret_cast<uintptr_t>(srow + g0) & 15) == 0 &&
+                     (reinterpret_cast<uintptr_t>(drow + g0) & 15) == 0 &&
+                     (!KL || ((reinterpret_cast<uintptr_t>(lsrc + g0) & 15) == 0 &&
+                              (reinterpret_cast<uintptr_t>(ldst + g0) & 15) == 0));
+    T v[C], lo[C];
+    if (vec) {
+#pragma unroll
+      for (int q = 0; q < C / VE; ++q) {
+        const V w = __ldcs(reinterpret_cast<const V*>(srow + g0) + q);
+        const T* wp = reinterpret_cast<const T*>(&w);
+#pragma unroll
+        for (int e = 0; e < VE; ++e) v[q * VE + e] = wp[e];
+        if constexpr (KL) {
+          const V wl = __ldcs(reinterpret_cast<const V*>(lsrc + g0) + q);
+          const T* wlp = reinterpret_cast<const T*>(&wl);
+#pragma unroll
+          for (int e = 0; e < VE; ++e) lo[q * VE + e] = wlp[e];
+        }
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < C; ++j) {
+        v[j] = j < cnt ? srow[g0 + j] : T(0);
+        lo[j] = (KL && j < cnt) ? lsrc[g0 + j] : T(0);
+      }
+    }
+    if constexpr (!KL) {
+#pragma unroll
+      for (int j = 0; j < C; ++j) lo[j] = T(0);
+    }
+    // neighbours: the adjacent lane's edge node when it is the adjacent node
+    T left = shfl_up(v[C - 1], 1);
+    T right = shfl_down(v[0], 1);
+    const bool per = rd.bc == BC_PERIODIC;
+    if (cnt > 0) {
+      if (lane == 0 || g0 == 0) left = g0 > 0 ? srow[g0 - 1] : (per ? srow[n - 1] : T(0));
+      if (lane == 31 || cnt < C || g0 + C == n)
+        right = g0 + cnt < n ? srow[g0 + cnt] : (per ? srow[0] : T(0));
+    }
+    if (cnt == 0) continue;
+    if (step_base < rd.nsteps) {
+      const T r = T(rd.r), h = T(0.5 * rd.r), s = T(rd.s);
+      T prev = left;
+#pragma unroll
+      for (int j = 0; j < C; ++j) {
+        const T cur = v[j];
+        const T ur = j + 1 < cnt ? v[j + 1] : right;
+        T l0 = lo[j];
+        const T nv = explicit_update(cur, prev, ur, r, h, s, l0);
+        const int64_t gi = g0 + j;
+        const bool keep = j >= cnt || (!per && (gi == 0 || gi == n - 1));
+        if (!keep) { v[j] = nv; lo[j] = l0; }
+        prev = cur;
+      }
+    }
+    if (vec) {
+#pragma unroll
+      for (int q = 0; q < C / VE; ++q) {
+        V w, wl;
+        T* wp = reinterpret_cast<T*>(&w);
+        T* wlp = reinterpret_cast<T*>(&wl);
+#pragma unroll
+        for (int e = 0; e < VE; ++e) { wp[e] = v[q * VE + e]; wlp[e] = lo[q * VE + e]; }
+        __stcs(reinterpret_cast<V*>(drow + g0) + q, w);
+        if constexpr (KL) __stcs(reinterpret_cast<V*>(ldst + g0) + q, wl);
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < C; ++j)
+        if (j < cnt) {
+          drow[g0 + j] = v[j];
+          if constexpr (KL) ldst[g0 + j] = lo[j];
+        }
+    }
+  }
+}
+
 #define REG_RES(T, DT, NT, C)                                                               \
   reg.push_back({K_EXPLICIT_RESIDENT, DT, NT, C, 1,                                         \
                  reinterpret_cast<const void*>(&k_explicit_resident<T, NT, C, true>), 0});  \
@@ -386,6 +493,11 @@ void register_explicit(std::vector<KernelEntry>& reg) {
   REG_STREAM(float, 0, 512, 16) REG_STREAM(float, 0, 256, 32)
   REG_STREAM(double, 1, 32, 4) REG_STREAM(double, 1, 128, 8) REG_STREAM(double, 1, 256, 8)
   REG_STREAM(double, 1, 256, 16)
+  // one step per pass
+  reg.push_back({K_EXPLICIT_STEP1, 0, 256, 8, 0,
+                 reinterpret_cast<const void*>(&k_explicit_step1<float, 256, 8>), 0});
+  reg.push_back({K_EXPLICIT_STEP1, 1, 256, 4, 0,
+                 reinterpret_cast<const void*>(&k_explicit_step1<double, 256, 4>), 0});
 }
 
 }  // namespace burgers

@@ -23,6 +23,7 @@ enum KernelKind : int32_t {
   K_BTCS_TOP = 5,           // multi-level BTCS: resident solve of the top level
   K_ADJ_EXPLICIT = 6,       // adjoint of the explicit solve (resident rows)
   K_ADJ_BTCS = 7,           // adjoint of the BTCS solve (resident rows)
+  K_EXPLICIT_STEP1 = 8,     // one explicit step per HBM pass over tiles of long rows
   K_KIND_COUNT
 };
 
