@@ -63,7 +63,7 @@ def _load():
         P = ctypes.c_void_p
         lib.or_cfl_dt.restype = d
         lib.or_cfl_dt.argtypes = [P, i64, d, d, d]
-        for name in ("or_explicit", "or_btcs"):
+        for name in ("or_explicit", "or_btcs", "or_rk4"):
             f = getattr(lib, name)
             f.restype = c
             f.argtypes = [P, i64, i32, d, d, d, i64]
@@ -73,7 +73,7 @@ def _load():
         lib.or_thomas.argtypes = [i64, P, P, P, P, P]
         lib.or_cyclic.restype = c
         lib.or_cyclic.argtypes = [i64, P, P, P, P, P]
-        for name in ("or_explicit_batch", "or_btcs_batch"):
+        for name in ("or_explicit_batch", "or_btcs_batch", "or_rk4_batch"):
             f = getattr(lib, name)
             f.restype = c
             f.argtypes = [P, i64, P, P, P, P, P, P, P, c]
@@ -121,6 +121,13 @@ def explicit(u0, bc: int, dx: float, nu: float, dt: float, nsteps: int) -> np.nd
     """Forward-Euler upwind/central solve (Eq. 21), returns u(nsteps*dt)."""
     u = _f64(u0).copy()
     _check(_load().or_explicit(_p(u), u.size, int(bc), dx, nu, dt, int(nsteps)), "explicit")
+    return u
+
+
+def rk4(u0, bc: int, dx: float, nu: float, dt: float, nsteps: int) -> np.ndarray:
+    """Classical fourth-order Runge-Kutta (Eq. 22) on the operator of Eq. 21."""
+    u = _f64(u0).copy()
+    _check(_load().or_rk4(_p(u), u.size, int(bc), dx, nu, dt, int(nsteps)), "rk4")
     return u
 
 
@@ -178,6 +185,12 @@ def _run_batch(fn, name, u, offsets, ns, bcs, dxs, nus, dts, nsteps, threads):
 def explicit_batch(u, offsets, ns, bcs, dxs, nus, dts, nsteps, threads: int = 0) -> np.ndarray:
     """Independent explicit solves of a packed batch (one thread per instance)."""
     return _run_batch(_load().or_explicit_batch, "explicit_batch", u, offsets, ns, bcs,
+                      dxs, nus, dts, nsteps, threads)
+
+
+def rk4_batch(u, offsets, ns, bcs, dxs, nus, dts, nsteps, threads: int = 0) -> np.ndarray:
+    """Independent RK4 solves of a packed batch (one thread per instance)."""
+    return _run_batch(_load().or_rk4_batch, "rk4_batch", u, offsets, ns, bcs,
                       dxs, nus, dts, nsteps, threads)
 
 

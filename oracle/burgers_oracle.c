@@ -15,6 +15,8 @@
  *                   the Laplacian), with the upwind side chosen by the sign of
  *                   u_i as Sec. 2.2 describes: backward difference for u_i > 0,
  *                   forward difference for u_i < 0.
+ *   RK4 step        Eq. 22: classical fourth-order Runge-Kutta on the spatial
+ *                   operator of Eq. 21, stage by stage.
  *   BTCS step       Sec. 2.4 / Eq. 23: all spatial terms at t^{n+1}; the
  *                   convecting velocity is lagged (one Picard linearisation per
  *                   step, coefficients from u^n) and the upwind side is chosen
@@ -254,6 +256,53 @@ int or_max_threads(void) {
 #endif
 }
 
+/* ------------------------------------------------------------------------ */
+/* Classical fourth-order Runge-Kutta in time, Eq. 22, on the semi-discrete  */
+/* operator of Eq. 21 (upwind side by the sign of u_i, Sec. 2.2):            */
+/*   F(u)_i = -(a+ (u_i - u_{i-1}) + a- (u_{i+1} - u_i))/dx                   */
+/*            + nu (u_{i+1} - 2 u_i + u_{i-1})/dx^2,     a = u_i,             */
+/* F = 0 at held Dirichlet ends.                                             */
+/*   k1 = F(u^n), k2 = F(u^n + dt/2 k1), k3 = F(u^n + dt/2 k2),              */
+/*   k4 = F(u^n + dt k3),  u^{n+1} = u^n + dt/6 (k1 + 2 k2 + 2 k3 + k4).      */
+/* ------------------------------------------------------------------------ */
+static void burgers_rhs(const double* u, double* f, int64_t n, int bc, double dx, double nu) {
+  for (int64_t i = 0; i < n; ++i) {
+    if (bc == OR_DIRICHLET && (i == 0 || i == n - 1)) {
+      f[i] = 0.0;
+      continue;
+    }
+    int64_t im = (i == 0) ? n - 1 : i - 1;
+    int64_t ip = (i == n - 1) ? 0 : i + 1;
+    double a = u[i];
+    double convection = (pos_part(a) * (u[i] - u[im]) + neg_part(a) * (u[ip] - u[i])) / dx;
+    double diffusion = nu * (u[ip] - 2.0 * u[i] + u[im]) / (dx * dx);
+    f[i] = -convection + diffusion;
+  }
+}
+
+int or_rk4(double* u, int64_t n, int bc, double dx, double nu, double dt, int64_t nsteps) {
+  if (!u || bad_common(n, bc, dx, nu, dt, nsteps)) return -1;
+  double* k1 = (double*)malloc(sizeof(double) * (size_t)n * 5);
+  if (!k1) return -2;
+  double* k2 = k1 + n;
+  double* k3 = k2 + n;
+  double* k4 = k3 + n;
+  double* w = k4 + n;
+  for (int64_t k = 0; k < nsteps; ++k) {
+    burgers_rhs(u, k1, n, bc, dx, nu);
+    for (int64_t i = 0; i < n; ++i) w[i] = u[i] + 0.5 * dt * k1[i];
+    burgers_rhs(w, k2, n, bc, dx, nu);
+    for (int64_t i = 0; i < n; ++i) w[i] = u[i] + 0.5 * dt * k2[i];
+    burgers_rhs(w, k3, n, bc, dx, nu);
+    for (int64_t i = 0; i < n; ++i) w[i] = u[i] + dt * k3[i];
+    burgers_rhs(w, k4, n, bc, dx, nu);
+    for (int64_t i = 0; i < n; ++i)
+      u[i] = u[i] + dt / 6.0 * (k1[i] + 2.0 * k2[i] + 2.0 * k3[i] + k4[i]);
+  }
+  free(k1);
+  return 0;
+}
+
 typedef int (*stepper_fn)(double*, int64_t, int, double, double, double, int64_t);
 
 static int run_batch(stepper_fn f, double* u, int64_t count, const int64_t* offset,
@@ -276,6 +325,12 @@ int or_explicit_batch(double* u, int64_t count, const int64_t* offset, const int
                       const int32_t* bc, const double* dx, const double* nu, const double* dt,
                       const int64_t* nsteps, int nthreads) {
   return run_batch(or_explicit, u, count, offset, n, bc, dx, nu, dt, nsteps, nthreads);
+}
+
+int or_rk4_batch(double* u, int64_t count, const int64_t* offset, const int32_t* n,
+                 const int32_t* bc, const double* dx, const double* nu, const double* dt,
+                 const int64_t* nsteps, int nthreads) {
+  return run_batch(or_rk4, u, count, offset, n, bc, dx, nu, dt, nsteps, nthreads);
 }
 
 int or_btcs_batch(double* u, int64_t count, const int64_t* offset, const int32_t* n,

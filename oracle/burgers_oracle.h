@@ -25,6 +25,7 @@ double or_cfl_dt(const double* u, int64_t n, double dx, double nu, double cfl);
 
 int or_explicit(double* u, int64_t n, int bc, double dx, double nu, double dt, int64_t nsteps);
 int or_btcs(double* u, int64_t n, int bc, double dx, double nu, double dt, int64_t nsteps);
+int or_rk4(double* u, int64_t n, int bc, double dx, double nu, double dt, int64_t nsteps);
 
 int or_btcs_system(const double* un, int64_t n, int bc, double r, double s,
                    double* l, double* d, double* c, double* rhs);
@@ -36,6 +37,9 @@ int or_cyclic(int64_t n, const double* l, const double* d, const double* c,
 int or_explicit_batch(double* u, int64_t count, const int64_t* offset, const int32_t* n,
                       const int32_t* bc, const double* dx, const double* nu, const double* dt,
                       const int64_t* nsteps, int nthreads);
+int or_rk4_batch(double* u, int64_t count, const int64_t* offset, const int32_t* n,
+                 const int32_t* bc, const double* dx, const double* nu, const double* dt,
+                 const int64_t* nsteps, int nthreads);
 int or_btcs_batch(double* u, int64_t count, const int64_t* offset, const int32_t* n,
                   const int32_t* bc, const double* dx, const double* nu, const double* dt,
                   const int64_t* nsteps, int nthreads);

@@ -80,7 +80,13 @@ def _periodic(n, L=2 * math.pi):
     return W.grid(n, P, 0.0, L)
 
 
-@pytest.mark.parametrize("scheme", ["explicit", "btcs"])
+def rk4_factor(z):
+    """Amplification of classical RK4 (Eq. 22) for du/dt = (z/dt) u: the
+    degree-4 Taylor polynomial of exp(z)."""
+    return 1 + z + z**2 / 2 + z**3 / 6 + z**4 / 24
+
+
+@pytest.mark.parametrize("scheme", ["explicit", "btcs", "rk4"])
 def test_small_amplitude_is_heat_equation(orc, scheme):
     n, k, eps = 64, 3, 1e-9
     x, dx = _periodic(n)
@@ -93,12 +99,15 @@ def test_small_amplitude_is_heat_equation(orc, scheme):
     u = eps * np.sin(k * x)
     out = getattr(orc, scheme)(u, P, dx, nu, dt, steps)
     sn2 = math.sin(k * dx / 2) ** 2
-    g = 1 - 4 * s * sn2 if scheme == "explicit" else 1 / (1 + 4 * s * sn2)
+    if scheme == "rk4":
+        g = rk4_factor(-4 * s * sn2)
+    else:
+        g = 1 - 4 * s * sn2 if scheme == "explicit" else 1 / (1 + 4 * s * sn2)
     expect = eps * g**steps * np.sin(k * x)
     assert np.max(np.abs(out - expect)) <= 1e-6 * eps
 
 
-@pytest.mark.parametrize("scheme", ["explicit", "btcs"])
+@pytest.mark.parametrize("scheme", ["explicit", "btcs", "rk4"])
 @pytest.mark.parametrize("c0", [0.7, -0.7])
 def test_linear_advection_upwind_side(orc, scheme, c0):
     """u = c + eps w: the perturbation obeys the linear upwind scheme whose
@@ -119,12 +128,15 @@ def test_linear_advection_upwind_side(orc, scheme, c0):
     else:
         conv = r * c0 * (e - 1)
     diff = 4 * s * math.sin(k * dx / 2) ** 2
-    g = 1 - conv - diff if scheme == "explicit" else 1 / (1 + conv + diff)
+    if scheme == "rk4":
+        g = rk4_factor(-conv - diff)
+    else:
+        g = 1 - conv - diff if scheme == "explicit" else 1 / (1 + conv + diff)
     expect = c0 + eps * np.imag(g**steps * np.exp(1j * k * x))
     assert np.max(np.abs(out - expect)) <= 2e-3 * eps
 
 
-@pytest.mark.parametrize("scheme", ["explicit", "btcs"])
+@pytest.mark.parametrize("scheme", ["explicit", "btcs", "rk4"])
 @pytest.mark.parametrize("bc", [P, D])
 def test_constant_state_is_fixed_point(orc, scheme, bc):
     n = 37
@@ -179,7 +191,7 @@ def test_explicit_beyond_cfl_oscillates(orc):
     assert np.max(np.abs(ub)) <= np.max(np.abs(u0))
 
 
-@pytest.mark.parametrize("scheme", ["explicit", "btcs"])
+@pytest.mark.parametrize("scheme", ["explicit", "btcs", "rk4"])
 def test_mirror_symmetry(orc, scheme):
     """u0(x) -> -u0(-x) maps solutions to mirrored solutions; the odd IC of
     configuration 1 stays odd: u_i = -u_{N-1-i}."""
@@ -190,7 +202,7 @@ def test_mirror_symmetry(orc, scheme):
     assert np.max(np.abs(out + out[::-1])) <= 1e-14
 
 
-@pytest.mark.parametrize("scheme", ["explicit", "btcs"])
+@pytest.mark.parametrize("scheme", ["explicit", "btcs", "rk4"])
 def test_shift_equivariance_periodic(orc, scheme):
     e = W.fourier_ensemble(1, 96, seed=11)
     u0, dx, nu = e.u0, e.dxs[0], e.nus[0]
@@ -201,7 +213,7 @@ def test_shift_equivariance_periodic(orc, scheme):
         assert np.max(np.abs(got - np.roll(base, sh))) <= 1e-13
 
 
-@pytest.mark.parametrize("scheme", ["explicit", "btcs"])
+@pytest.mark.parametrize("scheme", ["explicit", "btcs", "rk4"])
 def test_batch_matches_single(orc, scheme):
     e = W.mixed_ensemble(9, 5, 80, seed=5)
     dts = np.array([0.4 * min(e.dxs[b] / np.max(np.abs(e.row(b))), e.dxs[b] ** 2 / (2 * e.nus[b]))
@@ -286,7 +298,7 @@ def _order(errs, ns):
     return [math.log(errs[i] / errs[i + 1]) / math.log(ns[i + 1] / ns[i]) for i in range(len(ns) - 1)]
 
 
-@pytest.mark.parametrize("scheme", ["explicit", "btcs"])
+@pytest.mark.parametrize("scheme", ["explicit", "btcs", "rk4"])
 def test_first_order_convergence_to_cole_hopf(orc, scheme):
     """Smooth regime (t < shock time 1): error vs Cole-Hopf falls at order ~1
     (upwind convection + forward/backward Euler with dt ~ dx), not the O(dx^2)
@@ -306,6 +318,32 @@ def test_first_order_convergence_to_cole_hopf(orc, scheme):
         errs.append(orc.rms(u, CH.hopf(prof, x, t, nu)))
     orders = _order(errs, ns)
     assert all(0.8 <= o <= 1.25 for o in orders), (errs, orders)
+
+
+def test_rk4_is_fourth_order_in_time(orc):
+    """Eq. 22 on a fixed grid: halving dt cuts the error against a much finer
+    time step by ~2^4 (a wrong stage weight or stage offset drops the order),
+    while forward Euler on the same problem gains only ~2^1. u > 0 everywhere,
+    so the upwind side never switches and the semi-discrete operator is smooth."""
+    n, nu, t = 64, 0.05, 0.2
+    x, dx = _periodic(n)
+    u0 = 1.0 + 0.3 * np.sin(x) + 0.1 * np.cos(3 * x)
+    ref = orc.rk4(u0, P, dx, nu, t / 4096, 4096)
+    for scheme, lo, hi in (("rk4", 13.0, 19.0), ("explicit", 1.7, 2.3)):
+        errs = []
+        for steps in (64, 128, 256):
+            out = getattr(orc, scheme)(u0, P, dx, nu, t / steps, steps)
+            errs.append(np.max(np.abs(out - ref)))
+        ratios = [errs[i] / errs[i + 1] for i in range(2)]
+        assert all(lo <= q <= hi for q in ratios), (scheme, errs, ratios)
+
+
+def test_rk4_dirichlet_ends_held(orc):
+    e = W.plain_sine(64)
+    u0 = e.u0.copy()
+    u0[0], u0[-1] = 0.3, -0.2
+    out = orc.rk4(u0, D, e.dxs[0], e.nus[0], 0.004, 40)
+    assert out[0] == 0.3 and out[-1] == -0.2
 
 
 def test_inviscid_limit_converges_to_characteristics(orc):
