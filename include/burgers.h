@@ -60,7 +60,7 @@ typedef enum {
 
 typedef enum { BURGERS_F32 = 0, BURGERS_F64 = 1 } burgers_dtype;
 typedef enum { BURGERS_PERIODIC = 0, BURGERS_DIRICHLET = 1 } burgers_bc;
-typedef enum { BURGERS_EXPLICIT = 0, BURGERS_BTCS = 1 } burgers_scheme;
+typedef enum { BURGERS_EXPLICIT = 0, BURGERS_BTCS = 1, BURGERS_RK4 = 2 } burgers_scheme;
 
 /* One row of a batch (see the conventions above). */
 typedef struct {
@@ -159,6 +159,17 @@ burgers_status burgers_explicit_advance(burgers_ctx* ctx, const burgers_batch* b
 burgers_status burgers_btcs_advance(burgers_ctx* ctx, const burgers_batch* batch,
                                     void* u_dev, burgers_stream stream);
 
+/* Classical fourth-order Runge-Kutta solve (Eq. 22) on the spatial operator
+ * of Eq. 21 (upwind side by the sign of u_i, Sec. 2.2): with Delta(w) the
+ * forward-Euler increment of burgers_explicit_advance for the state w,
+ *   K1 = Delta(u), K2 = Delta(u + K1/2), K3 = Delta(u + K2/2), K4 = Delta(u + K3),
+ *   u' = u + (K1 + 2 K2 + 2 K3 + K4)/6.
+ * Dirichlet end nodes are held in every stage. In place, layout, ownership and
+ * errors as burgers_explicit_advance; no CFL check is made (RK4 is stable for
+ * the same CFL-limited dt as forward Euler). */
+burgers_status burgers_rk4_advance(burgers_ctx* ctx, const burgers_batch* batch,
+                                   void* u_dev, burgers_stream stream);
+
 /* burgers_explicit_advance for one row, without allocating device memory.
  * The paper has no counterpart: this exists for callers that cannot allocate
  * device memory while they run (an arena that already owns the GPU's memory,
@@ -177,7 +188,7 @@ burgers_status burgers_explicit_advance_noalloc(const burgers_instance* inst, in
                                                 void* u_dev, burgers_stream stream);
 
 /* End-to-end variant through host memory: copies every row from u_host to a
- * context-owned device buffer, advances it with `scheme` (burgers_scheme),
+ * context-owned device buffer, advances it with `scheme` (any burgers_scheme),
  * copies the rows back into u_host. Blocking. u_host should be pinned for
  * full copy bandwidth. */
 burgers_status burgers_solve_host(burgers_ctx* ctx, int32_t scheme, const burgers_batch* batch,

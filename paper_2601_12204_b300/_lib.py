@@ -31,6 +31,7 @@ BURGERS_PERIODIC = 0
 BURGERS_DIRICHLET = 1
 BURGERS_EXPLICIT = 0
 BURGERS_BTCS = 1
+BURGERS_RK4 = 2
 
 BURGERS_OPT_GRAPHS = 0
 BURGERS_OPT_PLAIN = 1
@@ -73,6 +74,7 @@ SIGNATURES = {
     "burgers_cfl_dt": (_ST, [_P, _P, _P, _D, _P, _P]),
     "burgers_explicit_advance": (_ST, [_P, _P, _P, _P]),
     "burgers_btcs_advance": (_ST, [_P, _P, _P, _P]),
+    "burgers_rk4_advance": (_ST, [_P, _P, _P, _P]),
     "burgers_solve_host": (_ST, [_P, _I32, _P, _P, _P]),
     "burgers_rel_l2": (_ST, [_P, _P, _P, _P, _I32, _P, _P, _P]),
     "burgers_adjoint": (_ST, [_P, _I32, _P, _P, _P, _P, _P, _I64, _P]),

@@ -130,11 +130,21 @@ class Context:
         L.check(self._lib.burgers_btcs_advance(self.h, batch.ref(), p, self._stream(stream, u)),
                 "burgers_btcs_advance")
 
+    def rk4_advance(self, batch: Batch, u, stream=None) -> None:
+        """Classical RK4 in time (Eq. 22) on the explicit step's operator."""
+        p = self._check_tensor(u, batch)
+        L.check(self._lib.burgers_rk4_advance(self.h, batch.ref(), p, self._stream(stream, u)),
+                "burgers_rk4_advance")
+
     def advance(self, scheme: int, batch: Batch, u, stream=None) -> None:
         if scheme == L.BURGERS_EXPLICIT:
             self.explicit_advance(batch, u, stream)
-        else:
+        elif scheme == L.BURGERS_RK4:
+            self.rk4_advance(batch, u, stream)
+        elif scheme == L.BURGERS_BTCS:
             self.btcs_advance(batch, u, stream)
+        else:
+            raise ValueError(f"unknown scheme {scheme}")
 
     def cfl_dt(self, batch: Batch, u, cfl: float = 0.4, stream=None) -> np.ndarray:
         p = self._check_tensor(u, batch)

@@ -19,7 +19,7 @@ import numpy as np
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--case", choices=["explicit", "btcs"], default="explicit")
+    ap.add_argument("--case", choices=["explicit", "btcs", "rk4"], default="explicit")
     ap.add_argument("--rows", type=int, default=4096)
     ap.add_argument("--n", type=int, default=4096)
     ap.add_argument("--steps", type=int, default=200)
@@ -47,9 +47,9 @@ def main():
         ctx.set(L.BURGERS_OPT_STREAM_K, a.stream_k)
     u0 = torch.tensor(ens.u0, dtype=tdt, device="cuda")
     dt = ctx.cfl_dt(Batch.from_ensemble(ens, 1.0, 0, dt_code), u0, 0.4)
-    fac = a.dt_factor if a.dt_factor is not None else (1.0 if a.case == "explicit" else 10.0)
+    fac = a.dt_factor if a.dt_factor is not None else (10.0 if a.case == "btcs" else 1.0)
     b = Batch.from_ensemble(ens, dt * fac, a.steps, dt_code)
-    scheme = L.BURGERS_EXPLICIT if a.case == "explicit" else L.BURGERS_BTCS
+    scheme = {"explicit": L.BURGERS_EXPLICIT, "btcs": L.BURGERS_BTCS, "rk4": L.BURGERS_RK4}[a.case]
     if a.tune_file and os.path.exists(a.tune_file):
         ctx.tune_load(a.tune_file)
     elif a.autotune:

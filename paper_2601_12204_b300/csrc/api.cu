@@ -89,7 +89,14 @@ static const std::vector<Shape>& resident_shapes(int kind, int dtype) {
                                           {512, 8},  {128, 32}, {512, 16}, {1024, 8}, {256, 32}};
   static const std::vector<Shape> bt64 = {{32, 1},  {32, 2},  {32, 4},   {32, 8},   {64, 8},
                                           {128, 8}, {256, 8}, {128, 16}, {512, 8}, {256, 16}};
+  static const std::vector<Shape> rk32 = {{32, 1},   {32, 2},  {32, 4},   {32, 8},  {64, 8},
+                                          {128, 8},  {64, 16}, {128, 16}, {256, 8}, {256, 16},
+                                          {512, 8},  {512, 16}};
+  static const std::vector<Shape> rk64 = {{32, 1},  {32, 2},   {32, 4},   {32, 8},  {64, 8},
+                                          {128, 4}, {128, 8},  {256, 4},  {256, 8}, {512, 4},
+                                          {512, 8}, {1024, 4}};
   if (kind == K_EXPLICIT_RESIDENT) return dtype == 0 ? ex32 : ex64;
+  if (kind == K_RK4_RESIDENT) return dtype == 0 ? rk32 : rk64;
   return dtype == 0 ? bt32 : bt64;
 }
 
@@ -220,25 +227,30 @@ static int blocks_per_sm(const KernelEntry* k) {
   return b;
 }
 
-// Streaming shape for a long explicit row: the largest registered window that
-// fits the row, with K = min(requested, W/4).
-static bool pick_stream(const burgers_ctx* ctx, int dtype, int64_t n_min, Shape* sh, int* K) {
+// Streaming shape for a long explicit (kind K_EXPLICIT_STREAM) or RK4
+// (K_RK4_STREAM) row: the largest registered window that fits the row, with K
+// steps per pass such that the stale edges (K nodes per side, 4K for RK4)
+// take at most a quarter of the window.
+static bool pick_stream(const burgers_ctx* ctx, int kind, int dtype, int64_t n_min, Shape* sh,
+                        int* K) {
   static const Shape s32[] = {{256, 16}, {128, 16}, {32, 4}};
   static const Shape s64[] = {{256, 8}, {128, 8}, {32, 4}};
   const Shape* list = dtype == 0 ? s32 : s64;
-  auto it = ctx->tuned.find(tune_key(K_EXPLICIT_STREAM, dtype, 0, 0));
+  const int per_step = kind == K_RK4_STREAM ? 4 : 1;
+  auto it = ctx->tuned.find(tune_key(kind, dtype, 0, 0));
   if (ctx->stream_k == 0 && it != ctx->tuned.end() &&
       int64_t(it->second.nt) * it->second.c <= n_min) {
     *sh = Shape{it->second.nt, it->second.c};
-    *K = int(std::min<int64_t>(it->second.k, int64_t(sh->nt) * sh->c / 4));
+    *K = int(std::max<int64_t>(1, std::min<int64_t>(it->second.k, int64_t(sh->nt) * sh->c /
+                                                                      (4 * per_step))));
     return true;
   }
   for (int i = 0; i < 3; ++i) {
     int64_t W = int64_t(list[i].nt) * list[i].c;
     if (W <= n_min) {
       *sh = list[i];
-      int k = ctx->stream_k > 0 ? ctx->stream_k : (dtype == 0 ? 32 : 16);
-      *K = int(std::min<int64_t>(k, W / 4));
+      int k = ctx->stream_k > 0 ? ctx->stream_k : (dtype == 0 ? 32 : 16) / per_step;
+      *K = int(std::max<int64_t>(1, std::min<int64_t>(k, W / (4 * per_step))));
       return true;
     }
   }
@@ -251,7 +263,8 @@ static burgers_status build_plan(burgers_ctx* ctx, int scheme, const burgers_bat
   const int dtype = batch->dtype;
   p->dtype = dtype;
   p->scheme = scheme;
-  const int rkind = scheme == BURGERS_EXPLICIT ? K_EXPLICIT_RESIDENT : K_BTCS_RESIDENT;
+  const int rkind = resident_kind(scheme);
+  const bool stencil = scheme != BURGERS_BTCS;  // explicit Euler or RK4
   const int64_t rlim = resident_limit(ctx, rkind, dtype);
   struct Grp {
     Shape sh;
@@ -265,7 +278,7 @@ static burgers_status build_plan(burgers_ctx* ctx, int scheme, const burgers_bat
     if (in.nsteps == 0) continue;
     // long rows: streaming explicit windows / multi-level BTCS (which needs at
     // least a few chunks; shorter rows stay resident whatever the limit)
-    const int64_t min_long = scheme == BURGERS_EXPLICIT ? 128 : 64;
+    const int64_t min_long = stencil ? 128 : 64;
     if (in.n > rlim && in.n >= min_long && in.n > 0) {
       longs.push_back(b);
       continue;
@@ -314,7 +327,8 @@ static burgers_status build_plan(burgers_ctx* ctx, int scheme, const burgers_bat
     }
   }
   if (!longs.empty()) {
-    if (scheme == BURGERS_EXPLICIT) {
+    if (stencil) {
+      const int skind = scheme == BURGERS_RK4 ? K_RK4_STREAM : K_EXPLICIT_STREAM;
       int64_t nmin = INT64_MAX, smax = 0, span = 0;
       for (int64_t b : longs) {
         nmin = std::min<int64_t>(nmin, batch->inst[b].n);
@@ -323,17 +337,19 @@ static burgers_status build_plan(burgers_ctx* ctx, int scheme, const burgers_bat
       }
       Shape sh;
       int K;
-      if (!pick_stream(ctx, dtype, nmin, &sh, &K))
+      if (!pick_stream(ctx, skind, dtype, nmin, &sh, &K))
         return set_error(BURGERS_EINVAL, "row too short for the streaming kernel");
       const KernelEntry* k = nullptr;
-      if (K == 1) {  // one step per pass: the bandwidth-bound single-step kernel
+      const bool step1 = K == 1 && scheme == BURGERS_EXPLICIT;
+      if (step1) {  // one Euler step per pass: the bandwidth-bound single-step kernel
         k = find_kernel(K_EXPLICIT_STEP1, dtype, 256, dtype == 0 ? 8 : 4, 0);
         sh = Shape{256, dtype == 0 ? 8 : 4};
       } else {
-        k = find_kernel(K_EXPLICIT_STREAM, dtype, sh.nt, sh.c, 0);
+        k = find_kernel(skind, dtype, sh.nt, sh.c, 0);
       }
       if (!k) return set_error(BURGERS_EINVAL, "streaming shape not instantiated");
-      const int64_t W = int64_t(sh.nt) * sh.c, O = K == 1 ? W : W - 2 * K;
+      const int64_t H = int64_t(K) * (scheme == BURGERS_RK4 ? 4 : 1);  // stale nodes per side
+      const int64_t W = int64_t(sh.nt) * sh.c, O = step1 ? W : W - 2 * H;
       int rbegin = int(p->rows.size());
       int ibegin = int(p->items.size());
       for (size_t q = 0; q < longs.size(); ++q) {
@@ -346,8 +362,8 @@ static burgers_status build_plan(burgers_ctx* ctx, int scheme, const burgers_bat
       int nitems = int(p->items.size()) - ibegin;
       // the single-step kernel streams: one CTA per tile lets the scheduler
       // overlap the tiles' memory traffic
-      int grid = K == 1 ? std::min(nitems, 1 << 20)
-                        : std::min(nitems, ctx->sm_count * blocks_per_sm(k));
+      int grid = step1 ? std::min(nitems, 1 << 20)
+                       : std::min(nitems, ctx->sm_count * blocks_per_sm(k));
       int64_t passes = (smax + K - 1) / K;
       for (int64_t ps = 0; ps < passes; ++ps) {
         Launch L;
@@ -667,6 +683,11 @@ burgers_status burgers_btcs_advance(burgers_ctx* ctx, const burgers_batch* batch
   return advance(ctx, BURGERS_BTCS, batch, u_dev, reinterpret_cast<cudaStream_t>(stream));
 }
 
+burgers_status burgers_rk4_advance(burgers_ctx* ctx, const burgers_batch* batch, void* u_dev,
+                                   burgers_stream stream) {
+  return advance(ctx, BURGERS_RK4, batch, u_dev, reinterpret_cast<cudaStream_t>(stream));
+}
+
 burgers_status burgers_adjoint(burgers_ctx* ctx, int32_t scheme, const burgers_batch* batch,
                                const void* u0_dev, const void* gT_dev, void* gu0_dev,
                                double* gnu_dev, int64_t ckpt_stride, burgers_stream stream) {
@@ -848,7 +869,8 @@ burgers_status burgers_cfl_dt(burgers_ctx* ctx, const burgers_batch* batch, cons
 burgers_status burgers_solve_host(burgers_ctx* ctx, int32_t scheme, const burgers_batch* batch,
                                   void* u_host, burgers_stream stream) {
   if (!ctx) return set_error(BURGERS_EINVAL, "ctx is NULL");
-  if (scheme != BURGERS_EXPLICIT && scheme != BURGERS_BTCS) return set_error(BURGERS_EINVAL, "bad scheme");
+  if (scheme != BURGERS_EXPLICIT && scheme != BURGERS_BTCS && scheme != BURGERS_RK4)
+    return set_error(BURGERS_EINVAL, "bad scheme");
   burgers_status st = validate_batch(batch, false);
   if (st != BURGERS_OK) return st;
   if (batch->count == 0) return BURGERS_OK;

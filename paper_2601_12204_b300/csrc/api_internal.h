@@ -130,6 +130,12 @@ burgers_status plan_multilevel(burgers_ctx* ctx, const burgers_batch* batch,
                                const std::vector<int64_t>& longs, Plan* p);
 cudaError_t enqueue_multilevel_launch(burgers_ctx* ctx, Plan* p, const Launch& L, void* u,
                                       cudaStream_t st);
+// Resident kernel kind of a scheme (burgers_scheme).
+inline int resident_kind(int scheme) {
+  return scheme == BURGERS_EXPLICIT ? K_EXPLICIT_RESIDENT
+                                    : (scheme == BURGERS_RK4 ? K_RK4_RESIDENT : K_BTCS_RESIDENT);
+}
+
 burgers_status advance(burgers_ctx* ctx, int scheme, const burgers_batch* batch, void* u_dev,
                        cudaStream_t stream);
 burgers_status advance_uncached(burgers_ctx* ctx, int scheme, const burgers_batch* batch,

@@ -23,14 +23,8 @@
 namespace burgers {
 
 enum : int { MODE_EXACT = 0, MODE_RAGGED = 1, MODE_WINDOW = 2, MODE_WINDOW_DIR = 3 };
+enum : int { INTEG_EULER = 0, INTEG_RK4 = 1 };
 
-// Advances the C nodes held by this thread `nsteps` steps.
-//   MODE_EXACT      row length n == NT*C; periodic wrap through the halo slots.
-//   MODE_RAGGED     n < NT*C; nodes >= n are inert padding, the periodic wrap
-//                   pairs node 0 with node n-1 explicitly.
-//   MODE_WINDOW     streaming window; its two edges go stale one node per step.
-//   MODE_WINDOW_DIR streaming window that contains a Dirichlet end node.
-// gbase is the row index of this thread's first node.
 // Exchanges this thread's edge values for its neighbours' (left = value of
 // the node before its first, right = after its last). Periodic rows wrap
 // through the slots of the first and last warp; WRAPX rows (ragged periodic)
@@ -143,6 +137,99 @@ __device__ __forceinline__ void explicit_steps_split(float (&v)[C], float (&lo)[
   for (int j = 0; j < C; ++j) lo[j] = -lo[j];
 }
 
+// Classical fourth-order Runge-Kutta in time (Eq. 22) on the same spatial
+// operator. With Delta(w) the forward-Euler increment of the state w for the
+// whole dt (p (w_r - w) - q (w - w_l), as above), a step is
+//   K1 = Delta(u), K2 = Delta(u + K1/2), K3 = Delta(u + K2/2), K4 = Delta(u + K3),
+//   u' = u + (K1 + 2 K2 + 2 K3 + K4)/6,
+// i.e. Eq. 22 with k_j = K_j/dt. Every stage needs its own neighbour exchange.
+// Held nodes (Dirichlet ends, padding) have zero increments in every stage.
+// FP32 keeps the split state of explicit_steps_split (the stage states are
+// evaluated from it; the step's combined increment goes into d); FP64 adds the
+// combined increment to u directly.
+template <typename T, int NT, int C, int MODE, int BCT>
+__device__ __forceinline__ void rk4_steps(T (&v)[C], T (&lo)[C], int64_t nsteps, T r, T h, T s,
+                                          int n, int64_t gbase, T* sh_last, T* sh_first,
+                                          T* sh_wrap) {
+  constexpr bool SPLIT = Kahan<T>::on;
+  constexpr bool WRAPX = (MODE == MODE_RAGGED && BCT == BC_PERIODIC);
+  const int tid = threadIdx.x;
+  const int jstar = int(n - 1 - gbase);
+  if constexpr (SPLIT) {
+#pragma unroll
+    for (int j = 0; j < C; ++j) lo[j] = -lo[j];  // lo becomes d
+  }
+  T K[C], acc[C];
+#pragma unroll
+  for (int j = 0; j < C; ++j) K[j] = T(0);
+  for (int64_t k = 0; k < nsteps; ++k) {
+#pragma unroll
+    for (int st = 0; st < 4; ++st) {
+      const T cst = st == 0 ? T(0) : (st == 3 ? T(1) : T(0.5));
+      // state of this stage at node j: u + cst * K_prev
+      auto wv = [&](int j) -> T {
+        T u = v[j];
+        if constexpr (SPLIT) u = v[j] + lo[j];
+        return st == 0 ? u : tfma(cst, K[j], u);
+      };
+      const T first = wv(0), last = wv(C - 1);
+      T wsel = T(0);
+      bool has_wrap = false;
+      if constexpr (WRAPX) {
+        has_wrap = jstar >= 0 && jstar < C;
+        T sv = v[0], sd = lo[0], sk = K[0];
+#pragma unroll
+        for (int j = 1; j < C; ++j)
+          if (j == jstar) { sv = v[j]; sd = lo[j]; sk = K[j]; }
+        T su = sv;
+        if constexpr (SPLIT) su = sv + sd;
+        wsel = st == 0 ? su : tfma(cst, sk, su);
+      }
+      T left, right, wrapL = T(0), wrapR = T(0);
+      halo_exchange<T, NT, WRAPX>(first, last, wsel, has_wrap, st & 1, sh_last, sh_first,
+                                  sh_wrap, left, right, wrapL, wrapR);
+      T wl = left, wc = first;
+      if constexpr (WRAPX) {
+        if (tid == 0) wl = wrapL;
+      }
+#pragma unroll
+      for (int j = 0; j < C; ++j) {
+        T wr = (j + 1 < C) ? wv(j + 1) : right;
+        if constexpr (WRAPX) {
+          if (j == jstar) wr = wrapR;
+        }
+        T kn = explicit_increment(wc, wl, wr, r, h, s, T(0));
+        if (keep_node<NT, C, MODE, BCT>(j, jstar, gbase, n)) kn = T(0);
+        if (st == 0) acc[j] = kn;
+        else acc[j] = tfma((st == 3) ? T(1) : T(2), kn, acc[j]);
+        K[j] = kn;
+        wl = wc;
+        wc = wr;
+      }
+    }
+    const T sixth = T(1) / T(6);
+    if constexpr (SPLIT) {
+#pragma unroll
+      for (int j = 0; j < C; ++j) lo[j] = tfma(sixth, acc[j], lo[j]);
+      if (((k + 1) & (SPLIT_FOLD - 1)) == 0 || k + 1 == nsteps) {
+#pragma unroll
+        for (int j = 0; j < C; ++j) {
+          const T t = v[j] + lo[j];
+          lo[j] = lo[j] - (t - v[j]);
+          v[j] = t;
+        }
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < C; ++j) v[j] = tfma(sixth, acc[j], v[j]);
+    }
+  }
+  if constexpr (SPLIT) {
+#pragma unroll
+    for (int j = 0; j < C; ++j) lo[j] = -lo[j];
+  }
+}
+
 // Advances the C nodes held by this thread `nsteps` steps.
 //   MODE_EXACT      row length n == NT*C; periodic wrap through the halo slots.
 //   MODE_RAGGED     n < NT*C; nodes >= n are inert padding, the periodic wrap
@@ -150,12 +237,15 @@ __device__ __forceinline__ void explicit_steps_split(float (&v)[C], float (&lo)[
 //   MODE_WINDOW     streaming window; its two edges go stale one node per step.
 //   MODE_WINDOW_DIR streaming window that contains a Dirichlet end node.
 // gbase is the row index of this thread's first node. FP32 runs the split
-// state above; FP64 updates the values in place.
-template <typename T, int NT, int C, int MODE, int BCT>
+// state above; FP64 updates the values in place. INTEG selects forward Euler
+// (Eq. 21) or RK4 (Eq. 22).
+template <typename T, int NT, int C, int MODE, int BCT, int INTEG = INTEG_EULER>
 __device__ __forceinline__ void explicit_steps(T (&v)[C], T (&lo)[C], int64_t nsteps, T r, T h, T s,
                                                int n, int64_t gbase, T* sh_last, T* sh_first,
                                                T* sh_wrap) {
-  if constexpr (Kahan<T>::on) {
+  if constexpr (INTEG == INTEG_RK4) {
+    rk4_steps<T, NT, C, MODE, BCT>(v, lo, nsteps, r, h, s, n, gbase, sh_last, sh_first, sh_wrap);
+  } else if constexpr (Kahan<T>::on) {
     explicit_steps_split<NT, C, MODE, BCT>(v, lo, nsteps, r, h, s, n, gbase, sh_last, sh_first,
                                            sh_wrap);
   } else {
@@ -196,7 +286,7 @@ __device__ __forceinline__ void explicit_steps(T (&v)[C], T (&lo)[C], int64_t ns
   }
 }
 
-template <typename T, int NT, int C, bool EXACT>
+template <typename T, int NT, int C, bool EXACT, int INTEG = INTEG_EULER>
 __global__ void __launch_bounds__(NT) k_explicit_resident(T* __restrict__ u,
                                                           const RowDesc* __restrict__ rows,
                                                           int count, int* __restrict__ counter) {
@@ -220,11 +310,11 @@ __global__ void __launch_bounds__(NT) k_explicit_resident(T* __restrict__ u,
     const T r = T(rd.r), h = T(0.5 * rd.r), s = T(rd.s);
     constexpr int M = EXACT ? MODE_EXACT : MODE_RAGGED;
     if (rd.bc == BC_PERIODIC)
-      explicit_steps<T, NT, C, M, BC_PERIODIC>(v, lo, rd.nsteps, r, h, s, rd.n, base, sh_last,
-                                               sh_first, sh_wrap);
+      explicit_steps<T, NT, C, M, BC_PERIODIC, INTEG>(v, lo, rd.nsteps, r, h, s, rd.n, base,
+                                                      sh_last, sh_first, sh_wrap);
     else
-      explicit_steps<T, NT, C, M, BC_DIRICHLET>(v, lo, rd.nsteps, r, h, s, rd.n, base, sh_last,
-                                                sh_first, sh_wrap);
+      explicit_steps<T, NT, C, M, BC_DIRICHLET, INTEG>(v, lo, rd.nsteps, r, h, s, rd.n, base,
+                                                       sh_last, sh_first, sh_wrap);
 #pragma unroll
     for (int j = 0; j < C; ++j)
       if (EXACT || base + j < rd.n) row[base + j] = v[j];
@@ -269,7 +359,7 @@ __device__ __forceinline__ int skew32(int i) { return i + (i >> 5); }
 // carry the Kahan compensation term through lo_src / lo_dst (same layout as
 // the rows); FP64 passes get null pointers. Results leave through a skewed
 // shared-memory stage so the stores of the W - 2K output nodes are coalesced.
-template <typename T, int NT, int C>
+template <typename T, int NT, int C, int INTEG = INTEG_EULER>
 __global__ void __launch_bounds__(NT) k_explicit_stream(const T* __restrict__ src,
                                                         T* __restrict__ dst,
                                                         const T* __restrict__ lo_src,
@@ -284,7 +374,9 @@ __global__ void __launch_bounds__(NT) k_explicit_stream(const T* __restrict__ sr
   T* stage = reinterpret_cast<T*>(dsm);   // WS values
   T* stage_lo = stage + WS;                 // WS values (FP32 only)
   __shared__ T sh_last[2 * NW], sh_first[2 * NW], sh_wrap[4];
-  const int O = W - 2 * K;
+  // each step (each RK4 stage) makes one more node per side stale
+  const int H = K * (INTEG == INTEG_RK4 ? 4 : 1);
+  const int O = W - 2 * H;
   const int base = threadIdx.x * C;
   for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
     const TileItem ti = items[it];
@@ -292,7 +384,7 @@ __global__ void __launch_bounds__(NT) k_explicit_stream(const T* __restrict__ sr
     const int64_t n = rd.n;
     const int64_t out_lo = int64_t(ti.tile) * O;
     const int64_t out_hi = min(out_lo + O, n);
-    const int64_t ws = out_lo - K;
+    const int64_t ws = out_lo - H;
     const int64_t rem = rd.nsteps - step_base;
     const int kk = rem <= 0 ? 0 : (rem < K ? int(rem) : K);
     const T* srow = src + rd.offset;
@@ -336,11 +428,12 @@ __global__ void __launch_bounds__(NT) k_explicit_stream(const T* __restrict__ sr
     const bool has_end = rd.bc == BC_DIRICHLET && ((ws <= 0 && ws + W > 0) ||
                                                    (ws <= n - 1 && ws + W > n - 1));
     if (has_end)
-      explicit_steps<T, NT, C, MODE_WINDOW_DIR, BC_DIRICHLET>(v, lo, kk, r, h, s, int(n), g0,
-                                                              sh_last, sh_first, sh_wrap);
+      explicit_steps<T, NT, C, MODE_WINDOW_DIR, BC_DIRICHLET, INTEG>(v, lo, kk, r, h, s, int(n),
+                                                                     g0, sh_last, sh_first,
+                                                                     sh_wrap);
     else
-      explicit_steps<T, NT, C, MODE_WINDOW, BC_PERIODIC>(v, lo, kk, r, h, s, int(n), g0, sh_last,
-                                                         sh_first, sh_wrap);
+      explicit_steps<T, NT, C, MODE_WINDOW, BC_PERIODIC, INTEG>(v, lo, kk, r, h, s, int(n), g0,
+                                                                sh_last, sh_first, sh_wrap);
 #pragma unroll
     for (int j = 0; j < C; ++j) {
       stage[skew32(base + j)] = v[j];
@@ -350,8 +443,8 @@ __global__ void __launch_bounds__(NT) k_explicit_stream(const T* __restrict__ sr
     for (int i = threadIdx.x; i < O; i += NT) {
       const int64_t gi = out_lo + i;
       if (gi < out_hi) {
-        drow[gi] = stage[skew32(K + i)];
-        if constexpr (Kahan<T>::on) lo_dst[rd.offset + gi] = stage_lo[skew32(K + i)];
+        drow[gi] = stage[skew32(H + i)];
+        if constexpr (Kahan<T>::on) lo_dst[rd.offset + gi] = stage_lo[skew32(H + i)];
       }
     }
     __syncthreads();
@@ -470,6 +563,19 @@ __global__ void __launch_bounds__(NT) k_explicit_step1(const T* __restrict__ src
                  reinterpret_cast<const void*>(&k_explicit_resident<T, NT, C, true>), 0});  \
   reg.push_back({K_EXPLICIT_RESIDENT, DT, NT, C, 0,                                         \
                  reinterpret_cast<const void*>(&k_explicit_resident<T, NT, C, false>), 0});
+#define REG_RK4(T, DT, NT, C)                                                               \
+  reg.push_back({K_RK4_RESIDENT, DT, NT, C, 1,                                              \
+                 reinterpret_cast<const void*>(                                             \
+                     &k_explicit_resident<T, NT, C, true, INTEG_RK4>),                      \
+                 0});                                                                       \
+  reg.push_back({K_RK4_RESIDENT, DT, NT, C, 0,                                              \
+                 reinterpret_cast<const void*>(                                             \
+                     &k_explicit_resident<T, NT, C, false, INTEG_RK4>),                     \
+                 0});
+#define REG_RK4_STREAM(T, DT, NT, C)                                                        \
+  reg.push_back({K_RK4_STREAM, DT, NT, C, 0,                                               \
+                 reinterpret_cast<const void*>(&k_explicit_stream<T, NT, C, INTEG_RK4>),  \
+                 sizeof(T) * size_t(NT * C + NT * C / 32) * (Kahan<T>::on ? 2 : 1)});
 #define REG_STREAM(T, DT, NT, C)                                                            \
   reg.push_back({K_EXPLICIT_STREAM, DT, NT, C, 0,                                          \
                  reinterpret_cast<const void*>(&k_explicit_stream<T, NT, C>),             \
@@ -493,6 +599,19 @@ void register_explicit(std::vector<KernelEntry>& reg) {
   REG_STREAM(float, 0, 512, 16) REG_STREAM(float, 0, 256, 32)
   REG_STREAM(double, 1, 32, 4) REG_STREAM(double, 1, 128, 8) REG_STREAM(double, 1, 256, 8)
   REG_STREAM(double, 1, 256, 16)
+  // RK4 (Eq. 22): resident and streaming shapes
+  REG_RK4(float, 0, 32, 1) REG_RK4(float, 0, 32, 2) REG_RK4(float, 0, 32, 4)
+  REG_RK4(float, 0, 32, 8) REG_RK4(float, 0, 64, 8) REG_RK4(float, 0, 128, 8)
+  REG_RK4(float, 0, 64, 16) REG_RK4(float, 0, 128, 16) REG_RK4(float, 0, 256, 8)
+  REG_RK4(float, 0, 256, 16) REG_RK4(float, 0, 512, 8) REG_RK4(float, 0, 512, 16)
+  REG_RK4(double, 1, 32, 1) REG_RK4(double, 1, 32, 2) REG_RK4(double, 1, 32, 4)
+  REG_RK4(double, 1, 32, 8) REG_RK4(double, 1, 64, 8) REG_RK4(double, 1, 128, 8)
+  REG_RK4(double, 1, 256, 8) REG_RK4(double, 1, 512, 8) REG_RK4(double, 1, 128, 4)
+  REG_RK4(double, 1, 256, 4) REG_RK4(double, 1, 512, 4) REG_RK4(double, 1, 1024, 4)
+  REG_RK4_STREAM(float, 0, 32, 4) REG_RK4_STREAM(float, 0, 128, 16)
+  REG_RK4_STREAM(float, 0, 256, 16)
+  REG_RK4_STREAM(double, 1, 32, 4) REG_RK4_STREAM(double, 1, 128, 8)
+  REG_RK4_STREAM(double, 1, 256, 8)
   // one step per pass
   reg.push_back({K_EXPLICIT_STEP1, 0, 256, 8, 0,
                  reinterpret_cast<const void*>(&k_explicit_step1<float, 256, 8>), 0});

@@ -24,6 +24,8 @@ enum KernelKind : int32_t {
   K_ADJ_EXPLICIT = 6,       // adjoint of the explicit solve (resident rows)
   K_ADJ_BTCS = 7,           // adjoint of the BTCS solve (resident rows)
   K_EXPLICIT_STEP1 = 8,     // one explicit step per HBM pass over tiles of long rows
+  K_RK4_RESIDENT = 9,       // RK4 (Eq. 22), whole row in registers
+  K_RK4_STREAM = 10,        // RK4 window of a long row, K steps per HBM pass
   K_KIND_COUNT
 };
 

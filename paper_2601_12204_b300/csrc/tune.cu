@@ -82,7 +82,7 @@ burgers_status autotune(burgers_ctx* ctx, int scheme, const burgers_batch* batch
                         int* tuned_out) {
   const int dtype = batch->dtype;
   const size_t esz = dtype == 0 ? 4 : 8;
-  const int kind = scheme == BURGERS_EXPLICIT ? K_EXPLICIT_RESIDENT : K_BTCS_RESIDENT;
+  const int kind = resident_kind(scheme);
   const int64_t rlim = resident_capacity(ctx, kind, dtype);
   // capacity classes of the resident rows
   std::map<std::pair<int64_t, int>, std::vector<int64_t>> classes;
@@ -251,7 +251,8 @@ burgers_status burgers_autotune(burgers_ctx* ctx, int32_t scheme, const burgers_
                                 burgers_stream stream) {
   using namespace burgers;
   if (!ctx) return set_error(BURGERS_EINVAL, "ctx is NULL");
-  if (scheme != BURGERS_EXPLICIT && scheme != BURGERS_BTCS) return set_error(BURGERS_EINVAL, "bad scheme");
+  if (scheme != BURGERS_EXPLICIT && scheme != BURGERS_BTCS && scheme != BURGERS_RK4)
+    return set_error(BURGERS_EINVAL, "bad scheme");
   if (probe_steps < 1) return set_error(BURGERS_EINVAL, "probe_steps must be >= 1");
   burgers_status st = validate_batch(batch, false);
   if (st != BURGERS_OK) return st;

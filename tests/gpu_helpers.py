@@ -6,7 +6,7 @@ import oracle
 from paper_2601_12204_b300 import _lib as L
 from paper_2601_12204_b300.api import Batch
 
-EXPLICIT, BTCS = L.BURGERS_EXPLICIT, L.BURGERS_BTCS
+EXPLICIT, BTCS, RK4 = L.BURGERS_EXPLICIT, L.BURGERS_BTCS, L.BURGERS_RK4
 F32, F64 = L.BURGERS_F32, L.BURGERS_F64
 
 # Parity bars. FP64: relative L2 <= 1e-12 per row; elementwise |gpu - oracle|
@@ -34,7 +34,7 @@ def run_gpu(ctx, scheme, ens, dts, nsteps, dtype, u0=None):
 
 
 def run_oracle(scheme, ens, dts, nsteps, threads=0):
-    f = oracle.explicit_batch if scheme == EXPLICIT else oracle.btcs_batch
+    f = {EXPLICIT: oracle.explicit_batch, BTCS: oracle.btcs_batch, RK4: oracle.rk4_batch}[scheme]
     steps = np.broadcast_to(np.asarray(nsteps, dtype=np.int64), (ens.count,))
     return f(ens.u0, ens.offsets, ens.ns, ens.bcs, ens.dxs, ens.nus, dts, steps, threads)
 
