@@ -215,8 +215,11 @@ __device__ __forceinline__ void btcs_steps(int64_t nsteps, T r, T s, int n, Btcs
   }
 }
 
+// FP32: at most 128 registers per thread, so 512 threads' worth of CTAs fit
+// on an SM (four CTAs of the 128 x 32 shape hide each other's serial phase).
 template <typename T, int NT, int C, bool EXACT>
-__global__ void __launch_bounds__(NT) k_btcs_resident(T* __restrict__ u,
+__global__ void __launch_bounds__(NT, (sizeof(T) == 4 && NT <= 512) ? 512 / NT : 1)
+    k_btcs_resident(T* __restrict__ u,
                                                       const RowDesc* __restrict__ rows, int count,
                                                       int* __restrict__ counter) {
   __shared__ BtcsShared<T, NT> sm;

@@ -129,8 +129,8 @@ __device__ __forceinline__ void reduced_solve(BtcsShared<T, NT>& sm, int tl, int
     T fac = T(0);
     if (lane == 0) {
       const double fd = double(fa);
-      const double vy = double(sm.X[sk(0)]) + fd * double(sm.X[sk(tl)]);
-      const double vz = double(sm.Z[sk(0)]) + fd * double(sm.Z[sk(tl)]);
+      const double vy = fma(fd, double(sm.X[sk(tl)]), double(sm.X[sk(0)]));
+      const double vz = fma(fd, double(sm.Z[sk(tl)]), double(sm.Z[sk(0)]));
       fac = T(vy / (1.0 + vz));
     }
     fac = shfl(fac, 0);
