@@ -47,6 +47,14 @@ EXPLICIT_OPS = 7 + 3 / 32
 # BTCS: assembly 4 + right-hand side 3 + forward elimination 6 (+1 MUFU rcp) +
 # backward 3 + back-substitution 2 + compensated addition 4 (+2 min/max on ALU)
 BTCS_OPS = 22
+LARGE_EXPLICIT_STEPS, LARGE_BTCS_STEPS = 10000, 100
+# RK4 (Eq. 22) on the bench ensemble at the forward-Euler dt. FMA-pipe FP32
+# lane-instructions per cell-update: u = uh + d once per step (1) and the first
+# stage's increment (6); stages 2-4 add the stage offset (1), the increment (6)
+# and the weighted accumulation (1); the step adds the sum/6 to d (1); every 32
+# steps a three-operation fold.
+RK4_STEPS = 500
+RK4_OPS = 7 + 3 * 8 + 1 + 3 / 32
 SMS, FP32_LANES = 148, 128
 
 
@@ -420,6 +428,41 @@ def extras(args, ctx, ens, u0, batches, probe, dev, world, rank):
     out["fp64"] = fp64
     del u64
 
+    # ---- RK4 (Eq. 22) on the same ensemble and dt: throughput, roofline of the
+    # resident kernel, FP32 against FP64
+    br = Batch.from_ensemble(ens, dt0, RK4_STEPS, F32)
+    ctx.autotune(L.BURGERS_RK4, br, u0, probe_steps=50)
+    w = u0.clone()
+    ctx.rk4_advance(br, w)  # warm
+    torch.cuda.synchronize()
+    w.copy_(u0)
+    a, z = ev(), ev()
+    a.record(stream)
+    ctx.rk4_advance(br, w)
+    z.record(stream)
+    torch.cuda.synchronize()
+    t_rk = a.elapsed_time(z) / 1000.0
+    w64 = torch.tensor(ens.u0, dtype=torch.float64, device=dev)
+    a, z = ev(), ev()
+    a.record(stream)
+    ctx.rk4_advance(br.with_fields(dtype=F64), w64)
+    z.record(stream)
+    torch.cuda.synchronize()
+    t_rk64 = a.elapsed_time(z) / 1000.0
+    rel, _ = ctx.rel_l2(br, w, w64)
+    cells = float(B_ROWS) * N_NODES * RK4_STEPS
+    ach = RK4_OPS * cells / t_rk / 1e12
+    peak_ops = SMS * FP32_LANES * 2032e6 / 1e12
+    out["rk4"] = {"steps": RK4_STEPS, "cups": cells / t_rk, "fp64_cups": cells / t_rk64,
+                  "l2_fp32_vs_fp64": {"max": float(np.max(rel)), "median": float(np.median(rel))},
+                  "roofline": {"bound": "alu", "kernel": "k_explicit_resident<float, tuned shape, "
+                                                          "exact, RK4>",
+                               "achieved": ach, "peak": peak_ops,
+                               "unit": "Tops/s (FP32 lane-instructions)",
+                               "frac": ach / peak_ops,
+                               "per_unit": f"{RK4_OPS:.4g} FMA-pipe FP32 instr per cell-update"}}
+    del w, w64
+
     # ---- plain one-row-per-launch path on a subset, same kernels
     P = 64
     sub = Batch(F32, ens.offsets[:P], N_NODES, 0, ens.dxs[:P], ens.nus[:P], dt0[:P], EXPLICIT_STEPS)
@@ -465,42 +508,66 @@ def extras(args, ctx, ens, u0, batches, probe, dev, world, rank):
                           "buffers; dt from the device CFL reduction of the same inputs"}
     del ha, hb, hu0
 
-    # ---- large single grid (N = 2^24, periodic): streaming explicit
+    # ---- large single grid (N = 2^24, periodic): streaming explicit, multi-level BTCS,
+    # FP32 against FP64 on the same device
     lg = W.large_grid(1 << 24)
+    nlg = float(lg.ns[0])
     ul = torch.tensor(lg.u0, dtype=torch.float32, device=dev)
+    ul64 = torch.tensor(lg.u0, dtype=torch.float64, device=dev)
     pb = Batch.from_ensemble(lg, 1.0, 0, F32)
     dtl = ctx.cfl_dt(pb, ul, CFL)
     large = {}
-    for K, steps in ((0, 10000), (1, 200)):
-        ctx.set(L.BURGERS_OPT_STREAM_K, K)
-        bl = Batch.from_ensemble(lg, dtl, steps, F32)
-        w = ul.clone()
-        ctx.explicit_advance(bl, w)  # warm (graph capture)
+
+    def timed(scheme, batch, src):
+        w = src.clone()
+        adv = ctx.explicit_advance if scheme == L.BURGERS_EXPLICIT else ctx.btcs_advance
+        adv(batch, w)  # warm (plan, graph capture)
         torch.cuda.synchronize()
-        w.copy_(ul)
+        w.copy_(src)
         a, z = ev(), ev()
         a.record(stream)
-        ctx.explicit_advance(bl, w)
+        adv(batch, w)
         z.record(stream)
         torch.cuda.synchronize()
-        t = a.elapsed_time(z) / 1000.0
-        cups = float(lg.ns[0]) * steps / t
+        return w, a.elapsed_time(z) / 1000.0
+
+    for K, steps in ((0, LARGE_EXPLICIT_STEPS), (1, 200)):
+        ctx.set(L.BURGERS_OPT_STREAM_K, K)
+        w, t = timed(L.BURGERS_EXPLICIT, Batch.from_ensemble(lg, dtl, steps, F32), ul)
+        cups = nlg * steps / t
         if K == 0:
             large["explicit_cups"] = cups
             large["explicit_steps"] = steps
+            w64, t64 = timed(L.BURGERS_EXPLICIT, Batch.from_ensemble(lg, dtl, steps, F64), ul64)
+            large["explicit_fp64_cups"] = nlg * steps / t64
+            rel, _ = ctx.rel_l2(Batch.from_ensemble(lg, dtl, steps, F32), w, w64)
+            large["explicit_l2_fp32_vs_fp64"] = float(rel[0])
+            del w64
         else:
             peak, src = hbm_peak()
-            gbs = 16.0 * float(lg.ns[0]) * steps / t / 1e9
+            gbs = 16.0 * nlg * steps / t / 1e9
             large["stream_k1_cups"] = cups
             large["stream_k1_gbs"] = gbs
             large["stream_k1_hbm_frac"] = gbs / peak
             large["stream_k1_peak"] = {"gbs": peak, "source": src}
     ctx.set(L.BURGERS_OPT_STREAM_K, 0)
-    large["note"] = ("N=2^24 periodic FP32, nu=1e-3; K=0: tuned temporal blocking; K=1: one step per "
-                     "HBM pass (k_explicit_step1), algorithmic 16 B per cell-update (u and its FP32 "
-                     "compensation term, each read and written once) against the HBM copy bandwidth")
+    bl32 = Batch.from_ensemble(lg, dtl * BTCS_DT_FACTOR, LARGE_BTCS_STEPS, F32)
+    bl64 = Batch.from_ensemble(lg, dtl * BTCS_DT_FACTOR, LARGE_BTCS_STEPS, F64)
+    w, t = timed(L.BURGERS_BTCS, bl32, ul)
+    w64, t64 = timed(L.BURGERS_BTCS, bl64, ul64)
+    rel, _ = ctx.rel_l2(bl32, w, w64)
+    large["btcs_cups"] = nlg * LARGE_BTCS_STEPS / t
+    large["btcs_fp64_cups"] = nlg * LARGE_BTCS_STEPS / t64
+    large["btcs_steps"] = LARGE_BTCS_STEPS
+    large["btcs_l2_fp32_vs_fp64"] = float(rel[0])
+    del w64
+    large["note"] = ("N=2^24 periodic, nu=1e-3. Explicit: K=0 tuned temporal blocking, "
+                     "K=1 one step per HBM pass (k_explicit_step1), algorithmic 16 B per "
+                     "cell-update (u and its FP32 compensation term, each read and written once) "
+                     "against the HBM copy bandwidth. BTCS at 10x dt through the multi-level "
+                     "partitioned solver. l2 = per-row relative L2 of FP32 against FP64")
     out["large_grid"] = large
-    del ul, w
+    del ul, ul64, w
     return out
 
 
