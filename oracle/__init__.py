@@ -63,7 +63,7 @@ def _load():
         P = ctypes.c_void_p
         lib.or_cfl_dt.restype = d
         lib.or_cfl_dt.argtypes = [P, i64, d, d, d]
-        for name in ("or_explicit", "or_btcs", "or_rk4"):
+        for name in ("or_explicit", "or_btcs", "or_rk4", "or_cn"):
             f = getattr(lib, name)
             f.restype = c
             f.argtypes = [P, i64, i32, d, d, d, i64]
@@ -73,7 +73,17 @@ def _load():
         lib.or_thomas.argtypes = [i64, P, P, P, P, P]
         lib.or_cyclic.restype = c
         lib.or_cyclic.argtypes = [i64, P, P, P, P, P]
-        for name in ("or_explicit_batch", "or_btcs_batch", "or_rk4_batch"):
+        for name in ("or_picard", "or_newton"):
+            f = getattr(lib, name)
+            f.restype = c
+            f.argtypes = [P, i64, i32, d, d, d, i64, c]
+        lib.or_newton_residual.restype = c
+        lib.or_newton_residual.argtypes = [P, P, i64, i32, d, d, d, P]
+        for name in ("or_picard_batch", "or_newton_batch"):
+            f = getattr(lib, name)
+            f.restype = c
+            f.argtypes = [P, i64, P, P, P, P, P, P, P, c, c]
+        for name in ("or_explicit_batch", "or_btcs_batch", "or_rk4_batch", "or_cn_batch"):
             f = getattr(lib, name)
             f.restype = c
             f.argtypes = [P, i64, P, P, P, P, P, P, P, c]
@@ -129,6 +139,36 @@ def rk4(u0, bc: int, dx: float, nu: float, dt: float, nsteps: int) -> np.ndarray
     u = _f64(u0).copy()
     _check(_load().or_rk4(_p(u), u.size, int(bc), dx, nu, dt, int(nsteps)), "rk4")
     return u
+
+
+def cn(u0, bc: int, dx: float, nu: float, dt: float, nsteps: int) -> np.ndarray:
+    """Crank-Nicolson with the convecting velocity lagged at u^n (upwind side by sign)."""
+    u = _f64(u0).copy()
+    _check(_load().or_cn(_p(u), u.size, int(bc), dx, nu, dt, int(nsteps)), "cn")
+    return u
+
+
+def picard(u0, bc: int, dx: float, nu: float, dt: float, nsteps: int, iters: int) -> np.ndarray:
+    """`iters` Picard iterations A(w) w' = u^n per step (iters = 1: lagged BTCS)."""
+    u = _f64(u0).copy()
+    _check(_load().or_picard(_p(u), u.size, int(bc), dx, nu, dt, int(nsteps), int(iters)), "picard")
+    return u
+
+
+def newton(u0, bc: int, dx: float, nu: float, dt: float, nsteps: int, iters: int) -> np.ndarray:
+    """`iters` Newton-Raphson iterations per step on the residual of Eq. 11."""
+    u = _f64(u0).copy()
+    _check(_load().or_newton(_p(u), u.size, int(bc), dx, nu, dt, int(nsteps), int(iters)), "newton")
+    return u
+
+
+def newton_residual(w, un, bc: int, dx: float, nu: float, dt: float) -> np.ndarray:
+    """F(w) of Eq. 11 for the step from un (zero at Dirichlet ends)."""
+    w, un = _f64(w), _f64(un)
+    f = np.empty_like(w)
+    _check(_load().or_newton_residual(_p(w), _p(un), w.size, int(bc), dx, nu, dt, _p(f)),
+           "newton_residual")
+    return f
 
 
 def btcs(u0, bc: int, dx: float, nu: float, dt: float, nsteps: int) -> np.ndarray:
@@ -192,6 +232,35 @@ def rk4_batch(u, offsets, ns, bcs, dxs, nus, dts, nsteps, threads: int = 0) -> n
     """Independent RK4 solves of a packed batch (one thread per instance)."""
     return _run_batch(_load().or_rk4_batch, "rk4_batch", u, offsets, ns, bcs,
                       dxs, nus, dts, nsteps, threads)
+
+
+def cn_batch(u, offsets, ns, bcs, dxs, nus, dts, nsteps, threads: int = 0) -> np.ndarray:
+    """Independent Crank-Nicolson solves of a packed batch."""
+    return _run_batch(_load().or_cn_batch, "cn_batch", u, offsets, ns, bcs,
+                      dxs, nus, dts, nsteps, threads)
+
+
+def _run_batch_iter(fn, name, u, offsets, ns, bcs, dxs, nus, dts, nsteps, iters, threads):
+    u = _f64(u).copy()
+    arrs = _batch_arrays(offsets, ns, bcs, dxs, nus, dts, nsteps)
+    count = arrs[0].size
+    for a in arrs:
+        if a.size != count:
+            raise ValueError("batch arrays differ in length")
+    _check(fn(_p(u), count, *[_p(a) for a in arrs], int(iters), int(threads)), name)
+    return u
+
+
+def picard_batch(u, offsets, ns, bcs, dxs, nus, dts, nsteps, iters, threads: int = 0):
+    """Independent Picard-iterated implicit solves of a packed batch."""
+    return _run_batch_iter(_load().or_picard_batch, "picard_batch", u, offsets, ns, bcs, dxs,
+                           nus, dts, nsteps, iters, threads)
+
+
+def newton_batch(u, offsets, ns, bcs, dxs, nus, dts, nsteps, iters, threads: int = 0):
+    """Independent Newton (Eq. 10-15) solves of a packed batch."""
+    return _run_batch_iter(_load().or_newton_batch, "newton_batch", u, offsets, ns, bcs, dxs,
+                           nus, dts, nsteps, iters, threads)
 
 
 def btcs_batch(u, offsets, ns, bcs, dxs, nus, dts, nsteps, threads: int = 0) -> np.ndarray:

@@ -15,6 +15,11 @@
  *                   the Laplacian), with the upwind side chosen by the sign of
  *                   u_i as Sec. 2.2 describes: backward difference for u_i > 0,
  *                   forward difference for u_i < 0.
+ *   CN step         Crank-Nicolson (named in Sec. 2.2) with the convecting
+ *                   velocity lagged at u^n, upwind side by its sign.
+ *   Picard / Newton the implicit upwind equation iterated to convergence by
+ *                   Picard; Newton-Raphson on the residual of Eq. 11 (central
+ *                   convection), Eq. 10-15.
  *   RK4 step        Eq. 22: classical fourth-order Runge-Kutta on the spatial
  *                   operator of Eq. 21, stage by stage.
  *   BTCS step       Sec. 2.4 / Eq. 23: all spatial terms at t^{n+1}; the
@@ -246,6 +251,144 @@ int or_btcs(double* u, int64_t n, int bc, double dx, double nu, double dt, int64
 }
 
 /* ------------------------------------------------------------------------ */
+/* Further implicit variants (the paper names Crank-Nicolson, Sec. 2.2, and   */
+/* Newton-Raphson on the residual of Eq. 11, Eq. 10-15).                      */
+/* Each step solves tridiagonal systems (cyclic when periodic) with the        */
+/* solvers above; Dirichlet end values are held and moved to the right-hand  */
+/* side of the interior system.                                               */
+/* ------------------------------------------------------------------------ */
+
+/* Solves the n-row system (l, d, c, rhs) for the new state x: periodic rows  */
+/* as a cyclic system; Dirichlet rows 1..n-2 with x[0], x[n-1] known (their   */
+/* couplings moved to the right-hand side). l, d, c, rhs are clobbered.       */
+static int solve_rows(int64_t n, int bc, double* l, double* d, double* c, double* rhs,
+                      double* x, double* tmp) {
+  if (bc == OR_PERIODIC) {
+    int rc = or_cyclic(n, l, d, c, rhs, tmp);
+    if (rc == 0) memcpy(x, tmp, sizeof(double) * (size_t)n);
+    return rc;
+  }
+  int64_t m = n - 2;
+  rhs[1] -= l[1] * x[0];
+  rhs[n - 2] -= c[n - 2] * x[n - 1];
+  l[1] = 0.0;
+  c[n - 2] = 0.0;
+  int rc = or_thomas(m, l + 1, d + 1, c + 1, rhs + 1, tmp);
+  if (rc == 0) memcpy(x + 1, tmp, sizeof(double) * (size_t)m);
+  return rc;
+}
+
+/* Crank-Nicolson with the convecting velocity lagged at u^n (upwind side by  */
+/* its sign, as for BTCS): with L(a) the upwind/central operator of Eq. 21,   */
+/*   (I - dt/2 L(u^n)) u^{n+1} = (I + dt/2 L(u^n)) u^n,                        */
+/* i.e. BTCS rows with r/2, s/2 and the right-hand side u^n plus half the     */
+/* forward-Euler increment of u^n.                                            */
+int or_cn(double* u, int64_t n, int bc, double dx, double nu, double dt, int64_t nsteps) {
+  if (!u || bad_common(n, bc, dx, nu, dt, nsteps)) return -1;
+  double r = dt / dx, s = nu * dt / (dx * dx);
+  double* buf = (double*)malloc(sizeof(double) * (size_t)n * 6);
+  if (!buf) return -2;
+  double *l = buf, *d = buf + n, *c = buf + 2 * n, *rhs = buf + 3 * n, *half = buf + 4 * n,
+         *tmp = buf + 5 * n;
+  int rc = 0;
+  for (int64_t k = 0; rc == 0 && k < nsteps; ++k) {
+    explicit_step(u, half, n, bc, 0.5 * r, 0.5 * s); /* u^n + dt/2 L(u^n) u^n */
+    for (int64_t i = 0; i < n; ++i) {
+      btcs_row(u[i], 0.5 * r, 0.5 * s, &l[i], &d[i], &c[i]);
+      rhs[i] = half[i];
+    }
+    rc = solve_rows(n, bc, l, d, c, rhs, u, tmp);
+  }
+  free(buf);
+  return rc;
+}
+
+/* Picard iteration on the implicit upwind equation: iterate                  */
+/*   A(w) w' = u^n,  w^0 = u^n,                                                */
+/* `iters` times per step (A as in BTCS, coefficients from the latest iterate); */
+/* iters = 1 is the lagged BTCS step.                                          */
+int or_picard(double* u, int64_t n, int bc, double dx, double nu, double dt, int64_t nsteps,
+              int iters) {
+  if (!u || bad_common(n, bc, dx, nu, dt, nsteps) || iters < 1) return -1;
+  double r = dt / dx, s = nu * dt / (dx * dx);
+  double* buf = (double*)malloc(sizeof(double) * (size_t)n * 6);
+  if (!buf) return -2;
+  double *l = buf, *d = buf + n, *c = buf + 2 * n, *rhs = buf + 3 * n, *w = buf + 4 * n,
+         *tmp = buf + 5 * n;
+  int rc = 0;
+  for (int64_t k = 0; rc == 0 && k < nsteps; ++k) {
+    memcpy(w, u, sizeof(double) * (size_t)n);
+    for (int it = 0; rc == 0 && it < iters; ++it) {
+      for (int64_t i = 0; i < n; ++i) {
+        btcs_row(w[i], r, s, &l[i], &d[i], &c[i]);
+        rhs[i] = u[i];
+      }
+      rc = solve_rows(n, bc, l, d, c, rhs, w, tmp);
+    }
+    memcpy(u, w, sizeof(double) * (size_t)n);
+  }
+  free(buf);
+  return rc;
+}
+
+/* Residual of Eq. 11 (central convection, all terms at the new level) at    */
+/* node i, for a periodic row or an interior Dirichlet node.                   */
+static double newton_residual(const double* w, const double* un, int64_t n, int64_t i, double r,
+                              double s) {
+  int64_t im = (i == 0) ? n - 1 : i - 1;
+  int64_t ip = (i == n - 1) ? 0 : i + 1;
+  return w[i] - un[i] + 0.5 * r * w[i] * (w[ip] - w[im]) - s * (w[ip] - 2.0 * w[i] + w[im]);
+}
+
+/* Newton-Raphson on F(w) = 0, F of Eq. 11 (Eq. 10-14), `iters` iterations per */
+/* step from w^0 = u^n. The Jacobian follows from Eq. 11 (Eq. 15 prints only   */
+/* a sub-diagonal entry, with a garbled sign on its diffusive part):           */
+/*   dF_i/dw_{i-1} = -r/2 w_i - s,  dF_i/dw_i = 1 + r/2 (w_{i+1} - w_{i-1}) + 2s, */
+/*   dF_i/dw_{i+1} = r/2 w_i - s.                                              */
+/* Dirichlet end values are held (zero Newton update there).                   */
+int or_newton(double* u, int64_t n, int bc, double dx, double nu, double dt, int64_t nsteps,
+              int iters) {
+  if (!u || bad_common(n, bc, dx, nu, dt, nsteps) || iters < 1) return -1;
+  double r = dt / dx, s = nu * dt / (dx * dx);
+  double* buf = (double*)malloc(sizeof(double) * (size_t)n * 7);
+  if (!buf) return -2;
+  double *l = buf, *d = buf + n, *c = buf + 2 * n, *rhs = buf + 3 * n, *w = buf + 4 * n,
+         *du = buf + 5 * n, *tmp = buf + 6 * n;
+  int rc = 0;
+  for (int64_t k = 0; rc == 0 && k < nsteps; ++k) {
+    memcpy(w, u, sizeof(double) * (size_t)n);
+    for (int it = 0; rc == 0 && it < iters; ++it) {
+      for (int64_t i = 0; i < n; ++i) {
+        int64_t im = (i == 0) ? n - 1 : i - 1;
+        int64_t ip = (i == n - 1) ? 0 : i + 1;
+        l[i] = -0.5 * r * w[i] - s;
+        d[i] = 1.0 + 0.5 * r * (w[ip] - w[im]) + 2.0 * s;
+        c[i] = 0.5 * r * w[i] - s;
+        rhs[i] = -newton_residual(w, u, n, i, r, s);
+      }
+      du[0] = 0.0;
+      du[n - 1] = 0.0;
+      rc = solve_rows(n, bc, l, d, c, rhs, du, tmp);
+      for (int64_t i = 0; i < n; ++i) w[i] += du[i];
+    }
+    memcpy(u, w, sizeof(double) * (size_t)n);
+  }
+  free(buf);
+  return rc;
+}
+
+/* Residual of Eq. 11 for the whole row (Dirichlet ends report 0).            */
+int or_newton_residual(const double* w, const double* un, int64_t n, int bc, double dx,
+                       double nu, double dt, double* f) {
+  if (!w || !un || !f || bad_common(n, bc, dx, nu, dt, 0)) return -1;
+  double r = dt / dx, s = nu * dt / (dx * dx);
+  for (int64_t i = 0; i < n; ++i)
+    f[i] = (bc == OR_DIRICHLET && (i == 0 || i == n - 1)) ? 0.0
+                                                          : newton_residual(w, un, n, i, r, s);
+  return 0;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Batched drivers: independent instances, one OpenMP thread per instance.   */
 /* ------------------------------------------------------------------------ */
 int or_max_threads(void) {
@@ -331,6 +474,42 @@ int or_rk4_batch(double* u, int64_t count, const int64_t* offset, const int32_t*
                  const int32_t* bc, const double* dx, const double* nu, const double* dt,
                  const int64_t* nsteps, int nthreads) {
   return run_batch(or_rk4, u, count, offset, n, bc, dx, nu, dt, nsteps, nthreads);
+}
+
+int or_cn_batch(double* u, int64_t count, const int64_t* offset, const int32_t* n,
+                const int32_t* bc, const double* dx, const double* nu, const double* dt,
+                const int64_t* nsteps, int nthreads) {
+  return run_batch(or_cn, u, count, offset, n, bc, dx, nu, dt, nsteps, nthreads);
+}
+
+typedef int (*iter_fn)(double*, int64_t, int, double, double, double, int64_t, int);
+
+static int run_batch_iter(iter_fn f, double* u, int64_t count, const int64_t* offset,
+                          const int32_t* n, const int32_t* bc, const double* dx, const double* nu,
+                          const double* dt, const int64_t* nsteps, int iters, int nthreads) {
+  int err = 0;
+#ifdef _OPENMP
+  if (nthreads < 1) nthreads = omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads) reduction(| : err)
+#endif
+  for (int64_t b = 0; b < count; ++b) {
+    int rc = f(u + offset[b], n[b], bc[b], dx[b], nu[b], dt[b], nsteps[b], iters);
+    if (rc) err |= 1;
+  }
+  (void)nthreads;
+  return err ? -1 : 0;
+}
+
+int or_picard_batch(double* u, int64_t count, const int64_t* offset, const int32_t* n,
+                    const int32_t* bc, const double* dx, const double* nu, const double* dt,
+                    const int64_t* nsteps, int iters, int nthreads) {
+  return run_batch_iter(or_picard, u, count, offset, n, bc, dx, nu, dt, nsteps, iters, nthreads);
+}
+
+int or_newton_batch(double* u, int64_t count, const int64_t* offset, const int32_t* n,
+                    const int32_t* bc, const double* dx, const double* nu, const double* dt,
+                    const int64_t* nsteps, int iters, int nthreads) {
+  return run_batch_iter(or_newton, u, count, offset, n, bc, dx, nu, dt, nsteps, iters, nthreads);
 }
 
 int or_btcs_batch(double* u, int64_t count, const int64_t* offset, const int32_t* n,

@@ -26,6 +26,13 @@ double or_cfl_dt(const double* u, int64_t n, double dx, double nu, double cfl);
 int or_explicit(double* u, int64_t n, int bc, double dx, double nu, double dt, int64_t nsteps);
 int or_btcs(double* u, int64_t n, int bc, double dx, double nu, double dt, int64_t nsteps);
 int or_rk4(double* u, int64_t n, int bc, double dx, double nu, double dt, int64_t nsteps);
+int or_cn(double* u, int64_t n, int bc, double dx, double nu, double dt, int64_t nsteps);
+int or_picard(double* u, int64_t n, int bc, double dx, double nu, double dt, int64_t nsteps,
+              int iters);
+int or_newton(double* u, int64_t n, int bc, double dx, double nu, double dt, int64_t nsteps,
+              int iters);
+int or_newton_residual(const double* w, const double* un, int64_t n, int bc, double dx,
+                       double nu, double dt, double* f);
 
 int or_btcs_system(const double* un, int64_t n, int bc, double r, double s,
                    double* l, double* d, double* c, double* rhs);
@@ -40,6 +47,15 @@ int or_explicit_batch(double* u, int64_t count, const int64_t* offset, const int
 int or_rk4_batch(double* u, int64_t count, const int64_t* offset, const int32_t* n,
                  const int32_t* bc, const double* dx, const double* nu, const double* dt,
                  const int64_t* nsteps, int nthreads);
+int or_cn_batch(double* u, int64_t count, const int64_t* offset, const int32_t* n,
+                const int32_t* bc, const double* dx, const double* nu, const double* dt,
+                const int64_t* nsteps, int nthreads);
+int or_picard_batch(double* u, int64_t count, const int64_t* offset, const int32_t* n,
+                    const int32_t* bc, const double* dx, const double* nu, const double* dt,
+                    const int64_t* nsteps, int iters, int nthreads);
+int or_newton_batch(double* u, int64_t count, const int64_t* offset, const int32_t* n,
+                    const int32_t* bc, const double* dx, const double* nu, const double* dt,
+                    const int64_t* nsteps, int iters, int nthreads);
 int or_btcs_batch(double* u, int64_t count, const int64_t* offset, const int32_t* n,
                   const int32_t* bc, const double* dx, const double* nu, const double* dt,
                   const int64_t* nsteps, int nthreads);

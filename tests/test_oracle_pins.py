@@ -413,3 +413,149 @@ def test_adjoint_matches_central_differences(orc, scheme, bc, shift):
         d_u, d_nu = _loss_and_fd(orc, scheme, u0, bc, dx, nu, dt, steps, target, v, 1e-6)
         assert float(gu0 @ v) == pytest.approx(d_u, rel=2e-6, abs=1e-10)
     assert gnu == pytest.approx(d_nu, rel=2e-6, abs=1e-10)
+
+
+# --------------------------------------------------------------------------
+# Further implicit variants: Crank-Nicolson (lagged upwind), Picard-iterated
+# implicit upwind, Newton-Raphson on the residual of Eq. 11.
+# --------------------------------------------------------------------------
+def test_cn_heat_and_advection_limits(orc):
+    """Small perturbations obey the linear CN scheme: amplification
+    (1 - z/2)/(1 + z/2) with z the upwind/central eigenvalue (both signs of
+    the convecting velocity)."""
+    n, k, eps = 48, 2, 1e-7
+    x, dx = _periodic(n)
+    nu = 0.02
+    for c0 in (0.0, 0.7, -0.7):
+        amp = eps if c0 == 0.0 else eps
+        dt = 0.4 * (dx * dx / (2 * nu) if c0 == 0.0 else min(dx / abs(c0), dx * dx / (2 * nu))) * 5
+        r, s = dt / dx, nu * dt / dx**2
+        steps = 30
+        out = orc.cn(c0 + amp * np.sin(k * x), P, dx, nu, dt, steps)
+        e = np.exp(1j * k * dx)
+        conv = 0.0 if c0 == 0.0 else (r * c0 * (1 - 1 / e) if c0 > 0 else r * c0 * (e - 1))
+        z = conv + 4 * s * math.sin(k * dx / 2) ** 2
+        g = (1 - z / 2) / (1 + z / 2)
+        expect = c0 + amp * np.imag(g**steps * np.exp(1j * k * x))
+        assert np.max(np.abs(out - expect)) <= 2e-3 * amp, c0
+
+
+def test_cn_second_order_in_time_for_heat(orc):
+    """In the heat limit CN converges at second order in dt to the
+    semi-discrete solution exp(-4 nu sin^2(k dx/2)/dx^2 t); BTCS at first."""
+    n, k, eps, nu, t = 32, 3, 1e-9, 0.2, 0.5
+    x, dx = _periodic(n)
+    lam = 4 * nu * math.sin(k * dx / 2) ** 2 / dx**2
+    exact = eps * math.exp(-lam * t) * np.sin(k * x)
+    for scheme, lo, hi in (("cn", 3.6, 4.4), ("btcs", 1.7, 2.3)):
+        errs = []
+        for steps in (40, 80, 160):
+            out = getattr(orc, scheme)(eps * np.sin(k * x), P, dx, nu, t / steps, steps)
+            errs.append(np.max(np.abs(out - exact)))
+        ratios = [errs[i] / errs[i + 1] for i in range(2)]
+        assert all(lo <= q <= hi for q in ratios), (scheme, errs, ratios)
+
+
+@pytest.mark.parametrize("scheme", ["cn"])
+@pytest.mark.parametrize("bc", [P, D])
+def test_cn_invariants(orc, scheme, bc):
+    for cval in (0.0, 1.25, -0.8):
+        out = orc.cn(np.full(37, cval), bc, 0.05, 0.01, 0.01, 25)
+        assert np.max(np.abs(out - cval)) <= 1e-14 * max(1, abs(cval))
+    e = W.plain_sine(101)
+    out = orc.cn(e.u0, D, e.dxs[0], e.nus[0], 0.004, 60)
+    assert np.max(np.abs(out + out[::-1])) <= 1e-14 and out[0] == 0.0 and out[-1] == 0.0
+
+
+@pytest.mark.parametrize("bc", [P, D])
+def test_picard_one_iteration_is_btcs(orc, bc):
+    e = W.mixed_ensemble(4, 20, 200, seed=3)
+    for b in range(e.count):
+        u0, dx, nu = e.row(b), e.dxs[b], e.nus[b]
+        dt = 5 * orc.cfl_dt(u0, dx, nu)
+        assert np.array_equal(orc.picard(u0, bc, dx, nu, dt, 7, 1), orc.btcs(u0, bc, dx, nu, dt, 7))
+
+
+def _upwind_implicit_residual(w, un, dx, nu, dt, bc):
+    """w_i + r (w_i+ (w_i - w_{i-1}) + w_i- (w_{i+1} - w_i)) - s (w_{i+1} - 2 w_i + w_{i-1}) - un_i."""
+    r, s = dt / dx, nu * dt / dx**2
+    wm, wp = np.roll(w, 1), np.roll(w, -1)
+    res = w + r * (np.maximum(w, 0) * (w - wm) + np.minimum(w, 0) * (wp - w)) \
+        - s * (wp - 2 * w + wm) - un
+    if bc == D:
+        res[0] = res[-1] = 0.0
+    return res
+
+
+@pytest.mark.parametrize("bc", [P, D])
+def test_picard_converges_to_the_implicit_upwind_equation(orc, bc):
+    """Iterating the lagged solve reaches the fixed point of the fully implicit
+    upwind equation; the iterates contract geometrically."""
+    x, dx = _periodic(64)
+    u0 = 0.2 + 0.8 * np.sin(x)
+    nu = 0.02
+    dt = 3 * orc.cfl_dt(u0, dx, nu)
+    prev, diffs = None, []
+    for it in range(1, 9):
+        w = orc.picard(u0, bc, dx, nu, dt, 1, it)
+        if prev is not None:
+            diffs.append(np.max(np.abs(w - prev)))
+        prev = w
+    assert all(diffs[i + 1] < 0.7 * diffs[i] for i in range(len(diffs) - 1) if diffs[i] > 1e-14)
+    w = orc.picard(u0, bc, dx, nu, dt, 1, 60)
+    assert np.max(np.abs(_upwind_implicit_residual(w, u0, dx, nu, dt, bc))) <= 1e-13
+
+
+def test_newton_linear_limits_are_central_implicit(orc):
+    """Small perturbations of a constant state obey the implicit scheme with
+    CENTRAL convection of Eq. 11: amplification 1/(1 + i r c sin(k dx) +
+    4 s sin^2(k dx/2)) (an upwind or sign-flipped convection fails)."""
+    n, k, eps = 48, 2, 1e-8
+    x, dx = _periodic(n)
+    nu = 0.02
+    for c0 in (0.0, 0.6, -0.6):
+        dt = 0.01
+        r, s = dt / dx, nu * dt / dx**2
+        steps = 25
+        out = orc.newton(c0 + eps * np.sin(k * x), P, dx, nu, dt, steps, 3)
+        g = 1 / (1 + 1j * r * c0 * math.sin(k * dx) + 4 * s * math.sin(k * dx / 2) ** 2)
+        expect = c0 + eps * np.imag(g**steps * np.exp(1j * k * x))
+        assert np.max(np.abs(out - expect)) <= 1e-4 * eps, c0
+
+
+@pytest.mark.parametrize("bc", [P, D])
+def test_newton_converges_quadratically(orc, bc):
+    """||F(w_{k+1})|| <= C ||F(w_k)||^2 for the residual of Eq. 11: the
+    Jacobian matches F (a wrong entry, e.g. the sign Eq. 15 prints for the
+    diffusive part, gives linear convergence)."""
+    x, dx = _periodic(96)
+    u0 = 0.3 + 0.9 * np.sin(x) + 0.2 * np.cos(2 * x)
+    nu, dt = 0.03, 0.02
+    norms = []
+    for it in range(1, 6):
+        w = orc.newton(u0, bc, dx, nu, dt, 1, it)
+        norms.append(np.max(np.abs(orc.newton_residual(w, u0, bc, dx, nu, dt))))
+    f0 = np.max(np.abs(orc.newton_residual(u0, u0, bc, dx, nu, dt)))
+    seq = [f0] + norms
+    assert seq[-1] <= 1e-13
+    for a, b in zip(seq, seq[1:]):
+        if b > 1e-12:
+            assert b <= 10.0 * a * a, seq
+
+
+@pytest.mark.parametrize("scheme", ["cn", "picard", "newton"])
+def test_implicit_variants_batch_matches_single(orc, scheme):
+    e = W.mixed_ensemble(7, 5, 80, seed=6)
+    dts = np.array([2 * orc.cfl_dt(e.row(b), e.dxs[b], e.nus[b]) for b in range(e.count)])
+    steps = np.arange(e.count) + 2
+    if scheme == "cn":
+        out = orc.cn_batch(e.u0, e.offsets, e.ns, e.bcs, e.dxs, e.nus, dts, steps, threads=3)
+        one = lambda b: orc.cn(e.row(b), e.bcs[b], e.dxs[b], e.nus[b], dts[b], steps[b])  # noqa: E731
+    else:
+        fb = getattr(orc, scheme + "_batch")
+        out = fb(e.u0, e.offsets, e.ns, e.bcs, e.dxs, e.nus, dts, steps, 3, threads=3)
+        f1 = getattr(orc, scheme)
+        one = lambda b: f1(e.row(b), e.bcs[b], e.dxs[b], e.nus[b], dts[b], steps[b], 3)  # noqa: E731
+    for b in range(e.count):
+        o = e.offsets[b]
+        assert np.array_equal(out[o:o + e.ns[b]], one(b))
