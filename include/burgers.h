@@ -60,7 +60,14 @@ typedef enum {
 
 typedef enum { BURGERS_F32 = 0, BURGERS_F64 = 1 } burgers_dtype;
 typedef enum { BURGERS_PERIODIC = 0, BURGERS_DIRICHLET = 1 } burgers_bc;
-typedef enum { BURGERS_EXPLICIT = 0, BURGERS_BTCS = 1, BURGERS_RK4 = 2 } burgers_scheme;
+typedef enum {
+  BURGERS_EXPLICIT = 0, /* forward Euler, Eq. 21 */
+  BURGERS_BTCS = 1,     /* lagged upwind BTCS, Eq. 23 */
+  BURGERS_RK4 = 2,      /* classical RK4, Eq. 22 */
+  BURGERS_CN = 3,       /* Crank-Nicolson, lagged upwind coefficients */
+  BURGERS_PICARD = 4,   /* implicit upwind, Picard-iterated */
+  BURGERS_NEWTON = 5    /* Newton-Raphson on the residual of Eq. 11 */
+} burgers_scheme;
 
 /* One row of a batch (see the conventions above). */
 typedef struct {
@@ -170,6 +177,37 @@ burgers_status burgers_btcs_advance(burgers_ctx* ctx, const burgers_batch* batch
 burgers_status burgers_rk4_advance(burgers_ctx* ctx, const burgers_batch* batch,
                                    void* u_dev, burgers_stream stream);
 
+/* Crank-Nicolson (named as an implicit option in Sec. 2.2) with the
+ * convecting velocity lagged at u^n and the upwind side chosen by its sign:
+ *   (I - dt/2 L(u^n)) u^{n+1} = (I + dt/2 L(u^n)) u^n,
+ * L the upwind/central operator of Eq. 21 (so the rows are those of
+ * burgers_btcs_advance with r/2 and s/2). Rows up to the resident capacity
+ * (8192 nodes FP32, 4096 FP64); longer rows: EINVAL. In place, layout,
+ * ownership and errors as burgers_btcs_advance. */
+burgers_status burgers_cn_advance(burgers_ctx* ctx, const burgers_batch* batch, void* u_dev,
+                                  burgers_stream stream);
+
+/* Fully implicit upwind step solved by `iters` Picard iterations per step,
+ * A(w) w' = u^n from w = u^n, with A as in burgers_btcs_advance but its
+ * coefficients taken from the latest iterate (iters = 1 is the lagged BTCS
+ * step). iters in [1, 64], else EINVAL. Row limits as burgers_cn_advance. */
+burgers_status burgers_picard_advance(burgers_ctx* ctx, const burgers_batch* batch, void* u_dev,
+                                      int32_t iters, burgers_stream stream);
+
+/* Implicit step with central convection (Eq. 11) solved by `iters`
+ * Newton-Raphson iterations per step (Eq. 10-14) from w = u^n:
+ *   J(w) dw = -F(w), w += dw,
+ *   F_i = w_i - u^n_i + r/2 w_i (w_{i+1} - w_{i-1}) - s (w_{i+1} - 2 w_i + w_{i-1}),
+ *   J: sub -r/2 w_i - s, diag 1 + r/2 (w_{i+1} - w_{i-1}) + 2s, super r/2 w_i - s
+ * (derived from Eq. 11; Eq. 15 prints only the sub-diagonal, with the sign of
+ * its diffusive part garbled). Dirichlet ends held. No pivoting: the Jacobian
+ * is strictly diagonally dominant while r max|w| < 1/2 (dt below half the
+ * convective CFL limit dx/max|u|); beyond that it may not be, and the solve is
+ * then not guaranteed. iters in [1, 64], else EINVAL. Row limits as
+ * burgers_cn_advance. */
+burgers_status burgers_newton_advance(burgers_ctx* ctx, const burgers_batch* batch, void* u_dev,
+                                      int32_t iters, burgers_stream stream);
+
 /* burgers_explicit_advance for one row, without allocating device memory.
  * The paper has no counterpart: this exists for callers that cannot allocate
  * device memory while they run (an arena that already owns the GPU's memory,
@@ -188,7 +226,8 @@ burgers_status burgers_explicit_advance_noalloc(const burgers_instance* inst, in
                                                 void* u_dev, burgers_stream stream);
 
 /* End-to-end variant through host memory: copies every row from u_host to a
- * context-owned device buffer, advances it with `scheme` (any burgers_scheme),
+ * context-owned device buffer, advances it with `scheme` (a burgers_scheme;
+ * BURGERS_PICARD and BURGERS_NEWTON with one iteration per step),
  * copies the rows back into u_host. Blocking. u_host should be pinned for
  * full copy bandwidth. */
 burgers_status burgers_solve_host(burgers_ctx* ctx, int32_t scheme, const burgers_batch* batch,

@@ -32,6 +32,9 @@ BURGERS_DIRICHLET = 1
 BURGERS_EXPLICIT = 0
 BURGERS_BTCS = 1
 BURGERS_RK4 = 2
+BURGERS_CN = 3
+BURGERS_PICARD = 4
+BURGERS_NEWTON = 5
 
 BURGERS_OPT_GRAPHS = 0
 BURGERS_OPT_PLAIN = 1
@@ -75,6 +78,9 @@ SIGNATURES = {
     "burgers_explicit_advance": (_ST, [_P, _P, _P, _P]),
     "burgers_btcs_advance": (_ST, [_P, _P, _P, _P]),
     "burgers_rk4_advance": (_ST, [_P, _P, _P, _P]),
+    "burgers_cn_advance": (_ST, [_P, _P, _P, _P]),
+    "burgers_picard_advance": (_ST, [_P, _P, _P, ctypes.c_int32, _P]),
+    "burgers_newton_advance": (_ST, [_P, _P, _P, ctypes.c_int32, _P]),
     "burgers_solve_host": (_ST, [_P, _I32, _P, _P, _P]),
     "burgers_rel_l2": (_ST, [_P, _P, _P, _P, _I32, _P, _P, _P]),
     "burgers_adjoint": (_ST, [_P, _I32, _P, _P, _P, _P, _P, _I64, _P]),

@@ -136,13 +136,39 @@ class Context:
         L.check(self._lib.burgers_rk4_advance(self.h, batch.ref(), p, self._stream(stream, u)),
                 "burgers_rk4_advance")
 
-    def advance(self, scheme: int, batch: Batch, u, stream=None) -> None:
+    def cn_advance(self, batch: Batch, u, stream=None) -> None:
+        """Crank-Nicolson with lagged upwind coefficients (resident rows)."""
+        p = self._check_tensor(u, batch)
+        L.check(self._lib.burgers_cn_advance(self.h, batch.ref(), p, self._stream(stream, u)),
+                "burgers_cn_advance")
+
+    def picard_advance(self, batch: Batch, u, iters: int, stream=None) -> None:
+        """Implicit upwind step, `iters` Picard iterations per step (resident rows)."""
+        p = self._check_tensor(u, batch)
+        L.check(self._lib.burgers_picard_advance(self.h, batch.ref(), p, int(iters),
+                                                 self._stream(stream, u)),
+                "burgers_picard_advance")
+
+    def newton_advance(self, batch: Batch, u, iters: int, stream=None) -> None:
+        """Eq. 11 implicit step, `iters` Newton iterations per step (resident rows)."""
+        p = self._check_tensor(u, batch)
+        L.check(self._lib.burgers_newton_advance(self.h, batch.ref(), p, int(iters),
+                                                 self._stream(stream, u)),
+                "burgers_newton_advance")
+
+    def advance(self, scheme: int, batch: Batch, u, stream=None, iters: int = 1) -> None:
         if scheme == L.BURGERS_EXPLICIT:
             self.explicit_advance(batch, u, stream)
         elif scheme == L.BURGERS_RK4:
             self.rk4_advance(batch, u, stream)
         elif scheme == L.BURGERS_BTCS:
             self.btcs_advance(batch, u, stream)
+        elif scheme == L.BURGERS_CN:
+            self.cn_advance(batch, u, stream)
+        elif scheme == L.BURGERS_PICARD:
+            self.picard_advance(batch, u, iters, stream)
+        elif scheme == L.BURGERS_NEWTON:
+            self.newton_advance(batch, u, iters, stream)
         else:
             raise ValueError(f"unknown scheme {scheme}")
 

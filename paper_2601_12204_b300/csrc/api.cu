@@ -95,8 +95,16 @@ static const std::vector<Shape>& resident_shapes(int kind, int dtype) {
   static const std::vector<Shape> rk64 = {{32, 1},  {32, 2},   {32, 4},   {32, 8},  {64, 8},
                                           {128, 4}, {128, 8},  {256, 4},  {256, 8}, {512, 4},
                                           {512, 8}, {1024, 4}};
+  // Crank-Nicolson, Picard and Newton share the BTCS kernel shape
+  static const std::vector<Shape> im32 = {{32, 1},   {32, 2},   {32, 4},   {32, 8},
+                                          {64, 8},   {128, 8},  {256, 8},  {128, 16},
+                                          {256, 16}, {128, 32}, {256, 32}};
+  static const std::vector<Shape> im64 = {{32, 1},  {32, 2},   {32, 4},   {32, 8},  {64, 8},
+                                          {128, 8}, {256, 8},  {128, 16}, {512, 8}};
   if (kind == K_EXPLICIT_RESIDENT) return dtype == 0 ? ex32 : ex64;
   if (kind == K_RK4_RESIDENT) return dtype == 0 ? rk32 : rk64;
+  if (kind == K_CN_RESIDENT || kind == K_PICARD_RESIDENT || kind == K_NEWTON_RESIDENT)
+    return dtype == 0 ? im32 : im64;
   return dtype == 0 ? bt32 : bt64;
 }
 
@@ -207,8 +215,9 @@ burgers_status validate_batch(const burgers_batch* batch, bool allow_empty) {
   return BURGERS_OK;
 }
 
-static RowDesc make_row(const burgers_instance& in) {
+static RowDesc make_row(const burgers_instance& in, int iters = 1) {
   RowDesc d;
+  d.iters = iters;
   d.offset = in.offset;
   d.nsteps = in.nsteps;
   d.r = in.dt / in.dx;
@@ -259,7 +268,8 @@ static bool pick_stream(const burgers_ctx* ctx, int kind, int dtype, int64_t n_m
 
 // Builds the plan of one advance call.
 static burgers_status build_plan(burgers_ctx* ctx, int scheme, const burgers_batch* batch,
-                                 Plan* p, PlanScratch* ext, cudaStream_t ext_stream) {
+                                 Plan* p, PlanScratch* ext, cudaStream_t ext_stream,
+                                 int iters = 1) {
   const int dtype = batch->dtype;
   p->dtype = dtype;
   p->scheme = scheme;
@@ -280,6 +290,8 @@ static burgers_status build_plan(burgers_ctx* ctx, int scheme, const burgers_bat
     // least a few chunks; shorter rows stay resident whatever the limit)
     const int64_t min_long = stencil ? 128 : 64;
     if (in.n > rlim && in.n >= min_long && in.n > 0) {
+      if (!has_long_path(scheme))
+        return set_error(BURGERS_EINVAL, "row longer than the resident capacity of this scheme");
       longs.push_back(b);
       continue;
     }
@@ -302,7 +314,7 @@ static burgers_status build_plan(burgers_ctx* ctx, int scheme, const burgers_bat
     const KernelEntry* k = find_kernel(rkind, dtype, g.sh.nt, g.sh.c, g.exact);
     if (!k) return set_error(BURGERS_EINVAL, "kernel shape not instantiated");
     int begin = int(p->rows.size());
-    for (auto& pr : g.rows) p->rows.push_back(make_row(batch->inst[pr.second]));
+    for (auto& pr : g.rows) p->rows.push_back(make_row(batch->inst[pr.second], iters));
     int cnt = int(g.rows.size());
     if (ctx->plain) {
       for (int i = 0; i < cnt; ++i) {
@@ -552,15 +564,16 @@ static burgers_status run_plan(burgers_ctx* ctx, Plan* p, void* u, cudaStream_t 
   return BURGERS_OK;
 }
 
-static uint64_t plan_key(const burgers_ctx* ctx, int scheme, const burgers_batch* b) {
+static uint64_t plan_key(const burgers_ctx* ctx, int scheme, const burgers_batch* b, int iters) {
   uint64_t h = fnv1a(b->inst, sizeof(burgers_instance) * size_t(b->count));
   int32_t hdr[8] = {scheme, b->dtype, ctx->plain ? 1 : 0, ctx->stream_k, int32_t(ctx->resident_max),
-                    int32_t(ctx->tune_version), ctx->resident_override, 0};
+                    int32_t(ctx->tune_version), ctx->resident_override, iters};
   return fnv1a(hdr, sizeof hdr, h);
 }
 
-Plan* get_plan(burgers_ctx* ctx, int scheme, const burgers_batch* batch, burgers_status* st) {
-  const uint64_t key = plan_key(ctx, scheme, batch);
+Plan* get_plan(burgers_ctx* ctx, int scheme, const burgers_batch* batch, burgers_status* st,
+               int iters) {
+  const uint64_t key = plan_key(ctx, scheme, batch, iters);
   for (auto it = ctx->plans.begin(); it != ctx->plans.end(); ++it) {
     if ((*it)->key == key && (*it)->count == batch->count) {
       ctx->plans.splice(ctx->plans.begin(), ctx->plans, it);  // most recent first
@@ -571,7 +584,7 @@ Plan* get_plan(burgers_ctx* ctx, int scheme, const burgers_batch* batch, burgers
   auto p = std::make_unique<Plan>();
   p->key = key;
   p->count = batch->count;
-  *st = build_plan(ctx, scheme, batch, p.get(), nullptr, nullptr);
+  *st = build_plan(ctx, scheme, batch, p.get(), nullptr, nullptr, iters);
   if (*st != BURGERS_OK) return nullptr;
   ctx->plans.push_front(std::move(p));
   while (ctx->plans.size() > 64) {
@@ -582,15 +595,17 @@ Plan* get_plan(burgers_ctx* ctx, int scheme, const burgers_batch* batch, burgers
 }
 
 burgers_status advance(burgers_ctx* ctx, int scheme, const burgers_batch* batch, void* u_dev,
-                       cudaStream_t stream) {
+                       cudaStream_t stream, int iters) {
   if (!ctx) return set_error(BURGERS_EINVAL, "ctx is NULL");
+  if (!valid_scheme(scheme)) return set_error(BURGERS_EINVAL, "bad scheme");
+  if (iters < 1 || iters > 64) return set_error(BURGERS_EINVAL, "iterations outside [1, 64]");
   burgers_status st = validate_batch(batch, false);
   if (st != BURGERS_OK) return st;
   if (batch->count == 0) return BURGERS_OK;
   if (!u_dev) return set_error(BURGERS_EINVAL, "u_dev is NULL");
   cudaError_t e = cudaSetDevice(ctx->device);
   if (e != cudaSuccess) return cuda_error(e, "cudaSetDevice");
-  Plan* p = get_plan(ctx, scheme, batch, &st);
+  Plan* p = get_plan(ctx, scheme, batch, &st, iters);
   if (!p) return st;
   return run_plan(ctx, p, u_dev, stream);
 }
@@ -686,6 +701,21 @@ burgers_status burgers_btcs_advance(burgers_ctx* ctx, const burgers_batch* batch
 burgers_status burgers_rk4_advance(burgers_ctx* ctx, const burgers_batch* batch, void* u_dev,
                                    burgers_stream stream) {
   return advance(ctx, BURGERS_RK4, batch, u_dev, reinterpret_cast<cudaStream_t>(stream));
+}
+
+burgers_status burgers_cn_advance(burgers_ctx* ctx, const burgers_batch* batch, void* u_dev,
+                                  burgers_stream stream) {
+  return advance(ctx, BURGERS_CN, batch, u_dev, reinterpret_cast<cudaStream_t>(stream));
+}
+
+burgers_status burgers_picard_advance(burgers_ctx* ctx, const burgers_batch* batch, void* u_dev,
+                                      int32_t iters, burgers_stream stream) {
+  return advance(ctx, BURGERS_PICARD, batch, u_dev, reinterpret_cast<cudaStream_t>(stream), iters);
+}
+
+burgers_status burgers_newton_advance(burgers_ctx* ctx, const burgers_batch* batch, void* u_dev,
+                                      int32_t iters, burgers_stream stream) {
+  return advance(ctx, BURGERS_NEWTON, batch, u_dev, reinterpret_cast<cudaStream_t>(stream), iters);
 }
 
 burgers_status burgers_adjoint(burgers_ctx* ctx, int32_t scheme, const burgers_batch* batch,
@@ -869,8 +899,7 @@ burgers_status burgers_cfl_dt(burgers_ctx* ctx, const burgers_batch* batch, cons
 burgers_status burgers_solve_host(burgers_ctx* ctx, int32_t scheme, const burgers_batch* batch,
                                   void* u_host, burgers_stream stream) {
   if (!ctx) return set_error(BURGERS_EINVAL, "ctx is NULL");
-  if (scheme != BURGERS_EXPLICIT && scheme != BURGERS_BTCS && scheme != BURGERS_RK4)
-    return set_error(BURGERS_EINVAL, "bad scheme");
+  if (!valid_scheme(scheme)) return set_error(BURGERS_EINVAL, "bad scheme");
   burgers_status st = validate_batch(batch, false);
   if (st != BURGERS_OK) return st;
   if (batch->count == 0) return BURGERS_OK;

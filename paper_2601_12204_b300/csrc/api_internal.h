@@ -132,12 +132,23 @@ cudaError_t enqueue_multilevel_launch(burgers_ctx* ctx, Plan* p, const Launch& L
                                       cudaStream_t st);
 // Resident kernel kind of a scheme (burgers_scheme).
 inline int resident_kind(int scheme) {
-  return scheme == BURGERS_EXPLICIT ? K_EXPLICIT_RESIDENT
-                                    : (scheme == BURGERS_RK4 ? K_RK4_RESIDENT : K_BTCS_RESIDENT);
+  switch (scheme) {
+    case BURGERS_EXPLICIT: return K_EXPLICIT_RESIDENT;
+    case BURGERS_RK4: return K_RK4_RESIDENT;
+    case BURGERS_CN: return K_CN_RESIDENT;
+    case BURGERS_PICARD: return K_PICARD_RESIDENT;
+    case BURGERS_NEWTON: return K_NEWTON_RESIDENT;
+    default: return K_BTCS_RESIDENT;
+  }
+}
+inline bool valid_scheme(int scheme) { return scheme >= BURGERS_EXPLICIT && scheme <= BURGERS_NEWTON; }
+// Schemes whose long rows have a streaming / multi-level path.
+inline bool has_long_path(int scheme) {
+  return scheme == BURGERS_EXPLICIT || scheme == BURGERS_RK4 || scheme == BURGERS_BTCS;
 }
 
 burgers_status advance(burgers_ctx* ctx, int scheme, const burgers_batch* batch, void* u_dev,
-                       cudaStream_t stream);
+                       cudaStream_t stream, int iters = 1);
 burgers_status advance_uncached(burgers_ctx* ctx, int scheme, const burgers_batch* batch,
                                 void* u_dev, cudaStream_t stream, PlanScratch* ps);
 int64_t adjoint_max_n(int dtype);

@@ -1,0 +1,29 @@
+// btcs_cn.cu -- instantiations of the resident implicit kernel for
+// Crank-Nicolson with lagged upwind coefficients (named in Sec. 2.2).
+#include "btcs_kernel.cuh"
+
+namespace burgers {
+
+#define REG_VAR(KIND, VAR, T, DT, NT, C)                                                    \
+  reg.push_back({KIND, DT, NT, C, 1,                                                        \
+                 reinterpret_cast<const void*>(&k_btcs_resident<T, NT, C, true, VAR>),     \
+                 btcs_dsm<T, NT, C, VAR>()});                                              \
+  reg.push_back({KIND, DT, NT, C, 0,                                                        \
+                 reinterpret_cast<const void*>(&k_btcs_resident<T, NT, C, false, VAR>),    \
+                 btcs_dsm<T, NT, C, VAR>()});
+#define REG_SHAPES(KIND, VAR)                                                                \
+  REG_VAR(KIND, VAR, float, 0, 32, 1) REG_VAR(KIND, VAR, float, 0, 32, 2)                  \
+  REG_VAR(KIND, VAR, float, 0, 32, 4) REG_VAR(KIND, VAR, float, 0, 32, 8)                  \
+  REG_VAR(KIND, VAR, float, 0, 64, 8) REG_VAR(KIND, VAR, float, 0, 128, 8)                 \
+  REG_VAR(KIND, VAR, float, 0, 256, 8) REG_VAR(KIND, VAR, float, 0, 128, 16)               \
+  REG_VAR(KIND, VAR, float, 0, 256, 16) REG_VAR(KIND, VAR, float, 0, 128, 32)              \
+  REG_VAR(KIND, VAR, float, 0, 256, 32)                                                    \
+  REG_VAR(KIND, VAR, double, 1, 32, 1) REG_VAR(KIND, VAR, double, 1, 32, 2)                \
+  REG_VAR(KIND, VAR, double, 1, 32, 4) REG_VAR(KIND, VAR, double, 1, 32, 8)                \
+  REG_VAR(KIND, VAR, double, 1, 64, 8) REG_VAR(KIND, VAR, double, 1, 128, 8)               \
+  REG_VAR(KIND, VAR, double, 1, 256, 8) REG_VAR(KIND, VAR, double, 1, 128, 16)             \
+  REG_VAR(KIND, VAR, double, 1, 512, 8)
+
+void register_cn(std::vector<KernelEntry>& reg) { REG_SHAPES(K_CN_RESIDENT, VAR_CN) }
+
+}  // namespace burgers

@@ -1,0 +1,321 @@
+// btcs_kernel.cuh -- the resident implicit-step kernel (lagged BTCS and the
+// variants that solve the same tridiagonal shape), instantiated by btcs.cu,
+// btcs_cn.cu, btcs_picard.cu and btcs_newton.cu.
+#pragma once
+
+#include "btcs_common.cuh"
+#include "common.cuh"
+#include "kernels.h"
+
+namespace burgers {
+
+enum : int { VAR_BTCS = 0, VAR_CN = 1, VAR_PICARD = 2, VAR_NEWTON = 3 };
+
+// Dynamic shared memory of k_btcs_resident: the state (and FP32 Kahan term)
+// per node, plus e = w - u^n for the iterating variants.
+template <typename T, int NT, int C, int VAR>
+constexpr size_t btcs_dsm() {
+  return sizeof(T) * size_t(NT) * size_t(C) *
+         ((Kahan<T>::on ? 2 : 1) + ((VAR == VAR_PICARD || VAR == VAR_NEWTON) ? 1 : 0));
+}
+
+
+// Advances the row held by this CTA `nsteps` BTCS steps; thread t owns nodes
+// [tC, tC + C).
+//
+// Increment form: with a = u^n, A(u^n) u^n = u^n - Delta(u^n) where Delta is the
+// explicit forward-Euler increment of the same r, s (Eq. 21), so the step is
+//     A(u^n) delta = Delta(u^n),   u^{n+1} = u^n + delta,
+// the same solution as A u^{n+1} = u^n in exact arithmetic. Solving for the
+// small increment instead of the full state keeps the FP32 solve error
+// proportional to |delta| rather than |u|. Dirichlet end rows and padding rows
+// are identity rows with a zero increment.
+//
+// The row state lives in shared memory, laid out [j][thread] so a warp's
+// accesses are conflict-free, and the elimination holds only its three
+// coefficient arrays in registers. FP32 adds u + delta with Kahan compensation
+// (the term lo per node, also in shared memory): BTCS steps are long, so an
+// increment can be a sizeable part of u and must be compensated every step.
+//
+// Two barriers per solve. Each thread publishes the reduced-system data of its
+// chunk; warp 0 forms the reduced rows, solves them, and also computes the
+// value every chunk's first and last node will have for the next solve (the
+// owner computes the same numbers from the same operands), so the neighbour
+// values need no exchange of their own.
+//
+// VAR selects the implicit scheme; every variant solves tridiagonal systems
+// of this shape in increment form:
+//   VAR_BTCS    one lagged solve (above).
+//   VAR_CN      Crank-Nicolson, convecting velocity lagged at u^n:
+//               (I - dt/2 L) delta = dt L u^n, i.e. the BTCS rows with r/2,
+//               s/2 and the full forward-Euler increment as right-hand side.
+//   VAR_PICARD  `iters` Picard iterations A(w) w' = u^n: with w = u^n + e,
+//               A(w) delta = Delta(w) - e, e += delta (coefficients from w).
+//   VAR_NEWTON  `iters` Newton-Raphson iterations on the residual F of Eq. 11
+//               (central convection, Eq. 10-14): J(w) delta = -F(w) with
+//               J rows l = -r/2 w_i - s, d = 1 + r/2 (w_{i+1} - w_{i-1}) + 2s,
+//               c = r/2 w_i - s, and -F_i = -e_i - r/2 w_i (w_{i+1} - w_{i-1})
+//               + s (w_{i+1} - 2 w_i + w_{i-1}).
+// The iterating variants keep e = w - u^n per node in shared memory (es) and
+// add it to u^n, compensated, after the last iteration. The Newton Jacobian is
+// not an M-matrix in general (central convection): |l| + |c| = max(2s, r|w_i|)
+// and d >= 1 + 2s - r max|w|, so it is strictly diagonally dominant while
+// r max|w| < 1/2.
+template <typename T, int NT, int C, bool EXACT, int BCT, int VAR>
+__device__ __forceinline__ void btcs_steps(int64_t nsteps, int iters, T r, T s, int n,
+                                           BtcsShared<T, NT>& sm, T* hfirst, T* hlast, T* us,
+                                           T* lo, T* es) {
+  constexpr bool ITER = VAR == VAR_PICARD || VAR == VAR_NEWTON;
+  constexpr bool PER = BCT == BC_PERIODIC;
+  constexpr int Q = NT / 32;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int tl = EXACT ? NT - 1 : (n - 1) / C;  // chunk holding node n-1
+  const int jstar = n - 1 - tid * C;              // local index of node n-1
+  const int je = EXACT ? C - 1 : (jstar < C ? jstar : C - 1);  // chunk end row
+  // matrix coefficients (Crank-Nicolson: half of the step's r and s)
+  const T rm = VAR == VAR_CN ? T(0.5) * r : r, smat = VAR == VAR_CN ? T(0.5) * s : s;
+  const T ds1 = T(1) + T(2) * smat;
+  const T hr = T(0.5) * r;
+  const int nit = ITER ? iters : 1;
+  // the current iterate (u^n itself for the single-solve variants)
+  auto uval = [&](int j, int t) -> T {
+    if constexpr (ITER) return us[j * NT + t] + es[j * NT + t];
+    else return us[j * NT + t];
+  };
+  // value of node j of chunk t for the next solve, from this solve's
+  // increment (the owner's arithmetic)
+  auto next_u = [&](int j, int t, T delta, bool last) -> T {
+    T inc = delta;
+    if constexpr (ITER) {
+      inc = es[j * NT + t] + delta;
+      if (!last) return us[j * NT + t] + inc;
+    }
+    T l0 = T(0);
+    if constexpr (Kahan<T>::on) l0 = lo[j * NT + t];
+    return comp_add(us[j * NT + t], inc, l0);
+  };
+  T ch[C], ah[C], dd[C];
+  for (int64_t step = 0; step < nsteps; ++step) {
+  if constexpr (ITER) {
+#pragma unroll
+    for (int j = 0; j < C; ++j) es[j * NT + tid] = T(0);
+  }
+  for (int it = 0; it < nit; ++it) {
+    const bool last = it + 1 == nit;
+    T left = T(0), right = T(0);
+    if (tid > 0) left = hlast[tid - 1];
+    else if constexpr (PER) left = hlast[tl];
+    if (tid < tl) right = hfirst[tid + 1];
+    else if constexpr (PER) right = hfirst[0];
+    // ---- assembly of rows and right-hand sides fused with the forward sweep
+    T chp = T(0), ahp = T(-1), dhp = T(0);
+    T ul = left, a = uval(0, tid);
+#pragma unroll
+    for (int j = 0; j < C; ++j) {
+      const T an = (j + 1 < C) ? uval(j + 1, tid) : right;
+      T ur = an;
+      if constexpr (!EXACT) {
+        if (j == jstar) ur = right;
+      }
+      T l, c, d, rhs;
+      if constexpr (VAR == VAR_NEWTON) {
+        const T e = es[j * NT + tid];
+        const T ha = hr * a;
+        l = -ha - s;
+        c = ha - s;
+        d = tfma(hr, ur - ul, ds1);
+        rhs = tfma(s, (ur - a) - (a - ul), tfma(-ha, ur - ul, -e));
+      } else {
+        const T ra = rm * a;
+        l = -smat - tmax(ra, T(0));
+        c = tmin(ra, T(0)) - smat;
+        d = ds1 + tabs(ra);
+        // explicit increment (Eq. 21) from the same coefficients: -c (ur - a) + l (a - ul)
+        rhs = tfma(l, a - ul, -c * (ur - a));
+        if constexpr (VAR == VAR_CN) rhs = T(2) * rhs;  // the full step's increment
+        if constexpr (VAR == VAR_PICARD) rhs = rhs - es[j * NT + tid];
+      }
+      bool ident = false;
+      if constexpr (BCT == BC_DIRICHLET) {
+        if constexpr (EXACT)
+          ident = (j == 0 && tid == 0) || (j == C - 1 && tid == NT - 1);
+        else
+          ident = (j == 0 && tid == 0) || j == jstar;
+      }
+      if constexpr (!EXACT) {
+        if (j > jstar) ident = true;
+      }
+      if (ident) { l = T(0); c = T(0); d = T(1); rhs = T(0); }
+      const T inv = recip(tfma(-l, chp, d));
+      const T li = l * inv;
+      chp = c * inv;
+      ahp = -li * ahp;
+      dhp = tfma(-li, dhp, rhs * inv);
+      ch[j] = chp;
+      ah[j] = ahp;
+      dd[j] = dhp;
+      ul = a;
+      a = an;
+    }
+    T e_ch = T(0), e_ah = T(0), e_dh = T(0);
+    if constexpr (EXACT) {
+      e_ch = ch[C - 1]; e_ah = ah[C - 1]; e_dh = dd[C - 1];
+    } else {
+#pragma unroll
+      for (int j = 0; j < C; ++j)
+        if (j == je) { e_ch = ch[j]; e_ah = ah[j]; e_dh = dd[j]; }
+    }
+    // ---- backward sweep: (delta, alpha, gamma) into (dd, ah, ch)
+    T cd = T(0), ca = T(0), cg = T(-1);
+    if constexpr (EXACT) {
+      dd[C - 1] = T(0); ah[C - 1] = T(0); ch[C - 1] = T(-1);
+#pragma unroll
+      for (int j = C - 2; j >= 0; --j) {
+        const T cj = ch[j];
+        cd = tfma(-cj, cd, dd[j]);
+        ca = tfma(-cj, ca, ah[j]);
+        cg = -cj * cg;
+        dd[j] = cd; ah[j] = ca; ch[j] = cg;
+      }
+    } else {
+#pragma unroll
+      for (int j = C - 1; j >= 0; --j) {
+        const T cj = ch[j];
+        T nd = tfma(-cj, cd, dd[j]);
+        T na = tfma(-cj, ca, ah[j]);
+        T ng = -cj * cg;
+        const bool past = j > je, at = j == je;
+        if (past || at) { nd = T(0); na = T(0); ng = at ? T(-1) : T(0); }
+        dd[j] = nd; ah[j] = na; ch[j] = ng;
+        if (past || at) { cd = T(0); ca = T(0); cg = T(-1); }
+        else { cd = nd; ca = na; cg = ng; }
+      }
+    }
+    // ---- this chunk's first-row and end-row relations
+    sm.rd[sk(tid)] = dd[0];
+    sm.ra[sk(tid)] = ah[0];
+    sm.rg[sk(tid)] = ch[0];
+    {
+      const int si = sk(tid);
+      sm.A[si] = e_ah;
+      sm.Cc[si] = e_ch;
+      sm.D[si] = e_dh;
+    }
+    __syncthreads();
+    if (warp == 0) {
+      // reduced row of each of this lane's chunks: end row of chunk t with the
+      // first-row relation of chunk t + 1 substituted (chunk 0 after the last)
+#pragma unroll
+      for (int q = 0; q < Q; ++q) {
+        const int t = lane * Q + q, i = sk(t);
+        T A = T(0), B = T(1), Cc = T(0), D = T(0);
+        if (t <= tl) {
+          const int nx = (t == tl) ? 0 : t + 1;
+          const T ech = sm.Cc[i];
+          A = sm.A[i];
+          B = T(1) - ech * sm.ra[sk(nx)];
+          Cc = -ech * sm.rg[sk(nx)];
+          D = tfma(-ech, sm.rd[sk(nx)], sm.D[i]);
+        }
+        sm.A[i] = A; sm.B[i] = B; sm.Cc[i] = Cc; sm.D[i] = D; sm.U[i] = T(0);
+      }
+      __syncwarp();
+      reduced_solve<T, NT, PER>(sm, tl, lane);
+      __syncwarp();
+      // next step's first and last node of each chunk
+#pragma unroll
+      for (int q = 0; q < Q; ++q) {
+        const int t = lane * Q + q;
+        if (t <= tl) {
+          const T Xt = sm.X[sk(t)];
+          T L = T(0);
+          if (t > 0) L = sm.X[sk(t - 1)];
+          else if constexpr (PER) L = sm.X[sk(tl)];
+          const int jt = (t == tl) ? (n - 1) - t * C : C - 1;  // end row of chunk t
+          const T d0 = jt == 0 ? Xt : tfma(-sm.rg[sk(t)], Xt, tfma(-sm.ra[sk(t)], L, sm.rd[sk(t)]));
+          hfirst[t] = next_u(0, t, d0, last);
+          hlast[t] = next_u(jt, t, Xt, last);
+        }
+      }
+    }
+    __syncthreads();
+    // ---- back-substitution of the increment and the update of the state
+    if (tid <= tl) {
+      T L = T(0);
+      if (tid > 0) L = sm.X[sk(tid - 1)];
+      else if constexpr (PER) L = sm.X[sk(tl)];
+      const T Xt = sm.X[sk(tid)];
+#pragma unroll
+      for (int j = 0; j < C; ++j) {
+        if (EXACT || j <= je) {
+          const T delta = (j == je) ? Xt : tfma(-ch[j], Xt, tfma(-ah[j], L, dd[j]));
+          const int o = j * NT + tid;
+          T inc = delta;
+          if constexpr (ITER) {
+            inc = es[o] + delta;
+            if (!last) {
+              es[o] = inc;
+              continue;
+            }
+          }
+          T l0 = T(0);
+          if constexpr (Kahan<T>::on) l0 = lo[o];
+          us[o] = comp_add(us[o], inc, l0);
+          if constexpr (Kahan<T>::on) lo[o] = l0;
+        }
+      }
+    }
+  }  // iterations
+  }  // steps
+}
+
+// FP32: at most 128 registers per thread, so 512 threads' worth of CTAs fit
+// on an SM (four CTAs of the 128 x 32 shape hide each other's serial phase).
+template <typename T, int NT, int C, bool EXACT, int VAR>
+__global__ void __launch_bounds__(NT, (sizeof(T) == 4 && NT <= 512) ? 512 / NT : 1)
+    k_btcs_resident(T* __restrict__ u,
+                                                      const RowDesc* __restrict__ rows, int count,
+                                                      int* __restrict__ counter) {
+  __shared__ BtcsShared<T, NT> sm;
+  __shared__ T hfirst[NT], hlast[NT];
+  __shared__ int s_item;
+  extern __shared__ __align__(16) unsigned char dsm[];
+  T* us = reinterpret_cast<T*>(dsm);                   // C * NT values
+  T* lo = us + C * NT;                                 // C * NT values (FP32)
+  T* es = us + (Kahan<T>::on ? 2 : 1) * C * NT;        // C * NT values (iterating variants)
+  const int tid = threadIdx.x;
+  for (;;) {
+    if (tid == 0) s_item = atomicAdd(counter, 1);
+    __syncthreads();
+    const int item = s_item;
+    if (item >= count) return;
+    const RowDesc rd = rows[item];
+    T* row = u + rd.offset;
+    const int base = tid * C;
+    const int n = rd.n;
+    const int tl = EXACT ? NT - 1 : (n - 1) / C;
+    const int jt = (tid == tl) ? (n - 1) - base : C - 1;
+#pragma unroll
+    for (int j = 0; j < C; ++j) {
+      const T x = (EXACT || base + j < n) ? row[base + j] : T(0);
+      us[j * NT + tid] = x;
+      if constexpr (Kahan<T>::on) lo[j * NT + tid] = T(0);
+      if (j == 0) hfirst[tid] = x;
+      if (j == jt) hlast[tid] = x;
+    }
+    __syncthreads();
+    const T r = T(rd.r), s = T(rd.s);
+    if (rd.bc == BC_PERIODIC)
+      btcs_steps<T, NT, C, EXACT, BC_PERIODIC, VAR>(rd.nsteps, rd.iters, r, s, n, sm, hfirst,
+                                                    hlast, us, lo, es);
+    else
+      btcs_steps<T, NT, C, EXACT, BC_DIRICHLET, VAR>(rd.nsteps, rd.iters, r, s, n, sm, hfirst,
+                                                     hlast, us, lo, es);
+#pragma unroll
+    for (int j = 0; j < C; ++j)
+      if (EXACT || base + j < n) row[base + j] = us[j * NT + tid];
+    __syncthreads();
+  }
+}
+
+}  // namespace burgers

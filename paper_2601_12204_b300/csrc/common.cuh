@@ -18,6 +18,8 @@ struct RowDesc {
   double ds_dnu;   // dt / dx^2 (derivative of s with respect to nu)
   int32_t n;       // nodes
   int32_t bc;      // 0 periodic, 1 Dirichlet
+  int32_t iters = 1;  // iterations per step (Picard / Newton variants)
+  int32_t pad = 0;
 };
 
 enum : int32_t { BC_PERIODIC = 0, BC_DIRICHLET = 1 };

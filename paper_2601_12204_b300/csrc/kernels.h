@@ -26,6 +26,9 @@ enum KernelKind : int32_t {
   K_EXPLICIT_STEP1 = 8,     // one explicit step per HBM pass over tiles of long rows
   K_RK4_RESIDENT = 9,       // RK4 (Eq. 22), whole row in registers
   K_RK4_STREAM = 10,        // RK4 window of a long row, K steps per HBM pass
+  K_CN_RESIDENT = 11,       // Crank-Nicolson (lagged upwind), whole row per CTA
+  K_PICARD_RESIDENT = 12,   // Picard-iterated implicit upwind, whole row per CTA
+  K_NEWTON_RESIDENT = 13,   // Newton on the Eq. 11 residual, whole row per CTA
   K_KIND_COUNT
 };
 

@@ -8,6 +8,9 @@ namespace burgers {
 
 void register_explicit(std::vector<KernelEntry>& reg);
 void register_btcs(std::vector<KernelEntry>& reg);
+void register_cn(std::vector<KernelEntry>& reg);
+void register_picard(std::vector<KernelEntry>& reg);
+void register_newton(std::vector<KernelEntry>& reg);
 void register_multilevel(std::vector<KernelEntry>& reg);
 void register_adjoint(std::vector<KernelEntry>& reg);
 
@@ -17,6 +20,9 @@ const std::vector<KernelEntry>& kernel_registry() {
   std::call_once(once, [] {
     register_explicit(reg);
     register_btcs(reg);
+    register_cn(reg);
+    register_picard(reg);
+    register_newton(reg);
     register_multilevel(reg);
     register_adjoint(reg);
   });

@@ -251,8 +251,7 @@ burgers_status burgers_autotune(burgers_ctx* ctx, int32_t scheme, const burgers_
                                 burgers_stream stream) {
   using namespace burgers;
   if (!ctx) return set_error(BURGERS_EINVAL, "ctx is NULL");
-  if (scheme != BURGERS_EXPLICIT && scheme != BURGERS_BTCS && scheme != BURGERS_RK4)
-    return set_error(BURGERS_EINVAL, "bad scheme");
+  if (!valid_scheme(scheme)) return set_error(BURGERS_EINVAL, "bad scheme");
   if (probe_steps < 1) return set_error(BURGERS_EINVAL, "probe_steps must be >= 1");
   burgers_status st = validate_batch(batch, false);
   if (st != BURGERS_OK) return st;

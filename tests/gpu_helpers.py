@@ -7,6 +7,7 @@ from paper_2601_12204_b300 import _lib as L
 from paper_2601_12204_b300.api import Batch
 
 EXPLICIT, BTCS, RK4 = L.BURGERS_EXPLICIT, L.BURGERS_BTCS, L.BURGERS_RK4
+CN, PICARD, NEWTON = L.BURGERS_CN, L.BURGERS_PICARD, L.BURGERS_NEWTON
 F32, F64 = L.BURGERS_F32, L.BURGERS_F64
 
 # Parity bars. FP64: relative L2 <= 1e-12 per row; elementwise |gpu - oracle|
@@ -22,20 +23,24 @@ def oracle_dts(ens, factor=1.0, cfl=0.4):
                      for b in range(ens.count)])
 
 
-def run_gpu(ctx, scheme, ens, dts, nsteps, dtype, u0=None):
+def run_gpu(ctx, scheme, ens, dts, nsteps, dtype, u0=None, iters=1):
     import torch
     tdt = torch.float32 if dtype == F32 else torch.float64
     b = Batch.from_ensemble(ens, dts, nsteps, dtype)
     src = ens.u0 if u0 is None else u0
     u = torch.tensor(np.asarray(src, dtype=np.float64), dtype=tdt, device="cuda")
-    ctx.advance(scheme, b, u)
+    ctx.advance(scheme, b, u, iters=iters)
     torch.cuda.synchronize()
     return u.cpu().double().numpy()
 
 
-def run_oracle(scheme, ens, dts, nsteps, threads=0):
-    f = {EXPLICIT: oracle.explicit_batch, BTCS: oracle.btcs_batch, RK4: oracle.rk4_batch}[scheme]
+def run_oracle(scheme, ens, dts, nsteps, threads=0, iters=1):
     steps = np.broadcast_to(np.asarray(nsteps, dtype=np.int64), (ens.count,))
+    if scheme in (PICARD, NEWTON):
+        f = oracle.picard_batch if scheme == PICARD else oracle.newton_batch
+        return f(ens.u0, ens.offsets, ens.ns, ens.bcs, ens.dxs, ens.nus, dts, steps, iters, threads)
+    f = {EXPLICIT: oracle.explicit_batch, BTCS: oracle.btcs_batch, RK4: oracle.rk4_batch,
+         CN: oracle.cn_batch}[scheme]
     return f(ens.u0, ens.offsets, ens.ns, ens.bcs, ens.dxs, ens.nus, dts, steps, threads)
 
 
