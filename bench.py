@@ -463,6 +463,51 @@ def extras(args, ctx, ens, u0, batches, probe, dev, world, rank):
                                "per_unit": f"{RK4_OPS:.4g} FMA-pipe FP32 instr per cell-update"}}
     del w, w64
 
+    # ---- further implicit schemes on the same ensemble (resident kernel
+    # variants): Crank-Nicolson and 3 Picard iterations at the BTCS dt; 3
+    # Newton iterations (central convection, Eq. 11) at the explicit dt on
+    # rows whose viscosity is raised to keep the cell Peclet number <= 1.5
+    # (central convection needs a resolved grid). FP32 against FP64 each.
+    ens_n = ens.subset(np.arange(ens.count))
+    for bb_ in range(ens_n.count):
+        peak = float(np.max(np.abs(ens_n.row(bb_))))
+        ens_n.nus[bb_] = max(ens_n.nus[bb_], peak * ens_n.dxs[bb_] / 1.5)
+    variants = {}
+    for name, scheme, iters, batch32 in (
+            ("cn", L.BURGERS_CN, 1, Batch.from_ensemble(ens, dt0 * BTCS_DT_FACTOR, BTCS_STEPS, F32)),
+            ("picard3", L.BURGERS_PICARD, 3,
+             Batch.from_ensemble(ens, dt0 * BTCS_DT_FACTOR, BTCS_STEPS, F32)),
+            ("newton3", L.BURGERS_NEWTON, 3, Batch.from_ensemble(ens_n, dt0, BTCS_STEPS, F32))):
+        ctx.autotune(scheme, batch32, u0, probe_steps=20)
+        w = u0.clone()
+        ctx.advance(scheme, batch32, w, iters=iters)  # warm
+        torch.cuda.synchronize()
+        w.copy_(u0)
+        a, z = ev(), ev()
+        a.record(stream)
+        ctx.advance(scheme, batch32, w, iters=iters)
+        z.record(stream)
+        torch.cuda.synchronize()
+        t32 = a.elapsed_time(z) / 1000.0
+        w64 = torch.tensor(ens.u0, dtype=torch.float64, device=dev)
+        a, z = ev(), ev()
+        a.record(stream)
+        ctx.advance(scheme, batch32.with_fields(dtype=F64), w64, iters=iters)
+        z.record(stream)
+        torch.cuda.synchronize()
+        t64 = a.elapsed_time(z) / 1000.0
+        rel, _ = ctx.rel_l2(batch32, w, w64)
+        cells = float(B_ROWS) * N_NODES * BTCS_STEPS
+        variants[name] = {"iters": iters, "steps": BTCS_STEPS, "cups": cells / t32,
+                          "fp64_cups": cells / t64,
+                          "l2_fp32_vs_fp64": {"max": float(np.max(rel)),
+                                              "median": float(np.median(rel))}}
+        del w, w64
+    variants["note"] = ("cell-updates/s counts one node advanced one step whatever the "
+                        "iterations per step; CN and Picard at 10x the CFL dt, Newton at the "
+                        "CFL dt on viscosity-raised rows (cell Peclet <= 1.5)")
+    out["implicit_variants"] = variants
+
     # ---- plain one-row-per-launch path on a subset, same kernels
     P = 64
     sub = Batch(F32, ens.offsets[:P], N_NODES, 0, ens.dxs[:P], ens.nus[:P], dt0[:P], EXPLICIT_STEPS)
