@@ -113,7 +113,10 @@ typedef enum {
   BURGERS_OPT_RESIDENT_MAX = 3,  /* rows longer than this use the streaming explicit kernel and
                                     the multi-level BTCS solver; 0 = device limit (default 0) */
   BURGERS_OPT_AUTOTUNE = 4,      /* 1: time candidate launch shapes on first use (default 0) */
-  BURGERS_OPT_LAUNCH_COUNT = 5   /* write-only reset of the launch counter (value ignored) */
+  BURGERS_OPT_LAUNCH_COUNT = 5,  /* write-only reset of the launch counter (value ignored) */
+  BURGERS_OPT_CLUSTER = 6        /* 1: BTCS rows up to 8 CTAs long stay resident in a
+                                    thread-block cluster (default 1); 0: multi-level solver.
+                                    Ignored while BURGERS_OPT_RESIDENT_MAX is set. */
 } burgers_option;
 burgers_status burgers_ctx_set(burgers_ctx* ctx, int32_t option, int64_t value);
 

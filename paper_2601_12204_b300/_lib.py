@@ -42,6 +42,7 @@ BURGERS_OPT_STREAM_K = 2
 BURGERS_OPT_RESIDENT_MAX = 3
 BURGERS_OPT_AUTOTUNE = 4
 BURGERS_OPT_LAUNCH_COUNT = 5
+BURGERS_OPT_CLUSTER = 6
 
 # numpy mirror of burgers_instance (48 bytes, natural alignment)
 INSTANCE_DTYPE = np.dtype([("offset", "<i8"), ("n", "<i4"), ("bc", "<i4"), ("dx", "<f8"),

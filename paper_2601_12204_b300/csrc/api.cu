@@ -412,8 +412,61 @@ static burgers_status build_plan(burgers_ctx* ctx, int scheme, const burgers_bat
       // ping-pong copy of the rows, plus two Kahan compensation buffers (FP32)
       p->scratch_elems = dtype == 0 ? 3 * span : span;
     } else {
-      burgers_status st = plan_multilevel(ctx, batch, longs, p);
-      if (st != BURGERS_OK) return st;
+      // rows that fit a cluster of at most 8 CTAs stay resident in its shared
+      // memory (k_btcs_cluster); longer ones go through the multi-level solver
+      std::vector<int64_t> mlrows;
+      struct CGrp {
+        int nt, c, cs;
+        std::vector<std::pair<double, int64_t>> rows;
+      };
+      std::vector<CGrp> cgroups;
+      const bool cl = scheme == BURGERS_BTCS && ctx->cluster && ctx->resident_max == 0 &&
+                      !ctx->resident_override;
+      for (int64_t b : longs) {
+        const burgers_instance& in = batch->inst[b];
+        int nt = 0, c = 0;
+        if (cl) {
+          if (dtype == 0 && in.n <= 8 * 4096) { nt = 128; c = 32; }
+          else if (dtype == 0 && in.n <= 8 * 8192) { nt = 256; c = 32; }
+        }
+        const int64_t W = int64_t(nt) * c;
+        const int cs = nt ? int((in.n + W - 1) / W) : 0;
+        if (!nt || cs < 2 || !find_kernel(K_BTCS_CLUSTER, dtype, nt, c, cs)) {
+          mlrows.push_back(b);
+          continue;
+        }
+        CGrp* g = nullptr;
+        for (CGrp& x : cgroups)
+          if (x.nt == nt && x.c == c && x.cs == cs) g = &x;
+        if (!g) {
+          cgroups.push_back(CGrp{nt, c, cs, {}});
+          g = &cgroups.back();
+        }
+        g->rows.emplace_back(double(in.n) * double(in.nsteps), b);
+      }
+      for (CGrp& g : cgroups) {
+        std::stable_sort(g.rows.begin(), g.rows.end(),
+                         [](const auto& a, const auto& b) { return a.first > b.first; });
+        const KernelEntry* k = find_kernel(K_BTCS_CLUSTER, dtype, g.nt, g.c, g.cs);
+        int begin = int(p->rows.size());
+        for (auto& pr : g.rows) p->rows.push_back(make_row(batch->inst[pr.second], iters));
+        const int cnt = int(g.rows.size());
+        // one cluster per row: grid = rows x cluster size
+        for (int i0 = 0; i0 < cnt; i0 += ctx->plain ? 1 : cnt) {
+          Launch L;
+          L.k = k;
+          L.type = LAUNCH_RESIDENT;
+          L.row_begin = begin + i0;
+          L.row_count = ctx->plain ? 1 : cnt;
+          L.grid = L.row_count * g.cs;
+          L.counter = p->ncounters++;
+          p->launches.push_back(L);
+        }
+      }
+      if (!mlrows.empty()) {
+        burgers_status st = plan_multilevel(ctx, batch, mlrows, p);
+        if (st != BURGERS_OK) return st;
+      }
     }
   }
   // device image: rows | items | counters (+ multilevel descriptors)
@@ -566,8 +619,9 @@ static burgers_status run_plan(burgers_ctx* ctx, Plan* p, void* u, cudaStream_t 
 
 static uint64_t plan_key(const burgers_ctx* ctx, int scheme, const burgers_batch* b, int iters) {
   uint64_t h = fnv1a(b->inst, sizeof(burgers_instance) * size_t(b->count));
-  int32_t hdr[8] = {scheme, b->dtype, ctx->plain ? 1 : 0, ctx->stream_k, int32_t(ctx->resident_max),
-                    int32_t(ctx->tune_version), ctx->resident_override, iters};
+  int32_t hdr[8] = {scheme, b->dtype, (ctx->plain ? 1 : 0) | (ctx->cluster ? 2 : 0), ctx->stream_k,
+                    int32_t(ctx->resident_max), int32_t(ctx->tune_version), ctx->resident_override,
+                    iters};
   return fnv1a(hdr, sizeof hdr, h);
 }
 
@@ -682,6 +736,7 @@ burgers_status burgers_ctx_set(burgers_ctx* ctx, int32_t option, int64_t value) 
       return BURGERS_OK;
     case BURGERS_OPT_AUTOTUNE: ctx->autotune = value != 0; return BURGERS_OK;
     case BURGERS_OPT_LAUNCH_COUNT: ctx->launches = 0; return BURGERS_OK;
+    case BURGERS_OPT_CLUSTER: ctx->cluster = value != 0; return BURGERS_OK;
     default: return set_error(BURGERS_EINVAL, "unknown option");
   }
 }

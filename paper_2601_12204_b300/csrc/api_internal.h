@@ -100,6 +100,7 @@ struct burgers_ctx {
   size_t smem_optin = 0;
   bool graphs = true;
   bool plain = false;
+  bool cluster = true;  // cluster-resident BTCS for rows up to 8 CTAs
   bool autotune = false;
   int stream_k = 0;
   int64_t resident_max = 0;

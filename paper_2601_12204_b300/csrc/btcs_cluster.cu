@@ -1,0 +1,464 @@
+// btcs_cluster.cu -- lagged upwind BTCS (Sec. 2.4, Eq. 23) for rows too long
+// for one CTA but short enough for a thread-block cluster: the row stays in
+// the shared memory of CS CTAs for all of its steps, as in the resident kernel.
+//
+// Three levels of the same partitioned elimination:
+//   chunk   each thread eliminates its C rows (as in btcs.cu) and leaves one
+//           reduced row per chunk in its unknown X_t (the chunk-end value);
+//   block   warp 0 of each CTA expresses the reduced unknowns of its chunks
+//           0..ti-1 through the value P before the block (the previous CTA's
+//           interface) and its own interface Y = X_ti (ti = its last chunk):
+//               X_t = y_t - alpha_t P - gamma_t Y,
+//           by solving its block with three right-hand sides at once;
+//   cluster substituting those relations into the interface rows leaves one
+//           row per CTA in Y_{k-1}, Y_k, Y_{k+1} (cyclic when periodic), which
+//           warp 0 of CTA 0 solves, one row per lane (Sherman-Morrison
+//           correction in FP64).
+// CTA 0 sends every CTA its Y and P and the new values of the nodes next to
+// its ends (computed with the owners' arithmetic from their operands), so the
+// neighbour values of the next step need no further exchange. A step costs two
+// cluster barriers and two CTA barriers. Increment form and Kahan-compensated
+// FP32 state as in btcs.cu.
+#include <cooperative_groups.h>
+
+#include <type_traits>
+
+#include "btcs_common.cuh"
+#include "common.cuh"
+#include "kernels.h"
+
+namespace cg = cooperative_groups;
+
+namespace burgers {
+
+// What each CTA contributes to the cluster system (written into CTA 0).
+template <typename T>
+struct ClusterSlot {
+  T eah, ech, edh;      // end relation of the interface chunk
+  T rd0, ra0, rg0;      // first-row relation of chunk 0
+  T yl, al, gl;         // block relation of chunk ti - 1 (when ti > 0)
+  T y0, a0, g0;         // block relation of chunk 0 (when ti > 0)
+  T uf, lf;             // state (and Kahan term) of the CTA's first node
+  T ul, ll;             // ... of its last node (end of chunk ti)
+  int ti;               // interface chunk
+  int jf;               // end row of chunk 0 (0: chunk 0 is a single node)
+};
+
+// What CTA 0 sends back to each CTA.
+template <typename T>
+struct ClusterReply {
+  T Y, P;               // own interface value and the one before the block
+  T halo_l, halo_r;     // new values of the nodes before the first / after the last
+};
+
+template <typename T, int NT>
+struct ClusterShared {
+  BtcsShared<T, NT> sm;
+  T V[NT + NT / 32];    // block right-hand side of the interface coupling
+  T Wg[NT + NT / 32];   // ... and its solution (gamma)
+  T hfirst[NT], hlast[NT];
+  ClusterSlot<T> slots[16];  // CTA 0 only
+  ClusterReply<T> reply;
+};
+
+// Block solve of warp 0: rows 0..NT-1 of sm (identity beyond the block) with
+// right-hand sides D, U and V; leaves the solutions in X, Z and Wg. Same
+// elimination as reduced_solve (per-lane rows, then cyclic reduction over
+// the 32 lanes), non-cyclic, three right-hand sides.
+template <typename T, int NT>
+__device__ __forceinline__ void block_solve3(ClusterShared<T, NT>& cs, int lane) {
+  constexpr int Q = NT / 32;
+  BtcsShared<T, NT>& sm = cs.sm;
+  const int r0 = lane * Q;
+  T chp = T(0), ahp = T(-1), dhp = T(0), uhp = T(0), vhp = T(0);
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    const int i = sk(r0 + q);
+    const T a = sm.A[i], b = sm.B[i], c = sm.Cc[i];
+    const T inv = recip(tfma(-a, chp, b));
+    const T ai = a * inv;
+    chp = c * inv;
+    ahp = -ai * ahp;
+    dhp = tfma(-ai, dhp, sm.D[i] * inv);
+    uhp = tfma(-ai, uhp, sm.U[i] * inv);
+    vhp = tfma(-ai, vhp, cs.V[i] * inv);
+    sm.Cc[i] = chp;
+    sm.A[i] = ahp;
+    sm.D[i] = dhp;
+    sm.U[i] = uhp;
+    cs.V[i] = vhp;
+  }
+  const T e_ch = chp, e_ah = ahp, e_dh = dhp, e_uh = uhp, e_vh = vhp;
+  T cd = T(0), ca = T(0), cg_ = T(-1), cu = T(0), cv = T(0);
+#pragma unroll
+  for (int q = Q - 2; q >= 0; --q) {
+    const int i = sk(r0 + q);
+    const T ch = sm.Cc[i];
+    cd = tfma(-ch, cd, sm.D[i]);
+    ca = tfma(-ch, ca, sm.A[i]);
+    cg_ = -ch * cg_;
+    cu = tfma(-ch, cu, sm.U[i]);
+    cv = tfma(-ch, cv, cs.V[i]);
+    sm.D[i] = cd;
+    sm.A[i] = ca;
+    sm.Cc[i] = cg_;
+    sm.U[i] = cu;
+    cs.V[i] = cv;
+  }
+  T nd = shfl_down(cd, 1), na = shfl_down(ca, 1), ng = shfl_down(cg_, 1);
+  T nu = shfl_down(cu, 1), nv = shfl_down(cv, 1);
+  if (lane == 31) { nd = T(0); na = T(0); ng = T(0); nu = T(0); nv = T(0); }
+  T a32 = e_ah, b32 = T(1) - e_ch * na, c32 = -e_ch * ng;
+  T d32 = tfma(-e_ch, nd, e_dh), u32 = tfma(-e_ch, nu, e_uh), v32 = tfma(-e_ch, nv, e_vh);
+  {
+    const T inv = recip(b32);
+    a32 *= inv; c32 *= inv; d32 *= inv; u32 *= inv; v32 *= inv;
+  }
+#pragma unroll
+  for (int k = 1; k < 32; k <<= 1) {
+    T am = shfl_up(a32, k), cm = shfl_up(c32, k), dm = shfl_up(d32, k);
+    T um = shfl_up(u32, k), vm = shfl_up(v32, k);
+    T ap = shfl_down(a32, k), cp = shfl_down(c32, k), dp = shfl_down(d32, k);
+    T up = shfl_down(u32, k), vp = shfl_down(v32, k);
+    if (lane < k) { am = T(0); cm = T(0); dm = T(0); um = T(0); vm = T(0); }
+    if (lane + k > 31) { ap = T(0); cp = T(0); dp = T(0); up = T(0); vp = T(0); }
+    const T inv = recip(T(1) - a32 * cm - c32 * ap);
+    const T na2 = -a32 * am * inv, nc2 = -c32 * cp * inv;
+    d32 = (d32 - a32 * dm - c32 * dp) * inv;
+    u32 = (u32 - a32 * um - c32 * up) * inv;
+    v32 = (v32 - a32 * vm - c32 * vp) * inv;
+    a32 = na2;
+    c32 = nc2;
+  }
+  T YL = shfl_up(d32, 1), UL = shfl_up(u32, 1), VL = shfl_up(v32, 1);
+  if (lane == 0) { YL = T(0); UL = T(0); VL = T(0); }
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    const int i = sk(r0 + q);
+    T y = d32, z = u32, w = v32;
+    if (q < Q - 1) {
+      y = tfma(-sm.Cc[i], d32, tfma(-sm.A[i], YL, sm.D[i]));
+      z = tfma(-sm.Cc[i], u32, tfma(-sm.A[i], UL, sm.U[i]));
+      w = tfma(-sm.Cc[i], v32, tfma(-sm.A[i], VL, cs.V[i]));
+    }
+    sm.X[i] = y;
+    sm.Z[i] = z;
+    cs.Wg[i] = w;
+  }
+}
+
+// Warp 0 of CTA 0: the cluster system in the interface values Y_k, one row
+// per lane (lanes >= CS carry identity rows), solved by cyclic reduction over
+// the lanes; the cyclic corners are split off by Sherman-Morrison with the
+// correction factor in FP64 (as in the CTA-level solve). Lane k then sends CTA
+// k its Y and P and the new values of the nodes next to its ends. Dirichlet
+// rows have identity rows at the row's ends, so the first block has no left
+// neighbour (P = 0) and the system is plain.
+template <typename T, int NT, int CS>
+__device__ __forceinline__ void cluster_solve(ClusterShared<T, NT>& cs, bool per, int lane,
+                                              cg::cluster_group& cluster) {
+  const bool on = lane < CS;
+  const int k = on ? lane : 0;
+  const ClusterSlot<T>& s = cs.slots[k];
+  const ClusterSlot<T>& sn = cs.slots[(k + 1) % CS];
+  T a = T(0), b = T(1), c = T(0), d = T(0), uu = T(0);
+  if (on) {
+    const T A = s.eah, B = T(1) - s.ech * sn.ra0, C = -s.ech * sn.rg0;
+    const T D = tfma(-s.ech, sn.rd0, s.edh);
+    T pa = A, pb = T(0), pd = T(0);
+    if (s.ti > 0) { pa = -A * s.al; pb = -A * s.gl; pd = A * s.yl; }
+    T qa = T(0), qb = C, qd = T(0);
+    if (sn.ti > 0) { qa = -C * sn.a0; qb = -C * sn.g0; qd = C * sn.y0; }
+    a = pa;
+    b = B + pb + qa;
+    c = qb;
+    d = D - pd - qd;
+  }
+  // Sherman-Morrison split of the corners: gamma = -b_0, fa = a_0 / gamma
+  T fa = T(0);
+  if (per) {
+    const T gam = -shfl(b, 0);
+    fa = shfl(a, 0) / gam;
+    const T cl = shfl(c, CS - 1);
+    if (lane == 0) { b -= gam; uu = gam; }
+    if (lane == CS - 1) { b -= cl * fa; uu = cl; }
+  }
+  if (lane == 0) a = T(0);
+  if (lane >= CS - 1) c = T(0);
+  // cyclic reduction over the lanes (rows normalised to a unit diagonal)
+  {
+    const T inv = T(1) / b;
+    a *= inv; c *= inv; d *= inv; uu *= inv;
+  }
+#pragma unroll
+  for (int st = 1; st < 32; st <<= 1) {
+    T am = shfl_up(a, st), cm = shfl_up(c, st), dm = shfl_up(d, st), um = shfl_up(uu, st);
+    T ap = shfl_down(a, st), cp = shfl_down(c, st), dp = shfl_down(d, st), up = shfl_down(uu, st);
+    if (lane < st) { am = T(0); cm = T(0); dm = T(0); um = T(0); }
+    if (lane + st > 31) { ap = T(0); cp = T(0); dp = T(0); up = T(0); }
+    const T inv = T(1) / (T(1) - a * cm - c * ap);
+    const T na = -a * am * inv, nc = -c * cp * inv;
+    d = (d - a * dm - c * dp) * inv;
+    uu = (uu - a * um - c * up) * inv;
+    a = na;
+    c = nc;
+  }
+  T Y = d;
+  if (per) {
+    const double fd = double(fa);
+    const double vy = fma(fd, double(shfl(d, CS - 1)), double(shfl(d, 0)));
+    const double vz = fma(fd, double(shfl(uu, CS - 1)), double(shfl(uu, 0)));
+    const T fac = T(vy / (1.0 + vz));
+    Y = tfma(-fac, uu, d);
+  }
+  // P of block k is the interface before it; new first / last node values
+  T P = shfl(Y, (lane + CS - 1) % CS);
+  if (!per && lane == 0) P = T(0);
+  T first = T(0), last = T(0);
+  if (on) {
+    const T X0 = s.ti > 0 ? tfma(-s.g0, Y, tfma(-s.a0, P, s.y0)) : Y;
+    const T d0 = s.jf == 0 ? X0 : tfma(-s.rg0, X0, tfma(-s.ra0, P, s.rd0));
+    T lf = s.lf, ll = s.ll;
+    first = comp_add(s.uf, d0, lf);
+    last = comp_add(s.ul, Y, ll);
+  }
+  const T last_prev = shfl(last, (lane + CS - 1) % CS);
+  const T first_next = shfl(first, (lane + 1) % CS);
+  if (on) {
+    ClusterReply<T>* rp = cluster.map_shared_rank(&cs.reply, k);
+    rp->Y = Y;
+    rp->P = P;
+    rp->halo_l = (k > 0 || per) ? last_prev : T(0);
+    rp->halo_r = (k + 1 < CS || per) ? first_next : T(0);
+  }
+}
+
+// One cluster per row: CTA k holds nodes [k W, min((k+1) W, n)), W = NT*C,
+// thread t its chunk of C nodes. Rows have (CS-1) W < n <= CS W.
+template <typename T, int NT, int C, int CS>
+__global__ void __cluster_dims__(CS, 1, 1)
+__launch_bounds__(NT, (sizeof(T) == 4 && NT <= 512) ? 512 / NT : 1)
+    k_btcs_cluster(T* __restrict__ u, const RowDesc* __restrict__ rows, int count,
+                   int* __restrict__ counter) {
+  (void)counter;
+  constexpr int W = NT * C;
+  constexpr int Q = NT / 32;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int rank = int(cluster.block_rank());
+  const int item = int(blockIdx.x) / CS;
+  extern __shared__ __align__(16) unsigned char dsm[];
+  __shared__ ClusterShared<T, NT> cs;
+  BtcsShared<T, NT>& sm = cs.sm;
+  T* us = reinterpret_cast<T*>(dsm);  // C * NT values
+  T* lo = us + C * NT;                // C * NT values (FP32)
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const bool valid = item < count;    // grid is count * CS: always true
+  const RowDesc rd = rows[valid ? item : 0];
+  const int n = rd.n;
+  const bool per = rd.bc == BC_PERIODIC;
+  const bool lastcta = rank == CS - 1;
+  const int nc = lastcta ? n - rank * W : W;  // nodes of this CTA
+  const int tl = (nc - 1) / C;                // its last chunk (the interface)
+  const int jstar = nc - 1 - tid * C;         // local index of the CTA's last node
+  const int je = jstar < C ? jstar : C - 1;   // end row of this chunk
+  T* row = u + rd.offset + int64_t(rank) * W;
+  // ---- load, publish the chunk edges and this CTA's ends to its neighbours
+#pragma unroll
+  for (int j = 0; j < C; ++j) {
+    const int li = tid * C + j;
+    const T x = li < nc ? row[li] : T(0);
+    us[j * NT + tid] = x;
+    if constexpr (Kahan<T>::on) lo[j * NT + tid] = T(0);
+    if (j == 0) cs.hfirst[tid] = x;
+    if (j == je) cs.hlast[tid] = x;
+  }
+  __syncthreads();
+  cluster.sync();  // every CTA of the cluster runs before any addresses another's memory
+  if (tid == 0) {
+    const int kl = rank > 0 ? rank - 1 : CS - 1, kr = rank + 1 < CS ? rank + 1 : 0;
+    cluster.map_shared_rank(&cs.reply, kr)->halo_l = cs.hlast[tl];
+    cluster.map_shared_rank(&cs.reply, kl)->halo_r = cs.hfirst[0];
+  }
+  cluster.sync();
+  const T r = T(rd.r), s = T(rd.s), ds1 = T(1) + T(2) * s;
+  T ch[C], ah[C], dd[C];
+  for (int64_t step = 0; step < rd.nsteps; ++step) {
+    const T halo_l = cs.reply.halo_l, halo_r = cs.reply.halo_r;
+    T left = tid > 0 ? cs.hlast[tid - 1] : halo_l;
+    T right = tid < tl ? cs.hfirst[tid + 1] : halo_r;
+    // ---- assembly fused with the forward sweep (rows as in btcs.cu); chunks
+    // with no padding and no Dirichlet end row take the branch-free path
+    const bool plainchunk = je == C - 1 && jstar >= C - 1 &&
+                            (per || !((rank == 0 && tid == 0) || (lastcta && tid == tl)));
+    T e_ch = T(0), e_ah = T(0), e_dh = T(0);
+    auto sweep = [&](auto full_tag) {
+      constexpr bool FULL = decltype(full_tag)::value;
+      T chp = T(0), ahp = T(-1), dhp = T(0);
+      T ul = left, a = us[tid];
+#pragma unroll
+      for (int j = 0; j < C; ++j) {
+        const T an = (j + 1 < C) ? us[(j + 1) * NT + tid] : right;
+        const T ur = (FULL || j != jstar) ? an : right;
+        const T ra = r * a;
+        T l = -s - tmax(ra, T(0));
+        T c = tmin(ra, T(0)) - s;
+        T d = ds1 + tabs(ra);
+        T rhs = tfma(l, a - ul, -c * (ur - a));
+        if constexpr (!FULL) {
+          bool ident = j > jstar;  // padding of the row's last CTA
+          if (!per) ident = ident || (rank == 0 && tid == 0 && j == 0) || (lastcta && j == jstar);
+          if (ident) { l = T(0); c = T(0); d = T(1); rhs = T(0); }
+        }
+        const T inv = recip(tfma(-l, chp, d));
+        const T li = l * inv;
+        chp = c * inv;
+        ahp = -li * ahp;
+        dhp = tfma(-li, dhp, rhs * inv);
+        ch[j] = chp;
+        ah[j] = ahp;
+        dd[j] = dhp;
+        ul = a;
+        a = an;
+      }
+      if constexpr (FULL) {
+        e_ch = ch[C - 1]; e_ah = ah[C - 1]; e_dh = dd[C - 1];
+        T cd = T(0), ca = T(0), cgm = T(-1);
+        dd[C - 1] = T(0); ah[C - 1] = T(0); ch[C - 1] = T(-1);
+#pragma unroll
+        for (int j = C - 2; j >= 0; --j) {
+          const T cj = ch[j];
+          cd = tfma(-cj, cd, dd[j]);
+          ca = tfma(-cj, ca, ah[j]);
+          cgm = -cj * cgm;
+          dd[j] = cd; ah[j] = ca; ch[j] = cgm;
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < C; ++j)
+          if (j == je) { e_ch = ch[j]; e_ah = ah[j]; e_dh = dd[j]; }
+        T cd = T(0), ca = T(0), cgm = T(-1);
+#pragma unroll
+        for (int j = C - 1; j >= 0; --j) {
+          const T cj = ch[j];
+          T nd = tfma(-cj, cd, dd[j]);
+          T na = tfma(-cj, ca, ah[j]);
+          T ng = -cj * cgm;
+          const bool past = j > je, at = j == je;
+          if (past || at) { nd = T(0); na = T(0); ng = at ? T(-1) : T(0); }
+          dd[j] = nd; ah[j] = na; ch[j] = ng;
+          if (past || at) { cd = T(0); ca = T(0); cgm = T(-1); }
+          else { cd = nd; ca = na; cgm = ng; }
+        }
+      }
+    };
+    if (plainchunk) sweep(std::true_type{});
+    else sweep(std::false_type{});
+    sm.rd[sk(tid)] = dd[0];
+    sm.ra[sk(tid)] = ah[0];
+    sm.rg[sk(tid)] = ch[0];
+    sm.A[sk(tid)] = e_ah;
+    sm.Cc[sk(tid)] = e_ch;
+    sm.D[sk(tid)] = e_dh;
+    __syncthreads();
+    if (warp == 0) {
+      // block rows of chunks 0..tl-1 (the interface row tl is the cluster's)
+      T s_eah = T(0), s_ech = T(0), s_edh = T(0);
+      if (lane == 0) { s_eah = sm.A[sk(tl)]; s_ech = sm.Cc[sk(tl)]; s_edh = sm.D[sk(tl)]; }
+      __syncwarp();
+#pragma unroll
+      for (int q = 0; q < Q; ++q) {
+        const int t = lane * Q + q, i = sk(t);
+        T A = T(0), B = T(1), Cc = T(0), D = T(0), Uv = T(0), Vv = T(0);
+        if (t < tl) {
+          const T ech = sm.Cc[i];
+          A = sm.A[i];
+          B = T(1) - ech * sm.ra[sk(t + 1)];
+          Cc = -ech * sm.rg[sk(t + 1)];
+          D = tfma(-ech, sm.rd[sk(t + 1)], sm.D[i]);
+          if (t == 0) { Uv = A; A = T(0); }
+          if (t == tl - 1) { Vv = Cc; Cc = T(0); }
+        }
+        __syncwarp();
+        sm.A[i] = A; sm.B[i] = B; sm.Cc[i] = Cc; sm.D[i] = D; sm.U[i] = Uv; cs.V[i] = Vv;
+      }
+      __syncwarp();
+      block_solve3<T, NT>(cs, lane);
+      __syncwarp();
+      if (lane == 0) {
+        ClusterSlot<T> sl;
+        sl.eah = s_eah; sl.ech = s_ech; sl.edh = s_edh;
+        sl.rd0 = sm.rd[sk(0)]; sl.ra0 = sm.ra[sk(0)]; sl.rg0 = sm.rg[sk(0)];
+        sl.yl = tl > 0 ? sm.X[sk(tl - 1)] : T(0);
+        sl.al = tl > 0 ? sm.Z[sk(tl - 1)] : T(0);
+        sl.gl = tl > 0 ? cs.Wg[sk(tl - 1)] : T(0);
+        sl.y0 = sm.X[sk(0)]; sl.a0 = sm.Z[sk(0)]; sl.g0 = cs.Wg[sk(0)];
+        const int jl = nc - 1 - tl * C;  // end row of the interface chunk
+        sl.uf = us[0];
+        sl.ul = us[jl * NT + tl];
+        sl.lf = T(0);
+        sl.ll = T(0);
+        if constexpr (Kahan<T>::on) { sl.lf = lo[0]; sl.ll = lo[jl * NT + tl]; }
+        sl.ti = tl;
+        sl.jf = tl == 0 ? jl : C - 1;
+        *cluster.map_shared_rank(&cs.slots[rank], 0) = sl;
+      }
+    }
+    cluster.sync();
+    if (rank == 0 && warp == 0) cluster_solve<T, NT, CS>(cs, per, lane, cluster);
+    cluster.sync();
+    // ---- chunk-end values from the block relations, back-substitution
+    const T Y = cs.reply.Y, P = cs.reply.P;
+    if (tid <= tl) {
+      auto xend = [&](int t) -> T {
+        return t < tl ? tfma(-cs.Wg[sk(t)], Y, tfma(-sm.Z[sk(t)], P, sm.X[sk(t)])) : Y;
+      };
+      const T Xt = xend(tid);
+      const T L = tid > 0 ? xend(tid - 1) : P;
+      auto update = [&](auto full_tag) {
+        constexpr bool FULL = decltype(full_tag)::value;
+        const int jend = FULL ? C - 1 : je;
+#pragma unroll
+        for (int j = 0; j < C; ++j) {
+          if (FULL || j <= jend) {
+            const T delta = (j == jend) ? Xt : tfma(-ch[j], Xt, tfma(-ah[j], L, dd[j]));
+            const int o = j * NT + tid;
+            T l0 = T(0);
+            if constexpr (Kahan<T>::on) l0 = lo[o];
+            const T nv = comp_add(us[o], delta, l0);
+            us[o] = nv;
+            if constexpr (Kahan<T>::on) lo[o] = l0;
+            if (j == 0) cs.hfirst[tid] = nv;
+            if (j == jend) cs.hlast[tid] = nv;
+          }
+        }
+      };
+      if (plainchunk) update(std::true_type{});
+      else update(std::false_type{});
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int j = 0; j < C; ++j) {
+    const int li = tid * C + j;
+    if (li < nc) row[li] = us[j * NT + tid];
+  }
+  cluster.sync();  // no CTA leaves while another may still address its memory
+}
+
+#define REG_CLUSTER(T, DT, NT, C, CS)                                                       \
+  reg.push_back({K_BTCS_CLUSTER, DT, NT, C, CS,                                             \
+                 reinterpret_cast<const void*>(&k_btcs_cluster<T, NT, C, CS>),             \
+                 sizeof(T) * size_t(NT) * C * (Kahan<T>::on ? 2 : 1)});
+#define REG_CLUSTERS(T, DT, NT, C)                                                          \
+  REG_CLUSTER(T, DT, NT, C, 2) REG_CLUSTER(T, DT, NT, C, 3) REG_CLUSTER(T, DT, NT, C, 4)    \
+  REG_CLUSTER(T, DT, NT, C, 5) REG_CLUSTER(T, DT, NT, C, 6) REG_CLUSTER(T, DT, NT, C, 7)    \
+  REG_CLUSTER(T, DT, NT, C, 8)
+
+// FP32 only: FP64 rows are limited by the FP64 pipe, where the multi-level
+// solver is as fast.
+void register_btcs_cluster(std::vector<KernelEntry>& reg) {
+  REG_CLUSTERS(float, 0, 256, 32)
+  REG_CLUSTERS(float, 0, 128, 32)
+}
+
+}  // namespace burgers

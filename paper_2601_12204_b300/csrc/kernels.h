@@ -29,6 +29,7 @@ enum KernelKind : int32_t {
   K_CN_RESIDENT = 11,       // Crank-Nicolson (lagged upwind), whole row per CTA
   K_PICARD_RESIDENT = 12,   // Picard-iterated implicit upwind, whole row per CTA
   K_NEWTON_RESIDENT = 13,   // Newton on the Eq. 11 residual, whole row per CTA
+  K_BTCS_CLUSTER = 14,      // lagged BTCS, row resident in a cluster of `exact` CTAs
   K_KIND_COUNT
 };
 

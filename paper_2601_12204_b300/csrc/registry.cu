@@ -11,6 +11,7 @@ void register_btcs(std::vector<KernelEntry>& reg);
 void register_cn(std::vector<KernelEntry>& reg);
 void register_picard(std::vector<KernelEntry>& reg);
 void register_newton(std::vector<KernelEntry>& reg);
+void register_btcs_cluster(std::vector<KernelEntry>& reg);
 void register_multilevel(std::vector<KernelEntry>& reg);
 void register_adjoint(std::vector<KernelEntry>& reg);
 
@@ -23,6 +24,7 @@ const std::vector<KernelEntry>& kernel_registry() {
     register_cn(reg);
     register_picard(reg);
     register_newton(reg);
+    register_btcs_cluster(reg);
     register_multilevel(reg);
     register_adjoint(reg);
   });

@@ -28,7 +28,8 @@ def ctx():
 
 def _fresh(ctx):
     for opt, val in ((L.BURGERS_OPT_RESIDENT_MAX, 0), (L.BURGERS_OPT_PLAIN, 0),
-                     (L.BURGERS_OPT_GRAPHS, 1), (L.BURGERS_OPT_STREAM_K, 0)):
+                     (L.BURGERS_OPT_GRAPHS, 1), (L.BURGERS_OPT_STREAM_K, 0),
+                     (L.BURGERS_OPT_CLUSTER, 1)):
         ctx.set(opt, val)
 
 
@@ -365,3 +366,33 @@ def test_autotune_then_parity(ctx, scheme, tmp_path):
             c2.tune_load(str(bad))
     finally:
         c2.close()
+
+
+@pytest.mark.parametrize("dtype", [F32])
+def test_cluster_btcs(ctx, dtype):
+    """BTCS rows longer than one CTA (up to 8 CTAs) resident in a thread-block
+    cluster: every cluster size, ragged last CTAs, both BCs, against the oracle
+    and against the multi-level solver."""
+    _fresh(ctx)
+    W_ = 4096
+    ns = [2 * W_ + 1, 3 * W_ - 5, 3 * W_, 4 * W_ + 33, 5 * W_ - 1, 6 * W_ + 7, 7 * W_, 8 * W_]
+    if dtype == F32:
+        ns += [9 * W_ + 3, 12 * W_, 16 * W_]
+    ens = _concat([_one(n, bc, seed=n + bc) for n in ns for bc in (0, 1)])
+    dts = oracle_dts(ens, 8.0)
+    steps = np.array([5 + (i % 7) for i in range(ens.count)])
+    got = run_gpu(ctx, BTCS, ens, dts, steps, dtype)
+    ref = run_oracle(BTCS, ens, dts, steps)
+    assert_parity(ens, got, ref, dtype, "cluster")
+    ctx.set(L.BURGERS_OPT_CLUSTER, 0)
+    try:
+        ml = run_gpu(ctx, BTCS, ens, dts, steps, dtype)
+    finally:
+        ctx.set(L.BURGERS_OPT_CLUSTER, 1)
+    assert_parity(ens, ml, ref, dtype, "multilevel")
+    ctx.set(L.BURGERS_OPT_PLAIN, 1)
+    try:
+        pl = run_gpu(ctx, BTCS, ens, dts, steps, dtype)
+    finally:
+        _fresh(ctx)
+    assert np.array_equal(pl, got)
