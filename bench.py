@@ -695,7 +695,9 @@ def serve_bench(ctx, dev, duration: float, rate: float = 20000.0, plain_seconds:
            "offered_cups": float(cells.sum()) / duration,
            "max_submit_lag_ms": 1e3 * late, "slices": stats["slices"],
            "active_max": stats["active_max"], "pool_bytes": stats["pool_bytes"],
-           "pool_used_max": stats["pool_used_max"], "slice_steps": 256, "dtype": "f32"}
+           "pool_used_max": stats["pool_used_max"], "slice_steps": 256, "dtype": "f32",
+           "worker_s": {"enqueue": stats["t_enqueue_s"], "slice_wait": stats["t_slice_s"],
+                        "copies": stats["t_copy_s"]}}
     # plain path: one request per launch, FIFO in arrival order
     ctx.set(L.BURGERS_OPT_PLAIN, 1)
     buf = torch.empty(int(ns.max()), dtype=torch.float32, device=dev)

@@ -306,7 +306,10 @@ typedef struct {
   int64_t submitted, completed, slices, active_max, pool_used_max;
   double cell_updates; /* of completed requests */
   int64_t pending, active, pool_bytes, pool_used;
-  double now_s; /* server clock */
+  double now_s;       /* server clock */
+  double t_enqueue_s; /* worker time spent planning and enqueuing slices (host) */
+  double t_slice_s;   /* worker time waiting for slices to finish on the device */
+  double t_copy_s;    /* worker time in admission and result copies */
 } burgers_serve_stats;
 
 /* Creates a server on ctx (cfg may be NULL for defaults). The pool is half

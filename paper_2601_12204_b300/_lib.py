@@ -115,7 +115,8 @@ class burgers_serve_stats(ctypes.Structure):
                 ("pool_used_max", ctypes.c_int64), ("cell_updates", ctypes.c_double),
                 ("pending", ctypes.c_int64), ("active", ctypes.c_int64),
                 ("pool_bytes", ctypes.c_int64), ("pool_used", ctypes.c_int64),
-                ("now_s", ctypes.c_double)]
+                ("now_s", ctypes.c_double), ("t_enqueue_s", ctypes.c_double),
+                ("t_slice_s", ctypes.c_double), ("t_copy_s", ctypes.c_double)]
 
 
 SIGNATURES.update({

@@ -187,16 +187,17 @@ __device__ __forceinline__ void cluster_solve(ClusterShared<T, NT>& cs, bool per
   if (lane >= CS - 1) c = T(0);
   // cyclic reduction over the lanes (rows normalised to a unit diagonal)
   {
-    const T inv = T(1) / b;
+    const T inv = recip(b);
     a *= inv; c *= inv; d *= inv; uu *= inv;
   }
+  // rows beyond CS are decoupled identities: log2(CS) levels decouple the rest
 #pragma unroll
-  for (int st = 1; st < 32; st <<= 1) {
+  for (int st = 1; st < CS; st <<= 1) {
     T am = shfl_up(a, st), cm = shfl_up(c, st), dm = shfl_up(d, st), um = shfl_up(uu, st);
     T ap = shfl_down(a, st), cp = shfl_down(c, st), dp = shfl_down(d, st), up = shfl_down(uu, st);
     if (lane < st) { am = T(0); cm = T(0); dm = T(0); um = T(0); }
     if (lane + st > 31) { ap = T(0); cp = T(0); dp = T(0); up = T(0); }
-    const T inv = T(1) / (T(1) - a * cm - c * ap);
+    const T inv = recip(T(1) - a * cm - c * ap);
     const T na = -a * am * inv, nc = -c * cp * inv;
     d = (d - a * dm - c * dp) * inv;
     uu = (uu - a * um - c * up) * inv;

@@ -237,6 +237,7 @@ static void worker_loop(burgers_server* sv) {
       // host copies of the admitted u0 (their vectors are not touched again)
     }
     // ---- copy the new requests' u0 into their slots
+    double tw0 = now_s();
     cudaError_t e = cudaSuccess;
     for (Req* q : admitted) {
       e = cudaMemcpyAsync(static_cast<char*>(sv->pool) + q->off, q->u0.data(), q->u0.size(),
@@ -247,6 +248,7 @@ static void worker_loop(burgers_server* sv) {
       fail_all(sv, cuda_error(e, "serve admission copy"), burgers_last_error());
       return;
     }
+    double tw1 = now_s();
     // ---- one slice over every active request
     ie.clear(); ib.clear(); in_e.clear(); in_b.clear();
     {
@@ -274,7 +276,9 @@ static void worker_loop(burgers_server* sv) {
       e = cudaEventRecord(sv->ev, sv->stream);
       if (e != cudaSuccess) st = cuda_error(e, "serve record");
     }
+    double tw2 = now_s();
     if (st == BURGERS_OK) st = wait_event(sv, sv->cfg.slice_timeout_s);
+    double tw3 = now_s();
     if (st != BURGERS_OK) {
       fail_all(sv, st, burgers_last_error());
       return;
@@ -289,10 +293,14 @@ static void worker_loop(burgers_server* sv) {
         if (q->done_steps >= q->r.nsteps) finished.push_back(q);
       }
       sv->stats.slices += 1;
+      sv->stats.t_copy_s += tw1 - tw0;
+      sv->stats.t_enqueue_s += tw2 - tw1;
+      sv->stats.t_slice_s += tw3 - tw2;
       sv->stats.active_max = std::max<int64_t>(sv->stats.active_max, int64_t(sv->active.size()));
       sv->stats.pool_used_max = std::max<int64_t>(
           sv->stats.pool_used_max, sv->short_region.used() + sv->long_region.used());
     }
+    double tw4 = now_s();
     for (Req* q : finished) {
       q->out.resize(q->u0.size());
       e = cudaMemcpyAsync(q->out.data(), static_cast<char*>(sv->pool) + q->off, q->out.size(),
@@ -312,6 +320,7 @@ static void worker_loop(burgers_server* sv) {
     }
     {
       std::lock_guard<std::mutex> lk(sv->mu);
+      sv->stats.t_copy_s += now_s() - tw4;
       const double t = now_s() - sv->t0;
       for (Req* q : finished) {
         (q->long_row ? sv->long_region : sv->short_region).release(q->off, q->bytes);
