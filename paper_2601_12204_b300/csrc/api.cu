@@ -540,6 +540,19 @@ static cudaError_t enqueue_plan(burgers_ctx* ctx, Plan* p, void* u, cudaStream_t
                                     size_t(p->ml_span) * esz, st);
     if (e != cudaSuccess) return e;
   }
+  // Resident launches are independent of each other and of the long-row
+  // sequence: spread them over the side streams (forked from and joined back
+  // into st) so that one group's tail overlaps the next group's work. The
+  // long-row launches keep their order on st.
+  int nres = 0;
+  for (const Launch& L : p->launches) nres += L.type == LAUNCH_RESIDENT ? 1 : 0;
+  const bool fan = nres > 1 && !ctx->plain;
+  bool used[burgers_ctx::kSide] = {};
+  if (fan) {
+    cudaError_t e = cudaEventRecord(ctx->fork_ev, st);
+    if (e != cudaSuccess) return e;
+  }
+  int ri = 0;
   for (const Launch& L : p->launches) {
     cudaError_t e = cudaSuccess;
     if (L.type == LAUNCH_RESIDENT) {
@@ -547,7 +560,18 @@ static cudaError_t enqueue_plan(burgers_ctx* ctx, Plan* p, void* u, cudaStream_t
       int cnt = L.row_count;
       int* ctr = counters + L.counter;
       void* args[] = {&u, &r, &cnt, &ctr};
-      e = cudaLaunchKernel(L.k->fn, dim3(L.grid), dim3(L.k->nt), args, L.k->dyn_smem, st);
+      cudaStream_t ls = st;
+      const int lane = fan ? ri % (burgers_ctx::kSide + 1) : 0;
+      ++ri;
+      if (lane > 0) {
+        ls = ctx->side[lane - 1];
+        if (!used[lane - 1]) {
+          e = cudaStreamWaitEvent(ls, ctx->fork_ev, 0);
+          if (e != cudaSuccess) return e;
+          used[lane - 1] = true;
+        }
+      }
+      e = cudaLaunchKernel(L.k->fn, dim3(L.grid), dim3(L.k->nt), args, L.k->dyn_smem, ls);
     } else if (L.type == LAUNCH_STREAM) {
       const void* src = L.to_scratch ? u : scratch;
       void* dst = L.to_scratch ? scratch : u;
@@ -562,6 +586,12 @@ static cudaError_t enqueue_plan(burgers_ctx* ctx, Plan* p, void* u, cudaStream_t
     } else {
       e = enqueue_multilevel_launch(ctx, p, L, u, st);
     }
+    if (e != cudaSuccess) return e;
+  }
+  for (int i = 0; i < burgers_ctx::kSide; ++i) {
+    if (!used[i]) continue;
+    cudaError_t e = cudaEventRecord(ctx->join_ev[i], ctx->side[i]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ctx->join_ev[i], 0);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -667,6 +697,39 @@ burgers_status advance(burgers_ctx* ctx, int scheme, const burgers_batch* batch,
 // One-off plan through caller-owned descriptor buffers (no cache, no graph):
 // the serving loop, whose batch changes every slice. The caller must not
 // reuse `ps` before the work enqueued here has consumed the upload.
+// Two uncached calls on disjoint rows of the same buffer (the serving loop's
+// explicit and BTCS slices). When at most one of the plans needs the
+// context's scratch buffers they run concurrently, the second on stream_b
+// forked from and joined back into stream_a; otherwise one after the other.
+burgers_status advance_uncached_pair(burgers_ctx* ctx, int scheme_a, const burgers_batch* a,
+                                     PlanScratch* ps_a, int scheme_b, const burgers_batch* b,
+                                     PlanScratch* ps_b, void* u_dev, cudaStream_t stream_a,
+                                     cudaStream_t stream_b, cudaEvent_t fork, cudaEvent_t join) {
+  const bool has_a = a->count > 0, has_b = b->count > 0;
+  burgers_status st = BURGERS_OK;
+  if (has_a && (st = validate_batch(a, false)) != BURGERS_OK) return st;
+  if (has_b && (st = validate_batch(b, false)) != BURGERS_OK) return st;
+  Plan pa, pb;
+  if (has_a && (st = build_plan(ctx, scheme_a, a, &pa, ps_a, stream_a)) != BURGERS_OK) return st;
+  if (has_b && (st = build_plan(ctx, scheme_b, b, &pb, ps_b, stream_a)) != BURGERS_OK) return st;
+  const bool scratch_a = pa.scratch_elems > 0 || pa.ml_ws_elems > 0;
+  const bool scratch_b = pb.scratch_elems > 0 || pb.ml_ws_elems > 0;
+  if (!has_a || !has_b || (scratch_a && scratch_b)) {
+    if (has_a && (st = run_plan(ctx, &pa, u_dev, stream_a, false)) != BURGERS_OK) return st;
+    if (has_b) st = run_plan(ctx, &pb, u_dev, stream_a, false);
+    return st;
+  }
+  cudaError_t e = cudaEventRecord(fork, stream_a);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(stream_b, fork, 0);
+  if (e != cudaSuccess) return cuda_error(e, "fork");
+  if ((st = run_plan(ctx, &pb, u_dev, stream_b, false)) != BURGERS_OK) return st;
+  if ((st = run_plan(ctx, &pa, u_dev, stream_a, false)) != BURGERS_OK) return st;
+  e = cudaEventRecord(join, stream_b);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(stream_a, join, 0);
+  if (e != cudaSuccess) return cuda_error(e, "join");
+  return BURGERS_OK;
+}
+
 burgers_status advance_uncached(burgers_ctx* ctx, int scheme, const burgers_batch* batch,
                                 void* u_dev, cudaStream_t stream, PlanScratch* ps) {
   burgers_status st = validate_batch(batch, false);
@@ -705,6 +768,12 @@ burgers_status burgers_ctx_create(int device, burgers_ctx** out) {
   if (e != cudaSuccess) return cuda_error(e, "kernel attributes");
   e = cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking);
   if (e != cudaSuccess) return cuda_error(e, "cudaStreamCreate");
+  for (int i = 0; i < burgers_ctx::kSide && e == cudaSuccess; ++i) {
+    e = cudaStreamCreateWithFlags(&ctx->side[i], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->join_ev[i], cudaEventDisableTiming);
+  }
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->fork_ev, cudaEventDisableTiming);
+  if (e != cudaSuccess) return cuda_error(e, "cudaStreamCreate");
   *out = ctx.release();
   return BURGERS_OK;
 }
@@ -715,6 +784,11 @@ void burgers_ctx_destroy(burgers_ctx* ctx) {
   cudaDeviceSynchronize();
   ctx->plans.clear();
   if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
+  for (int i = 0; i < burgers_ctx::kSide; ++i) {
+    if (ctx->side[i]) cudaStreamDestroy(ctx->side[i]);
+    if (ctx->join_ev[i]) cudaEventDestroy(ctx->join_ev[i]);
+  }
+  if (ctx->fork_ev) cudaEventDestroy(ctx->fork_ev);
   if (ctx->adj_event) cudaEventDestroy(ctx->adj_event);
   delete ctx;
 }

@@ -107,6 +107,10 @@ struct burgers_ctx {
   int tune_version = 0;
   std::atomic<int64_t> launches{0};
   cudaStream_t capture_stream = nullptr;
+  // independent resident launches of one plan overlap on these side streams
+  static constexpr int kSide = 3;
+  cudaStream_t side[kSide] = {};
+  cudaEvent_t fork_ev = nullptr, join_ev[kSide] = {};
   std::list<std::unique_ptr<burgers::Plan>> plans;
   std::map<uint64_t, burgers::TuneVal> tuned;
   burgers::DevBuf scratch;  // streaming ping-pong
@@ -152,6 +156,10 @@ burgers_status advance(burgers_ctx* ctx, int scheme, const burgers_batch* batch,
                        cudaStream_t stream, int iters = 1);
 burgers_status advance_uncached(burgers_ctx* ctx, int scheme, const burgers_batch* batch,
                                 void* u_dev, cudaStream_t stream, PlanScratch* ps);
+burgers_status advance_uncached_pair(burgers_ctx* ctx, int scheme_a, const burgers_batch* a,
+                                     PlanScratch* ps_a, int scheme_b, const burgers_batch* b,
+                                     PlanScratch* ps_b, void* u_dev, cudaStream_t stream_a,
+                                     cudaStream_t stream_b, cudaEvent_t fork, cudaEvent_t join);
 int64_t adjoint_max_n(int dtype);
 int64_t resident_capacity(const burgers_ctx* ctx, int kind, int dtype);
 int64_t resident_class(int kind, int dtype, int64_t n);

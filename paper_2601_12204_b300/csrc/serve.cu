@@ -95,13 +95,73 @@ class Region {
   int64_t total_ = 0, used_ = 0;
 };
 
+// Page-locked host buffers for request states, carved out of 64 MiB slabs
+// (grown on demand up to a cap): u0 is copied into one at submit, the device
+// copies read and write it asynchronously at full DMA rate, and the result
+// lands in the same buffer. Past the cap requests fall back to pageable
+// vectors. Not thread-safe: the server's mutex guards every call.
+class PinnedArena {
+ public:
+  static constexpr int64_t kSlab = int64_t(64) << 20;
+  static constexpr int64_t kCap = int64_t(8) << 30;
+  unsigned char* alloc(int64_t bytes) {
+    for (Slab& sl : slabs_) {
+      int64_t off;
+      if (sl.rg.alloc(bytes, &off)) return sl.base + off;
+    }
+    const int64_t size = std::max<int64_t>(kSlab, (bytes + 255) & ~int64_t(255));
+    if (total_ + size > kCap) return nullptr;
+    void* p = nullptr;
+    if (cudaHostAlloc(&p, size_t(size), cudaHostAllocDefault) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    total_ += size;
+    slabs_.push_back(Slab{static_cast<unsigned char*>(p), size, Region()});
+    Slab& sl = slabs_.back();
+    sl.rg.init(0, size);
+    int64_t off = 0;
+    sl.rg.alloc(bytes, &off);
+    return sl.base + off;
+  }
+  void reserve(int slabs) {
+    std::vector<unsigned char*> held;
+    for (int i = 0; i < slabs; ++i) {
+      unsigned char* p = alloc(kSlab);
+      if (!p) break;
+      held.push_back(p);
+    }
+    for (unsigned char* p : held) release(p, kSlab);
+  }
+  void release(unsigned char* p, int64_t bytes) {
+    for (Slab& sl : slabs_)
+      if (p >= sl.base && p < sl.base + sl.size) {
+        sl.rg.release(p - sl.base, bytes);
+        return;
+      }
+  }
+  ~PinnedArena() {
+    for (Slab& sl : slabs_) cudaFreeHost(sl.base);
+  }
+
+ private:
+  struct Slab {
+    unsigned char* base;
+    int64_t size;
+    Region rg;
+  };
+  std::vector<Slab> slabs_;
+  int64_t total_ = 0;
+};
+
 enum ReqState : int { RQ_PENDING = 0, RQ_ACTIVE = 1, RQ_DONE = 2, RQ_CANCELED = 3, RQ_FAILED = 4 };
 
 struct Req {
   uint64_t ticket = 0;
   burgers_request r{};
-  std::vector<unsigned char> u0;
-  std::vector<unsigned char> out;
+  std::vector<unsigned char> u0;   // pageable fallback of pin
+  std::vector<unsigned char> out;  // pageable fallback of pin
+  unsigned char* pin = nullptr;    // page-locked state: u0, later the result
   int state = RQ_PENDING;
   burgers_status status = BURGERS_OK;
   bool long_row = false;
@@ -119,8 +179,8 @@ struct burgers_server {
   void* pool = nullptr;
   int64_t pool_bytes = 0;
   burgers::Region short_region, long_region;
-  cudaStream_t stream = nullptr;
-  cudaEvent_t ev = nullptr;
+  cudaStream_t stream = nullptr, stream_b = nullptr;  // BTCS slices run on stream_b
+  cudaEvent_t ev = nullptr, ev_fork = nullptr, ev_join = nullptr;
   std::thread worker;
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
@@ -133,7 +193,7 @@ struct burgers_server {
   burgers_status fault = BURGERS_OK;
   std::string fault_msg;
   burgers::PlanScratch ps_explicit, ps_btcs;
-  burgers::HostBuf staging;
+  burgers::PinnedArena pinned;
   burgers_serve_stats stats{};
   double t0 = 0;
 };
@@ -240,8 +300,9 @@ static void worker_loop(burgers_server* sv) {
     double tw0 = now_s();
     cudaError_t e = cudaSuccess;
     for (Req* q : admitted) {
-      e = cudaMemcpyAsync(static_cast<char*>(sv->pool) + q->off, q->u0.data(), q->u0.size(),
-                          cudaMemcpyHostToDevice, sv->stream);
+      e = cudaMemcpyAsync(static_cast<char*>(sv->pool) + q->off,
+                          q->pin ? static_cast<const void*>(q->pin) : q->u0.data(),
+                          size_t(q->bytes), cudaMemcpyHostToDevice, sv->stream);
       if (e != cudaSuccess) break;
     }
     if (e != cudaSuccess) {
@@ -268,10 +329,10 @@ static void worker_loop(burgers_server* sv) {
     }
     burgers_batch be{sv->cfg.dtype, 0, int64_t(ie.size()), ie.data()};
     burgers_batch bb{sv->cfg.dtype, 0, int64_t(ib.size()), ib.data()};
-    burgers_status st = BURGERS_OK;
-    if (!ie.empty()) st = advance_uncached(sv->ctx, BURGERS_EXPLICIT, &be, sv->pool, sv->stream, &sv->ps_explicit);
-    if (st == BURGERS_OK && !ib.empty())
-      st = advance_uncached(sv->ctx, BURGERS_BTCS, &bb, sv->pool, sv->stream, &sv->ps_btcs);
+    burgers_status st =
+        advance_uncached_pair(sv->ctx, BURGERS_EXPLICIT, &be, &sv->ps_explicit, BURGERS_BTCS, &bb,
+                              &sv->ps_btcs, sv->pool, sv->stream, sv->stream_b, sv->ev_fork,
+                              sv->ev_join);
     if (st == BURGERS_OK) {
       e = cudaEventRecord(sv->ev, sv->stream);
       if (e != cudaSuccess) st = cuda_error(e, "serve record");
@@ -302,8 +363,12 @@ static void worker_loop(burgers_server* sv) {
     }
     double tw4 = now_s();
     for (Req* q : finished) {
-      q->out.resize(q->u0.size());
-      e = cudaMemcpyAsync(q->out.data(), static_cast<char*>(sv->pool) + q->off, q->out.size(),
+      void* dst = q->pin;
+      if (!dst) {
+        q->out.resize(size_t(q->bytes));
+        dst = q->out.data();
+      }
+      e = cudaMemcpyAsync(dst, static_cast<char*>(sv->pool) + q->off, size_t(q->bytes),
                           cudaMemcpyDeviceToHost, sv->stream);
       if (e != cudaSuccess) break;
     }
@@ -386,8 +451,12 @@ burgers_status burgers_serve_create(burgers_ctx* ctx, const burgers_serve_cfg* c
     cudaFree(sv->pool);
     return set_error(BURGERS_ENOMEM, "serve scratch: out of device memory");
   }
+  sv->pinned.reserve(16);  // 1 GiB of page-locked request buffers up front
   e = cudaStreamCreateWithFlags(&sv->stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&sv->stream_b, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sv->ev, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sv->ev_fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sv->ev_join, cudaEventDisableTiming);
   if (e != cudaSuccess) {
     cudaFree(sv->pool);
     return cuda_error(e, "serve stream");
@@ -414,10 +483,15 @@ burgers_status burgers_serve_submit(burgers_server* sv, const burgers_request* r
   q->long_row = rq->n > long_limit(sv, rq->scheme);
   const Region& rg = q->long_row ? sv->long_region : sv->short_region;
   if (q->bytes > rg.total()) return set_error(BURGERS_ENOMEM, "request larger than the pool region");
-  q->u0.assign(static_cast<const unsigned char*>(rq->u0_host),
-               static_cast<const unsigned char*>(rq->u0_host) + q->bytes);
   std::lock_guard<std::mutex> lk(sv->mu);
   if (sv->fault != BURGERS_OK) return set_error(sv->fault, "server failed: " + sv->fault_msg);
+  q->pin = sv->pinned.alloc(q->bytes);
+  if (q->pin) {
+    memcpy(q->pin, rq->u0_host, size_t(q->bytes));
+  } else {
+    q->u0.assign(static_cast<const unsigned char*>(rq->u0_host),
+                 static_cast<const unsigned char*>(rq->u0_host) + q->bytes);
+  }
   q->t_submit = now_s() - sv->t0;
   q->ticket = sv->next_ticket++;
   *ticket = q->ticket;
@@ -438,7 +512,9 @@ static burgers_status take_result(burgers_server* sv, Req* q, void* out_host,
     rs->status = q->status;
   }
   burgers_status st = q->status;
-  if (q->state == RQ_DONE && out_host) memcpy(out_host, q->out.data(), q->out.size());
+  if (q->state == RQ_DONE && out_host)
+    memcpy(out_host, q->pin ? q->pin : q->out.data(), size_t(q->bytes));
+  if (q->pin) sv->pinned.release(q->pin, q->bytes);
   sv->reqs.erase(q->ticket);
   if (st != BURGERS_OK) return set_error(st, "request did not complete");
   return BURGERS_OK;
@@ -523,7 +599,11 @@ burgers_status burgers_serve_destroy(burgers_server* sv) {
   if (sv->worker.joinable()) sv->worker.join();
   cudaSetDevice(sv->ctx->device);
   if (sv->stream) cudaStreamSynchronize(sv->stream);
+  if (sv->stream_b) cudaStreamSynchronize(sv->stream_b);
   if (sv->ev) cudaEventDestroy(sv->ev);
+  if (sv->ev_fork) cudaEventDestroy(sv->ev_fork);
+  if (sv->ev_join) cudaEventDestroy(sv->ev_join);
+  if (sv->stream_b) cudaStreamDestroy(sv->stream_b);
   if (sv->stream) cudaStreamDestroy(sv->stream);
   if (sv->pool) cudaFree(sv->pool);
   burgers_status st = sv->fault;
