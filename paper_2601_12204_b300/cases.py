@@ -27,6 +27,8 @@ def main():
     ap.add_argument("--dt-factor", type=float, default=None)
     ap.add_argument("--large", action="store_true", help="one row: sin x + 0.5 + noise")
     ap.add_argument("--stream-k", type=int, default=0)
+    ap.add_argument("--no-cluster", action="store_true",
+                    help="long BTCS rows through the multi-level solver instead of clusters")
     ap.add_argument("--repeat", type=int, default=1)
     ap.add_argument("--autotune", action="store_true", help="tune launch shapes first and print the table")
     ap.add_argument("--tune-file", default=None,
@@ -45,6 +47,8 @@ def main():
     ctx = Context(0)
     if a.stream_k:
         ctx.set(L.BURGERS_OPT_STREAM_K, a.stream_k)
+    if a.no_cluster:
+        ctx.set(L.BURGERS_OPT_CLUSTER, 0)
     u0 = torch.tensor(ens.u0, dtype=tdt, device="cuda")
     dt = ctx.cfl_dt(Batch.from_ensemble(ens, 1.0, 0, dt_code), u0, 0.4)
     fac = a.dt_factor if a.dt_factor is not None else (10.0 if a.case == "btcs" else 1.0)
