@@ -773,6 +773,12 @@ burgers_status burgers_ctx_create(int device, burgers_ctx** out) {
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->join_ev[i], cudaEventDisableTiming);
   }
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->fork_ev, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->io_h2d, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->io_d2h, cudaStreamNonBlocking);
+  for (int i = 0; i < burgers_ctx::kIoChunks && e == cudaSuccess; ++i) {
+    e = cudaEventCreateWithFlags(&ctx->io_in[i], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->io_out[i], cudaEventDisableTiming);
+  }
   if (e != cudaSuccess) return cuda_error(e, "cudaStreamCreate");
   *out = ctx.release();
   return BURGERS_OK;
@@ -789,6 +795,12 @@ void burgers_ctx_destroy(burgers_ctx* ctx) {
     if (ctx->join_ev[i]) cudaEventDestroy(ctx->join_ev[i]);
   }
   if (ctx->fork_ev) cudaEventDestroy(ctx->fork_ev);
+  for (int i = 0; i < burgers_ctx::kIoChunks; ++i) {
+    if (ctx->io_in[i]) cudaEventDestroy(ctx->io_in[i]);
+    if (ctx->io_out[i]) cudaEventDestroy(ctx->io_out[i]);
+  }
+  if (ctx->io_h2d) cudaStreamDestroy(ctx->io_h2d);
+  if (ctx->io_d2h) cudaStreamDestroy(ctx->io_d2h);
   if (ctx->adj_event) cudaEventDestroy(ctx->adj_event);
   delete ctx;
 }
@@ -1037,40 +1049,85 @@ burgers_status burgers_solve_host(burgers_ctx* ctx, int32_t scheme, const burger
   cudaError_t e = cudaSetDevice(ctx->device);
   if (e != cudaSuccess) return cuda_error(e, "cudaSetDevice");
   const size_t esz = batch->dtype == BURGERS_F32 ? 4 : 8;
+  // rows in offset order, cut into up to kIoChunks chunks of whole rows: the
+  // copy of chunk c+1 in overlaps the solve of chunk c, and the copy of chunk
+  // c out overlaps the solve of chunk c+1 (copy streams, event-ordered)
+  std::vector<int64_t> order(static_cast<size_t>(batch->count));
+  for (int64_t b = 0; b < batch->count; ++b) order[size_t(b)] = b;
+  std::sort(order.begin(), order.end(), [&](int64_t x, int64_t y) {
+    return batch->inst[x].offset < batch->inst[y].offset;
+  });
   int64_t lo = INT64_MAX, hi = 0;
-  std::vector<std::pair<int64_t, int64_t>> spans;
   for (int64_t b = 0; b < batch->count; ++b) {
     lo = std::min<int64_t>(lo, batch->inst[b].offset);
     hi = std::max<int64_t>(hi, batch->inst[b].offset + batch->inst[b].n);
-    spans.emplace_back(batch->inst[b].offset, batch->inst[b].offset + batch->inst[b].n);
-  }
-  std::sort(spans.begin(), spans.end());
-  std::vector<std::pair<int64_t, int64_t>> runs;  // merged contiguous spans
-  for (auto& sp : spans) {
-    if (!runs.empty() && runs.back().second == sp.first) runs.back().second = sp.second;
-    else runs.push_back(sp);
   }
   e = ctx->iobuf.ensure(size_t(hi - lo) * esz);
   if (e != cudaSuccess) return set_error(BURGERS_ENOMEM, "host-solve buffer: out of device memory");
-  std::vector<burgers_instance> shifted(batch->inst, batch->inst + batch->count);
-  for (auto& in : shifted) in.offset -= lo;
-  burgers_batch b2 = *batch;
-  b2.inst = shifted.data();
+  const int nch = int(std::min<int64_t>(batch->count >= 64 ? burgers_ctx::kIoChunks : 1,
+                                        batch->count));
   char* dbase = static_cast<char*>(ctx->iobuf.ptr);
   char* hbase = static_cast<char*>(u_host);
-  for (auto& rn : runs) {
-    e = cudaMemcpyAsync(dbase + (rn.first - lo) * esz, hbase + rn.first * esz,
-                        size_t(rn.second - rn.first) * esz, cudaMemcpyHostToDevice, s);
-    if (e != cudaSuccess) return cuda_error(e, "solve_host H2D");
+  // per chunk: its rows (offsets relative to lo) and merged contiguous host spans
+  std::vector<std::vector<burgers_instance>> cinst(static_cast<size_t>(nch));
+  std::vector<std::vector<std::pair<int64_t, int64_t>>> cruns(static_cast<size_t>(nch));
+  for (int c = 0; c < nch; ++c) {
+    const int64_t r0 = batch->count * c / nch, r1 = batch->count * (c + 1) / nch;
+    for (int64_t i = r0; i < r1; ++i) {
+      burgers_instance in = batch->inst[order[size_t(i)]];
+      const int64_t a = in.offset, z = in.offset + in.n;
+      auto& rn = cruns[size_t(c)];
+      if (!rn.empty() && rn.back().second == a) rn.back().second = z;
+      else rn.emplace_back(a, z);
+      in.offset -= lo;
+      cinst[size_t(c)].push_back(in);
+    }
   }
-  st = advance(ctx, scheme, &b2, dbase, s);
-  if (st != BURGERS_OK) return st;
-  for (auto& rn : runs) {
-    e = cudaMemcpyAsync(hbase + rn.first * esz, dbase + (rn.first - lo) * esz,
-                        size_t(rn.second - rn.first) * esz, cudaMemcpyDeviceToHost, s);
-    if (e != cudaSuccess) return cuda_error(e, "solve_host D2H");
+  const bool pipe = nch > 1;
+  cudaStream_t sin = pipe ? ctx->io_h2d : s, sout = pipe ? ctx->io_d2h : s;
+  if (pipe) {  // the copies start after whatever the caller queued on s
+    e = cudaEventRecord(ctx->io_out[0], s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(sin, ctx->io_out[0], 0);
+    if (e != cudaSuccess) return cuda_error(e, "solve_host order");
   }
-  e = cudaStreamSynchronize(s);
+  for (int c = 0; c < nch; ++c) {
+    for (auto& rn : cruns[size_t(c)]) {
+      e = cudaMemcpyAsync(dbase + (rn.first - lo) * esz, hbase + rn.first * esz,
+                          size_t(rn.second - rn.first) * esz, cudaMemcpyHostToDevice, sin);
+      if (e != cudaSuccess) return cuda_error(e, "solve_host H2D");
+    }
+    if (pipe) {
+      e = cudaEventRecord(ctx->io_in[c], sin);
+      if (e != cudaSuccess) return cuda_error(e, "solve_host record");
+    }
+  }
+  // consecutive chunks alternate between two compute streams so that the tail
+  // of one chunk's persistent launch overlaps the start of the next
+  for (int c = 0; c < nch; ++c) {
+    cudaStream_t sc = (pipe && (c & 1)) ? ctx->side[burgers_ctx::kSide - 1] : s;
+    if (pipe) {
+      e = cudaStreamWaitEvent(sc, ctx->io_in[c], 0);
+      if (e != cudaSuccess) return cuda_error(e, "solve_host wait");
+    }
+    burgers_batch bc = *batch;
+    bc.count = int64_t(cinst[size_t(c)].size());
+    bc.inst = cinst[size_t(c)].data();
+    st = advance(ctx, scheme, &bc, dbase, sc);
+    if (st != BURGERS_OK) return st;
+    if (pipe) {
+      e = cudaEventRecord(ctx->io_out[c], sc);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(sout, ctx->io_out[c], 0);
+      if (e != cudaSuccess) return cuda_error(e, "solve_host order");
+    }
+    for (auto& rn : cruns[size_t(c)]) {
+      e = cudaMemcpyAsync(hbase + rn.first * esz, dbase + (rn.first - lo) * esz,
+                          size_t(rn.second - rn.first) * esz, cudaMemcpyDeviceToHost, sout);
+      if (e != cudaSuccess) return cuda_error(e, "solve_host D2H");
+    }
+  }
+  e = cudaStreamSynchronize(sout);
+  if (e == cudaSuccess && pipe) e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess && pipe) e = cudaStreamSynchronize(ctx->side[burgers_ctx::kSide - 1]);
   if (e != cudaSuccess) return cuda_error(e, "solve_host sync");
   return BURGERS_OK;
 }

@@ -111,6 +111,10 @@ struct burgers_ctx {
   static constexpr int kSide = 3;
   cudaStream_t side[kSide] = {};
   cudaEvent_t fork_ev = nullptr, join_ev[kSide] = {};
+  // host-memory solves: copy streams and per-chunk events of the pipeline
+  static constexpr int kIoChunks = 4;
+  cudaStream_t io_h2d = nullptr, io_d2h = nullptr;
+  cudaEvent_t io_in[kIoChunks] = {}, io_out[kIoChunks] = {};
   std::list<std::unique_ptr<burgers::Plan>> plans;
   std::map<uint64_t, burgers::TuneVal> tuned;
   burgers::DevBuf scratch;  // streaming ping-pong
