@@ -22,6 +22,22 @@ struct BtcsShared {
   T Z[SK];                               // cyclic case: solution for the correction vector
 };
 
+// Sherman-Morrison factor (v.y)/(1 + v.z) for v = e_0 + fa e_tl. The dot
+// products and the denominator are formed in FP64 whatever T is, so a
+// denominator near cancellation keeps its digits. For FP32 the quotient is
+// rounded to FP32 anyway, so it is taken in FP32 from the two FP64 operands
+// rounded to FP32 (within 1.5 ulp of their exact quotient): an FP64
+// divide is a long dependent sequence on the narrow FP64 pipe, and this factor
+// sits on the serial path of every solve.
+template <typename T>
+__device__ __forceinline__ T sm_factor(T fa, T y0, T ytl, T z0, T ztl) {
+  const double fd = double(fa);
+  const double vy = fma(fd, double(ytl), double(y0));
+  const double den = 1.0 + fma(fd, double(ztl), double(z0));
+  if constexpr (sizeof(T) == 4) return __fdiv_rn(float(vy), float(den));
+  else return vy / den;
+}
+
 // Solves the reduced system held in sm (rows 0..NT-1, rows beyond tl are
 // decoupled identities) with warp 0; leaves the solution in sm.X.
 template <typename T, int NT, bool CYC>
@@ -29,12 +45,12 @@ __device__ __forceinline__ void reduced_solve(BtcsShared<T, NT>& sm, int tl, int
   constexpr int Q = NT / 32;
   // Sherman-Morrison split: gamma = -B_0, v = e_0 + (A_0/gamma) e_tl. The ratio
   // is rounded once to T and used both in the modified diagonal and in v, so
-  // T~ + u v^T reproduces the cyclic matrix.
+  // T~ + u v^T reproduces the cyclic matrix up to the rounding of that ratio.
   T fa = T(0);
   if constexpr (CYC) {
     const T A0 = sm.A[sk(0)], B0 = sm.B[sk(0)], Ct = sm.Cc[sk(tl)], Bt = sm.B[sk(tl)];
     const T gam = -B0;
-    fa = A0 / gam;
+    fa = A0 * recip(gam);
     __syncwarp();
     if (lane == 0) {
       sm.B[sk(0)] = B0 - gam;
@@ -111,31 +127,46 @@ __device__ __forceinline__ void reduced_solve(BtcsShared<T, NT>& sm, int tl, int
   const T Ye = d32, Ze = u32;
   T YL = shfl_up(Ye, 1), ZL = shfl_up(Ze, 1);
   if (lane == 0) { YL = T(0); ZL = T(0); }
+  // up to 8 rows a lane keep y and z in registers through the correction;
+  // more go through shared memory
+  constexpr bool YREG = Q <= 8;
+  T y[YREG ? Q : 1], z[YREG ? Q : 1];
+  T ysel = T(0), zsel = T(0);  // row tl's values, on the lane that holds it
 #pragma unroll
   for (int q = 0; q < Q; ++q) {
     const int i = sk(r0 + q);
-    T y = Ye, z = Ze;
+    T yq = Ye, zq = Ze;
     if (q < Q - 1) {
-      y = tfma(-sm.Cc[i], Ye, tfma(-sm.A[i], YL, sm.D[i]));
-      if constexpr (CYC) z = tfma(-sm.Cc[i], Ze, tfma(-sm.A[i], ZL, sm.U[i]));
+      yq = tfma(-sm.Cc[i], Ye, tfma(-sm.A[i], YL, sm.D[i]));
+      if constexpr (CYC) zq = tfma(-sm.Cc[i], Ze, tfma(-sm.A[i], ZL, sm.U[i]));
     }
-    sm.X[sk(r0 + q)] = y;
-    if constexpr (CYC) sm.Z[sk(r0 + q)] = z;
+    if constexpr (CYC) {
+      if (r0 + q == tl) { ysel = yq; zsel = zq; }
+    }
+    if constexpr (YREG) {
+      y[q] = yq;
+      z[q] = zq;
+    } else {
+      sm.X[i] = yq;
+      if constexpr (CYC) sm.Z[i] = zq;
+    }
   }
   if constexpr (CYC) {
-    __syncwarp();
-    // x = y - (v.y)/(1 + v.z) z: dot products and denominator in FP64, on one
-    // lane (the FP64 pipe is narrow), the factor broadcast in T.
+    // x = y - (v.y)/(1 + v.z) z with v.y = y_0 + fa y_tl, v.z likewise: the
+    // corner values come from lane 0 (row 0) and the lane holding row tl.
+    const T ytl = shfl(ysel, tl / Q), ztl = shfl(zsel, tl / Q);
     T fac = T(0);
-    if (lane == 0) {
-      const double fd = double(fa);
-      const double vy = fma(fd, double(sm.X[sk(tl)]), double(sm.X[sk(0)]));
-      const double vz = fma(fd, double(sm.Z[sk(tl)]), double(sm.Z[sk(0)]));
-      fac = T(vy / (1.0 + vz));
-    }
+    if (lane == 0) fac = sm_factor(fa, YREG ? y[0] : sm.X[sk(0)], ytl, YREG ? z[0] : sm.Z[sk(0)], ztl);
     fac = shfl(fac, 0);
 #pragma unroll
-    for (int q = 0; q < Q; ++q) sm.X[sk(r0 + q)] = tfma(-fac, sm.Z[sk(r0 + q)], sm.X[sk(r0 + q)]);
+    for (int q = 0; q < Q; ++q) {
+      const int i = sk(r0 + q);
+      if constexpr (YREG) sm.X[i] = tfma(-fac, z[q], y[q]);
+      else sm.X[i] = tfma(-fac, sm.Z[i], sm.X[i]);
+    }
+  } else if constexpr (YREG) {
+#pragma unroll
+    for (int q = 0; q < Q; ++q) sm.X[sk(r0 + q)] = y[q];
   }
 }
 

@@ -38,10 +38,26 @@ constexpr size_t btcs_dsm() {
 // increment can be a sizeable part of u and must be compensated every step.
 //
 // Two barriers per solve. Each thread publishes the reduced-system data of its
-// chunk; warp 0 forms the reduced rows, solves them, and also computes the
-// value every chunk's first and last node will have for the next solve (the
-// owner computes the same numbers from the same operands), so the neighbour
-// values need no exchange of their own.
+// chunk; warp 0 forms the reduced rows and solves them.
+//
+// Neighbour values. A chunk's rows need the value left of its first node and
+// right of its end node. In BTCS, CN and Picard the row coefficients depend
+// on the node's own value only, so those two values enter the right-hand side
+// alone, linearly, through the differences u_left - u_0 and u_right - u_end.
+// The sweeps run with each edge node standing in for its own neighbour (both
+// differences zero); row 0 then reads
+//     l (x_{-1} + kap (u_left - u_0)) + d x_0 + c x_1 = rhs'
+// (kap = 2 for CN, whose matrix has half the step's coefficients; 1
+// otherwise), and likewise at the end row, so the chunk relations hold with L
+// replaced by L + kap (u_left - u_0) and warp 0 adds the neighbour terms when
+// it forms the reduced rows. The difference is the operand the right-hand side
+// itself holds, so the increment keeps its precision. The edge values of a
+// solve are those the owners publish (hfirst, hlast) during the previous
+// back-substitution, bitwise the values their sweeps read, and the first
+// barrier orders them before every read. Newton's Jacobian diagonal holds
+// w_{i+1} - w_{i-1}, so there the sweeps take the neighbours directly and warp
+// 0 computes every chunk's next edge values (the owner computes the same
+// numbers from the same operands) after the reduced solve.
 //
 // VAR selects the implicit scheme; every variant solves tridiagonal systems
 // of this shape in increment form:
@@ -67,6 +83,8 @@ __device__ __forceinline__ void btcs_steps(int64_t nsteps, int iters, T r, T s, 
                                            T* lo, T* es) {
   constexpr bool ITER = VAR == VAR_PICARD || VAR == VAR_NEWTON;
   constexpr bool PER = BCT == BC_PERIODIC;
+  constexpr bool DEFER = VAR != VAR_NEWTON;  // neighbour values folded into the reduced rows
+  const T kap = VAR == VAR_CN ? T(2) : T(1);
   constexpr int Q = NT / 32;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int tl = EXACT ? NT - 1 : (n - 1) / C;  // chunk holding node n-1
@@ -103,18 +121,23 @@ __device__ __forceinline__ void btcs_steps(int64_t nsteps, int iters, T r, T s, 
   for (int it = 0; it < nit; ++it) {
     const bool last = it + 1 == nit;
     T left = T(0), right = T(0);
-    if (tid > 0) left = hlast[tid - 1];
-    else if constexpr (PER) left = hlast[tl];
-    if (tid < tl) right = hfirst[tid + 1];
-    else if constexpr (PER) right = hfirst[0];
+    if constexpr (!DEFER) {
+      if (tid > 0) left = hlast[tid - 1];
+      else if constexpr (PER) left = hlast[tl];
+      if (tid < tl) right = hfirst[tid + 1];
+      else if constexpr (PER) right = hfirst[0];
+    }
     // ---- assembly of rows and right-hand sides fused with the forward sweep
     T chp = T(0), ahp = T(-1), dhp = T(0);
     T ul = left, a = uval(0, tid);
+    if constexpr (DEFER) ul = a;
 #pragma unroll
     for (int j = 0; j < C; ++j) {
       const T an = (j + 1 < C) ? uval(j + 1, tid) : right;
       T ur = an;
-      if constexpr (!EXACT) {
+      if constexpr (DEFER) {
+        if (j == C - 1 || (!EXACT && j == jstar)) ur = a;  // end row of the chunk
+      } else if constexpr (!EXACT) {
         if (j == jstar) ur = right;
       }
       T l, c, d, rhs;
@@ -202,6 +225,12 @@ __device__ __forceinline__ void btcs_steps(int64_t nsteps, int iters, T r, T s, 
       sm.D[si] = e_dh;
     }
     __syncthreads();
+    // u_left - u_0 of this chunk, from the values published before the barrier
+    T lft = T(0);
+    if constexpr (DEFER) {
+      if (tid > 0) lft = hlast[tid - 1] - hfirst[tid];
+      else if constexpr (PER) lft = hlast[tl] - hfirst[0];
+    }
     if (warp == 0) {
       // reduced row of each of this lane's chunks: end row of chunk t with the
       // first-row relation of chunk t + 1 substituted (chunk 0 after the last)
@@ -211,18 +240,32 @@ __device__ __forceinline__ void btcs_steps(int64_t nsteps, int iters, T r, T s, 
         T A = T(0), B = T(1), Cc = T(0), D = T(0);
         if (t <= tl) {
           const int nx = (t == tl) ? 0 : t + 1;
-          const T ech = sm.Cc[i];
+          const T ech = sm.Cc[i], ran = sm.ra[sk(nx)];
           A = sm.A[i];
-          B = T(1) - ech * sm.ra[sk(nx)];
+          T Dt = sm.D[i], rdn = sm.rd[sk(nx)];
+          if constexpr (DEFER) {
+            // neighbour differences of chunk t's edges; the end node of chunk
+            // t is the left neighbour of chunk nx's first node
+            const T f = hfirst[t], e = hlast[t], fn = hfirst[nx];
+            T lt = T(0), rt = T(0);
+            if (t > 0) lt = hlast[t - 1] - f;
+            else if constexpr (PER) lt = hlast[tl] - f;
+            if (t < tl) rt = fn - e;
+            else if constexpr (PER) rt = fn - e;
+            Dt = tfma(-kap * A, lt, tfma(-kap * ech, rt, Dt));
+            rdn = tfma(-kap * ran, e - fn, rdn);
+          }
+          B = T(1) - ech * ran;
           Cc = -ech * sm.rg[sk(nx)];
-          D = tfma(-ech, sm.rd[sk(nx)], sm.D[i]);
+          D = tfma(-ech, rdn, Dt);
         }
         sm.A[i] = A; sm.B[i] = B; sm.Cc[i] = Cc; sm.D[i] = D; sm.U[i] = T(0);
       }
       __syncwarp();
       reduced_solve<T, NT, PER>(sm, tl, lane);
+      // next step's first and last node of each chunk (Newton)
+      if constexpr (!DEFER) {
       __syncwarp();
-      // next step's first and last node of each chunk
 #pragma unroll
       for (int q = 0; q < Q; ++q) {
         const int t = lane * Q + q;
@@ -237,6 +280,7 @@ __device__ __forceinline__ void btcs_steps(int64_t nsteps, int iters, T r, T s, 
           hlast[t] = next_u(jt, t, Xt, last);
         }
       }
+      }
     }
     __syncthreads();
     // ---- back-substitution of the increment and the update of the state
@@ -245,6 +289,7 @@ __device__ __forceinline__ void btcs_steps(int64_t nsteps, int iters, T r, T s, 
       if (tid > 0) L = sm.X[sk(tid - 1)];
       else if constexpr (PER) L = sm.X[sk(tl)];
       const T Xt = sm.X[sk(tid)];
+      if constexpr (DEFER) L = tfma(kap, lft, L);
 #pragma unroll
       for (int j = 0; j < C; ++j) {
         if (EXACT || j <= je) {
@@ -255,13 +300,23 @@ __device__ __forceinline__ void btcs_steps(int64_t nsteps, int iters, T r, T s, 
             inc = es[o] + delta;
             if (!last) {
               es[o] = inc;
+              if constexpr (DEFER) {
+                // the next iterate's edge values
+                if (j == 0) hfirst[tid] = us[o] + inc;
+                if (j == je) hlast[tid] = us[o] + inc;
+              }
               continue;
             }
           }
           T l0 = T(0);
           if constexpr (Kahan<T>::on) l0 = lo[o];
-          us[o] = comp_add(us[o], inc, l0);
+          const T nv = comp_add(us[o], inc, l0);
+          us[o] = nv;
           if constexpr (Kahan<T>::on) lo[o] = l0;
+          if constexpr (DEFER) {
+            if (j == 0) hfirst[tid] = nv;
+            if (j == je) hlast[tid] = nv;
+          }
         }
       }
     }
