@@ -25,10 +25,29 @@ namespace burgers {
 enum : int { MODE_EXACT = 0, MODE_RAGGED = 1, MODE_WINDOW = 2, MODE_WINDOW_DIR = 3 };
 enum : int { INTEG_EULER = 0, INTEG_RK4 = 1 };
 
+// Shared-memory store executed only where pred holds: a predicated store
+// instruction, so the edge lanes publishing their values cost no branch.
+__device__ __forceinline__ void st_shared_if(float* p, float v, bool pred) {
+  asm volatile(
+      "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %2, 0;\n\t@q st.shared.f32 [%0], %1;\n\t}"
+      :: "r"(static_cast<unsigned>(__cvta_generic_to_shared(p))), "f"(v), "r"(int(pred))
+      : "memory");
+}
+__device__ __forceinline__ void st_shared_if(double* p, double v, bool pred) {
+  asm volatile(
+      "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %2, 0;\n\t@q st.shared.f64 [%0], %1;\n\t}"
+      :: "r"(static_cast<unsigned>(__cvta_generic_to_shared(p))), "d"(v), "r"(int(pred))
+      : "memory");
+}
+
 // Exchanges this thread's edge values for its neighbours' (left = value of
 // the node before its first, right = after its last). Periodic rows wrap
 // through the slots of the first and last warp; WRAPX rows (ragged periodic)
 // also publish node n-1 and node 0 (wrap_sel, first of thread 0).
+// Branch-free: within a warp the values move by shuffles; across warps lane
+// 31 publishes its last value and lane 0 its first with one predicated
+// store, and after the barrier every lane reads the neighbour warps' slots
+// (broadcast loads) and the edge lanes select them.
 template <typename T, int NT, bool WRAPX>
 __device__ __forceinline__ void halo_exchange(T first, T last, T wrap_sel, bool has_wrap, int p,
                                               T* sh_last, T* sh_first, T* sh_wrap, T& left,
@@ -38,17 +57,20 @@ __device__ __forceinline__ void halo_exchange(T first, T last, T wrap_sel, bool 
   left = shfl(last, (lane + 31) & 31);
   right = shfl(first, (lane + 1) & 31);
   if constexpr (NW > 1) {
-    if (lane == 31) sh_last[p * NW + warp] = last;
-    if (lane == 0) sh_first[p * NW + warp] = first;
+    const bool lo_lane = lane == 0;
+    st_shared_if((lo_lane ? sh_first : sh_last) + p * NW + warp, lo_lane ? first : last,
+                 lo_lane || lane == 31);
   }
   if constexpr (WRAPX) {
-    if (has_wrap) sh_wrap[p * 2 + 0] = wrap_sel;
-    if (tid == 0) sh_wrap[p * 2 + 1] = first;
+    st_shared_if(sh_wrap + p * 2 + 0, wrap_sel, has_wrap);
+    st_shared_if(sh_wrap + p * 2 + 1, first, tid == 0);
   }
   if constexpr (NW > 1 || WRAPX) __syncthreads();
   if constexpr (NW > 1) {
-    if (lane == 0) left = sh_last[p * NW + (warp + NW - 1) % NW];
-    if (lane == 31) right = sh_first[p * NW + (warp + 1) % NW];
+    const T lv = sh_last[p * NW + (warp + NW - 1) % NW];
+    const T rv = sh_first[p * NW + (warp + 1) % NW];
+    left = lane == 0 ? lv : left;
+    right = lane == 31 ? rv : right;
   }
   if constexpr (WRAPX) {
     wrapL = sh_wrap[p * 2 + 0];
@@ -92,8 +114,12 @@ __device__ __forceinline__ void explicit_steps_split(float (&v)[C], float (&lo)[
   // lo becomes d = -lo
 #pragma unroll
   for (int j = 0; j < C; ++j) lo[j] = -lo[j];
-  for (int64_t k = 0; k < nsteps; ++k) {
-    const int p = int(k & 1);
+  // blocks of SPLIT_FOLD steps (the last one shorter) with a fold after each;
+  // SPLIT_FOLD is even, so kk & 1 is the parity of the global step index
+  for (int64_t k0 = 0; k0 < nsteps; k0 += SPLIT_FOLD) {
+   const int kb = int(nsteps - k0 < SPLIT_FOLD ? nsteps - k0 : int64_t(SPLIT_FOLD));
+   for (int kk = 0; kk < kb; ++kk) {
+    const int p = kk & 1;
     const float first = v[0] + lo[0];
     const float last = v[C - 1] + lo[C - 1];
     float wsel = 0.f;
@@ -124,13 +150,12 @@ __device__ __forceinline__ void explicit_steps_split(float (&v)[C], float (&lo)[
       wl = wc;
       wc = wr;
     }
-    if (((k + 1) & (SPLIT_FOLD - 1)) == 0 || k + 1 == nsteps) {
+   }
 #pragma unroll
-      for (int j = 0; j < C; ++j) {
-        const float t = v[j] + lo[j];
-        lo[j] = lo[j] - (t - v[j]);
-        v[j] = t;
-      }
+    for (int j = 0; j < C; ++j) {
+      const float t = v[j] + lo[j];
+      lo[j] = lo[j] - (t - v[j]);
+      v[j] = t;
     }
   }
 #pragma unroll
