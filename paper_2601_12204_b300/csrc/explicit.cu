@@ -187,7 +187,10 @@ __device__ __forceinline__ void rk4_steps(T (&v)[C], T (&lo)[C], int64_t nsteps,
   T K[C], acc[C];
 #pragma unroll
   for (int j = 0; j < C; ++j) K[j] = T(0);
-  for (int64_t k = 0; k < nsteps; ++k) {
+  // blocks of SPLIT_FOLD steps (the last one shorter); FP32 folds after each
+  for (int64_t k0 = 0; k0 < nsteps; k0 += SPLIT_FOLD) {
+   const int kb = int(nsteps - k0 < SPLIT_FOLD ? nsteps - k0 : int64_t(SPLIT_FOLD));
+   for (int kk = 0; kk < kb; ++kk) {
 #pragma unroll
     for (int st = 0; st < 4; ++st) {
       const T cst = st == 0 ? T(0) : (st == 3 ? T(1) : T(0.5));
@@ -236,17 +239,18 @@ __device__ __forceinline__ void rk4_steps(T (&v)[C], T (&lo)[C], int64_t nsteps,
     if constexpr (SPLIT) {
 #pragma unroll
       for (int j = 0; j < C; ++j) lo[j] = tfma(sixth, acc[j], lo[j]);
-      if (((k + 1) & (SPLIT_FOLD - 1)) == 0 || k + 1 == nsteps) {
-#pragma unroll
-        for (int j = 0; j < C; ++j) {
-          const T t = v[j] + lo[j];
-          lo[j] = lo[j] - (t - v[j]);
-          v[j] = t;
-        }
-      }
     } else {
 #pragma unroll
       for (int j = 0; j < C; ++j) v[j] = tfma(sixth, acc[j], v[j]);
+    }
+   }
+    if constexpr (SPLIT) {
+#pragma unroll
+      for (int j = 0; j < C; ++j) {
+        const T t = v[j] + lo[j];
+        lo[j] = lo[j] - (t - v[j]);
+        v[j] = t;
+      }
     }
   }
   if constexpr (SPLIT) {
