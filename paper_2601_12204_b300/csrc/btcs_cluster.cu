@@ -13,7 +13,7 @@
 //   cluster substituting those relations into the interface rows leaves one
 //           row per CTA in Y_{k-1}, Y_k, Y_{k+1} (cyclic when periodic), which
 //           warp 0 of CTA 0 solves, one row per lane (Sherman-Morrison
-//           correction in FP64).
+//           correction with its denominator in FP64).
 // CTA 0 sends every CTA its Y and P and the new values of the nodes next to
 // its ends (computed with the owners' arithmetic from their operands), so the
 // neighbour values of the next step need no further exchange. A step costs two
@@ -150,7 +150,8 @@ __device__ __forceinline__ void block_solve3(ClusterShared<T, NT>& cs, int lane)
 // Warp 0 of CTA 0: the cluster system in the interface values Y_k, one row
 // per lane (lanes >= CS carry identity rows), solved by cyclic reduction over
 // the lanes; the cyclic corners are split off by Sherman-Morrison with the
-// correction factor in FP64 (as in the CTA-level solve). Lane k then sends CTA
+// correction factor's denominator in FP64 (sm_factor, as in the CTA-level
+// solve). Lane k then sends CTA
 // k its Y and P and the new values of the nodes next to its ends. Dirichlet
 // rows have identity rows at the row's ends, so the first block has no left
 // neighbour (P = 0) and the system is plain.
@@ -178,7 +179,7 @@ __device__ __forceinline__ void cluster_solve(ClusterShared<T, NT>& cs, bool per
   T fa = T(0);
   if (per) {
     const T gam = -shfl(b, 0);
-    fa = shfl(a, 0) / gam;
+    fa = shfl(a, 0) * recip(gam);
     const T cl = shfl(c, CS - 1);
     if (lane == 0) { b -= gam; uu = gam; }
     if (lane == CS - 1) { b -= cl * fa; uu = cl; }
@@ -206,10 +207,7 @@ __device__ __forceinline__ void cluster_solve(ClusterShared<T, NT>& cs, bool per
   }
   T Y = d;
   if (per) {
-    const double fd = double(fa);
-    const double vy = fma(fd, double(shfl(d, CS - 1)), double(shfl(d, 0)));
-    const double vz = fma(fd, double(shfl(uu, CS - 1)), double(shfl(uu, 0)));
-    const T fac = T(vy / (1.0 + vz));
+    const T fac = sm_factor(fa, shfl(d, 0), shfl(d, CS - 1), shfl(uu, 0), shfl(uu, CS - 1));
     Y = tfma(-fac, uu, d);
   }
   // P of block k is the interface before it; new first / last node values
