@@ -22,18 +22,21 @@ struct BtcsShared {
   T Z[SK];                               // cyclic case: solution for the correction vector
 };
 
-// Sherman-Morrison factor (v.y)/(1 + v.z) for v = e_0 + fa e_tl. The
-// denominator is formed in FP64 whatever T is, so one near cancellation keeps
-// its digits. For FP32 the numerator y_0 + fa y_tl is one FP32 fma and the
-// quotient, rounded to FP32 anyway, is an FP32 division by the FP64
-// denominator rounded to FP32 (within 1.5 ulp of the exact quotient of the
-// two): every FP64 operation is a long-latency step on B300's narrow FP64
-// pipe, and this factor sits on the serial path of every solve.
+// Sherman-Morrison factor (v.y)/(1 + v.z) for v = e_0 + fa e_tl. The dot
+// products and the denominator are formed in FP64 whatever T is, so a
+// denominator near cancellation keeps its digits. For FP32 the quotient,
+// rounded to FP32 anyway, is an FP32 division of the two FP64 values rounded
+// to FP32 (within 1.5 ulp of their exact quotient): an FP64 divide is a long
+// dependent sequence on B300's narrow FP64 pipe (each FP64 operation costs
+// about 60 cycles of latency), and this factor sits on the serial path of
+// every solve.
 template <typename T>
 __device__ __forceinline__ T sm_factor(T fa, T y0, T ytl, T z0, T ztl) {
-  const double den = 1.0 + fma(double(fa), double(ztl), double(z0));
-  if constexpr (sizeof(T) == 4) return __fdiv_rn(tfma(fa, ytl, y0), float(den));
-  else return fma(fa, ytl, y0) / den;
+  const double fd = double(fa);
+  const double vy = fma(fd, double(ytl), double(y0));
+  const double den = 1.0 + fma(fd, double(ztl), double(z0));
+  if constexpr (sizeof(T) == 4) return __fdiv_rn(float(vy), float(den));
+  else return vy / den;
 }
 
 // Solves the reduced system held in sm (rows 0..NT-1, rows beyond tl are
