@@ -197,32 +197,37 @@ def traffic_record(kernel: str):
 
 # ---------------------------------------------------------------------------
 def cpu_baseline_sample(target_s: float = 12.0, ids_offset: int = 0):
-    """Oracle (as it stands) on a bounded sample of the workload, all host cores."""
+    """Oracle (as it stands) on a bounded sample of the workload, all host cores,
+    plus the same on one core (a few rows)."""
     import oracle
     from paper_2601_12204_b300 import workloads as W
     threads = oracle.max_threads()
 
-    def run(count):
+    def run(count, nthreads):
         ens = W.fourier_ensemble(count, N_NODES, ids=np.arange(ids_offset, ids_offset + count))
         dts = np.array([oracle.cfl_dt(ens.row(b), ens.dxs[b], ens.nus[b], CFL)
                         for b in range(count)])
         t0 = time.perf_counter()
         oracle.explicit_batch(ens.u0, ens.offsets, ens.ns, ens.bcs, ens.dxs, ens.nus, dts,
-                              np.full(count, EXPLICIT_STEPS), threads)
+                              np.full(count, EXPLICIT_STEPS), nthreads)
         oracle.btcs_batch(ens.u0, ens.offsets, ens.ns, ens.bcs, ens.dxs, ens.nus,
-                          dts * BTCS_DT_FACTOR, np.full(count, BTCS_STEPS), threads)
+                          dts * BTCS_DT_FACTOR, np.full(count, BTCS_STEPS), nthreads)
         return time.perf_counter() - t0
 
     count = threads
-    t = run(count)
+    t = run(count, threads)
     if t < target_s / 3:
         count = max(threads, int(count * target_s / max(t, 1e-3)) // threads * threads)
         count = min(count, B_ROWS)
-        t = run(count)
+        t = run(count, threads)
     cells = count * N_NODES * (EXPLICIT_STEPS + BTCS_STEPS)
+    one = 4
+    t1 = run(one, 1)
     return {"value": cells / t, "unit": "cell-updates/s", "cores": threads, "kind": "oracle",
             "sample": f"{count} of {B_ROWS} rows (ids 0..{count - 1}), full {EXPLICIT_STEPS} "
-                      f"explicit + {BTCS_STEPS} BTCS steps, FP64 C oracle, {t:.1f} s"}
+                      f"explicit + {BTCS_STEPS} BTCS steps, FP64 C oracle, {t:.1f} s",
+            "one_core": {"value": one * N_NODES * (EXPLICIT_STEPS + BTCS_STEPS) / t1,
+                         "cores": 1, "sample": f"rows 0..{one - 1}, same steps, {t1:.2f} s"}}
 
 
 # ---------------------------------------------------------------------------
@@ -358,6 +363,9 @@ def run_ours(args):
 
     # ---- roofline of the dominant kernel (explicit resident, FP32 issue bound)
     peak_ops = SMS * FP32_LANES * 2032e6 / 1e12
+    # measured FMA issue rates (burgers_fma_peak), right after the timed region
+    fma32 = ctx.fma_peak(L.BURGERS_F32) / 1e12
+    fma64 = ctx.fma_peak(L.BURGERS_F64) / 1e12
     ach = EXPLICIT_OPS * B_ROWS * N_NODES * EXPLICIT_STEPS / (t_expl / 1000.0) / 1e12
     res["roofline"] = {
         "bound": "alu", "kernel": "k_explicit_resident<float, tuned shape, exact>",
@@ -366,12 +374,18 @@ def run_ours(args):
         "per_unit": f"{EXPLICIT_OPS:.4g} FMA-pipe FP32 instr per cell-update; "
                     f"4096 rows x 4096 nodes x 2000 steps per launch",
         "peak_note": "148 SMs x 128 FP32 lanes x 2032 MHz (max SM clock)",
+        "peak_measured": fma32, "frac_measured": ach / fma32,
+        "peak_measured_note": "burgers_fma_peak: 8 independent FMA chains x 2048 threads per SM, "
+                              "at the clock of the run",
         "kernel_ms": t_expl}
     achb = BTCS_OPS * B_ROWS * N_NODES * BTCS_STEPS / (t_btcs / 1000.0) / 1e12
     res["roofline_btcs"] = {"bound": "alu", "kernel": "k_btcs_resident<float, tuned shape, exact>",
                             "achieved": achb, "peak": peak_ops, "unit": "Tops/s (FP32 lane-instructions)",
                             "frac": achb / peak_ops, "kernel_ms": t_btcs,
+                            "peak_measured": fma32, "frac_measured": achb / fma32,
                             "per_unit": f"{BTCS_OPS} FMA-pipe FP32 instr + 1 MUFU rcp + 2 ALU per cell-update"}
+    res["fma_peak_measured"] = {"fp32_tops": fma32, "fp64_tops": fma64,
+                                "unit": "T lane-FMA/s"}
     res["explicit_cups"] = B_ROWS * N_NODES * EXPLICIT_STEPS / (t_expl / 1000.0)
     res["btcs_cups"] = B_ROWS * N_NODES * BTCS_STEPS / (t_btcs / 1000.0)
 
@@ -425,6 +439,12 @@ def extras(args, ctx, ens, u0, batches, probe, dev, world, rank):
         acc[name] = {"max": float(np.max(rel)), "median": float(np.median(rel))}
     acc["bound"] = 1e-5
     out["l2_fp32_vs_fp64"] = acc
+    # FP64 explicit against the measured FP64 FMA rate: 6 FP64 operations per
+    # cell-update (two differences, |u| - u, p, q and the two-FMA update into u)
+    f64pk = ctx.fma_peak(L.BURGERS_F64) / 1e12
+    fp64["explicit_roofline"] = {"bound": "fp64", "achieved": 6.0 * fp64["explicit_cups"] / 1e12,
+                                 "peak_measured": f64pk, "unit": "T FP64 lane-instr/s",
+                                 "frac": 6.0 * fp64["explicit_cups"] / 1e12 / f64pk}
     out["fp64"] = fp64
     del u64
 

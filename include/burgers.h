@@ -256,6 +256,19 @@ burgers_status burgers_adjoint(burgers_ctx* ctx, int32_t scheme, const burgers_b
                                const void* u0_dev, const void* gT_dev, void* gu0_dev,
                                double* gnu_dev, int64_t ckpt_stride, burgers_stream stream);
 
+/* ---- device peak (roofline denominator) ---------------------------------- */
+
+/* Blocking. Measures the FMA issue rate the device sustains for `dtype`
+ * (BURGERS_F32 or BURGERS_F64; anything else: EINVAL): every SM runs 2048
+ * threads of eight independent register-resident FMA chains, and
+ * *lane_fmas_per_s receives lane-FMAs per second at whatever SM clock the GPU
+ * runs during the call (the clock is neither set nor locked). Two launches on
+ * a stream of its own, the first a warm-up, a few ms each; a small workspace
+ * is allocated and freed inside the call. The step kernels are bound by this
+ * pipe, so this is the measured denominator of their roofline beside the one
+ * derived from SMs x lanes x clock. */
+burgers_status burgers_fma_peak(burgers_ctx* ctx, int32_t dtype, double* lane_fmas_per_s);
+
 /* ---- norms (Nomenclature "L2", Sec. 2.7.4) ------------------------------- */
 
 /* Blocking. out_host[b] = ||u_b - ref_b||_2 / ||ref_b||_2 over the n nodes of

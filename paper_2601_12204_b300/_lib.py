@@ -84,6 +84,7 @@ SIGNATURES = {
     "burgers_newton_advance": (_ST, [_P, _P, _P, ctypes.c_int32, _P]),
     "burgers_solve_host": (_ST, [_P, _I32, _P, _P, _P]),
     "burgers_rel_l2": (_ST, [_P, _P, _P, _P, _I32, _P, _P, _P]),
+    "burgers_fma_peak": (_ST, [_P, _I32, _P]),
     "burgers_adjoint": (_ST, [_P, _I32, _P, _P, _P, _P, _P, _I64, _P]),
     "burgers_autotune": (_ST, [_P, _I32, _P, _P, _I64, _P, _P]),
     "burgers_explicit_advance_noalloc": (_ST, [_P, _I32, _P, _P]),

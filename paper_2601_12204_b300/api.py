@@ -180,6 +180,14 @@ class Context:
                                          self._stream(stream, u)), "burgers_cfl_dt")
         return out
 
+    def fma_peak(self, dtype: int = L.BURGERS_F32) -> float:
+        """Measured FMA issue rate of the device (lane-FMAs per second) for dtype,
+        at the clock the GPU runs during the call."""
+        out = ctypes.c_double(0.0)
+        L.check(self._lib.burgers_fma_peak(self.h, int(dtype), ctypes.byref(out)),
+                "burgers_fma_peak")
+        return float(out.value)
+
     def rel_l2(self, batch: Batch, u, ref, stream=None):
         torch = _torch()
         p = self._check_tensor(u, batch)
