@@ -405,6 +405,89 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def differentiation_bench(ctx, dev):
+    """Configuration 5: J = 1/2 |u(T) - target|^2 over B = 1024 periodic rows of
+    2048 nodes (random-Fourier u0; the target is the same run from the
+    ensemble of the next seed, with a dt per row that satisfies the CFL limit
+    of both initial fields), 2000 explicit / 200 BTCS steps, gradients by
+    the hand-written adjoint with sqrt-step checkpointing. Times the forward
+    call and the adjoint call (which recomputes the forward states from its
+    checkpoints, then runs the reverse sweep); FP32 gradients against the
+    FP64 GPU gradients of the same problem."""
+    import torch
+
+    from paper_2601_12204_b300 import _lib as L
+    from paper_2601_12204_b300 import workloads as W
+    from paper_2601_12204_b300.api import Batch
+    F32, F64 = L.BURGERS_F32, L.BURGERS_F64
+    rows, n = 1024, 2048
+    ens = W.fourier_ensemble(rows, n)
+    tgt = W.fourier_ensemble(rows, n, seed=W.DEFAULT_SEED + 1)
+    u64 = torch.tensor(ens.u0, dtype=torch.float64, device=dev)
+    t64 = torch.tensor(tgt.u0, dtype=torch.float64, device=dev)
+    probe = Batch.from_ensemble(ens, 1.0, 0, F64)
+    # one dt per row that is stable for both runs (the target's u0 can be larger)
+    dt0 = np.minimum(ctx.cfl_dt(probe, u64, CFL), ctx.cfl_dt(probe, t64, CFL))
+    del t64
+    stream = torch.cuda.current_stream()
+    out = {"rows": rows, "n": n, "ckpt_stride": "ceil(sqrt(nsteps))"}
+    for name, scheme, steps, fac in (("explicit", L.BURGERS_EXPLICIT, EXPLICIT_STEPS, 1.0),
+                                     ("btcs", L.BURGERS_BTCS, BTCS_STEPS, BTCS_DT_FACTOR)):
+        grads = {}
+        rec = {"steps": steps}
+        for dt_, tdt in ((F64, torch.float64), (F32, torch.float32)):
+            b = Batch.from_ensemble(ens, dt0 * fac, steps, dt_)
+            u0 = torch.tensor(ens.u0, dtype=tdt, device=dev)
+            ut = torch.tensor(tgt.u0, dtype=tdt, device=dev)
+            ctx.advance(scheme, b, ut)          # target: the next seed's run
+            uT = u0.clone()
+            ctx.advance(scheme, b, uT)          # warm
+            uT = u0.clone()
+            a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            ctx.advance(scheme, b, uT)
+            z.record(stream)
+            torch.cuda.synchronize()
+            t_fwd = a.elapsed_time(z) / 1000.0
+            gT = uT - ut
+            gu0 = torch.empty_like(u0)
+            gnu = torch.empty(rows, dtype=torch.float64, device=dev)
+            ctx.adjoint(scheme, b, u0, gT, gu0, gnu)   # warm (workspace)
+            a.record(stream)
+            ctx.adjoint(scheme, b, u0, gT, gu0, gnu)
+            z.record(stream)
+            torch.cuda.synchronize()
+            t_adj = a.elapsed_time(z) / 1000.0
+            grads[dt_] = (gu0.double(), gnu.clone())
+            k = math.ceil(math.sqrt(steps))
+            nck = math.ceil(steps / k)
+            # checkpoints (FP32: state + compensation term) and k + 1 segment states per row
+            ck = ((2 * nck + k + 1) * 4 if dt_ == F32 else (nck + k + 1) * 8) * n * rows
+            tag = "fp64" if dt_ == F64 else "fp32"
+            rec[tag] = {"forward_cups": rows * n * steps / t_fwd,
+                        "adjoint_s": t_adj, "forward_s": t_fwd, "adjoint_over_forward": t_adj / t_fwd,
+                        "gradient_cups": rows * n * steps / t_adj,
+                        "checkpoint_workspace_bytes": ck}
+        g64, n64 = grads[F64]
+        g32, n32 = grads[F32]
+        gb = Batch.from_ensemble(ens, dt0 * fac, steps, F64)
+        rel, _ = ctx.rel_l2(gb, g32, g64)
+        a64 = g64.view(rows, n).abs().amax(dim=1).cpu().numpy()
+        fin32 = torch.isfinite(g32.view(rows, n)).all(dim=1).cpu().numpy() & np.isfinite(n32.cpu().numpy())
+        ok = fin32 & np.isfinite(a64) & np.isfinite(n64.cpu().numpy())
+        dnu = ((n32 - n64).abs() / n64.abs()[torch.from_numpy(ok).to(dev)].max()).cpu().numpy()
+        rec["grad_u0_fp64_row_absmax"] = {"max": float(np.max(a64)), "median": float(np.median(a64))}
+        rec["rows_with_nonfinite_fp32_gradient"] = int(np.sum(~fin32))
+        rec["grad_u0_fp32_vs_fp64_rel_l2"] = {"max": float(np.max(rel[ok])), "median": float(np.median(rel[ok])),
+                                              "rows": int(np.sum(ok))}
+        rec["grad_nu_fp32_vs_fp64_max_rel"] = float(np.max(dnu[ok]))
+        out[name] = rec
+    out["note"] = ("gradient_cups = forward cell-updates of the problem per second of the adjoint call "
+                   "(checkpoint recompute + reverse sweep); checkpoint workspace per row = ceil(steps/k) "
+                   "checkpoints (FP32: state + compensation) + k + 1 segment states, k = ceil(sqrt(steps))")
+    return out
+
+
 def extras(args, ctx, ens, u0, batches, probe, dev, world, rank):
     import torch
 
@@ -527,6 +610,7 @@ def extras(args, ctx, ens, u0, batches, probe, dev, world, rank):
                         "iterations per step; CN and Picard at 10x the CFL dt, Newton at the "
                         "CFL dt on viscosity-raised rows (cell Peclet <= 1.5)")
     out["implicit_variants"] = variants
+    out["differentiation"] = differentiation_bench(ctx, dev)
 
     # ---- plain one-row-per-launch path on a subset, same kernels
     P = 64

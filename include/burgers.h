@@ -249,9 +249,12 @@ burgers_status burgers_solve_host(burgers_ctx* ctx, int32_t scheme, const burger
  * fixed. u0_dev holds u(0) and is not modified. At u_i = 0 the derivative of
  * u+ is taken as 0 and that of u- as 1. The forward states are recomputed
  * from checkpoints every `ckpt_stride` steps (0 = ceil(sqrt(nsteps))), with
- * (ceil(nsteps/stride) + stride + 1) * n values of context-owned workspace per
- * row; the nu gradient is accumulated in FP64. Rows longer than 4096 (FP32)
- * or 2048 (FP64) nodes: EINVAL. Asynchronous on `stream`. */
+ * (w ceil(nsteps/stride) + stride + 1) * m values of context-owned workspace
+ * per row: w = 2 for FP32 (state and compensation term), 1 for FP64, and m the
+ * capacity of the kernel shape that holds the row (the smallest of 32, 128,
+ * 512, 1024, 2048 and, FP32 only, 4096 nodes that is >= n). The nu gradient
+ * is accumulated in FP64. Rows longer than 4096 (FP32) or 2048 (FP64) nodes:
+ * EINVAL. Asynchronous on `stream`. */
 burgers_status burgers_adjoint(burgers_ctx* ctx, int32_t scheme, const burgers_batch* batch,
                                const void* u0_dev, const void* gT_dev, void* gu0_dev,
                                double* gnu_dev, int64_t ckpt_stride, burgers_stream stream);

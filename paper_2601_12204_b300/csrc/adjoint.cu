@@ -206,10 +206,14 @@ __global__ void __launch_bounds__(NT) k_adjoint(const T* __restrict__ u0, const 
     const bool per = rd.bc == BC_PERIODIC;
     const T r = T(rd.r), s = T(rd.s), h = T(0.5 * rd.r);
     const int64_t ns = rd.nsteps, k = ar.stride;
-    // checkpoints: ar.nckpt states of n values (FP32: followed by the n Kahan terms)
+    // Stored states use the kernel's own layout, element (j, thread) at
+    // j * NT + tid of a CAP-value slot, so that every store and load of a
+    // warp is one contiguous line. Checkpoints: ar.nckpt slots (FP32: each
+    // followed by a slot of Kahan terms); segment states: k + 1 slots.
+    constexpr int CAP = NT * C;
     constexpr int CKW = Kahan<T>::on ? 2 : 1;
     T* ck = ws + ar.ckpt;
-    T* sg = ws + ar.seg;  // segment states, k + 1 of n values
+    T* sg = ws + ar.seg;
     int p = 0;
     T v[C], lo[C];
 #pragma unroll
@@ -220,13 +224,12 @@ __global__ void __launch_bounds__(NT) k_adjoint(const T* __restrict__ u0, const 
     // ---- forward pass with checkpoints every k steps
     for (int64_t st = 0; st < ns; ++st) {
       if (st % k == 0) {
-        T* dst = ck + (st / k) * n * CKW;
+        T* dst = ck + (st / k) * CAP * CKW;
 #pragma unroll
-        for (int j = 0; j < C; ++j)
-          if (base + j < n) {
-            dst[base + j] = v[j];
-            if constexpr (Kahan<T>::on) dst[n + base + j] = lo[j];
-          }
+        for (int j = 0; j < C; ++j) {
+          dst[j * NT + tid] = v[j];
+          if constexpr (Kahan<T>::on) dst[CAP + j * NT + tid] = lo[j];
+        }
       }
       if (st + 1 == ns) break;  // the last state is not needed
       if constexpr (SCHEME == 0) fwd_explicit_step<T, NT, C>(v, lo, n, base, per, r, h, s, sm.xa, p);
@@ -242,25 +245,43 @@ __global__ void __launch_bounds__(NT) k_adjoint(const T* __restrict__ u0, const 
       const int64_t s0 = sgi * k;
       const int64_t s1 = (s0 + k < ns) ? s0 + k : ns;
       // recompute the states s0 .. s1 (BTCS needs u^{s+1}; explicit only u^s)
+      const T* src = ck + sgi * CAP * CKW;
 #pragma unroll
       for (int j = 0; j < C; ++j) {
-        v[j] = base + j < n ? ck[sgi * n * CKW + base + j] : T(0);
-        if constexpr (Kahan<T>::on) lo[j] = base + j < n ? ck[sgi * n * CKW + n + base + j] : T(0);
+        v[j] = base + j < n ? src[j * NT + tid] : T(0);
+        if constexpr (Kahan<T>::on) lo[j] = base + j < n ? src[CAP + j * NT + tid] : T(0);
       }
       const int64_t last = SCHEME == 0 ? s1 - 1 : s1;
       for (int64_t st = s0; st <= last; ++st) {
-        T* dst = sg + (st - s0) * n;
+        T* dst = sg + (st - s0) * CAP;
 #pragma unroll
-        for (int j = 0; j < C; ++j)
-          if (base + j < n) dst[base + j] = v[j];
+        for (int j = 0; j < C; ++j) dst[j * NT + tid] = v[j];
         if (st == last) break;
         if constexpr (SCHEME == 0) fwd_explicit_step<T, NT, C>(v, lo, n, base, per, r, h, s, sm.xa, p);
         else fwd_btcs_step<T, NT, C>(v, lo, n, base, per, r, s, sm.bt, sm.xa, p);
       }
-      for (int64_t st = s1 - 1; st >= s0; --st) {
-        const T* us = sg + (st - s0) * n;
+      // reverse through the segment; the state of the next (earlier) step is
+      // loaded while this one computes, and BTCS takes u^{s+1} from the
+      // previous iteration's u^s
+      T vn[C], vx[C];
+      {
+        const T* us = sg + (s1 - 1 - s0) * CAP;
 #pragma unroll
-        for (int j = 0; j < C; ++j) v[j] = base + j < n ? us[base + j] : T(0);
+        for (int j = 0; j < C; ++j) vn[j] = base + j < n ? us[j * NT + tid] : T(0);
+        if constexpr (SCHEME == 1) {
+          const T* ux = sg + (s1 - s0) * CAP;  // u^{s1}
+#pragma unroll
+          for (int j = 0; j < C; ++j) vx[j] = base + j < n ? ux[j * NT + tid] : T(0);
+        }
+      }
+      for (int64_t st = s1 - 1; st >= s0; --st) {
+#pragma unroll
+        for (int j = 0; j < C; ++j) v[j] = vn[j];
+        if (st > s0) {
+          const T* us = sg + (st - 1 - s0) * CAP;
+#pragma unroll
+          for (int j = 0; j < C; ++j) vn[j] = base + j < n ? us[j * NT + tid] : T(0);
+        }
         T part = T(0);
         if constexpr (SCHEME == 0) {
           // transposed explicit step
@@ -317,10 +338,7 @@ __global__ void __launch_bounds__(NT) k_adjoint(const T* __restrict__ u0, const 
             rhs = lam[j];
           };
           resident_solve<T, NT, C>(mu, ah, ch, trows, n, per, sm.bt);
-          const T* ux = sg + (st + 1 - s0) * n;  // x = u^{s+1}
-          T xv[C];
-#pragma unroll
-          for (int j = 0; j < C; ++j) xv[j] = base + j < n ? ux[base + j] : T(0);
+          T (&xv)[C] = vx;  // x = u^{s+1}
           xch_publish<T, NT, C>(xv, jstar, sm.xb, p);
           __syncthreads();
           T xl0, xr0, xw;
@@ -338,6 +356,8 @@ __global__ void __launch_bounds__(NT) k_adjoint(const T* __restrict__ u0, const 
             if (!bI && gi < n) part = tfma(mu[j], xr - T(2) * xv[j] + xl, part);
             lam[j] = gi < n ? out : T(0);
           }
+#pragma unroll
+          for (int j = 0; j < C; ++j) vx[j] = v[j];  // u^s is the next step's u^{s+1}
         }
         gacc += double(part);
       }
@@ -428,10 +448,12 @@ burgers_status adjoint_run(burgers_ctx* ctx, int scheme, const burgers_batch* ba
       if (k < 1) k = 1;
       a.stride = k;
       a.nckpt = in.nsteps > 0 ? (in.nsteps + k - 1) / k : 0;
+      // state slots of the kernel shape's capacity (its [j][thread] layout)
+      const int64_t cap = int64_t(shapes[g].nt) * shapes[g].c;
       a.ckpt = ws;
-      ws += ((a.nckpt * in.n * (dtype == 0 ? 2 : 1) + 63) / 64) * 64;
+      ws += ((a.nckpt * cap * (dtype == 0 ? 2 : 1) + 63) / 64) * 64;
       a.seg = ws;
-      ws += (((k + 1) * in.n + 63) / 64) * 64;
+      ws += (((k + 1) * cap + 63) / 64) * 64;
       a.out_index = int32_t(pr.second);
       a.pad = 0;
       rows.push_back(d);
