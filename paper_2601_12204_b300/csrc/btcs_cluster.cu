@@ -14,11 +14,14 @@
 //           row per CTA in Y_{k-1}, Y_k, Y_{k+1} (cyclic when periodic), which
 //           warp 0 of CTA 0 solves, one row per lane (Sherman-Morrison
 //           correction with its denominator in FP64).
-// CTA 0 sends every CTA its Y and P and the new values of the nodes next to
-// its ends (computed with the owners' arithmetic from their operands), so the
-// neighbour values of the next step need no further exchange. A step costs two
-// cluster barriers and two CTA barriers. Increment form and Kahan-compensated
-// FP32 state as in btcs.cu.
+// Every CTA stages its contribution to the cluster system in its own shared
+// memory (slots double-buffered by step parity); after one cluster barrier
+// warp 0 of each CTA reads all of them through distributed shared memory and
+// solves the same small system with the same arithmetic, keeping its own Y and P and the new values
+// of the nodes next to its ends (computed with the owners' arithmetic from
+// their operands), so the neighbour values of the next step need no further
+// exchange. A step costs one cluster barrier and three CTA barriers.
+// Increment form and Kahan-compensated FP32 state as in btcs.cu.
 #include <cooperative_groups.h>
 
 #include <type_traits>
@@ -31,9 +34,11 @@ namespace cg = cooperative_groups;
 
 namespace burgers {
 
-// What each CTA contributes to the cluster system (written into CTA 0).
+// What each CTA contributes to the cluster system (read by every CTA of the
+// cluster). Aligned and padded to 16 bytes, so that a remote read is a few
+// vector loads.
 template <typename T>
-struct ClusterSlot {
+struct alignas(16) ClusterSlot {
   T eah, ech, edh;      // end relation of the interface chunk
   T rd0, ra0, rg0;      // first-row relation of chunk 0
   T yl, al, gl;         // block relation of chunk ti - 1 (when ti > 0)
@@ -44,7 +49,21 @@ struct ClusterSlot {
   int jf;               // end row of chunk 0 (0: chunk 0 is a single node)
 };
 
-// What CTA 0 sends back to each CTA.
+// Copies a slot from (distributed) shared memory in 16-byte pieces.
+template <typename T>
+__device__ __forceinline__ ClusterSlot<T> load_slot(const ClusterSlot<T>* p) {
+  static_assert(sizeof(ClusterSlot<T>) % 16 == 0, "slot size must be a multiple of 16 bytes");
+  union {
+    ClusterSlot<T> s;
+    float4 v[sizeof(ClusterSlot<T>) / 16];
+  } u;
+  const float4* src = reinterpret_cast<const float4*>(p);
+#pragma unroll
+  for (int i = 0; i < int(sizeof(ClusterSlot<T>) / 16); ++i) u.v[i] = src[i];
+  return u.s;
+}
+
+// What the cluster solve leaves for its CTA.
 template <typename T>
 struct ClusterReply {
   T Y, P;               // own interface value and the one before the block
@@ -57,7 +76,7 @@ struct ClusterShared {
   T V[NT + NT / 32];    // block right-hand side of the interface coupling
   T Wg[NT + NT / 32];   // ... and its solution (gamma)
   T hfirst[NT], hlast[NT];
-  ClusterSlot<T> slots[16];  // CTA 0 only
+  ClusterSlot<T> slots[2][16];  // [step parity][contributing CTA]
   ClusterReply<T> reply;
 };
 
@@ -147,21 +166,33 @@ __device__ __forceinline__ void block_solve3(ClusterShared<T, NT>& cs, int lane)
   }
 }
 
-// Warp 0 of CTA 0: the cluster system in the interface values Y_k, one row
-// per lane (lanes >= CS carry identity rows), solved by cyclic reduction over
-// the lanes; the cyclic corners are split off by Sherman-Morrison with the
-// correction factor's denominator in FP64 (sm_factor, as in the CTA-level
-// solve). Lane k then sends CTA
-// k its Y and P and the new values of the nodes next to its ends. Dirichlet
-// rows have identity rows at the row's ends, so the first block has no left
-// neighbour (P = 0) and the system is plain.
+// Warp 0 of every CTA: the cluster system in the interface values Y_k, one
+// row per lane (lanes >= CS carry identity rows), from the contributions in
+// slots[par], solved by cyclic reduction over the lanes; the cyclic corners
+// are split off by Sherman-Morrison with the correction factor's denominator
+// in FP64 (sm_factor, as in the CTA-level solve). Every CTA solves the same
+// system with the same arithmetic and keeps, for itself (rank), its Y and P
+// and the new values of the nodes next to its ends. Dirichlet rows have
+// identity rows at the row's ends, so the first block has no left neighbour
+// (P = 0) and the system is plain.
 template <typename T, int NT, int CS>
 __device__ __forceinline__ void cluster_solve(ClusterShared<T, NT>& cs, bool per, int lane,
-                                              cg::cluster_group& cluster) {
+                                              int rank, int par, cg::cluster_group& cluster) {
   const bool on = lane < CS;
   const int k = on ? lane : 0;
-  const ClusterSlot<T>& s = cs.slots[k];
-  const ClusterSlot<T>& sn = cs.slots[(k + 1) % CS];
+  // lane k reads CTA k's contribution from that CTA's memory, and the fields
+  // of CTA k + 1's that its row needs from lane k + 1
+  const ClusterSlot<T> s = load_slot(cluster.map_shared_rank(&cs.slots[par][k], k));
+  struct {
+    T ra0, rg0, rd0, a0, g0, y0;
+    int ti;
+  } sn;
+  {
+    const int kn = (k + 1) % CS;
+    sn.ra0 = shfl(s.ra0, kn); sn.rg0 = shfl(s.rg0, kn); sn.rd0 = shfl(s.rd0, kn);
+    sn.a0 = shfl(s.a0, kn); sn.g0 = shfl(s.g0, kn); sn.y0 = shfl(s.y0, kn);
+    sn.ti = __shfl_sync(FULL_MASK, s.ti, kn);
+  }
   T a = T(0), b = T(1), c = T(0), d = T(0), uu = T(0);
   if (on) {
     const T A = s.eah, B = T(1) - s.ech * sn.ra0, C = -s.ech * sn.rg0;
@@ -223,12 +254,13 @@ __device__ __forceinline__ void cluster_solve(ClusterShared<T, NT>& cs, bool per
   }
   const T last_prev = shfl(last, (lane + CS - 1) % CS);
   const T first_next = shfl(first, (lane + 1) % CS);
-  if (on) {
-    ClusterReply<T>* rp = cluster.map_shared_rank(&cs.reply, k);
-    rp->Y = Y;
-    rp->P = P;
-    rp->halo_l = (k > 0 || per) ? last_prev : T(0);
-    rp->halo_r = (k + 1 < CS || per) ? first_next : T(0);
+  const T myY = shfl(Y, rank), myP = shfl(P, rank);
+  const T hl = shfl(last_prev, rank), hr = shfl(first_next, rank);
+  if (lane == 0) {
+    cs.reply.Y = myY;
+    cs.reply.P = myP;
+    cs.reply.halo_l = (rank > 0 || per) ? hl : T(0);
+    cs.reply.halo_r = (rank + 1 < CS || per) ? hr : T(0);
   }
 }
 
@@ -281,6 +313,7 @@ __launch_bounds__(NT, (sizeof(T) == 4 && NT <= 512) ? 512 / NT : 1)
   cluster.sync();
   const T r = T(rd.r), s = T(rd.s), ds1 = T(1) + T(2) * s;
   T ch[C], ah[C], dd[C];
+  int par = 0;  // slot buffer of this step
   for (int64_t step = 0; step < rd.nsteps; ++step) {
     const T halo_l = cs.reply.halo_l, halo_r = cs.reply.halo_r;
     T left = tid > 0 ? cs.hlast[tid - 1] : halo_l;
@@ -361,8 +394,9 @@ __launch_bounds__(NT, (sizeof(T) == 4 && NT <= 512) ? 512 / NT : 1)
     __syncthreads();
     if (warp == 0) {
       // block rows of chunks 0..tl-1 (the interface row tl is the cluster's)
-      T s_eah = T(0), s_ech = T(0), s_edh = T(0);
-      if (lane == 0) { s_eah = sm.A[sk(tl)]; s_ech = sm.Cc[sk(tl)]; s_edh = sm.D[sk(tl)]; }
+      // (every lane reads the interface chunk's end relation before the rows
+      // below overwrite it, and builds this CTA's contribution in registers)
+      const T s_eah = sm.A[sk(tl)], s_ech = sm.Cc[sk(tl)], s_edh = sm.D[sk(tl)];
       __syncwarp();
 #pragma unroll
       for (int q = 0; q < Q; ++q) {
@@ -399,12 +433,15 @@ __launch_bounds__(NT, (sizeof(T) == 4 && NT <= 512) ? 512 / NT : 1)
         if constexpr (Kahan<T>::on) { sl.lf = lo[0]; sl.ll = lo[jl * NT + tl]; }
         sl.ti = tl;
         sl.jf = tl == 0 ? jl : C - 1;
-        *cluster.map_shared_rank(&cs.slots[rank], 0) = sl;
+        // staged in this CTA's own memory; every CTA reads it after the
+        // cluster barrier
+        if (lane == 0) cs.slots[par][rank] = sl;
       }
     }
     cluster.sync();
-    if (rank == 0 && warp == 0) cluster_solve<T, NT, CS>(cs, per, lane, cluster);
-    cluster.sync();
+    if (warp == 0) cluster_solve<T, NT, CS>(cs, per, lane, rank, par, cluster);
+    __syncthreads();
+    par ^= 1;
     // ---- chunk-end values from the block relations, back-substitution
     const T Y = cs.reply.Y, P = cs.reply.P;
     if (tid <= tl) {
