@@ -5,7 +5,9 @@
 Each case builds one seeded batch on the device, runs the CFL reduction, then
 exactly one advance call of the named scheme (one resident kernel launch, or
 the streaming / multi-level launch sequence for long rows), and prints its
-CUDA-event time.
+CUDA-event time. The adjoint cases (adjoint-explicit, adjoint-btcs) time one
+burgers_adjoint call instead (checkpointed forward recompute and reverse
+sweep) on dJ/du(T) = u(T), after one untimed forward advance.
 """
 from __future__ import annotations
 
@@ -19,7 +21,8 @@ import numpy as np
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--case", choices=["explicit", "btcs", "rk4"], default="explicit")
+    ap.add_argument("--case", choices=["explicit", "btcs", "rk4", "adjoint-explicit", "adjoint-btcs"],
+                    default="explicit")
     ap.add_argument("--rows", type=int, default=4096)
     ap.add_argument("--n", type=int, default=4096)
     ap.add_argument("--steps", type=int, default=200)
@@ -51,9 +54,12 @@ def main():
         ctx.set(L.BURGERS_OPT_CLUSTER, 0)
     u0 = torch.tensor(ens.u0, dtype=tdt, device="cuda")
     dt = ctx.cfl_dt(Batch.from_ensemble(ens, 1.0, 0, dt_code), u0, 0.4)
-    fac = a.dt_factor if a.dt_factor is not None else (10.0 if a.case == "btcs" else 1.0)
+    btcs_like = a.case in ("btcs", "adjoint-btcs")
+    fac = a.dt_factor if a.dt_factor is not None else (10.0 if btcs_like else 1.0)
     b = Batch.from_ensemble(ens, dt * fac, a.steps, dt_code)
-    scheme = {"explicit": L.BURGERS_EXPLICIT, "btcs": L.BURGERS_BTCS, "rk4": L.BURGERS_RK4}[a.case]
+    scheme = {"explicit": L.BURGERS_EXPLICIT, "btcs": L.BURGERS_BTCS, "rk4": L.BURGERS_RK4,
+              "adjoint-explicit": L.BURGERS_EXPLICIT, "adjoint-btcs": L.BURGERS_BTCS}[a.case]
+    adjoint = a.case.startswith("adjoint")
     if a.tune_file and os.path.exists(a.tune_file):
         ctx.tune_load(a.tune_file)
     elif a.autotune:
@@ -62,11 +68,19 @@ def main():
         ctx.tune_save(path)
         print(json.dumps({"tuned_classes": ntuned, "table": open(path).read().splitlines()[1:]}))
     times = []
+    if adjoint:
+        gT = u0.clone()
+        ctx.advance(scheme, b, gT)  # dJ/du(T) = u(T): J = |u(T)|^2 / 2
+        gu0 = torch.empty_like(u0)
+        gnu = torch.empty(ens.count, dtype=torch.float64, device="cuda")
     for _ in range(a.repeat):
         u = u0.clone()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        ctx.advance(scheme, b, u)
+        if adjoint:
+            ctx.adjoint(scheme, b, u0, gT, gu0, gnu)
+        else:
+            ctx.advance(scheme, b, u)
         e1.record()
         torch.cuda.synchronize()
         times.append(e0.elapsed_time(e1))
