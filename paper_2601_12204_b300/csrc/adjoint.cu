@@ -380,9 +380,240 @@ __global__ void __launch_bounds__(NT) k_adjoint(const T* __restrict__ u0, const 
   }
 }
 
+// ---------------------------------------------------------------------------
+// Explicit scheme, rows of exactly NT*C nodes. Same adjoint as k_adjoint
+// (forward pass with checkpoints every k steps, per segment a recompute that
+// stores the states, then the transposed steps backwards through them), with
+// the forward step of k_explicit_resident: FP32 evaluates the split state
+// u = uh + d and folds d into uh after every step whose global index + 1 is a
+// multiple of SPLIT_FOLD, so the checkpoint pass and every recompute follow
+// the same rounding and give the main kernel's trajectory; FP64 updates in
+// place. Neighbour values move branch-free (shuffles inside a warp, one
+// predicated shared-memory store per warp edge and one barrier per exchange,
+// u and lambda together in the reverse step), and the boundary cases of
+// Dirichlet rows are the handful of nodes next to the row's ends.
+template <typename T, int NT>
+struct AdjFastShared {
+  static constexpr int NW = NT / 32;
+  T slot[2][2][2][NW];  // [parity][0: first of a warp, 1: last][quantity][warp]
+  double red[NW];
+};
+
+// Exchanges K quantities' chunk-edge values: left[k] = value of quantity k
+// at the node before this thread's first, right[k] after its last (periodic
+// wrap through the first and last warp).
+template <typename T, int NT, int K>
+__device__ __forceinline__ void adj_xch(const T (&first)[K], const T (&last)[K], int p,
+                                        AdjFastShared<T, NT>& sh, T (&left)[K], T (&right)[K]) {
+  constexpr int NW = NT / 32;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    left[k] = shfl(last[k], (lane + 31) & 31);
+    right[k] = shfl(first[k], (lane + 1) & 31);
+  }
+  if constexpr (NW > 1) {
+    const bool lo_lane = lane == 0;
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+      st_shared_if(&sh.slot[p][lo_lane ? 0 : 1][k][warp], lo_lane ? first[k] : last[k],
+                   lo_lane || lane == 31);
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const T lv = sh.slot[p][1][k][(warp + NW - 1) % NW];
+      const T rv = sh.slot[p][0][k][(warp + 1) % NW];
+      left[k] = lane == 0 ? lv : left[k];
+      right[k] = lane == 31 ? rv : right[k];
+    }
+  }
+}
+
+// One forward step (Eq. 21) of the global step index `st`.
+template <typename T, int NT, int C, int BCT>
+__device__ __forceinline__ void adj_fwd_step(T (&v)[C], T (&d)[C], int64_t st, int& p, T r, T h,
+                                             T s, AdjFastShared<T, NT>& sh) {
+  constexpr bool SPLIT = Kahan<T>::on;
+  const int tid = threadIdx.x;
+  auto w = [&](int j) -> T { return SPLIT ? v[j] + d[j] : v[j]; };
+  T fl[1] = {w(0)}, la[1] = {w(C - 1)}, L[1], R[1];
+  adj_xch<T, NT, 1>(fl, la, p, sh, L, R);
+  p ^= 1;
+  T wl = L[0], wc = fl[0];
+#pragma unroll
+  for (int j = 0; j < C; ++j) {
+    const T wr = (j + 1 < C) ? w(j + 1) : R[0];
+    bool keep = false;
+    if constexpr (BCT == BC_DIRICHLET) keep = (j == 0 && tid == 0) || (j == C - 1 && tid == NT - 1);
+    if constexpr (SPLIT) {
+      const T dn = explicit_increment(wc, wl, wr, r, h, s, d[j]);
+      if (!keep) d[j] = dn;
+    } else {
+      const T nv = explicit_increment(wc, wl, wr, r, h, s, wc);
+      if (!keep) v[j] = nv;
+    }
+    wl = wc;
+    wc = wr;
+  }
+  if constexpr (SPLIT) {
+    if ((st + 1) % SPLIT_FOLD == 0) {
+#pragma unroll
+      for (int j = 0; j < C; ++j) {
+        const T t = v[j] + d[j];
+        d[j] = d[j] - (t - v[j]);
+        v[j] = t;
+      }
+    }
+  }
+}
+
+template <typename T, int NT, int C, int BCT>
+__device__ __forceinline__ void adj_explicit_exact_row(const T* __restrict__ u0, const T* gT,
+                                                       T* gu0, double* __restrict__ gnu,
+                                                       const RowDesc& rd, const AdjRow& ar,
+                                                       T* __restrict__ ws,
+                                                       AdjFastShared<T, NT>& sh) {
+  constexpr bool SPLIT = Kahan<T>::on;
+  constexpr int CAP = NT * C, CKW = SPLIT ? 2 : 1;
+  const int tid = threadIdx.x, base = tid * C;
+  const T r = T(rd.r), s = T(rd.s), h = T(0.5 * rd.r);
+  const int64_t ns = rd.nsteps, k = ar.stride;
+  T* ck = ws + ar.ckpt;
+  T* sg = ws + ar.seg;
+  int p = 0;
+  T v[C], d[C];
+#pragma unroll
+  for (int j = 0; j < C; ++j) {
+    v[j] = u0[rd.offset + base + j];
+    d[j] = T(0);
+  }
+  // ---- forward pass with checkpoints every k steps
+  for (int64_t st = 0; st < ns; ++st) {
+    if (st % k == 0) {
+      T* dst = ck + (st / k) * CAP * CKW;
+#pragma unroll
+      for (int j = 0; j < C; ++j) {
+        dst[j * NT + tid] = v[j];
+        if constexpr (SPLIT) dst[CAP + j * NT + tid] = d[j];
+      }
+    }
+    if (st + 1 == ns) break;  // the last state is not needed
+    adj_fwd_step<T, NT, C, BCT>(v, d, st, p, r, h, s, sh);
+  }
+  // ---- reverse pass
+  T lam[C];
+#pragma unroll
+  for (int j = 0; j < C; ++j) lam[j] = gT[rd.offset + base + j];
+  double gacc = 0.0;
+  const int64_t nseg = ns > 0 ? (ns + k - 1) / k : 0;
+  for (int64_t sgi = nseg - 1; sgi >= 0; --sgi) {
+    const int64_t s0 = sgi * k;
+    const int64_t s1 = (s0 + k < ns) ? s0 + k : ns;
+    // recompute the states s0 .. s1 - 1 (u = uh + d for FP32)
+    {
+      const T* src = ck + sgi * CAP * CKW;
+#pragma unroll
+      for (int j = 0; j < C; ++j) {
+        v[j] = src[j * NT + tid];
+        d[j] = SPLIT ? src[CAP + j * NT + tid] : T(0);
+      }
+    }
+    for (int64_t st = s0; st < s1; ++st) {
+      T* dst = sg + (st - s0) * CAP;
+#pragma unroll
+      for (int j = 0; j < C; ++j) dst[j * NT + tid] = SPLIT ? v[j] + d[j] : v[j];
+      if (st + 1 == s1) break;
+      adj_fwd_step<T, NT, C, BCT>(v, d, st, p, r, h, s, sh);
+    }
+    // transposed steps backwards through the segment; the state of the next
+    // (earlier) step is loaded while this one computes
+    T vn[C];
+    {
+      const T* us = sg + (s1 - 1 - s0) * CAP;
+#pragma unroll
+      for (int j = 0; j < C; ++j) vn[j] = us[j * NT + tid];
+    }
+    for (int64_t st = s1 - 1; st >= s0; --st) {
+#pragma unroll
+      for (int j = 0; j < C; ++j) v[j] = vn[j];
+      if (st > s0) {
+        const T* us = sg + (st - 1 - s0) * CAP;
+#pragma unroll
+        for (int j = 0; j < C; ++j) vn[j] = us[j * NT + tid];
+      }
+      T fl[2] = {v[0], lam[0]}, la[2] = {v[C - 1], lam[C - 1]}, L[2], R[2];
+      adj_xch<T, NT, 2>(fl, la, p, sh, L, R);
+      p ^= 1;
+      T ul = L[0], ll = L[1], part = T(0);
+      T nl[C];
+#pragma unroll
+      for (int j = 0; j < C; ++j) {
+        const T u = v[j];
+        const T ur = (j + 1 < C) ? v[j + 1] : R[0];
+        const T lr = (j + 1 < C) ? lam[j + 1] : R[1];
+        bool upI = true, upR = true, upL = true;  // node, right, left neighbour updated
+        if constexpr (BCT == BC_DIRICHLET) {
+          const int gi = base + j;  // the row has CAP nodes; 0 and CAP - 1 are held
+          upI = gi != 0 && gi != CAP - 1;
+          upR = gi + 1 < CAP - 1;
+          upL = gi - 1 > 0;
+        }
+        const T dl = u - ul, dr = ur - u;
+        const T dii = upI ? T(1) - T(2) * s - r * ((u > T(0) ? dl : dr) + tabs(u)) : T(1);
+        T acc = dii * lam[j];
+        if (upR) acc = tfma(tfma(r, tmax(ur, T(0)), s), lr, acc);
+        if (upL) acc = tfma(tfma(-r, tmin(ul, T(0)), s), ll, acc);
+        if (upI) part = tfma(lam[j], dr - dl, part);
+        nl[j] = acc;
+        ul = u;
+        ll = lam[j];
+      }
+#pragma unroll
+      for (int j = 0; j < C; ++j) lam[j] = nl[j];
+      gacc += double(part);
+    }
+  }
+  // ---- outputs
+#pragma unroll
+  for (int j = 0; j < C; ++j) gu0[rd.offset + base + j] = lam[j];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) gacc += __shfl_xor_sync(FULL_MASK, gacc, o);
+  if ((tid & 31) == 0) sh.red[tid >> 5] = gacc;
+  __syncthreads();
+  if (tid == 0) {
+    double t = 0.0;
+    for (int w = 0; w < NT / 32; ++w) t += sh.red[w];
+    gnu[ar.out_index] = t * rd.ds_dnu;
+  }
+  __syncthreads();
+}
+
+template <typename T, int NT, int C>
+__global__ void __launch_bounds__(NT) k_adjoint_explicit_exact(
+    const T* __restrict__ u0, const T* gT, T* gu0, double* __restrict__ gnu,
+    const RowDesc* __restrict__ rows, const AdjRow* __restrict__ arows, int count,
+    int* __restrict__ counter, T* __restrict__ ws) {
+  __shared__ AdjFastShared<T, NT> sh;
+  __shared__ int s_item;
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
+    __syncthreads();
+    const int item = s_item;
+    if (item >= count) return;
+    const RowDesc rd = rows[item];
+    const AdjRow ar = arows[item];
+    if (rd.bc == BC_PERIODIC)
+      adj_explicit_exact_row<T, NT, C, BC_PERIODIC>(u0, gT, gu0, gnu, rd, ar, ws, sh);
+    else
+      adj_explicit_exact_row<T, NT, C, BC_DIRICHLET>(u0, gT, gu0, gnu, rd, ar, ws, sh);
+  }
+}
+
 #define REG_ADJ(T, DT, NT, C)                                                                      \
   reg.push_back({K_ADJ_EXPLICIT, DT, NT, C, 0, reinterpret_cast<const void*>(&k_adjoint<T, NT, C, 0>), \
                  0});                                                                              \
+  reg.push_back({K_ADJ_EXPLICIT, DT, NT, C, 1,                                                    \
+                 reinterpret_cast<const void*>(&k_adjoint_explicit_exact<T, NT, C>), 0});            \
   reg.push_back({K_ADJ_BTCS, DT, NT, C, 0, reinterpret_cast<const void*>(&k_adjoint<T, NT, C, 1>), 0});
 
 void register_adjoint(std::vector<KernelEntry>& reg) {
@@ -414,7 +645,9 @@ burgers_status adjoint_run(burgers_ctx* ctx, int scheme, const burgers_batch* ba
   const int nshapes = dtype == 0 ? 6 : 5;
   const int kind = scheme == BURGERS_EXPLICIT ? K_ADJ_EXPLICIT : K_ADJ_BTCS;
   const size_t esz = dtype == 0 ? 4 : 8;
-  std::vector<std::vector<std::pair<double, int64_t>>> groups(static_cast<size_t>(nshapes));
+  // groups by (shape, exact): explicit rows of exactly nt * c nodes take the
+  // k_adjoint_explicit_exact kernel of that shape
+  std::vector<std::vector<std::pair<double, int64_t>>> groups(static_cast<size_t>(2 * nshapes));
   for (int64_t b = 0; b < batch->count; ++b) {
     const burgers_instance& in = batch->inst[b];
     if (in.n > adjoint_max_n(dtype))
@@ -423,14 +656,16 @@ burgers_status adjoint_run(burgers_ctx* ctx, int scheme, const burgers_batch* ba
     for (int i = 0; i < nshapes && pick < 0; ++i)
       if (int64_t(shapes[i].nt) * shapes[i].c >= in.n && shapes[i].c < in.n) pick = i;
     if (pick < 0) return set_error(BURGERS_EINVAL, "adjoint: no kernel shape fits the row");
-    groups[size_t(pick)].emplace_back(double(in.n) * double(in.nsteps + 1), b);
+    const bool ex = scheme == BURGERS_EXPLICIT && in.n == int64_t(shapes[pick].nt) * shapes[pick].c;
+    groups[size_t(2 * pick + (ex ? 1 : 0))].emplace_back(double(in.n) * double(in.nsteps + 1), b);
   }
   std::vector<RowDesc> rows;
   std::vector<AdjRow> arows;
   std::vector<std::pair<int, int>> ranges;  // (shape, count)
   int64_t ws = 0;
-  for (int g = 0; g < nshapes; ++g) {
-    auto& G = groups[size_t(g)];
+  for (int gx = 0; gx < 2 * nshapes; ++gx) {
+    const int g = gx / 2;
+    auto& G = groups[size_t(gx)];
     if (G.empty()) continue;
     std::stable_sort(G.begin(), G.end(), [](const auto& a, const auto& b) { return a.first > b.first; });
     for (auto& pr : G) {
@@ -459,7 +694,7 @@ burgers_status adjoint_run(burgers_ctx* ctx, int scheme, const burgers_batch* ba
       rows.push_back(d);
       arows.push_back(a);
     }
-    ranges.emplace_back(g, int(G.size()));
+    ranges.emplace_back(gx, int(G.size()));
   }
   cudaError_t e = ctx->adjws.ensure(size_t(std::max<int64_t>(ws, 1)) * esz);
   if (e != cudaSuccess) return set_error(BURGERS_ENOMEM, "adjoint workspace: out of device memory");
@@ -487,8 +722,8 @@ burgers_status adjoint_run(burgers_ctx* ctx, int scheme, const burgers_batch* ba
   if (e != cudaSuccess) return cuda_error(e, "adjoint upload");
   int begin = 0;
   for (size_t q = 0; q < ranges.size(); ++q) {
-    const AShape sh = shapes[ranges[q].first];
-    const KernelEntry* k = find_kernel(kind, dtype, sh.nt, sh.c, 0);
+    const AShape sh = shapes[ranges[q].first / 2];
+    const KernelEntry* k = find_kernel(kind, dtype, sh.nt, sh.c, ranges[q].first % 2);
     if (!k) return set_error(BURGERS_EINVAL, "adjoint kernel shape missing");
     int cnt = ranges[q].second;
     int occ = 0;

@@ -44,6 +44,21 @@ __device__ __forceinline__ float recip(float x) {
 }
 __device__ __forceinline__ double recip(double x) { return 1.0 / x; }
 
+// Shared-memory store executed only where pred holds: a predicated store
+// instruction, so the edge lanes publishing their values cost no branch.
+__device__ __forceinline__ void st_shared_if(float* p, float v, bool pred) {
+  asm volatile(
+      "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %2, 0;\n\t@q st.shared.f32 [%0], %1;\n\t}"
+      :: "r"(static_cast<unsigned>(__cvta_generic_to_shared(p))), "f"(v), "r"(int(pred))
+      : "memory");
+}
+__device__ __forceinline__ void st_shared_if(double* p, double v, bool pred) {
+  asm volatile(
+      "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %2, 0;\n\t@q st.shared.f64 [%0], %1;\n\t}"
+      :: "r"(static_cast<unsigned>(__cvta_generic_to_shared(p))), "d"(v), "r"(int(pred))
+      : "memory");
+}
+
 template <typename T>
 __device__ __forceinline__ T shfl(T v, int src) {
   return __shfl_sync(FULL_MASK, v, src);

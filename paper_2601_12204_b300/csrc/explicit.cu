@@ -25,21 +25,6 @@ namespace burgers {
 enum : int { MODE_EXACT = 0, MODE_RAGGED = 1, MODE_WINDOW = 2, MODE_WINDOW_DIR = 3 };
 enum : int { INTEG_EULER = 0, INTEG_RK4 = 1 };
 
-// Shared-memory store executed only where pred holds: a predicated store
-// instruction, so the edge lanes publishing their values cost no branch.
-__device__ __forceinline__ void st_shared_if(float* p, float v, bool pred) {
-  asm volatile(
-      "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %2, 0;\n\t@q st.shared.f32 [%0], %1;\n\t}"
-      :: "r"(static_cast<unsigned>(__cvta_generic_to_shared(p))), "f"(v), "r"(int(pred))
-      : "memory");
-}
-__device__ __forceinline__ void st_shared_if(double* p, double v, bool pred) {
-  asm volatile(
-      "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %2, 0;\n\t@q st.shared.f64 [%0], %1;\n\t}"
-      :: "r"(static_cast<unsigned>(__cvta_generic_to_shared(p))), "d"(v), "r"(int(pred))
-      : "memory");
-}
-
 // Exchanges this thread's edge values for its neighbours' (left = value of
 // the node before its first, right = after its last). Periodic rows wrap
 // through the slots of the first and last warp; WRAPX rows (ragged periodic)

@@ -183,3 +183,34 @@ def test_config5_sampled(ctx, scheme):
         rel = oracle.rel_l2(got[o:o + N], ref[j * N:(j + 1) * N])
         assert rel <= 1e-4, f"row {b}: {rel}"
         assert abs(gnu[b] - gnu_ref[j]) <= 1e-3 * abs(gnu_ref[j]) + 1e-6 * np.max(np.abs(gnu_ref))
+
+
+@pytest.mark.parametrize("dtype", [F64, F32])
+@pytest.mark.parametrize("bc", [W.PERIODIC, W.DIRICHLET])
+def test_explicit_adjoint_exact_rows(ctx, dtype, bc):
+    """Rows of exactly a kernel shape's capacity take the exact-row explicit
+    adjoint kernel (split-state forward, folds on the global step index):
+    oracle parity, and a gradient bitwise independent of the checkpoint
+    stride (70 steps: segments that do not line up with the 32-step folds)."""
+    ns = [32, 128, 512, 1024, 2048] + ([4096] if dtype == F32 else [])
+    parts = []
+    for n in ns:
+        e = W.fourier_ensemble(2, n, seed=n + 5)
+        e.bcs[:] = bc
+        parts.append(e)
+    counts = np.array([p.count for p in parts])
+    lens = np.concatenate([p.ns for p in parts])
+    offs = np.zeros(lens.size, np.int64)
+    offs[1:] = np.cumsum(lens[:-1])
+    cat = lambda k: np.concatenate([getattr(p, k) for p in parts])  # noqa: E731
+    ens = W.Ensemble(cat("u0"), offs, lens, cat("bcs"), cat("dxs"), cat("nus"), cat("x0"),
+                     cat("length"))
+    assert counts.sum() == ens.count
+    steps = 70
+    dts, gT = _problem(ens, EXPLICIT, steps, 1.0)
+    ref, gnu_ref = _oracle_grads(EXPLICIT, ens, dts, steps, gT)
+    got, gnu = _gpu_grads(ctx, EXPLICIT, ens, dts, steps, gT, dtype)
+    _check(ens, got, ref, gnu, gnu_ref, dtype, f"exact-row adjoint bc{bc}")
+    for stride in (1, 7, 32, 70, 100):
+        g2, n2 = _gpu_grads(ctx, EXPLICIT, ens, dts, steps, gT, dtype, stride)
+        assert np.array_equal(got, g2) and np.array_equal(gnu, n2), f"stride {stride}"
