@@ -303,17 +303,22 @@ def run_ours(args):
 
     ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
 
+    # the timed step: the CFL time step of Eq. 7-8 on the device, then both
+    # advances reading it there (no host synchronisation inside the step)
+    dtd = torch.empty(B_ROWS, dtype=torch.float64, device=dev)
+    bde = Batch.from_ensemble(ens, 1.0, EXPLICIT_STEPS, F32)  # dt comes from dtd
+    bdb = Batch.from_ensemble(ens, 1.0, BTCS_STEPS, F32)
+
     def step(timing):
         e0, e1, e2, e3 = ev(), ev(), ev(), ev()
         e0.record(stream)
-        dt0 = ctx.cfl_dt(probe, u0, CFL)
-        be, bb = batches(dt0)
+        ctx.cfl_dt_device(probe, u0, CFL, dtd)
         ue.copy_(u0)
         e1.record(stream)
-        ctx.explicit_advance(be, ue)
+        ctx.advance_dt_device(L.BURGERS_EXPLICIT, bde, ue, dtd, 1.0)
         e2.record(stream)
         ub.copy_(u0)
-        ctx.btcs_advance(bb, ub)
+        ctx.advance_dt_device(L.BURGERS_BTCS, bdb, ub, dtd, BTCS_DT_FACTOR)
         e3.record(stream)
         timing.append((e0, e1, e2, e3))
 

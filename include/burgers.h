@@ -259,6 +259,37 @@ burgers_status burgers_adjoint(burgers_ctx* ctx, int32_t scheme, const burgers_b
                                const void* u0_dev, const void* gT_dev, void* gu0_dev,
                                double* gnu_dev, int64_t ckpt_stride, burgers_stream stream);
 
+/* ---- time step on the device (Eq. 7-8), no host round trip ------------------ */
+
+/* Asynchronous on `stream`: for every row b of `batch`, dt_dev[b] = cfl *
+ * min(dx / max|u|, dx^2 / (2 nu)) from the row's current values in `u_dev`,
+ * evaluated in FP64 on the device (as burgers_cfl_dt, without the copy to the
+ * host and the synchronisation). dt_dev: caller-owned device memory of
+ * batch->count doubles. A row with max|u| == 0 and nu == 0 has no finite
+ * limit and gets dt_dev[b] = -1. The rows' dt and nsteps are ignored. The
+ * reduction's descriptors are built once per batch layout (offsets, n, bc,
+ * dx, nu) and kept by the context (at most 16 layouts). Errors as
+ * burgers_cfl_dt, except that no row is rejected for its CFL limit. */
+burgers_status burgers_cfl_dt_device(burgers_ctx* ctx, const burgers_batch* batch,
+                                     const void* u_dev, double cfl, double* dt_dev,
+                                     burgers_stream stream);
+
+/* Asynchronous on `stream`: advances every row of `batch` by its nsteps steps
+ * of `scheme` (as burgers_explicit_advance ... burgers_newton_advance; iters
+ * for BURGERS_PICARD / BURGERS_NEWTON, ignored otherwise) with
+ * dt_b = dt_factor * dt_dev[b], read on the device (typically written by
+ * burgers_cfl_dt_device on the same stream), so a step sequence "CFL, then
+ * advance" needs no host synchronisation. The rows' dt fields are ignored; a
+ * row whose dt_dev[b] is not positive is left unchanged. Results are bitwise
+ * those of the host-dt entry point with dt = dt_factor * dt_dev[b]. Plans are
+ * cached as for the host-dt calls (keyed by the batch without its dt). Rows
+ * that need the multi-level solver (BTCS rows longer than the cluster limit,
+ * FP64 BTCS rows longer than one CTA): EINVAL. dt_factor <= 0: EINVAL. */
+burgers_status burgers_advance_dt_device(burgers_ctx* ctx, int32_t scheme,
+                                         const burgers_batch* batch, void* u_dev,
+                                         const double* dt_dev, double dt_factor, int32_t iters,
+                                         burgers_stream stream);
+
 /* ---- device peak (roofline denominator) ---------------------------------- */
 
 /* Blocking. Measures the FMA issue rate the device sustains for `dtype`

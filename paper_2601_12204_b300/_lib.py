@@ -76,6 +76,8 @@ SIGNATURES = {
     "burgers_ctx_set": (_ST, [_P, _I32, _I64]),
     "burgers_launch_count": (_I64, [_P]),
     "burgers_cfl_dt": (_ST, [_P, _P, _P, _D, _P, _P]),
+    "burgers_cfl_dt_device": (_ST, [_P, _P, _P, _D, _P, _P]),
+    "burgers_advance_dt_device": (_ST, [_P, _I32, _P, _P, _P, _D, _I32, _P]),
     "burgers_explicit_advance": (_ST, [_P, _P, _P, _P]),
     "burgers_btcs_advance": (_ST, [_P, _P, _P, _P]),
     "burgers_rk4_advance": (_ST, [_P, _P, _P, _P]),

@@ -180,6 +180,31 @@ class Context:
                                          self._stream(stream, u)), "burgers_cfl_dt")
         return out
 
+    def _check_dt(self, dt, batch: Batch) -> ctypes.c_void_p:
+        torch = _torch()
+        if (not dt.is_cuda or dt.dtype != torch.float64 or not dt.is_contiguous()
+                or dt.numel() < batch.count):
+            raise ValueError("dt must be a contiguous CUDA float64 tensor with one entry per row")
+        return ctypes.c_void_p(dt.data_ptr())
+
+    def cfl_dt_device(self, batch: Batch, u, cfl: float, dt, stream=None) -> None:
+        """dt[b] = cfl * min(dx/max|u_b|, dx^2/(2 nu_b)) on the device, asynchronously
+        (dt: CUDA float64 tensor, one entry per row; -1 where no limit is finite)."""
+        p = self._check_tensor(u, batch)
+        L.check(self._lib.burgers_cfl_dt_device(self.h, batch.ref(), p, float(cfl),
+                                                self._check_dt(dt, batch),
+                                                self._stream(stream, u)), "burgers_cfl_dt_device")
+
+    def advance_dt_device(self, scheme: int, batch: Batch, u, dt, factor: float = 1.0,
+                          iters: int = 1, stream=None) -> None:
+        """Advances every row by its nsteps steps with dt_b = factor * dt[b] read on
+        the device (the batch's dt is ignored); no host synchronisation."""
+        p = self._check_tensor(u, batch)
+        L.check(self._lib.burgers_advance_dt_device(self.h, int(scheme), batch.ref(), p,
+                                                    self._check_dt(dt, batch), float(factor),
+                                                    int(iters), self._stream(stream, u)),
+                "burgers_advance_dt_device")
+
     def fma_peak(self, dtype: int = L.BURGERS_F32) -> float:
         """Measured FMA issue rate of the device (lane-FMAs per second) for dtype,
         at the clock the GPU runs during the call."""

@@ -120,7 +120,10 @@ static int64_t max_resident(int kind, int dtype) {
 // context
 // ---------------------------------------------------------------------------
 burgers_ctx::burgers_ctx() = default;
-burgers_ctx::~burgers_ctx() = default;
+burgers_ctx::~burgers_ctx() {
+  for (auto& kv : redcache)
+    if (kv.second.dev) cudaFree(kv.second.dev);
+}
 
 namespace burgers {
 
@@ -170,9 +173,18 @@ static Shape pick_resident(const burgers_ctx* ctx, int kind, int dtype, int64_t 
   return best;
 }
 
+// FNV-1a over 64-bit words (then the tail bytes): the plan key hashes every
+// instance record of a batch on each call, 48 bytes per row.
 static uint64_t fnv1a(const void* data, size_t len, uint64_t h = 1469598103934665603ull) {
   const unsigned char* p = static_cast<const unsigned char*>(data);
-  for (size_t i = 0; i < len; ++i) {
+  size_t i = 0;
+  for (; i + 8 <= len; i += 8) {
+    uint64_t w;
+    memcpy(&w, p + i, 8);
+    h ^= w;
+    h *= 1099511628211ull;
+  }
+  for (; i < len; ++i) {
     h ^= p[i];
     h *= 1099511628211ull;
   }
@@ -314,7 +326,10 @@ static burgers_status build_plan(burgers_ctx* ctx, int scheme, const burgers_bat
     const KernelEntry* k = find_kernel(rkind, dtype, g.sh.nt, g.sh.c, g.exact);
     if (!k) return set_error(BURGERS_EINVAL, "kernel shape not instantiated");
     int begin = int(p->rows.size());
-    for (auto& pr : g.rows) p->rows.push_back(make_row(batch->inst[pr.second], iters));
+    for (auto& pr : g.rows) {
+      p->rows.push_back(make_row(batch->inst[pr.second], iters));
+      p->row_inst.push_back(int32_t(pr.second));
+    }
     int cnt = int(g.rows.size());
     if (ctx->plain) {
       for (int i = 0; i < cnt; ++i) {
@@ -367,6 +382,7 @@ static burgers_status build_plan(burgers_ctx* ctx, int scheme, const burgers_bat
       for (size_t q = 0; q < longs.size(); ++q) {
         const burgers_instance& in = batch->inst[longs[q]];
         p->rows.push_back(make_row(in));
+        p->row_inst.push_back(int32_t(longs[q]));
         int64_t tiles = (in.n + O - 1) / O;
         for (int64_t t = 0; t < tiles; ++t)
           p->items.push_back(TileItem{int32_t(q), int32_t(t)});
@@ -449,7 +465,10 @@ static burgers_status build_plan(burgers_ctx* ctx, int scheme, const burgers_bat
                          [](const auto& a, const auto& b) { return a.first > b.first; });
         const KernelEntry* k = find_kernel(K_BTCS_CLUSTER, dtype, g.nt, g.c, g.cs);
         int begin = int(p->rows.size());
-        for (auto& pr : g.rows) p->rows.push_back(make_row(batch->inst[pr.second], iters));
+        for (auto& pr : g.rows) {
+          p->rows.push_back(make_row(batch->inst[pr.second], iters));
+          p->row_inst.push_back(int32_t(pr.second));
+        }
         const int cnt = int(g.rows.size());
         // one cluster per row: grid = rows x cluster size
         for (int i0 = 0; i0 < cnt; i0 += ctx->plain ? 1 : cnt) {
@@ -514,6 +533,7 @@ static burgers_status build_plan(burgers_ctx* ctx, int scheme, const burgers_bat
 Plan::~Plan() {
   if (gexec) cudaGraphExecDestroy(gexec);
   if (dev && !dev_external) cudaFree(dev);
+  if (dtdev) cudaFree(dtdev);
 }
 
 static cudaError_t enqueue_plan(burgers_ctx* ctx, Plan* p, void* u, cudaStream_t st) {
@@ -647,17 +667,19 @@ static burgers_status run_plan(burgers_ctx* ctx, Plan* p, void* u, cudaStream_t 
   return BURGERS_OK;
 }
 
-static uint64_t plan_key(const burgers_ctx* ctx, int scheme, const burgers_batch* b, int iters) {
+static uint64_t plan_key(const burgers_ctx* ctx, int scheme, const burgers_batch* b, int iters,
+                         bool dtdev) {
   uint64_t h = fnv1a(b->inst, sizeof(burgers_instance) * size_t(b->count));
-  int32_t hdr[8] = {scheme, b->dtype, (ctx->plain ? 1 : 0) | (ctx->cluster ? 2 : 0), ctx->stream_k,
+  int32_t hdr[8] = {scheme, b->dtype,
+                    (ctx->plain ? 1 : 0) | (ctx->cluster ? 2 : 0) | (dtdev ? 4 : 0), ctx->stream_k,
                     int32_t(ctx->resident_max), int32_t(ctx->tune_version), ctx->resident_override,
                     iters};
   return fnv1a(hdr, sizeof hdr, h);
 }
 
 Plan* get_plan(burgers_ctx* ctx, int scheme, const burgers_batch* batch, burgers_status* st,
-               int iters) {
-  const uint64_t key = plan_key(ctx, scheme, batch, iters);
+               int iters, bool dtdev) {
+  const uint64_t key = plan_key(ctx, scheme, batch, iters, dtdev);
   for (auto it = ctx->plans.begin(); it != ctx->plans.end(); ++it) {
     if ((*it)->key == key && (*it)->count == batch->count) {
       ctx->plans.splice(ctx->plans.begin(), ctx->plans, it);  // most recent first
@@ -689,7 +711,7 @@ burgers_status advance(burgers_ctx* ctx, int scheme, const burgers_batch* batch,
   if (!u_dev) return set_error(BURGERS_EINVAL, "u_dev is NULL");
   cudaError_t e = cudaSetDevice(ctx->device);
   if (e != cudaSuccess) return cuda_error(e, "cudaSetDevice");
-  Plan* p = get_plan(ctx, scheme, batch, &st, iters);
+  Plan* p = get_plan(ctx, scheme, batch, &st, iters, false);
   if (!p) return st;
   return run_plan(ctx, p, u_dev, stream);
 }
@@ -952,6 +974,36 @@ HostBuf::~HostBuf() {
 
 }  // namespace burgers
 
+// Row coefficients of a device-dt plan from the per-instance dt on the device:
+// the same FP64 operations as make_row on dt = factor * dt_dev[b], so a
+// device-dt advance gives bitwise the result of a host advance with that dt.
+// An instance without a finite CFL limit (dt_dev < 0: u == 0 and nu == 0)
+// gets dt = 0, which leaves its row as it is.
+__global__ void k_rows_from_dt(RowDesc* __restrict__ rows, const int32_t* __restrict__ row_inst,
+                               const double2* __restrict__ dxnu, const double* __restrict__ dt_dev,
+                               double factor, int nrows) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nrows) return;
+  const int b = row_inst[i];
+  const double d0 = dt_dev[b];
+  const double dt = d0 > 0.0 ? d0 * factor : 0.0;
+  const double dx = dxnu[b].x, nu = dxnu[b].y;
+  rows[i].r = dt / dx;
+  rows[i].s = nu * dt / (dx * dx);
+  rows[i].ds_dnu = dt / (dx * dx);
+}
+
+// The batch with dt and nsteps replaced by placeholders (the device-dt
+// entry points ignore the rows' dt; the CFL reduction also their nsteps).
+static std::vector<burgers_instance> placeholder_dt(const burgers_batch* batch, bool keep_steps) {
+  std::vector<burgers_instance> tmp(batch->inst, batch->inst + batch->count);
+  for (auto& in : tmp) {
+    in.dt = 1.0;
+    if (!keep_steps) in.nsteps = 0;
+  }
+  return tmp;
+}
+
 extern "C" {
 
 burgers_status burgers_rel_l2(burgers_ctx* ctx, const burgers_batch* batch, const void* u_dev,
@@ -1130,6 +1182,130 @@ burgers_status burgers_solve_host(burgers_ctx* ctx, int32_t scheme, const burger
   if (e == cudaSuccess && pipe) e = cudaStreamSynchronize(ctx->side[burgers_ctx::kSide - 1]);
   if (e != cudaSuccess) return cuda_error(e, "solve_host sync");
   return BURGERS_OK;
+}
+
+burgers_status burgers_cfl_dt_device(burgers_ctx* ctx, const burgers_batch* batch,
+                                     const void* u_dev, double cfl, double* dt_dev,
+                                     burgers_stream stream) {
+  if (!ctx) return set_error(BURGERS_EINVAL, "ctx is NULL");
+  if (!batch || batch->count < 0 || (batch->count > 0 && !batch->inst))
+    return set_error(BURGERS_EINVAL, "bad batch");
+  if (batch->count == 0) return BURGERS_OK;
+  if (!u_dev || !dt_dev) return set_error(BURGERS_EINVAL, "NULL pointer");
+  if (!(cfl > 0.0)) return set_error(BURGERS_EINVAL, "cfl must be > 0");
+  std::vector<burgers_instance> tmp = placeholder_dt(batch, false);
+  burgers_batch b2 = *batch;
+  b2.inst = tmp.data();
+  burgers_status st = validate_batch(&b2, false);
+  if (st != BURGERS_OK) return st;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaSetDevice(ctx->device);
+  if (e != cudaSuccess) return cuda_error(e, "cudaSetDevice");
+  // the reduction's descriptors depend on the batch layout only: built and
+  // uploaded once per layout, then reused by every call (no host staging)
+  int32_t hdr[2] = {batch->dtype, 0};
+  const uint64_t key = fnv1a(hdr, sizeof hdr, fnv1a(tmp.data(), tmp.size() * sizeof(burgers_instance)));
+  auto it = ctx->redcache.find(key);
+  if (it == ctx->redcache.end()) {
+    if (ctx->redcache.size() >= 16) {  // bounded: drop the cached layouts
+      e = cudaDeviceSynchronize();
+      if (e != cudaSuccess) return cuda_error(e, "cfl cache");
+      for (auto& kv : ctx->redcache) cudaFree(kv.second.dev);
+      ctx->redcache.clear();
+    }
+    std::vector<RowDesc> rows;
+    std::vector<TileItem> items;
+    std::vector<int32_t> first;
+    reduction_setup(ctx, &b2, &rows, &items, &first);
+    std::vector<double2> dxnu(size_t(batch->count));
+    for (int64_t b = 0; b < batch->count; ++b) dxnu[size_t(b)] = make_double2(tmp[b].dx, tmp[b].nu);
+    auto align = [](size_t x) { return (x + 255) & ~size_t(255); };
+    RedCache rc;
+    rc.off[0] = 0;
+    rc.off[1] = align(rows.size() * sizeof(RowDesc));
+    rc.off[2] = align(rc.off[1] + items.size() * sizeof(TileItem));
+    rc.off[3] = align(rc.off[2] + first.size() * sizeof(int32_t));
+    rc.off[4] = align(rc.off[3] + dxnu.size() * sizeof(double2));
+    const size_t total = align(rc.off[4] + items.size() * sizeof(double));
+    rc.nrows = int(rows.size());
+    rc.nitems = int(items.size());
+    std::vector<unsigned char> img(rc.off[4], 0);
+    memcpy(img.data() + rc.off[0], rows.data(), rows.size() * sizeof(RowDesc));
+    memcpy(img.data() + rc.off[1], items.data(), items.size() * sizeof(TileItem));
+    memcpy(img.data() + rc.off[2], first.data(), first.size() * sizeof(int32_t));
+    memcpy(img.data() + rc.off[3], dxnu.data(), dxnu.size() * sizeof(double2));
+    e = cudaMalloc(&rc.dev, total);
+    if (e != cudaSuccess) return set_error(BURGERS_ENOMEM, "cfl descriptors: out of device memory");
+    e = cudaMemcpy(rc.dev, img.data(), img.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      cudaFree(rc.dev);
+      return cuda_error(e, "cfl descriptors");
+    }
+    it = ctx->redcache.emplace(key, rc).first;
+  }
+  const RedCache& rc = it->second;
+  char* base = static_cast<char*>(rc.dev);
+  e = launch_cfl(batch->dtype, u_dev, reinterpret_cast<RowDesc*>(base + rc.off[0]),
+                 reinterpret_cast<TileItem*>(base + rc.off[1]), rc.nitems,
+                 reinterpret_cast<int32_t*>(base + rc.off[2]), reinterpret_cast<double2*>(base + rc.off[3]),
+                 rc.nrows, NORM_CHUNK, cfl, reinterpret_cast<double*>(base + rc.off[4]), dt_dev, s);
+  if (e != cudaSuccess) return cuda_error(e, "cfl launch");
+  ctx->launches += 2;
+  return BURGERS_OK;
+}
+
+burgers_status burgers_advance_dt_device(burgers_ctx* ctx, int32_t scheme,
+                                         const burgers_batch* batch, void* u_dev,
+                                         const double* dt_dev, double dt_factor, int32_t iters,
+                                         burgers_stream stream) {
+  if (!ctx) return set_error(BURGERS_EINVAL, "ctx is NULL");
+  if (!valid_scheme(scheme)) return set_error(BURGERS_EINVAL, "bad scheme");
+  if (iters < 1 || iters > 64) return set_error(BURGERS_EINVAL, "iterations outside [1, 64]");
+  if (!batch || batch->count < 0 || (batch->count > 0 && !batch->inst))
+    return set_error(BURGERS_EINVAL, "bad batch");
+  if (batch->count == 0) return BURGERS_OK;
+  if (!u_dev || !dt_dev) return set_error(BURGERS_EINVAL, "NULL pointer");
+  if (!(dt_factor > 0.0)) return set_error(BURGERS_EINVAL, "dt_factor must be > 0");
+  std::vector<burgers_instance> tmp = placeholder_dt(batch, true);
+  burgers_batch b2 = *batch;
+  b2.inst = tmp.data();
+  burgers_status st = validate_batch(&b2, false);
+  if (st != BURGERS_OK) return st;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaSetDevice(ctx->device);
+  if (e != cudaSuccess) return cuda_error(e, "cudaSetDevice");
+  const int it_used = (scheme == BURGERS_PICARD || scheme == BURGERS_NEWTON) ? iters : 1;
+  Plan* p = get_plan(ctx, scheme, &b2, &st, it_used, true);
+  if (!p) return st;
+  if (p->ml_rows > 0)
+    return set_error(BURGERS_EINVAL,
+                     "device dt: rows that take the multi-level solver are not supported");
+  if (!p->rows.empty()) {
+    if (!p->dtdev) {  // the plan's map from rows to instances and their (dx, nu), once
+      const size_t o_dx = (p->row_inst.size() * sizeof(int32_t) + 255) & ~size_t(255);
+      std::vector<unsigned char> img(o_dx + size_t(batch->count) * sizeof(double2), 0);
+      memcpy(img.data(), p->row_inst.data(), p->row_inst.size() * sizeof(int32_t));
+      double2* dxnu = reinterpret_cast<double2*>(img.data() + o_dx);
+      for (int64_t b = 0; b < batch->count; ++b) dxnu[b] = make_double2(tmp[b].dx, tmp[b].nu);
+      e = cudaMalloc(&p->dtdev, img.size());
+      if (e != cudaSuccess) {
+        p->dtdev = nullptr;
+        return set_error(BURGERS_ENOMEM, "device-dt descriptors: out of device memory");
+      }
+      e = cudaMemcpy(p->dtdev, img.data(), img.size(), cudaMemcpyHostToDevice);
+      if (e != cudaSuccess) return cuda_error(e, "device-dt descriptors");
+    }
+    const size_t o_dx = (p->row_inst.size() * sizeof(int32_t) + 255) & ~size_t(255);
+    const int nrows = int(p->rows.size());
+    RowDesc* rows = reinterpret_cast<RowDesc*>(static_cast<char*>(p->dev) + p->rows_off);
+    k_rows_from_dt<<<(nrows + 255) / 256, 256, 0, s>>>(
+        rows, static_cast<const int32_t*>(p->dtdev),
+        reinterpret_cast<const double2*>(static_cast<char*>(p->dtdev) + o_dx), dt_dev, dt_factor, nrows);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_error(e, "device-dt rows");
+    ctx->launches += 1;
+  }
+  return run_plan(ctx, p, u_dev, s);
 }
 
 }  // extern "C"

@@ -59,6 +59,7 @@ struct Plan {
   int64_t count = 0;
   int dtype = 0, scheme = 0;
   std::vector<RowDesc> rows;
+  std::vector<int32_t> row_inst;        // batch instance of each entry of rows
   std::vector<TileItem> items;
   std::vector<unsigned char> ml_bytes;  // multi-level row descriptors
   int ml_rows = 0;
@@ -72,10 +73,19 @@ struct Plan {
   void* dev = nullptr;
   bool dev_external = false;
   size_t rows_off = 0, items_off = 0, counters_off = 0, ml_off = 0, dev_bytes = 0;
+  void* dtdev = nullptr;  // device-dt plans: row_inst and (dx, nu) per instance
   cudaGraphExec_t gexec = nullptr;
   void* g_u = nullptr;
   uint64_t g_scratch_gen = 0, g_ml_gen = 0;
   ~Plan();
+};
+
+// Device-resident descriptors of the CFL reduction of one batch layout
+// (burgers_cfl_dt_device).
+struct RedCache {
+  void* dev = nullptr;
+  size_t off[6] = {0, 0, 0, 0, 0, 0};
+  int nrows = 0, nitems = 0;
 };
 
 // Descriptor buffers owned by a caller of advance_uncached().
@@ -130,6 +140,7 @@ struct burgers_ctx {
   burgers::HostBuf adjhost;
   cudaEvent_t adj_event = nullptr;
   size_t red_offsets[6] = {0, 0, 0, 0, 0, 0};
+  std::map<uint64_t, burgers::RedCache> redcache;  // burgers_cfl_dt_device
   burgers_ctx();
   ~burgers_ctx();
 };
