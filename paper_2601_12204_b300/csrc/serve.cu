@@ -12,7 +12,11 @@
 //      buffer, slot offsets are the row offsets);
 //   3. completion: finished requests are copied back to host memory and their
 //      slots return to the free list, which is what lets the next arrivals in.
-// Requests that arrive while a slice runs join at the next slice boundary.
+// Which requests a slice finishes follows from the step counts, so the worker
+// plans and enqueues the next slice (with its admission and result copies)
+// while the current one runs: two slices in flight at most, and the GPU is not
+// idle during a slice boundary's host work. Requests that arrive while a slice
+// runs join at the next slice boundary.
 // Slices start at fixed multiples of S steps of each request, so a request's
 // result does not depend on what else is in the mix (same kernel shape, same
 // slice boundaries): the result alone and in the mix is bitwise the same.
@@ -180,7 +184,8 @@ struct burgers_server {
   int64_t pool_bytes = 0;
   burgers::Region short_region, long_region;
   cudaStream_t stream = nullptr, stream_b = nullptr;  // BTCS slices run on stream_b
-  cudaEvent_t ev = nullptr, ev_fork = nullptr, ev_join = nullptr;
+  cudaEvent_t ev[2] = {nullptr, nullptr};  // end of the slices in flight (by parity)
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   std::thread worker;
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
@@ -192,7 +197,7 @@ struct burgers_server {
   bool stop = false;
   burgers_status fault = BURGERS_OK;
   std::string fault_msg;
-  burgers::PlanScratch ps_explicit, ps_btcs;
+  burgers::PlanScratch ps_explicit[2], ps_btcs[2];  // descriptors of the slices in flight
   burgers::PinnedArena pinned;
   burgers_serve_stats stats{};
   double t0 = 0;
@@ -251,11 +256,11 @@ static void fail_all(burgers_server* sv, burgers_status st, const std::string& m
   sv->cv_done.notify_all();
 }
 
-// Waits for the worker's event with a deadline (never spins unbounded).
-static burgers_status wait_event(burgers_server* sv, double timeout_s) {
+// Waits for one of the worker's events with a deadline (never spins unbounded).
+static burgers_status wait_event(burgers_server* sv, cudaEvent_t ev, double timeout_s) {
   const double end = now_s() + timeout_s;
   for (;;) {
-    cudaError_t e = cudaEventQuery(sv->ev);
+    cudaError_t e = cudaEventQuery(ev);
     if (e == cudaSuccess) return BURGERS_OK;
     if (e != cudaErrorNotReady) return cuda_error(e, "serve slice");
     if (now_s() > end) return set_error(BURGERS_ETIMEOUT, "serve slice exceeded its deadline");
@@ -263,13 +268,70 @@ static burgers_status wait_event(burgers_server* sv, double timeout_s) {
   }
 }
 
+// A slice in flight: its event (recorded after the slice and the result
+// copies of the requests it finishes) and those requests.
+struct InFlight {
+  bool on = false;
+  std::vector<Req*> finished;
+};
+
+// Waits for a slice in flight and reports the requests it finished.
+static burgers_status retire(burgers_server* sv, InFlight& f, int idx) {
+  const double tw = now_s();
+  burgers_status st = wait_event(sv, sv->ev[idx], sv->cfg.slice_timeout_s);
+  if (st != BURGERS_OK) return st;
+  std::lock_guard<std::mutex> lk(sv->mu);
+  const double t = now_s() - sv->t0;
+  sv->stats.t_slice_s += now_s() - tw;
+  for (Req* q : f.finished) {
+    q->state = RQ_DONE;
+    q->t_done = t;
+    sv->done_q.push_back(q->ticket);
+    sv->stats.completed += 1;
+    sv->stats.cell_updates += double(q->r.n) * double(q->r.nsteps);
+    std::vector<unsigned char>().swap(q->u0);
+  }
+  if (!f.finished.empty()) sv->cv_done.notify_all();
+  f.finished.clear();
+  f.on = false;
+  return BURGERS_OK;
+}
+
+// Fails every request, including those of the slices in flight.
+static void fail_worker(burgers_server* sv, InFlight* fl, burgers_status st, const std::string& msg) {
+  {
+    std::lock_guard<std::mutex> lk(sv->mu);
+    for (int k = 0; k < 2; ++k) {
+      for (Req* q : fl[k].finished) {
+        q->state = RQ_FAILED;
+        q->status = st;
+        sv->done_q.push_back(q->ticket);
+      }
+      fl[k].finished.clear();
+      fl[k].on = false;
+    }
+  }
+  fail_all(sv, st, msg);
+}
+
+// The worker. Which requests a slice finishes follows from the step counts,
+// so the next slice is planned, its admission copies queued and it is
+// enqueued while the current one runs (two slices in flight at most, each
+// with its own descriptor buffers and event): the GPU is not left idle while
+// the host does a slice boundary's bookkeeping. Everything of a slice is
+// ordered on the worker's stream (the BTCS half forks to stream_b and joins
+// back), so a slot released by a finished request can take an admitted one
+// at once: its upload is queued after the result copy that frees it.
 static void worker_loop(burgers_server* sv) {
   cudaSetDevice(sv->ctx->device);
   const int64_t S = sv->cfg.slice_steps;
   std::vector<burgers_instance> ie, ib;
-  std::vector<Req*> admitted, in_e, in_b, finished;
+  std::vector<Req*> admitted, finished;
+  InFlight fl[2];
+  int par = 0;  // parity of the next slice
   for (;;) {
     admitted.clear();
+    bool work = false;
     {
       std::unique_lock<std::mutex> lk(sv->mu);
       for (;;) {
@@ -291,10 +353,25 @@ static void worker_loop(burgers_server* sv) {
           }
         }
         admit(sv, &admitted);
-        if (!sv->active.empty()) break;
+        if (!sv->active.empty()) {
+          work = true;
+          break;
+        }
+        if (fl[0].on || fl[1].on) break;  // nothing new: finish what is in flight
         sv->cv_work.wait_for(lk, std::chrono::milliseconds(2));
       }
-      // host copies of the admitted u0 (their vectors are not touched again)
+    }
+    if (!work) {  // retire the slices in flight, oldest first
+      for (int k = 0; k < 2; ++k) {
+        const int idx = (par + k) & 1;
+        if (!fl[idx].on) continue;
+        burgers_status st = retire(sv, fl[idx], idx);
+        if (st != BURGERS_OK) {
+          fail_worker(sv, fl, st, burgers_last_error());
+          return;
+        }
+      }
+      continue;
     }
     // ---- copy the new requests' u0 into their slots
     double tw0 = now_s();
@@ -306,12 +383,12 @@ static void worker_loop(burgers_server* sv) {
       if (e != cudaSuccess) break;
     }
     if (e != cudaSuccess) {
-      fail_all(sv, cuda_error(e, "serve admission copy"), burgers_last_error());
+      fail_worker(sv, fl, cuda_error(e, "serve admission copy"), burgers_last_error());
       return;
     }
     double tw1 = now_s();
     // ---- one slice over every active request
-    ie.clear(); ib.clear(); in_e.clear(); in_b.clear();
+    ie.clear(); ib.clear(); finished.clear();
     {
       std::lock_guard<std::mutex> lk(sv->mu);
       for (Req* q : sv->active) {
@@ -323,29 +400,22 @@ static void worker_loop(burgers_server* sv) {
         in.nu = q->r.nu;
         in.dt = q->r.dt;
         in.nsteps = std::min<int64_t>(S, q->r.nsteps - q->done_steps);
-        if (q->r.scheme == BURGERS_EXPLICIT) { ie.push_back(in); in_e.push_back(q); }
-        else { ib.push_back(in); in_b.push_back(q); }
+        if (q->r.scheme == BURGERS_EXPLICIT) ie.push_back(in);
+        else ib.push_back(in);
       }
     }
     burgers_batch be{sv->cfg.dtype, 0, int64_t(ie.size()), ie.data()};
     burgers_batch bb{sv->cfg.dtype, 0, int64_t(ib.size()), ib.data()};
     burgers_status st =
-        advance_uncached_pair(sv->ctx, BURGERS_EXPLICIT, &be, &sv->ps_explicit, BURGERS_BTCS, &bb,
-                              &sv->ps_btcs, sv->pool, sv->stream, sv->stream_b, sv->ev_fork,
-                              sv->ev_join);
-    if (st == BURGERS_OK) {
-      e = cudaEventRecord(sv->ev, sv->stream);
-      if (e != cudaSuccess) st = cuda_error(e, "serve record");
-    }
+        advance_uncached_pair(sv->ctx, BURGERS_EXPLICIT, &be, &sv->ps_explicit[par], BURGERS_BTCS,
+                              &bb, &sv->ps_btcs[par], sv->pool, sv->stream, sv->stream_b,
+                              sv->ev_fork, sv->ev_join);
     double tw2 = now_s();
-    if (st == BURGERS_OK) st = wait_event(sv, sv->cfg.slice_timeout_s);
-    double tw3 = now_s();
     if (st != BURGERS_OK) {
-      fail_all(sv, st, burgers_last_error());
+      fail_worker(sv, fl, st, burgers_last_error());
       return;
     }
-    // ---- completions
-    finished.clear();
+    // ---- the requests this slice finishes: result copies queued after it
     {
       std::lock_guard<std::mutex> lk(sv->mu);
       for (Req* q : sv->active) {
@@ -353,15 +423,7 @@ static void worker_loop(burgers_server* sv) {
         q->slices += 1;
         if (q->done_steps >= q->r.nsteps) finished.push_back(q);
       }
-      sv->stats.slices += 1;
-      sv->stats.t_copy_s += tw1 - tw0;
-      sv->stats.t_enqueue_s += tw2 - tw1;
-      sv->stats.t_slice_s += tw3 - tw2;
-      sv->stats.active_max = std::max<int64_t>(sv->stats.active_max, int64_t(sv->active.size()));
-      sv->stats.pool_used_max = std::max<int64_t>(
-          sv->stats.pool_used_max, sv->short_region.used() + sv->long_region.used());
     }
-    double tw4 = now_s();
     for (Req* q : finished) {
       void* dst = q->pin;
       if (!dst) {
@@ -372,38 +434,40 @@ static void worker_loop(burgers_server* sv) {
                           cudaMemcpyDeviceToHost, sv->stream);
       if (e != cudaSuccess) break;
     }
-    if (e == cudaSuccess && !finished.empty()) {
-      e = cudaEventRecord(sv->ev, sv->stream);
-      if (e == cudaSuccess) st = wait_event(sv, sv->cfg.slice_timeout_s);
-      else st = cuda_error(e, "serve record");
-    } else if (e != cudaSuccess) {
-      st = cuda_error(e, "serve result copy");
-    }
-    if (st != BURGERS_OK) {
-      fail_all(sv, st, burgers_last_error());
+    if (e == cudaSuccess) e = cudaEventRecord(sv->ev[par], sv->stream);
+    if (e != cudaSuccess) {
+      fail_worker(sv, fl, cuda_error(e, "serve result copy"), burgers_last_error());
       return;
     }
     {
       std::lock_guard<std::mutex> lk(sv->mu);
-      sv->stats.t_copy_s += now_s() - tw4;
-      const double t = now_s() - sv->t0;
-      for (Req* q : finished) {
+      for (Req* q : finished)
         (q->long_row ? sv->long_region : sv->short_region).release(q->off, q->bytes);
-        q->state = RQ_DONE;
-        q->t_done = t;
-        sv->done_q.push_back(q->ticket);
-        sv->stats.completed += 1;
-        sv->stats.cell_updates += double(q->r.n) * double(q->r.nsteps);
-        std::vector<unsigned char>().swap(q->u0);
-      }
       if (!finished.empty()) {
         auto& act = sv->active;
         act.erase(std::remove_if(act.begin(), act.end(),
-                                 [](Req* q) { return q->state == RQ_DONE; }),
+                                 [](Req* q) { return q->done_steps >= q->r.nsteps; }),
                   act.end());
-        sv->cv_done.notify_all();
+      }
+      sv->stats.slices += 1;
+      sv->stats.t_copy_s += (tw1 - tw0) + (now_s() - tw2);
+      sv->stats.t_enqueue_s += tw2 - tw1;
+      sv->stats.active_max = std::max<int64_t>(sv->stats.active_max,
+                                               int64_t(sv->active.size() + finished.size()));
+      sv->stats.pool_used_max = std::max<int64_t>(
+          sv->stats.pool_used_max, sv->short_region.used() + sv->long_region.used());
+    }
+    fl[par].on = true;
+    fl[par].finished.swap(finished);
+    // keep at most two slices in flight: wait for the previous one
+    if (fl[par ^ 1].on) {
+      st = retire(sv, fl[par ^ 1], par ^ 1);
+      if (st != BURGERS_OK) {
+        fail_worker(sv, fl, st, burgers_last_error());
+        return;
       }
     }
+    par ^= 1;
   }
 }
 
@@ -454,7 +518,8 @@ burgers_status burgers_serve_create(burgers_ctx* ctx, const burgers_serve_cfg* c
   sv->pinned.reserve(16);  // 1 GiB of page-locked request buffers up front
   e = cudaStreamCreateWithFlags(&sv->stream, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&sv->stream_b, cudaStreamNonBlocking);
-  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sv->ev, cudaEventDisableTiming);
+  for (int k = 0; k < 2 && e == cudaSuccess; ++k)
+    e = cudaEventCreateWithFlags(&sv->ev[k], cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sv->ev_fork, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sv->ev_join, cudaEventDisableTiming);
   if (e != cudaSuccess) {
@@ -600,7 +665,8 @@ burgers_status burgers_serve_destroy(burgers_server* sv) {
   cudaSetDevice(sv->ctx->device);
   if (sv->stream) cudaStreamSynchronize(sv->stream);
   if (sv->stream_b) cudaStreamSynchronize(sv->stream_b);
-  if (sv->ev) cudaEventDestroy(sv->ev);
+  for (int k = 0; k < 2; ++k)
+    if (sv->ev[k]) cudaEventDestroy(sv->ev[k]);
   if (sv->ev_fork) cudaEventDestroy(sv->ev_fork);
   if (sv->ev_join) cudaEventDestroy(sv->ev_join);
   if (sv->stream_b) cudaStreamDestroy(sv->stream_b);

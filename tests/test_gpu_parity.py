@@ -396,3 +396,40 @@ def test_cluster_btcs(ctx, dtype):
     finally:
         _fresh(ctx)
     assert np.array_equal(pl, got)
+
+
+@pytest.mark.parametrize("scheme", SCHEMES)
+def test_config2_bench_launch_configuration(ctx, scheme):
+    """The step the bench times, as it times it: 4096 x 4096 FP32, launch
+    shapes from the autotuner, the CFL time step on the device and the advance
+    reading it there (burgers_cfl_dt_device + burgers_advance_dt_device).
+    Sampled rows against the FP64 oracle at the bench's own dt."""
+    import torch
+
+    from paper_2601_12204_b300.api import Batch, Context
+    ens = W.fourier_ensemble(4096, 4096, seed=W.DEFAULT_SEED)
+    factor = 1.0 if scheme == EXPLICIT else 10.0
+    steps = 2000 if scheme == EXPLICIT else 200
+    c = Context(0)
+    try:
+        u0 = torch.tensor(ens.u0, dtype=torch.float32, device="cuda")
+        probe = Batch.from_ensemble(ens, 1.0, 0, F32)
+        dt_host = c.cfl_dt(probe, u0, 0.4)
+        c.autotune(scheme, Batch.from_ensemble(ens, dt_host * factor, steps, F32), u0,
+                   probe_steps=50)
+        dtd = torch.empty(ens.count, dtype=torch.float64, device="cuda")
+        b = Batch.from_ensemble(ens, 1.0, steps, F32)
+        u = u0.clone()
+        c.cfl_dt_device(probe, u0, 0.4, dtd)
+        c.advance_dt_device(scheme, b, u, dtd, factor)
+        torch.cuda.synchronize()
+        got = u.cpu().numpy().astype(np.float64)
+        dts = dtd.cpu().numpy() * factor
+    finally:
+        c.close()
+    ids = np.array([3, 1500, 4094])
+    sub = ens.subset(ids)
+    ref = run_oracle(scheme, sub, dts[ids], steps)
+    for j, bi in enumerate(ids):
+        o, so = int(ens.offsets[bi]), int(sub.offsets[j])
+        assert oracle.rel_l2(got[o:o + 4096], ref[so:so + 4096]) <= 1e-5
