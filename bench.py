@@ -807,6 +807,8 @@ def serve_bench(ctx, dev, duration: float, rate: float = 20000.0, plain_seconds:
            "pool_used_max": stats["pool_used_max"], "slice_steps": 256, "dtype": "f32",
            "worker_s": {"enqueue": stats["t_enqueue_s"], "slice_wait": stats["t_slice_s"],
                         "copies": stats["t_copy_s"]}}
+    if plain_seconds <= 0:
+        return res
     # plain path: one request per launch, FIFO in arrival order
     ctx.set(L.BURGERS_OPT_PLAIN, 1)
     buf = torch.empty(int(ns.max()), dtype=torch.float32, device=dev)
@@ -852,9 +854,23 @@ def main():
                     help="launch-shape table: loaded if it exists, else written after tuning")
     ap.add_argument("--serve-seconds", type=float, default=1.0,
                     help="length of the Poisson trace of the serving measurement (0 = skip)")
+    ap.add_argument("--serve-only", action="store_true",
+                    help="run only the serving measurement (configuration 4) and print its JSON")
+    ap.add_argument("--serve-plain-seconds", type=float, default=5.0,
+                    help="time limit of the one-request-per-launch comparison path (0 = skip it)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.serve_only:
+        import torch
+
+        from paper_2601_12204_b300.api import Context
+        dev = torch.device("cuda", 0)
+        torch.cuda.set_device(dev)
+        ctx = Context(0)
+        print(json.dumps({"serve": serve_bench(ctx, dev, max(args.serve_seconds, 0.1),
+                                               plain_seconds=args.serve_plain_seconds)}), flush=True)
+        ctx.close()
     else:
         run_ours(args)
 

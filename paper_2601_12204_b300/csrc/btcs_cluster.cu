@@ -411,7 +411,8 @@ __launch_bounds__(NT, (sizeof(T) == 4 && NT <= 512) ? 512 / NT : 1)
           if (t == 0) { Uv = A; A = T(0); }
           if (t == tl - 1) { Vv = Cc; Cc = T(0); }
         }
-        __syncwarp();
+        // a lane rewrites only its own rows; the next chunk's first-row
+        // relation it reads (ra, rg, rd) is not written here
         sm.A[i] = A; sm.B[i] = B; sm.Cc[i] = Cc; sm.D[i] = D; sm.U[i] = Uv; cs.V[i] = Vv;
       }
       __syncwarp();
