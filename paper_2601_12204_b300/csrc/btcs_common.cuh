@@ -41,14 +41,19 @@ __device__ __forceinline__ T sm_factor(T fa, T y0, T ytl, T z0, T ztl) {
 
 // Solves the reduced system held in sm (rows 0..NT-1, rows beyond tl are
 // decoupled identities) with warp 0; leaves the solution in sm.X.
-template <typename T, int NT, bool CYC>
-__device__ __forceinline__ void reduced_solve(BtcsShared<T, NT>& sm, int tl, int lane) {
+// PRESPLIT: the caller has already applied the split below to rows 0 and tl
+// (and set U) and passes the ratio in fa_pre.
+template <typename T, int NT, bool CYC, bool PRESPLIT = false>
+__device__ __forceinline__ void reduced_solve(BtcsShared<T, NT>& sm, int tl, int lane,
+                                              T fa_pre = T(0)) {
   constexpr int Q = NT / 32;
   // Sherman-Morrison split: gamma = -B_0, v = e_0 + (A_0/gamma) e_tl. The ratio
   // is rounded once to T and used both in the modified diagonal and in v, so
   // T~ + u v^T reproduces the cyclic matrix up to the rounding of that ratio.
   T fa = T(0);
-  if constexpr (CYC) {
+  if constexpr (CYC && PRESPLIT) {
+    fa = fa_pre;
+  } else if constexpr (CYC) {
     const T A0 = sm.A[sk(0)], B0 = sm.B[sk(0)], Ct = sm.Cc[sk(tl)], Bt = sm.B[sk(tl)];
     const T gam = -B0;
     fa = A0 * recip(gam);

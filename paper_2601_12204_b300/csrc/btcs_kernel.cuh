@@ -79,8 +79,8 @@ constexpr size_t btcs_dsm() {
 // r max|w| < 1/2.
 template <typename T, int NT, int C, bool EXACT, int BCT, int VAR>
 __device__ __forceinline__ void btcs_steps(int64_t nsteps, int iters, T r, T s, int n,
-                                           BtcsShared<T, NT>& sm, T* hfirst, T* hlast, T* us,
-                                           T* lo, T* es) {
+                                           BtcsShared<T, NT>& sm, T* hfirst, T* hlast, T* c0,
+                                           T* us, T* lo, T* es) {
   constexpr bool ITER = VAR == VAR_PICARD || VAR == VAR_NEWTON;
   constexpr bool PER = BCT == BC_PERIODIC;
   constexpr bool DEFER = VAR != VAR_NEWTON;  // neighbour values folded into the reduced rows
@@ -214,15 +214,13 @@ __device__ __forceinline__ void btcs_steps(int64_t nsteps, int iters, T r, T s, 
         else { cd = nd; ca = na; cg = ng; }
       }
     }
-    // ---- this chunk's first-row and end-row relations
+    // ---- this chunk's first-row relation (the previous chunk's row reads it);
+    // chunk 0 also publishes its end relation (every row's corner split does)
     sm.rd[sk(tid)] = dd[0];
     sm.ra[sk(tid)] = ah[0];
     sm.rg[sk(tid)] = ch[0];
-    {
-      const int si = sk(tid);
-      sm.A[si] = e_ah;
-      sm.Cc[si] = e_ch;
-      sm.D[si] = e_dh;
+    if constexpr (PER) {
+      if (tid == 0) { c0[0] = e_ah; c0[1] = e_ch; }
     }
     __syncthreads();
     // u_left - u_0 of this chunk, from the values published before the barrier
@@ -231,38 +229,49 @@ __device__ __forceinline__ void btcs_steps(int64_t nsteps, int iters, T r, T s, 
       if (tid > 0) lft = hlast[tid - 1] - hfirst[tid];
       else if constexpr (PER) lft = hlast[tl] - hfirst[0];
     }
-    if (warp == 0) {
-      // reduced row of each of this lane's chunks: end row of chunk t with the
-      // first-row relation of chunk t + 1 substituted (chunk 0 after the last)
-#pragma unroll
-      for (int q = 0; q < Q; ++q) {
-        const int t = lane * Q + q, i = sk(t);
-        T A = T(0), B = T(1), Cc = T(0), D = T(0);
-        if (t <= tl) {
-          const int nx = (t == tl) ? 0 : t + 1;
-          const T ech = sm.Cc[i], ran = sm.ra[sk(nx)];
-          A = sm.A[i];
-          T Dt = sm.D[i], rdn = sm.rd[sk(nx)];
-          if constexpr (DEFER) {
-            // neighbour differences of chunk t's edges; the end node of chunk
-            // t is the left neighbour of chunk nx's first node
-            const T f = hfirst[t], e = hlast[t], fn = hfirst[nx];
-            T lt = T(0), rt = T(0);
-            if (t > 0) lt = hlast[t - 1] - f;
-            else if constexpr (PER) lt = hlast[tl] - f;
-            if (t < tl) rt = fn - e;
-            else if constexpr (PER) rt = fn - e;
-            Dt = tfma(-kap * A, lt, tfma(-kap * ech, rt, Dt));
-            rdn = tfma(-kap * ran, e - fn, rdn);
-          }
-          B = T(1) - ech * ran;
-          Cc = -ech * sm.rg[sk(nx)];
-          D = tfma(-ech, rdn, Dt);
+    // ---- the reduced row of this thread's chunk t: its end row with the
+    // first-row relation of chunk t + 1 substituted (chunk 0 after the last).
+    // Periodic rows split their corners off here (Sherman-Morrison, gamma =
+    // -B_0, as reduced_solve does): threads 0 and tl modify their rows, and
+    // every thread knows the ratio A_0 / gamma.
+    T fa = T(0);
+    {
+      const int t = tid, i = sk(t);
+      T A = T(0), B = T(1), Cc = T(0), D = T(0), U = T(0);
+      if (t <= tl) {
+        const int nx = (t == tl) ? 0 : t + 1;
+        const T ech = e_ch, ran = sm.ra[sk(nx)];
+        A = e_ah;
+        T Dt = e_dh, rdn = sm.rd[sk(nx)];
+        if constexpr (DEFER) {
+          // neighbour differences of chunk t's edges; the end node of chunk t
+          // is the left neighbour of chunk nx's first node
+          const T f = hfirst[t], e = hlast[t], fn = hfirst[nx];
+          T lt = T(0), rt = T(0);
+          if (t > 0) lt = hlast[t - 1] - f;
+          else if constexpr (PER) lt = hlast[tl] - f;
+          if (t < tl) rt = fn - e;
+          else if constexpr (PER) rt = fn - e;
+          Dt = tfma(-kap * A, lt, tfma(-kap * ech, rt, Dt));
+          rdn = tfma(-kap * ran, e - fn, rdn);
         }
-        sm.A[i] = A; sm.B[i] = B; sm.Cc[i] = Cc; sm.D[i] = D; sm.U[i] = T(0);
+        B = T(1) - ech * ran;
+        Cc = -ech * sm.rg[sk(nx)];
+        D = tfma(-ech, rdn, Dt);
       }
-      __syncwarp();
-      reduced_solve<T, NT, PER>(sm, tl, lane);
+      if constexpr (PER) {
+        // chunk 0's row (tl >= 1: its next chunk is chunk 1), as thread 0 forms it
+        const T A0 = c0[0], B0 = T(1) - c0[1] * sm.ra[sk(1)];
+        const T gam = -B0;
+        fa = A0 * recip(gam);
+        if (t == 0) { B = B0 - gam; A = T(0); U = gam; }
+        if (t == tl) { B = B - Cc * fa; U = Cc; Cc = T(0); }
+      }
+      sm.A[i] = A; sm.B[i] = B; sm.Cc[i] = Cc; sm.D[i] = D; sm.U[i] = U;
+    }
+    __syncthreads();
+    if (warp == 0) {
+      reduced_solve<T, NT, PER, true>(sm, tl, lane, fa);
       // next step's first and last node of each chunk (Newton)
       if constexpr (!DEFER) {
       __syncwarp();
@@ -332,7 +341,7 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 && NT <= 512) ? 512 / NT :
                                                       const RowDesc* __restrict__ rows, int count,
                                                       int* __restrict__ counter) {
   __shared__ BtcsShared<T, NT> sm;
-  __shared__ T hfirst[NT], hlast[NT];
+  __shared__ T hfirst[NT], hlast[NT], c0[2];
   __shared__ int s_item;
   extern __shared__ __align__(16) unsigned char dsm[];
   T* us = reinterpret_cast<T*>(dsm);                   // C * NT values
@@ -362,10 +371,10 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 && NT <= 512) ? 512 / NT :
     const T r = T(rd.r), s = T(rd.s);
     if (rd.bc == BC_PERIODIC)
       btcs_steps<T, NT, C, EXACT, BC_PERIODIC, VAR>(rd.nsteps, rd.iters, r, s, n, sm, hfirst,
-                                                    hlast, us, lo, es);
+                                                    hlast, c0, us, lo, es);
     else
       btcs_steps<T, NT, C, EXACT, BC_DIRICHLET, VAR>(rd.nsteps, rd.iters, r, s, n, sm, hfirst,
-                                                     hlast, us, lo, es);
+                                                     hlast, c0, us, lo, es);
 #pragma unroll
     for (int j = 0; j < C; ++j)
       if (EXACT || base + j < n) row[base + j] = us[j * NT + tid];
