@@ -69,6 +69,12 @@ __device__ __forceinline__ void reduced_solve(BtcsShared<T, NT>& sm, int tl, int
     __syncwarp();
   }
   const int r0 = lane * Q;
+  // FP32 with up to 4 rows a lane keeps the sweeps' results in registers (rc,
+  // ra, rd, ru); otherwise they go back to shared memory (in FP64 the extra
+  // registers would cost resident CTAs)
+  constexpr bool REGQ = Q <= 4 && sizeof(T) == 4;
+  constexpr int QR = REGQ ? Q : 1;
+  T rc[QR], ra[QR], rd[QR], ru[QR];
   // forward sweep over this lane's Q reduced rows
   T chp = T(0), ahp = T(-1), dhp = T(0), uhp = T(0);
 #pragma unroll
@@ -80,12 +86,14 @@ __device__ __forceinline__ void reduced_solve(BtcsShared<T, NT>& sm, int tl, int
     chp = c * inv;
     ahp = -ai * ahp;
     dhp = tfma(-ai, dhp, d * inv);
-    sm.Cc[i] = chp;
-    sm.A[i] = ahp;
-    sm.D[i] = dhp;
-    if constexpr (CYC) {
-      uhp = tfma(-ai, uhp, sm.U[i] * inv);
-      sm.U[i] = uhp;
+    if constexpr (CYC) uhp = tfma(-ai, uhp, sm.U[i] * inv);
+    if constexpr (REGQ) {
+      rc[q] = chp; ra[q] = ahp; rd[q] = dhp; ru[q] = uhp;
+    } else {
+      sm.Cc[i] = chp;
+      sm.A[i] = ahp;
+      sm.D[i] = dhp;
+      if constexpr (CYC) sm.U[i] = uhp;
     }
   }
   const T e_ch = chp, e_ah = ahp, e_dh = dhp, e_uh = uhp;
@@ -94,16 +102,25 @@ __device__ __forceinline__ void reduced_solve(BtcsShared<T, NT>& sm, int tl, int
 #pragma unroll
   for (int q = Q - 2; q >= 0; --q) {
     const int i = sk(r0 + q);
-    const T ch = sm.Cc[i];
-    cd = tfma(-ch, cd, sm.D[i]);
-    ca = tfma(-ch, ca, sm.A[i]);
-    cg = -ch * cg;
-    sm.D[i] = cd;
-    sm.A[i] = ca;
-    sm.Cc[i] = cg;
-    if constexpr (CYC) {
-      cu = tfma(-ch, cu, sm.U[i]);
-      sm.U[i] = cu;
+    if constexpr (REGQ) {
+      const T ch = rc[q];
+      cd = tfma(-ch, cd, rd[q]);
+      ca = tfma(-ch, ca, ra[q]);
+      cg = -ch * cg;
+      if constexpr (CYC) cu = tfma(-ch, cu, ru[q]);
+      rd[q] = cd; ra[q] = ca; rc[q] = cg; ru[q] = cu;
+    } else {
+      const T ch = sm.Cc[i];
+      cd = tfma(-ch, cd, sm.D[i]);
+      ca = tfma(-ch, ca, sm.A[i]);
+      cg = -ch * cg;
+      sm.D[i] = cd;
+      sm.A[i] = ca;
+      sm.Cc[i] = cg;
+      if constexpr (CYC) {
+        cu = tfma(-ch, cu, sm.U[i]);
+        sm.U[i] = cu;
+      }
     }
   }
   // next lane's first-row relation
@@ -143,8 +160,13 @@ __device__ __forceinline__ void reduced_solve(BtcsShared<T, NT>& sm, int tl, int
     const int i = sk(r0 + q);
     T yq = Ye, zq = Ze;
     if (q < Q - 1) {
-      yq = tfma(-sm.Cc[i], Ye, tfma(-sm.A[i], YL, sm.D[i]));
-      if constexpr (CYC) zq = tfma(-sm.Cc[i], Ze, tfma(-sm.A[i], ZL, sm.U[i]));
+      if constexpr (REGQ) {
+        yq = tfma(-rc[q], Ye, tfma(-ra[q], YL, rd[q]));
+        if constexpr (CYC) zq = tfma(-rc[q], Ze, tfma(-ra[q], ZL, ru[q]));
+      } else {
+        yq = tfma(-sm.Cc[i], Ye, tfma(-sm.A[i], YL, sm.D[i]));
+        if constexpr (CYC) zq = tfma(-sm.Cc[i], Ze, tfma(-sm.A[i], ZL, sm.U[i]));
+      }
     }
     if constexpr (CYC) {
       if (r0 + q == tl) { ysel = yq; zsel = zq; }
