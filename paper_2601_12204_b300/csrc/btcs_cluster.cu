@@ -20,7 +20,7 @@
 // solves the same small system with the same arithmetic, keeping its own Y and P and the new values
 // of the nodes next to its ends (computed with the owners' arithmetic from
 // their operands), so the neighbour values of the next step need no further
-// exchange. A step costs one cluster barrier and three CTA barriers.
+// exchange. A step costs one cluster barrier and four CTA barriers.
 // Increment form and Kahan-compensated FP32 state as in btcs.cu.
 #include <cooperative_groups.h>
 
@@ -76,6 +76,7 @@ struct ClusterShared {
   T V[NT + NT / 32];    // block right-hand side of the interface coupling
   T Wg[NT + NT / 32];   // ... and its solution (gamma)
   T hfirst[NT], hlast[NT];
+  T iface[3];                   // end relation of the interface chunk tl
   ClusterSlot<T> slots[2][16];  // [step parity][contributing CTA]
   ClusterReply<T> reply;
 };
@@ -388,39 +389,32 @@ __launch_bounds__(NT, (sizeof(T) == 4 && NT <= 512) ? 512 / NT : 1)
     sm.rd[sk(tid)] = dd[0];
     sm.ra[sk(tid)] = ah[0];
     sm.rg[sk(tid)] = ch[0];
-    sm.A[sk(tid)] = e_ah;
-    sm.Cc[sk(tid)] = e_ch;
-    sm.D[sk(tid)] = e_dh;
+    if (tid == tl) { cs.iface[0] = e_ah; cs.iface[1] = e_ch; cs.iface[2] = e_dh; }
+    __syncthreads();
+    // ---- the block row of this thread's chunk t (chunks 0..tl-1; the
+    // interface row tl is the cluster's): its end row with the first-row
+    // relation of chunk t + 1 substituted, every thread its own
+    {
+      const int t = tid, i = sk(t);
+      T A = T(0), B = T(1), Cc = T(0), D = T(0), Uv = T(0), Vv = T(0);
+      if (t < tl) {
+        const T ech = e_ch;
+        A = e_ah;
+        B = T(1) - ech * sm.ra[sk(t + 1)];
+        Cc = -ech * sm.rg[sk(t + 1)];
+        D = tfma(-ech, sm.rd[sk(t + 1)], e_dh);
+        if (t == 0) { Uv = A; A = T(0); }
+        if (t == tl - 1) { Vv = Cc; Cc = T(0); }
+      }
+      sm.A[i] = A; sm.B[i] = B; sm.Cc[i] = Cc; sm.D[i] = D; sm.U[i] = Uv; cs.V[i] = Vv;
+    }
     __syncthreads();
     if (warp == 0) {
-      // block rows of chunks 0..tl-1 (the interface row tl is the cluster's)
-      // (every lane reads the interface chunk's end relation before the rows
-      // below overwrite it, and builds this CTA's contribution in registers)
-      const T s_eah = sm.A[sk(tl)], s_ech = sm.Cc[sk(tl)], s_edh = sm.D[sk(tl)];
-      __syncwarp();
-#pragma unroll
-      for (int q = 0; q < Q; ++q) {
-        const int t = lane * Q + q, i = sk(t);
-        T A = T(0), B = T(1), Cc = T(0), D = T(0), Uv = T(0), Vv = T(0);
-        if (t < tl) {
-          const T ech = sm.Cc[i];
-          A = sm.A[i];
-          B = T(1) - ech * sm.ra[sk(t + 1)];
-          Cc = -ech * sm.rg[sk(t + 1)];
-          D = tfma(-ech, sm.rd[sk(t + 1)], sm.D[i]);
-          if (t == 0) { Uv = A; A = T(0); }
-          if (t == tl - 1) { Vv = Cc; Cc = T(0); }
-        }
-        // a lane rewrites only its own rows; the next chunk's first-row
-        // relation it reads (ra, rg, rd) is not written here
-        sm.A[i] = A; sm.B[i] = B; sm.Cc[i] = Cc; sm.D[i] = D; sm.U[i] = Uv; cs.V[i] = Vv;
-      }
-      __syncwarp();
       block_solve3<T, NT>(cs, lane);
       __syncwarp();
       if (lane == 0) {
         ClusterSlot<T> sl;
-        sl.eah = s_eah; sl.ech = s_ech; sl.edh = s_edh;
+        sl.eah = cs.iface[0]; sl.ech = cs.iface[1]; sl.edh = cs.iface[2];
         sl.rd0 = sm.rd[sk(0)]; sl.ra0 = sm.ra[sk(0)]; sl.rg0 = sm.rg[sk(0)];
         sl.yl = tl > 0 ? sm.X[sk(tl - 1)] : T(0);
         sl.al = tl > 0 ? sm.Z[sk(tl - 1)] : T(0);
