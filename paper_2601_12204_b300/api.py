@@ -322,6 +322,13 @@ class Server:
         rc, out, st = self._result(self._lib.burgers_serve_poll, ticket, n)
         return rc, (out if rc == L.BURGERS_OK else None), st
 
+    def poll_stats(self, ticket: int):
+        """(status, stats) without the result (it is dropped with the ticket);
+        status EAGAIN while running."""
+        st = L.burgers_req_stats()
+        rc = self._lib.burgers_serve_poll(self.h, ctypes.c_uint64(ticket), None, ctypes.byref(st))
+        return rc, st
+
     def wait(self, ticket: int, n: int, timeout_s: float = 60.0):
         rc, out, st = self._result(self._lib.burgers_serve_wait, ticket, n,
                                    ctypes.c_double(timeout_s))
