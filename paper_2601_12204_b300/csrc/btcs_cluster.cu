@@ -90,6 +90,10 @@ __device__ __forceinline__ void block_solve3(ClusterShared<T, NT>& cs, int lane)
   constexpr int Q = NT / 32;
   BtcsShared<T, NT>& sm = cs.sm;
   const int r0 = lane * Q;
+  // up to 4 rows a lane keep the sweeps' results in registers
+  constexpr bool REGQ = Q <= 4;
+  constexpr int QR = REGQ ? Q : 1;
+  T rc[QR], ra[QR], rd[QR], ru[QR], rv[QR];
   T chp = T(0), ahp = T(-1), dhp = T(0), uhp = T(0), vhp = T(0);
 #pragma unroll
   for (int q = 0; q < Q; ++q) {
@@ -102,28 +106,42 @@ __device__ __forceinline__ void block_solve3(ClusterShared<T, NT>& cs, int lane)
     dhp = tfma(-ai, dhp, sm.D[i] * inv);
     uhp = tfma(-ai, uhp, sm.U[i] * inv);
     vhp = tfma(-ai, vhp, cs.V[i] * inv);
-    sm.Cc[i] = chp;
-    sm.A[i] = ahp;
-    sm.D[i] = dhp;
-    sm.U[i] = uhp;
-    cs.V[i] = vhp;
+    if constexpr (REGQ) {
+      rc[q] = chp; ra[q] = ahp; rd[q] = dhp; ru[q] = uhp; rv[q] = vhp;
+    } else {
+      sm.Cc[i] = chp;
+      sm.A[i] = ahp;
+      sm.D[i] = dhp;
+      sm.U[i] = uhp;
+      cs.V[i] = vhp;
+    }
   }
   const T e_ch = chp, e_ah = ahp, e_dh = dhp, e_uh = uhp, e_vh = vhp;
   T cd = T(0), ca = T(0), cg_ = T(-1), cu = T(0), cv = T(0);
 #pragma unroll
   for (int q = Q - 2; q >= 0; --q) {
     const int i = sk(r0 + q);
-    const T ch = sm.Cc[i];
-    cd = tfma(-ch, cd, sm.D[i]);
-    ca = tfma(-ch, ca, sm.A[i]);
-    cg_ = -ch * cg_;
-    cu = tfma(-ch, cu, sm.U[i]);
-    cv = tfma(-ch, cv, cs.V[i]);
-    sm.D[i] = cd;
-    sm.A[i] = ca;
-    sm.Cc[i] = cg_;
-    sm.U[i] = cu;
-    cs.V[i] = cv;
+    if constexpr (REGQ) {
+      const T ch = rc[q];
+      cd = tfma(-ch, cd, rd[q]);
+      ca = tfma(-ch, ca, ra[q]);
+      cg_ = -ch * cg_;
+      cu = tfma(-ch, cu, ru[q]);
+      cv = tfma(-ch, cv, rv[q]);
+      rd[q] = cd; ra[q] = ca; rc[q] = cg_; ru[q] = cu; rv[q] = cv;
+    } else {
+      const T ch = sm.Cc[i];
+      cd = tfma(-ch, cd, sm.D[i]);
+      ca = tfma(-ch, ca, sm.A[i]);
+      cg_ = -ch * cg_;
+      cu = tfma(-ch, cu, sm.U[i]);
+      cv = tfma(-ch, cv, cs.V[i]);
+      sm.D[i] = cd;
+      sm.A[i] = ca;
+      sm.Cc[i] = cg_;
+      sm.U[i] = cu;
+      cs.V[i] = cv;
+    }
   }
   T nd = shfl_down(cd, 1), na = shfl_down(ca, 1), ng = shfl_down(cg_, 1);
   T nu = shfl_down(cu, 1), nv = shfl_down(cv, 1);
@@ -157,9 +175,15 @@ __device__ __forceinline__ void block_solve3(ClusterShared<T, NT>& cs, int lane)
     const int i = sk(r0 + q);
     T y = d32, z = u32, w = v32;
     if (q < Q - 1) {
-      y = tfma(-sm.Cc[i], d32, tfma(-sm.A[i], YL, sm.D[i]));
-      z = tfma(-sm.Cc[i], u32, tfma(-sm.A[i], UL, sm.U[i]));
-      w = tfma(-sm.Cc[i], v32, tfma(-sm.A[i], VL, cs.V[i]));
+      if constexpr (REGQ) {
+        y = tfma(-rc[q], d32, tfma(-ra[q], YL, rd[q]));
+        z = tfma(-rc[q], u32, tfma(-ra[q], UL, ru[q]));
+        w = tfma(-rc[q], v32, tfma(-ra[q], VL, rv[q]));
+      } else {
+        y = tfma(-sm.Cc[i], d32, tfma(-sm.A[i], YL, sm.D[i]));
+        z = tfma(-sm.Cc[i], u32, tfma(-sm.A[i], UL, sm.U[i]));
+        w = tfma(-sm.Cc[i], v32, tfma(-sm.A[i], VL, cs.V[i]));
+      }
     }
     sm.X[i] = y;
     sm.Z[i] = z;
