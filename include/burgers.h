@@ -114,11 +114,29 @@ typedef enum {
                                     the multi-level BTCS solver; 0 = device limit (default 0) */
   BURGERS_OPT_AUTOTUNE = 4,      /* 1: time candidate launch shapes on first use (default 0) */
   BURGERS_OPT_LAUNCH_COUNT = 5,  /* write-only reset of the launch counter (value ignored) */
-  BURGERS_OPT_CLUSTER = 6        /* 1: BTCS rows up to 8 CTAs long stay resident in a
-                                    thread-block cluster (default 1); 0: multi-level solver.
+  BURGERS_OPT_CLUSTER = 6        /* FP32 BTCS rows longer than one CTA but at most 65536
+                                    nodes stay resident in a thread-block cluster.
+                                    1 (default): 128-thread CTAs in clusters of up to 16
+                                    where the device can schedule them (non-portable size,
+                                    checked with the occupancy API when the context is
+                                    created), else up to 8, then 256-thread CTAs up to 8;
+                                    2: portable cluster sizes only (<= 8 CTAs);
+                                    0: the multi-level solver. Other values: EINVAL.
                                     Ignored while BURGERS_OPT_RESIDENT_MAX is set. */
 } burgers_option;
 burgers_status burgers_ctx_set(burgers_ctx* ctx, int32_t option, int64_t value);
+
+/* Read-only facts of a context, for burgers_ctx_get. */
+typedef enum {
+  BURGERS_INFO_SM_COUNT = 100,          /* streaming multiprocessors of the context's device */
+  BURGERS_INFO_CLUSTER_CTAS_MAX = 101   /* largest cluster of 128-thread BTCS CTAs the device
+                                           schedules (8..16; 16 means rows up to 65536 nodes) */
+} burgers_info;
+
+/* Current value of a tunable (any burgers_option but LAUNCH_COUNT) or of a
+ * burgers_info key, written to *value. Host only, no device work. EINVAL for
+ * a NULL pointer or an unknown key (*value untouched). */
+burgers_status burgers_ctx_get(const burgers_ctx* ctx, int32_t key, int64_t* value);
 
 /* Number of kernel launches this context has issued (graph replays count the
  * kernels they contain). */

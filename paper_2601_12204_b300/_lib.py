@@ -43,6 +43,8 @@ BURGERS_OPT_RESIDENT_MAX = 3
 BURGERS_OPT_AUTOTUNE = 4
 BURGERS_OPT_LAUNCH_COUNT = 5
 BURGERS_OPT_CLUSTER = 6
+BURGERS_INFO_SM_COUNT = 100
+BURGERS_INFO_CLUSTER_CTAS_MAX = 101
 
 # numpy mirror of burgers_instance (48 bytes, natural alignment)
 INSTANCE_DTYPE = np.dtype([("offset", "<i8"), ("n", "<i4"), ("bc", "<i4"), ("dx", "<f8"),
@@ -74,6 +76,7 @@ SIGNATURES = {
     "burgers_ctx_destroy": (None, [_P]),
     "burgers_last_error": (ctypes.c_char_p, []),
     "burgers_ctx_set": (_ST, [_P, _I32, _I64]),
+    "burgers_ctx_get": (_ST, [_P, _I32, ctypes.POINTER(ctypes.c_int64)]),
     "burgers_launch_count": (_I64, [_P]),
     "burgers_cfl_dt": (_ST, [_P, _P, _P, _D, _P, _P]),
     "burgers_cfl_dt_device": (_ST, [_P, _P, _P, _D, _P, _P]),

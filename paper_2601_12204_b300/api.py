@@ -117,6 +117,11 @@ class Context:
     def set(self, option: int, value: int) -> None:
         L.check(self._lib.burgers_ctx_set(self.h, int(option), int(value)), "burgers_ctx_set")
 
+    def get(self, key: int) -> int:
+        v = ctypes.c_int64(0)
+        L.check(self._lib.burgers_ctx_get(self.h, int(key), ctypes.byref(v)), "burgers_ctx_get")
+        return int(v.value)
+
     def launch_count(self) -> int:
         return int(self._lib.burgers_launch_count(self.h))
 

@@ -32,6 +32,8 @@ def main():
     ap.add_argument("--stream-k", type=int, default=0)
     ap.add_argument("--no-cluster", action="store_true",
                     help="long BTCS rows through the multi-level solver instead of clusters")
+    ap.add_argument("--portable-clusters", action="store_true",
+                    help="cluster-resident BTCS in clusters of at most 8 CTAs")
     ap.add_argument("--repeat", type=int, default=1)
     ap.add_argument("--autotune", action="store_true", help="tune launch shapes first and print the table")
     ap.add_argument("--tune-file", default=None,
@@ -52,6 +54,8 @@ def main():
         ctx.set(L.BURGERS_OPT_STREAM_K, a.stream_k)
     if a.no_cluster:
         ctx.set(L.BURGERS_OPT_CLUSTER, 0)
+    elif a.portable_clusters:
+        ctx.set(L.BURGERS_OPT_CLUSTER, 2)
     u0 = torch.tensor(ens.u0, dtype=tdt, device="cuda")
     dt = ctx.cfl_dt(Batch.from_ensemble(ens, 1.0, 0, dt_code), u0, 0.4)
     btcs_like = a.case in ("btcs", "adjoint-btcs")

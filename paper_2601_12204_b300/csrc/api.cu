@@ -428,8 +428,11 @@ static burgers_status build_plan(burgers_ctx* ctx, int scheme, const burgers_bat
       // ping-pong copy of the rows, plus two Kahan compensation buffers (FP32)
       p->scratch_elems = dtype == 0 ? 3 * span : span;
     } else {
-      // rows that fit a cluster of at most 8 CTAs stay resident in its shared
-      // memory (k_btcs_cluster); longer ones go through the multi-level solver
+      // rows that fit a cluster stay resident in its shared memory
+      // (k_btcs_cluster): 128-thread CTAs of 4096 nodes in clusters of up to
+      // 16 where the device schedules them (8 in portable mode), else
+      // 256-thread CTAs of 8192 nodes in clusters of up to 8; longer rows go
+      // through the multi-level solver
       std::vector<int64_t> mlrows;
       struct CGrp {
         int nt, c, cs;
@@ -441,9 +444,10 @@ static burgers_status build_plan(burgers_ctx* ctx, int scheme, const burgers_bat
       for (int64_t b : longs) {
         const burgers_instance& in = batch->inst[b];
         int nt = 0, c = 0;
-        if (cl) {
-          if (dtype == 0 && in.n <= 8 * 4096) { nt = 128; c = 32; }
-          else if (dtype == 0 && in.n <= 8 * 8192) { nt = 256; c = 32; }
+        if (cl && dtype == 0) {
+          const int64_t cs128 = ctx->cluster == 2 ? 8 : ctx->cluster_cs128;
+          if (in.n <= cs128 * 4096) { nt = 128; c = 32; }
+          else if (in.n <= 8 * 8192) { nt = 256; c = 32; }
         }
         const int64_t W = int64_t(nt) * c;
         const int cs = nt ? int((in.n + W - 1) / W) : 0;
@@ -670,8 +674,9 @@ static burgers_status run_plan(burgers_ctx* ctx, Plan* p, void* u, cudaStream_t 
 static uint64_t plan_key(const burgers_ctx* ctx, int scheme, const burgers_batch* b, int iters,
                          bool dtdev) {
   uint64_t h = fnv1a(b->inst, sizeof(burgers_instance) * size_t(b->count));
-  int32_t hdr[8] = {scheme, b->dtype,
-                    (ctx->plain ? 1 : 0) | (ctx->cluster ? 2 : 0) | (dtdev ? 4 : 0), ctx->stream_k,
+  const int32_t flags = (ctx->plain ? 1 : 0) | (ctx->cluster ? 2 : 0) | (dtdev ? 4 : 0) |
+                        (ctx->cluster == 2 ? 8 : 0);
+  int32_t hdr[8] = {scheme, b->dtype, flags, ctx->stream_k,
                     int32_t(ctx->resident_max), int32_t(ctx->tune_version), ctx->resident_override,
                     iters};
   return fnv1a(hdr, sizeof hdr, h);
@@ -788,6 +793,11 @@ burgers_status burgers_ctx_create(int device, burgers_ctx** out) {
   ctx->smem_optin = prop.sharedMemPerBlockOptin;
   e = prepare_kernels();
   if (e != cudaSuccess) return cuda_error(e, "kernel attributes");
+  for (int cs = 9; cs <= 16; ++cs) {  // wide clusters: every size up to the largest that fits
+    const KernelEntry* k = find_kernel(K_BTCS_CLUSTER, 0, 128, 32, cs);
+    if (!k || !cluster_fits(*k)) break;
+    ctx->cluster_cs128 = cs;
+  }
   e = cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking);
   if (e != cudaSuccess) return cuda_error(e, "cudaStreamCreate");
   for (int i = 0; i < burgers_ctx::kSide && e == cudaSuccess; ++i) {
@@ -844,9 +854,30 @@ burgers_status burgers_ctx_set(burgers_ctx* ctx, int32_t option, int64_t value) 
       return BURGERS_OK;
     case BURGERS_OPT_AUTOTUNE: ctx->autotune = value != 0; return BURGERS_OK;
     case BURGERS_OPT_LAUNCH_COUNT: ctx->launches = 0; return BURGERS_OK;
-    case BURGERS_OPT_CLUSTER: ctx->cluster = value != 0; return BURGERS_OK;
+    case BURGERS_OPT_CLUSTER:
+      if (value < 0 || value > 2) return set_error(BURGERS_EINVAL, "cluster mode is 0, 1 or 2");
+      ctx->cluster = int(value);
+      return BURGERS_OK;
     default: return set_error(BURGERS_EINVAL, "unknown option");
   }
+}
+
+burgers_status burgers_ctx_get(const burgers_ctx* ctx, int32_t key, int64_t* value) {
+  if (!ctx || !value) return set_error(BURGERS_EINVAL, "NULL pointer");
+  int64_t v = 0;
+  switch (key) {
+    case BURGERS_OPT_GRAPHS: v = ctx->graphs ? 1 : 0; break;
+    case BURGERS_OPT_PLAIN: v = ctx->plain ? 1 : 0; break;
+    case BURGERS_OPT_STREAM_K: v = ctx->stream_k; break;
+    case BURGERS_OPT_RESIDENT_MAX: v = ctx->resident_max; break;
+    case BURGERS_OPT_AUTOTUNE: v = ctx->autotune ? 1 : 0; break;
+    case BURGERS_OPT_CLUSTER: v = ctx->cluster; break;
+    case BURGERS_INFO_SM_COUNT: v = ctx->sm_count; break;
+    case BURGERS_INFO_CLUSTER_CTAS_MAX: v = ctx->cluster_cs128; break;
+    default: return set_error(BURGERS_EINVAL, "unknown key");
+  }
+  *value = v;
+  return BURGERS_OK;
 }
 
 int64_t burgers_launch_count(const burgers_ctx* ctx) { return ctx ? ctx->launches.load() : 0; }

@@ -110,7 +110,8 @@ struct burgers_ctx {
   size_t smem_optin = 0;
   bool graphs = true;
   bool plain = false;
-  bool cluster = true;  // cluster-resident BTCS for rows up to 8 CTAs
+  int cluster = 1;      // cluster-resident BTCS: 0 off, 1 any size the device fits, 2 portable (<= 8)
+  int cluster_cs128 = 8;  // largest schedulable cluster of 128-thread BTCS CTAs (8..16)
   bool autotune = false;
   int stream_k = 0;
   int64_t resident_max = 0;

@@ -77,7 +77,7 @@ struct ClusterShared {
   T Wg[NT + NT / 32];   // ... and its solution (gamma)
   T hfirst[NT], hlast[NT];
   T iface[3];                   // end relation of the interface chunk tl
-  ClusterSlot<T> slots[2][16];  // [step parity][contributing CTA]
+  ClusterSlot<T> slots[2][16];  // [step parity][contributing CTA] (clusters up to 16)
   ClusterReply<T> reply;
 };
 
@@ -299,6 +299,7 @@ __launch_bounds__(NT, (sizeof(T) == 4 && NT <= 512) ? 512 / NT : 1)
   (void)counter;
   constexpr int W = NT * C;
   constexpr int Q = NT / 32;
+  static_assert(CS >= 2 && CS <= 16, "slots hold at most 16 CTAs");
   cg::cluster_group cluster = cg::this_cluster();
   const int rank = int(cluster.block_rank());
   const int item = int(blockIdx.x) / CS;
@@ -337,16 +338,22 @@ __launch_bounds__(NT, (sizeof(T) == 4 && NT <= 512) ? 512 / NT : 1)
   }
   cluster.sync();
   const T r = T(rd.r), s = T(rd.s), ds1 = T(1) + T(2) * s;
+  // Warps whose chunks all lie inside the row and hold no Dirichlet end row
+  // take the branch-free path; any other warp takes the general one with all
+  // its lanes (one pass instead of both, one after the other, in a diverged
+  // warp), and warps past the row's end skip the sweep. The cluster barrier
+  // paces every step by the slowest CTA, so a ragged last CTA must not be slow.
+  const bool plainchunk = __all_sync(
+      FULL_MASK, je == C - 1 && jstar >= C - 1 &&
+                     (per || !((rank == 0 && tid == 0) || (lastcta && tid == tl))));
+  const bool padwarp = __all_sync(FULL_MASK, jstar < 0);
   T ch[C], ah[C], dd[C];
   int par = 0;  // slot buffer of this step
   for (int64_t step = 0; step < rd.nsteps; ++step) {
     const T halo_l = cs.reply.halo_l, halo_r = cs.reply.halo_r;
     T left = tid > 0 ? cs.hlast[tid - 1] : halo_l;
     T right = tid < tl ? cs.hfirst[tid + 1] : halo_r;
-    // ---- assembly fused with the forward sweep (rows as in btcs.cu); chunks
-    // with no padding and no Dirichlet end row take the branch-free path
-    const bool plainchunk = je == C - 1 && jstar >= C - 1 &&
-                            (per || !((rank == 0 && tid == 0) || (lastcta && tid == tl)));
+    // ---- assembly fused with the forward sweep (rows as in btcs.cu)
     T e_ch = T(0), e_ah = T(0), e_dh = T(0);
     auto sweep = [&](auto full_tag) {
       constexpr bool FULL = decltype(full_tag)::value;
@@ -408,8 +415,13 @@ __launch_bounds__(NT, (sizeof(T) == 4 && NT <= 512) ? 512 / NT : 1)
         }
       }
     };
-    if (plainchunk) sweep(std::true_type{});
-    else sweep(std::false_type{});
+    if (plainchunk) {
+      sweep(std::true_type{});
+    } else if (padwarp) {  // all rows identity: what the general sweep leaves
+      dd[0] = T(0); ah[0] = T(0); ch[0] = T(0);
+    } else {
+      sweep(std::false_type{});
+    }
     sm.rd[sk(tid)] = dd[0];
     sm.ra[sk(tid)] = ah[0];
     sm.rg[sk(tid)] = ch[0];
@@ -508,12 +520,21 @@ __launch_bounds__(NT, (sizeof(T) == 4 && NT <= 512) ? 512 / NT : 1)
   REG_CLUSTER(T, DT, NT, C, 2) REG_CLUSTER(T, DT, NT, C, 3) REG_CLUSTER(T, DT, NT, C, 4)    \
   REG_CLUSTER(T, DT, NT, C, 5) REG_CLUSTER(T, DT, NT, C, 6) REG_CLUSTER(T, DT, NT, C, 7)    \
   REG_CLUSTER(T, DT, NT, C, 8)
+// cluster sizes above the portable 8 (launchable where the device can
+// schedule them; the planner asks the occupancy API first)
+#define REG_CLUSTERS_WIDE(T, DT, NT, C)                                                     \
+  REG_CLUSTER(T, DT, NT, C, 9) REG_CLUSTER(T, DT, NT, C, 10) REG_CLUSTER(T, DT, NT, C, 11)  \
+  REG_CLUSTER(T, DT, NT, C, 12) REG_CLUSTER(T, DT, NT, C, 13) REG_CLUSTER(T, DT, NT, C, 14) \
+  REG_CLUSTER(T, DT, NT, C, 15) REG_CLUSTER(T, DT, NT, C, 16)
 
 // FP32 only: FP64 rows are limited by the FP64 pipe, where the multi-level
-// solver is as fast.
+// solver is as fast. 128-thread CTAs (4096 nodes each) in clusters of up to
+// 16 cover rows up to 65536 nodes at half the padding granularity of the
+// 256-thread shapes, which remain for devices (or modes) limited to 8.
 void register_btcs_cluster(std::vector<KernelEntry>& reg) {
   REG_CLUSTERS(float, 0, 256, 32)
   REG_CLUSTERS(float, 0, 128, 32)
+  REG_CLUSTERS_WIDE(float, 0, 128, 32)
 }
 
 }  // namespace burgers

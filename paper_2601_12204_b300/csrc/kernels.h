@@ -58,4 +58,8 @@ const KernelEntry* find_kernel(int kind, int dtype, int nt, int c, int exact);
 // Sets the dynamic shared memory attribute of every registered kernel.
 cudaError_t prepare_kernels();
 
+// Whether at least one cluster of a K_BTCS_CLUSTER entry (exact = cluster
+// size) can be resident on the current device.
+bool cluster_fits(const KernelEntry& e);
+
 }  // namespace burgers

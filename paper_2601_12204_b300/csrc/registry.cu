@@ -45,8 +45,34 @@ cudaError_t prepare_kernels() {
                                              int(e.dyn_smem));
       if (err != cudaSuccess) return err;
     }
+    if (e.kind == K_BTCS_CLUSTER && e.exact > 8) {
+      // a refusal only leaves the wide clusters unused (cluster_fits says so)
+      if (cudaFuncSetAttribute(e.fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+          cudaSuccess)
+        (void)cudaGetLastError();
+    }
   }
   return cudaSuccess;
+}
+
+bool cluster_fits(const KernelEntry& e) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(unsigned(e.exact));
+  cfg.blockDim = dim3(unsigned(e.nt));
+  cfg.dynamicSmemBytes = e.dyn_smem;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = unsigned(e.exact);
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, e.fn, &cfg) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return false;
+  }
+  return n > 0;
 }
 
 }  // namespace burgers

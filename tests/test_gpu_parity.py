@@ -370,20 +370,36 @@ def test_autotune_then_parity(ctx, scheme, tmp_path):
 
 @pytest.mark.parametrize("dtype", [F32])
 def test_cluster_btcs(ctx, dtype):
-    """BTCS rows longer than one CTA (up to 8 CTAs) resident in a thread-block
-    cluster: every cluster size, ragged last CTAs, both BCs, against the oracle
-    and against the multi-level solver."""
+    """BTCS rows longer than one CTA resident in a thread-block cluster: every
+    cluster size (128-thread CTAs in clusters of 2..16, the sizes above 8
+    non-portable; in portable mode 256-thread CTAs for rows past 8 x 4096),
+    ragged last CTAs, both BCs, against the oracle and against the multi-level
+    solver."""
     _fresh(ctx)
+    # a B300 schedules 16-CTA clusters of this kernel
+    assert ctx.get(L.BURGERS_INFO_CLUSTER_CTAS_MAX) == 16
     W_ = 4096
     ns = [2 * W_ + 1, 3 * W_ - 5, 3 * W_, 4 * W_ + 33, 5 * W_ - 1, 6 * W_ + 7, 7 * W_, 8 * W_]
     if dtype == F32:
-        ns += [9 * W_ + 3, 12 * W_, 16 * W_]
+        ns += [9 * W_ + 3, 10 * W_ - 7, 11 * W_ + 1, 12 * W_, 13 * W_ + 5, 14 * W_,
+               15 * W_ - 3, 16 * W_]
     ens = _concat([_one(n, bc, seed=n + bc) for n in ns for bc in (0, 1)])
     dts = oracle_dts(ens, 8.0)
     steps = np.array([5 + (i % 7) for i in range(ens.count)])
     got = run_gpu(ctx, BTCS, ens, dts, steps, dtype)
     ref = run_oracle(BTCS, ens, dts, steps)
     assert_parity(ens, got, ref, dtype, "cluster")
+    ctx.set(L.BURGERS_OPT_CLUSTER, 2)
+    assert ctx.get(L.BURGERS_OPT_CLUSTER) == 2
+    try:
+        portable = run_gpu(ctx, BTCS, ens, dts, steps, dtype)
+    finally:
+        ctx.set(L.BURGERS_OPT_CLUSTER, 1)
+    assert_parity(ens, portable, ref, dtype, "cluster (portable sizes)")
+    # rows up to 8 x 4096 nodes (the first 8 lengths, both BCs) take the same
+    # 128-thread kernels in both modes
+    head = int(ens.offsets[16])
+    assert np.array_equal(portable[:head], got[:head])
     ctx.set(L.BURGERS_OPT_CLUSTER, 0)
     try:
         ml = run_gpu(ctx, BTCS, ens, dts, steps, dtype)
@@ -396,6 +412,33 @@ def test_cluster_btcs(ctx, dtype):
     finally:
         _fresh(ctx)
     assert np.array_equal(pl, got)
+
+
+def test_ctx_options_round_trip(ctx):
+    """burgers_ctx_get reads back what burgers_ctx_set wrote, reports the
+    device facts, and rejects unknown keys and out-of-range cluster modes."""
+    _fresh(ctx)
+    try:
+        for opt, val in ((L.BURGERS_OPT_GRAPHS, 0), (L.BURGERS_OPT_PLAIN, 1),
+                         (L.BURGERS_OPT_STREAM_K, 7), (L.BURGERS_OPT_RESIDENT_MAX, 1 << 20),
+                         (L.BURGERS_OPT_AUTOTUNE, 1), (L.BURGERS_OPT_CLUSTER, 2),
+                         (L.BURGERS_OPT_CLUSTER, 0)):
+            ctx.set(opt, val)
+            assert ctx.get(opt) == val
+        import torch
+        assert ctx.get(L.BURGERS_INFO_SM_COUNT) == \
+            torch.cuda.get_device_properties(0).multi_processor_count
+        assert 8 <= ctx.get(L.BURGERS_INFO_CLUSTER_CTAS_MAX) <= 16
+        for bad in (3, -1):
+            with pytest.raises(Exception):
+                ctx.set(L.BURGERS_OPT_CLUSTER, bad)
+        with pytest.raises(Exception):
+            ctx.get(L.BURGERS_OPT_LAUNCH_COUNT)
+        with pytest.raises(Exception):
+            ctx.get(12345)
+    finally:
+        ctx.set(L.BURGERS_OPT_AUTOTUNE, 0)
+        _fresh(ctx)
 
 
 @pytest.mark.parametrize("scheme", SCHEMES)
