@@ -76,7 +76,10 @@ struct Shape {
 
 // Default resident shapes per (kind, dtype), ascending capacity; the first
 // entry of a capacity is the default, later entries are autotuning
-// alternatives of the same capacity.
+// alternatives of the same capacity. The defaults are the shapes the
+// autotuner picks on a B300 for full batches of that capacity class (FP32
+// BTCS and the implicit variants: 128 x 16, 128 x 32 and 256 x 32 for 2048,
+// 4096 and 8192 nodes, 1.5-1.8x the 256 x 8, 256 x 16 and 512 x 16 shapes).
 static const std::vector<Shape>& resident_shapes(int kind, int dtype) {
   static const std::vector<Shape> ex32 = {{32, 1},   {32, 2},    {32, 4},   {32, 8},  {64, 8},
                                           {128, 8},  {64, 16},   {128, 16}, {256, 8}, {256, 16},
@@ -84,21 +87,21 @@ static const std::vector<Shape>& resident_shapes(int kind, int dtype) {
   static const std::vector<Shape> ex64 = {{32, 1},  {32, 2},   {32, 4},  {32, 8},   {64, 8},
                                           {128, 8}, {256, 8},  {128, 16}, {512, 8}, {256, 16},
                                           {1024, 8}, {512, 16}};
-  static const std::vector<Shape> bt32 = {{32, 1},   {32, 2},   {32, 4},   {32, 8},  {64, 8},
-                                          {128, 8},  {256, 8},  {128, 16}, {64, 32}, {256, 16},
-                                          {512, 8},  {128, 32}, {512, 16}, {1024, 8}, {256, 32}};
+  static const std::vector<Shape> bt32 = {{32, 1},   {32, 2},   {32, 4},   {32, 8},    {64, 8},
+                                          {128, 8},  {128, 16}, {256, 8},  {64, 32},   {128, 32},
+                                          {256, 16}, {512, 8},  {256, 32}, {512, 16},  {1024, 8}};
   static const std::vector<Shape> bt64 = {{32, 1},  {32, 2},  {32, 4},   {32, 8},   {64, 8},
                                           {128, 8}, {256, 8}, {128, 16}, {512, 8}, {256, 16}};
   static const std::vector<Shape> rk32 = {{32, 1},   {32, 2},  {32, 4},   {32, 8},  {64, 8},
-                                          {128, 8},  {64, 16}, {128, 16}, {256, 8}, {256, 16},
-                                          {512, 8},  {512, 16}};
+                                          {128, 8},  {64, 16}, {128, 16}, {256, 8}, {512, 8},
+                                          {256, 16}, {512, 16}};
   static const std::vector<Shape> rk64 = {{32, 1},  {32, 2},   {32, 4},   {32, 8},  {64, 8},
                                           {128, 4}, {128, 8},  {256, 4},  {256, 8}, {512, 4},
                                           {512, 8}, {1024, 4}};
   // Crank-Nicolson, Picard and Newton share the BTCS kernel shape
   static const std::vector<Shape> im32 = {{32, 1},   {32, 2},   {32, 4},   {32, 8},
-                                          {64, 8},   {128, 8},  {256, 8},  {128, 16},
-                                          {256, 16}, {128, 32}, {256, 32}};
+                                          {64, 8},   {128, 8},  {128, 16}, {256, 8},
+                                          {128, 32}, {256, 16}, {256, 32}};
   static const std::vector<Shape> im64 = {{32, 1},  {32, 2},   {32, 4},   {32, 8},  {64, 8},
                                           {128, 8}, {256, 8},  {128, 16}, {512, 8}};
   if (kind == K_EXPLICIT_RESIDENT) return dtype == 0 ? ex32 : ex64;
@@ -170,6 +173,10 @@ static Shape pick_resident(const burgers_ctx* ctx, int kind, int dtype, int64_t 
     auto it = ctx->tuned.find(tune_key(kind, dtype, cap, cap == n));
     if (it != ctx->tuned.end()) return Shape{it->second.nt, it->second.c};
   }
+  // ragged FP32 explicit rows of up to 4096 nodes: 128 x 32 leaves fewer
+  // warps on the general path than 256 x 16 (about 10% faster; exact rows
+  // keep 256 x 16)
+  if (kind == K_EXPLICIT_RESIDENT && dtype == 0 && cap == 4096 && n < cap) return Shape{128, 32};
   return best;
 }
 

@@ -3,6 +3,8 @@
 // btcs_cn.cu, btcs_picard.cu and btcs_newton.cu.
 #pragma once
 
+#include <type_traits>
+
 #include "btcs_common.cuh"
 #include "common.cuh"
 #include "kernels.h"
@@ -90,6 +92,16 @@ __device__ __forceinline__ void btcs_steps(int64_t nsteps, int iters, T r, T s, 
   const int tl = EXACT ? NT - 1 : (n - 1) / C;  // chunk holding node n-1
   const int jstar = n - 1 - tid * C;              // local index of node n-1
   const int je = EXACT ? C - 1 : (jstar < C ? jstar : C - 1);  // chunk end row
+  // Ragged rows: only the warp holding node n-1 runs the general sweep (end
+  // row and padding tests per node); warps inside the row run the exact-row
+  // sweep and warps wholly past the end skip it. Warp-uniform: no warp runs
+  // two paths. Both sweeps in one kernel need registers for both: FP32
+  // shapes of up to 16 nodes a thread and 512 threads have them; the others
+  // keep the general sweep in every warp (two copies of a 32-node sweep
+  // spill).
+  constexpr bool WSPLIT = !EXACT && sizeof(T) == 4 && C <= 16 && NT <= 512;
+  const bool rw_edge = WSPLIT ? __any_sync(FULL_MASK, jstar >= 0 && jstar < C) != 0 : !EXACT;
+  const bool rw_pad = WSPLIT && __all_sync(FULL_MASK, jstar < 0) != 0;
   // matrix coefficients (Crank-Nicolson: half of the step's r and s)
   const T rm = VAR == VAR_CN ? T(0.5) * r : r, smat = VAR == VAR_CN ? T(0.5) * s : s;
   const T ds1 = T(1) + T(2) * smat;
@@ -127,7 +139,12 @@ __device__ __forceinline__ void btcs_steps(int64_t nsteps, int iters, T r, T s, 
       if (tid < tl) right = hfirst[tid + 1];
       else if constexpr (PER) right = hfirst[0];
     }
-    // ---- assembly of rows and right-hand sides fused with the forward sweep
+    // ---- assembly of rows and right-hand sides fused with the forward sweep,
+    // then the backward sweep: (delta, alpha, gamma) into (dd, ah, ch). G: the
+    // general chunk (the row's end or padding inside it) of a ragged row.
+    T e_ch = T(0), e_ah = T(0), e_dh = T(0);
+    auto sweep = [&](auto gen_tag) {
+    constexpr bool G = decltype(gen_tag)::value;
     T chp = T(0), ahp = T(-1), dhp = T(0);
     T ul = left, a = uval(0, tid);
     if constexpr (DEFER) ul = a;
@@ -136,8 +153,8 @@ __device__ __forceinline__ void btcs_steps(int64_t nsteps, int iters, T r, T s, 
       const T an = (j + 1 < C) ? uval(j + 1, tid) : right;
       T ur = an;
       if constexpr (DEFER) {
-        if (j == C - 1 || (!EXACT && j == jstar)) ur = a;  // end row of the chunk
-      } else if constexpr (!EXACT) {
+        if (j == C - 1 || (G && j == jstar)) ur = a;  // end row of the chunk
+      } else if constexpr (G) {
         if (j == jstar) ur = right;
       }
       T l, c, d, rhs;
@@ -162,10 +179,12 @@ __device__ __forceinline__ void btcs_steps(int64_t nsteps, int iters, T r, T s, 
       if constexpr (BCT == BC_DIRICHLET) {
         if constexpr (EXACT)
           ident = (j == 0 && tid == 0) || (j == C - 1 && tid == NT - 1);
-        else
+        else if constexpr (G)
           ident = (j == 0 && tid == 0) || j == jstar;
+        else  // a chunk inside a ragged row: only the row's first node
+          ident = j == 0 && tid == 0;
       }
-      if constexpr (!EXACT) {
+      if constexpr (G) {
         if (j > jstar) ident = true;
       }
       if (ident) { l = T(0); c = T(0); d = T(1); rhs = T(0); }
@@ -180,17 +199,9 @@ __device__ __forceinline__ void btcs_steps(int64_t nsteps, int iters, T r, T s, 
       ul = a;
       a = an;
     }
-    T e_ch = T(0), e_ah = T(0), e_dh = T(0);
-    if constexpr (EXACT) {
-      e_ch = ch[C - 1]; e_ah = ah[C - 1]; e_dh = dd[C - 1];
-    } else {
-#pragma unroll
-      for (int j = 0; j < C; ++j)
-        if (j == je) { e_ch = ch[j]; e_ah = ah[j]; e_dh = dd[j]; }
-    }
-    // ---- backward sweep: (delta, alpha, gamma) into (dd, ah, ch)
     T cd = T(0), ca = T(0), cg = T(-1);
-    if constexpr (EXACT) {
+    if constexpr (!G) {
+      e_ch = ch[C - 1]; e_ah = ah[C - 1]; e_dh = dd[C - 1];
       dd[C - 1] = T(0); ah[C - 1] = T(0); ch[C - 1] = T(-1);
 #pragma unroll
       for (int j = C - 2; j >= 0; --j) {
@@ -201,6 +212,9 @@ __device__ __forceinline__ void btcs_steps(int64_t nsteps, int iters, T r, T s, 
         dd[j] = cd; ah[j] = ca; ch[j] = cg;
       }
     } else {
+#pragma unroll
+      for (int j = 0; j < C; ++j)
+        if (j == je) { e_ch = ch[j]; e_ah = ah[j]; e_dh = dd[j]; }
 #pragma unroll
       for (int j = C - 1; j >= 0; --j) {
         const T cj = ch[j];
@@ -213,6 +227,17 @@ __device__ __forceinline__ void btcs_steps(int64_t nsteps, int iters, T r, T s, 
         if (past || at) { cd = T(0); ca = T(0); cg = T(-1); }
         else { cd = nd; ca = na; cg = ng; }
       }
+    }
+    };
+    if constexpr (!WSPLIT) {
+      if constexpr (EXACT) sweep(std::false_type{});
+      else sweep(std::true_type{});
+    } else if (!rw_edge && !rw_pad) {
+      sweep(std::false_type{});
+    } else if (rw_edge) {
+      sweep(std::true_type{});
+    } else {  // padding chunks: identity rows, what the general sweep leaves
+      dd[0] = T(0); ah[0] = T(0); ch[0] = T(0);
     }
     // ---- this chunk's first-row relation (the previous chunk's row reads it);
     // chunk 0 also publishes its end relation (every row's corner split does)
@@ -299,10 +324,13 @@ __device__ __forceinline__ void btcs_steps(int64_t nsteps, int iters, T r, T s, 
       else if constexpr (PER) L = sm.X[sk(tl)];
       const T Xt = sm.X[sk(tid)];
       if constexpr (DEFER) L = tfma(kap, lft, L);
+      auto update = [&](auto gen_tag) {
+      constexpr bool G = decltype(gen_tag)::value;
 #pragma unroll
       for (int j = 0; j < C; ++j) {
-        if (EXACT || j <= je) {
-          const T delta = (j == je) ? Xt : tfma(-ch[j], Xt, tfma(-ah[j], L, dd[j]));
+        const bool jend = G ? j == je : j == C - 1;
+        if (!G || j <= je) {
+          const T delta = jend ? Xt : tfma(-ch[j], Xt, tfma(-ah[j], L, dd[j]));
           const int o = j * NT + tid;
           T inc = delta;
           if constexpr (ITER) {
@@ -312,7 +340,7 @@ __device__ __forceinline__ void btcs_steps(int64_t nsteps, int iters, T r, T s, 
               if constexpr (DEFER) {
                 // the next iterate's edge values
                 if (j == 0) hfirst[tid] = us[o] + inc;
-                if (j == je) hlast[tid] = us[o] + inc;
+                if (jend) hlast[tid] = us[o] + inc;
               }
               continue;
             }
@@ -324,9 +352,18 @@ __device__ __forceinline__ void btcs_steps(int64_t nsteps, int iters, T r, T s, 
           if constexpr (Kahan<T>::on) lo[o] = l0;
           if constexpr (DEFER) {
             if (j == 0) hfirst[tid] = nv;
-            if (j == je) hlast[tid] = nv;
+            if (jend) hlast[tid] = nv;
           }
         }
+      }
+      };
+      if constexpr (!WSPLIT) {
+        if constexpr (EXACT) update(std::false_type{});
+        else update(std::true_type{});
+      } else if (rw_edge) {
+        update(std::true_type{});
+      } else {
+        update(std::false_type{});
       }
     }
   }  // iterations

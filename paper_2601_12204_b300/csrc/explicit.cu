@@ -17,6 +17,8 @@
 //    node per side per step: trapezoidal temporal blocking) and writes the
 //    central W - 2K nodes, so a pass costs about 2*sizeof(T) bytes of HBM per
 //    node for K steps.
+#include <type_traits>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -81,6 +83,35 @@ __device__ __forceinline__ bool keep_node(int j, int jstar, int64_t gbase, int n
   }
 }
 
+// Ragged rows (MODE_RAGGED): only the warp holding node n-1 needs the
+// per-node end and padding tests; warps wholly inside the row run the loop
+// of an exact row, and warps wholly past its end (padding) skip the update.
+// The tests are warp-uniform, so no warp runs two paths.
+struct RaggedWarp {
+  bool ragged, edge, pad;
+};
+template <int C, int MODE>
+__device__ __forceinline__ RaggedWarp ragged_warp(int jstar) {
+  if constexpr (MODE == MODE_RAGGED) {
+    return {true, __any_sync(FULL_MASK, jstar >= 0 && jstar < C) != 0,
+            __all_sync(FULL_MASK, jstar < 0) != 0};
+  } else {
+    return {false, false, false};
+  }
+}
+
+// keep_node for the two warp classes of a ragged row: EDGE = the general
+// test; otherwise (interior warp, every jstar >= C) only a Dirichlet row's
+// first node is held.
+template <int NT, int C, int MODE, int BCT, bool EDGE>
+__device__ __forceinline__ bool keep_node_w(int j, int jstar, int64_t gbase, int n) {
+  if constexpr (MODE == MODE_RAGGED && !EDGE) {
+    return BCT == BC_DIRICHLET && j == 0 && threadIdx.x == 0;
+  } else {
+    return keep_node<NT, C, MODE, BCT>(j, jstar, gbase, n);
+  }
+}
+
 // FP32 steps with a split state: each node carries uh (its value at the last
 // fold) and d (the increments summed since), and a step evaluates the stencil
 // on u = uh + d and adds the increment to d. Every SPLIT_FOLD steps, and after the
@@ -96,6 +127,7 @@ __device__ __forceinline__ void explicit_steps_split(float (&v)[C], float (&lo)[
   constexpr bool WRAPX = (MODE == MODE_RAGGED && BCT == BC_PERIODIC);
   const int tid = threadIdx.x;
   const int jstar = int(n - 1 - gbase);  // local index of node n-1 (resident modes)
+  const RaggedWarp rw = ragged_warp<C, MODE>(jstar);
   // lo becomes d = -lo
 #pragma unroll
   for (int j = 0; j < C; ++j) lo[j] = -lo[j];
@@ -111,30 +143,38 @@ __device__ __forceinline__ void explicit_steps_split(float (&v)[C], float (&lo)[
     bool has_wrap = false;
     if constexpr (WRAPX) {
       has_wrap = jstar >= 0 && jstar < C;
-      float sv = v[0], sd = lo[0];
+      if (rw.edge) {  // only the warp holding node n-1 looks for it
+        float sv = v[0], sd = lo[0];
 #pragma unroll
-      for (int j = 1; j < C; ++j)
-        if (j == jstar) { sv = v[j]; sd = lo[j]; }
-      wsel = sv + sd;
+        for (int j = 1; j < C; ++j)
+          if (j == jstar) { sv = v[j]; sd = lo[j]; }
+        wsel = sv + sd;
+      }
     }
     float left, right, wrapL = 0.f, wrapR = 0.f;
     halo_exchange<float, NT, WRAPX>(first, last, wsel, has_wrap, p, sh_last, sh_first, sh_wrap,
                                     left, right, wrapL, wrapR);
-    float wl = left, wc = first;
+    float wl0 = left;
     if constexpr (WRAPX) {
-      if (tid == 0) wl = wrapL;
+      if (tid == 0) wl0 = wrapL;
     }
+    auto update = [&](auto edge_tag) {
+      constexpr bool EDGE = decltype(edge_tag)::value;
+      float wl = wl0, wc = first;
 #pragma unroll
-    for (int j = 0; j < C; ++j) {
-      float wr = (j + 1 < C) ? v[j + 1] + lo[j + 1] : right;
-      if constexpr (WRAPX) {
-        if (j == jstar) wr = wrapR;
+      for (int j = 0; j < C; ++j) {
+        float wr = (j + 1 < C) ? v[j + 1] + lo[j + 1] : right;
+        if constexpr (WRAPX && EDGE) {
+          if (j == jstar) wr = wrapR;
+        }
+        const float dn = explicit_increment(wc, wl, wr, r, h, s, lo[j]);
+        if (!keep_node_w<NT, C, MODE, BCT, EDGE>(j, jstar, gbase, n)) lo[j] = dn;
+        wl = wc;
+        wc = wr;
       }
-      const float dn = explicit_increment(wc, wl, wr, r, h, s, lo[j]);
-      if (!keep_node<NT, C, MODE, BCT>(j, jstar, gbase, n)) lo[j] = dn;
-      wl = wc;
-      wc = wr;
-    }
+    };
+    if (!rw.ragged || rw.edge) update(std::true_type{});
+    else if (!rw.pad) update(std::false_type{});
    }
 #pragma unroll
     for (int j = 0; j < C; ++j) {
@@ -165,6 +205,7 @@ __device__ __forceinline__ void rk4_steps(T (&v)[C], T (&lo)[C], int64_t nsteps,
   constexpr bool WRAPX = (MODE == MODE_RAGGED && BCT == BC_PERIODIC);
   const int tid = threadIdx.x;
   const int jstar = int(n - 1 - gbase);
+  const RaggedWarp rw = ragged_warp<C, MODE>(jstar);
   if constexpr (SPLIT) {
 #pragma unroll
     for (int j = 0; j < C; ++j) lo[j] = -lo[j];  // lo becomes d
@@ -190,34 +231,51 @@ __device__ __forceinline__ void rk4_steps(T (&v)[C], T (&lo)[C], int64_t nsteps,
       bool has_wrap = false;
       if constexpr (WRAPX) {
         has_wrap = jstar >= 0 && jstar < C;
-        T sv = v[0], sd = lo[0], sk = K[0];
+        if (rw.edge) {
+          T sv = v[0], sd = lo[0], sk = K[0];
 #pragma unroll
-        for (int j = 1; j < C; ++j)
-          if (j == jstar) { sv = v[j]; sd = lo[j]; sk = K[j]; }
-        T su = sv;
-        if constexpr (SPLIT) su = sv + sd;
-        wsel = st == 0 ? su : tfma(cst, sk, su);
+          for (int j = 1; j < C; ++j)
+            if (j == jstar) { sv = v[j]; sd = lo[j]; sk = K[j]; }
+          T su = sv;
+          if constexpr (SPLIT) su = sv + sd;
+          wsel = st == 0 ? su : tfma(cst, sk, su);
+        }
       }
       T left, right, wrapL = T(0), wrapR = T(0);
       halo_exchange<T, NT, WRAPX>(first, last, wsel, has_wrap, st & 1, sh_last, sh_first,
                                   sh_wrap, left, right, wrapL, wrapR);
-      T wl = left, wc = first;
+      T wl0 = left;
       if constexpr (WRAPX) {
-        if (tid == 0) wl = wrapL;
+        if (tid == 0) wl0 = wrapL;
       }
+      auto stage = [&](auto edge_tag) {
+        constexpr bool EDGE = decltype(edge_tag)::value;
+        T wl = wl0, wc = first;
 #pragma unroll
-      for (int j = 0; j < C; ++j) {
-        T wr = (j + 1 < C) ? wv(j + 1) : right;
-        if constexpr (WRAPX) {
-          if (j == jstar) wr = wrapR;
+        for (int j = 0; j < C; ++j) {
+          T wr = (j + 1 < C) ? wv(j + 1) : right;
+          if constexpr (WRAPX && EDGE) {
+            if (j == jstar) wr = wrapR;
+          }
+          T kn = explicit_increment(wc, wl, wr, r, h, s, T(0));
+          if (keep_node_w<NT, C, MODE, BCT, EDGE>(j, jstar, gbase, n)) kn = T(0);
+          if (st == 0) acc[j] = kn;
+          else acc[j] = tfma((st == 3) ? T(1) : T(2), kn, acc[j]);
+          K[j] = kn;
+          wl = wc;
+          wc = wr;
         }
-        T kn = explicit_increment(wc, wl, wr, r, h, s, T(0));
-        if (keep_node<NT, C, MODE, BCT>(j, jstar, gbase, n)) kn = T(0);
-        if (st == 0) acc[j] = kn;
-        else acc[j] = tfma((st == 3) ? T(1) : T(2), kn, acc[j]);
-        K[j] = kn;
-        wl = wc;
-        wc = wr;
+      };
+      if (!rw.ragged || rw.edge) {
+        stage(std::true_type{});
+      } else if (!rw.pad) {
+        stage(std::false_type{});
+      } else {  // padding: held nodes, zero increments
+#pragma unroll
+        for (int j = 0; j < C; ++j) {
+          if (st == 0) acc[j] = T(0);
+          K[j] = T(0);
+        }
       }
     }
     const T sixth = T(1) / T(6);
@@ -266,6 +324,7 @@ __device__ __forceinline__ void explicit_steps(T (&v)[C], T (&lo)[C], int64_t ns
     constexpr bool WRAPX = (MODE == MODE_RAGGED && BCT == BC_PERIODIC);
     const int tid = threadIdx.x;
     const int jstar = int(n - 1 - gbase);
+    const RaggedWarp rw = ragged_warp<C, MODE>(jstar);
     for (int64_t k = 0; k < nsteps; ++k) {
       const int p = int(k & 1);
       const T first = v[0], last = v[C - 1];
@@ -273,29 +332,37 @@ __device__ __forceinline__ void explicit_steps(T (&v)[C], T (&lo)[C], int64_t ns
       bool has_wrap = false;
       if constexpr (WRAPX) {
         has_wrap = jstar >= 0 && jstar < C;
-        wsel = v[0];
+        if (rw.edge) {
+          wsel = v[0];
 #pragma unroll
-        for (int j = 1; j < C; ++j)
-          if (j == jstar) wsel = v[j];
+          for (int j = 1; j < C; ++j)
+            if (j == jstar) wsel = v[j];
+        }
       }
       T left, right, wrapL = T(0), wrapR = T(0);
       halo_exchange<T, NT, WRAPX>(first, last, wsel, has_wrap, p, sh_last, sh_first, sh_wrap, left,
                                   right, wrapL, wrapR);
-      T prev = left;
+      T prev0 = left;
       if constexpr (WRAPX) {
-        if (tid == 0) prev = wrapL;
+        if (tid == 0) prev0 = wrapL;
       }
+      auto update = [&](auto edge_tag) {
+        constexpr bool EDGE = decltype(edge_tag)::value;
+        T prev = prev0;
 #pragma unroll
-      for (int j = 0; j < C; ++j) {
-        const T cur = v[j];
-        T ur = (j + 1 < C) ? v[j + 1] : right;
-        if constexpr (WRAPX) {
-          if (j == jstar) ur = wrapR;
+        for (int j = 0; j < C; ++j) {
+          const T cur = v[j];
+          T ur = (j + 1 < C) ? v[j + 1] : right;
+          if constexpr (WRAPX && EDGE) {
+            if (j == jstar) ur = wrapR;
+          }
+          const T nv = explicit_update(cur, prev, ur, r, h, s, lo[j]);
+          if (!keep_node_w<NT, C, MODE, BCT, EDGE>(j, jstar, gbase, n)) v[j] = nv;
+          prev = cur;
         }
-        const T nv = explicit_update(cur, prev, ur, r, h, s, lo[j]);
-        if (!keep_node<NT, C, MODE, BCT>(j, jstar, gbase, n)) v[j] = nv;
-        prev = cur;
-      }
+      };
+      if (!rw.ragged || rw.edge) update(std::true_type{});
+      else if (!rw.pad) update(std::false_type{});
     }
   }
 }
