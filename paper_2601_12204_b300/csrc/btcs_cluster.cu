@@ -342,11 +342,19 @@ __launch_bounds__(NT, (sizeof(T) == 4 && NT <= 512) ? 512 / NT : 1)
   // take the branch-free path; any other warp takes the general one with all
   // its lanes (one pass instead of both, one after the other, in a diverged
   // warp), and warps past the row's end skip the sweep. The cluster barrier
-  // paces every step by the slowest CTA, so a ragged last CTA must not be slow.
-  const bool plainchunk = __all_sync(
-      FULL_MASK, je == C - 1 && jstar >= C - 1 &&
-                     (per || !((rank == 0 && tid == 0) || (lastcta && tid == tl))));
+  // paces every step by the slowest CTA, so a ragged last CTA must not be
+  // slow: the general path runs the same forward sweep (the chunk holding the
+  // row's last node stores its right neighbour in its first padding slot, so
+  // its end row reads it there; rows past the end give unused finite values,
+  // the system being diagonally dominant) and restarts the backward sweep at
+  // the chunk's end row. Dirichlet identity rows: the row's first node is
+  // replaced at j = 0; its last one only sets the chunk's end relation, which
+  // is zeroed after the sweep.
+  const bool dfirst = !per && rank == 0 && tid == 0;
+  const bool dlast = !per && lastcta && tid == tl;
+  const bool plainchunk = __all_sync(FULL_MASK, je == C - 1 && jstar >= C - 1 && !dfirst && !dlast);
   const bool padwarp = __all_sync(FULL_MASK, jstar < 0);
+  const bool endslot = jstar >= 0 && jstar < C - 1;  // chunk with padding after node n-1
   T ch[C], ah[C], dd[C];
   int par = 0;  // slot buffer of this step
   for (int64_t step = 0; step < rd.nsteps; ++step) {
@@ -357,21 +365,22 @@ __launch_bounds__(NT, (sizeof(T) == 4 && NT <= 512) ? 512 / NT : 1)
     T e_ch = T(0), e_ah = T(0), e_dh = T(0);
     auto sweep = [&](auto full_tag) {
       constexpr bool FULL = decltype(full_tag)::value;
+      if constexpr (!FULL) {
+        if (endslot) us[(jstar + 1) * NT + tid] = right;
+      }
       T chp = T(0), ahp = T(-1), dhp = T(0);
       T ul = left, a = us[tid];
 #pragma unroll
       for (int j = 0; j < C; ++j) {
         const T an = (j + 1 < C) ? us[(j + 1) * NT + tid] : right;
-        const T ur = (FULL || j != jstar) ? an : right;
+        const T ur = an;
         const T ra = r * a;
         T l = -s - tmax(ra, T(0));
         T c = tmin(ra, T(0)) - s;
         T d = ds1 + tabs(ra);
         T rhs = tfma(l, a - ul, -c * (ur - a));
         if constexpr (!FULL) {
-          bool ident = j > jstar;  // padding of the row's last CTA
-          if (!per) ident = ident || (rank == 0 && tid == 0 && j == 0) || (lastcta && j == jstar);
-          if (ident) { l = T(0); c = T(0); d = T(1); rhs = T(0); }
+          if (j == 0 && dfirst) { l = T(0); c = T(0); d = T(1); rhs = T(0); }
         }
         const T inv = recip(tfma(-l, chp, d));
         const T li = l * inv;
@@ -397,22 +406,21 @@ __launch_bounds__(NT, (sizeof(T) == 4 && NT <= 512) ? 512 / NT : 1)
           dd[j] = cd; ah[j] = ca; ch[j] = cgm;
         }
       } else {
-#pragma unroll
-        for (int j = 0; j < C; ++j)
-          if (j == je) { e_ch = ch[j]; e_ah = ah[j]; e_dh = dd[j]; }
+        // as above, restarted at the end row je (values past it are unused)
+        e_ch = ch[C - 1]; e_ah = ah[C - 1]; e_dh = dd[C - 1];
         T cd = T(0), ca = T(0), cgm = T(-1);
+        dd[C - 1] = T(0); ah[C - 1] = T(0); ch[C - 1] = T(-1);
 #pragma unroll
-        for (int j = C - 1; j >= 0; --j) {
+        for (int j = C - 2; j >= 0; --j) {
           const T cj = ch[j];
-          T nd = tfma(-cj, cd, dd[j]);
-          T na = tfma(-cj, ca, ah[j]);
-          T ng = -cj * cgm;
-          const bool past = j > je, at = j == je;
-          if (past || at) { nd = T(0); na = T(0); ng = at ? T(-1) : T(0); }
-          dd[j] = nd; ah[j] = na; ch[j] = ng;
-          if (past || at) { cd = T(0); ca = T(0); cgm = T(-1); }
-          else { cd = nd; ca = na; cgm = ng; }
+          const bool at = j == je;
+          if (at) { e_ch = cj; e_ah = ah[j]; e_dh = dd[j]; }
+          cd = at ? T(0) : tfma(-cj, cd, dd[j]);
+          ca = at ? T(0) : tfma(-cj, ca, ah[j]);
+          cgm = at ? T(-1) : -cj * cgm;
+          dd[j] = cd; ah[j] = ca; ch[j] = cgm;
         }
+        if (dlast) { e_ch = T(0); e_ah = T(0); e_dh = T(0); }
       }
     };
     if (plainchunk) {
