@@ -92,8 +92,8 @@ __device__ __forceinline__ void btcs_steps(int64_t nsteps, int iters, T r, T s, 
   const int tl = EXACT ? NT - 1 : (n - 1) / C;  // chunk holding node n-1
   const int jstar = n - 1 - tid * C;              // local index of node n-1
   const int je = EXACT ? C - 1 : (jstar < C ? jstar : C - 1);  // chunk end row
-  // Ragged rows: only the warp holding node n-1 runs the general sweep (end
-  // row and padding tests per node); warps inside the row run the exact-row
+  // Ragged rows: only the warp holding node n-1 runs the general sweep (its
+  // backward sweep restarts at the chunk's end row); warps inside the row run the exact-row
   // sweep and warps wholly past the end skip it. Warp-uniform: no warp runs
   // two paths. Both sweeps in one kernel need registers for both: FP32
   // shapes of up to 16 nodes a thread and 512 threads have them; the others
@@ -102,6 +102,7 @@ __device__ __forceinline__ void btcs_steps(int64_t nsteps, int iters, T r, T s, 
   constexpr bool WSPLIT = !EXACT && sizeof(T) == 4 && C <= 16 && NT <= 512;
   const bool rw_edge = WSPLIT ? __any_sync(FULL_MASK, jstar >= 0 && jstar < C) != 0 : !EXACT;
   const bool rw_pad = WSPLIT && __all_sync(FULL_MASK, jstar < 0) != 0;
+  const bool endslot = !EXACT && jstar >= 0 && jstar < C - 1;  // padding after node n-1
   // matrix coefficients (Crank-Nicolson: half of the step's r and s)
   const T rm = VAR == VAR_CN ? T(0.5) * r : r, smat = VAR == VAR_CN ? T(0.5) * s : s;
   const T ds1 = T(1) + T(2) * smat;
@@ -145,6 +146,11 @@ __device__ __forceinline__ void btcs_steps(int64_t nsteps, int iters, T r, T s, 
     T e_ch = T(0), e_ah = T(0), e_dh = T(0);
     auto sweep = [&](auto gen_tag) {
     constexpr bool G = decltype(gen_tag)::value;
+    if constexpr (G) {
+      // the end row reads its right neighbour from the first padding slot
+      // (deferred rows: the node itself); padding slots have es = 0
+      if (endslot) us[(jstar + 1) * NT + tid] = DEFER ? uval(jstar, tid) : right;
+    }
     T chp = T(0), ahp = T(-1), dhp = T(0);
     T ul = left, a = uval(0, tid);
     if constexpr (DEFER) ul = a;
@@ -153,9 +159,7 @@ __device__ __forceinline__ void btcs_steps(int64_t nsteps, int iters, T r, T s, 
       const T an = (j + 1 < C) ? uval(j + 1, tid) : right;
       T ur = an;
       if constexpr (DEFER) {
-        if (j == C - 1 || (G && j == jstar)) ur = a;  // end row of the chunk
-      } else if constexpr (G) {
-        if (j == jstar) ur = right;
+        if (j == C - 1) ur = a;  // end row of the chunk
       }
       T l, c, d, rhs;
       if constexpr (VAR == VAR_NEWTON) {
@@ -179,13 +183,8 @@ __device__ __forceinline__ void btcs_steps(int64_t nsteps, int iters, T r, T s, 
       if constexpr (BCT == BC_DIRICHLET) {
         if constexpr (EXACT)
           ident = (j == 0 && tid == 0) || (j == C - 1 && tid == NT - 1);
-        else if constexpr (G)
-          ident = (j == 0 && tid == 0) || j == jstar;
-        else  // a chunk inside a ragged row: only the row's first node
+        else  // ragged: the row's first node (its last one: end relation below)
           ident = j == 0 && tid == 0;
-      }
-      if constexpr (G) {
-        if (j > jstar) ident = true;
       }
       if (ident) { l = T(0); c = T(0); d = T(1); rhs = T(0); }
       const T inv = recip(tfma(-l, chp, d));
@@ -212,21 +211,23 @@ __device__ __forceinline__ void btcs_steps(int64_t nsteps, int iters, T r, T s, 
         dd[j] = cd; ah[j] = ca; ch[j] = cg;
       }
     } else {
+      // restarted at the end row je; rows past it (padding, finite values of
+      // a diagonally dominant system) are never used
+      e_ch = ch[C - 1]; e_ah = ah[C - 1]; e_dh = dd[C - 1];
+      dd[C - 1] = T(0); ah[C - 1] = T(0); ch[C - 1] = T(-1);
 #pragma unroll
-      for (int j = 0; j < C; ++j)
-        if (j == je) { e_ch = ch[j]; e_ah = ah[j]; e_dh = dd[j]; }
-#pragma unroll
-      for (int j = C - 1; j >= 0; --j) {
+      for (int j = C - 2; j >= 0; --j) {
         const T cj = ch[j];
-        T nd = tfma(-cj, cd, dd[j]);
-        T na = tfma(-cj, ca, ah[j]);
-        T ng = -cj * cg;
-        const bool past = j > je, at = j == je;
-        if (past || at) { nd = T(0); na = T(0); ng = at ? T(-1) : T(0); }
-        dd[j] = nd; ah[j] = na; ch[j] = ng;
-        if (past || at) { cd = T(0); ca = T(0); cg = T(-1); }
-        else { cd = nd; ca = na; cg = ng; }
+        const bool at = j == je;
+        if (at) { e_ch = cj; e_ah = ah[j]; e_dh = dd[j]; }
+        cd = at ? T(0) : tfma(-cj, cd, dd[j]);
+        ca = at ? T(0) : tfma(-cj, ca, ah[j]);
+        cg = at ? T(-1) : -cj * cg;
+        dd[j] = cd; ah[j] = ca; ch[j] = cg;
       }
+      // Dirichlet: the row's last node is an identity row, which leaves the
+      // chunk's end relation zero
+      if (BCT == BC_DIRICHLET && tid == tl) { e_ch = T(0); e_ah = T(0); e_dh = T(0); }
     }
     };
     if constexpr (!WSPLIT) {
