@@ -116,12 +116,20 @@ class PinnedArena {
     const int64_t size = std::max<int64_t>(kSlab, (bytes + 255) & ~int64_t(255));
     if (total_ + size > kCap) return nullptr;
     void* p = nullptr;
-    if (cudaHostAlloc(&p, size_t(size), cudaHostAllocDefault) != cudaSuccess) {
+    if (cudaHostAlloc(&p, size_t(size), cudaHostAllocMapped) != cudaSuccess) {
       cudaGetLastError();
       return nullptr;
     }
+    // the copy kernels reach the slab through its device alias; without one
+    // its requests fall back to cudaMemcpyAsync
+    void* dp = nullptr;
+    if (cudaHostGetDevicePointer(&dp, p, 0) != cudaSuccess) {
+      cudaGetLastError();
+      dp = nullptr;
+    }
     total_ += size;
-    slabs_.push_back(Slab{static_cast<unsigned char*>(p), size, Region()});
+    slabs_.push_back(Slab{static_cast<unsigned char*>(p), static_cast<unsigned char*>(dp), size,
+                          Region()});
     Slab& sl = slabs_.back();
     sl.rg.init(0, size);
     int64_t off = 0;
@@ -144,6 +152,13 @@ class PinnedArena {
         return;
       }
   }
+  // Device alias of the page-locked bytes [p, p + bytes), or nullptr.
+  void* device_alias(unsigned char* p, int64_t bytes) const {
+    for (const Slab& sl : slabs_)
+      if (p >= sl.base && p + bytes <= sl.base + sl.size)
+        return sl.dev ? static_cast<void*>(sl.dev + (p - sl.base)) : nullptr;
+    return nullptr;
+  }
   ~PinnedArena() {
     for (Slab& sl : slabs_) cudaFreeHost(sl.base);
   }
@@ -151,11 +166,85 @@ class PinnedArena {
  private:
   struct Slab {
     unsigned char* base;
+    unsigned char* dev;  // device alias of the mapped slab
     int64_t size;
     Region rg;
   };
   std::vector<Slab> slabs_;
   int64_t total_ = 0;
+};
+
+// One request's transfer between its page-locked buffer (through the device
+// alias) and its slot in the pool. Both ends 16-byte aligned, bytes a
+// multiple of 4 (FP32 / FP64 rows).
+struct CopyDesc {
+  const void* src;
+  void* dst;
+  int64_t bytes;
+};
+
+// All admission (or all result) transfers of a slice in one launch instead
+// of one cudaMemcpyAsync per request, whose host-side cost dominated the
+// worker's slice boundary: CTA i moves requests i, i + grid, ... with
+// 16-byte accesses (the tail in 4-byte words).
+__global__ void __launch_bounds__(256) k_serve_copy(const CopyDesc* __restrict__ d, int count) {
+  for (int i = blockIdx.x; i < count; i += gridDim.x) {
+    const CopyDesc c = d[i];
+    const int64_t nv = c.bytes >> 4;
+    const uint4* src = static_cast<const uint4*>(c.src);
+    uint4* dst = static_cast<uint4*>(c.dst);
+    for (int64_t k = threadIdx.x; k < nv; k += blockDim.x) dst[k] = src[k];
+    const int tail = int((c.bytes - (nv << 4)) >> 2);
+    if (int(threadIdx.x) < tail) {
+      const uint32_t* s4 = reinterpret_cast<const uint32_t*>(static_cast<const char*>(c.src) + (nv << 4));
+      uint32_t* d4 = reinterpret_cast<uint32_t*>(static_cast<char*>(c.dst) + (nv << 4));
+      d4[threadIdx.x] = s4[threadIdx.x];
+    }
+  }
+}
+
+// Page-locked, mapped descriptor list of one direction of one slice (the
+// kernel reads it through its device alias). Rewritten only after the slice
+// that last read it has retired.
+class CopyStage {
+ public:
+  bool push(const void* src, void* dst, int64_t bytes) {
+    if (n_ == cap_ && !grow()) return false;
+    host_[n_++] = CopyDesc{src, dst, bytes};
+    return true;
+  }
+  void clear() { n_ = 0; }
+  int size() const { return n_; }
+  const CopyDesc* device() const { return dev_; }
+  ~CopyStage() {
+    if (host_) cudaFreeHost(host_);
+  }
+
+ private:
+  bool grow() {
+    const int cap = cap_ ? 2 * cap_ : 1024;
+    void* p = nullptr;
+    if (cudaHostAlloc(&p, sizeof(CopyDesc) * size_t(cap), cudaHostAllocMapped) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    void* dp = nullptr;
+    if (cudaHostGetDevicePointer(&dp, p, 0) != cudaSuccess) {
+      cudaGetLastError();
+      cudaFreeHost(p);
+      return false;
+    }
+    if (n_) memcpy(p, host_, sizeof(CopyDesc) * size_t(n_));
+    // the old list is not in use: this stage's previous slice has retired
+    if (host_) cudaFreeHost(host_);
+    host_ = static_cast<CopyDesc*>(p);
+    dev_ = static_cast<CopyDesc*>(dp);
+    cap_ = cap;
+    return true;
+  }
+  CopyDesc* host_ = nullptr;
+  CopyDesc* dev_ = nullptr;
+  int n_ = 0, cap_ = 0;
 };
 
 enum ReqState : int { RQ_PENDING = 0, RQ_ACTIVE = 1, RQ_DONE = 2, RQ_CANCELED = 3, RQ_FAILED = 4 };
@@ -198,6 +287,7 @@ struct burgers_server {
   burgers_status fault = BURGERS_OK;
   std::string fault_msg;
   burgers::PlanScratch ps_explicit[2], ps_btcs[2];  // descriptors of the slices in flight
+  burgers::CopyStage stage_in[2], stage_out[2];     // their admission / result transfers
   burgers::PinnedArena pinned;
   burgers_serve_stats stats{};
   double t0 = 0;
@@ -314,6 +404,19 @@ static void fail_worker(burgers_server* sv, InFlight* fl, burgers_status st, con
   fail_all(sv, st, msg);
 }
 
+static bool aligned16(const void* a, const void* b) {
+  return ((reinterpret_cast<uintptr_t>(a) | reinterpret_cast<uintptr_t>(b)) & 15) == 0;
+}
+
+// Moves the transfers listed in `st` on the worker's stream.
+static cudaError_t launch_copies(burgers_server* sv, const CopyStage& st) {
+  if (st.size() == 0) return cudaSuccess;
+  const int grid = std::min(st.size(), 4 * sv->ctx->sm_count);
+  k_serve_copy<<<grid, 256, 0, sv->stream>>>(st.device(), st.size());
+  sv->ctx->launches += 1;
+  return cudaGetLastError();
+}
+
 // The worker. Which requests a slice finishes follows from the step counts,
 // so the next slice is planned, its admission copies queued and it is
 // enqueued while the current one runs (two slices in flight at most, each
@@ -373,15 +476,21 @@ static void worker_loop(burgers_server* sv) {
       }
       continue;
     }
-    // ---- copy the new requests' u0 into their slots
+    // ---- copy the new requests' u0 into their slots (one kernel for those
+    // in mapped page-locked buffers, a copy each for the rest)
     double tw0 = now_s();
     cudaError_t e = cudaSuccess;
+    CopyStage& sin = sv->stage_in[par];
+    sin.clear();
     for (Req* q : admitted) {
-      e = cudaMemcpyAsync(static_cast<char*>(sv->pool) + q->off,
-                          q->pin ? static_cast<const void*>(q->pin) : q->u0.data(),
+      char* slot = static_cast<char*>(sv->pool) + q->off;
+      const void* src = q->pin ? sv->pinned.device_alias(q->pin, q->bytes) : nullptr;
+      if (src && aligned16(src, slot) && sin.push(src, slot, q->bytes)) continue;
+      e = cudaMemcpyAsync(slot, q->pin ? static_cast<const void*>(q->pin) : q->u0.data(),
                           size_t(q->bytes), cudaMemcpyHostToDevice, sv->stream);
       if (e != cudaSuccess) break;
     }
+    if (e == cudaSuccess) e = launch_copies(sv, sin);
     if (e != cudaSuccess) {
       fail_worker(sv, fl, cuda_error(e, "serve admission copy"), burgers_last_error());
       return;
@@ -424,16 +533,21 @@ static void worker_loop(burgers_server* sv) {
         if (q->done_steps >= q->r.nsteps) finished.push_back(q);
       }
     }
+    CopyStage& sout = sv->stage_out[par];
+    sout.clear();
     for (Req* q : finished) {
+      const char* slot = static_cast<const char*>(sv->pool) + q->off;
+      void* alias = q->pin ? sv->pinned.device_alias(q->pin, q->bytes) : nullptr;
+      if (alias && aligned16(alias, slot) && sout.push(slot, alias, q->bytes)) continue;
       void* dst = q->pin;
       if (!dst) {
         q->out.resize(size_t(q->bytes));
         dst = q->out.data();
       }
-      e = cudaMemcpyAsync(dst, static_cast<char*>(sv->pool) + q->off, size_t(q->bytes),
-                          cudaMemcpyDeviceToHost, sv->stream);
+      e = cudaMemcpyAsync(dst, slot, size_t(q->bytes), cudaMemcpyDeviceToHost, sv->stream);
       if (e != cudaSuccess) break;
     }
+    if (e == cudaSuccess) e = launch_copies(sv, sout);
     if (e == cudaSuccess) e = cudaEventRecord(sv->ev[par], sv->stream);
     if (e != cudaSuccess) {
       fail_worker(sv, fl, cuda_error(e, "serve result copy"), burgers_last_error());
