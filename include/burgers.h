@@ -249,7 +249,7 @@ burgers_status burgers_explicit_advance_noalloc(const burgers_instance* inst, in
 /* End-to-end variant through host memory: copies every row from u_host to a
  * context-owned device buffer, advances it with `scheme` (a burgers_scheme;
  * BURGERS_PICARD and BURGERS_NEWTON with one iteration per step), copies the
- * rows back into u_host. Batches of 64 rows or more are cut into four chunks
+ * rows back into u_host. Batches of 64 rows or more are cut into eight chunks
  * of whole rows (in offset order) that are copied in, solved and copied out
  * as a pipeline on the context's copy streams, so transfers overlap the
  * solves. Rows are independent, so the result does not depend on the cut.

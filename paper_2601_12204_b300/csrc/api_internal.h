@@ -123,7 +123,7 @@ struct burgers_ctx {
   cudaStream_t side[kSide] = {};
   cudaEvent_t fork_ev = nullptr, join_ev[kSide] = {};
   // host-memory solves: copy streams and per-chunk events of the pipeline
-  static constexpr int kIoChunks = 4;
+  static constexpr int kIoChunks = 8;
   cudaStream_t io_h2d = nullptr, io_d2h = nullptr;
   cudaEvent_t io_in[kIoChunks] = {}, io_out[kIoChunks] = {};
   std::list<std::unique_ptr<burgers::Plan>> plans;
