@@ -411,7 +411,7 @@ def run_ours(args):
 
 
 def differentiation_bench(ctx, dev):
-    """Configuration 5: J = 1/2 |u(T) - target|^2 over B = 1024 periodic rows of
+    """Differentiation workload: J = 1/2 |u(T) - target|^2 over B = 1024 periodic rows of
     2048 nodes (random-Fourier u0; the target is the same run from the
     ensemble of the next seed, with a dt per row that satisfies the CFL limit
     of both initial fields), 2000 explicit / 200 BTCS steps, gradients by
@@ -726,7 +726,7 @@ def extras(args, ctx, ens, u0, batches, probe, dev, world, rank):
 
 
 def serve_bench(ctx, dev, duration: float, rate: float = 20000.0, plain_seconds: float = 5.0):
-    """Configuration 4: Poisson arrivals at `rate` for `duration` s of mixed
+    """Serving workload: Poisson arrivals at `rate` for `duration` s of mixed
     requests through the continuous-batching server; latency = done - submit
     on the server clock. Also the plain path: the same trace served one
     request per launch, in arrival order, for at most `plain_seconds`."""
@@ -860,7 +860,7 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=1.0,
                     help="length of the Poisson trace of the serving measurement (0 = skip)")
     ap.add_argument("--serve-only", action="store_true",
-                    help="run only the serving measurement (configuration 4) and print its JSON")
+                    help="run only the serving measurement and print its JSON")
     ap.add_argument("--serve-plain-seconds", type=float, default=5.0,
                     help="time limit of the one-request-per-launch comparison path (0 = skip it)")
     args = ap.parse_args()

@@ -109,9 +109,16 @@ class PinnedArena {
   static constexpr int64_t kSlab = int64_t(64) << 20;
   static constexpr int64_t kCap = int64_t(8) << 30;
   unsigned char* alloc(int64_t bytes) {
-    for (Slab& sl : slabs_) {
+    // first fit, starting at the slab that served the last request (requests
+    // come and go roughly in order, so the slabs before it are mostly full)
+    const size_t ns = slabs_.size();
+    for (size_t k = 0; k < ns; ++k) {
+      const size_t i = (hint_ + k) % ns;
       int64_t off;
-      if (sl.rg.alloc(bytes, &off)) return sl.base + off;
+      if (slabs_[i].rg.alloc(bytes, &off)) {
+        hint_ = i;
+        return slabs_[i].base + off;
+      }
     }
     const int64_t size = std::max<int64_t>(kSlab, (bytes + 255) & ~int64_t(255));
     if (total_ + size > kCap) return nullptr;
@@ -134,6 +141,7 @@ class PinnedArena {
     sl.rg.init(0, size);
     int64_t off = 0;
     sl.rg.alloc(bytes, &off);
+    hint_ = slabs_.size() - 1;
     return sl.base + off;
   }
   void reserve(int slabs) {
@@ -171,6 +179,7 @@ class PinnedArena {
     Region rg;
   };
   std::vector<Slab> slabs_;
+  size_t hint_ = 0;
   int64_t total_ = 0;
 };
 
@@ -255,6 +264,7 @@ struct Req {
   std::vector<unsigned char> u0;   // pageable fallback of pin
   std::vector<unsigned char> out;  // pageable fallback of pin
   unsigned char* pin = nullptr;    // page-locked state: u0, later the result
+  void* pin_dev = nullptr;         // its device alias (nullptr: copied by cudaMemcpyAsync)
   int state = RQ_PENDING;
   burgers_status status = BURGERS_OK;
   bool long_row = false;
@@ -288,6 +298,7 @@ struct burgers_server {
   std::string fault_msg;
   burgers::PlanScratch ps_explicit[2], ps_btcs[2];  // descriptors of the slices in flight
   burgers::CopyStage stage_in[2], stage_out[2];     // their admission / result transfers
+  std::mutex pin_mu;  // guards `pinned` (taken alone, or after mu)
   burgers::PinnedArena pinned;
   burgers_serve_stats stats{};
   double t0 = 0;
@@ -484,7 +495,7 @@ static void worker_loop(burgers_server* sv) {
     sin.clear();
     for (Req* q : admitted) {
       char* slot = static_cast<char*>(sv->pool) + q->off;
-      const void* src = q->pin ? sv->pinned.device_alias(q->pin, q->bytes) : nullptr;
+      const void* src = q->pin_dev;
       if (src && aligned16(src, slot) && sin.push(src, slot, q->bytes)) continue;
       e = cudaMemcpyAsync(slot, q->pin ? static_cast<const void*>(q->pin) : q->u0.data(),
                           size_t(q->bytes), cudaMemcpyHostToDevice, sv->stream);
@@ -537,7 +548,7 @@ static void worker_loop(burgers_server* sv) {
     sout.clear();
     for (Req* q : finished) {
       const char* slot = static_cast<const char*>(sv->pool) + q->off;
-      void* alias = q->pin ? sv->pinned.device_alias(q->pin, q->bytes) : nullptr;
+      void* alias = q->pin_dev;
       if (alias && aligned16(alias, slot) && sout.push(slot, alias, q->bytes)) continue;
       void* dst = q->pin;
       if (!dst) {
@@ -662,14 +673,26 @@ burgers_status burgers_serve_submit(burgers_server* sv, const burgers_request* r
   q->long_row = rq->n > long_limit(sv, rq->scheme);
   const Region& rg = q->long_row ? sv->long_region : sv->short_region;
   if (q->bytes > rg.total()) return set_error(BURGERS_ENOMEM, "request larger than the pool region");
-  std::lock_guard<std::mutex> lk(sv->mu);
-  if (sv->fault != BURGERS_OK) return set_error(sv->fault, "server failed: " + sv->fault_msg);
-  q->pin = sv->pinned.alloc(q->bytes);
+  // the page-locked copy of u0 is made outside the server lock (the arena has
+  // its own), so neither the worker nor other submitters wait on it
+  {
+    std::lock_guard<std::mutex> pk(sv->pin_mu);
+    q->pin = sv->pinned.alloc(q->bytes);
+    if (q->pin) q->pin_dev = sv->pinned.device_alias(q->pin, q->bytes);
+  }
   if (q->pin) {
     memcpy(q->pin, rq->u0_host, size_t(q->bytes));
   } else {
     q->u0.assign(static_cast<const unsigned char*>(rq->u0_host),
                  static_cast<const unsigned char*>(rq->u0_host) + q->bytes);
+  }
+  std::lock_guard<std::mutex> lk(sv->mu);
+  if (sv->fault != BURGERS_OK) {
+    if (q->pin) {
+      std::lock_guard<std::mutex> pk(sv->pin_mu);
+      sv->pinned.release(q->pin, q->bytes);
+    }
+    return set_error(sv->fault, "server failed: " + sv->fault_msg);
   }
   q->t_submit = now_s() - sv->t0;
   q->ticket = sv->next_ticket++;
@@ -693,7 +716,10 @@ static burgers_status take_result(burgers_server* sv, Req* q, void* out_host,
   burgers_status st = q->status;
   if (q->state == RQ_DONE && out_host)
     memcpy(out_host, q->pin ? q->pin : q->out.data(), size_t(q->bytes));
-  if (q->pin) sv->pinned.release(q->pin, q->bytes);
+  if (q->pin) {
+    std::lock_guard<std::mutex> pk(sv->pin_mu);  // lock order: mu, then pin_mu
+    sv->pinned.release(q->pin, q->bytes);
+  }
   sv->reqs.erase(q->ticket);
   if (st != BURGERS_OK) return set_error(st, "request did not complete");
   return BURGERS_OK;

@@ -154,7 +154,7 @@ def test_autograd_function(ctx, scheme):
 
 
 @pytest.mark.parametrize("scheme", [EXPLICIT, BTCS])
-def test_config5_sampled(ctx, scheme):
+def test_differentiation_1024x2048_sampled(ctx, scheme):
     """B = 1024 periodic rows x 2048 nodes, FP32, 2000 explicit / 200 BTCS steps,
     target from seed + 1: sampled rows against the FP64 oracle gradient."""
     B, N = 1024, 2048

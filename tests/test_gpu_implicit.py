@@ -69,7 +69,7 @@ def _concat(parts):
 
 @pytest.mark.parametrize("scheme,iters,fac", CASES)
 @pytest.mark.parametrize("dtype", [F64, F32])
-def test_config1_plain_sine(ctx, scheme, iters, fac, dtype):
+def test_plain_sine_n256(ctx, scheme, iters, fac, dtype):
     """N = 256 Dirichlet, u0 = -sin(pi x), nu = 0.01/pi, t_f = 1/pi."""
     _fresh(ctx)
     e = W.plain_sine(256)
@@ -78,7 +78,7 @@ def test_config1_plain_sine(ctx, scheme, iters, fac, dtype):
     dts = np.array([e.meta["t_final"] / n])
     got = run_gpu(ctx, scheme, e, dts, n, dtype, iters=iters)
     ref = run_oracle(scheme, e, dts, n, iters=iters)
-    assert_parity(e, got, ref, dtype, f"cfg1 s{scheme}")
+    assert_parity(e, got, ref, dtype, f"plain sine s{scheme}")
     assert got[0] == 0.0 and got[-1] == 0.0
 
 

@@ -35,7 +35,7 @@ def _fresh(ctx):
 
 @pytest.mark.parametrize("scheme", SCHEMES)
 @pytest.mark.parametrize("dtype", [F64, F32])
-def test_config1_plain_sine(ctx, scheme, dtype):
+def test_plain_sine_n256(ctx, scheme, dtype):
     """N = 256 Dirichlet, u0 = -sin(pi x), nu = 0.01/pi, t_f = 1/pi, 102 steps."""
     _fresh(ctx)
     e = W.plain_sine(256)
@@ -45,7 +45,7 @@ def test_config1_plain_sine(ctx, scheme, dtype):
     assert n == 102
     got = run_gpu(ctx, scheme, e, dts, n, dtype)
     ref = run_oracle(scheme, e, dts, n)
-    assert_parity(e, got, ref, dtype, "cfg1")
+    assert_parity(e, got, ref, dtype, "plain sine")
     # the odd initial condition stays odd on the GPU too
     # (the partitioned solve is not mirror-symmetric in rounding: FP32 bar)
     assert np.max(np.abs(got + got[::-1])) <= (1e-13 if dtype == F64 else 1e-5)
@@ -169,7 +169,7 @@ def test_gaps_between_rows_untouched(ctx):
 
 
 @pytest.mark.parametrize("scheme", SCHEMES)
-def test_config2_full_size_sampled(ctx, scheme):
+def test_ensemble_4096x4096_sampled(ctx, scheme):
     """4096 periodic rows x 4096 nodes, FP32 and FP64, 2000 explicit steps at
     CFL 0.4 or 200 BTCS steps at 10x that dt: sampled rows against the oracle,
     and every FP32 row against the GPU FP64 result (the FP32 error per row)."""
@@ -442,7 +442,7 @@ def test_ctx_options_round_trip(ctx):
 
 
 @pytest.mark.parametrize("scheme", SCHEMES)
-def test_config2_bench_launch_configuration(ctx, scheme):
+def test_ensemble_4096x4096_bench_launch(ctx, scheme):
     """The step the bench times, as it times it: 4096 x 4096 FP32, launch
     shapes from the autotuner, the CFL time step on the device and the advance
     reading it there (burgers_cfl_dt_device + burgers_advance_dt_device).

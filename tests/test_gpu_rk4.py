@@ -47,7 +47,7 @@ def _concat(parts):
 
 
 @pytest.mark.parametrize("dtype", [F64, F32])
-def test_rk4_config1_plain_sine(ctx, dtype):
+def test_rk4_plain_sine_n256(ctx, dtype):
     """N = 256 Dirichlet, u0 = -sin(pi x), nu = 0.01/pi, t_f = 1/pi at the
     forward-Euler CFL step (102 steps)."""
     _fresh(ctx)
@@ -57,7 +57,7 @@ def test_rk4_config1_plain_sine(ctx, dtype):
     dts = np.array([e.meta["t_final"] / n])
     got = run_gpu(ctx, RK4, e, dts, n, dtype)
     ref = run_oracle(RK4, e, dts, n)
-    assert_parity(e, got, ref, dtype, "rk4 cfg1")
+    assert_parity(e, got, ref, dtype, "rk4 plain sine")
     assert got[0] == 0.0 and got[-1] == 0.0
 
 

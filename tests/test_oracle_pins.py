@@ -194,7 +194,7 @@ def test_explicit_beyond_cfl_oscillates(orc):
 @pytest.mark.parametrize("scheme", ["explicit", "btcs", "rk4"])
 def test_mirror_symmetry(orc, scheme):
     """u0(x) -> -u0(-x) maps solutions to mirrored solutions; the odd IC of
-    configuration 1 stays odd: u_i = -u_{N-1-i}."""
+    the plain sine case (u0 = -sin(pi x), Dirichlet) stays odd: u_i = -u_{N-1-i}."""
     e = W.plain_sine(101)
     dx, nu = e.dxs[0], e.nus[0]
     dt = 0.004
