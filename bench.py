@@ -857,8 +857,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tune-file", default=None,
                     help="launch-shape table: loaded if it exists, else written after tuning")
-    ap.add_argument("--serve-seconds", type=float, default=1.0,
-                    help="length of the Poisson trace of the serving measurement (0 = skip)")
+    ap.add_argument("--serve-seconds", type=float, default=10.0,
+                    help="length of the Poisson trace of the serving measurement (0 = skip); "
+                         "the serving workload is 10 s of arrivals at 20k requests/s")
     ap.add_argument("--serve-only", action="store_true",
                     help="run only the serving measurement and print its JSON")
     ap.add_argument("--serve-plain-seconds", type=float, default=5.0,
