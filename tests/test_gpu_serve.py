@@ -131,3 +131,45 @@ def test_serve_cancel_timeout_and_bad_requests(ctx):
     rc, out, _ = sv.wait(t2, 2048, timeout_s=60)
     assert rc == L.BURGERS_OK and np.array_equal(out, u0.astype(np.float32))
     assert sv.close() == 0
+
+
+def test_serve_concurrent_submitters(ctx):
+    """Four client threads submit and collect at once (the page-locked arena
+    is taken outside the server lock); every result matches the oracle and
+    the tickets are distinct."""
+    import threading
+
+    from paper_2601_12204_b300.api import Server
+    sv = Server(ctx, F32, hbm_budget=256 << 20, slice_steps=32)
+    reqs = _requests(96, seed=23, nmax=40000, smax=200)
+    parts = [reqs[i::4] for i in range(4)]
+    results, errors = [None] * 4, []
+
+    def client(k):
+        try:
+            mine = [(q, dt, sv.submit(q.scheme, q.bc, q.u0, q.dx, q.nu, dt, q.nsteps))
+                    for q, dt in parts[k]]
+            outs = []
+            for q, dt, t in mine:
+                rc, out, _ = sv.wait(t, q.n, timeout_s=120)
+                outs.append((q, dt, t, rc, out))
+            results[k] = outs
+        except Exception as e:  # noqa: BLE001
+            errors.append(repr(e))
+
+    try:
+        ths = [threading.Thread(target=client, args=(k,)) for k in range(4)]
+        for th in ths:
+            th.start()
+        for th in ths:
+            th.join(300)
+        assert not errors, errors
+        tickets = [t for r in results for (_, _, t, _, _) in r]
+        assert len(tickets) == len(reqs) == len(set(tickets))
+        for r in results:
+            for q, dt, _, rc, out in r:
+                assert rc == L.BURGERS_OK, L.last_error()
+                assert oracle.rel_l2(out.astype(np.float64), _oracle(q, dt)) <= 1e-5, \
+                    (q.scheme, q.bc, q.n, q.nsteps)
+    finally:
+        sv.close()
