@@ -398,7 +398,7 @@ def run_ours(args):
         res.update(extras(args, ctx, ens, u0, batches, probe, dev, world, rank))
         if args.serve_seconds > 0 and world == 1:
             log("serving ...")
-            res["serve"] = serve_bench(ctx, dev, args.serve_seconds)
+            res["serve"] = serve_bench(ctx, dev, args.serve_seconds, rate=args.serve_rate)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         log("cpu baseline ...")
         res["cpu_baseline"] = cpu_baseline_sample()
@@ -860,6 +860,8 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=10.0,
                     help="length of the Poisson trace of the serving measurement (0 = skip); "
                          "the serving workload is 10 s of arrivals at 20k requests/s")
+    ap.add_argument("--serve-rate", type=float, default=20000.0,
+                    help="Poisson arrival rate of the serving measurement (requests/s)")
     ap.add_argument("--serve-only", action="store_true",
                     help="run only the serving measurement and print its JSON")
     ap.add_argument("--serve-plain-seconds", type=float, default=5.0,
@@ -874,7 +876,7 @@ def main():
         dev = torch.device("cuda", 0)
         torch.cuda.set_device(dev)
         ctx = Context(0)
-        print(json.dumps({"serve": serve_bench(ctx, dev, max(args.serve_seconds, 0.1),
+        print(json.dumps({"serve": serve_bench(ctx, dev, max(args.serve_seconds, 0.1), rate=args.serve_rate,
                                                plain_seconds=args.serve_plain_seconds)}), flush=True)
         ctx.close()
     else:
