@@ -352,7 +352,10 @@ __launch_bounds__(NT, (sizeof(T) == 4 && NT <= 512) ? 512 / NT : 1)
   // is zeroed after the sweep.
   const bool dfirst = !per && rank == 0 && tid == 0;
   const bool dlast = !per && lastcta && tid == tl;
-  const bool plainchunk = __all_sync(FULL_MASK, je == C - 1 && jstar >= C - 1 && !dfirst && !dlast);
+  // (lanes past the row's end may take the branch-free path too: their
+  // values are never read)
+  const bool plainchunk =
+      __all_sync(FULL_MASK, ((je == C - 1 && jstar >= C - 1) || jstar < 0) && !dfirst && !dlast);
   const bool padwarp = __all_sync(FULL_MASK, jstar < 0);
   const bool endslot = jstar >= 0 && jstar < C - 1;  // chunk with padding after node n-1
   T ch[C], ah[C], dd[C];
@@ -423,10 +426,10 @@ __launch_bounds__(NT, (sizeof(T) == 4 && NT <= 512) ? 512 / NT : 1)
         if (dlast) { e_ch = T(0); e_ah = T(0); e_dh = T(0); }
       }
     };
-    if (plainchunk) {
-      sweep(std::true_type{});
-    } else if (padwarp) {  // all rows identity: what the general sweep leaves
+    if (padwarp) {  // all rows identity: what the general sweep leaves
       dd[0] = T(0); ah[0] = T(0); ch[0] = T(0);
+    } else if (plainchunk) {
+      sweep(std::true_type{});
     } else {
       sweep(std::false_type{});
     }
