@@ -235,10 +235,19 @@ __global__ void __launch_bounds__(NT) k_adjoint(const T* __restrict__ u0, const 
       if constexpr (SCHEME == 0) fwd_explicit_step<T, NT, C>(v, lo, n, base, per, r, h, s, sm.xa, p);
       else fwd_btcs_step<T, NT, C>(v, lo, n, base, per, r, s, sm.bt, sm.xa, p);
     }
-    // ---- reverse pass
-    T lam[C];
+    // ---- reverse pass. lambda advances in increment form, lambda' = lambda +
+    // dlam (explicit: the transposed stencil minus lambda; BTCS: mu - lambda
+    // from the increment form of the transposed solve, minus the coefficient
+    // term); FP32 keeps a split state, lambda = lam + lamd with lamd the
+    // increments since the last fold, folded every SPLIT_FOLD reverse steps.
+    constexpr bool SPLIT = Kahan<T>::on;
+    T lam[C], lamd[C];
 #pragma unroll
-    for (int j = 0; j < C; ++j) lam[j] = base + j < n ? gT[rd.offset + base + j] : T(0);
+    for (int j = 0; j < C; ++j) {
+      lam[j] = base + j < n ? gT[rd.offset + base + j] : T(0);
+      lamd[j] = T(0);
+    }
+    int64_t nrev = 0;
     double gacc = 0.0;
     const int64_t nseg = ns > 0 ? (ns + k - 1) / k : 0;
     for (int64_t sgi = nseg - 1; sgi >= 0; --sgi) {
@@ -283,48 +292,57 @@ __global__ void __launch_bounds__(NT) k_adjoint(const T* __restrict__ u0, const 
           for (int j = 0; j < C; ++j) vn[j] = base + j < n ? us[j * NT + tid] : T(0);
         }
         T part = T(0);
+        T w[C];  // lambda of this step
+#pragma unroll
+        for (int j = 0; j < C; ++j) w[j] = SPLIT ? lam[j] + lamd[j] : lam[j];
         if constexpr (SCHEME == 0) {
           // transposed explicit step
           xch_publish<T, NT, C>(v, jstar, sm.xa, p);
-          xch_publish<T, NT, C>(lam, jstar, sm.xb, p);
+          xch_publish<T, NT, C>(w, jstar, sm.xb, p);
           __syncthreads();
           T ul0, ur0, uw, ll0, lr0, lw;
           xch_read<T, NT>(sm.xa, p, ul0, ur0, uw);
           xch_read<T, NT>(sm.xb, p, ll0, lr0, lw);
           p ^= 1;
-          T nl[C];
 #pragma unroll
           for (int j = 0; j < C; ++j) {
             const int gi = base + j;
             T ul, ur, ll, lr;
             nbrs<T, C>(v, j, jstar, ul0, ur0, uw, ul, ur);
-            nbrs<T, C>(lam, j, jstar, ll0, lr0, lw, ll, lr);
+            nbrs<T, C>(w, j, jstar, ll0, lr0, lw, ll, lr);
             const T u = v[j];
             const bool upI = per || (gi > 0 && gi < n - 1);
             const bool upR = per || (gi + 1 < n - 1);
             const bool upL = per || (gi - 1 > 0);
             const T dl = u - ul, dr = ur - u;
-            const T dii = upI ? T(1) - T(2) * s - r * ((u > T(0) ? dl : dr) + tabs(u)) : T(1);
-            T acc = dii * lam[j];
-            if (upR) acc = tfma(tfma(r, tmax(ur, T(0)), s), lr, acc);
-            if (upL) acc = tfma(tfma(-r, tmin(ul, T(0)), s), ll, acc);
-            if (upI) part = tfma(lam[j], dr - dl, part);
-            nl[j] = gi < n ? acc : T(0);
+            // 1 - diagonal of the step's Jacobian
+            const T cI = upI ? tfma(r, (u > T(0) ? dl : dr) + tabs(u), T(2) * s) : T(0);
+            T inc = -cI * w[j];
+            if (upR) inc = tfma(tfma(r, tmax(ur, T(0)), s), lr, inc);
+            if (upL) inc = tfma(tfma(-r, tmin(ul, T(0)), s), ll, inc);
+            if (upI) part = tfma(w[j], dr - dl, part);
+            if (gi >= n) inc = T(0);
+            if constexpr (SPLIT) lamd[j] += inc;
+            else lam[j] = w[j] + inc;
           }
-#pragma unroll
-          for (int j = 0; j < C; ++j) lam[j] = nl[j];
         } else {
-          // transposed BTCS step: mu = A(u^s)^{-T} lam, then the coefficient term
+          // transposed BTCS step in increment form: with mu = lam + nu,
+          // A^T nu = lam - A^T lam, whose right-hand side is minus the
+          // off-identity part of the transposed rows applied to lam; then
+          // lam' = mu - mu drow = lam + (nu - mu drow)
           xch_publish<T, NT, C>(v, jstar, sm.xa, p);
+          xch_publish<T, NT, C>(w, jstar, sm.xb, p);
           __syncthreads();
-          T ul0, ur0, uw;
+          T ul0, ur0, uw, ll0, lr0, lw;
           xch_read<T, NT>(sm.xa, p, ul0, ur0, uw);
+          xch_read<T, NT>(sm.xb, p, ll0, lr0, lw);
           p ^= 1;
-          T mu[C], ah[C], ch[C];
+          T nu[C], ah[C], ch[C];
           auto trows = [&](int j, T& l, T& d, T& c, T& rhs) {
             const int gi = base + j;
-            T ul, ur;
+            T ul, ur, ll, lr;
             nbrs<T, C>(v, j, jstar, ul0, ur0, uw, ul, ur);
+            nbrs<T, C>(w, j, jstar, ll0, lr0, lw, ll, lr);
             T l0, d0, c0, lm, dm, cm, lp, dp, cp;
             btcs_coef(v[j], r, s, l0, d0, c0);
             btcs_coef(ul, r, s, lm, dm, cm);
@@ -335,9 +353,10 @@ __global__ void __launch_bounds__(NT) k_adjoint(const T* __restrict__ u0, const 
             l = (bL || (!per && gi == 0)) ? T(0) : cm;   // sub-diagonal: c_{i-1}
             c = (bR || (!per && gi == n - 1)) ? T(0) : lp;  // super-diagonal: l_{i+1}
             d = bI ? T(1) : d0;
-            rhs = lam[j];
+            const T dm1 = bI ? T(0) : tfma(r, tabs(v[j]), T(2) * s);  // d - 1
+            rhs = -tfma(l, ll, tfma(c, lr, dm1 * w[j]));
           };
-          resident_solve<T, NT, C>(mu, ah, ch, trows, n, per, sm.bt);
+          resident_solve<T, NT, C>(nu, ah, ch, trows, n, per, sm.bt);
           T (&xv)[C] = vx;  // x = u^{s+1}
           xch_publish<T, NT, C>(xv, jstar, sm.xb, p);
           __syncthreads();
@@ -352,20 +371,33 @@ __global__ void __launch_bounds__(NT) k_adjoint(const T* __restrict__ u0, const 
             const bool bI = !per && (gi == 0 || gi == n - 1);
             const T H = v[j] > T(0) ? T(1) : T(0);
             const T drow = r * (-H * xl + (T(2) * H - T(1)) * xv[j] + (T(1) - H) * xr);
-            T out = bI ? mu[j] : mu[j] - mu[j] * drow;
-            if (!bI && gi < n) part = tfma(mu[j], xr - T(2) * xv[j] + xl, part);
-            lam[j] = gi < n ? out : T(0);
+            const T mu = w[j] + nu[j];
+            T inc = bI ? nu[j] : tfma(-mu, drow, nu[j]);
+            if (!bI && gi < n) part = tfma(mu, xr - T(2) * xv[j] + xl, part);
+            if (gi >= n) inc = T(0);
+            if constexpr (SPLIT) lamd[j] += inc;
+            else lam[j] = w[j] + inc;
           }
 #pragma unroll
           for (int j = 0; j < C; ++j) vx[j] = v[j];  // u^s is the next step's u^{s+1}
         }
         gacc += double(part);
+        if constexpr (SPLIT) {
+          if (++nrev % SPLIT_FOLD == 0) {
+#pragma unroll
+            for (int j = 0; j < C; ++j) {
+              const T t = lam[j] + lamd[j];
+              lamd[j] = lamd[j] - (t - lam[j]);
+              lam[j] = t;
+            }
+          }
+        }
       }
     }
     // ---- outputs
 #pragma unroll
     for (int j = 0; j < C; ++j)
-      if (base + j < n) gu0[rd.offset + base + j] = lam[j];
+      if (base + j < n) gu0[rd.offset + base + j] = SPLIT ? lam[j] + lamd[j] : lam[j];
     // block reduction of the nu gradient (FP64)
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) gacc += __shfl_xor_sync(FULL_MASK, gacc, o);
@@ -500,11 +532,22 @@ __device__ __forceinline__ void adj_explicit_exact_row(const T* __restrict__ u0,
     if (st + 1 == ns) break;  // the last state is not needed
     adj_fwd_step<T, NT, C, BCT>(v, d, st, p, r, h, s, sh);
   }
-  // ---- reverse pass
-  T lam[C];
+  // ---- reverse pass. lambda advances in increment form, lambda' = lambda +
+  // dlam with dlam = -(2s + r(H dl + (1-H) dr + |u|)) lambda + (s + r u_{i+1}^+)
+  // lambda_{i+1} + (s - r u_{i-1}^-) lambda_{i-1}; FP32 keeps it as a split
+  // state (lh, the value at the last fold, plus ld, the increments summed
+  // since), evaluates the transposed stencil on lh + ld and folds ld into lh
+  // every SPLIT_FOLD reverse steps, so the rounding of lambda + dlam is not
+  // accumulated over the steps (plain FP32 accumulation drifts by ~6e-5 of
+  // the gradient over 2000 steps).
+  T lam[C], lamd[C];
 #pragma unroll
-  for (int j = 0; j < C; ++j) lam[j] = gT[rd.offset + base + j];
+  for (int j = 0; j < C; ++j) {
+    lam[j] = gT[rd.offset + base + j];
+    lamd[j] = T(0);
+  }
   double gacc = 0.0;
+  int64_t nrev = 0;  // reverse steps taken (fold schedule)
   const int64_t nseg = ns > 0 ? (ns + k - 1) / k : 0;
   for (int64_t sgi = nseg - 1; sgi >= 0; --sgi) {
     const int64_t s0 = sgi * k;
@@ -541,16 +584,18 @@ __device__ __forceinline__ void adj_explicit_exact_row(const T* __restrict__ u0,
 #pragma unroll
         for (int j = 0; j < C; ++j) vn[j] = us[j * NT + tid];
       }
-      T fl[2] = {v[0], lam[0]}, la[2] = {v[C - 1], lam[C - 1]}, L[2], R[2];
+      T w[C];  // lambda of this step
+#pragma unroll
+      for (int j = 0; j < C; ++j) w[j] = SPLIT ? lam[j] + lamd[j] : lam[j];
+      T fl[2] = {v[0], w[0]}, la[2] = {v[C - 1], w[C - 1]}, L[2], R[2];
       adj_xch<T, NT, 2>(fl, la, p, sh, L, R);
       p ^= 1;
       T ul = L[0], ll = L[1], part = T(0);
-      T nl[C];
 #pragma unroll
       for (int j = 0; j < C; ++j) {
         const T u = v[j];
         const T ur = (j + 1 < C) ? v[j + 1] : R[0];
-        const T lr = (j + 1 < C) ? lam[j + 1] : R[1];
+        const T lr = (j + 1 < C) ? w[j + 1] : R[1];
         bool upI = true, upR = true, upL = true;  // node, right, left neighbour updated
         if constexpr (BCT == BC_DIRICHLET) {
           const int gi = base + j;  // the row has CAP nodes; 0 and CAP - 1 are held
@@ -559,23 +604,33 @@ __device__ __forceinline__ void adj_explicit_exact_row(const T* __restrict__ u0,
           upL = gi - 1 > 0;
         }
         const T dl = u - ul, dr = ur - u;
-        const T dii = upI ? T(1) - T(2) * s - r * ((u > T(0) ? dl : dr) + tabs(u)) : T(1);
-        T acc = dii * lam[j];
-        if (upR) acc = tfma(tfma(r, tmax(ur, T(0)), s), lr, acc);
-        if (upL) acc = tfma(tfma(-r, tmin(ul, T(0)), s), ll, acc);
-        if (upI) part = tfma(lam[j], dr - dl, part);
-        nl[j] = acc;
+        // 1 - diagonal of the step's Jacobian
+        const T cI = upI ? tfma(r, (u > T(0) ? dl : dr) + tabs(u), T(2) * s) : T(0);
+        T inc = -cI * w[j];
+        if (upR) inc = tfma(tfma(r, tmax(ur, T(0)), s), lr, inc);
+        if (upL) inc = tfma(tfma(-r, tmin(ul, T(0)), s), ll, inc);
+        if (upI) part = tfma(w[j], dr - dl, part);
+        if constexpr (SPLIT) lamd[j] += inc;
+        else lam[j] = w[j] + inc;
         ul = u;
-        ll = lam[j];
+        ll = w[j];
       }
-#pragma unroll
-      for (int j = 0; j < C; ++j) lam[j] = nl[j];
       gacc += double(part);
+      if constexpr (SPLIT) {
+        if (++nrev % SPLIT_FOLD == 0) {
+#pragma unroll
+          for (int j = 0; j < C; ++j) {
+            const T t = lam[j] + lamd[j];
+            lamd[j] = lamd[j] - (t - lam[j]);
+            lam[j] = t;
+          }
+        }
+      }
     }
   }
   // ---- outputs
 #pragma unroll
-  for (int j = 0; j < C; ++j) gu0[rd.offset + base + j] = lam[j];
+  for (int j = 0; j < C; ++j) gu0[rd.offset + base + j] = SPLIT ? lam[j] + lamd[j] : lam[j];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) gacc += __shfl_xor_sync(FULL_MASK, gacc, o);
   if ((tid & 31) == 0) sh.red[tid >> 5] = gacc;

@@ -153,36 +153,98 @@ def test_autograd_function(ctx, scheme):
     _check(ens, u0.grad.cpu().numpy(), ref, nu.grad.cpu().numpy(), gnu_ref, F64, "autograd")
 
 
-@pytest.mark.parametrize("scheme", [EXPLICIT, BTCS])
-def test_differentiation_1024x2048_sampled(ctx, scheme):
-    """B = 1024 periodic rows x 2048 nodes, FP32, 2000 explicit / 200 BTCS steps,
-    target from seed + 1: sampled rows against the FP64 oracle gradient."""
+# Differentiation workload, FP32 against FP64 on every row. The discrete
+# gradient is that of a piecewise smooth map (the upwind side switches with
+# sign(u_i)), steep near forming shocks. Per row (fp32_gradient_bar): 1e-4,
+# plus 4 x (the FP64 gradient's change per unit trajectory deviation when u0
+# is rounded to FP32) x (the FP32 trajectory's deviation from the FP64 one);
+# 1e-2 for a row whose FP32 trajectory takes another upwind side than the
+# FP64 one at some (node, step): its gradient is that of another branch (one
+# flipped decision moved a row's gradient by 3.5e-3). Rows above 1e-4 (the
+# ones that need their wider bar) must stay rare.
+WIDE_ROWS_MAX = 0.02
+
+
+def _differentiation_problem(scheme):
     B, N = 1024, 2048
     ens = W.fourier_ensemble(B, N, seed=W.DEFAULT_SEED)
     tgt = W.fourier_ensemble(B, N, seed=W.DEFAULT_SEED + 1)
     steps = 2000 if scheme == EXPLICIT else 200
+    fac = 1.0 if scheme == EXPLICIT else 10.0
     # one dt per row stable for both runs: the target's u0 (seed + 1) can be
     # larger, and a dt set by the CFL limit of u0 alone can make it diverge
-    dts = np.minimum(oracle_dts(ens, 1.0 if scheme == EXPLICIT else 10.0),
+    dts = np.minimum(oracle_dts(ens, fac),
                      oracle_dts(W.Ensemble(tgt.u0, ens.offsets, ens.ns, ens.bcs, ens.dxs, ens.nus,
-                                           ens.x0, ens.length), 1.0 if scheme == EXPLICIT else 10.0))
-    # gT: the misfit gradient u(T) - target on the sampled rows (oracle forward
-    # solves from seed and seed + 1); any seeded field on the other rows (rows are
-    # independent, so it does not affect the sampled ones)
+                                           ens.x0, ens.length), fac))
+    return ens, tgt, dts, steps
+
+
+def _pipeline_grads(ctx, scheme, ens, tgt, dts, steps, dtype, round_u0=False):
+    """J = 1/2 |u(T) - target|^2 in one precision: forward of u0 and of the
+    target's u0 (seed + 1, same nu, dt, steps), gT = u(T) - target, adjoint.
+    round_u0: start from u0 rounded to FP32 (in either precision)."""
+    import torch
+
+    from paper_2601_12204_b300.api import Batch
+    tdt = torch.float32 if dtype == F32 else torch.float64
+    b = Batch.from_ensemble(ens, dts, steps, dtype)
+    u0 = torch.tensor(ens.u0, dtype=torch.float64, device="cuda")
+    if round_u0:
+        u0 = u0.float()
+    u0 = u0.to(tdt).contiguous()
+    ut = torch.tensor(tgt.u0, dtype=tdt, device="cuda")
+    uT = u0.clone()
+    ctx.advance(scheme, b, uT)
+    ctx.advance(scheme, b, ut)
+    gu0 = torch.zeros_like(u0)
+    gnu = torch.zeros(ens.count, dtype=torch.float64, device="cuda")
+    ctx.adjoint(scheme, b, u0, uT - ut, gu0, gnu)
+    torch.cuda.synchronize()
+    return gu0.double(), gnu
+
+
+@pytest.mark.parametrize("scheme", [EXPLICIT, BTCS])
+def test_differentiation_1024x2048_all_rows(ctx, scheme):
+    """B = 1024 periodic rows x 2048 nodes, 2000 explicit / 200 BTCS steps,
+    target from seed + 1. Every row: the FP32 gradient against the GPU FP64
+    gradient within the row's bar (1e-4 on well-conditioned rows, see above).
+    Sampled rows: the GPU FP64 gradient against the FP64 oracle at 1e-11, the
+    FP32 one at the row's bar."""
+    import torch
+
+    from paper_2601_12204_b300.api import Batch
+    from paper_2601_12204_b300.diagnostics import fp32_gradient_bar, trajectory_stats
+    ens, tgt, dts, steps = _differentiation_problem(scheme)
+    N = int(ens.ns[0])
+    g64, n64 = _pipeline_grads(ctx, scheme, ens, tgt, dts, steps, F64)
+    g64r, _ = _pipeline_grads(ctx, scheme, ens, tgt, dts, steps, F64, round_u0=True)
+    g32, n32 = _pipeline_grads(ctx, scheme, ens, tgt, dts, steps, F32)
+    G64, G32 = g64.view(ens.count, N), g32.view(ens.count, N)
+    assert bool(torch.isfinite(G32).all()) and bool(torch.isfinite(n32).all())
+    rel = ((G32 - G64).norm(dim=1) / G64.norm(dim=1)).cpu().numpy()
+    stats = trajectory_stats(ctx, scheme, Batch.from_ensemble(ens, dts, steps, F64),
+                             torch.tensor(ens.u0, dtype=torch.float64, device="cuda"), steps)
+    a64, a32 = G64.cpu().numpy(), G32.cpu().numpy()
+    bar = fp32_gradient_bar(a64, g64r.view(ens.count, N).cpu().numpy(), stats)
+    bad = np.nonzero(rel > bar)[0]
+    assert bad.size == 0, [(int(b), float(rel[b]), float(bar[b]), int(stats["flips"][b]))
+                           for b in bad[:10]]
+    assert np.mean(rel > 1e-4) <= WIDE_ROWS_MAX, f"{int(np.sum(rel > 1e-4))} rows above 1e-4"
+    free = stats["flips"] == 0
+    nd = (n32 - n64).abs().cpu().numpy()
+    na = n64.abs().cpu().numpy()
+    assert np.all(nd[free] <= 10 * bar[free] * na[free] + 1e-6 * na.max())
+    # sampled rows against the oracle (both precisions of the GPU gradient)
     ids = np.array([0, 511, 1023])
     sub, subt = ens.subset(ids), tgt.subset(ids)
     subt.nus = sub.nus.copy()  # target: same scheme, nu, dt and steps, u0 from seed + 1
     g_sub = run_oracle(scheme, sub, dts[ids], steps) - run_oracle(scheme, subt, dts[ids], steps)
-    gT = W.rng(99, 0).normal(0.0, 0.1, ens.u0.size)
-    for j, b in enumerate(ids):
-        gT[ens.offsets[b]:ens.offsets[b] + N] = g_sub[j * N:(j + 1) * N]
-    got, gnu = _gpu_grads(ctx, scheme, ens, dts, steps, gT, F32)
     ref, gnu_ref = _oracle_grads(scheme, sub, dts[ids], steps, g_sub)
     for j, b in enumerate(ids):
-        o = ens.offsets[b]
-        rel = oracle.rel_l2(got[o:o + N], ref[j * N:(j + 1) * N])
-        assert rel <= 1e-4, f"row {b}: {rel}"
-        assert abs(gnu[b] - gnu_ref[j]) <= 1e-3 * abs(gnu_ref[j]) + 1e-6 * np.max(np.abs(gnu_ref))
+        r = ref[j * N:(j + 1) * N]
+        assert oracle.rel_l2(a64[b], r) <= 1e-11, f"row {b} FP64"
+        assert abs(float(n64[b]) - gnu_ref[j]) <= 1e-10 * abs(gnu_ref[j]) + 1e-13 * np.max(np.abs(gnu_ref))
+        assert oracle.rel_l2(a32[b], r) <= bar[b], f"row {b} FP32"
 
 
 @pytest.mark.parametrize("dtype", [F64, F32])
