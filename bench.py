@@ -424,6 +424,7 @@ def differentiation_bench(ctx, dev):
     from paper_2601_12204_b300 import _lib as L
     from paper_2601_12204_b300 import workloads as W
     from paper_2601_12204_b300.api import Batch
+    from paper_2601_12204_b300.diagnostics import fp32_gradient_bar, trajectory_stats
     F32, F64 = L.BURGERS_F32, L.BURGERS_F64
     rows, n = 1024, 2048
     ens = W.fourier_ensemble(rows, n)
@@ -486,10 +487,95 @@ def differentiation_bench(ctx, dev):
         rec["grad_u0_fp32_vs_fp64_rel_l2"] = {"max": float(np.max(rel[ok])), "median": float(np.median(rel[ok])),
                                               "rows": int(np.sum(ok))}
         rec["grad_nu_fp32_vs_fp64_max_rel"] = float(np.max(dnu[ok]))
+        # per-row bar: 1e-4, widened by the row's conditioning (the FP64 gradient's
+        # change per unit trajectory deviation when u0 is rounded to FP32, times
+        # the FP32 trajectory's deviation), 1e-2 where the FP32 trajectory takes
+        # another upwind side than the FP64 one somewhere (another branch of the
+        # piecewise smooth solution map)
+        ur = u64.float().double()
+        ut64 = torch.tensor(tgt.u0, dtype=torch.float64, device=dev)
+        uT = ur.clone()
+        ctx.advance(scheme, gb, uT)
+        ctx.advance(scheme, gb, ut64)
+        g64r = torch.empty_like(ur)
+        ctx.adjoint(scheme, gb, ur, uT - ut64, g64r, torch.empty(rows, dtype=torch.float64, device=dev))
+        stats = trajectory_stats(ctx, scheme, gb, u64, steps)
+        bar = fp32_gradient_bar(g64.view(rows, n).cpu().numpy(), g64r.view(rows, n).cpu().numpy(), stats)
+        del ur, ut64, uT, g64r
+        flips = stats["flips"]
+        above = ok & (rel > 1e-4)
+        rec["grad_u0_fp32_vs_fp64_per_row_bar"] = {
+            "rows_within_bar": int(np.sum(ok & (rel <= bar))), "rows": int(np.sum(ok)),
+            "rows_above_1e-4": [{"row": int(b), "rel": float(rel[b]), "bar": float(bar[b]),
+                                 "flips": int(flips[b])} for b in np.nonzero(above)[0]],
+            "bar_max": float(np.max(bar[ok])), "bar_median": float(np.median(bar[ok])),
+            "flip_free_rows": {"rows": int(np.sum(ok & (flips == 0))),
+                               "max": float(np.max(rel[ok & (flips == 0)])),
+                               "median": float(np.median(rel[ok & (flips == 0)]))},
+            "note": ("bar = 1e-4 + 4 kappa dev32 (kappa: FP64 gradient change per unit trajectory "
+                     "deviation under u0 -> fp32(u0); dev32: max |u32 - u64| over nodes and steps); "
+                     "1e-2 where [u > 0] differs between the exact FP32 and FP64 trajectories "
+                     "(flips)")}
         out[name] = rec
     out["note"] = ("gradient_cups = forward cell-updates of the problem per second of the adjoint call "
                    "(checkpoint recompute + reverse sweep); checkpoint workspace per row = ceil(steps/k) "
                    "checkpoints (FP32: state + compensation) + k + 1 segment states, k = ceil(sqrt(steps))")
+    return out
+
+
+def step_ic_bench(ctx, dev, rows: int = 4096, n: int = 4096, sample: int = 8):
+    """Step-IC shock workload (Eq. 20, Sec. 3.4): `rows` Dirichlet rows of n
+    nodes on [0, 1] from u0 = 1 left of x = 1/2 and 0 right of it (u(0) = 1,
+    u(1) = 0 held), nu log-uniform in [1e-5, 1e-3]; 2000 explicit steps at
+    the CFL-0.4 step and 200 BTCS steps at dt = 5 dx / u_max (u_max = 1).
+    FP32 throughput, FP32 against the FP64 GPU path on every row, and both
+    precisions against the FP64 oracle on `sample` rows."""
+    import torch
+
+    import oracle
+    from paper_2601_12204_b300 import _lib as L
+    from paper_2601_12204_b300 import workloads as W
+    from paper_2601_12204_b300.api import Batch
+    F32, F64 = L.BURGERS_F32, L.BURGERS_F64
+    ens = W.step_ensemble(rows, n)
+    stream = torch.cuda.current_stream(dev)
+    u32 = torch.tensor(ens.u0, dtype=torch.float32, device=dev)
+    u64 = torch.tensor(ens.u0, dtype=torch.float64, device=dev)
+    dte = ctx.cfl_dt(Batch.from_ensemble(ens, 1.0, 0, F64), u64, CFL)
+    ids = np.linspace(0, rows - 1, sample).astype(np.int64)
+    sub = ens.subset(ids)
+    out = {"rows": rows, "n": n, "bc": "Dirichlet u(0)=1, u(1)=0", "nu": "log-U[1e-5,1e-3]"}
+    for name, scheme, steps, dts in (("explicit", L.BURGERS_EXPLICIT, EXPLICIT_STEPS, dte),
+                                     ("btcs", L.BURGERS_BTCS, BTCS_STEPS, 5.0 * ens.dxs / 1.0)):
+        b32 = Batch.from_ensemble(ens, dts, steps, F32)
+        b64 = b32.with_fields(dtype=F64)
+        w = u32.clone()
+        ctx.advance(scheme, b32, w)  # warm
+        w.copy_(u32)
+        a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        ctx.advance(scheme, b32, w)
+        z.record(stream)
+        w64 = u64.clone()
+        ctx.advance(scheme, b64, w64)
+        torch.cuda.synchronize()
+        t = a.elapsed_time(z) / 1000.0
+        rel, _ = ctx.rel_l2(b32, w, w64)
+        f = oracle.explicit_batch if scheme == L.BURGERS_EXPLICIT else oracle.btcs_batch
+        ref = f(sub.u0, sub.offsets, sub.ns, sub.bcs, sub.dxs, sub.nus, dts[ids],
+                np.full(sub.count, steps))
+        g32 = w.view(rows, n)[torch.from_numpy(ids).to(dev)].double().cpu().numpy()
+        g64 = w64.view(rows, n)[torch.from_numpy(ids).to(dev)].cpu().numpy()
+        r = ref.reshape(sample, n)
+        o32 = [oracle.rel_l2(g32[j], r[j]) for j in range(sample)]
+        o64 = [oracle.rel_l2(g64[j], r[j]) for j in range(sample)]
+        out[name] = {"steps": steps, "cups": rows * n * steps / t,
+                     "dt": "CFL 0.4" if scheme == L.BURGERS_EXPLICIT else "5 dx / u_max",
+                     "l2_fp32_vs_fp64": {"max": float(np.max(rel)), "median": float(np.median(rel))},
+                     "l2_vs_oracle_sampled": {"rows": ids.tolist(), "fp32_max": float(max(o32)),
+                                              "fp64_max": float(max(o64))},
+                     "range": [float(w.min()), float(w.max())]}
+        del w, w64
     return out
 
 
@@ -616,6 +702,7 @@ def extras(args, ctx, ens, u0, batches, probe, dev, world, rank):
                         "CFL dt on viscosity-raised rows (cell Peclet <= 1.5)")
     out["implicit_variants"] = variants
     out["differentiation"] = differentiation_bench(ctx, dev)
+    out["step_ic"] = step_ic_bench(ctx, dev)
 
     # ---- plain one-row-per-launch path on a subset, same kernels
     P = 64

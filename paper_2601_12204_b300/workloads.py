@@ -157,6 +157,21 @@ def step_ic(n: int, bc: int = DIRICHLET, length: float = 1.0) -> Ensemble:
                     np.array([dx]), np.array([0.0]), np.zeros(1), np.array([length]), {"x": x})
 
 
+def step_ensemble(count: int, n: int, bc: int = DIRICHLET, seed: int = DEFAULT_SEED,
+                  length: float = 1.0) -> Ensemble:
+    """The step-IC shock workload (Eq. 20, Sec. 3.4): every row starts from
+    u0 = 1 for x < L/2, 0 otherwise, on [0, L]; nu log-uniform in [1e-5, 1e-3]
+    from stream b (cell Peclet numbers u dx / nu from about 0.2 to 24 at
+    n = 4096 on [0, 1], from resolved to under-resolved fronts)."""
+    x, dx = grid(n, bc, 0.0, length)
+    row = np.where(x < 0.5 * length, 1.0, 0.0)
+    nus = np.array([math.exp(rng(seed, b).uniform(math.log(1e-5), math.log(1e-3)))
+                    for b in range(count)])
+    return Ensemble(np.tile(row, count), np.arange(count, dtype=np.int64) * n,
+                    np.full(count, n, np.int32), np.full(count, bc, np.int32),
+                    np.full(count, dx), nus, np.zeros(count), np.full(count, length), {"seed": seed})
+
+
 def mixed_ensemble(count: int, nmin: int, nmax: int, seed: int = DEFAULT_SEED,
                    bc_mix: bool = True) -> Ensemble:
     """Ragged batch: n log-uniform in [nmin, nmax], periodic/Dirichlet mixed,
