@@ -237,9 +237,10 @@ burgers_status burgers_newton_advance(burgers_ctx* ctx, const burgers_batch* bat
  * device array that every GPU loading this library holds until exit; the
  * caller passes the row. `inst` describes the row (its offset is applied to
  * u_dev); `dtype` is BURGERS_F32 or BURGERS_F64. Limits: 128 <= n <= 1048576
- * (EINVAL beyond, u untouched). The first call on a device looks up the
- * array's device address with that device current; make that first call
- * before any stream capture. Every call shares the array and leaves its
+ * (EINVAL beyond, u untouched). Every call looks up the array's device
+ * address on the current device; the first call on a device loads the
+ * library's module there, so make it before any stream capture. Every call
+ * shares the array and leaves its
  * contents behind (each call clears what must start at zero), so calls whose
  * work overlaps on the GPU race and must be serialised by the caller.
  * Asynchronous on `stream`; calls no cudaMalloc or cudaFree. */

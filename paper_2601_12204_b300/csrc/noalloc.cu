@@ -18,7 +18,6 @@
 #include <stdint.h>
 
 #include <algorithm>
-#include <mutex>
 
 #include "../../include/burgers.h"
 #include "api_internal.h"
@@ -35,9 +34,6 @@ constexpr size_t NA_DATA = 8192;        // row copy, then the two compensation b
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
 
-static std::mutex g_noalloc_mu;
-static void* g_noalloc_addr[256] = {};  // device address of the array, per device
-
 // Writes the row descriptor and the tile list of one row into the array.
 __global__ void k_noalloc_setup(RowDesc rd, RowDesc* desc, TileItem* items, int ntiles) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -45,18 +41,17 @@ __global__ void k_noalloc_setup(RowDesc rd, RowDesc* desc, TileItem* items, int 
   for (int t = i; t < ntiles; t += gridDim.x * blockDim.x) items[t] = TileItem{0, t};
 }
 
-// Device address of the static array on the current device (set up on the
-// first call per device).
-static burgers_status noalloc_base(int dev, char** out) {
-  if (dev < 0 || dev >= 256) return set_error(BURGERS_EINVAL, "device index out of range");
-  std::lock_guard<std::mutex> lk(g_noalloc_mu);
-  if (!g_noalloc_addr[dev]) {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess) return cuda_error(e, "cudaGetSymbolAddress(no-alloc scratch)");
-    g_noalloc_addr[dev] = p;
-  }
-  *out = static_cast<char*>(g_noalloc_addr[dev]);
+// Device address of the static array on the current device. Looked up on
+// every call (a table lookup once the module is loaded, and no allocation), so
+// a context recreated after cudaDeviceReset, whose module and array may sit
+// elsewhere, is never handed a stale address. The first call on a device
+// loads the library's module there, which is why it must not happen inside a
+// stream capture.
+static burgers_status noalloc_base(char** out) {
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess) return cuda_error(e, "cudaGetSymbolAddress(no-alloc scratch)");
+  *out = static_cast<char*>(p);
   return BURGERS_OK;
 }
 
@@ -83,10 +78,15 @@ extern "C" burgers_status burgers_explicit_advance_noalloc(const burgers_instanc
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_error(e, "cudaGetDevice");
   char* base = nullptr;
-  burgers_status st = noalloc_base(dev, &base);
+  burgers_status st = noalloc_base(&base);
   if (st != BURGERS_OK) return st;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  // window shape and steps per pass as the streaming path picks them by default
+  // window shape: 256 threads of 16 (FP32) or 8 (FP64) nodes for rows of 4096
+  // nodes or more, 32 threads of 4 nodes below; K steps per pass (32 FP32, 16
+  // FP64, at most a quarter of the window). The streaming path of
+  // burgers_explicit_advance picks its shape from its tuning table instead, and
+  // sends rows that fit one CTA to the resident kernel; results agree within
+  // the FP32 / FP64 parity bars, not bitwise.
   const int nt = in.n >= 4096 ? 256 : 32;
   const int c = in.n >= 4096 ? (dtype == BURGERS_F32 ? 16 : 8) : 4;
   const int W = nt * c;
@@ -117,6 +117,10 @@ extern "C" burgers_status burgers_explicit_advance_noalloc(const burgers_instanc
   e = cudaGetLastError();
   if (e == cudaSuccess && lo_a) e = cudaMemsetAsync(lo_a, 0, size_t(in.n) * esz, s);
   if (e != cudaSuccess) return cuda_error(e, "no-alloc set-up");
+  if (k->dyn_smem > 0) {  // no context may have prepared the kernel on this device
+    e = cudaFuncSetAttribute(k->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(k->dyn_smem));
+    if (e != cudaSuccess) return cuda_error(e, "no-alloc kernel attribute");
+  }
   int sms = 1, occ = 1;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k->fn, k->nt, k->dyn_smem) != cudaSuccess ||
