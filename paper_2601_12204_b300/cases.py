@@ -38,6 +38,9 @@ def main():
     ap.add_argument("--autotune", action="store_true", help="tune launch shapes first and print the table")
     ap.add_argument("--tune-file", default=None,
                     help="launch-shape table: loaded if it exists, else written after --autotune")
+    ap.add_argument("--shape", default=None,
+                    help="NTxC: force the resident kernel shape of rows of exactly NT*C nodes "
+                         "(a one-entry tuning table), so a profile names its shape on the command line")
     a = ap.parse_args()
 
     import torch
@@ -64,7 +67,17 @@ def main():
     scheme = {"explicit": L.BURGERS_EXPLICIT, "btcs": L.BURGERS_BTCS, "rk4": L.BURGERS_RK4,
               "adjoint-explicit": L.BURGERS_EXPLICIT, "adjoint-btcs": L.BURGERS_BTCS}[a.case]
     adjoint = a.case.startswith("adjoint")
-    if a.tune_file and os.path.exists(a.tune_file):
+    if a.shape:
+        nt, c = (int(v) for v in a.shape.lower().split("x"))
+        if nt * c != a.n:
+            raise SystemExit("--shape needs rows of exactly NT*C nodes")
+        kind = {L.BURGERS_EXPLICIT: 0, L.BURGERS_BTCS: 2, L.BURGERS_RK4: 9}[scheme]
+        key = (kind << 56) ^ (dt_code << 52) ^ (1 << 48) ^ a.n
+        path = os.path.join(tempfile.mkdtemp(), "shape.txt")
+        with open(path, "w") as f:
+            f.write(f"# forced shape\n{key} {nt} {c} 0\n")
+        ctx.tune_load(path)
+    elif a.tune_file and os.path.exists(a.tune_file):
         ctx.tune_load(a.tune_file)
     elif a.autotune:
         ntuned = ctx.autotune(scheme, b, u0, probe_steps=min(a.steps, 100))

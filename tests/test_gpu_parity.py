@@ -383,6 +383,10 @@ def test_cluster_btcs(ctx, dtype):
     if dtype == F32:
         ns += [9 * W_ + 3, 10 * W_ - 7, 11 * W_ + 1, 12 * W_, 13 * W_ + 5, 14 * W_,
                15 * W_ - 3, 16 * W_]
+        # the last CTA ends on a chunk boundary (32 nodes) with padding lanes
+        # behind it in the same warp: warp 0 of the last CTA holds the row's last
+        # chunk and 22 padding chunks; warp 1 holds 8 real chunks and 24 padding
+        ns += [3 * W_ + 320, 2 * W_ + 32 * 40]
     ens = _concat([_one(n, bc, seed=n + bc) for n in ns for bc in (0, 1)])
     dts = oracle_dts(ens, 8.0)
     steps = np.array([5 + (i % 7) for i in range(ens.count)])
