@@ -535,6 +535,15 @@ def differentiation_bench(ctx, dev):
     return out
 
 
+def _tune_lines(ctx):
+    """The context's tuning table as text lines ("key nt c k")."""
+    import tempfile
+    path = os.path.join(tempfile.mkdtemp(), "tune.txt")
+    ctx.tune_save(path)
+    with open(path) as f:
+        return [ln for ln in f.read().splitlines() if ln and not ln.startswith("#")]
+
+
 def step_ic_bench(ctx, dev, rows: int = 4096, n: int = 4096, sample: int = 8):
     """Step-IC shock workload (Eq. 20, Sec. 3.4): `rows` Dirichlet rows of n
     nodes on [0, 1] from u0 = 1 left of x = 1/2 and 0 right of it (u(0) = 1,
@@ -761,8 +770,23 @@ def extras(args, ctx, ens, u0, batches, probe, dev, world, rank):
                           "buffers; dt from the device CFL reduction of the same inputs"}
     del ha, hb, hu0
 
-    # ---- large single grid (N = 2^24, periodic): streaming explicit, multi-level BTCS,
-    # FP32 against FP64 on the same device
+    out["large_grid"] = large_grid_bench(ctx, dev)
+    return out
+
+
+def large_grid_bench(ctx, dev):
+    """Large single grid (N = 2^24, periodic, sin x + 0.5 + noise, nu = 1e-3):
+    the temporally blocked streaming explicit solve (10000 steps), the
+    one-step-per-pass kernel (K = 1) against the HBM roofline, and the
+    multi-level BTCS solve (100 steps at 10x dt); FP32 against FP64."""
+    import torch
+
+    from paper_2601_12204_b300 import _lib as L
+    from paper_2601_12204_b300 import workloads as W
+    from paper_2601_12204_b300.api import Batch
+    F32, F64 = L.BURGERS_F32, L.BURGERS_F64
+    stream = torch.cuda.current_stream(dev)
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
     lg = W.large_grid(1 << 24)
     nlg = float(lg.ns[0])
     ul = torch.tensor(lg.u0, dtype=torch.float32, device=dev)
@@ -784,26 +808,50 @@ def extras(args, ctx, ens, u0, batches, probe, dev, world, rank):
         torch.cuda.synchronize()
         return w, a.elapsed_time(z) / 1000.0
 
-    for K, steps in ((0, LARGE_EXPLICIT_STEPS), (1, 200)):
+    peak, src = hbm_peak()
+    issue_cups = ctx.get(L.BURGERS_INFO_SM_COUNT) * FP32_LANES * 2032e6 / ALG_EXPLICIT_OPS
+    for K, steps in ((0, LARGE_EXPLICIT_STEPS), (1, 200), (1, LARGE_EXPLICIT_STEPS)):
         ctx.set(L.BURGERS_OPT_STREAM_K, K)
-        w, t = timed(L.BURGERS_EXPLICIT, Batch.from_ensemble(lg, dtl, steps, F32), ul)
+        b32 = Batch.from_ensemble(lg, dtl, steps, F32)
+        w, t = timed(L.BURGERS_EXPLICIT, b32, ul)
         cups = nlg * steps / t
         if K == 0:
+            kt = ctx.get(L.BURGERS_OPT_STREAM_K)  # 0: the tuned K
             large["explicit_cups"] = cups
             large["explicit_steps"] = steps
             w64, t64 = timed(L.BURGERS_EXPLICIT, Batch.from_ensemble(lg, dtl, steps, F64), ul64)
             large["explicit_fp64_cups"] = nlg * steps / t64
-            rel, _ = ctx.rel_l2(Batch.from_ensemble(lg, dtl, steps, F32), w, w64)
+            rel, _ = ctx.rel_l2(b32, w, w64)
             large["explicit_l2_fp32_vs_fp64"] = float(rel[0])
             del w64
-        else:
-            peak, src = hbm_peak()
-            gbs = 16.0 * nlg * steps / t / 1e9
+        elif steps == 200:
+            # the method's traffic: 4 bytes of u read and 4 written per cell-update
             large["stream_k1_cups"] = cups
-            large["stream_k1_gbs"] = gbs
-            large["stream_k1_hbm_frac"] = gbs / peak
+            large["stream_k1_gbs_algorithmic"] = 8.0 * cups / 1e9
+            large["stream_k1_hbm_frac_algorithmic"] = 8.0 * cups / 1e9 / peak
+            large["stream_k1_gbs_moved"] = 10.0 * cups / 1e9
+            large["stream_k1_hbm_frac_moved"] = 10.0 * cups / 1e9 / peak
             large["stream_k1_peak"] = {"gbs": peak, "source": src}
+        else:
+            # K = 1 for the whole run: FP32 against FP64 after 10000 single-step passes
+            w64, _ = timed(L.BURGERS_EXPLICIT, Batch.from_ensemble(lg, dtl, steps, F64), ul64)
+            rel, _ = ctx.rel_l2(b32, w, w64)
+            large["stream_k1_10000_steps"] = {"cups": cups, "l2_fp32_vs_fp64": float(rel[0])}
+            del w64
     ctx.set(L.BURGERS_OPT_STREAM_K, 0)
+    # the temporally blocked run against min(HBM x K / 8 B, FP32 issue / 9 ops):
+    # K from the tuning table's streaming entry if there is one, else the
+    # library's default for FP32 windows of 4096 nodes (32 steps per pass)
+    kb = 32
+    for line in _tune_lines(ctx):
+        key, nt, c, k = (int(x) for x in line.split())
+        if key >> 56 == 1 and (key >> 52) & 0xF == 0 and k > 0:  # K_EXPLICIT_STREAM, FP32
+            kb = min(k, nt * c // 4)
+    bound = min(peak * 1e9 * kb / 8.0, issue_cups)
+    large["blocked"] = {"K": kb, "cups": large["explicit_cups"], "bound_cups": bound,
+                        "frac": large["explicit_cups"] / bound,
+                        "bound": "hbm" if peak * 1e9 * kb / 8.0 < issue_cups else "alu",
+                        "note": "bound = min(HBM x K / 8 B, SMs x 128 FP32 lanes x 2032 MHz / 9 ops)"}
     bl32 = Batch.from_ensemble(lg, dtl * BTCS_DT_FACTOR, LARGE_BTCS_STEPS, F32)
     bl64 = Batch.from_ensemble(lg, dtl * BTCS_DT_FACTOR, LARGE_BTCS_STEPS, F64)
     w, t = timed(L.BURGERS_BTCS, bl32, ul)
@@ -815,13 +863,13 @@ def extras(args, ctx, ens, u0, batches, probe, dev, world, rank):
     large["btcs_l2_fp32_vs_fp64"] = float(rel[0])
     del w64
     large["note"] = ("N=2^24 periodic, nu=1e-3. Explicit: K=0 tuned temporal blocking, "
-                     "K=1 one step per HBM pass (k_explicit_step1), algorithmic 16 B per "
-                     "cell-update (u and its FP32 compensation term, each read and written once) "
-                     "against the HBM copy bandwidth. BTCS at 10x dt through the multi-level "
-                     "partitioned solver. l2 = per-row relative L2 of FP32 against FP64")
-    out["large_grid"] = large
+                     "K=1 one step per HBM pass (k_explicit_step1): algorithmic 8 B per "
+                     "cell-update (u read and written once), moved 10 B (plus the 1-byte FP32 "
+                     "compensation term each way), against the HBM copy bandwidth. BTCS at 10x dt "
+                     "through the multi-level partitioned solver. l2 = per-row relative L2 of "
+                     "FP32 against FP64")
     del ul, ul64, w
-    return out
+    return large
 
 
 def serve_bench(ctx, dev, duration: float, rate: float = 20000.0, plain_seconds: float = 5.0):

@@ -142,6 +142,14 @@ burgers_status burgers_ctx_get(const burgers_ctx* ctx, int32_t key, int64_t* val
  * kernels they contain). */
 int64_t burgers_launch_count(const burgers_ctx* ctx);
 
+/* Blocking (synchronises the context's device). The context's device error
+ * word: bit 0 is set when a wait inside a kernel gave up (the single-step
+ * streaming kernel waits on its bulk copies for at most about two seconds,
+ * then stops that CTA's work, so a row's result is then incomplete). *bits
+ * receives the word; clear != 0 resets it to 0 afterwards. No paper
+ * counterpart: failure reporting of the GPU path. */
+burgers_status burgers_device_error(burgers_ctx* ctx, int32_t* bits, int32_t clear);
+
 /* Launch-shape autotuner. Blocking. For every capacity class of the rows of
  * `batch` (rows grouped by the smallest register capacity that holds them)
  * it times each registered kernel shape of that class on a private copy of up

@@ -78,6 +78,7 @@ SIGNATURES = {
     "burgers_ctx_set": (_ST, [_P, _I32, _I64]),
     "burgers_ctx_get": (_ST, [_P, _I32, ctypes.POINTER(ctypes.c_int64)]),
     "burgers_launch_count": (_I64, [_P]),
+    "burgers_device_error": (_ST, [_P, _P, _I32]),
     "burgers_cfl_dt": (_ST, [_P, _P, _P, _D, _P, _P]),
     "burgers_cfl_dt_device": (_ST, [_P, _P, _P, _D, _P, _P]),
     "burgers_advance_dt_device": (_ST, [_P, _I32, _P, _P, _P, _D, _I32, _P]),

@@ -125,6 +125,14 @@ class Context:
     def launch_count(self) -> int:
         return int(self._lib.burgers_launch_count(self.h))
 
+    def device_error(self, clear: bool = False) -> int:
+        """The context's device error word (blocking); bit 0: a bounded wait
+        inside a kernel gave up."""
+        v = ctypes.c_int32(0)
+        L.check(self._lib.burgers_device_error(self.h, ctypes.byref(v), int(bool(clear))),
+                "burgers_device_error")
+        return int(v.value)
+
     def explicit_advance(self, batch: Batch, u, stream=None) -> None:
         p = self._check_tensor(u, batch)
         L.check(self._lib.burgers_explicit_advance(self.h, batch.ref(), p, self._stream(stream, u)),

@@ -733,6 +733,7 @@ burgers_status adjoint_run(burgers_ctx* ctx, int scheme, const burgers_batch* ba
       d.ds_dnu = in.dt / (in.dx * in.dx);
       d.n = in.n;
       d.bc = in.bc;
+      set_fp32_coefs(d);
       AdjRow a;
       int64_t k = stride > 0 ? stride : int64_t(ceil(sqrt(double(std::max<int64_t>(in.nsteps, 1)))));
       if (k < 1) k = 1;

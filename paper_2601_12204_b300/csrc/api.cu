@@ -244,6 +244,7 @@ static RowDesc make_row(const burgers_instance& in, int iters = 1) {
   d.ds_dnu = in.dt / (in.dx * in.dx);
   d.n = in.n;
   d.bc = in.bc;
+  set_fp32_coefs(d);
   return d;
 }
 
@@ -375,9 +376,31 @@ static burgers_status build_plan(burgers_ctx* ctx, int scheme, const burgers_bat
         return set_error(BURGERS_EINVAL, "row too short for the streaming kernel");
       const KernelEntry* k = nullptr;
       const bool step1 = K == 1 && scheme == BURGERS_EXPLICIT;
+      const KernelEntry* kbulk = nullptr;
       if (step1) {  // one Euler step per pass: the bandwidth-bound single-step kernel
-        k = find_kernel(K_EXPLICIT_STEP1, dtype, 256, dtype == 0 ? 8 : 4, 0);
-        sh = Shape{256, dtype == 0 ? 8 : 4};
+        // tile shape from the tuning table if it names one (its k: the stage
+        // count of the bulk-copy kernel for the whole tiles, 0 = the per-tile
+        // kernel only), else the per-tile kernel with 512 threads of 8 nodes
+        // (FP32; measured on a B300 at 0.63 of the HBM copy rate in the method's
+        // 8 bytes per cell-update, the bulk-copy ring at 0.60) or 256 of 4 (FP64)
+        sh = Shape{dtype == 0 ? 512 : 256, dtype == 0 ? 8 : 4};
+        int stages = 0;
+        auto it1 = ctx->tuned.find(tune_key(K_EXPLICIT_STEP1, dtype, 0, 0));
+        if (it1 != ctx->tuned.end() &&
+            find_kernel(K_EXPLICIT_STEP1, dtype, it1->second.nt, it1->second.c, 0)) {
+          sh = Shape{it1->second.nt, it1->second.c};
+          stages = it1->second.k;
+        }
+        k = find_kernel(K_EXPLICIT_STEP1, dtype, sh.nt, sh.c, 0);
+        // whole tiles move by bulk copies when every row starts 16-byte aligned in
+        // the state and in the one-byte compensation buffers (offsets multiple of 16)
+        bool aligned = true;
+        for (int64_t b : longs) aligned = aligned && batch->inst[b].offset % 16 == 0;
+        if (aligned && stages > 0)
+          for (const KernelEntry& e : kernel_registry())
+            if (e.kind == K_EXPLICIT_STEP1_BULK && e.dtype == dtype && e.nt == sh.nt &&
+                e.c == sh.c && e.exact == stages && e.dyn_smem <= ctx->smem_optin)
+              kbulk = &e;
       } else {
         k = find_kernel(skind, dtype, sh.nt, sh.c, 0);
       }
@@ -390,15 +413,28 @@ static burgers_status build_plan(burgers_ctx* ctx, int scheme, const burgers_bat
         const burgers_instance& in = batch->inst[longs[q]];
         p->rows.push_back(make_row(in));
         p->row_inst.push_back(int32_t(longs[q]));
-        int64_t tiles = (in.n + O - 1) / O;
-        for (int64_t t = 0; t < tiles; ++t)
-          p->items.push_back(TileItem{int32_t(q), int32_t(t)});
+      }
+      // items: the bulk-copy kernel takes the whole tiles first, the tails last
+      int nbulk = -1;
+      for (int pass = kbulk ? 0 : 1; pass < 2; ++pass) {
+        for (size_t q = 0; q < longs.size(); ++q) {
+          const int64_t n = batch->inst[longs[q]].n;
+          const int64_t tiles = (n + O - 1) / O;
+          for (int64_t t = 0; t < tiles; ++t) {
+            const bool whole = (t + 1) * O <= n;
+            if (!kbulk || whole == (pass == 0)) p->items.push_back(TileItem{int32_t(q), int32_t(t)});
+          }
+        }
+        if (pass == 0) nbulk = int(p->items.size()) - ibegin;
       }
       int nitems = int(p->items.size()) - ibegin;
-      // the single-step kernel streams: one CTA per tile lets the scheduler
-      // overlap the tiles' memory traffic
+      // the per-tile single-step kernel streams with one CTA per tile, so the
+      // scheduler overlaps the tiles' memory traffic; the bulk-copy kernel is
+      // persistent (its stages keep the traffic in flight)
       int grid = step1 ? std::min(nitems, 1 << 20)
                        : std::min(nitems, ctx->sm_count * blocks_per_sm(k));
+      const int grid_bulk = kbulk ? std::max(1, std::min(nitems, ctx->sm_count * blocks_per_sm(kbulk)))
+                                  : 0;
       int64_t passes = (smax + K - 1) / K;
       for (int64_t ps = 0; ps < passes; ++ps) {
         Launch L;
@@ -412,6 +448,7 @@ static burgers_status build_plan(burgers_ctx* ctx, int scheme, const burgers_bat
         L.K = K;
         L.step_base = ps * K;
         L.to_scratch = (ps % 2) == 0;
+        if (kbulk) { L.k_fallback = k; L.k = kbulk; L.nbulk = nbulk; L.grid = grid_bulk; }
         p->launches.push_back(L);
       }
       if (passes % 2 == 1) {  // result sits in the scratch buffer: copy it back
@@ -426,14 +463,16 @@ static burgers_status build_plan(burgers_ctx* ctx, int scheme, const burgers_bat
         L.K = K;
         L.step_base = smax;  // every row done: copy-through
         L.to_scratch = false;
+        if (kbulk) { L.k_fallback = k; L.k = kbulk; L.nbulk = nbulk; L.grid = grid_bulk; }
         p->launches.push_back(L);
       }
       // the compensation buffers follow the row copy; keep every buffer start
-      // 256-byte aligned (the kernel's vector loads need 16-byte alignment)
-      span = (span + 63) & ~int64_t(63);
+      // 256-byte aligned (the kernels' vector loads need 16-byte alignment)
+      span = (span + 255) & ~int64_t(255);
       p->stream_span = span;
-      // ping-pong copy of the rows, plus two Kahan compensation buffers (FP32)
-      p->scratch_elems = dtype == 0 ? 3 * span : span;
+      // ping-pong copy of the rows, plus (FP32) two compensation buffers of one
+      // byte per node (span / 4 elements each)
+      p->scratch_elems = dtype == 0 ? span + span / 2 : span;
     } else {
       // rows that fit a cluster stay resident in its shared memory
       // (k_btcs_cluster): 128-thread CTAs of 4096 nodes in clusters of up to
@@ -560,10 +599,10 @@ static cudaError_t enqueue_plan(burgers_ctx* ctx, Plan* p, void* u, cudaStream_t
   void* scratch = ctx->scratch.ptr;
   void* lo_a = nullptr;
   void* lo_b = nullptr;
-  if (p->stream_span > 0 && p->dtype == 0) {
+  if (p->stream_span > 0 && p->dtype == 0) {  // one compensation byte per node
     lo_a = static_cast<char*>(scratch) + size_t(p->stream_span) * esz;
-    lo_b = static_cast<char*>(lo_a) + size_t(p->stream_span) * esz;
-    cudaError_t e = cudaMemsetAsync(lo_a, 0, size_t(p->stream_span) * esz, st);
+    lo_b = static_cast<char*>(lo_a) + size_t(p->stream_span);
+    cudaError_t e = cudaMemsetAsync(lo_a, 0, size_t(p->stream_span), st);
     if (e != cudaSuccess) return e;
   }
   if (p->ml_span > 0 && p->dtype == 0) {  // multi-level Kahan terms start at zero
@@ -612,8 +651,21 @@ static cudaError_t enqueue_plan(burgers_ctx* ctx, Plan* p, void* u, cudaStream_t
       TileItem* it = items + L.item_begin;
       int ni = L.item_count, K = L.K;
       int64_t sb = L.step_base;
-      void* args[] = {&src, &dst, &lsrc, &ldst, &r, &it, &ni, &K, &sb};
-      e = cudaLaunchKernel(L.k->fn, dim3(L.grid), dim3(L.k->nt), args, L.k->dyn_smem, st);
+      const bool bulk_ok = L.nbulk >= 0 && (reinterpret_cast<uintptr_t>(u) & 15) == 0 &&
+                           (reinterpret_cast<uintptr_t>(scratch) & 15) == 0;
+      if (bulk_ok) {
+        int nb = L.nbulk;
+        int* err = static_cast<int*>(ctx->errbuf.ptr);
+        void* args[] = {&src, &dst, &lsrc, &ldst, &r, &it, &nb, &ni, &sb, &err};
+        e = cudaLaunchKernel(L.k->fn, dim3(L.grid), dim3(L.k->nt), args, L.k->dyn_smem, st);
+      } else {
+        // the per-tile kernel handles any tile (a bulk launch's fallback when the
+        // caller's buffer does not start 16-byte aligned)
+        const KernelEntry* k1 = L.nbulk >= 0 ? L.k_fallback : L.k;
+        const int g1 = L.nbulk >= 0 ? std::min(ni, 1 << 20) : L.grid;
+        void* args[] = {&src, &dst, &lsrc, &ldst, &r, &it, &ni, &K, &sb};
+        e = cudaLaunchKernel(k1->fn, dim3(g1), dim3(k1->nt), args, k1->dyn_smem, st);
+      }
     } else {
       e = enqueue_multilevel_launch(ctx, p, L, u, st);
     }
@@ -812,6 +864,8 @@ burgers_status burgers_ctx_create(int device, burgers_ctx** out) {
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->join_ev[i], cudaEventDisableTiming);
   }
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->fork_ev, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = ctx->errbuf.ensure(256);
+  if (e == cudaSuccess) e = cudaMemset(ctx->errbuf.ptr, 0, 256);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->io_h2d, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->io_d2h, cudaStreamNonBlocking);
   for (int i = 0; i < burgers_ctx::kIoChunks && e == cudaSuccess; ++i) {
@@ -888,6 +942,18 @@ burgers_status burgers_ctx_get(const burgers_ctx* ctx, int32_t key, int64_t* val
 }
 
 int64_t burgers_launch_count(const burgers_ctx* ctx) { return ctx ? ctx->launches.load() : 0; }
+
+burgers_status burgers_device_error(burgers_ctx* ctx, int32_t* bits, int32_t clear) {
+  if (!ctx || !bits) return set_error(BURGERS_EINVAL, "NULL pointer");
+  cudaError_t e = cudaSetDevice(ctx->device);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  int32_t v = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(&v, ctx->errbuf.ptr, sizeof v, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && clear) e = cudaMemset(ctx->errbuf.ptr, 0, sizeof v);
+  if (e != cudaSuccess) return cuda_error(e, "device error word");
+  *bits = v;
+  return BURGERS_OK;
+}
 
 burgers_status burgers_explicit_advance(burgers_ctx* ctx, const burgers_batch* batch, void* u_dev,
                                         burgers_stream stream) {
@@ -1029,6 +1095,7 @@ __global__ void k_rows_from_dt(RowDesc* __restrict__ rows, const int32_t* __rest
   rows[i].r = dt / dx;
   rows[i].s = nu * dt / (dx * dx);
   rows[i].ds_dnu = dt / (dx * dx);
+  set_fp32_coefs(rows[i]);
 }
 
 // The batch with dt and nsteps replaced by placeholders (the device-dt

@@ -48,6 +48,8 @@ struct Launch {
   int counter = -1;
   int item_begin = 0, item_count = 0;
   int K = 0;
+  int nbulk = -1;  // bulk-copy single-step launch: items [0, nbulk) are whole aligned tiles
+  const KernelEntry* k_fallback = nullptr;  // its per-tile kernel (unaligned buffers)
   int64_t step_base = 0;
   bool to_scratch = false;
   int level = 0;   // multi-level: level of a reduce/recover launch
@@ -136,6 +138,7 @@ struct burgers_ctx {
   burgers::DevBuf tunebuf;  // autotuner row copies
   int resident_override = 0;  // autotuner: send every long-enough row to the long-row path
   burgers::HostBuf redhost;
+  burgers::DevBuf errbuf;   // device error word of the bounded waits (bit 0: a bulk-copy wait gave up)
   burgers::DevBuf adjws;    // adjoint checkpoints and segment states
   burgers::DevBuf adjdesc;  // adjoint descriptors
   burgers::HostBuf adjhost;

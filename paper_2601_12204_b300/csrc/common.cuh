@@ -20,7 +20,30 @@ struct RowDesc {
   int32_t bc;      // 0 periodic, 1 Dirichlet
   int32_t iters = 1;  // iterations per step (Picard / Newton variants)
   int32_t pad = 0;
+  float rf = 0.f, hf = 0.f, sf = 0.f;  // r, r/2, s rounded once to FP32 (set_fp32_coefs)
+  int32_t pad2 = 0;
 };
+
+// Fills the FP32 copies of a row's coefficients from its FP64 r and s, so the
+// FP32 kernels that read a descriptor per tile convert nothing: bitwise the
+// values float(r), float(r / 2) (= float(r) / 2) and float(s).
+__host__ __device__ inline void set_fp32_coefs(RowDesc& d) {
+  d.rf = static_cast<float>(d.r);
+  d.hf = static_cast<float>(0.5 * d.r);
+  d.sf = static_cast<float>(d.s);
+}
+
+// r, r/2 and s of a row in the kernel's type.
+template <typename T>
+struct RowCoefs {
+  T r, h, s;
+};
+__device__ __forceinline__ RowCoefs<float> row_coefs(const RowDesc& d, float) {
+  return {d.rf, d.hf, d.sf};
+}
+__device__ __forceinline__ RowCoefs<double> row_coefs(const RowDesc& d, double) {
+  return {d.r, 0.5 * d.r, d.s};
+}
 
 enum : int32_t { BC_PERIODIC = 0, BC_DIRICHLET = 1 };
 
@@ -131,6 +154,29 @@ __device__ __forceinline__ T explicit_update(T u, T ul, T ur, T r, T h, T s, T& 
     (void)lo;
     return explicit_increment(u, ul, ur, r, h, s, u);
   }
+}
+
+// The FP32 compensation term of a streamed state, stored in 8 bits. After a
+// compensated update the term lo of the value v satisfies |lo| <= ulp(v) / 2,
+// so lo / (ulp(v) / 256) lies in [-128, 128]: it is stored as that integer
+// (rounded to nearest, saturated to [-128, 127]) and read back as
+// q ulp(v) / 256. The quantum, 1/256 ulp(v), is far below what the
+// compensation has to carry across HBM passes (a 2^24-node diffusion-limited
+// run keeps the full Kahan accuracy with it). Both directions scale by powers
+// of two built from v's exponent bits with integer arithmetic (no branch):
+// 256 / ulp(v) = 2^(158 - e) and ulp(v) / 256 = 2^(e - 158) for the biased
+// exponent e of v. Values with e <= 31 (|v| < 2^-95) read back 0 whatever
+// was stored.
+__device__ __forceinline__ signed char lo8_encode(float v, float lo) {
+  const unsigned ebits = __float_as_uint(v) & 0x7f800000u;
+  const float inv = __uint_as_float(0x8e800000u - ebits);  // 2^(158 - e), exact for e >= 31
+  int q;
+  asm("cvt.rni.sat.s8.f32 %0, %1;" : "=r"(q) : "f"(lo * inv));
+  return static_cast<signed char>(q);
+}
+__device__ __forceinline__ float lo8_decode(float v, signed char q) {
+  const int ebits = int(__float_as_uint(v) & 0x7f800000u) - (31 << 23);
+  return static_cast<float>(q) * __int_as_float(ebits > 0 ? ebits : 0);  // 2^(e - 158), or 0
 }
 
 // u + d with the same compensation (BTCS increments).

@@ -21,6 +21,7 @@
 
 #include "common.cuh"
 #include "kernels.h"
+#include "step1.cuh"
 
 namespace burgers {
 
@@ -437,14 +438,15 @@ __device__ __forceinline__ int skew32(int i) { return i + (i >> 5); }
 // Streaming window kernel. Pass `step_base` advances every row by
 // min(K, nsteps - step_base) steps from src into dst (rows already done are
 // copied through, so src/dst stay consistent for the ping-pong). FP32 passes
-// carry the Kahan compensation term through lo_src / lo_dst (same layout as
-// the rows); FP64 passes get null pointers. Results leave through a skewed
-// shared-memory stage so the stores of the W - 2K output nodes are coalesced.
+// carry the Kahan compensation term through lo_src / lo_dst, one byte per node
+// in the rows' layout (lo8_encode); FP64 passes get null pointers. Results
+// leave through a skewed shared-memory stage so the stores of the W - 2K
+// output nodes are coalesced.
 template <typename T, int NT, int C, int INTEG = INTEG_EULER>
 __global__ void __launch_bounds__(NT) k_explicit_stream(const T* __restrict__ src,
                                                         T* __restrict__ dst,
-                                                        const T* __restrict__ lo_src,
-                                                        T* __restrict__ lo_dst,
+                                                        const signed char* __restrict__ lo_src,
+                                                        signed char* __restrict__ lo_dst,
                                                         const RowDesc* __restrict__ rows,
                                                         const TileItem* __restrict__ items,
                                                         int nitems, int K, int64_t step_base) {
@@ -452,8 +454,8 @@ __global__ void __launch_bounds__(NT) k_explicit_stream(const T* __restrict__ sr
   constexpr int W = NT * C;
   constexpr int WS = W + W / 32;
   extern __shared__ __align__(16) unsigned char dsm[];
-  T* stage = reinterpret_cast<T*>(dsm);   // WS values
-  T* stage_lo = stage + WS;                 // WS values (FP32 only)
+  T* stage = reinterpret_cast<T*>(dsm);                                  // WS values
+  signed char* stage_lo = reinterpret_cast<signed char*>(stage + WS);   // WS bytes (FP32 only)
   __shared__ T sh_last[2 * NW], sh_first[2 * NW], sh_wrap[4];
   // each step (each RK4 stage) makes one more node per side stale
   const int H = K * (INTEG == INTEG_RK4 ? 4 : 1);
@@ -480,16 +482,9 @@ __global__ void __launch_bounds__(NT) k_explicit_stream(const T* __restrict__ sr
     T v[C], lo[C];
     const int64_t g0 = ws + base;
     const bool interior = ws >= 0 && ws + W <= n;
-    bool aligned = (reinterpret_cast<uintptr_t>(srow + ws) & 15) == 0;
-    if constexpr (Kahan<T>::on)
-      aligned = aligned && (reinterpret_cast<uintptr_t>(lo_src + rd.offset + ws) & 15) == 0;
+    const bool aligned = (reinterpret_cast<uintptr_t>(srow + ws) & 15) == 0;
     if (interior && aligned && (C % Vec2<T>::width == 0)) {
       load_vec<T, C>(v, srow + g0);
-      if constexpr (Kahan<T>::on) load_vec<T, C>(lo, lo_src + rd.offset + g0);
-      else {
-#pragma unroll
-        for (int j = 0; j < C; ++j) lo[j] = T(0);
-      }
     } else {
 #pragma unroll
       for (int j = 0; j < C; ++j) {
@@ -501,31 +496,73 @@ __global__ void __launch_bounds__(NT) k_explicit_stream(const T* __restrict__ sr
           gi = gi < 0 ? 0 : (gi >= n ? n - 1 : gi);
         }
         v[j] = srow[gi];
-        if constexpr (Kahan<T>::on) lo[j] = lo_src[rd.offset + gi];
-        else lo[j] = T(0);
       }
     }
-    const T r = T(rd.r), h = T(0.5 * rd.r), s = T(rd.s);
+#pragma unroll
+    for (int j = 0; j < C; ++j) lo[j] = T(0);
+    if constexpr (Kahan<T>::on) {
+      // one byte per node: 16-byte words inside the row where aligned, else per
+      // node (the window's halo wraps or clamps)
+      const signed char* lp = lo_src + rd.offset + g0;
+      if (C % 16 == 0 && interior && (reinterpret_cast<uintptr_t>(lp) & 15) == 0) {
+#pragma unroll
+        for (int k = 0; k < C / 16; ++k) {
+          const uint4 w = __ldg(reinterpret_cast<const uint4*>(lp) + k);
+          const unsigned ww[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+          for (int e = 0; e < 16; ++e)
+            lo[16 * k + e] = lo8_decode(v[16 * k + e],
+                                        static_cast<signed char>(ww[e >> 2] >> (8 * (e & 3))));
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < C; ++j) {
+          int64_t gi = g0 + j;
+          if (!interior) {
+            if (rd.bc == BC_PERIODIC) {
+              gi %= n;
+              if (gi < 0) gi += n;
+            } else {
+              gi = gi < 0 ? 0 : (gi >= n ? n - 1 : gi);
+            }
+          }
+          lo[j] = lo8_decode(v[j], __ldg(lo_src + rd.offset + gi));
+        }
+      }
+    }
+    const RowCoefs<T> cf = row_coefs(rd, T(0));
     const bool has_end = rd.bc == BC_DIRICHLET && ((ws <= 0 && ws + W > 0) ||
                                                    (ws <= n - 1 && ws + W > n - 1));
     if (has_end)
-      explicit_steps<T, NT, C, MODE_WINDOW_DIR, BC_DIRICHLET, INTEG>(v, lo, kk, r, h, s, int(n),
-                                                                     g0, sh_last, sh_first,
+      explicit_steps<T, NT, C, MODE_WINDOW_DIR, BC_DIRICHLET, INTEG>(v, lo, kk, cf.r, cf.h, cf.s,
+                                                                     int(n), g0, sh_last, sh_first,
                                                                      sh_wrap);
     else
-      explicit_steps<T, NT, C, MODE_WINDOW, BC_PERIODIC, INTEG>(v, lo, kk, r, h, s, int(n), g0,
-                                                                sh_last, sh_first, sh_wrap);
+      explicit_steps<T, NT, C, MODE_WINDOW, BC_PERIODIC, INTEG>(v, lo, kk, cf.r, cf.h, cf.s,
+                                                                int(n), g0, sh_last, sh_first,
+                                                                sh_wrap);
 #pragma unroll
-    for (int j = 0; j < C; ++j) {
-      stage[skew32(base + j)] = v[j];
-      if constexpr (Kahan<T>::on) stage_lo[skew32(base + j)] = lo[j];
+    for (int j = 0; j < C; ++j) stage[skew32(base + j)] = v[j];
+    if constexpr (Kahan<T>::on) {
+      // bytes unskewed: each thread stores its C bytes as whole words (the
+      // stage starts 16-byte aligned and base is a multiple of C)
+      if constexpr (C % 4 == 0) {
+#pragma unroll
+        for (int k = 0; k < C / 4; ++k)
+          reinterpret_cast<unsigned*>(stage_lo + base)[k] =
+              pack4(lo8_encode(v[4 * k], lo[4 * k]), lo8_encode(v[4 * k + 1], lo[4 * k + 1]),
+                    lo8_encode(v[4 * k + 2], lo[4 * k + 2]), lo8_encode(v[4 * k + 3], lo[4 * k + 3]));
+      } else {
+#pragma unroll
+        for (int j = 0; j < C; ++j) stage_lo[base + j] = lo8_encode(v[j], lo[j]);
+      }
     }
     __syncthreads();
     for (int i = threadIdx.x; i < O; i += NT) {
       const int64_t gi = out_lo + i;
       if (gi < out_hi) {
         drow[gi] = stage[skew32(H + i)];
-        if constexpr (Kahan<T>::on) lo_dst[rd.offset + gi] = stage_lo[skew32(H + i)];
+        if constexpr (Kahan<T>::on) lo_dst[rd.offset + gi] = stage_lo[H + i];
       }
     }
     __syncthreads();
@@ -533,110 +570,20 @@ __global__ void __launch_bounds__(NT) k_explicit_stream(const T* __restrict__ sr
 }
 
 // One step per HBM pass (streaming with K = 1): the bandwidth-bound form of
-// the explicit step. Item `it` is tile ti.tile of row ti.row, NT*C nodes; a
-// thread updates C consecutive nodes read and written as 16-byte vectors when
-// the row's start allows it. The two neighbours of a thread's nodes come from
-// the adjacent lanes by shuffle, and from memory at warp and row edges. Same
-// arguments as k_explicit_stream (K is 1 here).
+// the explicit step, one tile of NT*C nodes per item (step1_tile, step1.cuh).
+// Same arguments as k_explicit_stream (K is 1 here). Handles any tile; the
+// bulk-copy kernel k_explicit_step1_bulk takes the full tiles of aligned rows.
 template <typename T, int NT, int C>
 __global__ void __launch_bounds__(NT) k_explicit_step1(const T* __restrict__ src,
                                                        T* __restrict__ dst,
-                                                       const T* __restrict__ lo_src,
-                                                       T* __restrict__ lo_dst,
+                                                       const signed char* __restrict__ lo_src,
+                                                       signed char* __restrict__ lo_dst,
                                                        const RowDesc* __restrict__ rows,
                                                        const TileItem* __restrict__ items,
                                                        int nitems, int K, int64_t step_base) {
   (void)K;
-  using V = typename Vec16<T>::type;
-  constexpr int VE = 16 / int(sizeof(T));
-  static_assert(C % VE == 0, "whole vectors per thread");
-  constexpr bool KL = Kahan<T>::on;
-  const int lane = threadIdx.x & 31;
-  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
-    const TileItem ti = items[it];
-    const RowDesc rd = rows[ti.row];
-    const int64_t n = rd.n;
-    const int64_t g0 = int64_t(ti.tile) * (NT * C) + int64_t(threadIdx.x) * C;
-    const int cnt = g0 >= n ? 0 : (n - g0 < C ? int(n - g0) : C);
-    const T* srow = src + rd.offset;
-    T* drow = dst + rd.offset;
-    const T* lsrc = KL ? lo_src + rd.offset : nullptr;
-    T* ldst = KL ? lo_dst + rd.offset : nullptr;
-    const bool vec = cnt == C && (reinterpret_cast<uintptr_t>(srow + g0) & 15) == 0 &&
-                     (reinterpret_cast<uintptr_t>(drow + g0) & 15) == 0 &&
-                     (!KL || ((reinterpret_cast<uintptr_t>(lsrc + g0) & 15) == 0 &&
-                              (reinterpret_cast<uintptr_t>(ldst + g0) & 15) == 0));
-    T v[C], lo[C];
-    if (vec) {
-#pragma unroll
-      for (int q = 0; q < C / VE; ++q) {
-        const V w = __ldcs(reinterpret_cast<const V*>(srow + g0) + q);
-        const T* wp = reinterpret_cast<const T*>(&w);
-#pragma unroll
-        for (int e = 0; e < VE; ++e) v[q * VE + e] = wp[e];
-        if constexpr (KL) {
-          const V wl = __ldcs(reinterpret_cast<const V*>(lsrc + g0) + q);
-          const T* wlp = reinterpret_cast<const T*>(&wl);
-#pragma unroll
-          for (int e = 0; e < VE; ++e) lo[q * VE + e] = wlp[e];
-        }
-      }
-    } else {
-#pragma unroll
-      for (int j = 0; j < C; ++j) {
-        v[j] = j < cnt ? srow[g0 + j] : T(0);
-        lo[j] = (KL && j < cnt) ? lsrc[g0 + j] : T(0);
-      }
-    }
-    if constexpr (!KL) {
-#pragma unroll
-      for (int j = 0; j < C; ++j) lo[j] = T(0);
-    }
-    // neighbours: the adjacent lane's edge node when it is the adjacent node
-    T left = shfl_up(v[C - 1], 1);
-    T right = shfl_down(v[0], 1);
-    const bool per = rd.bc == BC_PERIODIC;
-    if (cnt > 0) {
-      if (lane == 0 || g0 == 0) left = g0 > 0 ? srow[g0 - 1] : (per ? srow[n - 1] : T(0));
-      if (lane == 31 || cnt < C || g0 + C == n)
-        right = g0 + cnt < n ? srow[g0 + cnt] : (per ? srow[0] : T(0));
-    }
-    if (cnt == 0) continue;
-    if (step_base < rd.nsteps) {
-      const T r = T(rd.r), h = T(0.5 * rd.r), s = T(rd.s);
-      T prev = left;
-#pragma unroll
-      for (int j = 0; j < C; ++j) {
-        const T cur = v[j];
-        const T ur = j + 1 < cnt ? v[j + 1] : right;
-        T l0 = lo[j];
-        const T nv = explicit_update(cur, prev, ur, r, h, s, l0);
-        const int64_t gi = g0 + j;
-        const bool keep = j >= cnt || (!per && (gi == 0 || gi == n - 1));
-        if (!keep) { v[j] = nv; lo[j] = l0; }
-        prev = cur;
-      }
-    }
-    if (vec) {
-#pragma unroll
-      for (int q = 0; q < C / VE; ++q) {
-        V w, wl;
-        T* wp = reinterpret_cast<T*>(&w);
-        T* wlp = reinterpret_cast<T*>(&wl);
-#pragma unroll
-        for (int e = 0; e < VE; ++e) { wp[e] = v[q * VE + e]; wlp[e] = lo[q * VE + e]; }
-        __stcs(reinterpret_cast<V*>(drow + g0) + q, w);
-        if constexpr (KL) __stcs(reinterpret_cast<V*>(ldst + g0) + q, wl);
-      }
-    } else {
-#pragma unroll
-      for (int j = 0; j < C; ++j)
-        if (j < cnt) {
-          drow[g0 + j] = v[j];
-          if constexpr (KL) ldst[g0 + j] = lo[j];
-        }
-    }
-  }
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x)
+    step1_tile<T, NT, C>(src, dst, lo_src, lo_dst, rows, items[it], step_base);
 }
 
 #define REG_RES(T, DT, NT, C)                                                               \
@@ -656,11 +603,11 @@ __global__ void __launch_bounds__(NT) k_explicit_step1(const T* __restrict__ src
 #define REG_RK4_STREAM(T, DT, NT, C)                                                        \
   reg.push_back({K_RK4_STREAM, DT, NT, C, 0,                                               \
                  reinterpret_cast<const void*>(&k_explicit_stream<T, NT, C, INTEG_RK4>),  \
-                 sizeof(T) * size_t(NT * C + NT * C / 32) * (Kahan<T>::on ? 2 : 1)});
+                 (sizeof(T) + (Kahan<T>::on ? 1 : 0)) * size_t(NT * C + NT * C / 32)});
 #define REG_STREAM(T, DT, NT, C)                                                            \
   reg.push_back({K_EXPLICIT_STREAM, DT, NT, C, 0,                                          \
                  reinterpret_cast<const void*>(&k_explicit_stream<T, NT, C>),             \
-                 sizeof(T) * size_t(NT * C + NT * C / 32) * (Kahan<T>::on ? 2 : 1)});
+                 (sizeof(T) + (Kahan<T>::on ? 1 : 0)) * size_t(NT * C + NT * C / 32)});
 
 void register_explicit(std::vector<KernelEntry>& reg) {
   // FP32 resident shapes (capacity NT*C nodes)
@@ -696,6 +643,14 @@ void register_explicit(std::vector<KernelEntry>& reg) {
   // one step per pass
   reg.push_back({K_EXPLICIT_STEP1, 0, 256, 8, 0,
                  reinterpret_cast<const void*>(&k_explicit_step1<float, 256, 8>), 0});
+  reg.push_back({K_EXPLICIT_STEP1, 0, 256, 16, 0,
+                 reinterpret_cast<const void*>(&k_explicit_step1<float, 256, 16>), 0});
+  reg.push_back({K_EXPLICIT_STEP1, 0, 128, 16, 0,
+                 reinterpret_cast<const void*>(&k_explicit_step1<float, 128, 16>), 0});
+  reg.push_back({K_EXPLICIT_STEP1, 0, 512, 8, 0,
+                 reinterpret_cast<const void*>(&k_explicit_step1<float, 512, 8>), 0});
+  reg.push_back({K_EXPLICIT_STEP1, 1, 256, 8, 0,
+                 reinterpret_cast<const void*>(&k_explicit_step1<double, 256, 8>), 0});
   reg.push_back({K_EXPLICIT_STEP1, 1, 256, 4, 0,
                  reinterpret_cast<const void*>(&k_explicit_step1<double, 256, 4>), 0});
 }

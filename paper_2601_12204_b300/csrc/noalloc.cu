@@ -107,15 +107,19 @@ extern "C" burgers_status burgers_explicit_advance_noalloc(const burgers_instanc
   rd.ds_dnu = in.dt / (in.dx * in.dx);
   rd.n = in.n;
   rd.bc = in.bc;
+  set_fp32_coefs(rd);
   RowDesc* desc = reinterpret_cast<RowDesc*>(base + NA_DESC);
   TileItem* items = reinterpret_cast<TileItem*>(base + NA_ITEMS);
+  // the row copy, then (FP32) two compensation buffers of one byte per node,
+  // each start 256-byte aligned
   const size_t span = (size_t(in.n) * esz + 255) & ~size_t(255);
+  const size_t lo_span = (size_t(in.n) + 255) & ~size_t(255);
   void* copy = base + NA_DATA;
   void* lo_a = dtype == BURGERS_F32 ? base + NA_DATA + span : nullptr;
-  void* lo_b = dtype == BURGERS_F32 ? base + NA_DATA + 2 * span : nullptr;
+  void* lo_b = dtype == BURGERS_F32 ? base + NA_DATA + span + lo_span : nullptr;
   k_noalloc_setup<<<(ntiles + 255) / 256, 256, 0, s>>>(rd, desc, items, ntiles);
   e = cudaGetLastError();
-  if (e == cudaSuccess && lo_a) e = cudaMemsetAsync(lo_a, 0, size_t(in.n) * esz, s);
+  if (e == cudaSuccess && lo_a) e = cudaMemsetAsync(lo_a, 0, size_t(in.n), s);
   if (e != cudaSuccess) return cuda_error(e, "no-alloc set-up");
   if (k->dyn_smem > 0) {  // no context may have prepared the kernel on this device
     e = cudaFuncSetAttribute(k->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(k->dyn_smem));

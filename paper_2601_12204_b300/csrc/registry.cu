@@ -14,6 +14,7 @@ void register_newton(std::vector<KernelEntry>& reg);
 void register_btcs_cluster(std::vector<KernelEntry>& reg);
 void register_multilevel(std::vector<KernelEntry>& reg);
 void register_adjoint(std::vector<KernelEntry>& reg);
+void register_step1_bulk(std::vector<KernelEntry>& reg);
 
 const std::vector<KernelEntry>& kernel_registry() {
   static std::vector<KernelEntry> reg;
@@ -27,6 +28,7 @@ const std::vector<KernelEntry>& kernel_registry() {
     register_btcs_cluster(reg);
     register_multilevel(reg);
     register_adjoint(reg);
+    register_step1_bulk(reg);
   });
   return reg;
 }

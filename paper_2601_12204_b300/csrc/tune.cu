@@ -121,6 +121,7 @@ burgers_status autotune(burgers_ctx* ctx, int scheme, const burgers_batch* batch
       d.ds_dnu = in.dt / (in.dx * in.dx);
       d.n = in.n;
       d.bc = in.bc;
+      set_fp32_coefs(d);
       rows.push_back(d);
       orig_off.push_back(in.offset);
       off += in.n;

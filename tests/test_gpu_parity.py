@@ -112,6 +112,81 @@ def test_streaming_explicit(ctx, dtype, K):
         _fresh(ctx)
 
 
+# single-step tile shapes (threads, nodes a thread, bulk-copy stages; 0 = the
+# per-tile kernel only) of the K = 1 streaming path
+STEP1_SHAPES = {F32: [(512, 8, 0), (512, 8, 3), (512, 8, 4), (256, 16, 4), (128, 16, 6)],
+                F64: [(256, 4, 0), (256, 4, 4)]}
+
+
+@pytest.mark.parametrize("dtype", [F64, F32])
+@pytest.mark.parametrize("misalign", [0, 1])
+def test_streaming_k1_bulk_tiles(ctx, dtype, misalign, tmp_path):
+    """One step per pass (K = 1) with rows at 16-element offsets, for every
+    registered single-step shape (set through the tuning table): with bulk
+    stages, whole tiles go through the bulk-copy kernel (TMA ring) and row
+    tails through the per-tile path in the same launch; misalign = 1 shifts the
+    caller's buffer by one element, so every tile takes the per-tile kernel.
+    Both BCs, odd and even pass counts, against the oracle; the device error
+    word stays 0."""
+    key = (8 << 56) ^ (dtype << 52)  # K_EXPLICIT_STEP1, class 0
+    try:
+        for nt, c, stages in STEP1_SHAPES[dtype]:
+            path = tmp_path / f"step1_{nt}_{c}_{stages}.txt"
+            path.write_text(f"# step1 shape\n{key} {nt} {c} {stages}\n")
+            ctx.tune_load(str(path))
+            _k1_bulk_case(ctx, dtype, misalign, nt * c)
+    finally:  # back to the library's default shape
+        nt, c, stages = STEP1_SHAPES[dtype][0]
+        path = tmp_path / "step1_default.txt"
+        path.write_text(f"# step1 shape\n{key} {nt} {c} {stages}\n")
+        ctx.tune_load(str(path))
+
+
+def _k1_bulk_case(ctx, dtype, misalign, tile):
+    import torch
+
+    from paper_2601_12204_b300.api import Batch
+    _fresh(ctx)
+    ctx.set(L.BURGERS_OPT_RESIDENT_MAX, 1024)
+    ctx.set(L.BURGERS_OPT_STREAM_K, 1)
+    try:
+        lens = [3 * tile, 5 * tile + 123, 70001, 16 * tile + 16, 2 * tile - 5]
+        parts = [_one(n, bc, seed=n + 11 * bc) for n in lens for bc in (0, 1)]
+        offs, o = [], 0
+        for p in parts:
+            offs.append(o)
+            o = (o + int(p.ns[0]) + 37 + 15) // 16 * 16  # gaps, 16-element starts
+        span = o
+        ens = _concat(parts)
+        ens.offsets = np.array(offs, np.int64)
+        buf = np.full(span + 1, 2.5)
+        for b, p in enumerate(parts):
+            buf[offs[b]:offs[b] + int(p.ns[0])] = p.u0
+        dts = oracle_dts(ens)
+        steps = np.array([1, 2, 7, 8, 13, 1, 4, 5, 3, 6])
+        tdt = torch.float32 if dtype == F32 else torch.float64
+        if misalign:  # a view one element past an allocation's (aligned) start
+            base = torch.tensor(np.concatenate([[7.0], buf]), dtype=tdt, device="cuda")
+            u = base[1:]
+        else:
+            u = torch.tensor(buf, dtype=tdt, device="cuda")
+        b = Batch(dtype, ens.offsets, ens.ns, ens.bcs, ens.dxs, ens.nus, dts, steps)
+        ctx.explicit_advance(b, u)
+        torch.cuda.synchronize()
+        got_buf = u.cpu().double().numpy()
+        ref_ens = _concat(parts)
+        ref = run_oracle(EXPLICIT, ref_ens, dts, steps)
+        got = np.concatenate([got_buf[offs[i]:offs[i] + int(parts[i].ns[0])] for i in range(len(parts))])
+        assert_parity(ref_ens, got, ref, dtype, f"k1 bulk misalign {misalign}")
+        mask = np.ones(span + 1, bool)
+        for i, p in enumerate(parts):
+            mask[offs[i]:offs[i] + int(p.ns[0])] = False
+        assert np.all(got_buf[mask] == 2.5)  # gaps untouched
+        assert ctx.device_error() == 0
+    finally:
+        _fresh(ctx)
+
+
 @pytest.mark.parametrize("dtype", [F64, F32])
 def test_multilevel_btcs(ctx, dtype):
     """Long BTCS rows through the multi-level partitioned solver (one and two
