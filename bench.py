@@ -544,6 +544,72 @@ def _tune_lines(ctx):
         return [ln for ln in f.read().splitlines() if ln and not ln.startswith("#")]
 
 
+def short_rows_bench(dev, steps: int = 100):
+    """Many short BTCS rows (periodic random-Fourier ensembles, 10x the CFL dt):
+    the partitioned resident kernel and the per-thread Thomas kernel side by
+    side, each forced through the tuning table of a context of its own, and
+    the library's default choice; FP32 and FP64 throughput, both paths
+    against the FP64 oracle on sampled rows."""
+    import tempfile
+
+    import torch
+
+    import oracle
+    from paper_2601_12204_b300 import _lib as L
+    from paper_2601_12204_b300 import workloads as W
+    from paper_2601_12204_b300.api import Batch, Context
+    # (rows, n): the partitioned kernel's shape and the Thomas kernel's
+    # (threads, layout mode) of that capacity class, per dtype
+    part = {32: (32, 1), 64: (32, 2), 256: (32, 8), 512: (64, 8)}
+    thomas = {(0, 32): (256, 2), (0, 64): (256, 0), (0, 256): (32, 2), (0, 512): (64, 1),
+              (1, 32): (128, 0), (1, 64): (64, 1), (1, 256): (64, 1), (1, 512): (64, 1)}
+    out = {"steps": steps, "dt": "10x CFL", "note": "cell-updates/s; default = the library's own "
+           "choice (per-thread Thomas for classes of <= 64 FP32 / <= 128 FP64 nodes with >= 8192 rows)"}
+    for rows, n in ((4096, 256), (16384, 512), (16384, 32), (65536, 64)):
+        ens = W.fourier_ensemble(rows, n)
+        rec = {}
+        for dt_, tdt, name in ((L.BURGERS_F32, torch.float32, "fp32"), (L.BURGERS_F64, torch.float64, "fp64")):
+            u0 = torch.tensor(ens.u0, dtype=tdt, device=dev)
+            sub_ids = np.array([0, rows // 2, rows - 1])
+            r = {}
+            for path in ("default", "partitioned", "thomas"):
+                ctx = Context(dev.index or 0)
+                try:
+                    dts = ctx.cfl_dt(Batch.from_ensemble(ens, 1.0, 0, dt_), u0, CFL) * BTCS_DT_FACTOR
+                    if path != "default":
+                        key = lambda ex: (2 << 56) ^ (dt_ << 52) ^ (ex << 48) ^ n  # noqa: E731
+                        nt, c, k = ((*part[n], 0) if path == "partitioned"
+                                    else (thomas[(dt_, n)][0], n, 1 + thomas[(dt_, n)][1]))
+                        p = os.path.join(tempfile.mkdtemp(), "t.txt")
+                        with open(p, "w") as f:
+                            f.write(f"# forced\n{key(0)} {nt} {c} {k}\n{key(1)} {nt} {c} {k}\n")
+                        ctx.tune_load(p)
+                    b = Batch.from_ensemble(ens, dts, steps, dt_)
+                    ts = []
+                    for _ in range(8):  # the first two build the plan and warm the clocks
+                        w = u0.clone()
+                        a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                        a.record()
+                        ctx.btcs_advance(b, w)
+                        z.record()
+                        torch.cuda.synchronize()
+                        ts.append(a.elapsed_time(z) / 1e3)
+                    cups = rows * n * steps / min(ts[2:])
+                    g = w.double().view(rows, n)[torch.from_numpy(sub_ids).to(dev)].cpu().numpy()
+                    sub = ens.subset(sub_ids)
+                    ref = oracle.btcs_batch(sub.u0, sub.offsets, sub.ns, sub.bcs, sub.dxs, sub.nus,
+                                            dts[sub_ids], np.full(3, steps)).reshape(3, n)
+                    r[path] = {"cups": cups,
+                               "l2_vs_oracle_sampled_max": float(max(oracle.rel_l2(g[j], ref[j])
+                                                                     for j in range(3)))}
+                finally:
+                    ctx.close()
+            rec[name] = r
+            del u0
+        out[f"{rows}x{n}"] = rec
+    return out
+
+
 def step_ic_bench(ctx, dev, rows: int = 4096, n: int = 4096, sample: int = 8):
     """Step-IC shock workload (Eq. 20, Sec. 3.4): `rows` Dirichlet rows of n
     nodes on [0, 1] from u0 = 1 left of x = 1/2 and 0 right of it (u(0) = 1,
@@ -724,6 +790,7 @@ def extras(args, ctx, ens, u0, batches, probe, dev, world, rank):
     out["implicit_variants"] = variants
     out["differentiation"] = differentiation_bench(ctx, dev)
     out["step_ic"] = step_ic_bench(ctx, dev)
+    out["short_rows_btcs"] = short_rows_bench(dev)
 
     # ---- plain one-row-per-launch path on a subset, same kernels
     P = 64

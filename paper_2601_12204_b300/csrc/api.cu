@@ -111,6 +111,10 @@ static const std::vector<Shape>& resident_shapes(int kind, int dtype) {
   return dtype == 0 ? bt32 : bt64;
 }
 
+// A capacity class needs at least this many rows in a call to take the
+// per-thread Thomas kernel by default (pick_thomas).
+constexpr int64_t THOMAS_DEFAULT_MIN_ROWS = 8192;
+
 static int64_t max_resident(int kind, int dtype) {
   int64_t m = 0;
   for (const Shape& s : resident_shapes(kind, dtype)) m = std::max<int64_t>(m, int64_t(s.nt) * s.c);
@@ -178,6 +182,37 @@ static Shape pick_resident(const burgers_ctx* ctx, int kind, int dtype, int64_t 
   // keep 256 x 16)
   if (kind == K_EXPLICIT_RESIDENT && dtype == 0 && cap == 4096 && n < cap) return Shape{128, 32};
   return best;
+}
+
+// BTCS rows of a capacity class whose tuning-table entry has k >= 1 take the
+// per-thread Thomas kernel (k - 1: its layout mode, btcs_thomas.cu); an
+// entry with k = 0 keeps the partitioned kernel. Without an entry, a class
+// takes it when its rows are short and many (class_rows rows in the call):
+// one thread per row needs thousands of rows to fill the GPU, and its
+// elimination chain grows with the row. Measured on a B300 (100 steps at
+// 10x the CFL step, cell-updates/s): FP32 16384 x 32 7.3e10 against 3.6e10
+// partitioned, 65536 x 64 1.2e11 against 7.5e10, but 4096 x 64 4.1e10
+// against 6.9e10 and 16384 x 128 1.1e11 against 1.5e11; FP64 16384 x 32
+// 9.6e9 against 3.0e9, 65536 x 64 1.2e10 against 5.2e9, 16384 x 128 1.2e10
+// against 8.2e9, 4096 x 64 3.5e9 against 5.1e9.
+const KernelEntry* pick_thomas(const burgers_ctx* ctx, int dtype, int64_t n, int64_t class_rows) {
+  if (ctx->plain) return nullptr;
+  const int64_t cap = resident_class(K_BTCS_RESIDENT, dtype, n);
+  if (cap <= 0) return nullptr;
+  auto it = ctx->tuned.find(tune_key(K_BTCS_RESIDENT, dtype, cap, cap == n));
+  if (it != ctx->tuned.end()) {
+    if (it->second.k <= 0) return nullptr;
+    const KernelEntry* k = find_kernel(K_BTCS_THOMAS, dtype, it->second.nt, it->second.c,
+                                       it->second.k - 1);
+    return k && k->c >= n ? k : nullptr;
+  }
+  if (class_rows < THOMAS_DEFAULT_MIN_ROWS) return nullptr;
+  struct Def { int dtype, cap, nt, mode; };
+  static const Def defs[] = {{0, 32, 256, 2}, {0, 64, 256, 0},
+                             {1, 32, 128, 0}, {1, 64, 64, 1}, {1, 128, 64, 1}};
+  for (const Def& d : defs)
+    if (d.dtype == dtype && d.cap == cap) return find_kernel(K_BTCS_THOMAS, dtype, d.nt, d.cap, d.mode);
+  return nullptr;
 }
 
 // FNV-1a over 64-bit words (then the tail bytes): the plan key hashes every
@@ -302,7 +337,18 @@ static burgers_status build_plan(burgers_ctx* ctx, int scheme, const burgers_bat
     std::vector<std::pair<double, int64_t>> rows;  // (cost, index)
   };
   std::vector<Grp> groups;
+  struct TGrp {
+    const KernelEntry* k;
+    std::vector<std::pair<double, int64_t>> rows;
+  };
+  std::vector<TGrp> tgroups;
   std::vector<int64_t> longs;
+  // rows per BTCS capacity class (the per-thread Thomas kernel needs many)
+  std::map<int64_t, int64_t> class_rows;
+  if (scheme == BURGERS_BTCS)
+    for (int64_t b = 0; b < batch->count; ++b)
+      if (batch->inst[b].nsteps > 0 && batch->inst[b].n <= rlim)
+        ++class_rows[resident_class(K_BTCS_RESIDENT, dtype, batch->inst[b].n)];
   for (int64_t b = 0; b < batch->count; ++b) {
     const burgers_instance& in = batch->inst[b];
     if (in.nsteps == 0) continue;
@@ -315,6 +361,22 @@ static burgers_status build_plan(burgers_ctx* ctx, int scheme, const burgers_bat
       longs.push_back(b);
       continue;
     }
+    if (scheme == BURGERS_BTCS) {
+      const int64_t cap = resident_class(K_BTCS_RESIDENT, dtype, in.n);
+      auto cr = class_rows.find(cap);
+      if (const KernelEntry* kt =
+              pick_thomas(ctx, dtype, in.n, cr == class_rows.end() ? 0 : cr->second)) {
+        TGrp* g = nullptr;
+        for (TGrp& x : tgroups)
+          if (x.k == kt) g = &x;
+        if (!g) {
+          tgroups.push_back(TGrp{kt, {}});
+          g = &tgroups.back();
+        }
+        g->rows.emplace_back(double(in.n) * double(in.nsteps), b);
+        continue;
+      }
+    }
     Shape sh = pick_resident(ctx, rkind, dtype, in.n);
     if (sh.nt == 0) return set_error(BURGERS_EINVAL, "no resident kernel shape fits the row");
     int exact = int64_t(sh.nt) * sh.c == in.n ? 1 : 0;
@@ -326,6 +388,24 @@ static burgers_status build_plan(burgers_ctx* ctx, int scheme, const burgers_bat
       g = &groups.back();
     }
     g->rows.emplace_back(double(in.n) * double(in.nsteps), b);
+  }
+  // per-thread Thomas groups: one CTA per nt cost-sorted rows
+  for (TGrp& g : tgroups) {
+    std::stable_sort(g.rows.begin(), g.rows.end(),
+                     [](const auto& a, const auto& b) { return a.first > b.first; });
+    const int begin = int(p->rows.size());
+    for (auto& pr : g.rows) {
+      p->rows.push_back(make_row(batch->inst[pr.second], iters));
+      p->row_inst.push_back(int32_t(pr.second));
+    }
+    Launch L;
+    L.k = g.k;
+    L.type = LAUNCH_THOMAS;
+    L.row_begin = begin;
+    L.row_count = int(g.rows.size());
+    L.grid = (L.row_count + g.k->nt - 1) / g.k->nt;
+    L.ws_elems = int64_t(L.grid) * int64_t(thomas_ws_values(dtype, g.k->nt, g.k->c, g.k->exact));
+    p->launches.push_back(L);
   }
   // resident groups
   for (Grp& g : groups) {
@@ -538,6 +618,12 @@ static burgers_status build_plan(burgers_ctx* ctx, int scheme, const burgers_bat
       }
     }
   }
+  // per-thread Thomas workspaces follow whatever the long rows use of the scratch
+  for (Launch& L : p->launches)
+    if (L.type == LAUNCH_THOMAS) {
+      L.ws_off = (p->scratch_elems + 63) & ~int64_t(63);
+      p->scratch_elems = L.ws_off + L.ws_elems;
+    }
   // device image: rows | items | counters (+ multilevel descriptors)
   size_t off = 0;
   auto align = [](size_t x) { return (x + 255) & ~size_t(255); };
@@ -642,6 +728,12 @@ static cudaError_t enqueue_plan(burgers_ctx* ctx, Plan* p, void* u, cudaStream_t
         }
       }
       e = cudaLaunchKernel(L.k->fn, dim3(L.grid), dim3(L.k->nt), args, L.k->dyn_smem, ls);
+    } else if (L.type == LAUNCH_THOMAS) {
+      RowDesc* r = rows + L.row_begin;
+      int cnt = L.row_count;
+      void* ws = static_cast<char*>(scratch) + size_t(L.ws_off) * esz;
+      void* args[] = {&u, &r, &cnt, &ws};
+      e = cudaLaunchKernel(L.k->fn, dim3(L.grid), dim3(L.k->nt), args, L.k->dyn_smem, st);
     } else if (L.type == LAUNCH_STREAM) {
       const void* src = L.to_scratch ? u : scratch;
       void* dst = L.to_scratch ? scratch : u;

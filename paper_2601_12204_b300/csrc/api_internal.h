@@ -38,7 +38,7 @@ struct HostBuf {
   ~HostBuf();
 };
 
-enum LaunchType : int { LAUNCH_RESIDENT = 0, LAUNCH_STREAM = 1, LAUNCH_ML = 2 };
+enum LaunchType : int { LAUNCH_RESIDENT = 0, LAUNCH_STREAM = 1, LAUNCH_ML = 2, LAUNCH_THOMAS = 3 };
 
 struct Launch {
   const KernelEntry* k = nullptr;
@@ -49,6 +49,7 @@ struct Launch {
   int item_begin = 0, item_count = 0;
   int K = 0;
   int nbulk = -1;  // bulk-copy single-step launch: items [0, nbulk) are whole aligned tiles
+  int64_t ws_off = 0, ws_elems = 0;  // per-thread Thomas launch: its workspace in the scratch
   const KernelEntry* k_fallback = nullptr;  // its per-tile kernel (unaligned buffers)
   int64_t step_base = 0;
   bool to_scratch = false;
@@ -180,6 +181,12 @@ burgers_status advance_uncached_pair(burgers_ctx* ctx, int scheme_a, const burge
                                      PlanScratch* ps_b, void* u_dev, cudaStream_t stream_a,
                                      cudaStream_t stream_b, cudaEvent_t fork, cudaEvent_t join);
 int64_t adjoint_max_n(int dtype);
+// Workspace values of one CTA of the per-thread Thomas kernel (btcs_thomas.cu).
+size_t thomas_ws_values(int dtype, int nt, int nmax, int mode);
+// The per-thread Thomas kernel a BTCS row of n nodes takes, or nullptr for the
+// partitioned resident kernel (tuning table first, then the default classes;
+// class_rows: rows of the row's capacity class in the call).
+const KernelEntry* pick_thomas(const burgers_ctx* ctx, int dtype, int64_t n, int64_t class_rows);
 int64_t resident_capacity(const burgers_ctx* ctx, int kind, int dtype);
 int64_t resident_class(int kind, int dtype, int64_t n);
 std::vector<std::pair<int, int>> resident_shape_list(int kind, int dtype);

@@ -31,6 +31,7 @@ enum KernelKind : int32_t {
   K_NEWTON_RESIDENT = 13,   // Newton on the Eq. 11 residual, whole row per CTA
   K_BTCS_CLUSTER = 14,      // lagged BTCS, row resident in a cluster of `exact` CTAs
   K_EXPLICIT_STEP1_BULK = 15,  // K_EXPLICIT_STEP1 over tiles moved by bulk copies, `exact` stages
+  K_BTCS_THOMAS = 16,       // lagged BTCS, one thread per row (Thomas), c = longest row
   K_KIND_COUNT
 };
 

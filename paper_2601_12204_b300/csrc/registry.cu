@@ -15,6 +15,7 @@ void register_btcs_cluster(std::vector<KernelEntry>& reg);
 void register_multilevel(std::vector<KernelEntry>& reg);
 void register_adjoint(std::vector<KernelEntry>& reg);
 void register_step1_bulk(std::vector<KernelEntry>& reg);
+void register_btcs_thomas(std::vector<KernelEntry>& reg);
 
 const std::vector<KernelEntry>& kernel_registry() {
   static std::vector<KernelEntry> reg;
@@ -29,6 +30,7 @@ const std::vector<KernelEntry>& kernel_registry() {
     register_multilevel(reg);
     register_adjoint(reg);
     register_step1_bulk(reg);
+    register_btcs_thomas(reg);
   });
   return reg;
 }

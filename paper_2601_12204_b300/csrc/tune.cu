@@ -22,6 +22,7 @@
 namespace burgers {
 
 constexpr int TUNE_ROWS = 512;
+constexpr int THOMAS_TUNE_ROWS = 65536;
 
 struct Cand {
   int nt, c, k;
@@ -77,6 +78,53 @@ static burgers_status time_resident(burgers_ctx* ctx, const KernelEntry* k,
   return BURGERS_OK;
 }
 
+// Times the per-thread Thomas kernel k over the same rows (one CTA per k->nt
+// rows, its workspace in the context's scratch buffer).
+static burgers_status time_thomas(burgers_ctx* ctx, const KernelEntry* k,
+                                  const std::vector<RowDesc>& rows, void* buf, const void* orig,
+                                  const std::vector<int64_t>& orig_off, size_t esz, int dtype,
+                                  cudaStream_t st, float* ms) {
+  DevBuf& d = ctx->tunews;
+  const size_t need = rows.size() * sizeof(RowDesc) + 256;
+  cudaError_t e = d.ensure(need);
+  if (e != cudaSuccess) return set_error(BURGERS_ENOMEM, "tune descriptors");
+  RowDesc* rd = reinterpret_cast<RowDesc*>(static_cast<char*>(d.ptr) + 256);
+  e = cudaMemcpyAsync(rd, rows.data(), rows.size() * sizeof(RowDesc), cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return cuda_error(e, "tune upload");
+  int cnt = int(rows.size());
+  const int grid = (cnt + k->nt - 1) / k->nt;
+  e = ctx->scratch.ensure(std::max<size_t>(1, size_t(grid) * thomas_ws_values(dtype, k->nt, k->c, k->exact) * esz));
+  if (e != cudaSuccess) return set_error(BURGERS_ENOMEM, "tune workspace");
+  void* ws = ctx->scratch.ptr;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best = 1e30f;
+  for (int rep = 0; rep < 3; ++rep) {
+    for (size_t i = 0; i < rows.size(); ++i) {  // fresh copy of the rows
+      e = cudaMemcpyAsync(static_cast<char*>(buf) + size_t(rows[i].offset) * esz,
+                          static_cast<const char*>(orig) + size_t(orig_off[i]) * esz,
+                          size_t(rows[i].n) * esz, cudaMemcpyDeviceToDevice, st);
+      if (e != cudaSuccess) break;
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+    void* args[] = {&buf, &rd, &cnt, &ws};
+    if (e == cudaSuccess) e = cudaLaunchKernel(k->fn, dim3(grid), dim3(k->nt), args, k->dyn_smem, st);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    if (e != cudaSuccess) break;
+    float t = 0.f;
+    cudaEventElapsedTime(&t, e0, e1);
+    if (rep > 0) best = std::min(best, t);  // first run warms up
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e != cudaSuccess) return cuda_error(e, "tune run");
+  ctx->launches += 3;
+  *ms = best;
+  return BURGERS_OK;
+}
+
 burgers_status autotune(burgers_ctx* ctx, int scheme, const burgers_batch* batch,
                         const void* u_dev, int64_t probe_steps, cudaStream_t st,
                         int* tuned_out) {
@@ -105,9 +153,19 @@ burgers_status autotune(burgers_ctx* ctx, int scheme, const burgers_batch* batch
     for (const auto& sh : resident_shape_list(kind, dtype))
       if (int64_t(sh.first) * sh.second == cap && find_kernel(kind, dtype, sh.first, sh.second, exact))
         cands.push_back(Cand{sh.first, sh.second, 0});
+    // BTCS: the per-thread Thomas kernels of this capacity (k = 1 + planes in
+    // the workspace)
+    if (scheme == BURGERS_BTCS && !ctx->plain)
+      for (const KernelEntry& e : kernel_registry())
+        if (e.kind == K_BTCS_THOMAS && e.dtype == dtype && e.c == cap)
+          cands.push_back(Cand{e.nt, e.c, 1 + e.exact});
     if (cands.size() < 2) continue;
     std::vector<int64_t>& ids = kv.second;
-    if (ids.size() > size_t(TUNE_ROWS)) ids.resize(TUNE_ROWS);
+    // the per-thread Thomas kernel's speed depends on how many rows fill the
+    // GPU: classes where it competes are probed with up to THOMAS_TUNE_ROWS
+    const bool thomas = std::any_of(cands.begin(), cands.end(), [](const Cand& c) { return c.k >= 1; });
+    const size_t probe_rows = thomas ? size_t(THOMAS_TUNE_ROWS) : size_t(TUNE_ROWS);
+    if (ids.size() > probe_rows) ids.resize(probe_rows);
     std::vector<RowDesc> rows;
     std::vector<int64_t> orig_off;
     int64_t off = 0;
@@ -131,9 +189,15 @@ burgers_status autotune(burgers_ctx* ctx, int scheme, const burgers_batch* batch
     float best = 1e30f;
     Cand pick = cands[0];
     for (const Cand& c : cands) {
-      const KernelEntry* k = find_kernel(kind, dtype, c.nt, c.c, exact);
       float ms = 0.f;
-      burgers_status s2 = time_resident(ctx, k, rows, ctx->tunebuf.ptr, u_dev, orig_off, esz, st, &ms);
+      burgers_status s2;
+      if (c.k >= 1) {
+        const KernelEntry* k = find_kernel(K_BTCS_THOMAS, dtype, c.nt, c.c, c.k - 1);
+        s2 = time_thomas(ctx, k, rows, ctx->tunebuf.ptr, u_dev, orig_off, esz, dtype, st, &ms);
+      } else {
+        const KernelEntry* k = find_kernel(kind, dtype, c.nt, c.c, exact);
+        s2 = time_resident(ctx, k, rows, ctx->tunebuf.ptr, u_dev, orig_off, esz, st, &ms);
+      }
       if (s2 != BURGERS_OK) return s2;
       if (ms < best) {
         best = ms;
@@ -143,7 +207,7 @@ burgers_status autotune(burgers_ctx* ctx, int scheme, const burgers_batch* batch
     TuneVal tv;
     tv.nt = pick.nt;
     tv.c = pick.c;
-    tv.k = 0;
+    tv.k = pick.k;
     ctx->tuned[tune_key(kind, dtype, cap, exact)] = tv;
     ++ntuned;
   }
@@ -295,7 +359,11 @@ burgers_status burgers_tune_load(burgers_ctx* ctx, const char* path) {
     }
     const int kind = int(key >> 56), dtype = int((key >> 52) & 0xf), exact = int((key >> 48) & 0xf);
     const int exact_lookup = kind == K_EXPLICIT_STREAM ? 0 : exact;
-    if (!find_kernel(kind, dtype, v.nt, v.c, exact_lookup) || v.k < 0 || v.k > 64) {
+    // a BTCS class entry with k >= 1 names a per-thread Thomas kernel
+    const bool thomas = kind == K_BTCS_RESIDENT && v.k >= 1;
+    const bool known = thomas ? find_kernel(K_BTCS_THOMAS, dtype, v.nt, v.c, v.k - 1) != nullptr
+                              : find_kernel(kind, dtype, v.nt, v.c, exact_lookup) != nullptr;
+    if (!known || v.k < 0 || v.k > 64) {
       fclose(f);
       return set_error(BURGERS_EINVAL, "tuning table names a kernel shape that does not exist");
     }

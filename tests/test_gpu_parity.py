@@ -555,3 +555,84 @@ def test_ensemble_4096x4096_bench_launch(ctx, scheme):
     for j, bi in enumerate(ids):
         o, so = int(ens.offsets[bi]), int(sub.offsets[j])
         assert oracle.rel_l2(got[o:o + 4096], ref[so:so + 4096]) <= 1e-5
+
+
+# a partitioned resident BTCS shape of each capacity class
+PARTITIONED_SHAPE = {32: (32, 1), 64: (32, 2), 128: (32, 4), 256: (32, 8), 512: (64, 8),
+                     1024: (128, 8), 2048: (128, 16)}
+# (dtype, threads, longest row, layout mode) of every registered per-thread
+# Thomas kernel
+THOMAS_VARIANTS = [(F32, 256, 32, 0), (F32, 256, 64, 0), (F32, 128, 128, 0), (F32, 64, 256, 0),
+                   (F32, 64, 128, 1), (F32, 64, 256, 1), (F32, 64, 512, 1), (F32, 64, 1024, 1),
+                   (F32, 64, 2048, 1), (F32, 256, 32, 2), (F32, 128, 64, 2), (F32, 64, 128, 2),
+                   (F32, 32, 256, 2), (F64, 128, 32, 0), (F64, 128, 64, 0), (F64, 64, 128, 0),
+                   (F64, 64, 64, 1), (F64, 64, 128, 1), (F64, 64, 256, 1), (F64, 64, 512, 1),
+                   (F64, 64, 1024, 1), (F64, 128, 32, 2), (F64, 64, 64, 2), (F64, 32, 128, 2)]
+
+
+@pytest.mark.parametrize("variant", THOMAS_VARIANTS, ids=lambda v: f"d{v[0]}_{v[1]}x{v[2]}g{v[3]}")
+def test_thomas_per_thread_btcs(ctx, variant, tmp_path):
+    """BTCS rows through the per-thread Thomas kernel (one thread per row, no
+    barrier; forced for the capacity class through the tuning table): 2 nt + 7
+    rows of ragged lengths in the class (the class of 32 from n = 3), so
+    several CTAs and a partial last one, both BCs, ragged step counts, against
+    the oracle; the same rows through the partitioned kernel agree too."""
+    dtype, nt, nmax, g = variant
+    _fresh(ctx)
+    rng = np.random.default_rng(nmax + 7 * nt + g)
+    lo = 3 if nmax == 32 else nmax // 2 + 1
+    lens = list(rng.integers(lo, nmax + 1, 2 * nt + 7)) + [nmax, lo]
+    parts = [_one(int(n), int(i % 2), seed=int(n) + 1000 * i) for i, n in enumerate(lens)]
+    ens = _concat(parts)
+    dts = oracle_dts(ens, 6.0)
+    steps = rng.integers(0, 25, ens.count)
+    key = lambda ex: (2 << 56) ^ (dtype << 52) ^ (ex << 48) ^ nmax  # noqa: E731  K_BTCS_RESIDENT class
+    path = tmp_path / "thomas.txt"
+    path.write_text(f"# thomas\n{key(0)} {nt} {nmax} {1 + g}\n{key(1)} {nt} {nmax} {1 + g}\n")
+    ctx.tune_load(str(path))
+    try:
+        got = run_gpu(ctx, BTCS, ens, dts, steps, dtype)
+    finally:  # the partitioned kernel for this class again (a one-warp shape of its capacity)
+        pt, pc = PARTITIONED_SHAPE[nmax]
+        path.write_text(f"# partitioned\n{key(0)} {pt} {pc} 0\n{key(1)} {pt} {pc} 0\n")
+        ctx.tune_load(str(path))
+    ref = run_oracle(BTCS, ens, dts, steps)
+    assert_parity(ens, got, ref, dtype, f"thomas {variant}")
+    part = run_gpu(ctx, BTCS, ens, dts, steps, dtype)
+    assert_parity(ens, part, ref, dtype, f"partitioned, class {nmax}")
+
+
+@pytest.mark.parametrize("dtype", [F64, F32])
+def test_thomas_default_routing(dtype):
+    """A call with many short BTCS rows takes the per-thread Thomas kernel by
+    default (classes of 32 and 64 nodes with at least 8192 rows), mixed with
+    longer rows that keep the partitioned kernel; sampled rows of every length
+    against the oracle (a fresh context: no tuning-table entries)."""
+    import torch
+
+    from paper_2601_12204_b300.api import Batch, Context
+    rng = np.random.default_rng(41)
+    lens = list(rng.integers(17, 65, 9000)) + list(rng.integers(300, 900, 40))
+    offs = np.zeros(len(lens), np.int64)
+    offs[1:] = np.cumsum(lens[:-1])
+    x = np.concatenate([W.grid(int(n), i % 2, 0.0, W.TWO_PI)[0] for i, n in enumerate(lens)])
+    u0 = np.sin(x) + 0.3 * np.cos(3 * x + 0.2)
+    ens = W.Ensemble(u0, offs, np.array(lens, np.int32), np.arange(len(lens), dtype=np.int32) % 2,
+                     np.array([W.grid(int(n), i % 2, 0.0, W.TWO_PI)[1] for i, n in enumerate(lens)]),
+                     rng.uniform(1e-3, 5e-2, len(lens)), np.zeros(len(lens)), np.full(len(lens), W.TWO_PI))
+    dts = oracle_dts(ens, 6.0)
+    steps = rng.integers(1, 20, len(lens))
+    c = Context(0)
+    try:
+        tdt = torch.float32 if dtype == F32 else torch.float64
+        u = torch.tensor(ens.u0, dtype=tdt, device="cuda")
+        c.btcs_advance(Batch.from_ensemble(ens, dts, steps, dtype), u)
+        torch.cuda.synchronize()
+        got = u.cpu().double().numpy()
+    finally:
+        c.close()
+    ids = np.concatenate([rng.choice(9000, 60, replace=False), np.arange(9000, 9040)])
+    sub = ens.subset(ids)
+    ref = run_oracle(BTCS, sub, dts[ids], steps[ids])
+    g = np.concatenate([got[offs[i]:offs[i] + lens[i]] for i in ids])
+    assert_parity(sub, g, ref, dtype, "default routing")
