@@ -211,15 +211,18 @@ burgers_status burgers_rk4_advance(burgers_ctx* ctx, const burgers_batch* batch,
  *   (I - dt/2 L(u^n)) u^{n+1} = (I + dt/2 L(u^n)) u^n,
  * L the upwind/central operator of Eq. 21 (so the rows are those of
  * burgers_btcs_advance with r/2 and s/2). Rows up to the resident capacity
- * (8192 nodes FP32, 4096 FP64); longer rows: EINVAL. In place, layout,
- * ownership and errors as burgers_btcs_advance. */
+ * (8192 nodes FP32, 4096 FP64) stay in one CTA; longer rows, of any length,
+ * go through the multi-level partitioned solver of the long BTCS rows, with
+ * the same rows at its first level. In place, layout, ownership and errors as
+ * burgers_btcs_advance. */
 burgers_status burgers_cn_advance(burgers_ctx* ctx, const burgers_batch* batch, void* u_dev,
                                   burgers_stream stream);
 
 /* Fully implicit upwind step solved by `iters` Picard iterations per step,
  * A(w) w' = u^n from w = u^n, with A as in burgers_btcs_advance but its
  * coefficients taken from the latest iterate (iters = 1 is the lagged BTCS
- * step). iters in [1, 64], else EINVAL. Row limits as burgers_cn_advance. */
+ * step). iters in [1, 64], else EINVAL. Long rows as burgers_cn_advance
+ * (each iteration one multi-level solve). */
 burgers_status burgers_picard_advance(burgers_ctx* ctx, const burgers_batch* batch, void* u_dev,
                                       int32_t iters, burgers_stream stream);
 
@@ -232,8 +235,8 @@ burgers_status burgers_picard_advance(burgers_ctx* ctx, const burgers_batch* bat
  * its diffusive part garbled). Dirichlet ends held. No pivoting: the Jacobian
  * is strictly diagonally dominant while r max|w| < 1/2 (dt below half the
  * convective CFL limit dx/max|u|); beyond that it may not be, and the solve is
- * then not guaranteed. iters in [1, 64], else EINVAL. Row limits as
- * burgers_cn_advance. */
+ * then not guaranteed. iters in [1, 64], else EINVAL. Long rows as
+ * burgers_cn_advance (each iteration one multi-level solve). */
 burgers_status burgers_newton_advance(burgers_ctx* ctx, const burgers_batch* batch, void* u_dev,
                                       int32_t iters, burgers_stream stream);
 
@@ -311,7 +314,8 @@ burgers_status burgers_cfl_dt_device(burgers_ctx* ctx, const burgers_batch* batc
  * those of the host-dt entry point with dt = dt_factor * dt_dev[b]. Plans are
  * cached as for the host-dt calls (keyed by the batch without its dt). Rows
  * that need the multi-level solver (BTCS rows longer than the cluster limit,
- * FP64 BTCS rows longer than one CTA): EINVAL. dt_factor <= 0: EINVAL. */
+ * FP64 BTCS rows longer than one CTA, CN, Picard and Newton rows longer than
+ * the resident capacity): EINVAL. dt_factor <= 0: EINVAL. */
 burgers_status burgers_advance_dt_device(burgers_ctx* ctx, int32_t scheme,
                                          const burgers_batch* batch, void* u_dev,
                                          const double* dt_dev, double dt_factor, int32_t iters,

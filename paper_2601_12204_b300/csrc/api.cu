@@ -329,7 +329,7 @@ static burgers_status build_plan(burgers_ctx* ctx, int scheme, const burgers_bat
   p->dtype = dtype;
   p->scheme = scheme;
   const int rkind = resident_kind(scheme);
-  const bool stencil = scheme != BURGERS_BTCS;  // explicit Euler or RK4
+  const bool stencil = scheme == BURGERS_EXPLICIT || scheme == BURGERS_RK4;
   const int64_t rlim = resident_limit(ctx, rkind, dtype);
   struct Grp {
     Shape sh;
@@ -613,7 +613,11 @@ static burgers_status build_plan(burgers_ctx* ctx, int scheme, const burgers_bat
         }
       }
       if (!mlrows.empty()) {
-        burgers_status st = plan_multilevel(ctx, batch, mlrows, p);
+        const int var = scheme == BURGERS_CN       ? 1
+                        : scheme == BURGERS_PICARD ? 2
+                        : scheme == BURGERS_NEWTON ? 3
+                                                   : 0;
+        burgers_status st = plan_multilevel(ctx, batch, mlrows, p, var, iters);
         if (st != BURGERS_OK) return st;
       }
     }

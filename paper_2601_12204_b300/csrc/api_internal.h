@@ -55,6 +55,7 @@ struct Launch {
   bool to_scratch = false;
   int level = 0;   // multi-level: level of a reduce/recover launch
   int ml_phase = 0;
+  int iter = 0;    // multi-level: iteration of the step (Picard, Newton)
 };
 
 struct Plan {
@@ -73,6 +74,7 @@ struct Plan {
   int64_t stream_span = 0;    // elements covered by the streaming rows
   int64_t ml_span = 0;        // elements covered by the multi-level rows
   int64_t ml_ws_elems = 0;    // multi-level workspace, elements
+  int64_t ml_e_off = 0;       // multi-level: scratch offset of the two e planes, elements
   void* dev = nullptr;
   bool dev_external = false;
   size_t rows_off = 0, items_off = 0, counters_off = 0, ml_off = 0, dev_bytes = 0;
@@ -151,8 +153,10 @@ struct burgers_ctx {
 };
 
 namespace burgers {
+// var: 0 lagged BTCS, 1 Crank-Nicolson, 2 Picard, 3 Newton; iters: iterations
+// per step of the last two.
 burgers_status plan_multilevel(burgers_ctx* ctx, const burgers_batch* batch,
-                               const std::vector<int64_t>& longs, Plan* p);
+                               const std::vector<int64_t>& longs, Plan* p, int var, int iters);
 cudaError_t enqueue_multilevel_launch(burgers_ctx* ctx, Plan* p, const Launch& L, void* u,
                                       cudaStream_t st);
 // Resident kernel kind of a scheme (burgers_scheme).
@@ -167,10 +171,9 @@ inline int resident_kind(int scheme) {
   }
 }
 inline bool valid_scheme(int scheme) { return scheme >= BURGERS_EXPLICIT && scheme <= BURGERS_NEWTON; }
-// Schemes whose long rows have a streaming / multi-level path.
-inline bool has_long_path(int scheme) {
-  return scheme == BURGERS_EXPLICIT || scheme == BURGERS_RK4 || scheme == BURGERS_BTCS;
-}
+// Every scheme has a path for long rows: streaming windows (explicit Euler,
+// RK4) or the multi-level solver (BTCS and the implicit variants).
+inline bool has_long_path(int scheme) { return valid_scheme(scheme); }
 
 burgers_status advance(burgers_ctx* ctx, int scheme, const burgers_batch* batch, void* u_dev,
                        cudaStream_t stream, int iters = 1);

@@ -34,7 +34,10 @@ struct MLRow {
   int64_t offset;
   int64_t nsteps;
   double r, s;
-  int32_t n, bc, levels, pad;
+  int32_t n, bc, levels;
+  int32_t var;    // 0 lagged BTCS, 1 Crank-Nicolson, 2 Picard, 3 Newton (level-0 rows)
+  int32_t iters;  // iterations per step (Picard, Newton; else 1)
+  int32_t pad1, pad2, pad3;
   int64_t m[ML_MAXL + 1];   // rows per level, m[0] = n
   int64_t ef[ML_MAXL];      // workspace offset of the six chunk arrays of level l
   int64_t x[ML_MAXL + 1];   // workspace offset of the solution of level l >= 1
@@ -95,7 +98,9 @@ __global__ void __launch_bounds__(NT) k_ml_sweep(T* __restrict__ u, T* __restric
                                                  T* __restrict__ lo, T* __restrict__ ws,
                                                  const MLRow* __restrict__ rows,
                                                  const TileItem* __restrict__ items, int nitems,
-                                                 int level, int64_t step) {
+                                                 int level, int64_t step, int iter,
+                                                 T* __restrict__ ea, T* __restrict__ eb) {
+  (void)iter; (void)ea; (void)eb;
   T* src = (step & 1) ? u2 : u;
   T* dst = (step & 1) ? u : u2;
   for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
@@ -156,6 +161,132 @@ __global__ void __launch_bounds__(NT) k_ml_sweep(T* __restrict__ u, T* __restric
         for (int j = 0; j < C; ++j)
           if (j <= je) out[base + j] = tfma(-ch[j], Xk, tfma(-ah[j], L, v[j]));
       }
+    }
+  }
+}
+
+// Level-0 rows of the implicit variants that share the tridiagonal shape
+// (Crank-Nicolson, Picard, Newton; see btcs_kernel.cuh for their algebra),
+// in increment form: CN from u^n with r/2, s/2 and the full explicit
+// increment; Picard and Newton from the iterate w = u^n + e (e = 0 in the
+// first iteration), right-hand side Delta(w) - e (Picard) or -F(w) of Eq. 11
+// (Newton).
+template <typename T>
+struct VarRows {
+  const T* row;  // u^n
+  const T* e;    // e of this iteration (nullptr: zero)
+  int64_t n;
+  int64_t base;
+  int je;
+  T r, s;
+  int var;
+  bool dir;
+  __device__ __forceinline__ T w(int64_t i) const { return e ? row[i] + e[i] : row[i]; }
+  __device__ __forceinline__ void operator()(int j, T& l, T& d, T& c, T& rhs) const {
+    const int64_t gi = base + j;
+    if (j > je) { l = T(0); d = T(1); c = T(0); rhs = T(0); return; }
+    const int64_t il = gi == 0 ? n - 1 : gi - 1, ir = gi == n - 1 ? 0 : gi + 1;
+    if (var == 1) {  // Crank-Nicolson: half the coefficients, the full step's increment
+      const T a = row[gi], ul = row[il], ur = row[ir];
+      const T rm = T(0.5) * r, sm = T(0.5) * s;
+      const T ra = rm * a;
+      l = -sm - tmax(ra, T(0));
+      c = tmin(ra, T(0)) - sm;
+      d = T(1) + T(2) * sm + tabs(ra);
+      rhs = T(2) * tfma(l, a - ul, -c * (ur - a));
+    } else {
+      const T a = w(gi), ul = w(il), ur = w(ir);
+      const T ei = e ? e[gi] : T(0);
+      if (var == 3) {  // Newton on the Eq. 11 residual (central convection)
+        const T hr = T(0.5) * r, ha = hr * a;
+        l = -ha - s;
+        c = ha - s;
+        d = tfma(hr, ur - ul, T(1) + T(2) * s);
+        rhs = tfma(s, (ur - a) - (a - ul), tfma(-ha, ur - ul, -ei));
+      } else {  // Picard: the lagged rows of the latest iterate
+        const T ra = r * a;
+        l = -s - tmax(ra, T(0));
+        c = tmin(ra, T(0)) - s;
+        d = T(1) + T(2) * s + tabs(ra);
+        rhs = tfma(l, a - ul, -c * (ur - a)) - ei;
+      }
+    }
+    if (dir && (gi == 0 || gi == n - 1)) { l = T(0); c = T(0); d = T(1); rhs = T(0); }
+  }
+};
+
+// Level-0 sweep of the implicit variants (element loads, no staging).
+// Iteration `iter` of a step reads e from ea (even iterations after the
+// first) or eb (odd ones) and, unless it is the step's last iteration, writes
+// e + delta to the other buffer; the last iteration's recover sweep writes
+// u^{n+1} = u^n + (e + delta) (FP32: Kahan term in place) into the step's
+// other u buffer and copies finished rows through, as the BTCS sweeps do.
+template <typename T, int NT, int C, bool RECOVER>
+__global__ void __launch_bounds__(NT) k_ml_sweep0v(T* __restrict__ u, T* __restrict__ u2,
+                                                   T* __restrict__ lo, T* __restrict__ ws,
+                                                   const MLRow* __restrict__ rows,
+                                                   const TileItem* __restrict__ items, int nitems,
+                                                   int level, int64_t step, int iter,
+                                                   T* __restrict__ ea, T* __restrict__ eb) {
+  (void)level;
+  T* src = (step & 1) ? u2 : u;
+  T* dst = (step & 1) ? u : u2;
+  const T* ecur = iter == 0 ? nullptr : ((iter & 1) ? ea : eb);
+  T* enext = (iter & 1) ? eb : ea;
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const TileItem ti = items[it];
+    const MLRow& R = rows[ti.row];
+    const int64_t M = R.m[0];
+    const int64_t base = int64_t(ti.tile) * (NT * C) + int64_t(threadIdx.x) * C;
+    if (base >= M) continue;
+    const int je = int(M - 1 - base < int64_t(C - 1) ? M - 1 - base : int64_t(C - 1));
+    if (iter >= R.iters) continue;
+    const bool lastit = iter + 1 == R.iters;
+    if (step >= R.nsteps) {
+      if constexpr (RECOVER) {
+        if (lastit) {
+#pragma unroll
+          for (int j = 0; j < C; ++j)
+            if (j <= je) dst[R.offset + base + j] = src[R.offset + base + j];
+        }
+      }
+      continue;
+    }
+    T v[C], ah[C], ch[C];
+    T e_ch, e_ah, e_dh;
+    VarRows<T> rsrc{src + R.offset, ecur ? ecur + R.offset : nullptr, M, base, je,
+                    T(R.r), T(R.s), R.var, R.bc == BC_DIRICHLET};
+    chunk_forward<T, C>(v, ah, ch, je, rsrc, e_ch, e_ah, e_dh);
+    chunk_backward<T, C>(v, ah, ch, je);
+    const int64_t k = base / C;
+    const int64_t Mn = R.m[1];
+    if constexpr (!RECOVER) {
+      T* Eo = ws + R.ef[0];
+      Eo[k] = e_ch;
+      Eo[Mn + k] = e_ah;
+      Eo[2 * Mn + k] = e_dh;
+      Eo[3 * Mn + k] = v[0];
+      Eo[4 * Mn + k] = ah[0];
+      Eo[5 * Mn + k] = ch[0];
+    } else {
+      const T* Xn = ws + R.x[1];
+      const T L = k > 0 ? Xn[k - 1] : (R.bc == BC_PERIODIC ? Xn[Mn - 1] : T(0));
+      const T Xk = Xn[k];
+      const int64_t o = R.offset + base;
+#pragma unroll
+      for (int j = 0; j < C; ++j)
+        if (j <= je) {
+          const T delta = tfma(-ch[j], Xk, tfma(-ah[j], L, v[j]));
+          const T inc = ecur ? ecur[o + j] + delta : delta;
+          if (!lastit) {
+            enext[o + j] = inc;
+          } else {
+            T l0 = T(0);
+            if constexpr (Kahan<T>::on) l0 = lo[o + j];
+            dst[o + j] = comp_add(src[o + j], inc, l0);
+            if constexpr (Kahan<T>::on) lo[o + j] = l0;
+          }
+        }
     }
   }
 }
@@ -263,7 +394,8 @@ template <typename T, int NT, int C, bool RECOVER>
 __global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? 768 : 512) / NT)
     k_ml_sweep0(T* __restrict__ u, T* __restrict__ u2, T* __restrict__ lo, T* __restrict__ ws,
                 const MLRow* __restrict__ rows, const TileItem* __restrict__ items, int nitems,
-                int level, int64_t step) {
+                int level, int64_t step, int iter, T* __restrict__ ea, T* __restrict__ eb) {
+  (void)iter; (void)ea; (void)eb;
   using SM = Sweep0Smem<T, NT, C>;
   constexpr int TILE = SM::TILE, VE = SM::VE, SSK = SM::SSK;
   constexpr bool KL = RECOVER && Kahan<T>::on;
@@ -468,8 +600,9 @@ __global__ void __launch_bounds__(NT) k_ml_copy(T* __restrict__ u, T* __restrict
                                                 T* __restrict__ lo, T* __restrict__ ws,
                                                 const MLRow* __restrict__ rows,
                                                 const TileItem* __restrict__ items, int nitems,
-                                                int level, int64_t step) {
-  (void)lo; (void)ws; (void)level; (void)step;
+                                                int level, int64_t step, int iter,
+                                                T* __restrict__ ea, T* __restrict__ eb) {
+  (void)lo; (void)ws; (void)level; (void)step; (void)iter; (void)ea; (void)eb;
   for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
     const TileItem ti = items[it];
     const MLRow& R = rows[ti.row];
@@ -485,9 +618,10 @@ __global__ void __launch_bounds__(NT) k_ml_top(T* __restrict__ u, T* __restrict_
                                                T* __restrict__ lo, T* __restrict__ ws,
                                                const MLRow* __restrict__ rows,
                                                const TileItem* __restrict__ items, int nitems,
-                                               int level, int64_t step) {
+                                               int level, int64_t step, int iter,
+                                               T* __restrict__ ea, T* __restrict__ eb) {
   __shared__ BtcsShared<T, NT> sm;
-  (void)u; (void)u2; (void)lo;
+  (void)u; (void)u2; (void)lo; (void)iter; (void)ea; (void)eb;
   (void)level;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
@@ -548,6 +682,11 @@ __global__ void __launch_bounds__(NT) k_ml_top(T* __restrict__ u, T* __restrict_
                  Sweep0Smem<T, NT, C>::bytes(true)});                                         \
   reg.push_back({K_BTCS_RECOVER, DT, NT, C, 0,                                                \
                  reinterpret_cast<const void*>(&k_ml_sweep<T, NT, C, false, true>), 0});
+#define REG_SWEEPV(T, DT, NT, C)                                                             \
+  reg.push_back({K_BTCS_REDUCE, DT, NT, C, 2,                                                 \
+                 reinterpret_cast<const void*>(&k_ml_sweep0v<T, NT, C, false>), 0});         \
+  reg.push_back({K_BTCS_RECOVER, DT, NT, C, 2,                                                \
+                 reinterpret_cast<const void*>(&k_ml_sweep0v<T, NT, C, true>), 0});
 #define REG_TOP(T, DT, NT, C) \
   reg.push_back({K_BTCS_TOP, DT, NT, C, 0, reinterpret_cast<const void*>(&k_ml_top<T, NT, C>), 0});
 #define REG_COPY(T, DT, NT, C) \
@@ -556,6 +695,7 @@ __global__ void __launch_bounds__(NT) k_ml_top(T* __restrict__ u, T* __restrict_
 void register_multilevel(std::vector<KernelEntry>& reg) {
   REG_SWEEP(float, 0, 256, 16) REG_SWEEP(float, 0, 128, 8)
   REG_SWEEP(double, 1, 256, 8) REG_SWEEP(double, 1, 128, 4)
+  REG_SWEEPV(float, 0, 256, 16) REG_SWEEPV(double, 1, 256, 8)
   REG_TOP(float, 0, 32, 1) REG_TOP(float, 0, 32, 4) REG_TOP(float, 0, 128, 8)
   REG_TOP(float, 0, 256, 16)
   REG_TOP(double, 1, 32, 1) REG_TOP(double, 1, 32, 4) REG_TOP(double, 1, 128, 8)
@@ -577,14 +717,16 @@ const TopShape kTop64[] = {{32, 1}, {32, 4}, {128, 8}, {256, 8}};
 static int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
 burgers_status plan_multilevel(burgers_ctx* ctx, const burgers_batch* batch,
-                               const std::vector<int64_t>& longs, Plan* p) {
+                               const std::vector<int64_t>& longs, Plan* p, int var, int iters) {
   const int dtype = batch->dtype;
+  const int nit = (var == 2 || var == 3) ? iters : 1;
   const int snt = 256, sc = dtype == 0 ? 16 : 8;  // sweep shape
   const TopShape* tops = dtype == 0 ? kTop32 : kTop64;
   const int64_t top_cap = int64_t(tops[3].nt) * tops[3].c;
-  const KernelEntry* red0 = find_kernel(K_BTCS_REDUCE, dtype, snt, sc, 1);
+  // level 0: the staged BTCS sweeps, or the implicit variants' own rows
+  const KernelEntry* red0 = find_kernel(K_BTCS_REDUCE, dtype, snt, sc, var ? 2 : 1);
   const KernelEntry* red1 = find_kernel(K_BTCS_REDUCE, dtype, snt, sc, 0);
-  const KernelEntry* rec0 = find_kernel(K_BTCS_RECOVER, dtype, snt, sc, 1);
+  const KernelEntry* rec0 = find_kernel(K_BTCS_RECOVER, dtype, snt, sc, var ? 2 : 1);
   const KernelEntry* rec1 = find_kernel(K_BTCS_RECOVER, dtype, snt, sc, 0);
   if (!red0 || !red1 || !rec0 || !rec1) return set_error(BURGERS_EINVAL, "multi-level kernels missing");
   std::vector<MLRow> mrows;
@@ -602,6 +744,8 @@ burgers_status plan_multilevel(burgers_ctx* ctx, const burgers_batch* batch,
     R.s = in.nu * in.dt / (in.dx * in.dx);
     R.n = in.n;
     R.bc = in.bc;
+    R.var = var;
+    R.iters = nit;
     R.m[0] = in.n;
     int L = 0;
     while (L == 0 || R.m[L] > top_cap) {
@@ -629,8 +773,11 @@ burgers_status plan_multilevel(burgers_ctx* ctx, const burgers_batch* batch,
   for (const MLRow& R : mrows) span = std::max<int64_t>(span, R.offset + R.n);
   span = (span + 63) & ~int64_t(63);  // aligned start of the Kahan buffer
   p->ml_span = span;
-  // ping-pong copy of the rows (+ the Kahan terms for FP32)
-  p->scratch_elems = std::max<int64_t>(p->scratch_elems, dtype == 0 ? 2 * span : span);
+  // ping-pong copy of the rows (+ the Kahan terms for FP32), then for the
+  // iterating variants two planes of e = w - u^n (read by one iteration,
+  // written by it for the next)
+  p->ml_e_off = dtype == 0 ? 2 * span : span;
+  p->scratch_elems = std::max<int64_t>(p->scratch_elems, p->ml_e_off + (nit > 1 ? 2 * span : 0));
   p->ml_bytes.resize(mrows.size() * sizeof(MLRow));
   memcpy(p->ml_bytes.data(), mrows.data(), p->ml_bytes.size());
   // item lists: sweeps of each level, then one list per top shape
@@ -672,7 +819,8 @@ burgers_status plan_multilevel(burgers_ctx* ctx, const burgers_batch* batch,
       b = 1;
     return std::max(1, std::min(nitems, ctx->sm_count * b));
   };
-  for (int64_t s = 0; s < smax; ++s) {
+  for (int64_t s = 0; s < smax; ++s)
+  for (int it = 0; it < nit; ++it) {
     for (int l = 0; l < Lmax; ++l) {
       Launch L;
       L.type = LAUNCH_ML;
@@ -682,6 +830,7 @@ burgers_status plan_multilevel(burgers_ctx* ctx, const burgers_batch* batch,
       L.grid = grid_for(L.k, L.item_count);
       L.level = l;
       L.step_base = s;
+      L.iter = it;
       p->launches.push_back(L);
     }
     for (const TopGroup& g : tgroups) {
@@ -693,6 +842,7 @@ burgers_status plan_multilevel(burgers_ctx* ctx, const burgers_batch* batch,
       L.grid = g.count;
       L.level = 0;
       L.step_base = s;
+      L.iter = it;
       p->launches.push_back(L);
     }
     for (int l = Lmax - 1; l >= 0; --l) {
@@ -704,6 +854,7 @@ burgers_status plan_multilevel(burgers_ctx* ctx, const burgers_batch* batch,
       L.grid = grid_for(L.k, L.item_count);
       L.level = l;
       L.step_base = s;
+      L.iter = it;
       p->launches.push_back(L);
     }
   }
@@ -733,9 +884,12 @@ cudaError_t enqueue_multilevel_launch(burgers_ctx* ctx, Plan* p, const Launch& L
   const TileItem* items = reinterpret_cast<const TileItem*>(base + p->items_off) + L.item_begin;
   // the staged sweeps copy row records in 16-byte pieces
   if (reinterpret_cast<uintptr_t>(rows) & 15) return cudaErrorMisalignedAddress;
-  int ni = L.item_count, level = L.level;
+  int ni = L.item_count, level = L.level, iter = L.iter;
   int64_t step = L.step_base;
-  void* args[] = {&u, &u2, &lo, &ws, &rows, &items, &ni, &level, &step};
+  // e planes of the iterating variants (unused by the other launches)
+  void* ea = static_cast<char*>(ctx->scratch.ptr) + size_t(p->ml_e_off) * esz;
+  void* eb = static_cast<char*>(ea) + size_t(p->ml_span) * esz;
+  void* args[] = {&u, &u2, &lo, &ws, &rows, &items, &ni, &level, &step, &iter, &ea, &eb};
   return cudaLaunchKernel(L.k->fn, dim3(L.grid), dim3(L.k->nt), args, L.k->dyn_smem, st);
 }
 

@@ -140,9 +140,69 @@ def test_newton_converges_on_the_gpu(ctx):
         assert np.max(np.abs(f)) <= 1e-13
 
 
+# Rows beyond the resident capacity (8192 nodes FP32, 4096 FP64): one and two
+# reduction levels of the multi-level solver (FP32 chunks of 16 nodes and a
+# top level of up to 4096 rows: 9000 and 33000 one level, 70001 two; FP64
+# chunks of 8 and tops of up to 2048 rows: 9000 one level, 33000 and 70001 two).
+LONG_NS = (9000, 33000, 70001)
+
+
+@pytest.mark.parametrize("scheme,iters,fac", CASES)
+@pytest.mark.parametrize("dtype", [F64, F32])
+def test_long_rows_multilevel(ctx, scheme, iters, fac, dtype):
+    """Long rows of every variant, both BCs, ragged step counts, through the
+    multi-level solver against the oracle."""
+    _fresh(ctx)
+    ens = _resolved(_concat([_one(n, bc, seed=n + 5 * bc) for n in LONG_NS for bc in (0, 1)]),
+                    scheme)
+    dts = oracle_dts(ens, fac)
+    steps = np.array([12, 9, 20, 7, 15, 11])
+    got = run_gpu(ctx, scheme, ens, dts, steps, dtype, iters=iters)
+    ref = run_oracle(scheme, ens, dts, steps, iters=iters)
+    assert_parity(ens, got, ref, dtype, f"long s{scheme} it{iters}")
+
+
+@pytest.mark.parametrize("scheme,iters,fac", CASES)
+@pytest.mark.parametrize("dtype", [F64, F32])
+def test_short_rows_forced_multilevel(ctx, scheme, iters, fac, dtype):
+    """With the resident limit set to 64 nodes, rows of 100 to 5000 nodes go
+    through the multi-level solver too (every top-level shape, rows whose
+    steps end at different times, a row with no steps)."""
+    _fresh(ctx)
+    ctx.set(L.BURGERS_OPT_RESIDENT_MAX, 64)
+    try:
+        ns = (100, 700, 2049, 5000)
+        ens = _resolved(_concat([_one(n, bc, seed=n + 3 + bc) for n in ns for bc in (0, 1)]),
+                        scheme)
+        dts = oracle_dts(ens, fac)
+        steps = np.array([7, 3, 25, 0, 24, 1, 12, 13])
+        got = run_gpu(ctx, scheme, ens, dts, steps, dtype, iters=iters)
+        ref = run_oracle(scheme, ens, dts, steps, iters=iters)
+        assert_parity(ens, got, ref, dtype, f"forced s{scheme} it{iters}")
+    finally:
+        _fresh(ctx)
+
+
+@pytest.mark.parametrize("dtype", [F64, F32])
+def test_one_picard_iteration_is_the_btcs_step_long(ctx, dtype):
+    """On the multi-level path too, one Picard iteration is the lagged BTCS
+    step: the same rows at level 0, the same reduction (bitwise)."""
+    _fresh(ctx)
+    ens = _concat([_one(n, bc, seed=n + bc) for n in (9000, 70001) for bc in (0, 1)])
+    dts = oracle_dts(ens, 6.0)
+    ctx.set(L.BURGERS_OPT_CLUSTER, 0)
+    try:
+        a = run_gpu(ctx, PICARD, ens, dts, 10, dtype, iters=1)
+        b = run_gpu(ctx, BTCS, ens, dts, 10, dtype)
+    finally:
+        ctx.set(L.BURGERS_OPT_CLUSTER, 1)
+    assert np.array_equal(a, b)
+
+
 def test_rejections(ctx):
-    """Rows beyond the resident capacity and iteration counts outside [1, 64]
-    are refused before any work is queued."""
+    """Iteration counts outside [1, 64] are refused before any work is
+    queued, and so are long rows of the device-dt entry point (whose
+    multi-level rows carry host-computed coefficients)."""
     import torch
     from paper_2601_12204_b300.api import Batch
     _fresh(ctx)
@@ -150,10 +210,10 @@ def test_rejections(ctx):
     u = torch.tensor(long_row.u0, device="cuda")
     b = Batch.from_ensemble(long_row, oracle_dts(long_row), 3, F64)
     before = u.clone()
-    for fn in (lambda: ctx.cn_advance(b, u), lambda: ctx.picard_advance(b, u, 2),
-               lambda: ctx.newton_advance(b, u, 2)):
+    dt = torch.full((1,), float(oracle_dts(long_row)[0]), dtype=torch.float64, device="cuda")
+    for scheme in (CN, PICARD, NEWTON):
         with pytest.raises(Exception):
-            fn()
+            ctx.advance_dt_device(scheme, b, u, dt, 1.0, iters=2)
     short = _one(300, 0, 4)
     us = torch.tensor(short.u0, device="cuda")
     bs = Batch.from_ensemble(short, oracle_dts(short), 3, F64)
