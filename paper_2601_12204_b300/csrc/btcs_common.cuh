@@ -22,21 +22,46 @@ struct BtcsShared {
   T Z[SK];                               // cyclic case: solution for the correction vector
 };
 
-// Sherman-Morrison factor (v.y)/(1 + v.z) for v = e_0 + fa e_tl. The dot
-// products and the denominator are formed in FP64 whatever T is, so a
-// denominator near cancellation keeps its digits. For FP32 the quotient,
-// rounded to FP32 anyway, is an FP32 division of the two FP64 values rounded
-// to FP32 (within 1.5 ulp of their exact quotient): an FP64 divide is a long
-// dependent sequence on B300's narrow FP64 pipe (each FP64 operation costs
-// about 60 cycles of latency), and this factor sits on the serial path of
-// every solve.
+// Error-free sum (Knuth's TwoSum): a + b = s + e exactly. The intrinsics
+// keep the compiler from fusing or reassociating the operations.
+__device__ __forceinline__ float two_sum(float a, float b, float& e) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return s;
+}
+
+// Sherman-Morrison factor (v.y)/(1 + v.z) for v = e_0 + fa e_tl. The
+// denominator can sit near cancellation (it falls toward zero as the
+// diffusion number s = nu dt / dx^2 grows: about 1e-3 at s = 1e4 and 1e-5 at
+// s = 1e6 on a 64-node row), so it is formed in extended precision: FP64 for an FP64 solve; for FP32 an
+// unevaluated pair hi + lo of floats from error-free transformations (the
+// product by FMA, fa ztl = p + pe exactly, then two TwoSums and the sum of
+// the three error terms), which keeps about 48 bits where an FP64 evaluation
+// keeps 53 -- on B300 the FP64 pipe runs at a small fraction of the FP32 rate
+// with a long latency, and this factor sits on the serial path of every
+// solve. The FP32 numerator is one FMA (a single rounding of the exact dot
+// product), and the quotient by hi + lo is a reciprocal estimate with one
+// residual correction (within about one ulp).
 template <typename T>
 __device__ __forceinline__ T sm_factor(T fa, T y0, T ytl, T z0, T ztl) {
-  const double fd = double(fa);
-  const double vy = fma(fd, double(ytl), double(y0));
-  const double den = 1.0 + fma(fd, double(ztl), double(z0));
-  if constexpr (sizeof(T) == 4) return __fdiv_rn(float(vy), float(den));
-  else return vy / den;
+  if constexpr (sizeof(T) == 4) {
+    const float num = __fmaf_rn(fa, ytl, y0);
+    const float p = __fmul_rn(fa, ztl);
+    const float pe = __fmaf_rn(fa, ztl, -p);
+    float e1, e2;
+    const float s1 = two_sum(z0, p, e1);
+    const float hi = two_sum(1.0f, s1, e2);
+    const float lo = __fadd_rn(__fadd_rn(pe, e1), e2);
+    const float r = recip(hi);
+    const float q0 = __fmul_rn(num, r);
+    const float res = __fmaf_rn(-q0, lo, __fmaf_rn(-q0, hi, num));
+    return __fmaf_rn(res, r, q0);
+  } else {
+    const double vy = fma(fa, ytl, y0);
+    const double den = 1.0 + fma(fa, ztl, z0);
+    return vy / den;
+  }
 }
 
 // Solves the reduced system held in sm (rows 0..NT-1, rows beyond tl are

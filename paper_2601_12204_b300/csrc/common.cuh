@@ -100,15 +100,39 @@ __device__ __forceinline__ T shfl_down(T v, int d) {
 //   u' - u = -r (u+ (u - ul) + u- (ur - u)) + s (ur - 2u + ul)
 //          = p (ur - u) - q (u - ul),
 //   p = s - r u- = s + h (|u| - u),   q = s + r u+ = p + r u,   h = r/2,
-// returned plus `add`. Per node: one difference (u - ul is the previous
-// node's ur - u) and five FMA-pipe operations, no min/max.
+// returned plus `add`. FP64: one difference (u - ul is the previous node's
+// ur - u) and five FP64 operations, no min/max. FP32 forms q as s + r u+
+// (one rounding, from max(u, 0)), bitwise what the packed-pair steps of the
+// resident and windowed kernels compute, so every FP32 kernel (forward,
+// windowed, single-step, adjoint recompute) follows the same trajectory.
 template <typename T>
 __device__ __forceinline__ T explicit_increment(T u, T ul, T ur, T r, T h, T s, T add) {
   const T dr = ur - u;
   const T dl = u - ul;
   const T p = tfma(h, tabs(u) - u, s);
-  const T q = tfma(r, u, p);
-  return tfma(p, dr, tfma(-q, dl, add));
+  if constexpr (sizeof(T) == 4) {
+    const T q = tfma(r, tmax(u, T(0)), s);
+    return tfma(p, dr, tfma(-q, dl, add));
+  } else {
+    const T q = tfma(r, u, p);
+    return tfma(p, dr, tfma(-q, dl, add));
+  }
+}
+
+// Packed FP32 arithmetic (the f32x2 forms of add, sub and fma): one
+// instruction applies the operation to two independent float lanes, each
+// rounded as its scalar form would be. The FMA pipe executes the same number
+// of lane operations either way; the packed forms halve the instructions the
+// schedulers must issue, which is what limits the register-resident stencil.
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+  float2 d;
+  asm("{\n\t.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+      "sub.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return d;
 }
 
 // u' = u + increment. FP64 adds directly (one rounding per step is far below

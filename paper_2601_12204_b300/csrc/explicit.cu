@@ -4,9 +4,11 @@
 // Layout: thread t of a CTA holds C consecutive nodes of a row in registers.
 // Neighbour values cross lanes by warp shuffles and cross warps through a
 // double-buffered shared-memory slot per warp, so one step costs one
-// __syncthreads (none for single-warp rows) and, per node, six FMA-pipe
-// instructions; FP32 adds one to evaluate its split state (value at the last
-// fold plus the increments since) and three every 32 steps to fold it.
+// __syncthreads (none for single-warp rows) and, per node, five FMA-pipe
+// operations (FP64: six); FP32 adds one to evaluate its split state (value at
+// the last fold plus the increments since) and three every 32 steps to fold
+// it, and runs them on packed f32x2 pairs (half the instructions to issue)
+// with the upwind min/max on the ALU pipe.
 //
 //  * k_explicit_resident: the whole row lives in registers for all of its
 //    steps (the paper's time loop runs inside the kernel). CTAs are
@@ -120,11 +122,115 @@ __device__ __forceinline__ bool keep_node_w(int j, int jstar, int64_t gbase, int
 // two-sum as compensated summation), so increments are never rounded against
 // the full magnitude of u between folds. On entry and exit the state is
 // (v, lo) with the true value v - lo, as in Kahan summation.
+//
+// Even C runs on packed FP32 pairs: pair k holds nodes k and k + C/2 of the
+// thread's chunk, so the right neighbour of pair k is pair k + 1 in both
+// lanes and only the last pair's right and the first pair's left neighbours
+// are assembled from the other half and the halo. With m = min(u, 0) and
+// M = max(u, 0), the upwind coefficients are p = s - r m = s + (r/2)(|u| - u)
+// and q = s + r M = p + r u (Eq. 21), each one FMA from the min/max (which
+// run on the ALU pipe), and the increment p (u_r - u) - q (u - u_l) is two
+// more FMAs.
+template <int NT, int C, int MODE, int BCT>
+__device__ __forceinline__ void explicit_steps_split_x2(float (&v)[C], float (&lo)[C],
+                                                        int64_t nsteps, float r, float s, int n,
+                                                        int64_t gbase, float* sh_last,
+                                                        float* sh_first, float* sh_wrap) {
+  static_assert(C % 2 == 0, "pairs of nodes");
+  constexpr int H = C / 2;
+  constexpr bool WRAPX = (MODE == MODE_RAGGED && BCT == BC_PERIODIC);
+  const int tid = threadIdx.x;
+  const int jstar = int(n - 1 - gbase);  // local index of node n-1 (resident modes)
+  const RaggedWarp rw = ragged_warp<C, MODE>(jstar);
+  float2 V[H], D[H];
+#pragma unroll
+  for (int k = 0; k < H; ++k) {
+    V[k] = make_float2(v[k], v[k + H]);
+    D[k] = make_float2(-lo[k], -lo[k + H]);
+  }
+  const float2 NR = make_float2(-r, -r), S2 = make_float2(s, s), NS = make_float2(-s, -s);
+  for (int64_t k0 = 0; k0 < nsteps; k0 += SPLIT_FOLD) {
+   const int kb = int(nsteps - k0 < SPLIT_FOLD ? nsteps - k0 : int64_t(SPLIT_FOLD));
+   for (int kk = 0; kk < kb; ++kk) {
+    const int p = kk & 1;
+    const float2 U0 = add2(V[0], D[0]);
+    const float2 UL = add2(V[H - 1], D[H - 1]);
+    float wsel = 0.f;
+    bool has_wrap = false;
+    if constexpr (WRAPX) {
+      has_wrap = jstar >= 0 && jstar < C;
+      if (rw.edge) {  // only the warp holding node n-1 looks for it
+        float sv = V[0].x, sd = D[0].x;
+#pragma unroll
+        for (int j = 1; j < C; ++j)
+          if (j == jstar) {
+            sv = j < H ? V[j].x : V[j - H].y;
+            sd = j < H ? D[j].x : D[j - H].y;
+          }
+        wsel = sv + sd;
+      }
+    }
+    float left, right, wrapL = 0.f, wrapR = 0.f;
+    halo_exchange<float, NT, WRAPX>(U0.x, UL.y, wsel, has_wrap, p, sh_last, sh_first, sh_wrap,
+                                    left, right, wrapL, wrapR);
+    float wl0 = left;
+    if constexpr (WRAPX) {
+      if (tid == 0) wl0 = wrapL;
+    }
+    auto update = [&](auto edge_tag) {
+      constexpr bool EDGE = decltype(edge_tag)::value;
+      float2 Uk = U0;
+      float2 DL = sub2(U0, make_float2(wl0, UL.x));  // u - u_l of pair 0
+#pragma unroll
+      for (int k = 0; k < H; ++k) {
+        float2 UR = (k + 1 < H) ? add2(V[k + 1], D[k + 1]) : make_float2(U0.y, right);
+        const float2 Un = UR;
+        if constexpr (WRAPX && EDGE) {
+          if (k == jstar) UR.x = wrapR;
+          if (k + H == jstar) UR.y = wrapR;
+        }
+        const float2 E = sub2(UR, Uk);  // u_r - u
+        const float2 m = make_float2(fminf(Uk.x, 0.f), fminf(Uk.y, 0.f));
+        const float2 M = make_float2(fmaxf(Uk.x, 0.f), fmaxf(Uk.y, 0.f));
+        const float2 P = fma2(NR, m, S2);   // p
+        const float2 NQ = fma2(NR, M, NS);  // -q
+        const float2 dn = fma2(P, E, fma2(NQ, DL, D[k]));
+        if (!keep_node_w<NT, C, MODE, BCT, EDGE>(k, jstar, gbase, n)) D[k].x = dn.x;
+        if (!keep_node_w<NT, C, MODE, BCT, EDGE>(k + H, jstar, gbase, n)) D[k].y = dn.y;
+        DL = E;
+        Uk = Un;
+      }
+    };
+    if (!rw.ragged || rw.edge) update(std::true_type{});
+    else if (!rw.pad) update(std::false_type{});
+   }
+#pragma unroll
+    for (int k = 0; k < H; ++k) {
+      const float2 t = add2(V[k], D[k]);
+      D[k] = sub2(D[k], sub2(t, V[k]));
+      V[k] = t;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < H; ++k) {
+    v[k] = V[k].x;
+    v[k + H] = V[k].y;
+    lo[k] = -D[k].x;
+    lo[k + H] = -D[k].y;
+  }
+}
+
 template <int NT, int C, int MODE, int BCT>
 __device__ __forceinline__ void explicit_steps_split(float (&v)[C], float (&lo)[C], int64_t nsteps,
                                                      float r, float h, float s, int n,
                                                      int64_t gbase, float* sh_last,
                                                      float* sh_first, float* sh_wrap) {
+  if constexpr (C % 2 == 0) {
+    (void)h;
+    explicit_steps_split_x2<NT, C, MODE, BCT>(v, lo, nsteps, r, s, n, gbase, sh_last, sh_first,
+                                              sh_wrap);
+    return;
+  }
   constexpr bool WRAPX = (MODE == MODE_RAGGED && BCT == BC_PERIODIC);
   const int tid = threadIdx.x;
   const int jstar = int(n - 1 - gbase);  // local index of node n-1 (resident modes)
@@ -198,10 +304,127 @@ __device__ __forceinline__ void explicit_steps_split(float (&v)[C], float (&lo)[
 // FP32 keeps the split state of explicit_steps_split (the stage states are
 // evaluated from it; the step's combined increment goes into d); FP64 adds the
 // combined increment to u directly.
+// FP32 RK4 with even C on packed pairs (nodes k and k + C/2, as in
+// explicit_steps_split_x2); bitwise the arithmetic of rk4_steps below.
+template <int NT, int C, int MODE, int BCT>
+__device__ __forceinline__ void rk4_steps_x2(float (&v)[C], float (&lo)[C], int64_t nsteps,
+                                             float r, float s, int n, int64_t gbase,
+                                             float* sh_last, float* sh_first, float* sh_wrap) {
+  static_assert(C % 2 == 0, "pairs of nodes");
+  constexpr int H = C / 2;
+  constexpr bool WRAPX = (MODE == MODE_RAGGED && BCT == BC_PERIODIC);
+  const int tid = threadIdx.x;
+  const int jstar = int(n - 1 - gbase);
+  const RaggedWarp rw = ragged_warp<C, MODE>(jstar);
+  float2 V[H], D[H], K[H], ACC[H];
+#pragma unroll
+  for (int k = 0; k < H; ++k) {
+    V[k] = make_float2(v[k], v[k + H]);
+    D[k] = make_float2(-lo[k], -lo[k + H]);
+    K[k] = make_float2(0.f, 0.f);
+  }
+  const float2 NR = make_float2(-r, -r), S2 = make_float2(s, s), NS = make_float2(-s, -s);
+  const float2 Z2 = make_float2(0.f, 0.f);
+  for (int64_t k0 = 0; k0 < nsteps; k0 += SPLIT_FOLD) {
+   const int kb = int(nsteps - k0 < SPLIT_FOLD ? nsteps - k0 : int64_t(SPLIT_FOLD));
+   for (int kk = 0; kk < kb; ++kk) {
+    float2 U[H];
+#pragma unroll
+    for (int k = 0; k < H; ++k) U[k] = add2(V[k], D[k]);
+#pragma unroll
+    for (int st = 0; st < 4; ++st) {
+      const float cs = st == 0 ? 0.f : (st == 3 ? 1.f : 0.5f);
+      const float2 CST = make_float2(cs, cs);
+      float2 W[H];
+#pragma unroll
+      for (int k = 0; k < H; ++k) W[k] = st == 0 ? U[k] : fma2(CST, K[k], U[k]);
+      float wsel = 0.f;
+      bool has_wrap = false;
+      if constexpr (WRAPX) {
+        has_wrap = jstar >= 0 && jstar < C;
+        if (rw.edge) {
+          wsel = W[0].x;
+#pragma unroll
+          for (int j = 1; j < C; ++j)
+            if (j == jstar) wsel = j < H ? W[j].x : W[j - H].y;
+        }
+      }
+      float left, right, wrapL = 0.f, wrapR = 0.f;
+      halo_exchange<float, NT, WRAPX>(W[0].x, W[H - 1].y, wsel, has_wrap, st & 1, sh_last,
+                                      sh_first, sh_wrap, left, right, wrapL, wrapR);
+      float wl0 = left;
+      if constexpr (WRAPX) {
+        if (tid == 0) wl0 = wrapL;
+      }
+      auto stage = [&](auto edge_tag) {
+        constexpr bool EDGE = decltype(edge_tag)::value;
+        float2 DL = sub2(W[0], make_float2(wl0, W[H - 1].x));
+#pragma unroll
+        for (int k = 0; k < H; ++k) {
+          float2 WR = (k + 1 < H) ? W[k + 1] : make_float2(W[0].y, right);
+          if constexpr (WRAPX && EDGE) {
+            if (k == jstar) WR.x = wrapR;
+            if (k + H == jstar) WR.y = wrapR;
+          }
+          const float2 E = sub2(WR, W[k]);
+          const float2 m = make_float2(fminf(W[k].x, 0.f), fminf(W[k].y, 0.f));
+          const float2 M = make_float2(fmaxf(W[k].x, 0.f), fmaxf(W[k].y, 0.f));
+          const float2 P = fma2(NR, m, S2);
+          const float2 NQ = fma2(NR, M, NS);
+          float2 kn = fma2(P, E, fma2(NQ, DL, Z2));
+          if (keep_node_w<NT, C, MODE, BCT, EDGE>(k, jstar, gbase, n)) kn.x = 0.f;
+          if (keep_node_w<NT, C, MODE, BCT, EDGE>(k + H, jstar, gbase, n)) kn.y = 0.f;
+          if (st == 0) ACC[k] = kn;
+          else {
+            const float w = st == 3 ? 1.f : 2.f;
+            ACC[k] = fma2(make_float2(w, w), kn, ACC[k]);
+          }
+          K[k] = kn;
+          DL = E;
+        }
+      };
+      if (!rw.ragged || rw.edge) {
+        stage(std::true_type{});
+      } else if (!rw.pad) {
+        stage(std::false_type{});
+      } else {
+#pragma unroll
+        for (int k = 0; k < H; ++k) {
+          if (st == 0) ACC[k] = Z2;
+          K[k] = Z2;
+        }
+      }
+    }
+    const float sx = 1.f / 6.f;
+    const float2 SIX = make_float2(sx, sx);
+#pragma unroll
+    for (int k = 0; k < H; ++k) D[k] = fma2(SIX, ACC[k], D[k]);
+   }
+#pragma unroll
+    for (int k = 0; k < H; ++k) {
+      const float2 t = add2(V[k], D[k]);
+      D[k] = sub2(D[k], sub2(t, V[k]));
+      V[k] = t;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < H; ++k) {
+    v[k] = V[k].x;
+    v[k + H] = V[k].y;
+    lo[k] = -D[k].x;
+    lo[k + H] = -D[k].y;
+  }
+}
+
 template <typename T, int NT, int C, int MODE, int BCT>
 __device__ __forceinline__ void rk4_steps(T (&v)[C], T (&lo)[C], int64_t nsteps, T r, T h, T s,
                                           int n, int64_t gbase, T* sh_last, T* sh_first,
                                           T* sh_wrap) {
+  if constexpr (sizeof(T) == 4 && C % 2 == 0) {
+    (void)h;
+    rk4_steps_x2<NT, C, MODE, BCT>(v, lo, nsteps, r, s, n, gbase, sh_last, sh_first, sh_wrap);
+    return;
+  }
   constexpr bool SPLIT = Kahan<T>::on;
   constexpr bool WRAPX = (MODE == MODE_RAGGED && BCT == BC_PERIODIC);
   const int tid = threadIdx.x;

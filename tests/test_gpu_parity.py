@@ -636,3 +636,73 @@ def test_thomas_default_routing(dtype):
     ref = run_oracle(BTCS, sub, dts[ids], steps[ids])
     g = np.concatenate([got[offs[i]:offs[i] + lens[i]] for i in ids])
     assert_parity(sub, g, ref, dtype, "default routing")
+
+
+def _diffusion_bar(dtype, svals):
+    """Per-row bar of the strong-diffusion test. The solve is in increment
+    form (A delta = Delta(u^n)), whose right-hand side grows with the
+    diffusion number s = nu dt / dx^2 while the increment stays O(|u|), so its
+    rounding error grows about in proportion to s; and the Sherman-Morrison
+    denominator falls as s grows, which amplifies the error in z. FP64 is
+    held to the 1e-12 bar scaled by max(1, s) (measured on a B300: 7e-11 at
+    s = 1e4 and 1.8e-8 at s = 1e6 on 64-node rows of the partitioned kernel,
+    2e-13 s on rows of the per-thread Thomas kernel); FP32 is held to its
+    1e-5 bar up to s = 10 and not run beyond (at s = 1e2: 3.4e-6 on a 64-node
+    row of the partitioned kernel, 3.8e-5 on a 34-node row of the per-thread
+    Thomas kernel)."""
+    if dtype == F32:
+        return np.full(len(svals), 1e-5)
+    return 1e-12 * np.maximum(1.0, np.asarray(svals))
+
+
+def _assert_rel(ens, got, ref, bars, what):
+    for b in range(ens.count):
+        o, n = int(ens.offsets[b]), int(ens.ns[b])
+        g, r = got[o:o + n], ref[o:o + n]
+        assert np.all(np.isfinite(g)), f"{what} row {b}: non-finite"
+        rel = oracle.rel_l2(g, r)
+        assert rel <= bars[b], f"{what} row {b} (n={n}): rel L2 {rel:.3e} > {bars[b]:.1e}"
+
+
+@pytest.mark.parametrize("dtype", [F64, F32])
+def test_btcs_strong_diffusion_periodic(ctx, dtype, tmp_path):
+    """Periodic BTCS at diffusion numbers s = nu dt / dx^2 from 1 to 10
+    (FP32) or 1e6 (FP64), where the Sherman-Morrison denominator 1 + v.z falls
+    to about 1e-5: resident rows of 64, 512 and 4096 nodes, a
+    cluster-resident row of 20000 (FP32), a multi-level row of 70001, and
+    many rows of <= 64 nodes forced through the per-thread Thomas kernel,
+    against the oracle with the bars of _diffusion_bar."""
+    _fresh(ctx)
+    smax = 1e1 if dtype == F32 else 1e6
+    sgrid = [s for s in (1.0, 1e1, 1e2, 1e4, 1e6) if s <= smax]
+    parts, svals = [], []
+    for n in (64, 512, 4096, 20000, 70001):
+        for s in sgrid:
+            parts.append(_one(n, W.PERIODIC, seed=n + int(np.log10(s))))
+            svals.append(s)
+    ens = _concat(parts)
+    ens.nus[:] = 1.0
+    dts = np.array(svals) * ens.dxs ** 2
+    got = run_gpu(ctx, BTCS, ens, dts, 3, dtype)
+    ref = run_oracle(BTCS, ens, dts, 3)
+    _assert_rel(ens, got, ref, _diffusion_bar(dtype, svals), "strong diffusion")
+    # the per-thread Thomas kernel (class of 64 nodes, forced)
+    rng = np.random.default_rng(5)
+    lens = rng.integers(33, 65, 300)
+    ens = _concat([_one(int(n), W.PERIODIC, seed=int(n) + 17 * i) for i, n in enumerate(lens)])
+    ens.nus[:] = 1.0
+    svals = 10.0 ** rng.uniform(0, np.log10(smax), ens.count)
+    dts = svals * ens.dxs ** 2
+    nt = 128 if dtype == F32 else 64
+    key = lambda ex: (2 << 56) ^ (dtype << 52) ^ (ex << 48) ^ 64  # noqa: E731
+    path = tmp_path / "thomas.txt"
+    path.write_text(f"# thomas\n{key(0)} {nt} 64 3\n{key(1)} {nt} 64 3\n")
+    ctx.tune_load(str(path))
+    try:
+        got = run_gpu(ctx, BTCS, ens, dts, 3, dtype)
+    finally:
+        pt, pc = PARTITIONED_SHAPE[64]
+        path.write_text(f"# partitioned\n{key(0)} {pt} {pc} 0\n{key(1)} {pt} {pc} 0\n")
+        ctx.tune_load(str(path))
+    ref = run_oracle(BTCS, ens, dts, 3)
+    _assert_rel(ens, got, ref, _diffusion_bar(dtype, svals), "strong diffusion, per-thread Thomas")
