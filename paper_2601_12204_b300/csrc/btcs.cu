@@ -22,9 +22,19 @@
 // All pivots are >= 1 because every matrix involved is diagonally dominant by
 // a margin of one (an M-matrix and its Schur complements), so no pivoting is
 // needed.
-#include "btcs_kernel.cuh"
+#include "btcs_x2.cuh"
 
 namespace burgers {
+
+// FP32 rows of exactly NT*C nodes with C even run the packed-pair kernel
+// (btcs_x2.cuh); ragged rows the scalar one.
+#define REG_BTCS_X2(NT, C)                                                                      \
+  reg.push_back({K_BTCS_RESIDENT, 0, NT, C, 1,                                                  \
+                 reinterpret_cast<const void*>(&k_btcs_resident_x2<NT, C, VAR_BTCS>),          \
+                 btcs_x2_dsm<NT, C, VAR_BTCS>()});                                              \
+  reg.push_back({K_BTCS_RESIDENT, 0, NT, C, 0,                                                  \
+                 reinterpret_cast<const void*>(&k_btcs_resident<float, NT, C, false, VAR_BTCS>), \
+                 btcs_dsm<float, NT, C, VAR_BTCS>()});
 
 #define REG_BTCS(T, DT, NT, C)                                                                  \
   reg.push_back({K_BTCS_RESIDENT, DT, NT, C, 1,                                                 \
@@ -35,11 +45,11 @@ namespace burgers {
                  btcs_dsm<T, NT, C, VAR_BTCS>()});
 
 void register_btcs(std::vector<KernelEntry>& reg) {
-  REG_BTCS(float, 0, 32, 1) REG_BTCS(float, 0, 32, 2) REG_BTCS(float, 0, 32, 4)
-  REG_BTCS(float, 0, 32, 8) REG_BTCS(float, 0, 64, 8) REG_BTCS(float, 0, 128, 8)
-  REG_BTCS(float, 0, 256, 8) REG_BTCS(float, 0, 128, 16) REG_BTCS(float, 0, 256, 16)
-  REG_BTCS(float, 0, 512, 8) REG_BTCS(float, 0, 512, 16) REG_BTCS(float, 0, 1024, 8)
-  REG_BTCS(float, 0, 64, 32) REG_BTCS(float, 0, 128, 32) REG_BTCS(float, 0, 256, 32)
+  REG_BTCS(float, 0, 32, 1) REG_BTCS_X2(32, 2) REG_BTCS_X2(32, 4)
+  REG_BTCS_X2(32, 8) REG_BTCS_X2(64, 8) REG_BTCS_X2(128, 8)
+  REG_BTCS_X2(256, 8) REG_BTCS_X2(128, 16) REG_BTCS_X2(256, 16)
+  REG_BTCS_X2(512, 8) REG_BTCS_X2(512, 16) REG_BTCS_X2(1024, 8)
+  REG_BTCS_X2(64, 32) REG_BTCS_X2(128, 32) REG_BTCS_X2(256, 32)
   REG_BTCS(double, 1, 32, 1) REG_BTCS(double, 1, 32, 2) REG_BTCS(double, 1, 32, 4)
   REG_BTCS(double, 1, 32, 8) REG_BTCS(double, 1, 64, 8) REG_BTCS(double, 1, 128, 8)
   REG_BTCS(double, 1, 256, 8) REG_BTCS(double, 1, 512, 8) REG_BTCS(double, 1, 256, 16)

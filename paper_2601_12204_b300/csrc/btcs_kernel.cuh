@@ -39,8 +39,9 @@ constexpr size_t btcs_dsm() {
 // (the term lo per node, also in shared memory): BTCS steps are long, so an
 // increment can be a sizeable part of u and must be compensated every step.
 //
-// Two barriers per solve. Each thread publishes the reduced-system data of its
-// chunk; warp 0 forms the reduced rows and solves them.
+// Three CTA barriers per solve: after each thread publishes its chunk's
+// first-row relation, after each thread forms its chunk's reduced row, and
+// after the last warp has solved the reduced system.
 //
 // Neighbour values. A chunk's rows need the value left of its first node and
 // right of its end node. In BTCS, CN and Picard the row coefficients depend
@@ -301,7 +302,7 @@ __device__ __forceinline__ void btcs_steps(int64_t nsteps, int iters, T r, T s, 
       sm.A[i] = A; sm.B[i] = B; sm.Cc[i] = Cc; sm.D[i] = D; sm.U[i] = U;
     }
     __syncthreads();
-    if (warp == 0) {
+    if (warp == Q - 1) {  // the last warp (warp 0 also carries the row's first node)
       reduced_solve<T, NT, PER, true>(sm, tl, lane, fa);
       // next step's first and last node of each chunk (Newton)
       if constexpr (!DEFER) {

@@ -1,0 +1,303 @@
+// btcs_x2.cuh -- the FP32 resident implicit-step kernel for rows of exactly
+// NT*C nodes on packed f32x2 arithmetic (lagged BTCS, Crank-Nicolson and
+// Picard; the algebra of each variant is that of btcs_kernel.cuh).
+//
+// Each thread's chunk of C nodes is two half-chunks, A = nodes [0, C/2) and
+// B = [C/2, C), eliminated side by side: pair k holds node k of A and node k
+// of B, so every step of both eliminations is one packed instruction for the
+// two lanes (the reciprocals stay scalar). Splitting the chunk also halves the
+// length of each elimination's dependent chain.
+//
+// The chunk then has two unknown end values, X_A (node C/2 - 1) and X_B (node
+// C - 1). Substituting B's first-row relation into A's end row gives the row
+//     bA X_A + aA X_B(t-1) + cA X_B(t) = dA,
+// which the thread divides by bA and publishes (pa, pc, pd) with A's first-row
+// relation; substituting the next thread's first-row relation into B's end
+// row and eliminating X_A(t) and X_A(t+1) through their rows leaves one
+// tridiagonal row per thread in X_B(t-1), X_B(t), X_B(t+1): the same NT-row
+// reduced system (cyclic for periodic rows) as the scalar kernel, solved by
+// warp 0 with the same reduced_solve. Back-substitution recovers X_A from its
+// row and every node from its half's relation.
+//
+// Signs: the packed forms have no negated operands, so the sweeps carry
+// -rhs, -dh and -delta (and -ch beside ch), chosen so that every rounding is
+// that of the corresponding scalar operation (negation commutes with
+// round-to-nearest).
+#pragma once
+
+#include "btcs_kernel.cuh"
+
+namespace burgers {
+
+template <int NT>
+struct X2Shared {
+  static constexpr int SK = NT + NT / 32;
+  float pa[SK], pc[SK], pd[SK];  // thread's A row divided by bA
+  float c0[4];                   // thread 0: eBa, eBc, pa, pc (periodic corner split)
+};
+
+template <int NT, int C, int VAR>
+constexpr size_t btcs_x2_dsm() {
+  return sizeof(float2) * size_t(NT) * size_t(C / 2) * (2 + (VAR == VAR_PICARD ? 1 : 0));
+}
+
+// Thread 0's reduced row coefficients A_0, B_0 from its published values and
+// thread 1's (the same arithmetic wherever it is evaluated).
+__device__ __forceinline__ void x2_row0(const float* c0, float ran1, float rgn1, float pa1,
+                                        float& A0, float& B0) {
+  const float bB = 1.f - c0[1] * ran1;
+  const float cB = -c0[1] * rgn1;
+  A0 = -c0[0] * c0[2];
+  B0 = bB - c0[0] * c0[3] - cB * pa1;
+}
+
+template <int NT, int C, int BCT, int VAR>
+__device__ __forceinline__ void btcs_steps_x2(int64_t nsteps, int iters, float r, float s,
+                                              BtcsShared<float, NT>& sm, X2Shared<NT>& xs,
+                                              float* hfirst, float* hlast, float2* us, float2* lo,
+                                              float2* es, int solver) {
+  static_assert(C % 2 == 0 && C >= 2, "two half-chunks");
+  static_assert(VAR != VAR_NEWTON, "Newton takes its neighbours directly (scalar kernel)");
+  constexpr int H = C / 2;
+  constexpr bool ITER = VAR == VAR_PICARD;
+  constexpr bool PER = BCT == BC_PERIODIC;
+  const float kap = VAR == VAR_CN ? 2.f : 1.f;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int tl = NT - 1;
+  const float rm = VAR == VAR_CN ? 0.5f * r : r, smat = VAR == VAR_CN ? 0.5f * s : s;
+  const float2 RM2 = make_float2(rm, rm), SM2 = make_float2(smat, smat);
+  const float ds1 = 1.f + 2.f * smat;
+  const float2 DS1 = make_float2(ds1, ds1);
+  const int nit = ITER ? iters : 1;
+  auto W = [&](int k) -> float2 {
+    if constexpr (ITER) return add2(us[k * NT + tid], es[k * NT + tid]);
+    else return us[k * NT + tid];
+  };
+  float2 CH[H], AH[H], ND[H];  // forward: -ch, ah, -dh; backward: gamma, alpha, -delta
+  for (int64_t step = 0; step < nsteps; ++step) {
+  if constexpr (ITER) {
+#pragma unroll
+    for (int k = 0; k < H; ++k) es[k * NT + tid] = make_float2(0.f, 0.f);
+  }
+  for (int it = 0; it < nit; ++it) {
+    const bool last = it + 1 == nit;
+    // ---- forward sweep of both halves. A's first row stands in for its own
+    // left neighbour (deferred, as in the scalar kernel); B's first row reads
+    // node C/2 - 1; A's end row reads node C/2; B's end row stands in for its
+    // own right neighbour (deferred).
+    float2 a = W(0);
+    float2 DL = sub2(a, make_float2(a.x, W(H - 1).x));  // a - u_l
+    float2 chp = make_float2(0.f, 0.f), ahp = make_float2(-1.f, -1.f), ndhp = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int k = 0; k < H; ++k) {
+      const float2 an = (k + 1 < H) ? W(k + 1) : make_float2(W(0).y, a.y);
+      const float2 ER = sub2(an, a);  // u_r - a
+      const float2 ra = mul2(RM2, a);
+      const float2 M = make_float2(fmaxf(ra.x, 0.f), fmaxf(ra.y, 0.f));
+      const float2 m = make_float2(fminf(ra.x, 0.f), fminf(ra.y, 0.f));
+      float2 nl = add2(SM2, M);       // -l
+      float2 c = sub2(m, SM2);        // c
+      float2 nc = sub2(SM2, m);       // -c
+      float2 d = add2(DS1, sub2(M, m));
+      // -rhs = -(l (a - u_l) - c (u_r - a)) of the increment form
+      float2 nrhs = fma2(nl, DL, mul2(c, ER));
+      if constexpr (VAR == VAR_CN) nrhs = mul2(make_float2(2.f, 2.f), nrhs);
+      if constexpr (ITER) nrhs = add2(nrhs, es[k * NT + tid]);
+      if constexpr (BCT == BC_DIRICHLET) {  // the row's end nodes are identity rows
+        if (k == 0 && tid == 0) { nl.x = 0.f; c.x = 0.f; nc.x = 0.f; d.x = 1.f; nrhs.x = 0.f; }
+        if (k == H - 1 && tid == NT - 1) { nl.y = 0.f; c.y = 0.f; nc.y = 0.f; d.y = 1.f; nrhs.y = 0.f; }
+      }
+      const float2 den = fma2(nl, chp, d);
+      const float2 inv = make_float2(recip(den.x), recip(den.y));
+      const float2 nli = mul2(nl, inv);
+      chp = mul2(c, inv);
+      CH[k] = mul2(nc, inv);
+      ahp = mul2(nli, ahp);
+      ndhp = fma2(nli, ndhp, mul2(nrhs, inv));
+      AH[k] = ahp;
+      ND[k] = ndhp;
+      DL = ER;
+      a = an;
+    }
+    // end rows of both halves: x_e = dh - ah L - ch x_next
+    const float eAc = chp.x, eAa = ahp.x, eAd = -ndhp.x;
+    const float eBc = chp.y, eBa = ahp.y, eBd = -ndhp.y;
+    // ---- backward sweep: x_j = delta_j - alpha_j L - gamma_j X_e
+    {
+      float2 ncd = make_float2(0.f, 0.f), ca = make_float2(0.f, 0.f), cg = make_float2(-1.f, -1.f);
+      ND[H - 1] = ncd;
+      AH[H - 1] = ca;
+      CH[H - 1] = cg;
+#pragma unroll
+      for (int k = H - 2; k >= 0; --k) {
+        const float2 ncj = CH[k];
+        ncd = fma2(ncj, ncd, ND[k]);
+        ca = fma2(ncj, ca, AH[k]);
+        cg = mul2(ncj, cg);
+        ND[k] = ncd;
+        AH[k] = ca;
+        CH[k] = cg;
+      }
+    }
+    // ---- A's row, divided by bA, without the deferred term of its left
+    // neighbour (pd0: every reader adds -kap pa (u_left - u_0) after the
+    // first barrier, from the edge values the owners published); A's
+    // first-row relation
+    const float bA = 1.f - eAc * AH[0].y;
+    const float cA = -eAc * CH[0].y;
+    const float dA0 = tfma(-eAc, -ND[0].y, eAd);
+    const float ib = 1.f / bA;
+    const float pa = eAa * ib, pc = cA * ib, pd0 = dA0 * ib;
+    sm.rd[sk(tid)] = -ND[0].x;
+    sm.ra[sk(tid)] = AH[0].x;
+    sm.rg[sk(tid)] = CH[0].x;
+    xs.pa[sk(tid)] = pa;
+    xs.pc[sk(tid)] = pc;
+    xs.pd[sk(tid)] = pd0;
+    if constexpr (PER) {
+      if (tid == 0) { xs.c0[0] = eBa; xs.c0[1] = eBc; xs.c0[2] = pa; xs.c0[3] = pc; }
+    }
+    __syncthreads();
+    // u_left - u_0 of this chunk and A's row with it
+    const float lt = tid > 0 ? hlast[tid - 1] - hfirst[tid] : (PER ? hlast[tl] - hfirst[0] : 0.f);
+    const float pd = tfma(-kap * pa, lt, pd0);
+    // ---- the reduced row in X_B: B's end row with the next thread's
+    // first-row relation substituted, X_A(t) and X_A(t+1) eliminated
+    float fa = 0.f;
+    {
+      const int t = tid, i = sk(t);
+      const int nx = (t == tl) ? 0 : t + 1;
+      const bool has_next = PER || t < tl;
+      float A = -eBa * pa, B = 1.f, Cc = 0.f, D = 0.f, U = 0.f;
+      const float Dt0 = eBd;
+      if (has_next) {
+        const float e = hlast[t], fn = hfirst[nx];
+        const float rt = fn - e;
+        const float ran = sm.ra[sk(nx)], rgn = sm.rg[sk(nx)];
+        const float rdn = tfma(-kap * ran, e - fn, sm.rd[sk(nx)]);
+        const float Dt = tfma(-kap * eBc, rt, Dt0);
+        const float bB = 1.f - eBc * ran;
+        const float cB = -eBc * rgn;
+        const float dB = tfma(-eBc, rdn, Dt);
+        const float pan = xs.pa[sk(nx)], pcn = xs.pc[sk(nx)];
+        const float pdn = tfma(-kap * pan, e - fn, xs.pd[sk(nx)]);  // its u_left - u_0 is e - fn
+        B = bB - eBa * pc - cB * pan;
+        Cc = -cB * pcn;
+        D = dB - eBa * pd - cB * pdn;
+      } else {  // Dirichlet: the row's last node is an identity row
+        B = 1.f - eBa * pc;
+        D = Dt0 - eBa * pd;
+      }
+      if constexpr (PER) {
+        float A0, B0;
+        x2_row0(xs.c0, sm.ra[sk(1)], sm.rg[sk(1)], xs.pa[sk(1)], A0, B0);
+        const float gam = -B0;
+        fa = A0 * recip(gam);
+        if (t == 0) { B = B0 - gam; A = 0.f; U = gam; }
+        if (t == tl) { B = B - Cc * fa; U = Cc; Cc = 0.f; }
+      }
+      sm.A[i] = A; sm.B[i] = B; sm.Cc[i] = Cc; sm.D[i] = D; sm.U[i] = U;
+    }
+    __syncthreads();
+    if (warp == solver) reduced_solve<float, NT, PER, true>(sm, tl, lane, fa);
+    __syncthreads();
+    // ---- X_A from its row; every node from its half's relation; the update
+    {
+      float XBm = 0.f;
+      if (tid > 0) XBm = sm.X[sk(tid - 1)];
+      else if constexpr (PER) XBm = sm.X[sk(tl)];
+      const float XB = sm.X[sk(tid)];
+      const float XA = pd - pa * XBm - pc * XB;
+      const float2 Lp = make_float2(tfma(kap, lt, XBm), XA);
+      const float2 Xp = make_float2(XA, XB);
+#pragma unroll
+      for (int k = 0; k < H; ++k) {
+        const float2 ndelta = fma2(CH[k], Xp, fma2(AH[k], Lp, ND[k]));
+        const int o = k * NT + tid;
+        float2 nv;
+        if constexpr (ITER) {
+          const float2 inc = sub2(es[o], ndelta);
+          if (!last) {
+            es[o] = inc;
+            nv = add2(us[o], inc);  // the next iterate's value (edges below)
+          } else {
+            const float2 u = us[o], l0 = lo[o];
+            const float2 y = sub2(inc, l0);
+            nv = add2(u, y);
+            lo[o] = sub2(sub2(nv, u), y);
+            us[o] = nv;
+          }
+        } else {
+          const float2 u = us[o], l0 = lo[o];
+          const float2 ny = add2(ndelta, l0);
+          nv = sub2(u, ny);
+          lo[o] = add2(sub2(nv, u), ny);
+          us[o] = nv;
+        }
+        if (k == 0) hfirst[tid] = nv.x;
+        if (k == H - 1) hlast[tid] = nv.y;
+      }
+    }
+  }  // iterations
+  }  // steps
+}
+
+// FP32 rows of exactly NT*C nodes. Persistent CTAs take rows from an atomic
+// counter; the row state lives in shared memory as node pairs (k, k + C/2)
+// laid out [k][thread].
+template <int NT, int C, int VAR>
+__global__ void __launch_bounds__(NT, NT <= 512 ? 512 / NT : 1)
+    k_btcs_resident_x2(float* __restrict__ u, const RowDesc* __restrict__ rows, int count,
+                       int* __restrict__ counter) {
+  constexpr int H = C / 2;
+  __shared__ BtcsShared<float, NT> sm;
+  __shared__ X2Shared<NT> xs;
+  __shared__ float hfirst[NT], hlast[NT];
+  __shared__ int s_item, s_solver;
+  extern __shared__ __align__(16) unsigned char dsm[];
+  float2* us = reinterpret_cast<float2*>(dsm);  // H * NT pairs
+  float2* lo = us + H * NT;                      // H * NT pairs
+  float2* es = us + 2 * H * NT;                  // H * NT pairs (Picard)
+  const int tid = threadIdx.x;
+  // The last warp solves the reduced systems: warp 0 also carries the row's
+  // first node (its Dirichlet identity row, the periodic corner terms), and
+  // on a B300 the last warp as solver ran 4-7% faster over the exact shapes
+  // of 2048 to 8192 nodes. (Co-resident CTAs already have their warps 0 on different
+  // schedulers: the hardware rotates each CTA's warps across them.)
+  constexpr int NW = NT / 32;
+  if (tid == 0) s_solver = NW - 1;
+  for (;;) {
+    if (tid == 0) s_item = atomicAdd(counter, 1);
+    __syncthreads();
+    const int item = s_item;
+    if (item >= count) return;
+    const int solver = s_solver;
+    const RowDesc rd = rows[item];
+    float* row = u + rd.offset + tid * C;
+#pragma unroll
+    for (int k = 0; k < H; ++k) {
+      const float2 x = make_float2(row[k], row[k + H]);
+      us[k * NT + tid] = x;
+      lo[k * NT + tid] = make_float2(0.f, 0.f);
+      if (k == 0) hfirst[tid] = x.x;
+      if (k == H - 1) hlast[tid] = x.y;
+    }
+    __syncthreads();
+    const float r = rd.rf, s = rd.sf;
+    if (rd.bc == BC_PERIODIC)
+      btcs_steps_x2<NT, C, BC_PERIODIC, VAR>(rd.nsteps, rd.iters, r, s, sm, xs, hfirst, hlast, us,
+                                             lo, es, solver);
+    else
+      btcs_steps_x2<NT, C, BC_DIRICHLET, VAR>(rd.nsteps, rd.iters, r, s, sm, xs, hfirst, hlast,
+                                              us, lo, es, solver);
+#pragma unroll
+    for (int k = 0; k < H; ++k) {
+      const float2 x = us[k * NT + tid];
+      row[k] = x.x;
+      row[k + H] = x.y;
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace burgers

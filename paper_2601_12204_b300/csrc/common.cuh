@@ -125,6 +125,7 @@ __device__ __forceinline__ T explicit_increment(T u, T ul, T ur, T r, T h, T s, 
 // of lane operations either way; the packed forms halve the instructions the
 // schedulers must issue, which is what limits the register-resident stencil.
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 __device__ __forceinline__ float2 sub2(float2 a, float2 b) {
   float2 d;
