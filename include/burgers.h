@@ -190,7 +190,8 @@ burgers_status burgers_explicit_advance(burgers_ctx* ctx, const burgers_batch* b
 /* Lagged-coefficient upwind BTCS solve (Sec. 2.4, Eq. 23). In place, as
  * above. Step n solves A(u^n) u^{n+1} = u^n with
  *   l_i = -r a_i^+ - s,  d_i = 1 + r|a_i| + 2s,  c_i = r a_i^- - s,  a = u^n,
- * cyclically (periodic, Sherman-Morrison with an FP64 correction) or with the
+ * cyclically (periodic, Sherman-Morrison; the correction denominator in FP64,
+ * or for FP32 as a pair of floats from error-free transformations) or with the
  * boundary nodes held (Dirichlet). */
 burgers_status burgers_btcs_advance(burgers_ctx* ctx, const burgers_batch* batch,
                                     void* u_dev, burgers_stream stream);

@@ -14,7 +14,7 @@
 // tridiagonal row per chunk in the unknowns X_{t-1}, X_t, X_{t+1}: a reduced
 // system of NT rows (cyclic for periodic rows). Warp 0 solves it: the
 // cyclic corners are split off by Sherman-Morrison (gamma = -B_0, correction
-// factor (v.y)/(1 + v.z) evaluated in FP64), each lane eliminates Q = NT/32
+// factor (v.y)/(1 + v.z) with its denominator in extended precision), each lane eliminates Q = NT/32
 // reduced rows the same way, and the remaining 32-row system is solved by
 // parallel cyclic reduction over warp shuffles. Back-substitution then
 // recovers every node from delta, alpha, gamma and the chunk-end values.

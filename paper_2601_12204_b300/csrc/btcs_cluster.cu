@@ -5,19 +5,21 @@
 // Three levels of the same partitioned elimination:
 //   chunk   each thread eliminates its C rows (as in btcs.cu) and leaves one
 //           reduced row per chunk in its unknown X_t (the chunk-end value);
-//   block   warp 0 of each CTA expresses the reduced unknowns of its chunks
+//   block   one warp of each CTA expresses the reduced unknowns of its chunks
 //           0..ti-1 through the value P before the block (the previous CTA's
 //           interface) and its own interface Y = X_ti (ti = its last chunk):
 //               X_t = y_t - alpha_t P - gamma_t Y,
 //           by solving its block with three right-hand sides at once;
 //   cluster substituting those relations into the interface rows leaves one
 //           row per CTA in Y_{k-1}, Y_k, Y_{k+1} (cyclic when periodic), which
-//           warp 0 of CTA 0 solves, one row per lane (Sherman-Morrison
-//           correction with its denominator in FP64).
-// Every CTA stages its contribution to the cluster system in its own shared
-// memory (slots double-buffered by step parity); after one cluster barrier
-// warp 0 of each CTA reads all of them through distributed shared memory and
-// solves the same small system with the same arithmetic, keeping its own Y and P and the new values
+//           one warp of every CTA solves, one row per lane (Sherman-Morrison
+//           correction with its denominator in extended precision).
+// Every CTA pushes its contribution to the cluster system into the shared
+// memory of every CTA of the cluster (slots double-buffered by step parity,
+// written through distributed shared memory before the barrier, so no remote
+// read sits on the critical path); after one cluster barrier the last warp of
+// each CTA solves the same small system from its own copies with the same
+// arithmetic, keeping its own Y and P and the new values
 // of the nodes next to its ends (computed with the owners' arithmetic from
 // their operands), so the neighbour values of the next step need no further
 // exchange. A step costs one cluster barrier and four CTA barriers.
@@ -63,6 +65,19 @@ __device__ __forceinline__ ClusterSlot<T> load_slot(const ClusterSlot<T>* p) {
   return u.s;
 }
 
+// Stores a slot into (distributed) shared memory in 16-byte pieces.
+template <typename T>
+__device__ __forceinline__ void store_slot(ClusterSlot<T>* p, const ClusterSlot<T>& s) {
+  union {
+    ClusterSlot<T> s;
+    float4 v[sizeof(ClusterSlot<T>) / 16];
+  } u;
+  u.s = s;
+  float4* dst = reinterpret_cast<float4*>(p);
+#pragma unroll
+  for (int i = 0; i < int(sizeof(ClusterSlot<T>) / 16); ++i) dst[i] = u.v[i];
+}
+
 // What the cluster solve leaves for its CTA.
 template <typename T>
 struct ClusterReply {
@@ -81,7 +96,7 @@ struct ClusterShared {
   ClusterReply<T> reply;
 };
 
-// Block solve of warp 0: rows 0..NT-1 of sm (identity beyond the block) with
+// Block solve of one warp: rows 0..NT-1 of sm (identity beyond the block) with
 // right-hand sides D, U and V; leaves the solutions in X, Z and Wg. Same
 // elimination as reduced_solve (per-lane rows, then cyclic reduction over
 // the 32 lanes), non-cyclic, three right-hand sides.
@@ -191,11 +206,11 @@ __device__ __forceinline__ void block_solve3(ClusterShared<T, NT>& cs, int lane)
   }
 }
 
-// Warp 0 of every CTA: the cluster system in the interface values Y_k, one
+// One warp of every CTA: the cluster system in the interface values Y_k, one
 // row per lane (lanes >= CS carry identity rows), from the contributions in
 // slots[par], solved by cyclic reduction over the lanes; the cyclic corners
 // are split off by Sherman-Morrison with the correction factor's denominator
-// in FP64 (sm_factor, as in the CTA-level solve). Every CTA solves the same
+// in extended precision (sm_factor, as in the CTA-level solve). Every CTA solves the same
 // system with the same arithmetic and keeps, for itself (rank), its Y and P
 // and the new values of the nodes next to its ends. Dirichlet rows have
 // identity rows at the row's ends, so the first block has no left neighbour
@@ -205,9 +220,11 @@ __device__ __forceinline__ void cluster_solve(ClusterShared<T, NT>& cs, bool per
                                               int rank, int par, cg::cluster_group& cluster) {
   const bool on = lane < CS;
   const int k = on ? lane : 0;
-  // lane k reads CTA k's contribution from that CTA's memory, and the fields
-  // of CTA k + 1's that its row needs from lane k + 1
-  const ClusterSlot<T> s = load_slot(cluster.map_shared_rank(&cs.slots[par][k], k));
+  // lane k reads CTA k's contribution (pushed into this CTA's memory before
+  // the barrier), and the fields of CTA k + 1's that its row needs from lane
+  // k + 1
+  (void)cluster;
+  const ClusterSlot<T> s = load_slot(&cs.slots[par][k]);
   struct {
     T ra0, rg0, rd0, a0, g0, y0;
     int ti;
@@ -456,10 +473,10 @@ __launch_bounds__(NT, (sizeof(T) == 4 && NT <= 512) ? 512 / NT : 1)
       sm.A[i] = A; sm.B[i] = B; sm.Cc[i] = Cc; sm.D[i] = D; sm.U[i] = Uv; cs.V[i] = Vv;
     }
     __syncthreads();
-    if (warp == 0) {
+    if (warp == Q - 1) {  // the last warp (warp 0 also carries the CTA's first node)
       block_solve3<T, NT>(cs, lane);
       __syncwarp();
-      if (lane == 0) {
+      {
         ClusterSlot<T> sl;
         sl.eah = cs.iface[0]; sl.ech = cs.iface[1]; sl.edh = cs.iface[2];
         sl.rd0 = sm.rd[sk(0)]; sl.ra0 = sm.ra[sk(0)]; sl.rg0 = sm.rg[sk(0)];
@@ -475,13 +492,13 @@ __launch_bounds__(NT, (sizeof(T) == 4 && NT <= 512) ? 512 / NT : 1)
         if constexpr (Kahan<T>::on) { sl.lf = lo[0]; sl.ll = lo[jl * NT + tl]; }
         sl.ti = tl;
         sl.jf = tl == 0 ? jl : C - 1;
-        // staged in this CTA's own memory; every CTA reads it after the
-        // cluster barrier
-        if (lane == 0) cs.slots[par][rank] = sl;
+        // pushed into every CTA's memory (lane k writes CTA k's copy), so
+        // after the cluster barrier each CTA reads its own shared memory
+        if (lane < CS) store_slot(cluster.map_shared_rank(&cs.slots[par][rank], lane), sl);
       }
     }
     cluster.sync();
-    if (warp == 0) cluster_solve<T, NT, CS>(cs, per, lane, rank, par, cluster);
+    if (warp == Q - 1) cluster_solve<T, NT, CS>(cs, per, lane, rank, par, cluster);
     __syncthreads();
     par ^= 1;
     // ---- chunk-end values from the block relations, back-substitution

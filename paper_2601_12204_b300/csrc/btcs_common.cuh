@@ -1,8 +1,9 @@
 // btcs_common.cuh -- pieces of the partitioned tridiagonal elimination shared
 // by the resident BTCS kernel and the multi-level solver: the shared-memory
-// layout of a CTA's reduced system and its warp-0 solver (Sherman-Morrison
-// split of the cyclic corners with an FP64 correction, per-lane elimination,
-// parallel cyclic reduction over warp shuffles).
+// layout of a CTA's reduced system and its one-warp solver (Sherman-Morrison
+// split of the cyclic corners with an extended-precision correction
+// denominator, per-lane elimination, parallel cyclic reduction over warp
+// shuffles).
 #pragma once
 
 #include "common.cuh"

@@ -3,7 +3,7 @@
 // Thomas elimination (cyclic rows through Sherman-Morrison, Eq. 18).
 //
 // The partitioned resident kernel pays, every step, a reduced solve on one
-// warp (parallel cyclic reduction and the FP64 Sherman-Morrison factor) and
+// warp (parallel cyclic reduction and the Sherman-Morrison factor) and
 // three CTA barriers, whatever the row length; for rows of a few hundred
 // nodes that fixed cost dominates. Here a CTA of NT threads takes NT rows
 // (rows are cost-sorted, so neighbours have similar lengths and step counts)
@@ -32,7 +32,7 @@
 // (v.y)/(1 + v.z) needs y_0 and z_0 before the backward pass, which the
 // forward pass accumulates as y_0 = sum_k prod_{j<k} (-ch_j) dh_k (the
 // back-substitution unrolled), so the backward pass applies x = y - fac z
-// directly. The dot products and the denominator are FP64 (sm_factor).
+// directly. The denominator is formed in extended precision (sm_factor).
 #include <cuda_runtime.h>
 #include <stdint.h>
 

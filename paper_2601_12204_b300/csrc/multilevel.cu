@@ -10,9 +10,10 @@
 //     D_k = dh_k - ch_k delta_{k+1}               (k+1 taken cyclically),
 // so level l+1 has ceil(m_l / C) rows and is again (cyclic) tridiagonal. Once
 // a level fits one CTA, k_ml_top solves it like the resident kernel
-// (Sherman-Morrison split of the cyclic corners, FP64 correction). The
-// recover sweeps then walk back down: each chunk repeats its elimination
-// (nothing per row is stored, which halves the memory traffic) and forms
+// (Sherman-Morrison split of the cyclic corners, extended-precision
+// correction denominator). The recover sweeps then walk back down: each
+// chunk repeats its elimination (nothing per row is stored, which halves the
+// memory traffic) and forms
 //     x_j = delta_j - alpha_j X_{k-1} - gamma_j X_k
 // from the two solved chunk-end values. Level 0 reads u^n and writes u^{n+1}
 // in place: each thread reads and writes only its own nodes.
