@@ -166,132 +166,6 @@ __global__ void __launch_bounds__(NT) k_ml_sweep(T* __restrict__ u, T* __restric
   }
 }
 
-// Level-0 rows of the implicit variants that share the tridiagonal shape
-// (Crank-Nicolson, Picard, Newton; see btcs_kernel.cuh for their algebra),
-// in increment form: CN from u^n with r/2, s/2 and the full explicit
-// increment; Picard and Newton from the iterate w = u^n + e (e = 0 in the
-// first iteration), right-hand side Delta(w) - e (Picard) or -F(w) of Eq. 11
-// (Newton).
-template <typename T>
-struct VarRows {
-  const T* row;  // u^n
-  const T* e;    // e of this iteration (nullptr: zero)
-  int64_t n;
-  int64_t base;
-  int je;
-  T r, s;
-  int var;
-  bool dir;
-  __device__ __forceinline__ T w(int64_t i) const { return e ? row[i] + e[i] : row[i]; }
-  __device__ __forceinline__ void operator()(int j, T& l, T& d, T& c, T& rhs) const {
-    const int64_t gi = base + j;
-    if (j > je) { l = T(0); d = T(1); c = T(0); rhs = T(0); return; }
-    const int64_t il = gi == 0 ? n - 1 : gi - 1, ir = gi == n - 1 ? 0 : gi + 1;
-    if (var == 1) {  // Crank-Nicolson: half the coefficients, the full step's increment
-      const T a = row[gi], ul = row[il], ur = row[ir];
-      const T rm = T(0.5) * r, sm = T(0.5) * s;
-      const T ra = rm * a;
-      l = -sm - tmax(ra, T(0));
-      c = tmin(ra, T(0)) - sm;
-      d = T(1) + T(2) * sm + tabs(ra);
-      rhs = T(2) * tfma(l, a - ul, -c * (ur - a));
-    } else {
-      const T a = w(gi), ul = w(il), ur = w(ir);
-      const T ei = e ? e[gi] : T(0);
-      if (var == 3) {  // Newton on the Eq. 11 residual (central convection)
-        const T hr = T(0.5) * r, ha = hr * a;
-        l = -ha - s;
-        c = ha - s;
-        d = tfma(hr, ur - ul, T(1) + T(2) * s);
-        rhs = tfma(s, (ur - a) - (a - ul), tfma(-ha, ur - ul, -ei));
-      } else {  // Picard: the lagged rows of the latest iterate
-        const T ra = r * a;
-        l = -s - tmax(ra, T(0));
-        c = tmin(ra, T(0)) - s;
-        d = T(1) + T(2) * s + tabs(ra);
-        rhs = tfma(l, a - ul, -c * (ur - a)) - ei;
-      }
-    }
-    if (dir && (gi == 0 || gi == n - 1)) { l = T(0); c = T(0); d = T(1); rhs = T(0); }
-  }
-};
-
-// Level-0 sweep of the implicit variants (element loads, no staging).
-// Iteration `iter` of a step reads e from ea (even iterations after the
-// first) or eb (odd ones) and, unless it is the step's last iteration, writes
-// e + delta to the other buffer; the last iteration's recover sweep writes
-// u^{n+1} = u^n + (e + delta) (FP32: Kahan term in place) into the step's
-// other u buffer and copies finished rows through, as the BTCS sweeps do.
-template <typename T, int NT, int C, bool RECOVER>
-__global__ void __launch_bounds__(NT) k_ml_sweep0v(T* __restrict__ u, T* __restrict__ u2,
-                                                   T* __restrict__ lo, T* __restrict__ ws,
-                                                   const MLRow* __restrict__ rows,
-                                                   const TileItem* __restrict__ items, int nitems,
-                                                   int level, int64_t step, int iter,
-                                                   T* __restrict__ ea, T* __restrict__ eb) {
-  (void)level;
-  T* src = (step & 1) ? u2 : u;
-  T* dst = (step & 1) ? u : u2;
-  const T* ecur = iter == 0 ? nullptr : ((iter & 1) ? ea : eb);
-  T* enext = (iter & 1) ? eb : ea;
-  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
-    const TileItem ti = items[it];
-    const MLRow& R = rows[ti.row];
-    const int64_t M = R.m[0];
-    const int64_t base = int64_t(ti.tile) * (NT * C) + int64_t(threadIdx.x) * C;
-    if (base >= M) continue;
-    const int je = int(M - 1 - base < int64_t(C - 1) ? M - 1 - base : int64_t(C - 1));
-    if (iter >= R.iters) continue;
-    const bool lastit = iter + 1 == R.iters;
-    if (step >= R.nsteps) {
-      if constexpr (RECOVER) {
-        if (lastit) {
-#pragma unroll
-          for (int j = 0; j < C; ++j)
-            if (j <= je) dst[R.offset + base + j] = src[R.offset + base + j];
-        }
-      }
-      continue;
-    }
-    T v[C], ah[C], ch[C];
-    T e_ch, e_ah, e_dh;
-    VarRows<T> rsrc{src + R.offset, ecur ? ecur + R.offset : nullptr, M, base, je,
-                    T(R.r), T(R.s), R.var, R.bc == BC_DIRICHLET};
-    chunk_forward<T, C>(v, ah, ch, je, rsrc, e_ch, e_ah, e_dh);
-    chunk_backward<T, C>(v, ah, ch, je);
-    const int64_t k = base / C;
-    const int64_t Mn = R.m[1];
-    if constexpr (!RECOVER) {
-      T* Eo = ws + R.ef[0];
-      Eo[k] = e_ch;
-      Eo[Mn + k] = e_ah;
-      Eo[2 * Mn + k] = e_dh;
-      Eo[3 * Mn + k] = v[0];
-      Eo[4 * Mn + k] = ah[0];
-      Eo[5 * Mn + k] = ch[0];
-    } else {
-      const T* Xn = ws + R.x[1];
-      const T L = k > 0 ? Xn[k - 1] : (R.bc == BC_PERIODIC ? Xn[Mn - 1] : T(0));
-      const T Xk = Xn[k];
-      const int64_t o = R.offset + base;
-#pragma unroll
-      for (int j = 0; j < C; ++j)
-        if (j <= je) {
-          const T delta = tfma(-ch[j], Xk, tfma(-ah[j], L, v[j]));
-          const T inc = ecur ? ecur[o + j] + delta : delta;
-          if (!lastit) {
-            enext[o + j] = inc;
-          } else {
-            T l0 = T(0);
-            if constexpr (Kahan<T>::on) l0 = lo[o + j];
-            dst[o + j] = comp_add(src[o + j], inc, l0);
-            if constexpr (Kahan<T>::on) lo[o + j] = l0;
-          }
-        }
-    }
-  }
-}
-
 // ---------------------------------------------------------------------------
 // Level-0 sweeps with staged tiles. A CTA's tile of NT*C nodes and its two
 // halo nodes (and, for the recover sweep in FP32, the tile's Kahan terms) are
@@ -316,8 +190,11 @@ struct Sweep0Smem {
   static constexpr int GRP = 128 / int(sizeof(T));
   __device__ __host__ static constexpr int idx(int L) { return L + VE * (L / GRP); }
   static constexpr int SSK = (idx(TILE + VE) / VE + 1) * VE;  // one buffer, elements
-  static constexpr size_t bytes(bool recover) {
-    return sizeof(T) * size_t(SSK) * 2 * ((recover && Kahan<T>::on) ? 2 : 1);
+  // buffers: the state, its Kahan terms (FP32 recover sweeps) and the
+  // iterate's e (Picard, Newton), two of each
+  static constexpr size_t bytes(bool recover, bool iterating = false) {
+    return sizeof(T) * size_t(SSK) * 2 *
+           (1 + ((recover && Kahan<T>::on) ? 1 : 0) + (iterating ? 1 : 0));
   }
 };
 
@@ -387,19 +264,54 @@ __device__ __forceinline__ void stage_tile(T* buf, const T* row, int64_t t0, int
   }
 }
 
+// Level-0 row i of variant VAR from the iterate a = w_i and its neighbours
+// (e: the iterate's e_i; unused by BTCS and CN). rm, sm, ds1 are the matrix
+// coefficients (CN: r/2, s/2).
+template <typename T, int VAR>
+__device__ __forceinline__ void ml_row(T ul, T a, T ur, T e, T rm, T sm, T ds1, T hr, T& l,
+                                       T& d, T& c, T& rhs) {
+  if constexpr (VAR == 3) {  // Newton on the Eq. 11 residual (central convection)
+    const T ha = hr * a;
+    l = -ha - sm;
+    c = ha - sm;
+    d = tfma(hr, ur - ul, ds1);
+    rhs = tfma(sm, (ur - a) - (a - ul), tfma(-ha, ur - ul, -e));
+  } else {
+    const T ra = rm * a;
+    l = -sm - tmax(ra, T(0));
+    c = tmin(ra, T(0)) - sm;
+    d = ds1 + tabs(ra);
+    rhs = tfma(l, a - ul, -c * (ur - a));  // explicit increment from the same coefficients
+    if constexpr (VAR == 1) rhs = T(2) * rhs;
+    if constexpr (VAR == 2) rhs = rhs - e;
+  }
+}
+
 // The CTA handles items blockIdx.x + k * gridDim.x, k = 0, 1, ... Their
 // (row, tile, row offset, row length) are gathered into shared memory KC at a
 // time, so staging the next tile needs no dependent global loads; the row's
 // record travels with the tile (cp.async into a per-buffer copy).
-template <typename T, int NT, int C, bool RECOVER>
-__global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? 768 : 512) / NT)
+//
+// VAR selects the level-0 rows: 0 lagged BTCS, 1 Crank-Nicolson, 2 Picard,
+// 3 Newton (see ml_row and btcs_kernel.cuh). The iterating variants (2, 3)
+// stage the iterate's e beside u^n (iteration `iter` reads e from ea or eb,
+// none in the first) and, except in the step's last iteration, the recover
+// sweep writes e + delta to the other buffer instead of updating u.
+// (the iterating variants' six FP32 tile buffers allow two CTAs of 256
+// threads per SM, so their register budget is that of two)
+template <typename T, int NT, int C, bool RECOVER, int VAR = 0>
+__global__ void __launch_bounds__(NT, ((sizeof(T) == 4 && VAR < 2) ? 768 : 512) / NT)
     k_ml_sweep0(T* __restrict__ u, T* __restrict__ u2, T* __restrict__ lo, T* __restrict__ ws,
                 const MLRow* __restrict__ rows, const TileItem* __restrict__ items, int nitems,
                 int level, int64_t step, int iter, T* __restrict__ ea, T* __restrict__ eb) {
-  (void)iter; (void)ea; (void)eb;
+  constexpr bool ITV = VAR == 2 || VAR == 3;
+  const T* ecur = (ITV && iter > 0) ? ((iter & 1) ? ea : eb) : nullptr;
+  T* enext = (iter & 1) ? eb : ea;
+  if constexpr (!ITV) { (void)ecur; (void)enext; }
   using SM = Sweep0Smem<T, NT, C>;
   constexpr int TILE = SM::TILE, VE = SM::VE, SSK = SM::SSK;
   constexpr bool KL = RECOVER && Kahan<T>::on;
+  constexpr int EBUF = KL ? 4 : 2;  // first buffer of e
   constexpr int RV = int(sizeof(MLRow) / 16);
   static_assert(sizeof(MLRow) % 16 == 0, "row record moves in 16-byte pieces");
   extern __shared__ __align__(16) unsigned char dsm[];
@@ -448,6 +360,16 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? 768 : 512) / NT)
       cp_async_vec(reinterpret_cast<char*>(&srow[b]) + 16 * (tid - 32),
                    reinterpret_cast<const char*>(rows + rowi) + 16 * (tid - 32), 16);
     if constexpr (KL) stage_tile<T, NT, C>(sbase + (2 + b) * SSK, lo + coff[slot], t0, n);
+    if constexpr (ITV) {
+      if (ecur) {  // e of the tile and of its two neighbours
+        const T* erow = ecur + coff[slot];
+        T* se = sbase + (EBUF + b) * SSK;
+        stage_tile<T, NT, C>(se, erow, t0, n);
+        if (tid == 0) cp_async_elem(se + SM::idx(VE - 1), erow + (t0 == 0 ? n - 1 : t0 - 1), true);
+        if (tid == NT - 1)
+          cp_async_elem(se + SM::idx(VE + TILE), erow + (t0 + TILE < n ? t0 + TILE : 0), true);
+      }
+    }
     cp_async_commit();
   };
 
@@ -478,10 +400,12 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? 768 : 512) / NT)
     using V = typename Vec16<T>::type;
     constexpr int NV = C / VE;
     static_assert(C % VE == 0, "a chunk is whole vectors");
-    if (base < M) {
+    const bool lastit = !ITV || iter + 1 == R.iters;
+    if (base < M && iter < R.iters) {
       const bool active = step < R.nsteps;
-      // the chunk and its two neighbours: a[0] = u_{base-1}, a[1 + j] = u_{base+j}
-      T a[C + 2];
+      // the chunk and its two neighbours: a[0] = w_{base-1}, a[1 + j] = w_{base+j}
+      // (w = u^n, plus e for the iterating variants)
+      T a[C + 2], ev[C + 2];
       a[0] = su[SM::idx(lb - 1)];
 #pragma unroll
       for (int q = 0; q < NV; ++q) {
@@ -491,6 +415,26 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? 768 : 512) / NT)
         for (int e = 0; e < VE; ++e) a[1 + q * VE + e] = wp[e];
       }
       a[C + 1] = su[SM::idx(lb + C)];
+#pragma unroll
+      for (int j = 0; j < C + 2; ++j) ev[j] = T(0);
+      T ehr = T(0);
+      if constexpr (ITV) {
+        if (ecur) {
+          const T* se = sbase + (EBUF + b) * SSK;
+          ev[0] = se[SM::idx(lb - 1)];
+#pragma unroll
+          for (int q = 0; q < NV; ++q) {
+            const V w = *reinterpret_cast<const V*>(se + SM::idx(lb + q * VE));
+            const T* wp = reinterpret_cast<const T*>(&w);
+#pragma unroll
+            for (int e = 0; e < VE; ++e) ev[1 + q * VE + e] = wp[e];
+          }
+          ev[C + 1] = se[SM::idx(lb + C)];
+          ehr = se[SM::idx(VE + TILE)];
+#pragma unroll
+          for (int j = 0; j < C + 2; ++j) a[j] = a[j] + ev[j];
+        }
+      }
       const int64_t kk = base / C;
       const int64_t Mn = R.m[1];
       T L = T(0), Xk = T(0);
@@ -501,37 +445,33 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? 768 : 512) / NT)
           Xk = Xn[kk];
         }
       }
-      const T r = T(R.r), s = T(R.s), ds1 = T(1) + T(2) * s;
+      const T r = T(R.r), s = T(R.s);
+      // matrix coefficients of the variant (CN: half the step's r and s)
+      const T rm = VAR == 1 ? T(0.5) * r : r, smv = VAR == 1 ? T(0.5) * s : s;
+      const T ds1 = T(1) + T(2) * smv, hrv = T(0.5) * r;
       const bool dir = R.bc == BC_DIRICHLET;
       T v[C], ah[C], ch[C];
       T e_ch = T(0), e_ah = T(0), e_dh = T(0);
       int je = C - 1;
       if (!active) {
-        // rows already done: copied through by the recover sweep only
+        // rows already done: copied through by the last recover sweep only
       } else if (base + C < M && !(dir && base == 0)) {
         // interior chunk: no row end, no Dirichlet end row
         auto rowsrc = [&](int j, T& l, T& d, T& c, T& rhs) {
-          const T ra = r * a[j + 1];
-          l = -s - tmax(ra, T(0));
-          c = tmin(ra, T(0)) - s;
-          d = ds1 + tabs(ra);
-          rhs = tfma(l, a[j + 1] - a[j], -c * (a[j + 2] - a[j + 1]));
+          ml_row<T, VAR>(a[j], a[j + 1], a[j + 2], ev[j + 1], rm, smv, ds1, hrv, l, d, c, rhs);
         };
         chunk_forward<T, C>(v, ah, ch, C - 1, rowsrc, e_ch, e_ah, e_dh);
         chunk_backward<T, C>(v, ah, ch, C - 1);
       } else {
         je = int(M - 1 - base < int64_t(C - 1) ? M - 1 - base : int64_t(C - 1));
         const int jend = int(M - 1 - base);  // local index of the row's last node, if here
-        const T hr = su[SM::idx(VE + TILE)];  // right neighbour of the row's last node
+        // right neighbour of the row's last node
+        const T hr = ITV ? su[SM::idx(VE + TILE)] + ehr : su[SM::idx(VE + TILE)];
         auto rowsrc = [&](int j, T& l, T& d, T& c, T& rhs) {
           const int64_t gi = base + j;
           if (j > je) { l = T(0); d = T(1); c = T(0); rhs = T(0); return; }
           const T ur = j == jend ? hr : a[j + 2];
-          const T ra = r * a[j + 1];
-          l = -s - tmax(ra, T(0));
-          c = tmin(ra, T(0)) - s;
-          d = ds1 + tabs(ra);
-          rhs = tfma(l, a[j + 1] - a[j], -c * (ur - a[j + 1]));
+          ml_row<T, VAR>(a[j], a[j + 1], ur, ev[j + 1], rm, smv, ds1, hrv, l, d, c, rhs);
           if (dir && (gi == 0 || gi == M - 1)) { l = T(0); c = T(0); d = T(1); rhs = T(0); }
         };
         chunk_forward<T, C>(v, ah, ch, je, rowsrc, e_ch, e_ah, e_dh);
@@ -547,9 +487,21 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? 768 : 512) / NT)
           Eo[4 * Mn + kk] = ah[0];
           Eo[5 * Mn + kk] = ch[0];
         }
+      } else if (ITV && !lastit) {
+        // an iteration before the step's last: e + delta for the next one
+        if (active) {
+          T* erow = enext + R.offset + base;
+#pragma unroll
+          for (int j = 0; j < C; ++j)
+            if (j <= je) {
+              const T delta = tfma(-ch[j], Xk, tfma(-ah[j], L, v[j]));
+              erow[j] = ecur ? ev[j + 1] + delta : delta;
+            }
+        }
       } else {
-        // u^{n+1} = u^n + delta (FP32: compensated), one vector at a time, stored
-        // straight from registers; rows already done are copied through
+        // u^{n+1} = u^n + delta (FP32: compensated; the iterating variants
+        // add e + delta), one vector at a time, stored straight from
+        // registers; rows already done are copied through
         T* drow = dst + R.offset + base;
         T* lrow = lo + R.offset + base;
         const int cnt = M - base < C ? int(M - base) : C;
@@ -567,7 +519,10 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 ? 768 : 512) / NT)
             for (int e = 0; e < VE; ++e) {
               const int j = q * VE + e;
               if (j <= je) {
-                const T delta = tfma(-ch[j], Xk, tfma(-ah[j], L, v[j]));
+                T delta = tfma(-ch[j], Xk, tfma(-ah[j], L, v[j]));
+                if constexpr (ITV) {
+                  if (ecur) delta = ev[j + 1] + delta;
+                }
                 if constexpr (KL) {
                   wp[e] = comp_add(wp[e], delta, wlp[e]);
                 } else {
@@ -683,11 +638,17 @@ __global__ void __launch_bounds__(NT) k_ml_top(T* __restrict__ u, T* __restrict_
                  Sweep0Smem<T, NT, C>::bytes(true)});                                         \
   reg.push_back({K_BTCS_RECOVER, DT, NT, C, 0,                                                \
                  reinterpret_cast<const void*>(&k_ml_sweep<T, NT, C, false, true>), 0});
-#define REG_SWEEPV(T, DT, NT, C)                                                             \
-  reg.push_back({K_BTCS_REDUCE, DT, NT, C, 2,                                                 \
-                 reinterpret_cast<const void*>(&k_ml_sweep0v<T, NT, C, false>), 0});         \
-  reg.push_back({K_BTCS_RECOVER, DT, NT, C, 2,                                                \
-                 reinterpret_cast<const void*>(&k_ml_sweep0v<T, NT, C, true>), 0});
+// level-0 sweeps of the implicit variants: exact = 2 + variant (1 CN, 2
+// Picard, 3 Newton)
+#define REG_SWEEPV1(T, DT, NT, C, VAR)                                                         \
+  reg.push_back({K_BTCS_REDUCE, DT, NT, C, 2 + VAR,                                           \
+                 reinterpret_cast<const void*>(&k_ml_sweep0<T, NT, C, false, VAR>),          \
+                 Sweep0Smem<T, NT, C>::bytes(false, VAR >= 2)});                              \
+  reg.push_back({K_BTCS_RECOVER, DT, NT, C, 2 + VAR,                                          \
+                 reinterpret_cast<const void*>(&k_ml_sweep0<T, NT, C, true, VAR>),           \
+                 Sweep0Smem<T, NT, C>::bytes(true, VAR >= 2)});
+#define REG_SWEEPV(T, DT, NT, C) \
+  REG_SWEEPV1(T, DT, NT, C, 1) REG_SWEEPV1(T, DT, NT, C, 2) REG_SWEEPV1(T, DT, NT, C, 3)
 #define REG_TOP(T, DT, NT, C) \
   reg.push_back({K_BTCS_TOP, DT, NT, C, 0, reinterpret_cast<const void*>(&k_ml_top<T, NT, C>), 0});
 #define REG_COPY(T, DT, NT, C) \
@@ -725,9 +686,9 @@ burgers_status plan_multilevel(burgers_ctx* ctx, const burgers_batch* batch,
   const TopShape* tops = dtype == 0 ? kTop32 : kTop64;
   const int64_t top_cap = int64_t(tops[3].nt) * tops[3].c;
   // level 0: the staged BTCS sweeps, or the implicit variants' own rows
-  const KernelEntry* red0 = find_kernel(K_BTCS_REDUCE, dtype, snt, sc, var ? 2 : 1);
+  const KernelEntry* red0 = find_kernel(K_BTCS_REDUCE, dtype, snt, sc, var ? 2 + var : 1);
   const KernelEntry* red1 = find_kernel(K_BTCS_REDUCE, dtype, snt, sc, 0);
-  const KernelEntry* rec0 = find_kernel(K_BTCS_RECOVER, dtype, snt, sc, var ? 2 : 1);
+  const KernelEntry* rec0 = find_kernel(K_BTCS_RECOVER, dtype, snt, sc, var ? 2 + var : 1);
   const KernelEntry* rec1 = find_kernel(K_BTCS_RECOVER, dtype, snt, sc, 0);
   if (!red0 || !red1 || !rec0 || !rec1) return set_error(BURGERS_EINVAL, "multi-level kernels missing");
   std::vector<MLRow> mrows;
