@@ -343,6 +343,7 @@ def run_ours(args):
                  "btcs_classes": ctx.autotune(L.BURGERS_BTCS, bb0, u0, probe_steps=50)}
         if args.tune_file:
             ctx.tune_save(args.tune_file)
+    tuned["table"] = _tune_lines(ctx)  # "key nt c k" of the shapes the timed steps use
     for _ in range(max(3, args.warmup)):
         flush.zero_()
         step([])
@@ -404,6 +405,7 @@ def run_ours(args):
     res["roofline_btcs"] = {"bound": "alu", "kernel": "k_btcs_resident<float, tuned shape, exact>",
                             "achieved": achb, "peak": peak_ops, "unit": "Tops/s (FP32 lane-instructions)",
                             "frac": achb / peak_ops, "kernel_ms": t_btcs,
+                            "traffic": traffic_record("btcs_resident_f32_4096"),
                             "peak_measured": fma32, "frac_measured": achb / fma32,
                             "per_unit": f"{BTCS_OPS} FMA-pipe FP32 instr + 1 MUFU rcp + 2 ALU per cell-update"}
     res["fma_peak_measured"] = {"fp32_tops": fma32, "fp64_tops": fma64,
