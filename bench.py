@@ -555,9 +555,12 @@ def short_rows_bench(dev, steps: int = 100):
     """Many short BTCS rows (periodic random-Fourier ensembles, 10x the CFL dt):
     the partitioned resident kernel and the per-thread Thomas kernel side by
     side, each forced through the tuning table of a context of its own, and
-    the library's default choice; FP32 and FP64 throughput, and each path's
-    relative L2 difference to the default path of the same precision (parity
-    with the oracle at these shapes is a test)."""
+    the library's default choice; FP32 and FP64 throughput, each path's
+    relative L2 difference to the default path of the same precision, and
+    each path's FP32 result against its FP64 one, per row relative to the
+    row's norm at t_final and to its initial norm (these rows decay by up to
+    three orders of magnitude over the run, which inflates the first). Parity
+    with the oracle at these shapes is a test."""
     import tempfile
 
     import torch
@@ -575,6 +578,13 @@ def short_rows_bench(dev, steps: int = 100):
     for rows, n in ((4096, 256), (16384, 512), (16384, 32), (65536, 64)):
         ens = W.fourier_ensemble(rows, n)
         rec = {}
+        res = {}  # (path, dtype name) -> result, FP64 on the device
+        u64 = torch.tensor(ens.u0, dtype=torch.float64, device=dev)
+        c0 = Context(dev.index or 0)
+        try:  # one dt per row for both precisions (from the FP64 state)
+            dts = c0.cfl_dt(Batch.from_ensemble(ens, 1.0, 0, L.BURGERS_F64), u64, CFL) * BTCS_DT_FACTOR
+        finally:
+            c0.close()
         for dt_, tdt, name in ((L.BURGERS_F32, torch.float32, "fp32"), (L.BURGERS_F64, torch.float64, "fp64")):
             u0 = torch.tensor(ens.u0, dtype=tdt, device=dev)
             r = {}
@@ -582,7 +592,6 @@ def short_rows_bench(dev, steps: int = 100):
             for path in ("default", "partitioned", "thomas"):
                 ctx = Context(dev.index or 0)
                 try:
-                    dts = ctx.cfl_dt(Batch.from_ensemble(ens, 1.0, 0, dt_), u0, CFL) * BTCS_DT_FACTOR
                     if path != "default":
                         key = lambda ex: (2 << 56) ^ (dt_ << 52) ^ (ex << 48) ^ n  # noqa: E731
                         nt, c, k = ((*part[n], 0) if path == "partitioned"
@@ -608,11 +617,22 @@ def short_rows_bench(dev, steps: int = 100):
                     d = (torch.linalg.vector_norm(w2 - wdef, dim=1) /
                          torch.linalg.vector_norm(wdef, dim=1))
                     r[path] = {"cups": cups, "l2_vs_default_max": float(d.max())}
+                    res[(path, name)] = w2
                 finally:
                     ctx.close()
             rec[name] = r
             del u0
             del wdef
+        n0 = torch.linalg.vector_norm(u64.view(rows, n), dim=1)
+        for path in ("default", "partitioned", "thomas"):
+            w32, w64 = res[(path, "fp32")], res[(path, "fp64")]
+            e = torch.linalg.vector_norm(w32 - w64, dim=1)
+            rt = e / torch.linalg.vector_norm(w64, dim=1)
+            r0 = e / n0
+            rec["fp32"][path]["fp32_vs_fp64"] = {
+                "max_rel_final": float(rt.max()), "median_rel_final": float(rt.median()),
+                "max_rel_initial": float(r0.max())}
+        del res, u64
         out[f"{rows}x{n}"] = rec
     return out
 
