@@ -284,8 +284,17 @@ burgers_status burgers_solve_host(burgers_ctx* ctx, int32_t scheme, const burger
  * per row: w = 2 for FP32 (state and compensation term), 1 for FP64, and m the
  * capacity of the kernel shape that holds the row (the smallest of 32, 128,
  * 512, 1024, 2048 and, FP32 only, 4096 nodes that is >= n). The nu gradient
- * is accumulated in FP64. Rows longer than 4096 (FP32) or 2048 (FP64) nodes:
- * EINVAL. Asynchronous on `stream`. */
+ * is accumulated in FP64. Explicit rows longer than 4096 (FP32) or 2048 (FP64)
+ * nodes take a path that advances one step per pass over tiles: checkpoints
+ * every k steps (k = ckpt_stride, else ceil(sqrt(max nsteps)) over those rows)
+ * and the k states of a segment in a second context-owned workspace of
+ * (ceil(N/k) + k + 6) * span values for FP32 (plus one byte per node for the
+ * checkpoints and two state buffers) and (ceil(N/k) + k + 4) * span for FP64,
+ * span = the end of the last long row in the batch layout, N the largest
+ * step count of those rows; their dJ/dnu is summed per tile in a fixed
+ * order. BTCS rows longer than those limits: EINVAL.
+ * Asynchronous on `stream`, except that the long-row path waits for its
+ * previous call's descriptor upload. */
 burgers_status burgers_adjoint(burgers_ctx* ctx, int32_t scheme, const burgers_batch* batch,
                                const void* u0_dev, const void* gT_dev, void* gu0_dev,
                                double* gnu_dev, int64_t ckpt_stride, burgers_stream stream);

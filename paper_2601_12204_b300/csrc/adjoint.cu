@@ -703,10 +703,15 @@ burgers_status adjoint_run(burgers_ctx* ctx, int scheme, const burgers_batch* ba
   // groups by (shape, exact): explicit rows of exactly nt * c nodes take the
   // k_adjoint_explicit_exact kernel of that shape
   std::vector<std::vector<std::pair<double, int64_t>>> groups(static_cast<size_t>(2 * nshapes));
+  std::vector<int64_t> longs;  // explicit rows longer than one CTA holds (adjoint_long.cu)
   for (int64_t b = 0; b < batch->count; ++b) {
     const burgers_instance& in = batch->inst[b];
-    if (in.n > adjoint_max_n(dtype))
-      return set_error(BURGERS_EINVAL, "adjoint: row longer than the resident limit");
+    if (in.n > adjoint_max_n(dtype)) {
+      if (scheme != BURGERS_EXPLICIT)
+        return set_error(BURGERS_EINVAL, "adjoint: BTCS row longer than the resident limit");
+      longs.push_back(b);
+      continue;
+    }
     int pick = -1;
     for (int i = 0; i < nshapes && pick < 0; ++i)
       if (int64_t(shapes[i].nt) * shapes[i].c >= in.n && shapes[i].c < in.n) pick = i;
@@ -796,6 +801,7 @@ burgers_status adjoint_run(burgers_ctx* ctx, int scheme, const burgers_batch* ba
     ctx->launches += 1;
     begin += cnt;
   }
+  if (!longs.empty()) return adjoint_long_run(ctx, batch, longs, u0, gT, gu0, gnu, stride, st);
   return BURGERS_OK;
 }
 

@@ -14,4 +14,12 @@ struct AdjRow {
   int32_t pad;
 };
 
+// Per-row record of the long-row explicit adjoint (adjoint_long.cu).
+struct AdjLongRow {
+  int32_t tile_begin, tile_end;  // the row's tiles in the item list
+  int32_t out_index;             // index of the row in the caller's batch
+  int32_t pad;
+  double ds_dnu;                 // dt / dx^2
+};
+
 }  // namespace burgers

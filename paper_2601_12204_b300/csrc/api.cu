@@ -991,6 +991,7 @@ void burgers_ctx_destroy(burgers_ctx* ctx) {
   if (ctx->io_h2d) cudaStreamDestroy(ctx->io_h2d);
   if (ctx->io_d2h) cudaStreamDestroy(ctx->io_d2h);
   if (ctx->adj_event) cudaEventDestroy(ctx->adj_event);
+  if (ctx->adjl_event) cudaEventDestroy(ctx->adjl_event);
   delete ctx;
 }
 

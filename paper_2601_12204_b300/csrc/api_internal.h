@@ -146,6 +146,10 @@ struct burgers_ctx {
   burgers::DevBuf adjdesc;  // adjoint descriptors
   burgers::HostBuf adjhost;
   cudaEvent_t adj_event = nullptr;
+  burgers::DevBuf adjlong;   // long-row explicit adjoint: states, checkpoints, lambda
+  burgers::DevBuf adjldesc;  // its descriptors
+  burgers::HostBuf adjlhost;
+  cudaEvent_t adjl_event = nullptr;
   size_t red_offsets[6] = {0, 0, 0, 0, 0, 0};
   std::map<uint64_t, burgers::RedCache> redcache;  // burgers_cfl_dt_device
   burgers_ctx();
@@ -153,6 +157,10 @@ struct burgers_ctx {
 };
 
 namespace burgers {
+// Long-row explicit adjoint (adjoint_long.cu): the rows `longs` of the batch.
+burgers_status adjoint_long_run(burgers_ctx* ctx, const burgers_batch* batch,
+                                const std::vector<int64_t>& longs, const void* u0, const void* gT,
+                                void* gu0, double* gnu, int64_t stride, cudaStream_t st);
 // var: 0 lagged BTCS, 1 Crank-Nicolson, 2 Picard, 3 Newton; iters: iterations
 // per step of the last two.
 burgers_status plan_multilevel(burgers_ctx* ctx, const burgers_batch* batch,

@@ -16,6 +16,7 @@ void register_multilevel(std::vector<KernelEntry>& reg);
 void register_adjoint(std::vector<KernelEntry>& reg);
 void register_step1_bulk(std::vector<KernelEntry>& reg);
 void register_btcs_thomas(std::vector<KernelEntry>& reg);
+void register_adjoint_long(std::vector<KernelEntry>& reg);
 
 const std::vector<KernelEntry>& kernel_registry() {
   static std::vector<KernelEntry> reg;
@@ -31,6 +32,7 @@ const std::vector<KernelEntry>& kernel_registry() {
     register_adjoint(reg);
     register_step1_bulk(reg);
     register_btcs_thomas(reg);
+    register_adjoint_long(reg);
   });
   return reg;
 }
