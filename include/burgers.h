@@ -292,9 +292,12 @@ burgers_status burgers_solve_host(burgers_ctx* ctx, int32_t scheme, const burger
  * checkpoints and two state buffers) and (ceil(N/k) + k + 4) * span for FP64,
  * span = the end of the last long row in the batch layout, N the largest
  * step count of those rows; their dJ/dnu is summed per tile in a fixed
- * order. BTCS rows longer than those limits: EINVAL.
- * Asynchronous on `stream`, except that the long-row path waits for its
- * previous call's descriptor upload. */
+ * order. BTCS rows longer than those limits: the forward states come from
+ * the library's BTCS path one step per call (checkpoints as above, k + 1
+ * states per segment, one more span for the transposed solution), and each
+ * reverse step solves A(u^n)^T nu = lambda - A(u^n)^T lambda through the
+ * multi-level solver. Asynchronous on `stream`, except that the long-row
+ * path waits for its previous call's descriptor upload. */
 burgers_status burgers_adjoint(burgers_ctx* ctx, int32_t scheme, const burgers_batch* batch,
                                const void* u0_dev, const void* gT_dev, void* gu0_dev,
                                double* gnu_dev, int64_t ckpt_stride, burgers_stream stream);

@@ -707,8 +707,6 @@ burgers_status adjoint_run(burgers_ctx* ctx, int scheme, const burgers_batch* ba
   for (int64_t b = 0; b < batch->count; ++b) {
     const burgers_instance& in = batch->inst[b];
     if (in.n > adjoint_max_n(dtype)) {
-      if (scheme != BURGERS_EXPLICIT)
-        return set_error(BURGERS_EINVAL, "adjoint: BTCS row longer than the resident limit");
       longs.push_back(b);
       continue;
     }
@@ -801,7 +799,8 @@ burgers_status adjoint_run(burgers_ctx* ctx, int scheme, const burgers_batch* ba
     ctx->launches += 1;
     begin += cnt;
   }
-  if (!longs.empty()) return adjoint_long_run(ctx, batch, longs, u0, gT, gu0, gnu, stride, st);
+  if (!longs.empty())
+    return adjoint_long_run(ctx, scheme, batch, longs, u0, gT, gu0, gnu, stride, st);
   return BURGERS_OK;
 }
 

@@ -19,6 +19,13 @@
 // FP32 lambda carries a Kahan term across the steps. Rows are aligned at their
 // first step: a row with fewer steps than the longest is copied through by
 // both kernels until its own steps begin (reverse) or after they end (forward).
+//
+// BTCS (Sec. 2.4): the forward states come from the library's own BTCS plan
+// one step per call (checkpoints every k steps, a segment's k + 1 states
+// recomputed the same way), and each reverse step solves the transposed
+// system A(u^n)^T nu = lam - A(u^n)^T lam through the multi-level solver
+// (its level-0 rows transposed, transposed_btcs_solve), then updates lambda
+// from mu = lam + nu and u^{n+1} per tile (k_adjoint_btcs_update).
 #include <math.h>
 #include <string.h>
 
@@ -132,6 +139,84 @@ __global__ void __launch_bounds__(NT) k_adjoint_step1(const T* __restrict__ u,
   }
 }
 
+// The BTCS step's reverse update of every tile, given nu from the transposed
+// solve A(u^n)^T nu = lam - A(u^n)^T lam (mu = lam + nu) and x = u^{n+1}:
+//   lam_i <- mu_i - mu_i r (-H_i x_{i-1} + (2H_i - 1) x_i + (1 - H_i) x_{i+1}),
+// H_i = [u^n_i > 0], zero for Dirichlet identity rows, and dJ/dnu += (dt/dx^2)
+// mu_i (x_{i+1} - 2x_i + x_{i-1}) over the other rows (FP64 per tile).
+template <typename T, int NT, int C>
+__global__ void __launch_bounds__(NT) k_adjoint_btcs_update(
+    const T* __restrict__ un, const T* __restrict__ x, const T* __restrict__ lam,
+    T* __restrict__ lam2, const T* __restrict__ lc, T* __restrict__ lc2, const T* __restrict__ nu,
+    const RowDesc* __restrict__ rows, const TileItem* __restrict__ items, int nitems,
+    int64_t step, double* __restrict__ gtile) {
+  constexpr bool KL = Kahan<T>::on;
+  __shared__ double wsum[NT / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const TileItem ti = items[it];
+    const RowDesc& rd = rows[ti.row];
+    const int64_t n = rd.n;
+    const int64_t g0 = int64_t(ti.tile) * (NT * C) + int64_t(threadIdx.x) * C;
+    const int cnt = g0 >= n ? 0 : (n - g0 < C ? int(n - g0) : C);
+    double part = 0.0;
+    if (cnt > 0) {
+      const T* arow = un + rd.offset;
+      const T* xrow = x + rd.offset;
+      const T* lrow = lam + rd.offset;
+      const T* nrow = nu + rd.offset;
+      T* drow = lam2 + rd.offset;
+      const bool per = rd.bc == BC_PERIODIC;
+      const bool active = step < rd.nsteps;
+      const RowCoefs<T> cf = row_coefs(rd, T(0));
+      const T r = cf.r;
+#pragma unroll
+      for (int j = 0; j < C; ++j) {
+        if (j < cnt) {
+          const int64_t gi = g0 + j;
+          const T w = lrow[gi];
+          T kc = KL ? lc[rd.offset + gi] : T(0);
+          T out = w;
+          if (active) {
+            const bool ident = !per && (gi == 0 || gi == n - 1);
+            const T nv = nrow[gi];
+            const T mu = w + nv;
+            T inc = nv;
+            if (!ident) {
+              const int64_t il = gi > 0 ? gi - 1 : n - 1, ir = gi + 1 < n ? gi + 1 : 0;
+              const T xl = xrow[il], xc = xrow[gi], xr = xrow[ir];
+              const bool H = arow[gi] > T(0);
+              const T drw = r * (H ? (xc - xl) : (xr - xc));
+              inc = tfma(-mu, drw, nv);
+              part = fma(double(mu), double((xr - xc) - (xc - xl)), part);
+            }
+            if constexpr (KL) {
+              const T y = inc - kc;
+              out = w + y;
+              kc = (out - w) - y;
+            } else {
+              out = w + inc;
+            }
+          }
+          drow[gi] = out;
+          if constexpr (KL) lc2[rd.offset + gi] = kc;
+        }
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_down_sync(FULL_MASK, part, o);
+    if (lane == 0) wsum[warp] = part;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+#pragma unroll
+      for (int q = 0; q < NT / 32; ++q) t += wsum[q];
+      gtile[it] += t;
+    }
+    __syncthreads();
+  }
+}
+
 // dJ/dnu of each long row: ds/dnu times the sum of its tiles' parts.
 __global__ void k_adj_long_gnu(const double* __restrict__ gtile, const AdjLongRow* __restrict__ lr,
                                int nrows, double* __restrict__ gnu) {
@@ -147,17 +232,35 @@ void register_adjoint_long(std::vector<KernelEntry>& reg) {
                  reinterpret_cast<const void*>(&k_adjoint_step1<float, 512, 8>), 0});
   reg.push_back({K_ADJ_EXPLICIT, 1, 256, 4, 2,
                  reinterpret_cast<const void*>(&k_adjoint_step1<double, 256, 4>), 0});
+  reg.push_back({K_ADJ_BTCS, 0, 512, 8, 2,
+                 reinterpret_cast<const void*>(&k_adjoint_btcs_update<float, 512, 8>), 0});
+  reg.push_back({K_ADJ_BTCS, 1, 256, 4, 2,
+                 reinterpret_cast<const void*>(&k_adjoint_btcs_update<double, 256, 4>), 0});
 }
 
-burgers_status adjoint_long_run(burgers_ctx* ctx, const burgers_batch* batch,
+burgers_status adjoint_long_run(burgers_ctx* ctx, int scheme, const burgers_batch* batch,
                                 const std::vector<int64_t>& longs, const void* u0, const void* gT,
                                 void* gu0, double* gnu, int64_t stride, cudaStream_t st) {
   const int dtype = batch->dtype;
   const size_t esz = dtype == 0 ? 4 : 8;
+  const bool btcs = scheme == BURGERS_BTCS;
   const int nt = dtype == 0 ? 512 : 256, c = dtype == 0 ? 8 : 4;
   const KernelEntry* kf = find_kernel(K_EXPLICIT_STEP1, dtype, nt, c, 0);
-  const KernelEntry* ka = find_kernel(K_ADJ_EXPLICIT, dtype, nt, c, 2);
+  const KernelEntry* ka = find_kernel(btcs ? K_ADJ_BTCS : K_ADJ_EXPLICIT, dtype, nt, c, 2);
   if (!kf || !ka) return set_error(BURGERS_EINVAL, "long-row adjoint kernels missing");
+  // BTCS: the forward steps and the transposed solves go through the
+  // library's own plans on a batch of the long rows, one step per call
+  std::vector<burgers_instance> one;
+  for (int64_t b : longs) {
+    burgers_instance in = batch->inst[b];
+    in.nsteps = 1;
+    one.push_back(in);
+  }
+  burgers_batch b1;
+  b1.dtype = dtype;
+  b1.reserved = 0;
+  b1.count = int64_t(one.size());
+  b1.inst = one.data();
   const int64_t tile = int64_t(nt) * c;
   std::vector<RowDesc> rows;
   std::vector<TileItem> items;
@@ -190,7 +293,9 @@ burgers_status adjoint_long_run(burgers_ctx* ctx, const burgers_batch* batch,
   }
   const int64_t k = stride > 0 ? stride : std::max<int64_t>(1, int64_t(ceil(sqrt(double(std::max<int64_t>(nmax, 1))))));
   const int64_t nck = nmax > 0 ? (nmax + k - 1) / k : 0;
-  const int64_t seg = std::min<int64_t>(k, std::max<int64_t>(nmax, 1));
+  // segment states: u^{s0} .. u^{s1-1} (explicit), .. u^{s1} (BTCS: its
+  // reverse update also reads u^{n+1})
+  const int64_t seg = std::min<int64_t>(k, std::max<int64_t>(nmax, 1)) + (btcs ? 1 : 0);
   const int64_t span_rows = span;  // elements of the caller's buffers the rows cover
   span = (span + 63) & ~int64_t(63);
   const int nitems = int(items.size());
@@ -205,7 +310,8 @@ burgers_status adjoint_long_run(burgers_ctx* ctx, const burgers_batch* batch,
   const size_t o_seg = o_ck + size_t(nck) * ckb;
   const size_t o_la = o_seg + size_t(seg) * sb, o_lb = o_la + sb;
   const size_t o_ca = o_lb + sb, o_cb = o_ca + (fp32 ? sb : 0);
-  const size_t o_gt = (o_cb + (fp32 ? sb : 0) + 255) & ~size_t(255);
+  const size_t o_nu = (o_cb + (fp32 ? sb : 0) + 255) & ~size_t(255);
+  const size_t o_gt = (o_nu + (btcs ? sb : 0) + 255) & ~size_t(255);
   const size_t total = o_gt + size_t(std::max(nitems, 1)) * sizeof(double);
   cudaError_t e = ctx->adjlong.ensure(total);
   if (e != cudaSuccess) return set_error(BURGERS_ENOMEM, "long-row adjoint workspace: out of device memory");
@@ -263,17 +369,25 @@ burgers_status adjoint_long_run(burgers_ctx* ctx, const burgers_batch* batch,
   // recomputed in the reverse pass
   int cur = 0;
   const int64_t s_last = nck > 0 ? (nck - 1) * k : 0;
-  for (int64_t s = 0; s <= s_last && nck > 0 && e == cudaSuccess; ++s) {
+  burgers_status bs = BURGERS_OK;
+  for (int64_t s = 0; s <= s_last && nck > 0 && e == cudaSuccess && bs == BURGERS_OK; ++s) {
     if (s % k == 0) {
       char* ck = w + o_ck + size_t(s / k) * ckb;
       e = cudaMemcpyAsync(ck, X[cur], sb, cudaMemcpyDeviceToDevice, st);
-      if (e == cudaSuccess && fp32) e = cudaMemcpyAsync(ck + sb, LO[cur], lb, cudaMemcpyDeviceToDevice, st);
+      if (e == cudaSuccess && fp32 && !btcs)
+        e = cudaMemcpyAsync(ck + sb, LO[cur], lb, cudaMemcpyDeviceToDevice, st);
     }
     if (e == cudaSuccess && s < s_last) {
-      e = fwd(X[cur], X[cur ^ 1], LO[cur], LO[cur ^ 1], s);
-      cur ^= 1;
+      if (btcs) {  // in place, one step (every long row; the reverse pass ignores
+                   // the steps past a row's own count)
+        bs = advance(ctx, BURGERS_BTCS, &b1, X[cur], st);
+      } else {
+        e = fwd(X[cur], X[cur ^ 1], LO[cur], LO[cur ^ 1], s);
+        cur ^= 1;
+      }
     }
   }
+  if (bs != BURGERS_OK) return bs;
   // ---- reverse pass
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(LAM[0], gT, size_t(span_rows) * esz, cudaMemcpyDeviceToDevice, st);
@@ -285,13 +399,43 @@ burgers_status adjoint_long_run(burgers_ctx* ctx, const burgers_batch* batch,
     const char* ck = w + o_ck + size_t(cidx) * ckb;
     char* S0 = w + o_seg;
     e = cudaMemcpyAsync(S0, ck, sb, cudaMemcpyDeviceToDevice, st);
-    if (e == cudaSuccess && fp32) e = cudaMemcpyAsync(LO[0], ck + sb, lb, cudaMemcpyDeviceToDevice, st);
-    int lo = 0;
-    for (int64_t j = 1; j < s1 - s0 && e == cudaSuccess; ++j) {
-      e = fwd(S0 + size_t(j - 1) * sb, S0 + size_t(j) * sb, LO[lo], LO[lo ^ 1], s0 + j - 1);
-      lo ^= 1;
+    if (btcs) {  // u^{s0} .. u^{s1} through the BTCS plan, one step a call
+      if (e == cudaSuccess) e = cudaMemcpyAsync(X[0], ck, sb, cudaMemcpyDeviceToDevice, st);
+      for (int64_t j = 1; j <= s1 - s0 && e == cudaSuccess; ++j) {
+        bs = advance(ctx, BURGERS_BTCS, &b1, X[0], st);
+        if (bs != BURGERS_OK) return bs;
+        e = cudaMemcpyAsync(S0 + size_t(j) * sb, X[0], sb, cudaMemcpyDeviceToDevice, st);
+      }
+    } else {
+      if (e == cudaSuccess && fp32)
+        e = cudaMemcpyAsync(LO[0], ck + sb, lb, cudaMemcpyDeviceToDevice, st);
+      int lo = 0;
+      for (int64_t j = 1; j < s1 - s0 && e == cudaSuccess; ++j) {
+        e = fwd(S0 + size_t(j - 1) * sb, S0 + size_t(j) * sb, LO[lo], LO[lo ^ 1], s0 + j - 1);
+        lo ^= 1;
+      }
     }
     for (int64_t s = s1 - 1; s >= s0 && e == cudaSuccess; --s) {
+      if (btcs) {
+        const void* un = S0 + size_t(s - s0) * sb;
+        const void* xn = S0 + size_t(s - s0 + 1) * sb;
+        void* nuv = w + o_nu;
+        bs = transposed_btcs_solve(ctx, &b1, un, LAM[lcur], nuv, st);
+        if (bs != BURGERS_OK) return bs;
+        const void* ls = LAM[lcur];
+        void* ld = LAM[lcur ^ 1];
+        const void* cs = LC[lcur];
+        void* cd = LC[lcur ^ 1];
+        const void* nuc = nuv;
+        int ni = nitems;
+        int64_t sv = s;
+        void* args[] = {(void*)&un, (void*)&xn, (void*)&ls, &ld, (void*)&cs, &cd, (void*)&nuc,
+                        (void*)&drows, (void*)&ditems, &ni, &sv, &gt};
+        ctx->launches += 1;
+        e = cudaLaunchKernel(ka->fn, dim3(ga), dim3(ka->nt), args, 0, st);
+        lcur ^= 1;
+        continue;
+      }
       const void* us = S0 + size_t(s - s0) * sb;
       const void* ls = LAM[lcur];
       void* ld = LAM[lcur ^ 1];

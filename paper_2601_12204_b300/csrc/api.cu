@@ -330,7 +330,8 @@ static burgers_status build_plan(burgers_ctx* ctx, int scheme, const burgers_bat
   p->scheme = scheme;
   const int rkind = resident_kind(scheme);
   const bool stencil = scheme == BURGERS_EXPLICIT || scheme == BURGERS_RK4;
-  const int64_t rlim = resident_limit(ctx, rkind, dtype);
+  // (the adjoint's transposed solves have only the multi-level path)
+  const int64_t rlim = scheme == SCHEME_BTCS_T ? 0 : resident_limit(ctx, rkind, dtype);
   struct Grp {
     Shape sh;
     int exact;
@@ -616,6 +617,7 @@ static burgers_status build_plan(burgers_ctx* ctx, int scheme, const burgers_bat
         const int var = scheme == BURGERS_CN       ? 1
                         : scheme == BURGERS_PICARD ? 2
                         : scheme == BURGERS_NEWTON ? 3
+                        : scheme == SCHEME_BTCS_T  ? 4
                                                    : 0;
         burgers_status st = plan_multilevel(ctx, batch, mlrows, p, var, iters);
         if (st != BURGERS_OK) return st;
@@ -874,6 +876,29 @@ burgers_status advance(burgers_ctx* ctx, int scheme, const burgers_batch* batch,
   Plan* p = get_plan(ctx, scheme, batch, &st, iters, false);
   if (!p) return st;
   return run_plan(ctx, p, u_dev, stream);
+}
+
+burgers_status transposed_btcs_solve(burgers_ctx* ctx, const burgers_batch* batch, const void* u,
+                                     const void* lam, void* nu, cudaStream_t st) {
+  burgers_status s = BURGERS_OK;
+  Plan* p = get_plan(ctx, SCHEME_BTCS_T, batch, &s, 1, false);
+  if (!p) return s;
+  const size_t esz = p->dtype == 0 ? 4 : 8;
+  cudaError_t e = ctx->scratch.ensure(size_t(p->scratch_elems) * esz);
+  if (e != cudaSuccess) return set_error(BURGERS_ENOMEM, "adjoint scratch: out of device memory");
+  int64_t cover = 0;  // elements of the caller's buffers the rows cover
+  for (int64_t b = 0; b < batch->count; ++b)
+    cover = std::max<int64_t>(cover, batch->inst[b].offset + batch->inst[b].n);
+  char* ea = static_cast<char*>(ctx->scratch.ptr) + size_t(p->ml_e_off) * esz;
+  char* eb = ea + size_t(p->ml_span) * esz;
+  e = cudaMemcpyAsync(ea, lam, size_t(cover) * esz, cudaMemcpyDeviceToDevice, st);
+  if (e != cudaSuccess) return cuda_error(e, "adjoint lambda copy");
+  // the state pointer changes from call to call: direct launches, no graph
+  s = run_plan(ctx, p, const_cast<void*>(u), st, false);
+  if (s != BURGERS_OK) return s;
+  e = cudaMemcpyAsync(nu, eb, size_t(cover) * esz, cudaMemcpyDeviceToDevice, st);
+  if (e != cudaSuccess) return cuda_error(e, "adjoint nu copy");
+  return BURGERS_OK;
 }
 
 // One-off plan through caller-owned descriptor buffers (no cache, no graph):

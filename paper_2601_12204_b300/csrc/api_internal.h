@@ -157,8 +157,13 @@ struct burgers_ctx {
 };
 
 namespace burgers {
-// Long-row explicit adjoint (adjoint_long.cu): the rows `longs` of the batch.
-burgers_status adjoint_long_run(burgers_ctx* ctx, const burgers_batch* batch,
+// nu = A(u)^{-T} (lam - A(u)^T lam) for every row of `batch` (its nsteps must
+// be 1), u the state in the batch layout, lam and nu device buffers of the
+// same layout covering the rows; through the multi-level solver.
+burgers_status transposed_btcs_solve(burgers_ctx* ctx, const burgers_batch* batch, const void* u,
+                                     const void* lam, void* nu, cudaStream_t st);
+// Long-row adjoint (adjoint_long.cu): the rows `longs` of the batch.
+burgers_status adjoint_long_run(burgers_ctx* ctx, int scheme, const burgers_batch* batch,
                                 const std::vector<int64_t>& longs, const void* u0, const void* gT,
                                 void* gu0, double* gnu, int64_t stride, cudaStream_t st);
 // var: 0 lagged BTCS, 1 Crank-Nicolson, 2 Picard, 3 Newton; iters: iterations
@@ -179,9 +184,12 @@ inline int resident_kind(int scheme) {
   }
 }
 inline bool valid_scheme(int scheme) { return scheme >= BURGERS_EXPLICIT && scheme <= BURGERS_NEWTON; }
+// Internal scheme of the long-row BTCS adjoint: one solve with A(u)^T per row
+// through the multi-level solver (never valid on the public entry points).
+constexpr int SCHEME_BTCS_T = 100;
 // Every scheme has a path for long rows: streaming windows (explicit Euler,
 // RK4) or the multi-level solver (BTCS and the implicit variants).
-inline bool has_long_path(int scheme) { return valid_scheme(scheme); }
+inline bool has_long_path(int scheme) { return valid_scheme(scheme) || scheme == SCHEME_BTCS_T; }
 
 burgers_status advance(burgers_ctx* ctx, int scheme, const burgers_batch* batch, void* u_dev,
                        cudaStream_t stream, int iters = 1);

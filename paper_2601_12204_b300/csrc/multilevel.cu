@@ -287,6 +287,24 @@ __device__ __forceinline__ void ml_row(T ul, T a, T ur, T e, T rm, T sm, T ds1, 
   }
 }
 
+// Row i of A(u)^T (the lagged BTCS matrix of the state u transposed: sub
+// c_{i-1}, diagonal d_i, super l_{i+1}; a Dirichlet end row of A is an
+// identity row, so its coefficients enter as 0, 1, 0) with the right-hand
+// side of the increment form lam - A^T lam, from u and lam at nodes i-1, i,
+// i+1 and whether those rows are identity rows (the adjoint of the BTCS
+// step: A^T nu = lam - A^T lam, mu = lam + nu).
+template <typename T>
+__device__ __forceinline__ void ml_row_t(T am, T a, T ap, T lm, T lam, T lp, bool idm, bool id,
+                                         bool idp, T r, T s, T ds1, T& l, T& d, T& c, T& rhs) {
+  const T cm = idm ? T(0) : tmin(r * am, T(0)) - s;   // c_{i-1}
+  const T lpp = idp ? T(0) : -s - tmax(r * ap, T(0));  // l_{i+1}
+  const T dm1 = id ? T(0) : tfma(r, tabs(a), T(2) * s);  // d_i - 1
+  l = cm;
+  d = T(1) + dm1;
+  c = lpp;
+  rhs = -tfma(cm, lm, tfma(dm1, lam, lpp * lp));
+}
+
 // The CTA handles items blockIdx.x + k * gridDim.x, k = 0, 1, ... Their
 // (row, tile, row offset, row length) are gathered into shared memory KC at a
 // time, so staging the next tile needs no dependent global loads; the row's
@@ -305,9 +323,11 @@ __global__ void __launch_bounds__(NT, ((sizeof(T) == 4 && VAR < 2) ? 768 : 512) 
                 const MLRow* __restrict__ rows, const TileItem* __restrict__ items, int nitems,
                 int level, int64_t step, int iter, T* __restrict__ ea, T* __restrict__ eb) {
   constexpr bool ITV = VAR == 2 || VAR == 3;
-  const T* ecur = (ITV && iter > 0) ? ((iter & 1) ? ea : eb) : nullptr;
-  T* enext = (iter & 1) ? eb : ea;
-  if constexpr (!ITV) { (void)ecur; (void)enext; }
+  constexpr bool TR = VAR == 4;  // transposed system of the adjoint: lam in ea, nu to eb
+  constexpr bool STAGE_E = ITV || TR;
+  const T* ecur = TR ? ea : ((ITV && iter > 0) ? ((iter & 1) ? ea : eb) : nullptr);
+  T* enext = TR ? eb : ((iter & 1) ? eb : ea);
+  if constexpr (!STAGE_E) { (void)ecur; (void)enext; }
   using SM = Sweep0Smem<T, NT, C>;
   constexpr int TILE = SM::TILE, VE = SM::VE, SSK = SM::SSK;
   constexpr bool KL = RECOVER && Kahan<T>::on;
@@ -360,8 +380,8 @@ __global__ void __launch_bounds__(NT, ((sizeof(T) == 4 && VAR < 2) ? 768 : 512) 
       cp_async_vec(reinterpret_cast<char*>(&srow[b]) + 16 * (tid - 32),
                    reinterpret_cast<const char*>(rows + rowi) + 16 * (tid - 32), 16);
     if constexpr (KL) stage_tile<T, NT, C>(sbase + (2 + b) * SSK, lo + coff[slot], t0, n);
-    if constexpr (ITV) {
-      if (ecur) {  // e of the tile and of its two neighbours
+    if constexpr (STAGE_E) {
+      if (ecur) {  // e (lam) of the tile and of its two neighbours
         const T* erow = ecur + coff[slot];
         T* se = sbase + (EBUF + b) * SSK;
         stage_tile<T, NT, C>(se, erow, t0, n);
@@ -418,7 +438,7 @@ __global__ void __launch_bounds__(NT, ((sizeof(T) == 4 && VAR < 2) ? 768 : 512) 
 #pragma unroll
       for (int j = 0; j < C + 2; ++j) ev[j] = T(0);
       T ehr = T(0);
-      if constexpr (ITV) {
+      if constexpr (STAGE_E) {
         if (ecur) {
           const T* se = sbase + (EBUF + b) * SSK;
           ev[0] = se[SM::idx(lb - 1)];
@@ -431,8 +451,10 @@ __global__ void __launch_bounds__(NT, ((sizeof(T) == 4 && VAR < 2) ? 768 : 512) 
           }
           ev[C + 1] = se[SM::idx(lb + C)];
           ehr = se[SM::idx(VE + TILE)];
+          if constexpr (ITV) {
 #pragma unroll
-          for (int j = 0; j < C + 2; ++j) a[j] = a[j] + ev[j];
+            for (int j = 0; j < C + 2; ++j) a[j] = a[j] + ev[j];
+          }
         }
       }
       const int64_t kk = base / C;
@@ -455,7 +477,18 @@ __global__ void __launch_bounds__(NT, ((sizeof(T) == 4 && VAR < 2) ? 768 : 512) 
       int je = C - 1;
       if (!active) {
         // rows already done: copied through by the last recover sweep only
-      } else if (base + C < M && !(dir && base == 0)) {
+      } else if (base + C < M && !dir) {
+        // interior chunk of a periodic row: no row end
+        auto rowsrc = [&](int j, T& l, T& d, T& c, T& rhs) {
+          if constexpr (TR)
+            ml_row_t<T>(a[j], a[j + 1], a[j + 2], ev[j], ev[j + 1], ev[j + 2], false, false, false,
+                        r, s, ds1, l, d, c, rhs);
+          else
+            ml_row<T, VAR>(a[j], a[j + 1], a[j + 2], ev[j + 1], rm, smv, ds1, hrv, l, d, c, rhs);
+        };
+        chunk_forward<T, C>(v, ah, ch, C - 1, rowsrc, e_ch, e_ah, e_dh);
+        chunk_backward<T, C>(v, ah, ch, C - 1);
+      } else if (!TR && base + C < M && !(dir && base == 0)) {
         // interior chunk: no row end, no Dirichlet end row
         auto rowsrc = [&](int j, T& l, T& d, T& c, T& rhs) {
           ml_row<T, VAR>(a[j], a[j + 1], a[j + 2], ev[j + 1], rm, smv, ds1, hrv, l, d, c, rhs);
@@ -471,8 +504,17 @@ __global__ void __launch_bounds__(NT, ((sizeof(T) == 4 && VAR < 2) ? 768 : 512) 
           const int64_t gi = base + j;
           if (j > je) { l = T(0); d = T(1); c = T(0); rhs = T(0); return; }
           const T ur = j == jend ? hr : a[j + 2];
-          ml_row<T, VAR>(a[j], a[j + 1], ur, ev[j + 1], rm, smv, ds1, hrv, l, d, c, rhs);
-          if (dir && (gi == 0 || gi == M - 1)) { l = T(0); c = T(0); d = T(1); rhs = T(0); }
+          if constexpr (TR) {
+            const T lr = j == jend ? ehr : ev[j + 2];
+            // Dirichlet: rows 0 and M-1 are identity rows of A, and there is
+            // no row beyond either end
+            auto ident = [&](int64_t g) { return dir && (g <= 0 || g >= M - 1); };
+            ml_row_t<T>(a[j], a[j + 1], ur, ev[j], ev[j + 1], lr, ident(gi - 1), ident(gi),
+                        ident(gi + 1), r, s, ds1, l, d, c, rhs);
+          } else {
+            ml_row<T, VAR>(a[j], a[j + 1], ur, ev[j + 1], rm, smv, ds1, hrv, l, d, c, rhs);
+            if (dir && (gi == 0 || gi == M - 1)) { l = T(0); c = T(0); d = T(1); rhs = T(0); }
+          }
         };
         chunk_forward<T, C>(v, ah, ch, je, rowsrc, e_ch, e_ah, e_dh);
         chunk_backward<T, C>(v, ah, ch, je);
@@ -487,15 +529,16 @@ __global__ void __launch_bounds__(NT, ((sizeof(T) == 4 && VAR < 2) ? 768 : 512) 
           Eo[4 * Mn + kk] = ah[0];
           Eo[5 * Mn + kk] = ch[0];
         }
-      } else if (ITV && !lastit) {
+      } else if (TR || (ITV && !lastit)) {
         // an iteration before the step's last: e + delta for the next one
+        // (the transposed system: nu itself)
         if (active) {
           T* erow = enext + R.offset + base;
 #pragma unroll
           for (int j = 0; j < C; ++j)
             if (j <= je) {
               const T delta = tfma(-ch[j], Xk, tfma(-ah[j], L, v[j]));
-              erow[j] = ecur ? ev[j + 1] + delta : delta;
+              erow[j] = (!TR && ecur) ? ev[j + 1] + delta : delta;
             }
         }
       } else {
@@ -647,8 +690,9 @@ __global__ void __launch_bounds__(NT) k_ml_top(T* __restrict__ u, T* __restrict_
   reg.push_back({K_BTCS_RECOVER, DT, NT, C, 2 + VAR,                                          \
                  reinterpret_cast<const void*>(&k_ml_sweep0<T, NT, C, true, VAR>),           \
                  Sweep0Smem<T, NT, C>::bytes(true, VAR >= 2)});
-#define REG_SWEEPV(T, DT, NT, C) \
-  REG_SWEEPV1(T, DT, NT, C, 1) REG_SWEEPV1(T, DT, NT, C, 2) REG_SWEEPV1(T, DT, NT, C, 3)
+#define REG_SWEEPV(T, DT, NT, C)                                                         \
+  REG_SWEEPV1(T, DT, NT, C, 1) REG_SWEEPV1(T, DT, NT, C, 2) REG_SWEEPV1(T, DT, NT, C, 3) \
+  REG_SWEEPV1(T, DT, NT, C, 4)
 #define REG_TOP(T, DT, NT, C) \
   reg.push_back({K_BTCS_TOP, DT, NT, C, 0, reinterpret_cast<const void*>(&k_ml_top<T, NT, C>), 0});
 #define REG_COPY(T, DT, NT, C) \
@@ -739,7 +783,8 @@ burgers_status plan_multilevel(burgers_ctx* ctx, const burgers_batch* batch,
   // iterating variants two planes of e = w - u^n (read by one iteration,
   // written by it for the next)
   p->ml_e_off = dtype == 0 ? 2 * span : span;
-  p->scratch_elems = std::max<int64_t>(p->scratch_elems, p->ml_e_off + (nit > 1 ? 2 * span : 0));
+  p->scratch_elems =
+      std::max<int64_t>(p->scratch_elems, p->ml_e_off + ((nit > 1 || var == 4) ? 2 * span : 0));
   p->ml_bytes.resize(mrows.size() * sizeof(MLRow));
   memcpy(p->ml_bytes.data(), mrows.data(), p->ml_bytes.size());
   // item lists: sweeps of each level, then one list per top shape
@@ -820,7 +865,8 @@ burgers_status plan_multilevel(burgers_ctx* ctx, const burgers_batch* batch,
       p->launches.push_back(L);
     }
   }
-  if (smax % 2 == 1) {  // the result is in the scratch copy
+  if (smax % 2 == 1 && var != 4) {  // the result is in the scratch copy (the transposed
+                                    // solve writes only nu)
     Launch L;
     L.type = LAUNCH_ML;
     L.k = find_kernel(K_BTCS_TOP, dtype, snt, sc, 1);
