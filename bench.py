@@ -854,6 +854,7 @@ def extras(args, ctx, ens, u0, batches, probe, dev, world, rank):
     del ha, hb, hu0
 
     out["large_grid"] = large_grid_bench(ctx, dev)
+    out["adjoint_long"] = long_adjoint_bench(ctx, dev)
     return out
 
 
@@ -918,6 +919,64 @@ def long_variants_bench(ctx, dev, rows: int = 512, n: int = 32768, steps: int = 
                      "l2_fp32_vs_fp64": {"max": float(np.max(rel)), "median": float(np.median(rel))}}
         del w32, w64
     del u32, u64
+    return out
+
+
+def long_adjoint_bench(ctx, dev, rows: int = 64, n: int = 65536):
+    """Gradients by the long-row adjoint: `rows` periodic random-Fourier rows
+    of n nodes (longer than one CTA holds), explicit 200 steps at the CFL
+    step and BTCS 20 steps at 10x it, FP32 and FP64; forward cell-updates per
+    second of the adjoint call (checkpointed forward, segment recompute and
+    reverse sweep) and the forward's own rate for comparison. FP32 dJ/du0
+    against FP64 per row."""
+    import torch
+
+    from paper_2601_12204_b300 import _lib as L
+    from paper_2601_12204_b300 import workloads as W
+    from paper_2601_12204_b300.api import Batch
+    F32, F64 = L.BURGERS_F32, L.BURGERS_F64
+    stream = torch.cuda.current_stream(dev)
+    ens = W.fourier_ensemble(rows, n, seed=4242)
+    u64 = torch.tensor(ens.u0, dtype=torch.float64, device=dev)
+    dt0 = ctx.cfl_dt(Batch.from_ensemble(ens, 1.0, 0, F64), u64, CFL)
+    out = {"rows": rows, "n": n, "bc": "periodic"}
+    for name, scheme, steps, fac in (("explicit", L.BURGERS_EXPLICIT, 200, 1.0),
+                                     ("btcs", L.BURGERS_BTCS, 20, BTCS_DT_FACTOR)):
+        rec = {"steps": steps}
+        grads = {}
+        for dn, dt_, tdt in (("fp32", F32, torch.float32), ("fp64", F64, torch.float64)):
+            b = Batch.from_ensemble(ens, dt0 * fac, steps, dt_)
+            u0 = u64.to(tdt)
+            w = u0.clone()
+            ctx.advance(scheme, b, w)  # dJ/du(T) = u(T): J = |u(T)|^2 / 2
+            gT = w.clone()
+            gu0 = torch.empty_like(u0)
+            gnu = torch.zeros(rows, dtype=torch.float64, device=dev)
+            ctx.adjoint(scheme, b, u0, gT, gu0, gnu)  # warm: workspace, plans
+            torch.cuda.synchronize()
+            a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            ctx.adjoint(scheme, b, u0, gT, gu0, gnu)
+            z.record(stream)
+            torch.cuda.synchronize()
+            t_adj = a.elapsed_time(z) / 1e3
+            w.copy_(u0)
+            a.record(stream)
+            ctx.advance(scheme, b, w)
+            z.record(stream)
+            torch.cuda.synchronize()
+            t_fwd = a.elapsed_time(z) / 1e3
+            cells = float(rows) * n * steps
+            rec[dn] = {"gradient_cups": cells / t_adj, "forward_cups": cells / t_fwd,
+                       "adjoint_over_forward": t_adj / t_fwd}
+            grads[dn] = gu0.double().view(rows, n)
+        d = (torch.linalg.vector_norm(grads["fp32"] - grads["fp64"], dim=1) /
+             torch.linalg.vector_norm(grads["fp64"], dim=1))
+        rec["grad_u0_fp32_vs_fp64_rel_l2"] = {"max": float(d.max()), "median": float(d.median())}
+        out[name] = rec
+    out["note"] = ("rows longer than one CTA: explicit one step per pass over tiles, BTCS one "
+                   "step per call and transposed solves through the multi-level solver; "
+                   "checkpoints every ceil(sqrt(steps)) steps")
     return out
 
 
