@@ -355,8 +355,8 @@ __launch_bounds__(NT, (sizeof(T) == 4 && NT <= 512) ? 512 / NT : 1)
   }
   cluster.sync();
   const T r = T(rd.r), s = T(rd.s), ds1 = T(1) + T(2) * s;
-  // Warps whose chunks all lie inside the row and hold no Dirichlet end row
-  // take the branch-free path; any other warp takes the general one with all
+  // Warps whose chunks all end on their last node (or lie wholly past the
+  // row's end) take the branch-free path; any other warp takes the general one with all
   // its lanes (one pass instead of both, one after the other, in a diverged
   // warp), and warps past the row's end skip the sweep. The cluster barrier
   // paces every step by the slowest CTA, so a ragged last CTA must not be
@@ -366,13 +366,15 @@ __launch_bounds__(NT, (sizeof(T) == 4 && NT <= 512) ? 512 / NT : 1)
   // the system being diagonally dominant) and restarts the backward sweep at
   // the chunk's end row. Dirichlet identity rows: the row's first node is
   // replaced at j = 0; its last one only sets the chunk's end relation, which
-  // is zeroed after the sweep.
+  // is zeroed after the sweep. Both are selects that the branch-free path
+  // makes too, so a Dirichlet end in a full chunk does not send its warp
+  // (and through the barriers its CTA and cluster) down the general path.
   const bool dfirst = !per && rank == 0 && tid == 0;
   const bool dlast = !per && lastcta && tid == tl;
   // (lanes past the row's end may take the branch-free path too: their
   // values are never read)
   const bool plainchunk =
-      __all_sync(FULL_MASK, ((je == C - 1 && jstar >= C - 1) || jstar < 0) && !dfirst && !dlast);
+      __all_sync(FULL_MASK, (je == C - 1 && jstar >= C - 1) || jstar < 0);
   const bool padwarp = __all_sync(FULL_MASK, jstar < 0);
   const bool endslot = jstar >= 0 && jstar < C - 1;  // chunk with padding after node n-1
   T ch[C], ah[C], dd[C];
@@ -399,9 +401,7 @@ __launch_bounds__(NT, (sizeof(T) == 4 && NT <= 512) ? 512 / NT : 1)
         T c = tmin(ra, T(0)) - s;
         T d = ds1 + tabs(ra);
         T rhs = tfma(l, a - ul, -c * (ur - a));
-        if constexpr (!FULL) {
-          if (j == 0 && dfirst) { l = T(0); c = T(0); d = T(1); rhs = T(0); }
-        }
+        if (j == 0 && dfirst) { l = T(0); c = T(0); d = T(1); rhs = T(0); }
         const T inv = recip(tfma(-l, chp, d));
         const T li = l * inv;
         chp = c * inv;
@@ -425,6 +425,7 @@ __launch_bounds__(NT, (sizeof(T) == 4 && NT <= 512) ? 512 / NT : 1)
           cgm = -cj * cgm;
           dd[j] = cd; ah[j] = ca; ch[j] = cgm;
         }
+        if (dlast) { e_ch = T(0); e_ah = T(0); e_dh = T(0); }
       } else {
         // as above, restarted at the end row je (values past it are unused)
         e_ch = ch[C - 1]; e_ah = ah[C - 1]; e_dh = dd[C - 1];
