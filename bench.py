@@ -1149,6 +1149,7 @@ def serve_bench(ctx, dev, duration: float, rate: float = 20000.0, plain_seconds:
     # to completion plus the submission's lateness, so a client that falls
     # behind the trace cannot hide queueing time
     lat = np.array([done[t][3] - done[t][1] + lag[t] for t in order if t in done and done[t][0] == 0])
+    arr = np.array([q.t_arrive for q, t in zip(trace, order) if t in done and done[t][0] == 0])
     t_first = min(done[t][1] for t in order if t in done)
     t_last = max(done[t][3] for t in order if t in done)
     ok = [i for i, t in enumerate(order) if t in done and done[t][0] == 0]
@@ -1164,7 +1165,15 @@ def serve_bench(ctx, dev, duration: float, rate: float = 20000.0, plain_seconds:
            "active_max": stats["active_max"], "pool_bytes": stats["pool_bytes"],
            "pool_used_max": stats["pool_used_max"], "slice_steps": 256, "dtype": "f32",
            "worker_s": {"enqueue": stats["t_enqueue_s"], "slice_wait": stats["t_slice_s"],
-                        "copies": stats["t_copy_s"]}}
+                        "copies": stats["t_copy_s"]},
+           # device time inside the slices and between them (the device idle
+           # while the worker plans), against the server's wall time
+           "device_s": {"in_slices": stats["t_gpu_s"], "between_slices": stats["t_gpu_gap_s"],
+                        "wall": t_last - t_first},
+           # whether the server keeps up: latency of the requests arriving in
+           # the first and in the second half of the trace
+           "p99_ms_by_half": [1e3 * float(np.percentile(h, 99)) if h.size else None
+                              for h in (lat[arr < 0.5 * duration], lat[arr >= 0.5 * duration])]}
     if plain_seconds <= 0:
         return res
     # plain path: one request per launch, FIFO in arrival order

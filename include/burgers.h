@@ -404,6 +404,10 @@ typedef struct {
   double t_enqueue_s; /* worker time spent planning and enqueuing slices (host) */
   double t_slice_s;   /* worker time waiting for slices to finish on the device */
   double t_copy_s;    /* worker time in admission and result copies */
+  double t_gpu_s;     /* device time inside the slices (first to last stamp of each on the
+                         worker's stream, read as each slice retires) */
+  double t_gpu_gap_s; /* device time between one slice's last stamp and the next one's
+                         first: the device idle on the worker's stream */
 } burgers_serve_stats;
 
 /* Creates a server on ctx (cfg may be NULL for defaults). The pool is half

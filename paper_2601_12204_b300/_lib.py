@@ -123,7 +123,8 @@ class burgers_serve_stats(ctypes.Structure):
                 ("pending", ctypes.c_int64), ("active", ctypes.c_int64),
                 ("pool_bytes", ctypes.c_int64), ("pool_used", ctypes.c_int64),
                 ("now_s", ctypes.c_double), ("t_enqueue_s", ctypes.c_double),
-                ("t_slice_s", ctypes.c_double), ("t_copy_s", ctypes.c_double)]
+                ("t_slice_s", ctypes.c_double), ("t_copy_s", ctypes.c_double),
+                ("t_gpu_s", ctypes.c_double), ("t_gpu_gap_s", ctypes.c_double)]
 
 
 SIGNATURES.update({

@@ -101,11 +101,12 @@ __device__ __forceinline__ void btcs_steps(int64_t nsteps, int iters, T r, T s, 
   // keep the general sweep in every warp (two copies of a 32-node sweep
   // spill).
   constexpr bool WSPLIT = !EXACT && sizeof(T) == 4 && C <= 16 && NT <= 512;
-  // (a chunk that ends exactly at node n-1 is an interior one, a Dirichlet
-  // end row there only zeroing the chunk's end relation after the sweep;
-  // lanes past the end compute values nobody reads)
+  // (a chunk that ends exactly at node n-1 is an interior one, unless it
+  // holds a Dirichlet end row; lanes past the end compute values nobody reads)
   const bool rw_edge =
-      WSPLIT ? __any_sync(FULL_MASK, jstar >= 0 && jstar < C - 1) != 0 : !EXACT;
+      WSPLIT ? __any_sync(FULL_MASK, (jstar >= 0 && jstar < C - 1) ||
+                                         (BCT == BC_DIRICHLET && tid == tl)) != 0
+             : !EXACT;
   const bool rw_pad = WSPLIT && __all_sync(FULL_MASK, jstar < 0) != 0;
   const bool endslot = !EXACT && jstar >= 0 && jstar < C - 1;  // padding after node n-1
   // matrix coefficients (Crank-Nicolson: half of the step's r and s)
@@ -214,9 +215,6 @@ __device__ __forceinline__ void btcs_steps(int64_t nsteps, int iters, T r, T s, 
         ca = tfma(-cj, ca, ah[j]);
         cg = -cj * cg;
         dd[j] = cd; ah[j] = ca; ch[j] = cg;
-      }
-      if constexpr (!EXACT && BCT == BC_DIRICHLET) {
-        if (tid == tl) { e_ch = T(0); e_ah = T(0); e_dh = T(0); }
       }
     } else {
       // restarted at the end row je; rows past it (padding, finite values of

@@ -44,6 +44,10 @@
 
 namespace burgers {
 
+// Slices whose device-time stamps are kept at once (two in flight plus the
+// previous end of each).
+constexpr int kSliceRing = 4;
+
 static double now_s() {
   struct timespec ts;
   clock_gettime(CLOCK_MONOTONIC, &ts);
@@ -284,6 +288,10 @@ struct burgers_server {
   burgers::Region short_region, long_region;
   cudaStream_t stream = nullptr, stream_b = nullptr;  // BTCS slices run on stream_b
   cudaEvent_t ev[2] = {nullptr, nullptr};  // end of the slices in flight (by parity)
+  // device-time stamps of the start and end of each slice, a ring of four
+  // slices (two in flight, and the previous end of each kept for the gap)
+  cudaEvent_t tev[2 * burgers::kSliceRing] = {};
+  int64_t slices_enqueued = 0;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   std::thread worker;
   std::mutex mu;
@@ -373,8 +381,28 @@ static burgers_status wait_event(burgers_server* sv, cudaEvent_t ev, double time
 // copies of the requests it finishes) and those requests.
 struct InFlight {
   bool on = false;
+  int64_t no = 0;  // slice number (its timing events: slot no % kSliceRing)
   std::vector<Req*> finished;
 };
+
+// Device time of slice f (its first to its last stamp on the worker's stream)
+// and the idle time before it (from the previous slice's last stamp), added
+// to the statistics; both stamps have completed once the slice has.
+static void account_slice(burgers_server* sv, const InFlight& f) {
+  const int i = int(f.no % kSliceRing);
+  float ms = 0.f;
+  if (cudaEventElapsedTime(&ms, sv->tev[2 * i], sv->tev[2 * i + 1]) == cudaSuccess)
+    sv->stats.t_gpu_s += 1e-3 * ms;
+  else
+    (void)cudaGetLastError();
+  if (f.no > 0) {
+    const int j = int((f.no - 1) % kSliceRing);
+    if (cudaEventElapsedTime(&ms, sv->tev[2 * j + 1], sv->tev[2 * i]) == cudaSuccess)
+      sv->stats.t_gpu_gap_s += 1e-3 * std::max(0.f, ms);
+    else
+      (void)cudaGetLastError();
+  }
+}
 
 // Waits for a slice in flight and reports the requests it finished.
 static burgers_status retire(burgers_server* sv, InFlight& f, int idx) {
@@ -384,6 +412,7 @@ static burgers_status retire(burgers_server* sv, InFlight& f, int idx) {
   std::lock_guard<std::mutex> lk(sv->mu);
   const double t = now_s() - sv->t0;
   sv->stats.t_slice_s += now_s() - tw;
+  account_slice(sv, f);
   for (Req* q : f.finished) {
     q->state = RQ_DONE;
     q->t_done = t;
@@ -490,7 +519,9 @@ static void worker_loop(burgers_server* sv) {
     // ---- copy the new requests' u0 into their slots (one kernel for those
     // in mapped page-locked buffers, a copy each for the rest)
     double tw0 = now_s();
-    cudaError_t e = cudaSuccess;
+    const int64_t sno = sv->slices_enqueued;
+    const int ring = int(sno % kSliceRing);
+    cudaError_t e = cudaEventRecord(sv->tev[2 * ring], sv->stream);
     CopyStage& sin = sv->stage_in[par];
     sin.clear();
     for (Req* q : admitted) {
@@ -559,6 +590,7 @@ static void worker_loop(burgers_server* sv) {
       if (e != cudaSuccess) break;
     }
     if (e == cudaSuccess) e = launch_copies(sv, sout);
+    if (e == cudaSuccess) e = cudaEventRecord(sv->tev[2 * ring + 1], sv->stream);
     if (e == cudaSuccess) e = cudaEventRecord(sv->ev[par], sv->stream);
     if (e != cudaSuccess) {
       fail_worker(sv, fl, cuda_error(e, "serve result copy"), burgers_last_error());
@@ -583,6 +615,8 @@ static void worker_loop(burgers_server* sv) {
           sv->stats.pool_used_max, sv->short_region.used() + sv->long_region.used());
     }
     fl[par].on = true;
+    fl[par].no = sno;
+    sv->slices_enqueued = sno + 1;
     fl[par].finished.swap(finished);
     // keep at most two slices in flight: wait for the previous one
     if (fl[par ^ 1].on) {
@@ -647,6 +681,8 @@ burgers_status burgers_serve_create(burgers_ctx* ctx, const burgers_serve_cfg* c
     e = cudaEventCreateWithFlags(&sv->ev[k], cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sv->ev_fork, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sv->ev_join, cudaEventDisableTiming);
+  for (int k = 0; k < 2 * kSliceRing && e == cudaSuccess; ++k)
+    e = cudaEventCreate(&sv->tev[k]);
   if (e != cudaSuccess) {
     cudaFree(sv->pool);
     return cuda_error(e, "serve stream");
@@ -809,6 +845,8 @@ burgers_status burgers_serve_destroy(burgers_server* sv) {
     if (sv->ev[k]) cudaEventDestroy(sv->ev[k]);
   if (sv->ev_fork) cudaEventDestroy(sv->ev_fork);
   if (sv->ev_join) cudaEventDestroy(sv->ev_join);
+  for (int k = 0; k < 2 * kSliceRing; ++k)
+    if (sv->tev[k]) cudaEventDestroy(sv->tev[k]);
   if (sv->stream_b) cudaStreamDestroy(sv->stream_b);
   if (sv->stream) cudaStreamDestroy(sv->stream);
   if (sv->pool) cudaFree(sv->pool);
