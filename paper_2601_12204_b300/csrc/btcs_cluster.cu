@@ -3,8 +3,9 @@
 // the shared memory of CS CTAs for all of its steps, as in the resident kernel.
 //
 // Three levels of the same partitioned elimination:
-//   chunk   each thread eliminates its C rows (as in btcs.cu) and leaves one
-//           reduced row per chunk in its unknown X_t (the chunk-end value);
+//   chunk   each thread eliminates its C (or C - 1) rows (as in btcs.cu) and
+//           leaves one reduced row per chunk in its unknown X_t (the
+//           chunk-end value);
 //   block   one warp of each CTA expresses the reduced unknowns of its chunks
 //           0..ti-1 through the value P before the block (the previous CTA's
 //           interface) and its own interface Y = X_ti (ti = its last chunk):
@@ -306,17 +307,25 @@ __device__ __forceinline__ void cluster_solve(ClusterShared<T, NT>& cs, bool per
   }
 }
 
-// One cluster per row: CTA k holds nodes [k W, min((k+1) W, n)), W = NT*C,
-// thread t its chunk of C nodes. Rows have (CS-1) W < n <= CS W.
+// One cluster per row (rows have (CS-1) W < n <= CS W, W = NT*C). The row's
+// nodes are spread evenly over the CS CTAs, and each CTA's nk nodes over
+// tk = ceil(nk / C) chunks of C or C - 1 nodes, the last bk = tk C - nk of
+// them one node short; threads from tk on hold no nodes. Since nk > W/2 - 1,
+// tk > NT/2 > C > bk, so every row length has such a split. A short chunk
+// ends at node C - 2, a position known at compile time: every warp runs the
+// one sweep, and a short chunk costs a few selects at that position (a chunk
+// ending at an arbitrary node would need a select at every node, and the
+// warp holding it would pace the CTA and, through the cluster barrier, every
+// CTA of the row).
 template <typename T, int NT, int C, int CS>
 __global__ void __cluster_dims__(CS, 1, 1)
 __launch_bounds__(NT, (sizeof(T) == 4 && NT <= 512) ? 512 / NT : 1)
     k_btcs_cluster(T* __restrict__ u, const RowDesc* __restrict__ rows, int count,
                    int* __restrict__ counter) {
   (void)counter;
-  constexpr int W = NT * C;
   constexpr int Q = NT / 32;
   static_assert(CS >= 2 && CS <= 16, "slots hold at most 16 CTAs");
+  static_assert(C >= 3, "a short chunk keeps at least two nodes");
   cg::cluster_group cluster = cg::this_cluster();
   const int rank = int(cluster.block_rank());
   const int item = int(blockIdx.x) / CS;
@@ -331,20 +340,27 @@ __launch_bounds__(NT, (sizeof(T) == 4 && NT <= 512) ? 512 / NT : 1)
   const int n = rd.n;
   const bool per = rd.bc == BC_PERIODIC;
   const bool lastcta = rank == CS - 1;
-  const int nc = lastcta ? n - rank * W : W;  // nodes of this CTA
-  const int tl = (nc - 1) / C;                // its last chunk (the interface)
-  const int jstar = nc - 1 - tid * C;         // local index of the CTA's last node
-  const int je = jstar < C ? jstar : C - 1;   // end row of this chunk
-  T* row = u + rd.offset + int64_t(rank) * W;
+  const int nbase = n / CS, nrem = n % CS;
+  const int nk = nbase + (rank < nrem ? 1 : 0);                    // nodes of this CTA
+  const int64_t kstart = int64_t(rank) * nbase + (rank < nrem ? rank : nrem);
+  const int tk = (nk + C - 1) / C;            // chunks holding nodes
+  const int bk = tk * C - nk;                 // short chunks among them (the last ones)
+  const int tl = tk - 1;                      // its last chunk (the interface)
+  const int ts = tk - bk;                     // first short chunk
+  const bool active = tid < tk;
+  const bool shrt = active && tid >= ts;      // chunk of C - 1 nodes
+  const int cstart = tid * C - (shrt ? tid - ts : 0);  // first node of the chunk in the CTA
+  const int clen = active ? (shrt ? C - 1 : C) : 0;
+  T* row = u + rd.offset + kstart;
   // ---- load, publish the chunk edges and this CTA's ends to its neighbours
 #pragma unroll
   for (int j = 0; j < C; ++j) {
-    const int li = tid * C + j;
-    const T x = li < nc ? row[li] : T(0);
+    const T x = j < clen ? row[cstart + j] : T(0);
     us[j * NT + tid] = x;
     if constexpr (Kahan<T>::on) lo[j * NT + tid] = T(0);
     if (j == 0) cs.hfirst[tid] = x;
-    if (j == je) cs.hlast[tid] = x;
+    if (j == C - 2 && shrt) cs.hlast[tid] = x;
+    if (j == C - 1 && !shrt) cs.hlast[tid] = x;
   }
   __syncthreads();
   cluster.sync();  // every CTA of the cluster runs before any addresses another's memory
@@ -355,41 +371,29 @@ __launch_bounds__(NT, (sizeof(T) == 4 && NT <= 512) ? 512 / NT : 1)
   }
   cluster.sync();
   const T r = T(rd.r), s = T(rd.s), ds1 = T(1) + T(2) * s;
-  // Warps whose chunks all end on their last node (or lie wholly past the
-  // row's end) take the branch-free path; any other warp takes the general one with all
-  // its lanes (one pass instead of both, one after the other, in a diverged
-  // warp), and warps past the row's end skip the sweep. The cluster barrier
-  // paces every step by the slowest CTA, so a ragged last CTA must not be
-  // slow: the general path runs the same forward sweep (the chunk holding the
-  // row's last node stores its right neighbour in its first padding slot, so
-  // its end row reads it there; rows past the end give unused finite values,
-  // the system being diagonally dominant) and restarts the backward sweep at
-  // the chunk's end row. Dirichlet identity rows: the row's first node is
-  // replaced at j = 0; its last one only sets the chunk's end relation, which
-  // is zeroed after the sweep. Both are selects that the branch-free path
-  // makes too, so a Dirichlet end in a full chunk does not send its warp
-  // (and through the barriers its CTA and cluster) down the general path.
+  // Dirichlet identity rows: the row's first node is replaced at j = 0; its
+  // last one (the end row of chunk tl of the last CTA) only sets that chunk's
+  // end relation, which is zeroed after the sweep. Warps of chunks without
+  // nodes skip the sweep; lanes without nodes in a mixed warp compute values
+  // nobody reads.
   const bool dfirst = !per && rank == 0 && tid == 0;
   const bool dlast = !per && lastcta && tid == tl;
-  // (lanes past the row's end may take the branch-free path too: their
-  // values are never read)
-  const bool plainchunk =
-      __all_sync(FULL_MASK, (je == C - 1 && jstar >= C - 1) || jstar < 0);
-  const bool padwarp = __all_sync(FULL_MASK, jstar < 0);
-  const bool endslot = jstar >= 0 && jstar < C - 1;  // chunk with padding after node n-1
+  const bool padwarp = __all_sync(FULL_MASK, !active);
+  const bool tlshort = bk > 0;                // the interface chunk is short
   T ch[C], ah[C], dd[C];
   int par = 0;  // slot buffer of this step
   for (int64_t step = 0; step < rd.nsteps; ++step) {
     const T halo_l = cs.reply.halo_l, halo_r = cs.reply.halo_r;
     T left = tid > 0 ? cs.hlast[tid - 1] : halo_l;
     T right = tid < tl ? cs.hfirst[tid + 1] : halo_r;
-    // ---- assembly fused with the forward sweep (rows as in btcs.cu)
+    // ---- assembly fused with the forward sweep (rows as in btcs.cu), then
+    // the backward sweep: (delta, alpha, gamma) into (dd, ah, ch)
     T e_ch = T(0), e_ah = T(0), e_dh = T(0);
-    auto sweep = [&](auto full_tag) {
-      constexpr bool FULL = decltype(full_tag)::value;
-      if constexpr (!FULL) {
-        if (endslot) us[(jstar + 1) * NT + tid] = right;
-      }
+    if (padwarp) {  // all rows identity
+      dd[0] = T(0); ah[0] = T(0); ch[0] = T(0);
+    } else {
+      // a short chunk's end row reads its right neighbour from its last slot
+      if (shrt) us[(C - 1) * NT + tid] = right;
       T chp = T(0), ahp = T(-1), dhp = T(0);
       T ul = left, a = us[tid];
 #pragma unroll
@@ -413,43 +417,22 @@ __launch_bounds__(NT, (sizeof(T) == 4 && NT <= 512) ? 512 / NT : 1)
         ul = a;
         a = an;
       }
-      if constexpr (FULL) {
-        e_ch = ch[C - 1]; e_ah = ah[C - 1]; e_dh = dd[C - 1];
-        T cd = T(0), ca = T(0), cgm = T(-1);
-        dd[C - 1] = T(0); ah[C - 1] = T(0); ch[C - 1] = T(-1);
+      // the end row: node C - 1, or C - 2 of a short chunk
+      e_ch = shrt ? ch[C - 2] : ch[C - 1];
+      e_ah = shrt ? ah[C - 2] : ah[C - 1];
+      e_dh = shrt ? dd[C - 2] : dd[C - 1];
+      T cd = T(0), ca = T(0), cgm = T(-1);
+      dd[C - 1] = T(0); ah[C - 1] = T(0); ch[C - 1] = T(-1);
 #pragma unroll
-        for (int j = C - 2; j >= 0; --j) {
-          const T cj = ch[j];
-          cd = tfma(-cj, cd, dd[j]);
-          ca = tfma(-cj, ca, ah[j]);
-          cgm = -cj * cgm;
-          dd[j] = cd; ah[j] = ca; ch[j] = cgm;
-        }
-        if (dlast) { e_ch = T(0); e_ah = T(0); e_dh = T(0); }
-      } else {
-        // as above, restarted at the end row je (values past it are unused)
-        e_ch = ch[C - 1]; e_ah = ah[C - 1]; e_dh = dd[C - 1];
-        T cd = T(0), ca = T(0), cgm = T(-1);
-        dd[C - 1] = T(0); ah[C - 1] = T(0); ch[C - 1] = T(-1);
-#pragma unroll
-        for (int j = C - 2; j >= 0; --j) {
-          const T cj = ch[j];
-          const bool at = j == je;
-          if (at) { e_ch = cj; e_ah = ah[j]; e_dh = dd[j]; }
-          cd = at ? T(0) : tfma(-cj, cd, dd[j]);
-          ca = at ? T(0) : tfma(-cj, ca, ah[j]);
-          cgm = at ? T(-1) : -cj * cgm;
-          dd[j] = cd; ah[j] = ca; ch[j] = cgm;
-        }
-        if (dlast) { e_ch = T(0); e_ah = T(0); e_dh = T(0); }
+      for (int j = C - 2; j >= 0; --j) {
+        const T cj = ch[j];
+        cd = tfma(-cj, cd, dd[j]);
+        ca = tfma(-cj, ca, ah[j]);
+        cgm = -cj * cgm;
+        if (j == C - 2 && shrt) { cd = T(0); ca = T(0); cgm = T(-1); }  // a short chunk's end row
+        dd[j] = cd; ah[j] = ca; ch[j] = cgm;
       }
-    };
-    if (padwarp) {  // all rows identity: what the general sweep leaves
-      dd[0] = T(0); ah[0] = T(0); ch[0] = T(0);
-    } else if (plainchunk) {
-      sweep(std::true_type{});
-    } else {
-      sweep(std::false_type{});
+      if (dlast) { e_ch = T(0); e_ah = T(0); e_dh = T(0); }
     }
     sm.rd[sk(tid)] = dd[0];
     sm.ra[sk(tid)] = ah[0];
@@ -485,14 +468,14 @@ __launch_bounds__(NT, (sizeof(T) == 4 && NT <= 512) ? 512 / NT : 1)
         sl.al = tl > 0 ? sm.Z[sk(tl - 1)] : T(0);
         sl.gl = tl > 0 ? cs.Wg[sk(tl - 1)] : T(0);
         sl.y0 = sm.X[sk(0)]; sl.a0 = sm.Z[sk(0)]; sl.g0 = cs.Wg[sk(0)];
-        const int jl = nc - 1 - tl * C;  // end row of the interface chunk
+        const int jl = tlshort ? C - 2 : C - 1;  // end row of the interface chunk
         sl.uf = us[0];
         sl.ul = us[jl * NT + tl];
         sl.lf = T(0);
         sl.ll = T(0);
         if constexpr (Kahan<T>::on) { sl.lf = lo[0]; sl.ll = lo[jl * NT + tl]; }
         sl.ti = tl;
-        sl.jf = tl == 0 ? jl : C - 1;
+        sl.jf = C - 1;  // chunk 0 is never short (ts >= 1)
         // pushed into every CTA's memory (lane k writes CTA k's copy), so
         // after the cluster barrier each CTA reads its own shared memory
         if (lane < CS) store_slot(cluster.map_shared_rank(&cs.slots[par][rank], lane), sl);
@@ -502,7 +485,9 @@ __launch_bounds__(NT, (sizeof(T) == 4 && NT <= 512) ? 512 / NT : 1)
     if (warp == Q - 1) cluster_solve<T, NT, CS>(cs, per, lane, rank, par, cluster);
     __syncthreads();
     par ^= 1;
-    // ---- chunk-end values from the block relations, back-substitution
+    // ---- chunk-end values from the block relations, back-substitution (a
+    // short chunk's end row, restarted in the backward sweep, gives its X
+    // exactly: delta = Xt - 0 L + 0)
     const T Y = cs.reply.Y, P = cs.reply.P;
     if (tid <= tl) {
       auto xend = [&](int t) -> T {
@@ -510,34 +495,27 @@ __launch_bounds__(NT, (sizeof(T) == 4 && NT <= 512) ? 512 / NT : 1)
       };
       const T Xt = xend(tid);
       const T L = tid > 0 ? xend(tid - 1) : P;
-      auto update = [&](auto full_tag) {
-        constexpr bool FULL = decltype(full_tag)::value;
-        const int jend = FULL ? C - 1 : je;
 #pragma unroll
-        for (int j = 0; j < C; ++j) {
-          if (FULL || j <= jend) {
-            const T delta = (j == jend) ? Xt : tfma(-ch[j], Xt, tfma(-ah[j], L, dd[j]));
-            const int o = j * NT + tid;
-            T l0 = T(0);
-            if constexpr (Kahan<T>::on) l0 = lo[o];
-            const T nv = comp_add(us[o], delta, l0);
-            us[o] = nv;
-            if constexpr (Kahan<T>::on) lo[o] = l0;
-            if (j == 0) cs.hfirst[tid] = nv;
-            if (j == jend) cs.hlast[tid] = nv;
-          }
+      for (int j = 0; j < C; ++j) {
+        if (j < C - 1 || !shrt) {
+          const T delta = (j == C - 1) ? Xt : tfma(-ch[j], Xt, tfma(-ah[j], L, dd[j]));
+          const int o = j * NT + tid;
+          T l0 = T(0);
+          if constexpr (Kahan<T>::on) l0 = lo[o];
+          const T nv = comp_add(us[o], delta, l0);
+          us[o] = nv;
+          if constexpr (Kahan<T>::on) lo[o] = l0;
+          if (j == 0) cs.hfirst[tid] = nv;
+          if (j == C - 2 && shrt) cs.hlast[tid] = nv;
+          if (j == C - 1) cs.hlast[tid] = nv;
         }
-      };
-      if (plainchunk) update(std::true_type{});
-      else update(std::false_type{});
+      }
     }
     __syncthreads();
   }
 #pragma unroll
-  for (int j = 0; j < C; ++j) {
-    const int li = tid * C + j;
-    if (li < nc) row[li] = us[j * NT + tid];
-  }
+  for (int j = 0; j < C; ++j)
+    if (j < clen) row[cstart + j] = us[j * NT + tid];
   cluster.sync();  // no CTA leaves while another may still address its memory
 }
 
