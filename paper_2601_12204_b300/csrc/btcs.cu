@@ -26,15 +26,13 @@
 
 namespace burgers {
 
-// FP32 rows of exactly NT*C nodes with C even run the packed-pair kernel
-// (btcs_x2.cuh); ragged rows the scalar one.
+// FP32 rows with C even run the packed-pair kernel (btcs_x2.cuh): rows of
+// exactly NT*C nodes, and ragged rows where C >= 4.
 #define REG_BTCS_X2(NT, C)                                                                      \
   reg.push_back({K_BTCS_RESIDENT, 0, NT, C, 1,                                                  \
                  reinterpret_cast<const void*>(&k_btcs_resident_x2<NT, C, VAR_BTCS>),          \
                  btcs_x2_dsm<NT, C, VAR_BTCS>()});                                              \
-  reg.push_back({K_BTCS_RESIDENT, 0, NT, C, 0,                                                  \
-                 reinterpret_cast<const void*>(&k_btcs_resident<float, NT, C, false, VAR_BTCS>), \
-                 btcs_dsm<float, NT, C, VAR_BTCS>()});
+  reg.push_back(ragged_fp32_entry<NT, C, VAR_BTCS>(K_BTCS_RESIDENT));
 
 #define REG_BTCS(T, DT, NT, C)                                                                  \
   reg.push_back({K_BTCS_RESIDENT, DT, NT, C, 1,                                                 \

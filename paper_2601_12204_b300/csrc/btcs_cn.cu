@@ -11,14 +11,12 @@ namespace burgers {
   reg.push_back({KIND, DT, NT, C, 0,                                                        \
                  reinterpret_cast<const void*>(&k_btcs_resident<T, NT, C, false, VAR>),    \
                  btcs_dsm<T, NT, C, VAR>()});
-// FP32 rows of exactly NT*C nodes with C even: the packed-pair kernel
+// FP32 rows with C even: the packed-pair kernel (exact rows; ragged rows where C >= 4)
 #define REG_VAR_X2(KIND, VAR, NT, C)                                                         \
   reg.push_back({KIND, 0, NT, C, 1,                                                         \
                  reinterpret_cast<const void*>(&k_btcs_resident_x2<NT, C, VAR>),           \
                  btcs_x2_dsm<NT, C, VAR>()});                                              \
-  reg.push_back({KIND, 0, NT, C, 0,                                                         \
-                 reinterpret_cast<const void*>(&k_btcs_resident<float, NT, C, false, VAR>), \
-                 btcs_dsm<float, NT, C, VAR>()});
+  reg.push_back(ragged_fp32_entry<NT, C, VAR>(KIND));
 #define REG_SHAPES(KIND, VAR)                                                                \
   REG_VAR(KIND, VAR, float, 0, 32, 1) REG_VAR_X2(KIND, VAR, 32, 2)                  \
   REG_VAR_X2(KIND, VAR, 32, 4) REG_VAR_X2(KIND, VAR, 32, 8)                  \

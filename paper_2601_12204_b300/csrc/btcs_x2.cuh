@@ -1,6 +1,7 @@
-// btcs_x2.cuh -- the FP32 resident implicit-step kernel for rows of exactly
-// NT*C nodes on packed f32x2 arithmetic (lagged BTCS, Crank-Nicolson and
-// Picard; the algebra of each variant is that of btcs_kernel.cuh).
+// btcs_x2.cuh -- the FP32 resident implicit-step kernel on packed f32x2
+// arithmetic (lagged BTCS, Crank-Nicolson and Picard; the algebra of each
+// variant is that of btcs_kernel.cuh), for rows of exactly NT*C nodes and for
+// ragged rows of its capacity class (chunks of C or C - 1 nodes, below).
 //
 // Each thread's chunk of C nodes is two half-chunks, A = nodes [0, C/2) and
 // B = [C/2, C), eliminated side by side: pair k holds node k of A and node k
@@ -51,11 +52,12 @@ __device__ __forceinline__ void x2_row0(const float* c0, float ran1, float rgn1,
   B0 = bB - c0[0] * c0[3] - cB * pa1;
 }
 
-template <int NT, int C, int BCT, int VAR>
+template <int NT, int C, int BCT, int VAR, bool EXACT>
 __device__ __forceinline__ void btcs_steps_x2(int64_t nsteps, int iters, float r, float s,
                                               BtcsShared<float, NT>& sm, X2Shared<NT>& xs,
                                               float* hfirst, float* hlast, float2* us, float2* lo,
-                                              float2* es, int solver) {
+                                              float2* es, int solver, int tl_, bool shrt,
+                                              bool padwarp) {
   static_assert(C % 2 == 0 && C >= 2, "two half-chunks");
   static_assert(VAR != VAR_NEWTON, "Newton takes its neighbours directly (scalar kernel)");
   constexpr int H = C / 2;
@@ -63,7 +65,10 @@ __device__ __forceinline__ void btcs_steps_x2(int64_t nsteps, int iters, float r
   constexpr bool PER = BCT == BC_PERIODIC;
   const float kap = VAR == VAR_CN ? 2.f : 1.f;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  constexpr int tl = NT - 1;
+  // last chunk holding nodes (ragged rows: chunks past it hold none, and the
+  // short chunks end one pair early in their second half)
+  const int tl = EXACT ? NT - 1 : tl_;
+  const bool dlast = !EXACT && BCT == BC_DIRICHLET && tid == tl;
   const float rm = VAR == VAR_CN ? 0.5f * r : r, smat = VAR == VAR_CN ? 0.5f * s : s;
   const float2 RM2 = make_float2(rm, rm), SM2 = make_float2(smat, smat);
   const float ds1 = 1.f + 2.f * smat;
@@ -84,13 +89,22 @@ __device__ __forceinline__ void btcs_steps_x2(int64_t nsteps, int iters, float r
     // ---- forward sweep of both halves. A's first row stands in for its own
     // left neighbour (deferred, as in the scalar kernel); B's first row reads
     // node C/2 - 1; A's end row reads node C/2; B's end row stands in for its
-    // own right neighbour (deferred).
+    // own right neighbour (deferred). Warps without nodes (ragged rows) skip
+    // it where that costs no registers (up to 16 nodes a thread; with 32 the
+    // branch around the sweep spilled): nothing reads what they publish.
+    float eBc = 0.f, eBa = 0.f, eBd = 0.f, pa = 0.f, pc = 0.f, pd0 = 0.f;
+    if (EXACT || C > 16 || !padwarp) {
     float2 a = W(0);
     float2 DL = sub2(a, make_float2(a.x, W(H - 1).x));  // a - u_l
     float2 chp = make_float2(0.f, 0.f), ahp = make_float2(-1.f, -1.f), ndhp = make_float2(0.f, 0.f);
 #pragma unroll
     for (int k = 0; k < H; ++k) {
-      const float2 an = (k + 1 < H) ? W(k + 1) : make_float2(W(0).y, a.y);
+      float2 an = (k + 1 < H) ? W(k + 1) : make_float2(W(0).y, a.y);
+      // a short chunk's second half ends at pair H - 2 and stands in for its
+      // own right neighbour there (its pair H - 1 is padding)
+      if constexpr (!EXACT) {
+        if (k == H - 2 && shrt) an.y = a.y;
+      }
       const float2 ER = sub2(an, a);  // u_r - a
       const float2 ra = mul2(RM2, a);
       const float2 M = make_float2(fmaxf(ra.x, 0.f), fmaxf(ra.y, 0.f));
@@ -105,7 +119,10 @@ __device__ __forceinline__ void btcs_steps_x2(int64_t nsteps, int iters, float r
       if constexpr (ITER) nrhs = add2(nrhs, es[k * NT + tid]);
       if constexpr (BCT == BC_DIRICHLET) {  // the row's end nodes are identity rows
         if (k == 0 && tid == 0) { nl.x = 0.f; c.x = 0.f; nc.x = 0.f; d.x = 1.f; nrhs.x = 0.f; }
-        if (k == H - 1 && tid == NT - 1) { nl.y = 0.f; c.y = 0.f; nc.y = 0.f; d.y = 1.f; nrhs.y = 0.f; }
+        // (ragged rows: the last node only zeroes its chunk's end relation, below)
+        if (EXACT && k == H - 1 && tid == NT - 1) {
+          nl.y = 0.f; c.y = 0.f; nc.y = 0.f; d.y = 1.f; nrhs.y = 0.f;
+        }
       }
       const float2 den = fma2(nl, chp, d);
       const float2 inv = make_float2(recip(den.x), recip(den.y));
@@ -121,7 +138,11 @@ __device__ __forceinline__ void btcs_steps_x2(int64_t nsteps, int iters, float r
     }
     // end rows of both halves: x_e = dh - ah L - ch x_next
     const float eAc = chp.x, eAa = ahp.x, eAd = -ndhp.x;
-    const float eBc = chp.y, eBa = ahp.y, eBd = -ndhp.y;
+    eBc = chp.y; eBa = ahp.y; eBd = -ndhp.y;
+    if constexpr (!EXACT) {
+      if (shrt) { eBc = -CH[H - 2].y; eBa = AH[H - 2].y; eBd = -ND[H - 2].y; }
+      if (dlast) { eBc = 0.f; eBa = 0.f; eBd = 0.f; }  // Dirichlet: an identity end row
+    }
     // ---- backward sweep: x_j = delta_j - alpha_j L - gamma_j X_e
     {
       float2 ncd = make_float2(0.f, 0.f), ca = make_float2(0.f, 0.f), cg = make_float2(-1.f, -1.f);
@@ -134,6 +155,9 @@ __device__ __forceinline__ void btcs_steps_x2(int64_t nsteps, int iters, float r
         ncd = fma2(ncj, ncd, ND[k]);
         ca = fma2(ncj, ca, AH[k]);
         cg = mul2(ncj, cg);
+        if constexpr (!EXACT) {
+          if (k == H - 2 && shrt) { ncd.y = 0.f; ca.y = 0.f; cg.y = -1.f; }  // its end row
+        }
         ND[k] = ncd;
         AH[k] = ca;
         CH[k] = cg;
@@ -147,7 +171,7 @@ __device__ __forceinline__ void btcs_steps_x2(int64_t nsteps, int iters, float r
     const float cA = -eAc * CH[0].y;
     const float dA0 = tfma(-eAc, -ND[0].y, eAd);
     const float ib = 1.f / bA;
-    const float pa = eAa * ib, pc = cA * ib, pd0 = dA0 * ib;
+    pa = eAa * ib; pc = cA * ib; pd0 = dA0 * ib;
     sm.rd[sk(tid)] = -ND[0].x;
     sm.ra[sk(tid)] = AH[0].x;
     sm.rg[sk(tid)] = CH[0].x;
@@ -157,6 +181,7 @@ __device__ __forceinline__ void btcs_steps_x2(int64_t nsteps, int iters, float r
     if constexpr (PER) {
       if (tid == 0) { xs.c0[0] = eBa; xs.c0[1] = eBc; xs.c0[2] = pa; xs.c0[3] = pc; }
     }
+    }  // sweep
     __syncthreads();
     // u_left - u_0 of this chunk and A's row with it
     const float lt = tid > 0 ? hlast[tid - 1] - hfirst[tid] : (PER ? hlast[tl] - hfirst[0] : 0.f);
@@ -167,7 +192,8 @@ __device__ __forceinline__ void btcs_steps_x2(int64_t nsteps, int iters, float r
     {
       const int t = tid, i = sk(t);
       const int nx = (t == tl) ? 0 : t + 1;
-      const bool has_next = PER || t < tl;
+      // (ragged rows: threads past tl hold no chunk and give identity rows)
+      const bool has_next = (PER || t < tl) && (EXACT || t <= tl);
       float A = -eBa * pa, B = 1.f, Cc = 0.f, D = 0.f, U = 0.f;
       const float Dt0 = eBd;
       if (has_next) {
@@ -196,13 +222,16 @@ __device__ __forceinline__ void btcs_steps_x2(int64_t nsteps, int iters, float r
         if (t == 0) { B = B0 - gam; A = 0.f; U = gam; }
         if (t == tl) { B = B - Cc * fa; U = Cc; Cc = 0.f; }
       }
+      if constexpr (!EXACT) {
+        if (t > tl) { A = 0.f; B = 1.f; Cc = 0.f; D = 0.f; U = 0.f; }
+      }
       sm.A[i] = A; sm.B[i] = B; sm.Cc[i] = Cc; sm.D[i] = D; sm.U[i] = U;
     }
     __syncthreads();
     if (warp == solver) reduced_solve<float, NT, PER, true>(sm, tl, lane, fa);
     __syncthreads();
     // ---- X_A from its row; every node from its half's relation; the update
-    {
+    if (EXACT || tid <= tl) {
       float XBm = 0.f;
       if (tid > 0) XBm = sm.X[sk(tid - 1)];
       else if constexpr (PER) XBm = sm.X[sk(tl)];
@@ -212,7 +241,10 @@ __device__ __forceinline__ void btcs_steps_x2(int64_t nsteps, int iters, float r
       const float2 Xp = make_float2(XA, XB);
 #pragma unroll
       for (int k = 0; k < H; ++k) {
-        const float2 ndelta = fma2(CH[k], Xp, fma2(AH[k], Lp, ND[k]));
+        float2 ndelta = fma2(CH[k], Xp, fma2(AH[k], Lp, ND[k]));
+        if constexpr (!EXACT) {
+          if (k == H - 1 && shrt) ndelta.y = 0.f;  // the padding pair keeps its value
+        }
         const int o = k * NT + tid;
         float2 nv;
         if constexpr (ITER) {
@@ -235,21 +267,33 @@ __device__ __forceinline__ void btcs_steps_x2(int64_t nsteps, int iters, float r
           us[o] = nv;
         }
         if (k == 0) hfirst[tid] = nv.x;
-        if (k == H - 1) hlast[tid] = nv.y;
+        if (k == H - 1 && (EXACT || !shrt)) hlast[tid] = nv.y;
+        if constexpr (!EXACT) {
+          if (k == H - 2 && shrt) hlast[tid] = nv.y;
+        }
       }
     }
   }  // iterations
   }  // steps
 }
 
-// FP32 rows of exactly NT*C nodes. Persistent CTAs take rows from an atomic
-// counter; the row state lives in shared memory as node pairs (k, k + C/2)
-// laid out [k][thread].
-template <int NT, int C, int VAR>
+// FP32 rows of NT*C nodes (EXACT), or ragged rows of n < NT*C nodes whose
+// capacity class has this shape (n > NT*C/2). Persistent CTAs take rows from
+// an atomic counter; the row state lives in shared memory as node pairs
+// (k, k + C/2) laid out [k][thread].
+//
+// Ragged rows: tk = ceil(n / C) threads hold chunks, the last bk = tk C - n of
+// them C - 1 nodes (second half one node short); since n > NT C / 2, tk >
+// NT / 2 >= C > bk, so every such length has this split. A short chunk's end
+// sits at a position known at compile time (pair C/2 - 2 of its second half),
+// so all warps run the same sweep with a few selects there; warps wholly past
+// tk skip the sweep and threads past it give identity reduced rows.
+template <int NT, int C, int VAR, bool EXACT = true>
 __global__ void __launch_bounds__(NT, NT <= 512 ? 512 / NT : 1)
     k_btcs_resident_x2(float* __restrict__ u, const RowDesc* __restrict__ rows, int count,
                        int* __restrict__ counter) {
   constexpr int H = C / 2;
+  static_assert(EXACT || C >= 4, "a short chunk keeps a node in its second half");
   __shared__ BtcsShared<float, NT> sm;
   __shared__ X2Shared<NT> xs;
   __shared__ float hfirst[NT], hlast[NT];
@@ -273,31 +317,61 @@ __global__ void __launch_bounds__(NT, NT <= 512 ? 512 / NT : 1)
     if (item >= count) return;
     const int solver = s_solver;
     const RowDesc rd = rows[item];
-    float* row = u + rd.offset + tid * C;
+    const int n = EXACT ? NT * C : rd.n;
+    const int tk = EXACT ? NT : (n + C - 1) / C;  // chunks holding nodes
+    const int bk = tk * C - n;                     // short chunks (the last ones)
+    const bool active = tid < tk;
+    const bool shrt = !EXACT && active && tid >= tk - bk;
+    const int cstart = tid * C - (shrt ? tid - (tk - bk) : 0);
+    const int clen = active ? (shrt ? C - 1 : C) : 0;
+    const bool padwarp = !EXACT && __all_sync(FULL_MASK, !active);
+    float* row = u + rd.offset + cstart;
 #pragma unroll
     for (int k = 0; k < H; ++k) {
-      const float2 x = make_float2(row[k], row[k + H]);
+      float2 x;
+      if constexpr (EXACT) {
+        x = make_float2(row[k], row[k + H]);
+      } else {
+        x = make_float2(k < clen ? row[k] : 0.f, k + H < clen ? row[k + H] : 0.f);
+      }
       us[k * NT + tid] = x;
       lo[k * NT + tid] = make_float2(0.f, 0.f);
       if (k == 0) hfirst[tid] = x.x;
-      if (k == H - 1) hlast[tid] = x.y;
+      if (k == H - 1 && !shrt) hlast[tid] = x.y;
+      if (!EXACT && k == H - 2 && shrt) hlast[tid] = x.y;
     }
     __syncthreads();
     const float r = rd.rf, s = rd.sf;
     if (rd.bc == BC_PERIODIC)
-      btcs_steps_x2<NT, C, BC_PERIODIC, VAR>(rd.nsteps, rd.iters, r, s, sm, xs, hfirst, hlast, us,
-                                             lo, es, solver);
+      btcs_steps_x2<NT, C, BC_PERIODIC, VAR, EXACT>(rd.nsteps, rd.iters, r, s, sm, xs, hfirst,
+                                                    hlast, us, lo, es, solver, tk - 1, shrt,
+                                                    padwarp);
     else
-      btcs_steps_x2<NT, C, BC_DIRICHLET, VAR>(rd.nsteps, rd.iters, r, s, sm, xs, hfirst, hlast,
-                                              us, lo, es, solver);
+      btcs_steps_x2<NT, C, BC_DIRICHLET, VAR, EXACT>(rd.nsteps, rd.iters, r, s, sm, xs, hfirst,
+                                                     hlast, us, lo, es, solver, tk - 1, shrt,
+                                                     padwarp);
 #pragma unroll
     for (int k = 0; k < H; ++k) {
       const float2 x = us[k * NT + tid];
-      row[k] = x.x;
-      row[k + H] = x.y;
+      if (EXACT || k < clen) row[k] = x.x;
+      if (EXACT || k + H < clen) row[k + H] = x.y;
     }
     __syncthreads();
   }
+}
+
+// Registry entry of the ragged FP32 rows of a shape: the packed kernel when
+// its chunks have at least two node pairs, else the scalar one.
+template <int NT, int C, int VAR>
+inline KernelEntry ragged_fp32_entry(int kind) {
+  if constexpr (C >= 4)
+    return KernelEntry{kind, 0, NT, C, 0,
+                       reinterpret_cast<const void*>(&k_btcs_resident_x2<NT, C, VAR, false>),
+                       btcs_x2_dsm<NT, C, VAR>()};
+  else
+    return KernelEntry{kind, 0, NT, C, 0,
+                       reinterpret_cast<const void*>(&k_btcs_resident<float, NT, C, false, VAR>),
+                       btcs_dsm<float, NT, C, VAR>()};
 }
 
 }  // namespace burgers
