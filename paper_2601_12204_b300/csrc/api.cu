@@ -104,10 +104,15 @@ static const std::vector<Shape>& resident_shapes(int kind, int dtype) {
                                           {128, 32}, {256, 16}, {256, 32}};
   static const std::vector<Shape> im64 = {{32, 1},  {32, 2},   {32, 4},   {32, 8},  {64, 8},
                                           {128, 8}, {256, 8},  {128, 16}, {512, 8}};
+  // Crank-Nicolson and Picard also have the packed kernel at 64 x 32 (Newton
+  // has the scalar kernel only)
+  static const std::vector<Shape> cp32 = {{32, 1},   {32, 2},   {32, 4},   {32, 8},
+                                          {64, 8},   {128, 8},  {128, 16}, {256, 8},
+                                          {64, 32},  {128, 32}, {256, 16}, {256, 32}};
   if (kind == K_EXPLICIT_RESIDENT) return dtype == 0 ? ex32 : ex64;
   if (kind == K_RK4_RESIDENT) return dtype == 0 ? rk32 : rk64;
-  if (kind == K_CN_RESIDENT || kind == K_PICARD_RESIDENT || kind == K_NEWTON_RESIDENT)
-    return dtype == 0 ? im32 : im64;
+  if (kind == K_CN_RESIDENT || kind == K_PICARD_RESIDENT) return dtype == 0 ? cp32 : im64;
+  if (kind == K_NEWTON_RESIDENT) return dtype == 0 ? im32 : im64;
   return dtype == 0 ? bt32 : bt64;
 }
 
@@ -181,6 +186,14 @@ static Shape pick_resident(const burgers_ctx* ctx, int kind, int dtype, int64_t 
   // warps on the general path than 256 x 16 (about 10% faster; exact rows
   // keep 256 x 16)
   if (kind == K_EXPLICIT_RESIDENT && dtype == 0 && cap == 4096 && n < cap) return Shape{128, 32};
+  // ragged FP32 BTCS rows of up to 2048 nodes: the packed kernel at 64 x 32
+  // (longer chains, a 64-row reduced system) measured 6.5e11 against 5.4e11
+  // cell-updates/s at 128 x 16 on 2000-node rows (100 steps at 10x the CFL
+  // step); Crank-Nicolson and Picard take the same shape (one Picard
+  // iteration is then bitwise the BTCS step)
+  if ((kind == K_BTCS_RESIDENT || kind == K_CN_RESIDENT || kind == K_PICARD_RESIDENT) &&
+      dtype == 0 && cap == 2048 && n < cap)
+    return Shape{64, 32};
   return best;
 }
 

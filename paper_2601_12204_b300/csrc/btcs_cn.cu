@@ -21,6 +21,7 @@ namespace burgers {
   REG_VAR(KIND, VAR, float, 0, 32, 1) REG_VAR_X2(KIND, VAR, 32, 2)                  \
   REG_VAR_X2(KIND, VAR, 32, 4) REG_VAR_X2(KIND, VAR, 32, 8)                  \
   REG_VAR_X2(KIND, VAR, 64, 8) REG_VAR_X2(KIND, VAR, 128, 8)                 \
+  REG_VAR_X2(KIND, VAR, 64, 32)                                              \
   REG_VAR_X2(KIND, VAR, 256, 8) REG_VAR_X2(KIND, VAR, 128, 16)               \
   REG_VAR_X2(KIND, VAR, 256, 16) REG_VAR_X2(KIND, VAR, 128, 32)              \
   REG_VAR_X2(KIND, VAR, 256, 32)                                                    \
