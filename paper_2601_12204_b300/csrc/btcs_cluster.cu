@@ -3,9 +3,9 @@
 // the shared memory of CS CTAs for all of its steps, as in the resident kernel.
 //
 // Three levels of the same partitioned elimination:
-//   chunk   each thread eliminates its C (or C - 1) rows (as in btcs.cu) and
-//           leaves one reduced row per chunk in its unknown X_t (the
-//           chunk-end value);
+//   chunk   each thread eliminates its C (or C - 1) rows (as two half-chunks
+//           on packed f32x2 pairs, as btcs_x2.cuh does) and leaves one
+//           reduced row per chunk in its unknown X_t (the chunk-end value);
 //   block   one warp of each CTA expresses the reduced unknowns of its chunks
 //           0..ti-1 through the value P before the block (the previous CTA's
 //           interface) and its own interface Y = X_ti (ti = its last chunk):
@@ -26,8 +26,6 @@
 // exchange. A step costs one cluster barrier and four CTA barriers.
 // Increment form and Kahan-compensated FP32 state as in btcs.cu.
 #include <cooperative_groups.h>
-
-#include <type_traits>
 
 #include "btcs_common.cuh"
 #include "common.cuh"
@@ -307,60 +305,76 @@ __device__ __forceinline__ void cluster_solve(ClusterShared<T, NT>& cs, bool per
   }
 }
 
-// One cluster per row (rows have (CS-1) W < n <= CS W, W = NT*C). The row's
-// nodes are spread evenly over the CS CTAs, and each CTA's nk nodes over
+// One cluster per row (rows have (CS-1) W < n <= CS W, W = NT*C), FP32. The
+// row's nodes are spread evenly over the CS CTAs, and each CTA's nk nodes over
 // tk = ceil(nk / C) chunks of C or C - 1 nodes, the last bk = tk C - nk of
 // them one node short; threads from tk on hold no nodes. Since nk > W/2 - 1,
 // tk > NT/2 > C > bk, so every row length has such a split. A short chunk
-// ends at node C - 2, a position known at compile time: every warp runs the
-// one sweep, and a short chunk costs a few selects at that position (a chunk
-// ending at an arbitrary node would need a select at every node, and the
-// warp holding it would pace the CTA and, through the cluster barrier, every
-// CTA of the row).
-template <typename T, int NT, int C, int CS>
+// ends at a position known at compile time, so every warp runs the one sweep
+// and a short chunk costs a few selects there (a chunk ending at an arbitrary
+// node would need a select at every node, and the warp holding it would pace
+// the CTA and, through the cluster barrier, every CTA of the row: 13-20%
+// slower on ragged rows, measured).
+//
+// Each chunk is eliminated as two half-chunks on packed f32x2 pairs, as
+// btcs_x2.cuh does for rows of one CTA (pair k holds nodes k and k + C/2 of
+// the chunk; a chunk of C - 1 nodes ends its second half at pair C/2 - 2).
+// Neighbour values are read directly (the edge values of the previous step,
+// published before the barrier that ends it). Each thread folds its two
+// halves into the relations of a one-piece chunk in its own end value
+// X_t = X_B: with A's row X_A = pd - pa L - pc X_t,
+//     first node  x_0 = (rd_A - rg_A pd) - (ra_A - rg_A pa) L + rg_A pc X_t,
+//     end row     g x_e = (eB_d - eB_a pd) + eB_a pa L - eB_c x_next,
+//                 g = 1 - eB_a pc,
+// which the block rows, the block and cluster solves and the slots take. A
+// chunk's first node is updated through its first-node relation, the
+// arithmetic the cluster solve uses for a CTA's first node, so the halo
+// values are bitwise the owners'. Increment form and Kahan-compensated FP32
+// state as in btcs.cu.
+template <int NT, int C, int CS>
 __global__ void __cluster_dims__(CS, 1, 1)
-__launch_bounds__(NT, (sizeof(T) == 4 && NT <= 512) ? 512 / NT : 1)
-    k_btcs_cluster(T* __restrict__ u, const RowDesc* __restrict__ rows, int count,
-                   int* __restrict__ counter) {
+__launch_bounds__(NT, NT <= 512 ? 512 / NT : 1)
+    k_btcs_cluster_x2(float* __restrict__ u, const RowDesc* __restrict__ rows, int count,
+                      int* __restrict__ counter) {
   (void)counter;
   constexpr int Q = NT / 32;
+  constexpr int H = C / 2;
   static_assert(CS >= 2 && CS <= 16, "slots hold at most 16 CTAs");
-  static_assert(C >= 3, "a short chunk keeps at least two nodes");
+  static_assert(C % 2 == 0 && C >= 4, "two half-chunks of at least two nodes");
   cg::cluster_group cluster = cg::this_cluster();
   const int rank = int(cluster.block_rank());
   const int item = int(blockIdx.x) / CS;
   extern __shared__ __align__(16) unsigned char dsm[];
-  __shared__ ClusterShared<T, NT> cs;
-  BtcsShared<T, NT>& sm = cs.sm;
-  T* us = reinterpret_cast<T*>(dsm);  // C * NT values
-  T* lo = us + C * NT;                // C * NT values (FP32)
+  __shared__ ClusterShared<float, NT> cs;
+  BtcsShared<float, NT>& sm = cs.sm;
+  float2* us = reinterpret_cast<float2*>(dsm);  // H * NT pairs
+  float2* lo = us + H * NT;                      // H * NT pairs
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const bool valid = item < count;    // grid is count * CS: always true
+  const bool valid = item < count;  // grid is count * CS: always true
   const RowDesc rd = rows[valid ? item : 0];
   const int n = rd.n;
   const bool per = rd.bc == BC_PERIODIC;
   const bool lastcta = rank == CS - 1;
   const int nbase = n / CS, nrem = n % CS;
-  const int nk = nbase + (rank < nrem ? 1 : 0);                    // nodes of this CTA
+  const int nk = nbase + (rank < nrem ? 1 : 0);
   const int64_t kstart = int64_t(rank) * nbase + (rank < nrem ? rank : nrem);
-  const int tk = (nk + C - 1) / C;            // chunks holding nodes
-  const int bk = tk * C - nk;                 // short chunks among them (the last ones)
-  const int tl = tk - 1;                      // its last chunk (the interface)
-  const int ts = tk - bk;                     // first short chunk
+  const int tk = (nk + C - 1) / C;
+  const int bk = tk * C - nk;
+  const int tl = tk - 1;
+  const int ts = tk - bk;
   const bool active = tid < tk;
-  const bool shrt = active && tid >= ts;      // chunk of C - 1 nodes
-  const int cstart = tid * C - (shrt ? tid - ts : 0);  // first node of the chunk in the CTA
+  const bool shrt = active && tid >= ts;
+  const int cstart = tid * C - (shrt ? tid - ts : 0);
   const int clen = active ? (shrt ? C - 1 : C) : 0;
-  T* row = u + rd.offset + kstart;
-  // ---- load, publish the chunk edges and this CTA's ends to its neighbours
+  float* row = u + rd.offset + kstart + cstart;
 #pragma unroll
-  for (int j = 0; j < C; ++j) {
-    const T x = j < clen ? row[cstart + j] : T(0);
-    us[j * NT + tid] = x;
-    if constexpr (Kahan<T>::on) lo[j * NT + tid] = T(0);
-    if (j == 0) cs.hfirst[tid] = x;
-    if (j == C - 2 && shrt) cs.hlast[tid] = x;
-    if (j == C - 1 && !shrt) cs.hlast[tid] = x;
+  for (int k = 0; k < H; ++k) {
+    const float2 x = make_float2(k < clen ? row[k] : 0.f, k + H < clen ? row[k + H] : 0.f);
+    us[k * NT + tid] = x;
+    lo[k * NT + tid] = make_float2(0.f, 0.f);
+    if (k == 0) cs.hfirst[tid] = x.x;
+    if (k == H - 2 && shrt) cs.hlast[tid] = x.y;
+    if (k == H - 1 && !shrt) cs.hlast[tid] = x.y;
   }
   __syncthreads();
   cluster.sync();  // every CTA of the cluster runs before any addresses another's memory
@@ -370,159 +384,165 @@ __launch_bounds__(NT, (sizeof(T) == 4 && NT <= 512) ? 512 / NT : 1)
     cluster.map_shared_rank(&cs.reply, kl)->halo_r = cs.hfirst[0];
   }
   cluster.sync();
-  const T r = T(rd.r), s = T(rd.s), ds1 = T(1) + T(2) * s;
-  // Dirichlet identity rows: the row's first node is replaced at j = 0; its
-  // last one (the end row of chunk tl of the last CTA) only sets that chunk's
-  // end relation, which is zeroed after the sweep. Warps of chunks without
-  // nodes skip the sweep; lanes without nodes in a mixed warp compute values
-  // nobody reads.
+  const float r = rd.rf, s = rd.sf, ds1 = 1.f + 2.f * s;
+  const float2 R2 = make_float2(r, r), S2 = make_float2(s, s), DS1 = make_float2(ds1, ds1);
   const bool dfirst = !per && rank == 0 && tid == 0;
   const bool dlast = !per && lastcta && tid == tl;
-  const bool padwarp = __all_sync(FULL_MASK, !active);
-  const bool tlshort = bk > 0;                // the interface chunk is short
-  T ch[C], ah[C], dd[C];
-  int par = 0;  // slot buffer of this step
+  const bool tlshort = bk > 0;
+  float2 CH[H], AH[H], ND[H];  // forward: -ch, ah, -dh; backward: gamma, alpha, -delta
+  int par = 0;
   for (int64_t step = 0; step < rd.nsteps; ++step) {
-    const T halo_l = cs.reply.halo_l, halo_r = cs.reply.halo_r;
-    T left = tid > 0 ? cs.hlast[tid - 1] : halo_l;
-    T right = tid < tl ? cs.hfirst[tid + 1] : halo_r;
-    // ---- assembly fused with the forward sweep (rows as in btcs.cu), then
-    // the backward sweep: (delta, alpha, gamma) into (dd, ah, ch)
-    T e_ch = T(0), e_ah = T(0), e_dh = T(0);
-    if (padwarp) {  // all rows identity
-      dd[0] = T(0); ah[0] = T(0); ch[0] = T(0);
-    } else {
-      // a short chunk's end row reads its right neighbour from its last slot
-      if (shrt) us[(C - 1) * NT + tid] = right;
-      T chp = T(0), ahp = T(-1), dhp = T(0);
-      T ul = left, a = us[tid];
+    const float halo_l = cs.reply.halo_l, halo_r = cs.reply.halo_r;
+    const float left = tid > 0 ? cs.hlast[tid - 1] : halo_l;
+    const float right = tid < tl ? cs.hfirst[tid + 1] : halo_r;
+    // ---- forward sweep of both halves (A's first row reads the left
+    // neighbour, B's first row node C/2 - 1, A's end row node C/2, B's end
+    // row the right neighbour), then the backward sweep
+    float2 a = us[tid];
+    float2 DL = sub2(a, make_float2(left, us[(H - 1) * NT + tid].x));  // a - u_l
+    float2 chp = make_float2(0.f, 0.f), ahp = make_float2(-1.f, -1.f), ndhp = make_float2(0.f, 0.f);
 #pragma unroll
-      for (int j = 0; j < C; ++j) {
-        const T an = (j + 1 < C) ? us[(j + 1) * NT + tid] : right;
-        const T ur = an;
-        const T ra = r * a;
-        T l = -s - tmax(ra, T(0));
-        T c = tmin(ra, T(0)) - s;
-        T d = ds1 + tabs(ra);
-        T rhs = tfma(l, a - ul, -c * (ur - a));
-        if (j == 0 && dfirst) { l = T(0); c = T(0); d = T(1); rhs = T(0); }
-        const T inv = recip(tfma(-l, chp, d));
-        const T li = l * inv;
-        chp = c * inv;
-        ahp = -li * ahp;
-        dhp = tfma(-li, dhp, rhs * inv);
-        ch[j] = chp;
-        ah[j] = ahp;
-        dd[j] = dhp;
-        ul = a;
-        a = an;
-      }
-      // the end row: node C - 1, or C - 2 of a short chunk
-      e_ch = shrt ? ch[C - 2] : ch[C - 1];
-      e_ah = shrt ? ah[C - 2] : ah[C - 1];
-      e_dh = shrt ? dd[C - 2] : dd[C - 1];
-      T cd = T(0), ca = T(0), cgm = T(-1);
-      dd[C - 1] = T(0); ah[C - 1] = T(0); ch[C - 1] = T(-1);
-#pragma unroll
-      for (int j = C - 2; j >= 0; --j) {
-        const T cj = ch[j];
-        cd = tfma(-cj, cd, dd[j]);
-        ca = tfma(-cj, ca, ah[j]);
-        cgm = -cj * cgm;
-        if (j == C - 2 && shrt) { cd = T(0); ca = T(0); cgm = T(-1); }  // a short chunk's end row
-        dd[j] = cd; ah[j] = ca; ch[j] = cgm;
-      }
-      if (dlast) { e_ch = T(0); e_ah = T(0); e_dh = T(0); }
+    for (int k = 0; k < H; ++k) {
+      float2 an = (k + 1 < H) ? us[(k + 1) * NT + tid] : make_float2(us[tid].y, right);
+      if (k == H - 2 && shrt) an.y = right;  // a short chunk's end row
+      const float2 ER = sub2(an, a);         // u_r - a
+      const float2 ra = mul2(R2, a);
+      const float2 M = make_float2(fmaxf(ra.x, 0.f), fmaxf(ra.y, 0.f));
+      const float2 m = make_float2(fminf(ra.x, 0.f), fminf(ra.y, 0.f));
+      float2 nl = add2(S2, M);  // -l
+      float2 c = sub2(m, S2);   // c
+      float2 nc = sub2(S2, m);  // -c
+      float2 d = add2(DS1, sub2(M, m));
+      float2 nrhs = fma2(nl, DL, mul2(c, ER));  // -rhs of the increment form
+      if (k == 0 && dfirst) { nl.x = 0.f; c.x = 0.f; nc.x = 0.f; d.x = 1.f; nrhs.x = 0.f; }
+      const float2 den = fma2(nl, chp, d);
+      const float2 inv = make_float2(recip(den.x), recip(den.y));
+      const float2 nli = mul2(nl, inv);
+      chp = mul2(c, inv);
+      CH[k] = mul2(nc, inv);
+      ahp = mul2(nli, ahp);
+      ndhp = fma2(nli, ndhp, mul2(nrhs, inv));
+      AH[k] = ahp;
+      ND[k] = ndhp;
+      DL = ER;
+      a = an;
     }
-    sm.rd[sk(tid)] = dd[0];
-    sm.ra[sk(tid)] = ah[0];
-    sm.rg[sk(tid)] = ch[0];
+    const float eAc = chp.x, eAa = ahp.x, eAd = -ndhp.x;
+    float eBc = chp.y, eBa = ahp.y, eBd = -ndhp.y;
+    if (shrt) { eBc = -CH[H - 2].y; eBa = AH[H - 2].y; eBd = -ND[H - 2].y; }
+    if (dlast) { eBc = 0.f; eBa = 0.f; eBd = 0.f; }  // Dirichlet: an identity end row
+    {
+      float2 ncd = make_float2(0.f, 0.f), ca = make_float2(0.f, 0.f), cg = make_float2(-1.f, -1.f);
+      ND[H - 1] = ncd;
+      AH[H - 1] = ca;
+      CH[H - 1] = cg;
+#pragma unroll
+      for (int k = H - 2; k >= 0; --k) {
+        const float2 ncj = CH[k];
+        ncd = fma2(ncj, ncd, ND[k]);
+        ca = fma2(ncj, ca, AH[k]);
+        cg = mul2(ncj, cg);
+        if (k == H - 2 && shrt) { ncd.y = 0.f; ca.y = 0.f; cg.y = -1.f; }
+        ND[k] = ncd;
+        AH[k] = ca;
+        CH[k] = cg;
+      }
+    }
+    // A's row divided by bA, then the one-piece relations of the chunk
+    const float ib = 1.f / (1.f - eAc * AH[0].y);
+    const float pa = eAa * ib, pc = (-eAc * CH[0].y) * ib;
+    const float pd = tfma(-eAc, -ND[0].y, eAd) * ib;
+    const float rgA = CH[0].x, raA = AH[0].x, rdA = -ND[0].x;
+    const float frd = tfma(-rgA, pd, rdA), fra = tfma(-rgA, pa, raA), frg = -rgA * pc;
+    const float ig = 1.f / tfma(-eBa, pc, 1.f);
+    const float e_dh = tfma(-eBa, pd, eBd) * ig, e_ah = (-eBa * pa) * ig, e_ch = eBc * ig;
+    sm.rd[sk(tid)] = frd;
+    sm.ra[sk(tid)] = fra;
+    sm.rg[sk(tid)] = frg;
     if (tid == tl) { cs.iface[0] = e_ah; cs.iface[1] = e_ch; cs.iface[2] = e_dh; }
     __syncthreads();
-    // ---- the block row of this thread's chunk t (chunks 0..tl-1; the
-    // interface row tl is the cluster's): its end row with the first-row
-    // relation of chunk t + 1 substituted, every thread its own
-    {
+    {  // the block row of chunk t < tl, as in the scalar kernel
       const int t = tid, i = sk(t);
-      T A = T(0), B = T(1), Cc = T(0), D = T(0), Uv = T(0), Vv = T(0);
+      float A = 0.f, B = 1.f, Cc = 0.f, D = 0.f, Uv = 0.f, Vv = 0.f;
       if (t < tl) {
-        const T ech = e_ch;
         A = e_ah;
-        B = T(1) - ech * sm.ra[sk(t + 1)];
-        Cc = -ech * sm.rg[sk(t + 1)];
-        D = tfma(-ech, sm.rd[sk(t + 1)], e_dh);
-        if (t == 0) { Uv = A; A = T(0); }
-        if (t == tl - 1) { Vv = Cc; Cc = T(0); }
+        B = 1.f - e_ch * sm.ra[sk(t + 1)];
+        Cc = -e_ch * sm.rg[sk(t + 1)];
+        D = tfma(-e_ch, sm.rd[sk(t + 1)], e_dh);
+        if (t == 0) { Uv = A; A = 0.f; }
+        if (t == tl - 1) { Vv = Cc; Cc = 0.f; }
       }
       sm.A[i] = A; sm.B[i] = B; sm.Cc[i] = Cc; sm.D[i] = D; sm.U[i] = Uv; cs.V[i] = Vv;
     }
     __syncthreads();
-    if (warp == Q - 1) {  // the last warp (warp 0 also carries the CTA's first node)
-      block_solve3<T, NT>(cs, lane);
+    if (warp == Q - 1) {
+      block_solve3<float, NT>(cs, lane);
       __syncwarp();
       {
-        ClusterSlot<T> sl;
+        ClusterSlot<float> sl;
         sl.eah = cs.iface[0]; sl.ech = cs.iface[1]; sl.edh = cs.iface[2];
         sl.rd0 = sm.rd[sk(0)]; sl.ra0 = sm.ra[sk(0)]; sl.rg0 = sm.rg[sk(0)];
-        sl.yl = tl > 0 ? sm.X[sk(tl - 1)] : T(0);
-        sl.al = tl > 0 ? sm.Z[sk(tl - 1)] : T(0);
-        sl.gl = tl > 0 ? cs.Wg[sk(tl - 1)] : T(0);
+        sl.yl = sm.X[sk(tl - 1)];
+        sl.al = sm.Z[sk(tl - 1)];
+        sl.gl = cs.Wg[sk(tl - 1)];
         sl.y0 = sm.X[sk(0)]; sl.a0 = sm.Z[sk(0)]; sl.g0 = cs.Wg[sk(0)];
-        const int jl = tlshort ? C - 2 : C - 1;  // end row of the interface chunk
-        sl.uf = us[0];
-        sl.ul = us[jl * NT + tl];
-        sl.lf = T(0);
-        sl.ll = T(0);
-        if constexpr (Kahan<T>::on) { sl.lf = lo[0]; sl.ll = lo[jl * NT + tl]; }
+        const int jl = tlshort ? H - 2 : H - 1;  // end pair of the interface chunk
+        sl.uf = us[0].x;
+        sl.lf = lo[0].x;
+        sl.ul = us[jl * NT + tl].y;
+        sl.ll = lo[jl * NT + tl].y;
         sl.ti = tl;
-        sl.jf = C - 1;  // chunk 0 is never short (ts >= 1)
-        // pushed into every CTA's memory (lane k writes CTA k's copy), so
-        // after the cluster barrier each CTA reads its own shared memory
+        sl.jf = C - 1;
         if (lane < CS) store_slot(cluster.map_shared_rank(&cs.slots[par][rank], lane), sl);
       }
     }
     cluster.sync();
-    if (warp == Q - 1) cluster_solve<T, NT, CS>(cs, per, lane, rank, par, cluster);
+    if (warp == Q - 1) cluster_solve<float, NT, CS>(cs, per, lane, rank, par, cluster);
     __syncthreads();
     par ^= 1;
-    // ---- chunk-end values from the block relations, back-substitution (a
-    // short chunk's end row, restarted in the backward sweep, gives its X
-    // exactly: delta = Xt - 0 L + 0)
-    const T Y = cs.reply.Y, P = cs.reply.P;
+    // ---- chunk-end values, X_A, back-substitution of both halves
+    const float Y = cs.reply.Y, P = cs.reply.P;
     if (tid <= tl) {
-      auto xend = [&](int t) -> T {
+      auto xend = [&](int t) -> float {
         return t < tl ? tfma(-cs.Wg[sk(t)], Y, tfma(-sm.Z[sk(t)], P, sm.X[sk(t)])) : Y;
       };
-      const T Xt = xend(tid);
-      const T L = tid > 0 ? xend(tid - 1) : P;
+      const float Xt = xend(tid);
+      const float L = tid > 0 ? xend(tid - 1) : P;
+      const float XA = tfma(-pc, Xt, tfma(-pa, L, pd));
+      const float d0 = tfma(-frg, Xt, tfma(-fra, L, frd));  // the first node
+      const float2 Lp = make_float2(L, XA), Xp = make_float2(XA, Xt);
 #pragma unroll
-      for (int j = 0; j < C; ++j) {
-        if (j < C - 1 || !shrt) {
-          const T delta = (j == C - 1) ? Xt : tfma(-ch[j], Xt, tfma(-ah[j], L, dd[j]));
-          const int o = j * NT + tid;
-          T l0 = T(0);
-          if constexpr (Kahan<T>::on) l0 = lo[o];
-          const T nv = comp_add(us[o], delta, l0);
-          us[o] = nv;
-          if constexpr (Kahan<T>::on) lo[o] = l0;
-          if (j == 0) cs.hfirst[tid] = nv;
-          if (j == C - 2 && shrt) cs.hlast[tid] = nv;
-          if (j == C - 1) cs.hlast[tid] = nv;
-        }
+      for (int k = 0; k < H; ++k) {
+        float2 ndelta = fma2(CH[k], Xp, fma2(AH[k], Lp, ND[k]));
+        if (k == 0) ndelta.x = -d0;
+        if (k == H - 1 && shrt) ndelta.y = 0.f;  // the padding pair keeps its value
+        const int o = k * NT + tid;
+        const float2 uo = us[o], l0 = lo[o];
+        const float2 ny = add2(ndelta, l0);
+        const float2 nv = sub2(uo, ny);
+        lo[o] = add2(sub2(nv, uo), ny);
+        us[o] = nv;
+        if (k == 0) cs.hfirst[tid] = nv.x;
+        if (k == H - 2 && shrt) cs.hlast[tid] = nv.y;
+        if (k == H - 1 && !shrt) cs.hlast[tid] = nv.y;
       }
     }
     __syncthreads();
   }
 #pragma unroll
-  for (int j = 0; j < C; ++j)
-    if (j < clen) row[cstart + j] = us[j * NT + tid];
+  for (int k = 0; k < H; ++k) {
+    const float2 x = us[k * NT + tid];
+    if (k < clen) row[k] = x.x;
+    if (k + H < clen) row[k + H] = x.y;
+  }
   cluster.sync();  // no CTA leaves while another may still address its memory
 }
 
+// FP32 rows run the packed-pair form of the kernel (k_btcs_cluster_x2)
 #define REG_CLUSTER(T, DT, NT, C, CS)                                                       \
   reg.push_back({K_BTCS_CLUSTER, DT, NT, C, CS,                                             \
-                 reinterpret_cast<const void*>(&k_btcs_cluster<T, NT, C, CS>),             \
-                 sizeof(T) * size_t(NT) * C * (Kahan<T>::on ? 2 : 1)});
+                 reinterpret_cast<const void*>(&k_btcs_cluster_x2<NT, C, CS>),             \
+                 sizeof(T) * size_t(NT) * C * 2});
 #define REG_CLUSTERS(T, DT, NT, C)                                                          \
   REG_CLUSTER(T, DT, NT, C, 2) REG_CLUSTER(T, DT, NT, C, 3) REG_CLUSTER(T, DT, NT, C, 4)    \
   REG_CLUSTER(T, DT, NT, C, 5) REG_CLUSTER(T, DT, NT, C, 6) REG_CLUSTER(T, DT, NT, C, 7)    \
