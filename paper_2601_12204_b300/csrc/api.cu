@@ -394,6 +394,17 @@ static burgers_status build_plan(burgers_ctx* ctx, int scheme, const burgers_bat
     Shape sh = pick_resident(ctx, rkind, dtype, in.n);
     if (sh.nt == 0) return set_error(BURGERS_EINVAL, "no resident kernel shape fits the row");
     int exact = int64_t(sh.nt) * sh.c == in.n ? 1 : 0;
+    // ragged FP32 rows of the packed kernels are cut into t = ceil(n / C)
+    // chunks of C or C - 1 nodes, which needs t C - n <= t (true for every
+    // row of its capacity class; a tuning table could name another shape)
+    if (!exact && dtype == 0 && sh.c >= 4 && sh.c % 2 == 0 &&
+        (rkind == K_EXPLICIT_RESIDENT || rkind == K_BTCS_RESIDENT || rkind == K_CN_RESIDENT ||
+         rkind == K_PICARD_RESIDENT)) {
+      const int64_t t = (int64_t(in.n) + sh.c - 1) / sh.c;
+      if (t * sh.c - in.n > t || t > sh.nt)
+        return set_error(BURGERS_EINVAL, "row length has no split into chunks of C or C - 1 "
+                                         "nodes for its launch shape");
+    }
     Grp* g = nullptr;
     for (Grp& x : groups)
       if (x.sh.nt == sh.nt && x.sh.c == sh.c && x.exact == exact) g = &x;

@@ -220,6 +220,91 @@ __device__ __forceinline__ void explicit_steps_split_x2(float (&v)[C], float (&l
   }
 }
 
+// Ragged FP32 rows on packed pairs, chunks of C or C - 1 nodes (as the BTCS
+// kernels cut them): tl = ceil(n / C) - 1 is the last thread holding nodes,
+// and a short chunk's second half ends at pair C/2 - 2, its pair C/2 - 1
+// padding. Every end and padding position is known at compile time, so all
+// warps run one loop with a few selects there; the periodic wrap pairs the
+// last node of thread tl with thread 0's first through the wrap slots.
+// Threads past tl update values that no node reads (their neighbour chain
+// starts at thread tl's last node, whose right neighbour is replaced) and
+// are never written back.
+template <int NT, int C, int BCT>
+__device__ __forceinline__ void explicit_steps_split_x2_cc(float (&v)[C], float (&lo)[C],
+                                                           int64_t nsteps, float r, float s,
+                                                           int tl, bool shrt, float* sh_last,
+                                                           float* sh_first, float* sh_wrap) {
+  static_assert(C % 2 == 0 && C >= 4, "pairs of nodes, a short half of at least one");
+  // warps wholly past thread tl skip the update (their values stay zero)
+  const bool padwarp = __all_sync(FULL_MASK, int(threadIdx.x) > tl) != 0;
+  constexpr int H = C / 2;
+  constexpr bool PER = BCT == BC_PERIODIC;
+  const int tid = threadIdx.x;
+  const bool dfirst = !PER && tid == 0;
+  const bool dlast = !PER && tid == tl;
+  float2 V[H], D[H];
+#pragma unroll
+  for (int k = 0; k < H; ++k) {
+    V[k] = make_float2(v[k], v[k + H]);
+    D[k] = make_float2(-lo[k], -lo[k + H]);
+  }
+  const float2 NR = make_float2(-r, -r), S2 = make_float2(s, s), NS = make_float2(-s, -s);
+  for (int64_t k0 = 0; k0 < nsteps; k0 += SPLIT_FOLD) {
+   const int kb = int(nsteps - k0 < SPLIT_FOLD ? nsteps - k0 : int64_t(SPLIT_FOLD));
+   for (int kk = 0; kk < kb; ++kk) {
+    const int p = kk & 1;
+    const float2 U0 = add2(V[0], D[0]);
+    const float2 UL = add2(V[H - 1], D[H - 1]);
+    const float2 UE = add2(V[H - 2], D[H - 2]);
+    const float last = shrt ? UE.y : UL.y;  // the chunk's last node
+    float left, right, wrapL = 0.f, wrapR = 0.f;
+    halo_exchange<float, NT, PER>(U0.x, last, last, tid == tl, p, sh_last, sh_first, sh_wrap,
+                                  left, right, wrapL, wrapR);
+    if constexpr (PER) {
+      if (tid == 0) left = wrapL;
+      if (tid == tl) right = wrapR;
+    }
+    if (padwarp) continue;
+    float2 Uk = U0;
+    float2 DL = sub2(U0, make_float2(left, UL.x));  // u - u_l of pair 0
+#pragma unroll
+    for (int k = 0; k < H; ++k) {
+      float2 UR = (k + 1 < H) ? add2(V[k + 1], D[k + 1]) : make_float2(U0.y, right);
+      const float2 Un = UR;
+      if (k == H - 2 && shrt) UR.y = right;  // a short chunk's end node
+      const float2 E = sub2(UR, Uk);         // u_r - u
+      const float2 m = make_float2(fminf(Uk.x, 0.f), fminf(Uk.y, 0.f));
+      const float2 M = make_float2(fmaxf(Uk.x, 0.f), fmaxf(Uk.y, 0.f));
+      const float2 P = fma2(NR, m, S2);   // p
+      const float2 NQ = fma2(NR, M, NS);  // -q
+      const float2 dn = fma2(P, E, fma2(NQ, DL, D[k]));
+      // held: a Dirichlet row's first and last nodes, a short chunk's padding
+      bool keepx = false, keepy = false;
+      if (k == 0) keepx = dfirst;
+      if (k == H - 2) keepy = shrt && dlast;
+      if (k == H - 1) keepy = shrt || dlast;
+      if (!keepx) D[k].x = dn.x;
+      if (!keepy) D[k].y = dn.y;
+      DL = E;
+      Uk = Un;
+    }
+   }
+#pragma unroll
+    for (int k = 0; k < H; ++k) {
+      const float2 t = add2(V[k], D[k]);
+      D[k] = sub2(D[k], sub2(t, V[k]));
+      V[k] = t;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < H; ++k) {
+    v[k] = V[k].x;
+    v[k + H] = V[k].y;
+    lo[k] = -D[k].x;
+    lo[k + H] = -D[k].y;
+  }
+}
+
 template <int NT, int C, int MODE, int BCT>
 __device__ __forceinline__ void explicit_steps_split(float (&v)[C], float (&lo)[C], int64_t nsteps,
                                                      float r, float h, float s, int n,
@@ -606,23 +691,52 @@ __global__ void __launch_bounds__(NT) k_explicit_resident(T* __restrict__ u,
     const RowDesc rd = rows[item];
     T* row = u + rd.offset;
     const int base = threadIdx.x * C;
+    // ragged FP32 forward-Euler rows on packed pairs: chunks of C or C - 1
+    // nodes (explicit_steps_split_x2_cc); other ragged rows: chunks of C with
+    // the end found per node in the warp holding it
+    constexpr bool CC = !EXACT && sizeof(T) == 4 && INTEG == INTEG_EULER && C % 2 == 0 && C >= 4;
+    int cstart = base, clen = C, tl = NT - 1;
+    bool shrt = false;
+    if constexpr (CC) {
+      const int tk = (rd.n + C - 1) / C, bk = tk * C - rd.n, ts = tk - bk;
+      const bool active = int(threadIdx.x) < tk;
+      shrt = active && int(threadIdx.x) >= ts;
+      cstart = base - (shrt ? int(threadIdx.x) - ts : 0);
+      clen = active ? (shrt ? C - 1 : C) : 0;
+      tl = tk - 1;
+    }
     T v[C], lo[C];
 #pragma unroll
     for (int j = 0; j < C; ++j) {
-      v[j] = (EXACT || base + j < rd.n) ? row[base + j] : T(0);
+      if constexpr (CC) v[j] = j < clen ? row[cstart + j] : T(0);
+      else v[j] = (EXACT || base + j < rd.n) ? row[base + j] : T(0);
       lo[j] = T(0);
     }
     const T r = T(rd.r), h = T(0.5 * rd.r), s = T(rd.s);
     constexpr int M = EXACT ? MODE_EXACT : MODE_RAGGED;
-    if (rd.bc == BC_PERIODIC)
+    if constexpr (CC) {
+      (void)h;
+      if (rd.bc == BC_PERIODIC)
+        explicit_steps_split_x2_cc<NT, C, BC_PERIODIC>(v, lo, rd.nsteps, r, s, tl, shrt, sh_last,
+                                                       sh_first, sh_wrap);
+      else
+        explicit_steps_split_x2_cc<NT, C, BC_DIRICHLET>(v, lo, rd.nsteps, r, s, tl, shrt, sh_last,
+                                                        sh_first, sh_wrap);
+    } else if (rd.bc == BC_PERIODIC) {
       explicit_steps<T, NT, C, M, BC_PERIODIC, INTEG>(v, lo, rd.nsteps, r, h, s, rd.n, base,
                                                       sh_last, sh_first, sh_wrap);
-    else
+    } else {
       explicit_steps<T, NT, C, M, BC_DIRICHLET, INTEG>(v, lo, rd.nsteps, r, h, s, rd.n, base,
                                                        sh_last, sh_first, sh_wrap);
+    }
 #pragma unroll
-    for (int j = 0; j < C; ++j)
-      if (EXACT || base + j < rd.n) row[base + j] = v[j];
+    for (int j = 0; j < C; ++j) {
+      if constexpr (CC) {
+        if (j < clen) row[cstart + j] = v[j];
+      } else if (EXACT || base + j < rd.n) {
+        row[base + j] = v[j];
+      }
+    }
     __syncthreads();
   }
 }
