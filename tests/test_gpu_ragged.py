@@ -1,14 +1,14 @@
 """GPU parity of ragged rows on every warp path of the resident kernels.
 
-In a row shorter than its CTA's capacity NT x C, the warp holding node n-1
-runs the general loop, the warps before it the exact-row loop and the warps
-after it (padding) skip the update; the BTCS general sweep reads the end
-row's neighbour from the chunk's first padding slot and restarts its
-backward sweep at the end row. The row lengths below put node n-1 at the
-first and last node of a chunk, in the first and last lane of a warp, with
-and without padding warps behind it, for shapes forced through the tuning
-table (FP32 shapes of up to 16 nodes a thread split the paths by warp; the
-32-node ones and FP64 run the general BTCS sweep in every warp).
+In a row shorter than its CTA's capacity NT x C, the FP64 rows, RK4 and the
+BTCS shapes of fewer than 4 nodes a thread run the warp-uniform split: the
+warp holding node n-1 runs the general loop, the warps before it the
+exact-row loop and the warps after it (padding) skip the update. FP32 BTCS,
+Crank-Nicolson and forward-Euler rows on packed pairs are cut into chunks of
+C or C - 1 nodes instead (test_gpu_chunk_split.py puts that split at its
+extremes). The row lengths below put node n-1 at the first and last node of
+a chunk, in the first and last lane of a warp, with and without padding
+warps behind it, for shapes forced through the tuning table.
 """
 import numpy as np
 import pytest
