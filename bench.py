@@ -680,6 +680,57 @@ def step_ic_bench(ctx, dev, rows: int = 4096, n: int = 4096):
     return out
 
 
+def ragged_bench(ctx, dev):
+    """Ragged batches (row lengths log-uniform, periodic and Dirichlet mixed,
+    random-Fourier u0, nu log-uniform in [1e-3, 1e-1]): 4096 resident rows of
+    1025-8192 nodes (500 explicit steps at the CFL-0.4 step, 100 BTCS steps at
+    10x it) and 512 cluster rows of 8193-65536 nodes (100 BTCS steps). FP32
+    throughput and FP32 against the FP64 GPU path on every row."""
+    import torch
+
+    from paper_2601_12204_b300 import _lib as L
+    from paper_2601_12204_b300 import workloads as W
+    from paper_2601_12204_b300.api import Batch
+    F32, F64 = L.BURGERS_F32, L.BURGERS_F64
+    stream = torch.cuda.current_stream(dev)
+    out = {"note": "cell-updates/s; rows of every length of the range, so nearly all ragged"}
+    sets = (("resident", 4096, 1025, 8192, (("explicit", L.BURGERS_EXPLICIT, 500, 1.0),
+                                              ("btcs", L.BURGERS_BTCS, 100, BTCS_DT_FACTOR))),
+            ("cluster", 512, 8193, 65536, (("btcs", L.BURGERS_BTCS, 100, BTCS_DT_FACTOR),)))
+    for name, rows, nmin, nmax, runs in sets:
+        ens = W.mixed_ensemble(rows, nmin, nmax, seed=W.DEFAULT_SEED + 7)
+        u32 = torch.tensor(ens.u0, dtype=torch.float32, device=dev)
+        u64 = torch.tensor(ens.u0, dtype=torch.float64, device=dev)
+        dt0 = ctx.cfl_dt(Batch.from_ensemble(ens, 1.0, 0, F64), u64, CFL)
+        cells = float(np.sum(ens.ns))
+        res = {"rows": rows, "n": [nmin, nmax], "nodes": int(cells)}
+        for sname, scheme, steps, fac in runs:
+            b32 = Batch.from_ensemble(ens, dt0 * fac, steps, F32)
+            b64 = b32.with_fields(dtype=F64)
+            w = u32.clone()
+            ctx.advance(scheme, b32, w)  # warm
+            ts = []
+            for _ in range(3):
+                w.copy_(u32)
+                a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                ctx.advance(scheme, b32, w)
+                z.record(stream)
+                torch.cuda.synchronize()
+                ts.append(a.elapsed_time(z) / 1000.0)
+            w64 = u64.clone()
+            ctx.advance(scheme, b64, w64)
+            torch.cuda.synchronize()
+            rel, _ = ctx.rel_l2(b32, w, w64)
+            res[sname] = {"steps": steps, "cups": cells * steps / min(ts),
+                          "l2_fp32_vs_fp64": {"max": float(np.max(rel)),
+                                              "median": float(np.median(rel))}}
+            del w, w64
+        out[name] = res
+        del u32, u64
+    return out
+
+
 def extras(args, ctx, ens, u0, batches, probe, dev, world, rank):
     import torch
 
@@ -807,6 +858,7 @@ def extras(args, ctx, ens, u0, batches, probe, dev, world, rank):
     out["differentiation"] = differentiation_bench(ctx, dev)
     out["step_ic"] = step_ic_bench(ctx, dev)
     out["short_rows_btcs"] = short_rows_bench(dev)
+    out["ragged"] = ragged_bench(ctx, dev)
 
     # ---- plain one-row-per-launch path on a subset, same kernels
     P = 64
