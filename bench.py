@@ -912,12 +912,13 @@ def extras(args, ctx, ens, u0, batches, probe, dev, world, rank):
 
 def long_variants_bench(ctx, dev, rows: int = 512, n: int = 32768, steps: int = 40):
     """Implicit variants on rows longer than the resident capacity: `rows`
-    periodic random-Fourier rows of n nodes through the multi-level solver,
-    Crank-Nicolson and 3 Picard iterations at 10x the CFL dt, 3 Newton
-    iterations at the CFL dt on viscosity-raised rows (cell Peclet <= 1.5);
-    lagged BTCS on the same rows through the same solver (cluster off) and
-    through the default routing for comparison. FP32 and FP64 throughput, FP32
-    against FP64 on every row."""
+    periodic random-Fourier rows of n nodes. Crank-Nicolson at 10x the CFL dt
+    by the default routing (FP32: the cluster-resident kernel) and through the
+    multi-level solver (cluster off); 3 Picard iterations at 10x the CFL dt and
+    3 Newton iterations at the CFL dt on viscosity-raised rows (cell Peclet <=
+    1.5) through the multi-level solver; lagged BTCS through the multi-level
+    solver and by the default routing for comparison. FP32 and FP64
+    throughput, FP32 against FP64 on every row."""
     import torch
 
     from paper_2601_12204_b300 import _lib as L
@@ -952,6 +953,7 @@ def long_variants_bench(ctx, dev, rows: int = 512, n: int = 32768, steps: int = 
         return w, min(ts)
 
     cases = (("cn", L.BURGERS_CN, 1, ens, BTCS_DT_FACTOR, 1),
+             ("cn_multilevel", L.BURGERS_CN, 1, ens, BTCS_DT_FACTOR, 0),
              ("picard3", L.BURGERS_PICARD, 3, ens, BTCS_DT_FACTOR, 1),
              ("newton3", L.BURGERS_NEWTON, 3, ens_n, 1.0, 1),
              ("btcs_multilevel", L.BURGERS_BTCS, 1, ens, BTCS_DT_FACTOR, 0),

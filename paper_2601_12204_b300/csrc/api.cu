@@ -579,19 +579,21 @@ static burgers_status build_plan(burgers_ctx* ctx, int scheme, const burgers_bat
       // byte per node (span / 4 elements each)
       p->scratch_elems = dtype == 0 ? span + span / 2 : span;
     } else {
-      // rows that fit a cluster stay resident in its shared memory
-      // (k_btcs_cluster): 128-thread CTAs of 4096 nodes in clusters of up to
-      // 16 where the device schedules them (8 in portable mode), else
-      // 256-thread CTAs of 8192 nodes in clusters of up to 8; longer rows go
-      // through the multi-level solver
+      // lagged BTCS and Crank-Nicolson rows that fit a cluster stay resident
+      // in its shared memory (k_btcs_cluster_x2): 128-thread CTAs of 4096
+      // nodes in clusters of up to 16 where the device schedules them (8 in
+      // portable mode), else 256-thread CTAs of 8192 nodes in clusters of up
+      // to 8; longer rows, and Picard and Newton rows, go through the
+      // multi-level solver
       std::vector<int64_t> mlrows;
       struct CGrp {
         int nt, c, cs;
         std::vector<std::pair<double, int64_t>> rows;
       };
       std::vector<CGrp> cgroups;
-      const bool cl = scheme == BURGERS_BTCS && ctx->cluster && ctx->resident_max == 0 &&
-                      !ctx->resident_override;
+      const bool cl = (scheme == BURGERS_BTCS || scheme == BURGERS_CN) && ctx->cluster &&
+                      ctx->resident_max == 0 && !ctx->resident_override;
+      const int ckind = scheme == BURGERS_CN ? K_CN_CLUSTER : K_BTCS_CLUSTER;
       for (int64_t b : longs) {
         const burgers_instance& in = batch->inst[b];
         int nt = 0, c = 0;
@@ -602,7 +604,7 @@ static burgers_status build_plan(burgers_ctx* ctx, int scheme, const burgers_bat
         }
         const int64_t W = int64_t(nt) * c;
         const int cs = nt ? int((in.n + W - 1) / W) : 0;
-        if (!nt || cs < 2 || !find_kernel(K_BTCS_CLUSTER, dtype, nt, c, cs)) {
+        if (!nt || cs < 2 || !find_kernel(ckind, dtype, nt, c, cs)) {
           mlrows.push_back(b);
           continue;
         }
@@ -618,7 +620,7 @@ static burgers_status build_plan(burgers_ctx* ctx, int scheme, const burgers_bat
       for (CGrp& g : cgroups) {
         std::stable_sort(g.rows.begin(), g.rows.end(),
                          [](const auto& a, const auto& b) { return a.first > b.first; });
-        const KernelEntry* k = find_kernel(K_BTCS_CLUSTER, dtype, g.nt, g.c, g.cs);
+        const KernelEntry* k = find_kernel(ckind, dtype, g.nt, g.c, g.cs);
         int begin = int(p->rows.size());
         for (auto& pr : g.rows) {
           p->rows.push_back(make_row(batch->inst[pr.second], iters));

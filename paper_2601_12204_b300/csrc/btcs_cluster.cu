@@ -28,6 +28,7 @@
 #include <cooperative_groups.h>
 
 #include "btcs_common.cuh"
+#include "btcs_kernel.cuh"
 #include "common.cuh"
 #include "kernels.h"
 
@@ -331,7 +332,7 @@ __device__ __forceinline__ void cluster_solve(ClusterShared<T, NT>& cs, bool per
 // arithmetic the cluster solve uses for a CTA's first node, so the halo
 // values are bitwise the owners'. Increment form and Kahan-compensated FP32
 // state as in btcs.cu.
-template <int NT, int C, int CS>
+template <int NT, int C, int CS, int VAR = VAR_BTCS>
 __global__ void __cluster_dims__(CS, 1, 1)
 __launch_bounds__(NT, NT <= 512 ? 512 / NT : 1)
     k_btcs_cluster_x2(float* __restrict__ u, const RowDesc* __restrict__ rows, int count,
@@ -384,7 +385,11 @@ __launch_bounds__(NT, NT <= 512 ? 512 / NT : 1)
     cluster.map_shared_rank(&cs.reply, kl)->halo_r = cs.hfirst[0];
   }
   cluster.sync();
-  const float r = rd.rf, s = rd.sf, ds1 = 1.f + 2.f * s;
+  // matrix coefficients; Crank-Nicolson (VAR_CN): half of the step's r and s,
+  // with the full step's explicit increment as right-hand side
+  static_assert(VAR == VAR_BTCS || VAR == VAR_CN, "lagged BTCS or Crank-Nicolson rows");
+  const float r = VAR == VAR_CN ? 0.5f * rd.rf : rd.rf, s = VAR == VAR_CN ? 0.5f * rd.sf : rd.sf;
+  const float ds1 = 1.f + 2.f * s;
   const float2 R2 = make_float2(r, r), S2 = make_float2(s, s), DS1 = make_float2(ds1, ds1);
   const bool dfirst = !per && rank == 0 && tid == 0;
   const bool dlast = !per && lastcta && tid == tl;
@@ -414,6 +419,7 @@ __launch_bounds__(NT, NT <= 512 ? 512 / NT : 1)
       float2 nc = sub2(S2, m);  // -c
       float2 d = add2(DS1, sub2(M, m));
       float2 nrhs = fma2(nl, DL, mul2(c, ER));  // -rhs of the increment form
+      if constexpr (VAR == VAR_CN) nrhs = mul2(make_float2(2.f, 2.f), nrhs);
       if (k == 0 && dfirst) { nl.x = 0.f; c.x = 0.f; nc.x = 0.f; d.x = 1.f; nrhs.x = 0.f; }
       const float2 den = fma2(nl, chp, d);
       const float2 inv = make_float2(recip(den.x), recip(den.y));
@@ -538,10 +544,14 @@ __launch_bounds__(NT, NT <= 512 ? 512 / NT : 1)
   cluster.sync();  // no CTA leaves while another may still address its memory
 }
 
-// FP32 rows run the packed-pair form of the kernel (k_btcs_cluster_x2)
+// FP32 rows run the packed-pair form of the kernel (k_btcs_cluster_x2): the
+// lagged BTCS rows and the Crank-Nicolson rows
 #define REG_CLUSTER(T, DT, NT, C, CS)                                                       \
   reg.push_back({K_BTCS_CLUSTER, DT, NT, C, CS,                                             \
-                 reinterpret_cast<const void*>(&k_btcs_cluster_x2<NT, C, CS>),             \
+                 reinterpret_cast<const void*>(&k_btcs_cluster_x2<NT, C, CS, VAR_BTCS>),   \
+                 sizeof(T) * size_t(NT) * C * 2});                                          \
+  reg.push_back({K_CN_CLUSTER, DT, NT, C, CS,                                               \
+                 reinterpret_cast<const void*>(&k_btcs_cluster_x2<NT, C, CS, VAR_CN>),     \
                  sizeof(T) * size_t(NT) * C * 2});
 #define REG_CLUSTERS(T, DT, NT, C)                                                          \
   REG_CLUSTER(T, DT, NT, C, 2) REG_CLUSTER(T, DT, NT, C, 3) REG_CLUSTER(T, DT, NT, C, 4)    \
