@@ -579,21 +579,25 @@ static burgers_status build_plan(burgers_ctx* ctx, int scheme, const burgers_bat
       // byte per node (span / 4 elements each)
       p->scratch_elems = dtype == 0 ? span + span / 2 : span;
     } else {
-      // lagged BTCS and Crank-Nicolson rows that fit a cluster stay resident
-      // in its shared memory (k_btcs_cluster_x2): 128-thread CTAs of 4096
-      // nodes in clusters of up to 16 where the device schedules them (8 in
-      // portable mode), else 256-thread CTAs of 8192 nodes in clusters of up
-      // to 8; longer rows, and Picard and Newton rows, go through the
-      // multi-level solver
+      // lagged BTCS, Crank-Nicolson and Picard rows that fit a cluster stay
+      // resident in its shared memory (k_btcs_cluster_x2): 128-thread CTAs
+      // of 4096 nodes in clusters of up to 16 where the device schedules them
+      // (8 in portable mode), else 256-thread CTAs of 8192 nodes in clusters
+      // of up to 8; longer rows, and Newton rows, go through the multi-level
+      // solver, as do rows whose cluster the device cannot schedule for the
+      // variant's kernel (Picard's also stages the iterate's e).
       std::vector<int64_t> mlrows;
       struct CGrp {
         int nt, c, cs;
         std::vector<std::pair<double, int64_t>> rows;
       };
       std::vector<CGrp> cgroups;
-      const bool cl = (scheme == BURGERS_BTCS || scheme == BURGERS_CN) && ctx->cluster &&
-                      ctx->resident_max == 0 && !ctx->resident_override;
-      const int ckind = scheme == BURGERS_CN ? K_CN_CLUSTER : K_BTCS_CLUSTER;
+      const bool cl = (scheme == BURGERS_BTCS || scheme == BURGERS_CN ||
+                       scheme == BURGERS_PICARD) &&
+                      ctx->cluster && ctx->resident_max == 0 && !ctx->resident_override;
+      const int ckind = scheme == BURGERS_CN       ? K_CN_CLUSTER
+                        : scheme == BURGERS_PICARD ? K_PICARD_CLUSTER
+                                                   : K_BTCS_CLUSTER;
       for (int64_t b : longs) {
         const burgers_instance& in = batch->inst[b];
         int nt = 0, c = 0;
@@ -604,7 +608,10 @@ static burgers_status build_plan(burgers_ctx* ctx, int scheme, const burgers_bat
         }
         const int64_t W = int64_t(nt) * c;
         const int cs = nt ? int((in.n + W - 1) / W) : 0;
-        if (!nt || cs < 2 || !find_kernel(ckind, dtype, nt, c, cs)) {
+        const KernelEntry* ck = nt && cs >= 2 ? find_kernel(ckind, dtype, nt, c, cs) : nullptr;
+        // (the context's cluster limit was taken on the BTCS kernel; the
+        // variants' own kernels are checked with the occupancy API)
+        if (!ck || (ckind != K_BTCS_CLUSTER && !cluster_fits(*ck))) {
           mlrows.push_back(b);
           continue;
         }

@@ -47,6 +47,7 @@ struct alignas(16) ClusterSlot {
   T y0, a0, g0;         // block relation of chunk 0 (when ti > 0)
   T uf, lf;             // state (and Kahan term) of the CTA's first node
   T ul, ll;             // ... of its last node (end of chunk ti)
+  T ef, el;             // Picard: the iterate's offset e of those two nodes
   int ti;               // interface chunk
   int jf;               // end row of chunk 0 (0: chunk 0 is a single node)
 };
@@ -215,9 +216,13 @@ __device__ __forceinline__ void block_solve3(ClusterShared<T, NT>& cs, int lane)
 // and the new values of the nodes next to its ends. Dirichlet rows have
 // identity rows at the row's ends, so the first block has no left neighbour
 // (P = 0) and the system is plain.
+// mode 0: the step's new values u + delta (compensated); Picard iterations:
+// 1 the next iterate's u + (e + delta), 2 (the last) u + (e + delta)
+// compensated -- each the owner's arithmetic for its nodes.
 template <typename T, int NT, int CS>
 __device__ __forceinline__ void cluster_solve(ClusterShared<T, NT>& cs, bool per, int lane,
-                                              int rank, int par, cg::cluster_group& cluster) {
+                                              int rank, int par, cg::cluster_group& cluster,
+                                              int mode = 0) {
   const bool on = lane < CS;
   const int k = on ? lane : 0;
   // lane k reads CTA k's contribution (pushed into this CTA's memory before
@@ -291,8 +296,16 @@ __device__ __forceinline__ void cluster_solve(ClusterShared<T, NT>& cs, bool per
     const T X0 = s.ti > 0 ? tfma(-s.g0, Y, tfma(-s.a0, P, s.y0)) : Y;
     const T d0 = s.jf == 0 ? X0 : tfma(-s.rg0, X0, tfma(-s.ra0, P, s.rd0));
     T lf = s.lf, ll = s.ll;
-    first = comp_add(s.uf, d0, lf);
-    last = comp_add(s.ul, Y, ll);
+    if (mode == 0) {
+      first = comp_add(s.uf, d0, lf);
+      last = comp_add(s.ul, Y, ll);
+    } else if (mode == 1) {
+      first = s.uf + (s.ef + d0);
+      last = s.ul + (s.el + Y);
+    } else {
+      first = comp_add(s.uf, s.ef + d0, lf);
+      last = comp_add(s.ul, s.el + Y, ll);
+    }
   }
   const T last_prev = shfl(last, (lane + CS - 1) % CS);
   const T first_next = shfl(first, (lane + 1) % CS);
@@ -350,6 +363,8 @@ __launch_bounds__(NT, NT <= 512 ? 512 / NT : 1)
   BtcsShared<float, NT>& sm = cs.sm;
   float2* us = reinterpret_cast<float2*>(dsm);  // H * NT pairs
   float2* lo = us + H * NT;                      // H * NT pairs
+  float2* es = us + 2 * H * NT;                  // H * NT pairs (Picard: the iterate's e)
+  constexpr bool ITER = VAR == VAR_PICARD;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const bool valid = item < count;  // grid is count * CS: always true
   const RowDesc rd = rows[valid ? item : 0];
@@ -386,8 +401,12 @@ __launch_bounds__(NT, NT <= 512 ? 512 / NT : 1)
   }
   cluster.sync();
   // matrix coefficients; Crank-Nicolson (VAR_CN): half of the step's r and s,
-  // with the full step's explicit increment as right-hand side
-  static_assert(VAR == VAR_BTCS || VAR == VAR_CN, "lagged BTCS or Crank-Nicolson rows");
+  // with the full step's explicit increment as right-hand side. Picard
+  // (VAR_PICARD): `iters` solves a step, A(w) delta = Delta(w) - e with
+  // w = u^n + e and e += delta (the rows of the current iterate w)
+  static_assert(VAR == VAR_BTCS || VAR == VAR_CN || VAR == VAR_PICARD,
+                "lagged BTCS, Crank-Nicolson or Picard rows");
+  const int nit = ITER ? rd.iters : 1;
   const float r = VAR == VAR_CN ? 0.5f * rd.rf : rd.rf, s = VAR == VAR_CN ? 0.5f * rd.sf : rd.sf;
   const float ds1 = 1.f + 2.f * s;
   const float2 R2 = make_float2(r, r), S2 = make_float2(s, s), DS1 = make_float2(ds1, ds1);
@@ -397,18 +416,28 @@ __launch_bounds__(NT, NT <= 512 ? 512 / NT : 1)
   float2 CH[H], AH[H], ND[H];  // forward: -ch, ah, -dh; backward: gamma, alpha, -delta
   int par = 0;
   for (int64_t step = 0; step < rd.nsteps; ++step) {
+  if constexpr (ITER) {
+#pragma unroll
+    for (int k = 0; k < H; ++k) es[k * NT + tid] = make_float2(0.f, 0.f);
+  }
+  for (int it = 0; it < nit; ++it) {
+    const bool lastit = it + 1 == nit;
+    auto W = [&](int k) -> float2 {
+      if constexpr (ITER) return add2(us[k * NT + tid], es[k * NT + tid]);
+      else return us[k * NT + tid];
+    };
     const float halo_l = cs.reply.halo_l, halo_r = cs.reply.halo_r;
     const float left = tid > 0 ? cs.hlast[tid - 1] : halo_l;
     const float right = tid < tl ? cs.hfirst[tid + 1] : halo_r;
     // ---- forward sweep of both halves (A's first row reads the left
     // neighbour, B's first row node C/2 - 1, A's end row node C/2, B's end
     // row the right neighbour), then the backward sweep
-    float2 a = us[tid];
-    float2 DL = sub2(a, make_float2(left, us[(H - 1) * NT + tid].x));  // a - u_l
+    float2 a = W(0);
+    float2 DL = sub2(a, make_float2(left, W(H - 1).x));  // a - u_l
     float2 chp = make_float2(0.f, 0.f), ahp = make_float2(-1.f, -1.f), ndhp = make_float2(0.f, 0.f);
 #pragma unroll
     for (int k = 0; k < H; ++k) {
-      float2 an = (k + 1 < H) ? us[(k + 1) * NT + tid] : make_float2(us[tid].y, right);
+      float2 an = (k + 1 < H) ? W(k + 1) : make_float2(W(0).y, right);
       if (k == H - 2 && shrt) an.y = right;  // a short chunk's end row
       const float2 ER = sub2(an, a);         // u_r - a
       const float2 ra = mul2(R2, a);
@@ -420,6 +449,7 @@ __launch_bounds__(NT, NT <= 512 ? 512 / NT : 1)
       float2 d = add2(DS1, sub2(M, m));
       float2 nrhs = fma2(nl, DL, mul2(c, ER));  // -rhs of the increment form
       if constexpr (VAR == VAR_CN) nrhs = mul2(make_float2(2.f, 2.f), nrhs);
+      if constexpr (ITER) nrhs = add2(nrhs, es[k * NT + tid]);
       if (k == 0 && dfirst) { nl.x = 0.f; c.x = 0.f; nc.x = 0.f; d.x = 1.f; nrhs.x = 0.f; }
       const float2 den = fma2(nl, chp, d);
       const float2 inv = make_float2(recip(den.x), recip(den.y));
@@ -497,13 +527,16 @@ __launch_bounds__(NT, NT <= 512 ? 512 / NT : 1)
         sl.lf = lo[0].x;
         sl.ul = us[jl * NT + tl].y;
         sl.ll = lo[jl * NT + tl].y;
+        sl.ef = ITER ? es[0].x : 0.f;
+        sl.el = ITER ? es[jl * NT + tl].y : 0.f;
         sl.ti = tl;
         sl.jf = C - 1;
         if (lane < CS) store_slot(cluster.map_shared_rank(&cs.slots[par][rank], lane), sl);
       }
     }
     cluster.sync();
-    if (warp == Q - 1) cluster_solve<float, NT, CS>(cs, per, lane, rank, par, cluster);
+    if (warp == Q - 1)
+      cluster_solve<float, NT, CS>(cs, per, lane, rank, par, cluster, ITER ? (lastit ? 2 : 1) : 0);
     __syncthreads();
     par ^= 1;
     // ---- chunk-end values, X_A, back-substitution of both halves
@@ -523,18 +556,34 @@ __launch_bounds__(NT, NT <= 512 ? 512 / NT : 1)
         if (k == 0) ndelta.x = -d0;
         if (k == H - 1 && shrt) ndelta.y = 0.f;  // the padding pair keeps its value
         const int o = k * NT + tid;
-        const float2 uo = us[o], l0 = lo[o];
-        const float2 ny = add2(ndelta, l0);
-        const float2 nv = sub2(uo, ny);
-        lo[o] = add2(sub2(nv, uo), ny);
-        us[o] = nv;
+        float2 nv;
+        if constexpr (ITER) {
+          const float2 inc = sub2(es[o], ndelta);  // e + delta
+          if (!lastit) {
+            es[o] = inc;
+            nv = add2(us[o], inc);  // the next iterate's value (edges below)
+          } else {
+            const float2 uo = us[o], l0 = lo[o];
+            const float2 y = sub2(inc, l0);
+            nv = add2(uo, y);
+            lo[o] = sub2(sub2(nv, uo), y);
+            us[o] = nv;
+          }
+        } else {
+          const float2 uo = us[o], l0 = lo[o];
+          const float2 ny = add2(ndelta, l0);
+          nv = sub2(uo, ny);
+          lo[o] = add2(sub2(nv, uo), ny);
+          us[o] = nv;
+        }
         if (k == 0) cs.hfirst[tid] = nv.x;
         if (k == H - 2 && shrt) cs.hlast[tid] = nv.y;
         if (k == H - 1 && !shrt) cs.hlast[tid] = nv.y;
       }
     }
     __syncthreads();
-  }
+  }  // iterations
+  }  // steps
 #pragma unroll
   for (int k = 0; k < H; ++k) {
     const float2 x = us[k * NT + tid];
@@ -545,14 +594,18 @@ __launch_bounds__(NT, NT <= 512 ? 512 / NT : 1)
 }
 
 // FP32 rows run the packed-pair form of the kernel (k_btcs_cluster_x2): the
-// lagged BTCS rows and the Crank-Nicolson rows
+// lagged BTCS, Crank-Nicolson and Picard rows (Picard stages the iterate's e
+// beside the state: a third array of dynamic shared memory)
 #define REG_CLUSTER(T, DT, NT, C, CS)                                                       \
   reg.push_back({K_BTCS_CLUSTER, DT, NT, C, CS,                                             \
                  reinterpret_cast<const void*>(&k_btcs_cluster_x2<NT, C, CS, VAR_BTCS>),   \
                  sizeof(T) * size_t(NT) * C * 2});                                          \
   reg.push_back({K_CN_CLUSTER, DT, NT, C, CS,                                               \
                  reinterpret_cast<const void*>(&k_btcs_cluster_x2<NT, C, CS, VAR_CN>),     \
-                 sizeof(T) * size_t(NT) * C * 2});
+                 sizeof(T) * size_t(NT) * C * 2});                                          \
+  reg.push_back({K_PICARD_CLUSTER, DT, NT, C, CS,                                           \
+                 reinterpret_cast<const void*>(&k_btcs_cluster_x2<NT, C, CS, VAR_PICARD>), \
+                 sizeof(T) * size_t(NT) * C * 3});
 #define REG_CLUSTERS(T, DT, NT, C)                                                          \
   REG_CLUSTER(T, DT, NT, C, 2) REG_CLUSTER(T, DT, NT, C, 3) REG_CLUSTER(T, DT, NT, C, 4)    \
   REG_CLUSTER(T, DT, NT, C, 5) REG_CLUSTER(T, DT, NT, C, 6) REG_CLUSTER(T, DT, NT, C, 7)    \

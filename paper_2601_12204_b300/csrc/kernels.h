@@ -33,6 +33,7 @@ enum KernelKind : int32_t {
   K_EXPLICIT_STEP1_BULK = 15,  // K_EXPLICIT_STEP1 over tiles moved by bulk copies, `exact` stages
   K_BTCS_THOMAS = 16,       // lagged BTCS, one thread per row (Thomas), c = longest row
   K_CN_CLUSTER = 17,        // Crank-Nicolson, row resident in a cluster of `exact` CTAs
+  K_PICARD_CLUSTER = 18,    // Picard-iterated implicit upwind, row resident in a cluster
   K_KIND_COUNT
 };
 
