@@ -1,6 +1,8 @@
-// btcs_cluster.cu -- lagged upwind BTCS (Sec. 2.4, Eq. 23) for rows too long
-// for one CTA but short enough for a thread-block cluster: the row stays in
-// the shared memory of CS CTAs for all of its steps, as in the resident kernel.
+// btcs_cluster.cu -- lagged upwind BTCS (Sec. 2.4, Eq. 23), and the
+// Crank-Nicolson and Picard variants of the same tridiagonal rows, for rows
+// too long for one CTA but short enough for a thread-block cluster: the row
+// stays in the shared memory of CS CTAs for all of its steps, as in the
+// resident kernel.
 //
 // Three levels of the same partitioned elimination:
 //   chunk   each thread eliminates its C (or C - 1) rows (as two half-chunks
