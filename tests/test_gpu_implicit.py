@@ -199,6 +199,19 @@ def test_one_picard_iteration_is_the_btcs_step_long(ctx, dtype):
     assert np.array_equal(a, b)
 
 
+def test_one_picard_iteration_is_the_btcs_step_cluster(ctx):
+    """In the cluster-resident kernel (FP32 rows of up to 65536 nodes) one
+    Picard iteration is the lagged BTCS step: with the iterate's offset zero
+    every added term is exact, and the halo values take the same arithmetic
+    (bitwise)."""
+    _fresh(ctx)
+    ens = _concat([_one(n, bc, seed=n + bc) for n in (9000, 33001, 65000) for bc in (0, 1)])
+    dts = oracle_dts(ens, 6.0)
+    a = run_gpu(ctx, PICARD, ens, dts, 10, F32, iters=1)
+    b = run_gpu(ctx, BTCS, ens, dts, 10, F32)
+    assert np.array_equal(a, b)
+
+
 def test_rejections(ctx):
     """Iteration counts outside [1, 64] are refused before any work is
     queued, and so are long rows of the device-dt entry point (whose
