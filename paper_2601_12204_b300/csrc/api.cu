@@ -399,7 +399,7 @@ static burgers_status build_plan(burgers_ctx* ctx, int scheme, const burgers_bat
     // row of its capacity class; a tuning table could name another shape)
     if (!exact && dtype == 0 && sh.c >= 4 && sh.c % 2 == 0 &&
         (rkind == K_EXPLICIT_RESIDENT || rkind == K_BTCS_RESIDENT || rkind == K_CN_RESIDENT ||
-         rkind == K_PICARD_RESIDENT)) {
+         rkind == K_PICARD_RESIDENT || (rkind == K_RK4_RESIDENT && sh.c >= 16))) {
       const int64_t t = (int64_t(in.n) + sh.c - 1) / sh.c;
       if (t * sh.c - in.n > t || t > sh.nt)
         return set_error(BURGERS_EINVAL, "row length has no split into chunks of C or C - 1 "

@@ -501,6 +501,107 @@ __device__ __forceinline__ void rk4_steps_x2(float (&v)[C], float (&lo)[C], int6
   }
 }
 
+// RK4 (as rk4_steps_x2) on ragged FP32 rows cut into chunks of C or C - 1
+// nodes, as explicit_steps_split_x2_cc cuts them: every stage exchanges the
+// stage state's chunk edges (the periodic wrap through the wrap slots), and
+// held nodes (a Dirichlet row's ends, a short chunk's padding) have zero
+// increments in every stage.
+template <int NT, int C, int BCT>
+__device__ __forceinline__ void rk4_steps_x2_cc(float (&v)[C], float (&lo)[C], int64_t nsteps,
+                                                float r, float s, int tl, bool shrt,
+                                                float* sh_last, float* sh_first, float* sh_wrap) {
+  static_assert(C % 2 == 0 && C >= 4, "pairs of nodes, a short half of at least one");
+  constexpr int H = C / 2;
+  constexpr bool PER = BCT == BC_PERIODIC;
+  const int tid = threadIdx.x;
+  const bool dfirst = !PER && tid == 0;
+  const bool dlast = !PER && tid == tl;
+  const bool padwarp = __all_sync(FULL_MASK, tid > tl) != 0;
+  float2 V[H], D[H], K[H], ACC[H];
+#pragma unroll
+  for (int k = 0; k < H; ++k) {
+    V[k] = make_float2(v[k], v[k + H]);
+    D[k] = make_float2(-lo[k], -lo[k + H]);
+    K[k] = make_float2(0.f, 0.f);
+  }
+  const float2 NR = make_float2(-r, -r), S2 = make_float2(s, s), NS = make_float2(-s, -s);
+  const float2 Z2 = make_float2(0.f, 0.f);
+  for (int64_t k0 = 0; k0 < nsteps; k0 += SPLIT_FOLD) {
+   const int kb = int(nsteps - k0 < SPLIT_FOLD ? nsteps - k0 : int64_t(SPLIT_FOLD));
+   for (int kk = 0; kk < kb; ++kk) {
+    float2 U[H];
+#pragma unroll
+    for (int k = 0; k < H; ++k) U[k] = add2(V[k], D[k]);
+#pragma unroll
+    for (int st = 0; st < 4; ++st) {
+      const float cs = st == 0 ? 0.f : (st == 3 ? 1.f : 0.5f);
+      const float2 CST = make_float2(cs, cs);
+      float2 W[H];
+#pragma unroll
+      for (int k = 0; k < H; ++k) W[k] = st == 0 ? U[k] : fma2(CST, K[k], U[k]);
+      const float last = shrt ? W[H - 2].y : W[H - 1].y;  // the chunk's last node
+      float left, right, wrapL = 0.f, wrapR = 0.f;
+      halo_exchange<float, NT, PER>(W[0].x, last, last, tid == tl, st & 1, sh_last, sh_first,
+                                    sh_wrap, left, right, wrapL, wrapR);
+      if constexpr (PER) {
+        if (tid == 0) left = wrapL;
+        if (tid == tl) right = wrapR;
+      }
+      if (padwarp) {
+#pragma unroll
+        for (int k = 0; k < H; ++k) {
+          if (st == 0) ACC[k] = Z2;
+          K[k] = Z2;
+        }
+        continue;
+      }
+      float2 DL = sub2(W[0], make_float2(left, W[H - 1].x));
+#pragma unroll
+      for (int k = 0; k < H; ++k) {
+        float2 WR = (k + 1 < H) ? W[k + 1] : make_float2(W[0].y, right);
+        if (k == H - 2 && shrt) WR.y = right;  // a short chunk's end node
+        const float2 E = sub2(WR, W[k]);
+        const float2 m = make_float2(fminf(W[k].x, 0.f), fminf(W[k].y, 0.f));
+        const float2 M = make_float2(fmaxf(W[k].x, 0.f), fmaxf(W[k].y, 0.f));
+        const float2 P = fma2(NR, m, S2);
+        const float2 NQ = fma2(NR, M, NS);
+        float2 kn = fma2(P, E, fma2(NQ, DL, Z2));
+        bool keepx = false, keepy = false;
+        if (k == 0) keepx = dfirst;
+        if (k == H - 2) keepy = shrt && dlast;
+        if (k == H - 1) keepy = shrt || dlast;
+        if (keepx) kn.x = 0.f;
+        if (keepy) kn.y = 0.f;
+        if (st == 0) ACC[k] = kn;
+        else {
+          const float w = st == 3 ? 1.f : 2.f;
+          ACC[k] = fma2(make_float2(w, w), kn, ACC[k]);
+        }
+        K[k] = kn;
+        DL = E;
+      }
+    }
+    const float sx = 1.f / 6.f;
+    const float2 SIX = make_float2(sx, sx);
+#pragma unroll
+    for (int k = 0; k < H; ++k) D[k] = fma2(SIX, ACC[k], D[k]);
+   }
+#pragma unroll
+    for (int k = 0; k < H; ++k) {
+      const float2 t = add2(V[k], D[k]);
+      D[k] = sub2(D[k], sub2(t, V[k]));
+      V[k] = t;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < H; ++k) {
+    v[k] = V[k].x;
+    v[k + H] = V[k].y;
+    lo[k] = -D[k].x;
+    lo[k + H] = -D[k].y;
+  }
+}
+
 template <typename T, int NT, int C, int MODE, int BCT>
 __device__ __forceinline__ void rk4_steps(T (&v)[C], T (&lo)[C], int64_t nsteps, T r, T h, T s,
                                           int n, int64_t gbase, T* sh_last, T* sh_first,
@@ -691,10 +792,13 @@ __global__ void __launch_bounds__(NT) k_explicit_resident(T* __restrict__ u,
     const RowDesc rd = rows[item];
     T* row = u + rd.offset;
     const int base = threadIdx.x * C;
-    // ragged FP32 forward-Euler rows on packed pairs: chunks of C or C - 1
-    // nodes (explicit_steps_split_x2_cc); other ragged rows: chunks of C with
-    // the end found per node in the warp holding it
-    constexpr bool CC = !EXACT && sizeof(T) == 4 && INTEG == INTEG_EULER && C % 2 == 0 && C >= 4;
+    // ragged FP32 rows on packed pairs: chunks of C or C - 1 nodes (forward
+    // Euler, explicit_steps_split_x2_cc; RK4 from 16 nodes a thread,
+    // rk4_steps_x2_cc: at 512 x 8 that form took 70 registers, one CTA a SM,
+    // and measured no faster than the per-node end test); other ragged rows:
+    // chunks of C with the end found per node in the warp holding it
+    constexpr bool CC = !EXACT && sizeof(T) == 4 && C % 2 == 0 &&
+                        (INTEG == INTEG_EULER ? C >= 4 : C >= 16);
     int cstart = base, clen = C, tl = NT - 1;
     bool shrt = false;
     if constexpr (CC) {
@@ -714,7 +818,15 @@ __global__ void __launch_bounds__(NT) k_explicit_resident(T* __restrict__ u,
     }
     const T r = T(rd.r), h = T(0.5 * rd.r), s = T(rd.s);
     constexpr int M = EXACT ? MODE_EXACT : MODE_RAGGED;
-    if constexpr (CC) {
+    if constexpr (CC && INTEG == INTEG_RK4) {
+      (void)h;
+      if (rd.bc == BC_PERIODIC)
+        rk4_steps_x2_cc<NT, C, BC_PERIODIC>(v, lo, rd.nsteps, r, s, tl, shrt, sh_last, sh_first,
+                                            sh_wrap);
+      else
+        rk4_steps_x2_cc<NT, C, BC_DIRICHLET>(v, lo, rd.nsteps, r, s, tl, shrt, sh_last, sh_first,
+                                             sh_wrap);
+    } else if constexpr (CC) {
       (void)h;
       if (rd.bc == BC_PERIODIC)
         explicit_steps_split_x2_cc<NT, C, BC_PERIODIC>(v, lo, rd.nsteps, r, s, tl, shrt, sh_last,

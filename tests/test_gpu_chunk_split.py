@@ -1,7 +1,8 @@
 """GPU parity of the chunk split of ragged FP32 rows.
 
-FP32 BTCS, Crank-Nicolson, Picard and forward-Euler rows shorter than their
-CTA's capacity NT x C are cut into t = ceil(n / C) chunks of C or C - 1
+FP32 BTCS, Crank-Nicolson, Picard, forward-Euler and RK4 (16 nodes a thread
+and more) rows shorter than their CTA's capacity NT x C are cut into
+t = ceil(n / C) chunks of C or C - 1
 nodes, the last tC - n of them one node short, so a chunk's end sits at a
 position known when the kernel is compiled; threads past chunk t - 1 hold no
 nodes. Cluster rows are spread evenly over their CTAs and each CTA's nodes
@@ -14,14 +15,14 @@ boundary conditions, against the FP64 oracle at the FP32 bar.
 import numpy as np
 import pytest
 
-from gpu_helpers import (BTCS, CN, EXPLICIT, F32, PICARD, assert_parity, oracle_dts, run_gpu,
-                         run_oracle)
+from gpu_helpers import (BTCS, CN, EXPLICIT, F32, PICARD, RK4, assert_parity, oracle_dts,
+                         run_gpu, run_oracle)
 from test_gpu_ragged import _concat, _row, tune_key
 
 pytestmark = pytest.mark.gpu
 
 # kernel kinds of the tuning table (csrc/kernels.h)
-KIND = {EXPLICIT: 0, BTCS: 2, CN: 11, PICARD: 12}
+KIND = {EXPLICIT: 0, BTCS: 2, RK4: 9, CN: 11, PICARD: 12}
 
 
 def split_lengths(nt, c):
@@ -46,6 +47,7 @@ CASES = [
     (CN, 128, 32), (CN, 64, 32),
     (PICARD, 128, 16),
     (EXPLICIT, 128, 32), (EXPLICIT, 128, 16), (EXPLICIT, 512, 8),
+    (RK4, 128, 16), (RK4, 512, 16),
 ]
 
 
@@ -59,7 +61,7 @@ def test_chunk_split_extremes(scheme, nt, c, tmp_path):
     ns = split_lengths(nt, c)
     assert len(ns) >= 8
     ens = _concat([_row(n, bc, seed=11 * n + bc) for n in ns for bc in (0, 1)])
-    implicit = scheme != EXPLICIT
+    implicit = scheme in (BTCS, CN, PICARD)
     dts = oracle_dts(ens, 8.0 if implicit else 1.0)
     steps = np.array([9 + (i % 4) for i in range(ens.count)])
     iters = 2 if scheme == PICARD else 1
