@@ -137,7 +137,7 @@ __device__ __forceinline__ void resident_solve(T (&x)[C], T (&ah)[C], T (&ch)[C]
   const int si = sk(tid);
   sm.A[si] = A; sm.B[si] = B; sm.Cc[si] = Cc; sm.D[si] = D; sm.U[si] = T(0);
   __syncthreads();
-  if (warp == 0) {
+  if (warp == NT / 32 - 1) {  // the last warp (warp 0 also carries the row's first node)
     if (cyc) reduced_solve<T, NT, true>(sm, tl, lane);
     else reduced_solve<T, NT, false>(sm, tl, lane);
   }
@@ -358,11 +358,16 @@ __global__ void __launch_bounds__(NT) k_adjoint(const T* __restrict__ u0, const 
           };
           resident_solve<T, NT, C>(nu, ah, ch, trows, n, per, sm.bt);
           T (&xv)[C] = vx;  // x = u^{s+1}
-          xch_publish<T, NT, C>(xv, jstar, sm.xb, p);
-          __syncthreads();
+          // its neighbours across the chunk edges, read from the stored state
+          // (the values an exchange of xv would give, without its barrier)
           T xl0, xr0, xw;
-          xch_read<T, NT>(sm.xb, p, xl0, xr0, xw);
-          p ^= 1;
+          {
+            const T* ux = sg + (st + 1 - s0) * CAP;
+            const int tn = (n - 1) / C, jn = (n - 1) - tn * C;
+            xw = ux[0];
+            xl0 = tid > 0 ? ux[(C - 1) * NT + tid - 1] : ux[jn * NT + tn];
+            xr0 = tid + 1 < NT ? ux[tid + 1] : xw;
+          }
 #pragma unroll
           for (int j = 0; j < C; ++j) {
             const int gi = base + j;
