@@ -648,8 +648,213 @@ __device__ __forceinline__ void adj_explicit_exact_row(const T* __restrict__ u0,
   __syncthreads();
 }
 
+// FP32 rows of exactly NT*C nodes with C even: the same adjoint on packed
+// f32x2 pairs (nodes k and k + C/2 of a thread's chunk, as in the forward
+// kernel). The forward step is that of explicit_steps_split_x2 (bitwise the
+// scalar step above: p = s - r min(u, 0) is the rounding of s + (r/2)(|u| - u),
+// -q = -(s + r max(u, 0))), folded on the same global step index, so the
+// checkpoints and recomputes are those of the scalar form; the stored states
+// are pairs, [k][thread]. The reverse step applies the transposed stencil to
+// both nodes of a pair at once; the nu gradient sums each lane's nodes
+// separately (two partial sums per thread).
+template <int NT, int C, int BCT>
+__device__ __forceinline__ void adj_fwd_step_x2(float2 (&V)[C / 2], float2 (&D)[C / 2], int64_t st,
+                                                int& p, float r, float s,
+                                                AdjFastShared<float, NT>& sh) {
+  constexpr int H = C / 2;
+  const int tid = threadIdx.x;
+  const float2 NR = make_float2(-r, -r), S2 = make_float2(s, s), NS = make_float2(-s, -s);
+  const float2 U0 = add2(V[0], D[0]);
+  const float2 UL = add2(V[H - 1], D[H - 1]);
+  float fl[1] = {U0.x}, la[1] = {UL.y}, L[1], R[1];
+  adj_xch<float, NT, 1>(fl, la, p, sh, L, R);
+  p ^= 1;
+  float2 Uk = U0;
+  float2 DL = sub2(U0, make_float2(L[0], UL.x));  // u - u_l of pair 0
+#pragma unroll
+  for (int k = 0; k < H; ++k) {
+    const float2 UR = (k + 1 < H) ? add2(V[k + 1], D[k + 1]) : make_float2(U0.y, R[0]);
+    const float2 E = sub2(UR, Uk);  // u_r - u
+    const float2 m = make_float2(fminf(Uk.x, 0.f), fminf(Uk.y, 0.f));
+    const float2 M = make_float2(fmaxf(Uk.x, 0.f), fmaxf(Uk.y, 0.f));
+    const float2 P = fma2(NR, m, S2);   // p
+    const float2 NQ = fma2(NR, M, NS);  // -q
+    const float2 dn = fma2(P, E, fma2(NQ, DL, D[k]));
+    bool keepx = false, keepy = false;
+    if constexpr (BCT == BC_DIRICHLET) {
+      keepx = k == 0 && tid == 0;
+      keepy = k == H - 1 && tid == NT - 1;
+    }
+    if (!keepx) D[k].x = dn.x;
+    if (!keepy) D[k].y = dn.y;
+    DL = E;
+    Uk = UR;
+  }
+  if ((st + 1) % SPLIT_FOLD == 0) {
+#pragma unroll
+    for (int k = 0; k < H; ++k) {
+      const float2 t = add2(V[k], D[k]);
+      D[k] = sub2(D[k], sub2(t, V[k]));
+      V[k] = t;
+    }
+  }
+}
+
+template <int NT, int C, int BCT>
+__device__ __forceinline__ void adj_explicit_exact_row_x2(const float* __restrict__ u0,
+                                                          const float* gT, float* gu0,
+                                                          double* __restrict__ gnu,
+                                                          const RowDesc& rd, const AdjRow& ar,
+                                                          float* __restrict__ ws,
+                                                          AdjFastShared<float, NT>& sh) {
+  constexpr int H = C / 2, CAP = NT * C, HP = NT * H;  // a state slot: HP pairs
+  const int tid = threadIdx.x, base = tid * C;
+  const float r = float(rd.r), s = float(rd.s);
+  const int64_t ns = rd.nsteps, k = ar.stride;
+  float2* ck = reinterpret_cast<float2*>(ws + ar.ckpt);  // (V, D) pairs per checkpoint
+  float2* sg = reinterpret_cast<float2*>(ws + ar.seg);   // u pairs per segment state
+  int p = 0;
+  float2 V[H], D[H];
+#pragma unroll
+  for (int q = 0; q < H; ++q) {
+    V[q] = make_float2(u0[rd.offset + base + q], u0[rd.offset + base + q + H]);
+    D[q] = make_float2(0.f, 0.f);
+  }
+  // ---- forward pass with checkpoints every k steps
+  for (int64_t st = 0; st < ns; ++st) {
+    if (st % k == 0) {
+      float2* dst = ck + (st / k) * 2 * HP;
+#pragma unroll
+      for (int q = 0; q < H; ++q) {
+        dst[q * NT + tid] = V[q];
+        dst[HP + q * NT + tid] = D[q];
+      }
+    }
+    if (st + 1 == ns) break;
+    adj_fwd_step_x2<NT, C, BCT>(V, D, st, p, r, s, sh);
+  }
+  // ---- reverse pass (split lambda state, folded every SPLIT_FOLD steps)
+  float2 LH[H], LD[H];
+#pragma unroll
+  for (int q = 0; q < H; ++q) {
+    LH[q] = make_float2(gT[rd.offset + base + q], gT[rd.offset + base + q + H]);
+    LD[q] = make_float2(0.f, 0.f);
+  }
+  const float2 R2 = make_float2(r, r), NR2 = make_float2(-r, -r), S2 = make_float2(s, s);
+  const float2 TS2 = make_float2(2.f * s, 2.f * s), Z2 = make_float2(0.f, 0.f);
+  double gacc = 0.0;
+  int64_t nrev = 0;
+  const int64_t nseg = ns > 0 ? (ns + k - 1) / k : 0;
+  for (int64_t sgi = nseg - 1; sgi >= 0; --sgi) {
+    const int64_t s0 = sgi * k;
+    const int64_t s1 = (s0 + k < ns) ? s0 + k : ns;
+    {
+      const float2* src = ck + sgi * 2 * HP;
+#pragma unroll
+      for (int q = 0; q < H; ++q) {
+        V[q] = src[q * NT + tid];
+        D[q] = src[HP + q * NT + tid];
+      }
+    }
+    for (int64_t st = s0; st < s1; ++st) {
+      float2* dst = sg + (st - s0) * HP;
+#pragma unroll
+      for (int q = 0; q < H; ++q) dst[q * NT + tid] = add2(V[q], D[q]);
+      if (st + 1 == s1) break;
+      adj_fwd_step_x2<NT, C, BCT>(V, D, st, p, r, s, sh);
+    }
+    float2 UN[H];
+    {
+      const float2* us = sg + (s1 - 1 - s0) * HP;
+#pragma unroll
+      for (int q = 0; q < H; ++q) UN[q] = us[q * NT + tid];
+    }
+    for (int64_t st = s1 - 1; st >= s0; --st) {
+      float2 U[H];
+#pragma unroll
+      for (int q = 0; q < H; ++q) U[q] = UN[q];
+      if (st > s0) {
+        const float2* us = sg + (st - 1 - s0) * HP;
+#pragma unroll
+        for (int q = 0; q < H; ++q) UN[q] = us[q * NT + tid];
+      }
+      float2 W[H];  // lambda of this step
+#pragma unroll
+      for (int q = 0; q < H; ++q) W[q] = add2(LH[q], LD[q]);
+      float fl[2] = {U[0].x, W[0].x}, la[2] = {U[H - 1].y, W[H - 1].y}, L[2], R[2];
+      adj_xch<float, NT, 2>(fl, la, p, sh, L, R);
+      p ^= 1;
+      float2 ul = make_float2(L[0], U[H - 1].x), ll = make_float2(L[1], W[H - 1].x);
+      float2 part = Z2;
+#pragma unroll
+      for (int q = 0; q < H; ++q) {
+        const float2 u = U[q];
+        const float2 ur = (q + 1 < H) ? U[q + 1] : make_float2(U[0].y, R[0]);
+        const float2 lr = (q + 1 < H) ? W[q + 1] : make_float2(W[0].y, R[1]);
+        const float2 dl = sub2(u, ul), dr = sub2(ur, u);
+        // 1 - diagonal of the step's Jacobian: r ((u > 0 ? dl : dr) + |u|) + 2s
+        const float2 sel = make_float2(u.x > 0.f ? dl.x : dr.x, u.y > 0.f ? dl.y : dr.y);
+        const float2 cI = fma2(R2, add2(sel, make_float2(fabsf(u.x), fabsf(u.y))), TS2);
+        float2 inc = mul2(make_float2(-cI.x, -cI.y), W[q]);
+        const float2 incR = fma2(fma2(R2, make_float2(fmaxf(ur.x, 0.f), fmaxf(ur.y, 0.f)), S2), lr, inc);
+        const float2 incRL = fma2(fma2(NR2, make_float2(fminf(ul.x, 0.f), fminf(ul.y, 0.f)), S2), ll, incR);
+        const float2 pn = fma2(W[q], sub2(dr, dl), part);
+        if constexpr (BCT == BC_DIRICHLET) {
+          // rows 0 and CAP - 1 are held: no update of their own, none sent
+          // to or taken from them by their neighbours
+          const int gx = base + q, gy = base + q + H;
+          const bool upIx = gx != 0 && gx != CAP - 1, upIy = gy != 0 && gy != CAP - 1;
+          const bool upRx = gx + 1 < CAP - 1, upRy = gy + 1 < CAP - 1;
+          const bool upLx = gx - 1 > 0, upLy = gy - 1 > 0;
+          float2 ix = make_float2(upIx ? inc.x : 0.f, upIy ? inc.y : 0.f);
+          // replay the scalar order: -cI w, then the right term, then the left
+          if (upRx) ix.x = fmaf(fmaf(r, fmaxf(ur.x, 0.f), s), lr.x, ix.x);
+          if (upRy) ix.y = fmaf(fmaf(r, fmaxf(ur.y, 0.f), s), lr.y, ix.y);
+          if (upLx) ix.x = fmaf(fmaf(-r, fminf(ul.x, 0.f), s), ll.x, ix.x);
+          if (upLy) ix.y = fmaf(fmaf(-r, fminf(ul.y, 0.f), s), ll.y, ix.y);
+          part = make_float2(upIx ? pn.x : part.x, upIy ? pn.y : part.y);
+          LD[q] = add2(LD[q], ix);
+        } else {
+          part = pn;
+          LD[q] = add2(LD[q], incRL);
+        }
+        ul = u;
+        ll = W[q];
+      }
+      gacc += double(part.x) + double(part.y);
+      if (++nrev % SPLIT_FOLD == 0) {
+#pragma unroll
+        for (int q = 0; q < H; ++q) {
+          const float2 t = add2(LH[q], LD[q]);
+          LD[q] = sub2(LD[q], sub2(t, LH[q]));
+          LH[q] = t;
+        }
+      }
+    }
+  }
+  // ---- outputs
+#pragma unroll
+  for (int q = 0; q < H; ++q) {
+    const float2 g = add2(LH[q], LD[q]);
+    gu0[rd.offset + base + q] = g.x;
+    gu0[rd.offset + base + q + H] = g.y;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) gacc += __shfl_xor_sync(FULL_MASK, gacc, o);
+  if ((tid & 31) == 0) sh.red[tid >> 5] = gacc;
+  __syncthreads();
+  if (tid == 0) {
+    double t = 0.0;
+    for (int w = 0; w < NT / 32; ++w) t += sh.red[w];
+    gnu[ar.out_index] = t * rd.ds_dnu;
+  }
+  __syncthreads();
+}
+
+// FP32 on packed pairs, 16 nodes a thread: 512 threads a SM (128 registers).
 template <typename T, int NT, int C>
-__global__ void __launch_bounds__(NT) k_adjoint_explicit_exact(
+__global__ void __launch_bounds__(NT, (sizeof(T) == 4 && C == 16 && NT <= 256) ? 512 / NT : 1)
+    k_adjoint_explicit_exact(
     const T* __restrict__ u0, const T* gT, T* gu0, double* __restrict__ gnu,
     const RowDesc* __restrict__ rows, const AdjRow* __restrict__ arows, int count,
     int* __restrict__ counter, T* __restrict__ ws) {
@@ -662,10 +867,18 @@ __global__ void __launch_bounds__(NT) k_adjoint_explicit_exact(
     if (item >= count) return;
     const RowDesc rd = rows[item];
     const AdjRow ar = arows[item];
-    if (rd.bc == BC_PERIODIC)
+    // packed pairs for 16 nodes a thread (at 8 the packed form needed 106
+    // registers against the scalar form's 80)
+    if constexpr (sizeof(T) == 4 && C == 16) {
+      if (rd.bc == BC_PERIODIC)
+        adj_explicit_exact_row_x2<NT, C, BC_PERIODIC>(u0, gT, gu0, gnu, rd, ar, ws, sh);
+      else
+        adj_explicit_exact_row_x2<NT, C, BC_DIRICHLET>(u0, gT, gu0, gnu, rd, ar, ws, sh);
+    } else if (rd.bc == BC_PERIODIC) {
       adj_explicit_exact_row<T, NT, C, BC_PERIODIC>(u0, gT, gu0, gnu, rd, ar, ws, sh);
-    else
+    } else {
       adj_explicit_exact_row<T, NT, C, BC_DIRICHLET>(u0, gT, gu0, gnu, rd, ar, ws, sh);
+    }
   }
 }
 
