@@ -41,6 +41,43 @@ struct Xch {
   T first[2][NT], last[2][NT], wl[2], wr[2];
 };
 
+// dJ/dnu partial sums of the FP32 kernels between folds into the FP64 total:
+// Kahan summation over at most SPLIT_FOLD reverse steps, then s - c added in
+// FP64 (the fold schedule is the global reverse-step count, so the sum does
+// not depend on the checkpoint stride). One FP64 conversion and add per step
+// and thread would keep B300's FP64 pipe, which runs at a small fraction of
+// the FP32 rate, busy through the whole reverse sweep.
+struct NuSum {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    const float y = __fsub_rn(x, c);
+    const float t = __fadd_rn(s, y);
+    c = __fsub_rn(__fsub_rn(t, s), y);
+    s = t;
+  }
+  __device__ __forceinline__ void fold(double& acc) {
+    acc += double(s) - double(c);
+    s = 0.f;
+    c = 0.f;
+  }
+};
+
+// The same on packed pairs (two partial sums per thread).
+struct NuSum2 {
+  float2 s = make_float2(0.f, 0.f), c = make_float2(0.f, 0.f);
+  __device__ __forceinline__ void add(float2 x) {
+    const float2 y = sub2(x, c);
+    const float2 t = add2(s, y);
+    c = sub2(sub2(t, s), y);
+    s = t;
+  }
+  __device__ __forceinline__ void fold(double& acc) {
+    acc += (double(s.x) - double(c.x)) + (double(s.y) - double(c.y));
+    s = make_float2(0.f, 0.f);
+    c = make_float2(0.f, 0.f);
+  }
+};
+
 // Publishes this thread's end nodes of v; after the barrier, returns the
 // value left of node `base` (wrap: node n-1 for thread 0), right of node
 // base+C-1 and the periodic right neighbour of node n-1 (node 0).
@@ -249,6 +286,7 @@ __global__ void __launch_bounds__(NT) k_adjoint(const T* __restrict__ u0, const 
     }
     int64_t nrev = 0;
     double gacc = 0.0;
+    NuSum nus;  // FP32: this fold block's dJ/dnu partial sum
     const int64_t nseg = ns > 0 ? (ns + k - 1) / k : 0;
     for (int64_t sgi = nseg - 1; sgi >= 0; --sgi) {
       const int64_t s0 = sgi * k;
@@ -386,7 +424,8 @@ __global__ void __launch_bounds__(NT) k_adjoint(const T* __restrict__ u0, const 
 #pragma unroll
           for (int j = 0; j < C; ++j) vx[j] = v[j];  // u^s is the next step's u^{s+1}
         }
-        gacc += double(part);
+        if constexpr (SPLIT) nus.add(part);
+        else gacc += double(part);
         if constexpr (SPLIT) {
           if (++nrev % SPLIT_FOLD == 0) {
 #pragma unroll
@@ -395,10 +434,12 @@ __global__ void __launch_bounds__(NT) k_adjoint(const T* __restrict__ u0, const 
               lamd[j] = lamd[j] - (t - lam[j]);
               lam[j] = t;
             }
+            nus.fold(gacc);
           }
         }
       }
     }
+    if constexpr (SPLIT) nus.fold(gacc);
     // ---- outputs
 #pragma unroll
     for (int j = 0; j < C; ++j)
@@ -552,6 +593,7 @@ __device__ __forceinline__ void adj_explicit_exact_row(const T* __restrict__ u0,
     lamd[j] = T(0);
   }
   double gacc = 0.0;
+  NuSum nus;  // FP32: this fold block's dJ/dnu partial sum
   int64_t nrev = 0;  // reverse steps taken (fold schedule)
   const int64_t nseg = ns > 0 ? (ns + k - 1) / k : 0;
   for (int64_t sgi = nseg - 1; sgi >= 0; --sgi) {
@@ -620,7 +662,8 @@ __device__ __forceinline__ void adj_explicit_exact_row(const T* __restrict__ u0,
         ul = u;
         ll = w[j];
       }
-      gacc += double(part);
+      if constexpr (SPLIT) nus.add(part);
+      else gacc += double(part);
       if constexpr (SPLIT) {
         if (++nrev % SPLIT_FOLD == 0) {
 #pragma unroll
@@ -629,10 +672,12 @@ __device__ __forceinline__ void adj_explicit_exact_row(const T* __restrict__ u0,
             lamd[j] = lamd[j] - (t - lam[j]);
             lam[j] = t;
           }
+          nus.fold(gacc);
         }
       }
     }
   }
+  if constexpr (SPLIT) nus.fold(gacc);
   // ---- outputs
 #pragma unroll
   for (int j = 0; j < C; ++j) gu0[rd.offset + base + j] = SPLIT ? lam[j] + lamd[j] : lam[j];
@@ -743,6 +788,7 @@ __device__ __forceinline__ void adj_explicit_exact_row_x2(const float* __restric
   const float2 R2 = make_float2(r, r), NR2 = make_float2(-r, -r), S2 = make_float2(s, s);
   const float2 TS2 = make_float2(2.f * s, 2.f * s), Z2 = make_float2(0.f, 0.f);
   double gacc = 0.0;
+  NuSum2 nus;  // this fold block's dJ/dnu partial sums
   int64_t nrev = 0;
   const int64_t nseg = ns > 0 ? (ns + k - 1) / k : 0;
   for (int64_t sgi = nseg - 1; sgi >= 0; --sgi) {
@@ -821,7 +867,7 @@ __device__ __forceinline__ void adj_explicit_exact_row_x2(const float* __restric
         ul = u;
         ll = W[q];
       }
-      gacc += double(part.x) + double(part.y);
+      nus.add(part);
       if (++nrev % SPLIT_FOLD == 0) {
 #pragma unroll
         for (int q = 0; q < H; ++q) {
@@ -829,9 +875,11 @@ __device__ __forceinline__ void adj_explicit_exact_row_x2(const float* __restric
           LD[q] = sub2(LD[q], sub2(t, LH[q]));
           LH[q] = t;
         }
+        nus.fold(gacc);
       }
     }
   }
+  nus.fold(gacc);
   // ---- outputs
 #pragma unroll
   for (int q = 0; q < H; ++q) {
@@ -851,10 +899,9 @@ __device__ __forceinline__ void adj_explicit_exact_row_x2(const float* __restric
   __syncthreads();
 }
 
-// FP32 on packed pairs, 16 nodes a thread: 512 threads a SM (128 registers).
+// Persistent CTAs take rows from an atomic counter.
 template <typename T, int NT, int C>
-__global__ void __launch_bounds__(NT, (sizeof(T) == 4 && C == 16 && NT <= 256) ? 512 / NT : 1)
-    k_adjoint_explicit_exact(
+__device__ __forceinline__ void adj_explicit_exact_rows(
     const T* __restrict__ u0, const T* gT, T* gu0, double* __restrict__ gnu,
     const RowDesc* __restrict__ rows, const AdjRow* __restrict__ arows, int count,
     int* __restrict__ counter, T* __restrict__ ws) {
@@ -882,11 +929,39 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 && C == 16 && NT <= 256) ?
   }
 }
 
+template <typename T, int NT, int C>
+__global__ void __launch_bounds__(NT) k_adjoint_explicit_exact(
+    const T* __restrict__ u0, const T* gT, T* gu0, double* __restrict__ gnu,
+    const RowDesc* __restrict__ rows, const AdjRow* __restrict__ arows, int count,
+    int* __restrict__ counter, T* __restrict__ ws) {
+  adj_explicit_exact_rows<T, NT, C>(u0, gT, gu0, gnu, rows, arows, count, counter, ws);
+}
+
+// FP32 on packed pairs, 16 nodes a thread, capped at 512 threads a SM (128
+// registers; uncapped the packed form takes 160 and runs three CTAs of 128).
+// Its own kernel: a minimum-blocks bound on the other shapes, even 1, moves
+// ptxas to more registers for them.
+template <int NT>
+__global__ void __launch_bounds__(NT, 512 / NT) k_adjoint_explicit_exact_x2(
+    const float* __restrict__ u0, const float* gT, float* gu0, double* __restrict__ gnu,
+    const RowDesc* __restrict__ rows, const AdjRow* __restrict__ arows, int count,
+    int* __restrict__ counter, float* __restrict__ ws) {
+  static_assert(NT <= 512, "at least one CTA a SM");
+  adj_explicit_exact_rows<float, NT, 16>(u0, gT, gu0, gnu, rows, arows, count, counter, ws);
+}
+
+template <typename T, int NT, int C>
+const void* adj_exact_kernel() {
+  if constexpr (sizeof(T) == 4 && C == 16)
+    return reinterpret_cast<const void*>(&k_adjoint_explicit_exact_x2<NT>);
+  else
+    return reinterpret_cast<const void*>(&k_adjoint_explicit_exact<T, NT, C>);
+}
+
 #define REG_ADJ(T, DT, NT, C)                                                                      \
   reg.push_back({K_ADJ_EXPLICIT, DT, NT, C, 0, reinterpret_cast<const void*>(&k_adjoint<T, NT, C, 0>), \
                  0});                                                                              \
-  reg.push_back({K_ADJ_EXPLICIT, DT, NT, C, 1,                                                    \
-                 reinterpret_cast<const void*>(&k_adjoint_explicit_exact<T, NT, C>), 0});            \
+  reg.push_back({K_ADJ_EXPLICIT, DT, NT, C, 1, adj_exact_kernel<T, NT, C>(), 0});                  \
   reg.push_back({K_ADJ_BTCS, DT, NT, C, 0, reinterpret_cast<const void*>(&k_adjoint<T, NT, C, 1>), 0});
 
 void register_adjoint(std::vector<KernelEntry>& reg) {
