@@ -913,11 +913,11 @@ def extras(args, ctx, ens, u0, batches, probe, dev, world, rank):
 def long_variants_bench(ctx, dev, rows: int = 512, n: int = 32768, steps: int = 40):
     """Implicit variants on rows longer than the resident capacity: `rows`
     periodic random-Fourier rows of n nodes. Crank-Nicolson and 3 Picard
-    iterations at 10x the CFL dt by the default routing (FP32: the
-    cluster-resident kernel) and through the multi-level solver (cluster off);
-    3 Newton iterations at the CFL dt on viscosity-raised rows (cell Peclet <=
-    1.5) through the multi-level solver; lagged BTCS through the multi-level
-    solver and by the default routing for comparison. FP32 and FP64
+    iterations at 10x the CFL dt, and 3 Newton iterations at the CFL dt on
+    viscosity-raised rows (cell Peclet <= 1.5), by the default routing (FP32:
+    the cluster-resident kernel) and through the multi-level solver (cluster
+    off); lagged BTCS through the multi-level solver and by the default
+    routing for comparison. FP32 and FP64
     throughput, FP32 against FP64 on every row."""
     import torch
 
@@ -957,6 +957,7 @@ def long_variants_bench(ctx, dev, rows: int = 512, n: int = 32768, steps: int = 
              ("picard3", L.BURGERS_PICARD, 3, ens, BTCS_DT_FACTOR, 1),
              ("picard3_multilevel", L.BURGERS_PICARD, 3, ens, BTCS_DT_FACTOR, 0),
              ("newton3", L.BURGERS_NEWTON, 3, ens_n, 1.0, 1),
+             ("newton3_multilevel", L.BURGERS_NEWTON, 3, ens_n, 1.0, 0),
              ("btcs_multilevel", L.BURGERS_BTCS, 1, ens, BTCS_DT_FACTOR, 0),
              ("btcs_default", L.BURGERS_BTCS, 1, ens, BTCS_DT_FACTOR, 1))
     for name, scheme, iters, e, fac, cluster in cases:

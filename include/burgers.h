@@ -114,8 +114,9 @@ typedef enum {
                                     the multi-level BTCS solver; 0 = device limit (default 0) */
   BURGERS_OPT_AUTOTUNE = 4,      /* 1: time candidate launch shapes on first use (default 0) */
   BURGERS_OPT_LAUNCH_COUNT = 5,  /* write-only reset of the launch counter (value ignored) */
-  BURGERS_OPT_CLUSTER = 6        /* FP32 BTCS rows longer than one CTA but at most 65536
-                                    nodes stay resident in a thread-block cluster.
+  BURGERS_OPT_CLUSTER = 6        /* FP32 BTCS, Crank-Nicolson, Picard and Newton rows longer
+                                    than one CTA but at most 65536 nodes stay resident in a
+                                    thread-block cluster.
                                     1 (default): 128-thread CTAs in clusters of up to 16
                                     where the device can schedule them (non-portable size,
                                     checked with the occupancy API when the context is
@@ -212,9 +213,11 @@ burgers_status burgers_rk4_advance(burgers_ctx* ctx, const burgers_batch* batch,
  *   (I - dt/2 L(u^n)) u^{n+1} = (I + dt/2 L(u^n)) u^n,
  * L the upwind/central operator of Eq. 21 (so the rows are those of
  * burgers_btcs_advance with r/2 and s/2). Rows up to the resident capacity
- * (8192 nodes FP32, 4096 FP64) stay in one CTA; longer rows, of any length,
- * go through the multi-level partitioned solver of the long BTCS rows, with
- * the same rows at its first level. In place, layout, ownership and errors as
+ * (8192 nodes FP32, 4096 FP64) stay in one CTA; longer FP32 rows of up to
+ * 65536 nodes stay in the shared memory of a thread-block cluster
+ * (BURGERS_OPT_CLUSTER); other rows, of any length, go through the
+ * multi-level partitioned solver of the long BTCS rows, with the same rows at
+ * its first level. In place, layout, ownership and errors as
  * burgers_btcs_advance. */
 burgers_status burgers_cn_advance(burgers_ctx* ctx, const burgers_batch* batch, void* u_dev,
                                   burgers_stream stream);
@@ -223,7 +226,7 @@ burgers_status burgers_cn_advance(burgers_ctx* ctx, const burgers_batch* batch, 
  * A(w) w' = u^n from w = u^n, with A as in burgers_btcs_advance but its
  * coefficients taken from the latest iterate (iters = 1 is the lagged BTCS
  * step). iters in [1, 64], else EINVAL. Long rows as burgers_cn_advance
- * (each iteration one multi-level solve). */
+ * (each iteration one cluster or multi-level solve). */
 burgers_status burgers_picard_advance(burgers_ctx* ctx, const burgers_batch* batch, void* u_dev,
                                       int32_t iters, burgers_stream stream);
 
@@ -237,7 +240,7 @@ burgers_status burgers_picard_advance(burgers_ctx* ctx, const burgers_batch* bat
  * is strictly diagonally dominant while r max|w| < 1/2 (dt below half the
  * convective CFL limit dx/max|u|); beyond that it may not be, and the solve is
  * then not guaranteed. iters in [1, 64], else EINVAL. Long rows as
- * burgers_cn_advance (each iteration one multi-level solve). */
+ * burgers_cn_advance (each iteration one cluster or multi-level solve). */
 burgers_status burgers_newton_advance(burgers_ctx* ctx, const burgers_batch* batch, void* u_dev,
                                       int32_t iters, burgers_stream stream);
 
@@ -326,9 +329,9 @@ burgers_status burgers_cfl_dt_device(burgers_ctx* ctx, const burgers_batch* batc
  * row whose dt_dev[b] is not positive is left unchanged. Results are bitwise
  * those of the host-dt entry point with dt = dt_factor * dt_dev[b]. Plans are
  * cached as for the host-dt calls (keyed by the batch without its dt). Rows
- * that need the multi-level solver (BTCS rows longer than the cluster limit,
- * FP64 BTCS rows longer than one CTA, CN, Picard and Newton rows longer than
- * the resident capacity): EINVAL. dt_factor <= 0: EINVAL. */
+ * that need the multi-level solver (FP32 BTCS, CN, Picard and Newton rows
+ * longer than the cluster limit, FP64 rows of those schemes longer than the
+ * resident capacity): EINVAL. dt_factor <= 0: EINVAL. */
 burgers_status burgers_advance_dt_device(burgers_ctx* ctx, int32_t scheme,
                                          const burgers_batch* batch, void* u_dev,
                                          const double* dt_dev, double dt_factor, int32_t iters,

@@ -579,13 +579,14 @@ static burgers_status build_plan(burgers_ctx* ctx, int scheme, const burgers_bat
       // byte per node (span / 4 elements each)
       p->scratch_elems = dtype == 0 ? span + span / 2 : span;
     } else {
-      // lagged BTCS, Crank-Nicolson and Picard rows that fit a cluster stay
-      // resident in its shared memory (k_btcs_cluster_x2): 128-thread CTAs
-      // of 4096 nodes in clusters of up to 16 where the device schedules them
-      // (8 in portable mode), else 256-thread CTAs of 8192 nodes in clusters
-      // of up to 8; longer rows, and Newton rows, go through the multi-level
-      // solver, as do rows whose cluster the device cannot schedule for the
-      // variant's kernel (Picard's also stages the iterate's e).
+      // FP32 lagged BTCS, Crank-Nicolson, Picard and Newton rows that fit a
+      // cluster stay resident in its shared memory (k_btcs_cluster_x2):
+      // 128-thread CTAs of 4096 nodes in clusters of up to 16 where the
+      // device schedules them (8 in portable mode), else 256-thread CTAs of
+      // 8192 nodes in clusters of up to 8; longer rows go through the
+      // multi-level solver, as do rows whose cluster the device cannot
+      // schedule for the variant's kernel (the iterating variants also stage
+      // the iterate's e).
       std::vector<int64_t> mlrows;
       struct CGrp {
         int nt, c, cs;
@@ -593,10 +594,11 @@ static burgers_status build_plan(burgers_ctx* ctx, int scheme, const burgers_bat
       };
       std::vector<CGrp> cgroups;
       const bool cl = (scheme == BURGERS_BTCS || scheme == BURGERS_CN ||
-                       scheme == BURGERS_PICARD) &&
+                       scheme == BURGERS_PICARD || scheme == BURGERS_NEWTON) &&
                       ctx->cluster && ctx->resident_max == 0 && !ctx->resident_override;
       const int ckind = scheme == BURGERS_CN       ? K_CN_CLUSTER
                         : scheme == BURGERS_PICARD ? K_PICARD_CLUSTER
+                        : scheme == BURGERS_NEWTON ? K_NEWTON_CLUSTER
                                                    : K_BTCS_CLUSTER;
       for (int64_t b : longs) {
         const burgers_instance& in = batch->inst[b];

@@ -1,5 +1,5 @@
 // btcs_cluster.cu -- lagged upwind BTCS (Sec. 2.4, Eq. 23), and the
-// Crank-Nicolson and Picard variants of the same tridiagonal rows, for rows
+// Crank-Nicolson, Picard and Newton variants of tridiagonal rows, for rows
 // too long for one CTA but short enough for a thread-block cluster: the row
 // stays in the shared memory of CS CTAs for all of its steps, as in the
 // resident kernel.
@@ -49,7 +49,7 @@ struct alignas(16) ClusterSlot {
   T y0, a0, g0;         // block relation of chunk 0 (when ti > 0)
   T uf, lf;             // state (and Kahan term) of the CTA's first node
   T ul, ll;             // ... of its last node (end of chunk ti)
-  T ef, el;             // Picard: the iterate's offset e of those two nodes
+  T ef, el;             // Picard, Newton: the iterate's offset e of those two nodes
   int ti;               // interface chunk
   int jf;               // end row of chunk 0 (0: chunk 0 is a single node)
 };
@@ -218,7 +218,7 @@ __device__ __forceinline__ void block_solve3(ClusterShared<T, NT>& cs, int lane)
 // and the new values of the nodes next to its ends. Dirichlet rows have
 // identity rows at the row's ends, so the first block has no left neighbour
 // (P = 0) and the system is plain.
-// mode 0: the step's new values u + delta (compensated); Picard iterations:
+// mode 0: the step's new values u + delta (compensated); Picard and Newton iterations:
 // 1 the next iterate's u + (e + delta), 2 (the last) u + (e + delta)
 // compensated -- each the owner's arithmetic for its nodes.
 template <typename T, int NT, int CS>
@@ -365,8 +365,8 @@ __launch_bounds__(NT, NT <= 512 ? 512 / NT : 1)
   BtcsShared<float, NT>& sm = cs.sm;
   float2* us = reinterpret_cast<float2*>(dsm);  // H * NT pairs
   float2* lo = us + H * NT;                      // H * NT pairs
-  float2* es = us + 2 * H * NT;                  // H * NT pairs (Picard: the iterate's e)
-  constexpr bool ITER = VAR == VAR_PICARD;
+  float2* es = us + 2 * H * NT;                  // H * NT pairs (Picard, Newton: the iterate's e)
+  constexpr bool ITER = VAR == VAR_PICARD || VAR == VAR_NEWTON;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const bool valid = item < count;  // grid is count * CS: always true
   const RowDesc rd = rows[valid ? item : 0];
@@ -405,13 +405,20 @@ __launch_bounds__(NT, NT <= 512 ? 512 / NT : 1)
   // matrix coefficients; Crank-Nicolson (VAR_CN): half of the step's r and s,
   // with the full step's explicit increment as right-hand side. Picard
   // (VAR_PICARD): `iters` solves a step, A(w) delta = Delta(w) - e with
-  // w = u^n + e and e += delta (the rows of the current iterate w)
-  static_assert(VAR == VAR_BTCS || VAR == VAR_CN || VAR == VAR_PICARD,
-                "lagged BTCS, Crank-Nicolson or Picard rows");
+  // w = u^n + e and e += delta (the rows of the current iterate w). Newton
+  // (VAR_NEWTON, Eq. 10-14): `iters` solves J(w) delta = -F(w) of the
+  // central-convection residual of Eq. 11, e += delta, with the Jacobian rows
+  // l = -(r/2) w_i - s, d = 1 + (r/2)(w_{i+1} - w_{i-1}) + 2s,
+  // c = (r/2) w_i - s (the operands and roundings of the resident kernel's
+  // Newton rows)
+  static_assert(VAR == VAR_BTCS || VAR == VAR_CN || VAR == VAR_PICARD || VAR == VAR_NEWTON,
+                "lagged BTCS, Crank-Nicolson, Picard or Newton rows");
   const int nit = ITER ? rd.iters : 1;
   const float r = VAR == VAR_CN ? 0.5f * rd.rf : rd.rf, s = VAR == VAR_CN ? 0.5f * rd.sf : rd.sf;
   const float ds1 = 1.f + 2.f * s;
   const float2 R2 = make_float2(r, r), S2 = make_float2(s, s), DS1 = make_float2(ds1, ds1);
+  const float hr = 0.5f * r;
+  const float2 HR2 = make_float2(hr, hr), NS2 = make_float2(-s, -s);
   const bool dfirst = !per && rank == 0 && tid == 0;
   const bool dlast = !per && lastcta && tid == tl;
   const bool tlshort = bk > 0;
@@ -435,23 +442,36 @@ __launch_bounds__(NT, NT <= 512 ? 512 / NT : 1)
     // neighbour, B's first row node C/2 - 1, A's end row node C/2, B's end
     // row the right neighbour), then the backward sweep
     float2 a = W(0);
-    float2 DL = sub2(a, make_float2(left, W(H - 1).x));  // a - u_l
+    float2 ul = make_float2(left, W(H - 1).x);
+    float2 DL = sub2(a, ul);  // a - u_l
     float2 chp = make_float2(0.f, 0.f), ahp = make_float2(-1.f, -1.f), ndhp = make_float2(0.f, 0.f);
 #pragma unroll
     for (int k = 0; k < H; ++k) {
       float2 an = (k + 1 < H) ? W(k + 1) : make_float2(W(0).y, right);
       if (k == H - 2 && shrt) an.y = right;  // a short chunk's end row
       const float2 ER = sub2(an, a);         // u_r - a
-      const float2 ra = mul2(R2, a);
-      const float2 M = make_float2(fmaxf(ra.x, 0.f), fmaxf(ra.y, 0.f));
-      const float2 m = make_float2(fminf(ra.x, 0.f), fminf(ra.y, 0.f));
-      float2 nl = add2(S2, M);  // -l
-      float2 c = sub2(m, S2);   // c
-      float2 nc = sub2(S2, m);  // -c
-      float2 d = add2(DS1, sub2(M, m));
-      float2 nrhs = fma2(nl, DL, mul2(c, ER));  // -rhs of the increment form
-      if constexpr (VAR == VAR_CN) nrhs = mul2(make_float2(2.f, 2.f), nrhs);
-      if constexpr (ITER) nrhs = add2(nrhs, es[k * NT + tid]);
+      float2 nl, c, nc, d, nrhs;             // -l, c, -c, d, -rhs
+      if constexpr (VAR == VAR_NEWTON) {
+        const float2 ha = mul2(HR2, a);
+        const float2 cdf = sub2(an, ul);  // w_{i+1} - w_{i-1}
+        nl = add2(ha, S2);
+        c = sub2(ha, S2);
+        nc = sub2(S2, ha);
+        d = fma2(HR2, cdf, DS1);
+        // -rhs = F_i = e_i + (r/2) w_i (w_{i+1} - w_{i-1}) - s (w_{i+1} - 2 w_i + w_{i-1})
+        nrhs = fma2(NS2, sub2(ER, DL), fma2(ha, cdf, es[k * NT + tid]));
+      } else {
+        const float2 ra = mul2(R2, a);
+        const float2 M = make_float2(fmaxf(ra.x, 0.f), fmaxf(ra.y, 0.f));
+        const float2 m = make_float2(fminf(ra.x, 0.f), fminf(ra.y, 0.f));
+        nl = add2(S2, M);
+        c = sub2(m, S2);
+        nc = sub2(S2, m);
+        d = add2(DS1, sub2(M, m));
+        nrhs = fma2(nl, DL, mul2(c, ER));  // of the increment form
+        if constexpr (VAR == VAR_CN) nrhs = mul2(make_float2(2.f, 2.f), nrhs);
+        if constexpr (ITER) nrhs = add2(nrhs, es[k * NT + tid]);
+      }
       if (k == 0 && dfirst) { nl.x = 0.f; c.x = 0.f; nc.x = 0.f; d.x = 1.f; nrhs.x = 0.f; }
       const float2 den = fma2(nl, chp, d);
       const float2 inv = make_float2(recip(den.x), recip(den.y));
@@ -463,6 +483,7 @@ __launch_bounds__(NT, NT <= 512 ? 512 / NT : 1)
       AH[k] = ahp;
       ND[k] = ndhp;
       DL = ER;
+      ul = a;
       a = an;
     }
     const float eAc = chp.x, eAa = ahp.x, eAd = -ndhp.x;
@@ -596,8 +617,9 @@ __launch_bounds__(NT, NT <= 512 ? 512 / NT : 1)
 }
 
 // FP32 rows run the packed-pair form of the kernel (k_btcs_cluster_x2): the
-// lagged BTCS, Crank-Nicolson and Picard rows (Picard stages the iterate's e
-// beside the state: a third array of dynamic shared memory)
+// lagged BTCS, Crank-Nicolson, Picard and Newton rows (the iterating variants
+// stage the iterate's e beside the state: a third array of dynamic shared
+// memory)
 #define REG_CLUSTER(T, DT, NT, C, CS)                                                       \
   reg.push_back({K_BTCS_CLUSTER, DT, NT, C, CS,                                             \
                  reinterpret_cast<const void*>(&k_btcs_cluster_x2<NT, C, CS, VAR_BTCS>),   \
@@ -607,6 +629,9 @@ __launch_bounds__(NT, NT <= 512 ? 512 / NT : 1)
                  sizeof(T) * size_t(NT) * C * 2});                                          \
   reg.push_back({K_PICARD_CLUSTER, DT, NT, C, CS,                                           \
                  reinterpret_cast<const void*>(&k_btcs_cluster_x2<NT, C, CS, VAR_PICARD>), \
+                 sizeof(T) * size_t(NT) * C * 3});                                          \
+  reg.push_back({K_NEWTON_CLUSTER, DT, NT, C, CS,                                           \
+                 reinterpret_cast<const void*>(&k_btcs_cluster_x2<NT, C, CS, VAR_NEWTON>), \
                  sizeof(T) * size_t(NT) * C * 3});
 #define REG_CLUSTERS(T, DT, NT, C)                                                          \
   REG_CLUSTER(T, DT, NT, C, 2) REG_CLUSTER(T, DT, NT, C, 3) REG_CLUSTER(T, DT, NT, C, 4)    \

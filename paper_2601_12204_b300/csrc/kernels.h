@@ -34,6 +34,7 @@ enum KernelKind : int32_t {
   K_BTCS_THOMAS = 16,       // lagged BTCS, one thread per row (Thomas), c = longest row
   K_CN_CLUSTER = 17,        // Crank-Nicolson, row resident in a cluster of `exact` CTAs
   K_PICARD_CLUSTER = 18,    // Picard-iterated implicit upwind, row resident in a cluster
+  K_NEWTON_CLUSTER = 19,    // Newton on the Eq. 11 residual, row resident in a cluster
   K_KIND_COUNT
 };
 

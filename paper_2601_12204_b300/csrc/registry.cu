@@ -51,7 +51,8 @@ cudaError_t prepare_kernels() {
                                              int(e.dyn_smem));
       if (err != cudaSuccess) return err;
     }
-    if ((e.kind == K_BTCS_CLUSTER || e.kind == K_CN_CLUSTER || e.kind == K_PICARD_CLUSTER) &&
+    if ((e.kind == K_BTCS_CLUSTER || e.kind == K_CN_CLUSTER || e.kind == K_PICARD_CLUSTER ||
+         e.kind == K_NEWTON_CLUSTER) &&
         e.exact > 8) {
       // a refusal only leaves the wide clusters unused (cluster_fits says so)
       if (cudaFuncSetAttribute(e.fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=

@@ -15,8 +15,9 @@ boundary conditions, against the FP64 oracle at the FP32 bar.
 import numpy as np
 import pytest
 
-from gpu_helpers import (BTCS, CN, EXPLICIT, F32, PICARD, RK4, assert_parity, oracle_dts,
+from gpu_helpers import (BTCS, CN, EXPLICIT, F32, NEWTON, PICARD, RK4, assert_parity, oracle_dts,
                          run_gpu, run_oracle)
+from test_gpu_implicit import _resolved
 from test_gpu_ragged import _concat, _row, tune_key
 
 pytestmark = pytest.mark.gpu
@@ -88,15 +89,23 @@ CLUSTER_LENGTHS = [
 ]
 
 
-def test_cluster_chunk_split():
+# every variant the cluster kernel runs: (scheme, iterations, dt / CFL dt);
+# Newton on viscosity-raised rows at the CFL dt (its Jacobian is diagonally
+# dominant there)
+CLUSTER_CASES = [(BTCS, 1, 8.0), (CN, 1, 8.0), (PICARD, 2, 6.0), (NEWTON, 2, 1.0)]
+
+
+@pytest.mark.parametrize("scheme,iters,fac", CLUSTER_CASES)
+def test_cluster_chunk_split(scheme, iters, fac):
     from paper_2601_12204_b300.api import Context
     ens = _concat([_row(n, bc, seed=5 * n + bc) for n in CLUSTER_LENGTHS for bc in (0, 1)])
-    dts = oracle_dts(ens, 8.0)
+    ens = _resolved(ens, scheme)
+    dts = oracle_dts(ens, fac)
     steps = np.array([7 + (i % 3) for i in range(ens.count)])
     ctx = Context(0)
     try:
-        got = run_gpu(ctx, BTCS, ens, dts, steps, F32)
+        got = run_gpu(ctx, scheme, ens, dts, steps, F32, iters=iters)
     finally:
         ctx.close()
-    ref = run_oracle(BTCS, ens, dts, steps)
-    assert_parity(ens, got, ref, F32, "cluster split")
+    ref = run_oracle(scheme, ens, dts, steps, iters=iters)
+    assert_parity(ens, got, ref, F32, f"cluster split s{scheme} it{iters}")

@@ -140,9 +140,10 @@ def test_newton_converges_on_the_gpu(ctx):
         assert np.max(np.abs(f)) <= 1e-13
 
 
-# Rows beyond the resident capacity (8192 nodes FP32, 4096 FP64): one and two
-# reduction levels of the multi-level solver (FP32 chunks of 16 nodes and a
-# top level of up to 4096 rows: 9000 and 33000 one level, 70001 two; FP64
+# Rows beyond the resident capacity (8192 nodes FP32, 4096 FP64): FP32 rows of
+# up to 65536 nodes in a thread-block cluster by default; through the
+# multi-level solver, one and two reduction levels (FP32 chunks of 16 nodes and
+# a top level of up to 4096 rows: 9000 and 33000 one level, 70001 two; FP64
 # chunks of 8 and tops of up to 2048 rows: 9000 one level, 33000 and 70001 two).
 LONG_NS = (9000, 33000, 70001)
 
@@ -150,8 +151,10 @@ LONG_NS = (9000, 33000, 70001)
 @pytest.mark.parametrize("scheme,iters,fac", CASES)
 @pytest.mark.parametrize("dtype", [F64, F32])
 def test_long_rows_multilevel(ctx, scheme, iters, fac, dtype):
-    """Long rows of every variant, both BCs, ragged step counts, through the
-    multi-level solver against the oracle."""
+    """Long rows of every variant, both BCs, ragged step counts, by the
+    default routing against the oracle: FP32 rows of up to 65536 nodes in a
+    thread-block cluster, 70001 nodes and every FP64 row through the
+    multi-level solver."""
     _fresh(ctx)
     ens = _resolved(_concat([_one(n, bc, seed=n + 5 * bc) for n in LONG_NS for bc in (0, 1)]),
                     scheme)
@@ -160,6 +163,25 @@ def test_long_rows_multilevel(ctx, scheme, iters, fac, dtype):
     got = run_gpu(ctx, scheme, ens, dts, steps, dtype, iters=iters)
     ref = run_oracle(scheme, ens, dts, steps, iters=iters)
     assert_parity(ens, got, ref, dtype, f"long s{scheme} it{iters}")
+
+
+@pytest.mark.parametrize("scheme,iters,fac", CASES)
+def test_long_rows_cluster_off(ctx, scheme, iters, fac):
+    """FP32 rows of up to 65536 nodes run in a thread-block cluster by
+    default; with the cluster off the same rows take the multi-level solver
+    (FP32 9000 and 33000 nodes one level, 70001 two) against the oracle."""
+    _fresh(ctx)
+    ens = _resolved(_concat([_one(n, bc, seed=n + 5 * bc) for n in LONG_NS for bc in (0, 1)]),
+                    scheme)
+    dts = oracle_dts(ens, fac)
+    steps = np.array([12, 9, 20, 7, 15, 11])
+    ctx.set(L.BURGERS_OPT_CLUSTER, 0)
+    try:
+        got = run_gpu(ctx, scheme, ens, dts, steps, F32, iters=iters)
+    finally:
+        ctx.set(L.BURGERS_OPT_CLUSTER, 1)
+    ref = run_oracle(scheme, ens, dts, steps, iters=iters)
+    assert_parity(ens, got, ref, F32, f"long cluster off s{scheme} it{iters}")
 
 
 @pytest.mark.parametrize("scheme,iters,fac", CASES)
