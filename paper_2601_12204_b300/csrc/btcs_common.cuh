@@ -208,10 +208,11 @@ __device__ __forceinline__ void reduced_solve(BtcsShared<T, NT>& sm, int tl, int
   if constexpr (CYC) {
     // x = y - (v.y)/(1 + v.z) z with v.y = y_0 + fa y_tl, v.z likewise: the
     // corner values come from lane 0 (row 0) and the lane holding row tl.
+    // Every lane evaluates the factor from the same four values (one shuffle
+    // round, no broadcast of the result on the serial path).
     const T ytl = shfl(ysel, tl / Q), ztl = shfl(zsel, tl / Q);
-    T fac = T(0);
-    if (lane == 0) fac = sm_factor(fa, YREG ? y[0] : sm.X[sk(0)], ytl, YREG ? z[0] : sm.Z[sk(0)], ztl);
-    fac = shfl(fac, 0);
+    const T y0 = shfl(YREG ? y[0] : sm.X[sk(0)], 0), z0 = shfl(YREG ? z[0] : sm.Z[sk(0)], 0);
+    const T fac = sm_factor(fa, y0, ytl, z0, ztl);
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
       const int i = sk(r0 + q);
