@@ -1103,8 +1103,9 @@ def large_grid_bench(ctx, dev):
     ctx.set(L.BURGERS_OPT_STREAM_K, 0)
     # the temporally blocked run against min(HBM x K / 8 B, FP32 issue / 9 ops):
     # K from the tuning table's streaming entry if there is one, else the
-    # library's default for FP32 windows of 4096 nodes (32 steps per pass)
-    kb = 32
+    # library's default for FP32 forward-Euler windows (8192 nodes; 128 steps
+    # per pass on rows of 32 windows or more, else 64)
+    kb = 128 if nlg >= 32 * 8192 else 64
     for line in _tune_lines(ctx):
         key, nt, c, k = (int(x) for x in line.split())
         if key >> 56 == 1 and (key >> 52) & 0xF == 0 and k > 0:  # K_EXPLICIT_STREAM, FP32

@@ -109,7 +109,9 @@ typedef enum {
   BURGERS_OPT_GRAPHS = 0,        /* 1: replay multi-launch sequences as CUDA graphs (default 1) */
   BURGERS_OPT_PLAIN = 1,         /* 1: one launch per row per call, no batching (baseline) */
   BURGERS_OPT_STREAM_K = 2,      /* steps per HBM pass of the streaming explicit kernel, 1..64;
-                                    0 = tuned (default 0) */
+                                    0 (default) = the tuning table's entry, else FP32 64
+                                    (128 where every streamed row has 262144 nodes or more;
+                                    RK4 32), FP64 16 (RK4 4) */
   BURGERS_OPT_RESIDENT_MAX = 3,  /* rows longer than this use the streaming explicit kernel and
                                     the multi-level BTCS solver; 0 = device limit (default 0) */
   BURGERS_OPT_AUTOTUNE = 4,      /* 1: time candidate launch shapes on first use (default 0) */

@@ -307,13 +307,22 @@ static int blocks_per_sm(const KernelEntry* k) {
 // Streaming shape for a long explicit (kind K_EXPLICIT_STREAM) or RK4
 // (K_RK4_STREAM) row: the largest registered window that fits the row, with K
 // steps per pass such that the stale edges (K nodes per side, 4K for RK4)
-// take at most a quarter of the window.
+// take at most a quarter of the window. Untuned FP32 defaults: forward Euler
+// in windows of 8192 nodes with K = 64, or K = 128 where the shortest row
+// spans 32 windows or more (its last window's padding and the wider halo are
+// then small), RK4 in windows of 4096 with K = 32 (a window's load,
+// compensation decode and encode and store cost about as much as 11 of its
+// steps: on a 2^24-node row 256 x 16 with K = 32 ran 2.87e12 cell-updates/s,
+// 256 x 32 with K = 64 / 128 3.42e12 / 3.73e12; rows of 40000 nodes 2.33e12
+// at the old default, 2.86e12 at K = 64; RK4 K = 8 / 32 6.2e11 / 8.3e11).
 static bool pick_stream(const burgers_ctx* ctx, int kind, int dtype, int64_t n_min, Shape* sh,
                         int* K) {
-  static const Shape s32[] = {{256, 16}, {128, 16}, {32, 4}};
+  static const Shape s32[] = {{256, 32}, {256, 16}, {128, 16}, {32, 4}};
+  static const Shape s32rk[] = {{256, 16}, {128, 16}, {32, 4}};
   static const Shape s64[] = {{256, 8}, {128, 8}, {32, 4}};
-  const Shape* list = dtype == 0 ? s32 : s64;
   const int per_step = kind == K_RK4_STREAM ? 4 : 1;
+  const Shape* list = dtype != 0 ? s64 : (per_step == 4 ? s32rk : s32);
+  const int nlist = dtype == 0 && per_step == 1 ? 4 : 3;
   auto it = ctx->tuned.find(tune_key(kind, dtype, 0, 0));
   if (ctx->stream_k == 0 && it != ctx->tuned.end() &&
       int64_t(it->second.nt) * it->second.c <= n_min) {
@@ -322,11 +331,13 @@ static bool pick_stream(const burgers_ctx* ctx, int kind, int dtype, int64_t n_m
                                                                       (4 * per_step))));
     return true;
   }
-  for (int i = 0; i < 3; ++i) {
+  for (int i = 0; i < nlist; ++i) {
     int64_t W = int64_t(list[i].nt) * list[i].c;
     if (W <= n_min) {
       *sh = list[i];
-      int k = ctx->stream_k > 0 ? ctx->stream_k : (dtype == 0 ? 32 : 16) / per_step;
+      int k = ctx->stream_k > 0 ? ctx->stream_k
+                                : (dtype == 0 ? (per_step == 4 ? 32 : (n_min >= 32 * W ? 128 : 64))
+                                              : 16 / per_step);
       *K = int(std::max<int64_t>(1, std::min<int64_t>(k, W / (4 * per_step))));
       return true;
     }

@@ -231,7 +231,7 @@ burgers_status autotune(burgers_ctx* ctx, int scheme, const burgers_batch* batch
     const int shapes32[][2] = {{128, 16}, {256, 16}, {512, 16}, {256, 32}};
     const int shapes64[][2] = {{128, 8}, {256, 8}, {256, 16}};
     const int ns = dtype == 0 ? 4 : 3;
-    const int Ks[] = {8, 16, 32, 48, 64};
+    const int Ks[] = {8, 16, 32, 48, 64, 96, 128};
     float best = 1e30f;
     TuneVal pick;
     const int saved_k = ctx->stream_k;
@@ -363,7 +363,9 @@ burgers_status burgers_tune_load(burgers_ctx* ctx, const char* path) {
     const bool thomas = kind == K_BTCS_RESIDENT && v.k >= 1;
     const bool known = thomas ? find_kernel(K_BTCS_THOMAS, dtype, v.nt, v.c, v.k - 1) != nullptr
                               : find_kernel(kind, dtype, v.nt, v.c, exact_lookup) != nullptr;
-    if (!known || v.k < 0 || v.k > 64) {
+    // k: steps per pass of a streaming entry (up to 128), else a kernel index
+    const int kmax = (kind == K_EXPLICIT_STREAM || kind == K_RK4_STREAM) ? 128 : 64;
+    if (!known || v.k < 0 || v.k > kmax) {
       fclose(f);
       return set_error(BURGERS_EINVAL, "tuning table names a kernel shape that does not exist");
     }

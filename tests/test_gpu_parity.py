@@ -112,6 +112,25 @@ def test_streaming_explicit(ctx, dtype, K):
         _fresh(ctx)
 
 
+@pytest.mark.parametrize("dtype", [F64, F32])
+def test_streaming_explicit_default_windows(ctx, dtype):
+    """Rows of 8192 nodes and more with the untuned streaming defaults (FP32:
+    windows of 8192 nodes, 64 steps a pass): one window, two, a ragged last
+    window, both BCs, partial last passes."""
+    _fresh(ctx)
+    ctx.set(L.BURGERS_OPT_RESIDENT_MAX, 1024)
+    try:
+        ens = _concat([_one(n, bc, seed=n + bc) for n in (8192, 9001, 16385, 70001)
+                       for bc in (0, 1)])
+        dts = oracle_dts(ens)
+        steps = np.array([193, 128, 97, 64, 150, 1, 200, 65])
+        got = run_gpu(ctx, EXPLICIT, ens, dts, steps, dtype)
+        ref = run_oracle(EXPLICIT, ens, dts, steps)
+        assert_parity(ens, got, ref, dtype, "stream default K")
+    finally:
+        _fresh(ctx)
+
+
 # single-step tile shapes (threads, nodes a thread, bulk-copy stages; 0 = the
 # per-tile kernel only) of the K = 1 streaming path
 STEP1_SHAPES = {F32: [(512, 8, 0), (512, 8, 3), (512, 8, 4), (256, 16, 4), (128, 16, 6)],
@@ -208,11 +227,12 @@ def test_multilevel_btcs(ctx, dtype):
 @pytest.mark.parametrize("dtype", [F64, F32])
 def test_large_grid_both_schemes(ctx, dtype):
     """Configuration-3 shape at 2^22 nodes (periodic, sin x + 0.5 + noise,
-    nu = 1e-3): streaming explicit and multi-level BTCS against the oracle."""
+    nu = 1e-3): streaming explicit (FP32: the default 128 steps a pass, one
+    full pass and a partial one) and multi-level BTCS against the oracle."""
     _fresh(ctx)
     ens = W.large_grid(1 << 22)
     dt0 = oracle_dts(ens)
-    for scheme, dts, steps in ((EXPLICIT, dt0, 64), (BTCS, dt0 * 10.0, 4)):
+    for scheme, dts, steps in ((EXPLICIT, dt0, 160), (BTCS, dt0 * 10.0, 4)):
         got = run_gpu(ctx, scheme, ens, dts, steps, dtype)
         ref = run_oracle(scheme, ens, dts, steps)
         assert_parity(ens, got, ref, dtype, f"large s{scheme}")

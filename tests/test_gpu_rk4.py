@@ -112,6 +112,24 @@ def test_rk4_streaming(ctx, dtype, K):
         _fresh(ctx)
 
 
+@pytest.mark.parametrize("dtype", [F64, F32])
+def test_rk4_streaming_default_k(ctx, dtype):
+    """Long rows with the untuned RK4 streaming default (FP32: 32 steps a pass,
+    128 stale nodes per side; the next window prefetched into shared memory
+    while a window runs), both BCs, partial last passes."""
+    _fresh(ctx)
+    ctx.set(L.BURGERS_OPT_RESIDENT_MAX, 1024)
+    try:
+        ens = _concat([_one(n, bc, seed=n + bc) for n in (5000, 9001, 70001) for bc in (0, 1)])
+        dts = oracle_dts(ens)
+        steps = np.array([97, 64, 33, 32, 65, 1])
+        got = run_gpu(ctx, RK4, ens, dts, steps, dtype)
+        ref = run_oracle(RK4, ens, dts, steps)
+        assert_parity(ens, got, ref, dtype, "rk4 stream default K")
+    finally:
+        _fresh(ctx)
+
+
 def test_rk4_batched_plain_graphs_bitwise(ctx):
     """Batched, one-row-per-launch, graph and no-graph runs agree bitwise."""
     _fresh(ctx)
