@@ -557,7 +557,15 @@ __launch_bounds__(NT, NT <= 512 ? 512 / NT : 1)
         if (lane < CS) store_slot(cluster.map_shared_rank(&cs.slots[par][rank], lane), sl);
       }
     }
-    cluster.sync();
+    // the step's cluster barrier: the last warp (the only one that writes to or
+    // reads from another CTA's memory in the step loop) arrives with release
+    // semantics, the others relaxed, without a fence of their own; every
+    // thread waits (acquire)
+    if (warp == Q - 1)
+      asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+    else
+      asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory");
+    asm volatile("barrier.cluster.wait.aligned;" ::: "memory");
     if (warp == Q - 1)
       cluster_solve<float, NT, CS>(cs, per, lane, rank, par, cluster, ITER ? (lastit ? 2 : 1) : 0);
     __syncthreads();
