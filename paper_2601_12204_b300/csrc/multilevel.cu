@@ -64,6 +64,38 @@ struct UpperRows {
   }
 };
 
+// Upper-level tiles staged in shared memory: the CTA's TILE = NT*C rows of the
+// six chunk arrays of the level below (the first-row relation one row
+// further, for each row's right neighbour), loaded coalesced, each array
+// skewed by one element per C rows so that the C consecutive rows of the 32
+// threads of a warp fall in distinct banks (C + 1 is odd).
+template <typename T, int NT, int C>
+struct UpperSmem {
+  static constexpr int TILE = NT * C;
+  static constexpr int AS = TILE + TILE / C + 2;  // elements per array
+  static constexpr size_t bytes() { return sizeof(T) * 6 * size_t(AS); }
+  __device__ static __forceinline__ int sk(int p) { return p + p / C; }
+};
+
+// Row j of an upper level from the staged tile (the arithmetic of UpperRows).
+template <typename T, int NT, int C>
+struct UpperRowsSmem {
+  const T* S;
+  int lbase;  // the thread's first row within the tile
+  int je;
+  __device__ __forceinline__ void operator()(int j, T& l, T& d, T& c, T& rhs) const {
+    using U = UpperSmem<T, NT, C>;
+    if (j > je) { l = T(0); d = T(1); c = T(0); rhs = T(0); return; }
+    const int p = U::sk(lbase + j), p1 = U::sk(lbase + j + 1);
+    const T ech = S[p], eah = S[U::AS + p], edh = S[2 * U::AS + p];
+    const T fd = S[3 * U::AS + p1], fa = S[4 * U::AS + p1], fg = S[5 * U::AS + p1];
+    l = eah;
+    d = T(1) - ech * fa;
+    c = -ech * fg;
+    rhs = tfma(-ech, fd, edh);
+  }
+};
+
 // Level-0 rows in increment form: lagged upwind BTCS coefficients of u^n and
 // the explicit increment Delta(u^n) as right-hand side (A delta = Delta).
 template <typename T>
@@ -102,6 +134,76 @@ __global__ void __launch_bounds__(NT) k_ml_sweep(T* __restrict__ u, T* __restric
                                                  int level, int64_t step, int iter,
                                                  T* __restrict__ ea, T* __restrict__ eb) {
   (void)iter; (void)ea; (void)eb;
+  if constexpr (!LVL0) {
+    // upper levels: the tile staged in shared memory (UpperSmem); every
+    // thread passes the barriers, those past the level's end with no rows
+    using U = UpperSmem<T, NT, C>;
+    extern __shared__ __align__(16) unsigned char ml_dsm[];
+    T* S = reinterpret_cast<T*>(ml_dsm);
+    (void)u; (void)u2; (void)lo;
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+      const TileItem ti = items[it];
+      const MLRow& R = rows[ti.row];
+      if (step >= R.nsteps) continue;  // the whole CTA
+      const int64_t M = R.m[level];
+      const int64_t t0 = int64_t(ti.tile) * U::TILE;
+      const int nrow = int(M - t0 < int64_t(U::TILE) ? M - t0 : int64_t(U::TILE));
+      const T* E = ws + R.ef[level - 1];
+      for (int q = threadIdx.x; q <= nrow; q += NT) {
+        const int64_t i = t0 + q;
+        const int pq = U::sk(q);
+        if (q < nrow) {
+          S[pq] = E[i];
+          S[U::AS + pq] = E[M + i];
+          S[2 * U::AS + pq] = E[2 * M + i];
+        }
+        const int64_t i1 = (i == M) ? 0 : i;  // row i - 1's right neighbour (cyclic)
+        S[3 * U::AS + pq] = E[3 * M + i1];
+        S[4 * U::AS + pq] = E[4 * M + i1];
+        S[5 * U::AS + pq] = E[5 * M + i1];
+      }
+      __syncthreads();
+      const int lbase = int(threadIdx.x) * C;
+      const int64_t base = t0 + lbase;
+      const bool active = base < M;
+      const int je = !active ? -1
+                             : int(M - 1 - base < int64_t(C - 1) ? M - 1 - base : int64_t(C - 1));
+      T v[C], ah[C], ch[C];
+      T e_ch, e_ah, e_dh;
+      UpperRowsSmem<T, NT, C> rsrc{S, lbase, je};
+      chunk_forward<T, C>(v, ah, ch, je, rsrc, e_ch, e_ah, e_dh);
+      chunk_backward<T, C>(v, ah, ch, je);
+      const int64_t k = base / C;
+      const int64_t Mn = R.m[level + 1];
+      if constexpr (!RECOVER) {
+        if (active) {
+          T* Eo = ws + R.ef[level];
+          Eo[k] = e_ch;
+          Eo[Mn + k] = e_ah;
+          Eo[2 * Mn + k] = e_dh;
+          Eo[3 * Mn + k] = v[0];
+          Eo[4 * Mn + k] = ah[0];
+          Eo[5 * Mn + k] = ch[0];
+        }
+      } else {
+        // the solution of this thread's rows into its own slots of array 0
+        // (only it reads them), then the tile stored coalesced
+        if (active) {
+          const T* Xn = ws + R.x[level + 1];
+          const T L = k > 0 ? Xn[k - 1] : (R.bc == BC_PERIODIC ? Xn[Mn - 1] : T(0));
+          const T Xk = Xn[k];
+#pragma unroll
+          for (int j = 0; j < C; ++j)
+            if (j <= je) S[U::sk(lbase + j)] = tfma(-ch[j], Xk, tfma(-ah[j], L, v[j]));
+        }
+        __syncthreads();
+        T* out = ws + R.x[level];
+        for (int q = threadIdx.x; q < nrow; q += NT) out[t0 + q] = S[U::sk(q)];
+      }
+      __syncthreads();  // before the next tile is staged
+    }
+    return;
+  }
   T* src = (step & 1) ? u2 : u;
   T* dst = (step & 1) ? u : u2;
   for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
@@ -675,12 +777,14 @@ __global__ void __launch_bounds__(NT) k_ml_top(T* __restrict__ u, T* __restrict_
                  reinterpret_cast<const void*>(&k_ml_sweep0<T, NT, C, false>),               \
                  Sweep0Smem<T, NT, C>::bytes(false)});                                        \
   reg.push_back({K_BTCS_REDUCE, DT, NT, C, 0,                                                 \
-                 reinterpret_cast<const void*>(&k_ml_sweep<T, NT, C, false, false>), 0});    \
+                 reinterpret_cast<const void*>(&k_ml_sweep<T, NT, C, false, false>),         \
+                 UpperSmem<T, NT, C>::bytes()});                                              \
   reg.push_back({K_BTCS_RECOVER, DT, NT, C, 1,                                                \
                  reinterpret_cast<const void*>(&k_ml_sweep0<T, NT, C, true>),                \
                  Sweep0Smem<T, NT, C>::bytes(true)});                                         \
   reg.push_back({K_BTCS_RECOVER, DT, NT, C, 0,                                                \
-                 reinterpret_cast<const void*>(&k_ml_sweep<T, NT, C, false, true>), 0});
+                 reinterpret_cast<const void*>(&k_ml_sweep<T, NT, C, false, true>),          \
+                 UpperSmem<T, NT, C>::bytes()});
 // level-0 sweeps of the implicit variants: exact = 2 + variant (1 CN, 2
 // Picard, 3 Newton)
 #define REG_SWEEPV1(T, DT, NT, C, VAR)                                                         \
