@@ -722,6 +722,13 @@ __global__ void __launch_bounds__(NT) k_ml_top(T* __restrict__ u, T* __restrict_
                                                int level, int64_t step, int iter,
                                                T* __restrict__ ea, T* __restrict__ eb) {
   __shared__ BtcsShared<T, NT> sm;
+  // tops of 2048 rows or more stage their rows as the upper-level sweeps
+  // stage a tile (512 x 32768 one-level rows 7% faster, the 2^24-node row 3%;
+  // the smaller tops read them directly: staging made them 2-4% slower)
+  constexpr bool STAGE = NT * C >= 2048;
+  using U = UpperSmem<T, NT, C>;
+  extern __shared__ __align__(16) unsigned char ml_dsm[];
+  T* S = reinterpret_cast<T*>(ml_dsm);
   (void)u; (void)u2; (void)lo; (void)iter; (void)ea; (void)eb;
   (void)level;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -733,10 +740,32 @@ __global__ void __launch_bounds__(NT) k_ml_top(T* __restrict__ u, T* __restrict_
     const int base = tid * C;
     const int tl = int((M - 1) / C);
     const int je = base < M ? int(M - 1 - base < int64_t(C - 1) ? M - 1 - base : int64_t(C - 1)) : -1;
+    if constexpr (STAGE) {
+      const T* E = ws + R.ef[L - 1];
+      const int nrow = int(M);  // at most NT * C
+      for (int q = tid; q <= nrow; q += NT) {
+        const int pq = U::sk(q);
+        if (q < nrow) {
+          S[pq] = E[q];
+          S[U::AS + pq] = E[M + q];
+          S[2 * U::AS + pq] = E[2 * M + q];
+        }
+        const int64_t i1 = (q == nrow) ? 0 : q;  // row q - 1's right neighbour (cyclic)
+        S[3 * U::AS + pq] = E[3 * M + i1];
+        S[4 * U::AS + pq] = E[4 * M + i1];
+        S[5 * U::AS + pq] = E[5 * M + i1];
+      }
+      __syncthreads();
+    }
     T v[C], ah[C], ch[C];
     T e_ch, e_ah, e_dh;
-    UpperRows<T> src{ws + R.ef[L - 1], M, base, je};
-    chunk_forward<T, C>(v, ah, ch, je, src, e_ch, e_ah, e_dh);
+    if constexpr (STAGE) {
+      UpperRowsSmem<T, NT, C> src{S, base, je};
+      chunk_forward<T, C>(v, ah, ch, je, src, e_ch, e_ah, e_dh);
+    } else {
+      UpperRows<T> src{ws + R.ef[L - 1], M, base, je};
+      chunk_forward<T, C>(v, ah, ch, je, src, e_ch, e_ah, e_dh);
+    }
     chunk_backward<T, C>(v, ah, ch, je);
     sm.rd[sk(tid)] = v[0];
     sm.ra[sk(tid)] = ah[0];
@@ -763,12 +792,23 @@ __global__ void __launch_bounds__(NT) k_ml_top(T* __restrict__ u, T* __restrict_
       if (tid > 0) Lv = sm.X[sk(tid - 1)];
       else if (R.bc == BC_PERIODIC) Lv = sm.X[sk(tl)];
       const T Xt = sm.X[sk(tid)];
-      T* out = ws + R.x[L];
+      if constexpr (STAGE) {  // into this thread's own slots of array 0 (only it reads them)
 #pragma unroll
-      for (int j = 0; j < C; ++j)
-        if (j <= je) out[base + j] = tfma(-ch[j], Xt, tfma(-ah[j], Lv, v[j]));
+        for (int j = 0; j < C; ++j)
+          if (j <= je) S[U::sk(base + j)] = tfma(-ch[j], Xt, tfma(-ah[j], Lv, v[j]));
+      } else {
+        T* out = ws + R.x[L];
+#pragma unroll
+        for (int j = 0; j < C; ++j)
+          if (j <= je) out[base + j] = tfma(-ch[j], Xt, tfma(-ah[j], Lv, v[j]));
+      }
     }
     __syncthreads();
+    if constexpr (STAGE) {
+      T* out = ws + R.x[L];
+      for (int q = tid; q < int(M); q += NT) out[q] = S[U::sk(q)];
+      __syncthreads();
+    }
   }
 }
 
@@ -798,7 +838,8 @@ __global__ void __launch_bounds__(NT) k_ml_top(T* __restrict__ u, T* __restrict_
   REG_SWEEPV1(T, DT, NT, C, 1) REG_SWEEPV1(T, DT, NT, C, 2) REG_SWEEPV1(T, DT, NT, C, 3) \
   REG_SWEEPV1(T, DT, NT, C, 4)
 #define REG_TOP(T, DT, NT, C) \
-  reg.push_back({K_BTCS_TOP, DT, NT, C, 0, reinterpret_cast<const void*>(&k_ml_top<T, NT, C>), 0});
+  reg.push_back({K_BTCS_TOP, DT, NT, C, 0, reinterpret_cast<const void*>(&k_ml_top<T, NT, C>), \
+                 (NT * C >= 2048) ? UpperSmem<T, NT, C>::bytes() : 0});
 #define REG_COPY(T, DT, NT, C) \
   reg.push_back({K_BTCS_TOP, DT, NT, C, 1, reinterpret_cast<const void*>(&k_ml_copy<T, NT, C>), 0});
 
