@@ -743,9 +743,9 @@ static cudaError_t enqueue_plan(burgers_ctx* ctx, Plan* p, void* u, cudaStream_t
     cudaError_t e = cudaMemsetAsync(lo_a, 0, size_t(p->stream_span), st);
     if (e != cudaSuccess) return e;
   }
-  if (p->ml_span > 0 && p->dtype == 0) {  // multi-level Kahan terms start at zero
+  if (p->ml_span > 0 && p->dtype == 0) {  // multi-level Kahan terms (a byte a node) start at zero
     cudaError_t e = cudaMemsetAsync(static_cast<char*>(scratch) + size_t(p->ml_span) * esz, 0,
-                                    size_t(p->ml_span) * esz, st);
+                                    size_t(p->ml_span), st);
     if (e != cudaSuccess) return e;
   }
   // Resident launches are independent of each other and of the long-row

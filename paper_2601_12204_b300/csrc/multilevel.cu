@@ -96,36 +96,8 @@ struct UpperRowsSmem {
   }
 };
 
-// Level-0 rows in increment form: lagged upwind BTCS coefficients of u^n and
-// the explicit increment Delta(u^n) as right-hand side (A delta = Delta).
-template <typename T>
-struct NodeRows {
-  const T* row;
-  int64_t n;
-  int64_t base;
-  int je;
-  T r, s, ds1;
-  bool dir;
-  __device__ __forceinline__ void operator()(int j, T& l, T& d, T& c, T& rhs) const {
-    const int64_t gi = base + j;
-    if (j > je) { l = T(0); d = T(1); c = T(0); rhs = T(0); return; }
-    const T a = row[gi];
-    const T ul = row[gi == 0 ? n - 1 : gi - 1];
-    const T ur = row[gi == n - 1 ? 0 : gi + 1];
-    const T ra = r * a;
-    l = -s - tmax(ra, T(0));
-    c = tmin(ra, T(0)) - s;
-    d = ds1 + tabs(ra);
-    rhs = tfma(l, a - ul, -c * (ur - a));  // explicit increment from the same coefficients
-    if (dir && (gi == 0 || gi == n - 1)) { l = T(0); c = T(0); d = T(1); rhs = T(0); }
-  }
-};
-
-// One sweep of one level. Level 0 reads u^n from the buffer of the step's
-// parity (u for even steps, u2 for odd ones); its recover sweep writes
-// u^{n+1} = u^n + delta into the other buffer (FP32: Kahan term lo in place)
-// and copies rows whose steps are done straight through, so every row
-// alternates buffers in lockstep.
+// One sweep of an upper level (levels >= 1; level 0 runs k_ml_sweep0, whose
+// recover sweep writes u^{n+1} into the other buffer of the step's parity).
 template <typename T, int NT, int C, bool LVL0, bool RECOVER>
 __global__ void __launch_bounds__(NT) k_ml_sweep(T* __restrict__ u, T* __restrict__ u2,
                                                  T* __restrict__ lo, T* __restrict__ ws,
@@ -133,10 +105,11 @@ __global__ void __launch_bounds__(NT) k_ml_sweep(T* __restrict__ u, T* __restric
                                                  const TileItem* __restrict__ items, int nitems,
                                                  int level, int64_t step, int iter,
                                                  T* __restrict__ ea, T* __restrict__ eb) {
+  static_assert(!LVL0, "level 0 runs k_ml_sweep0");
   (void)iter; (void)ea; (void)eb;
-  if constexpr (!LVL0) {
-    // upper levels: the tile staged in shared memory (UpperSmem); every
-    // thread passes the barriers, those past the level's end with no rows
+  {
+    // the tile staged in shared memory (UpperSmem); every thread passes the
+    // barriers, those past the level's end with no rows
     using U = UpperSmem<T, NT, C>;
     extern __shared__ __align__(16) unsigned char ml_dsm[];
     T* S = reinterpret_cast<T*>(ml_dsm);
@@ -202,76 +175,12 @@ __global__ void __launch_bounds__(NT) k_ml_sweep(T* __restrict__ u, T* __restric
       }
       __syncthreads();  // before the next tile is staged
     }
-    return;
-  }
-  T* src = (step & 1) ? u2 : u;
-  T* dst = (step & 1) ? u : u2;
-  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
-    const TileItem ti = items[it];
-    const MLRow& R = rows[ti.row];
-    const int64_t M = R.m[level];
-    const int64_t base = int64_t(ti.tile) * (NT * C) + int64_t(threadIdx.x) * C;
-    if (base >= M) continue;
-    const int je = int(M - 1 - base < int64_t(C - 1) ? M - 1 - base : int64_t(C - 1));
-    if (step >= R.nsteps) {
-      if constexpr (LVL0 && RECOVER) {
-#pragma unroll
-        for (int j = 0; j < C; ++j)
-          if (j <= je) dst[R.offset + base + j] = src[R.offset + base + j];
-      }
-      continue;
-    }
-    T v[C], ah[C], ch[C];
-    T e_ch, e_ah, e_dh;
-    if constexpr (LVL0) {
-      const T s = T(R.s);
-      NodeRows<T> rsrc{src + R.offset, M, base, je, T(R.r), s, T(1) + T(2) * s,
-                       R.bc == BC_DIRICHLET};
-      chunk_forward<T, C>(v, ah, ch, je, rsrc, e_ch, e_ah, e_dh);
-    } else {
-      UpperRows<T> rsrc{ws + R.ef[level - 1], M, base, je};
-      chunk_forward<T, C>(v, ah, ch, je, rsrc, e_ch, e_ah, e_dh);
-    }
-    chunk_backward<T, C>(v, ah, ch, je);
-    const int64_t k = base / C;
-    const int64_t Mn = R.m[level + 1];
-    if constexpr (!RECOVER) {
-      T* Eo = ws + R.ef[level];
-      Eo[k] = e_ch;
-      Eo[Mn + k] = e_ah;
-      Eo[2 * Mn + k] = e_dh;
-      Eo[3 * Mn + k] = v[0];
-      Eo[4 * Mn + k] = ah[0];
-      Eo[5 * Mn + k] = ch[0];
-    } else {
-      const T* Xn = ws + R.x[level + 1];
-      const T L = k > 0 ? Xn[k - 1] : (R.bc == BC_PERIODIC ? Xn[Mn - 1] : T(0));
-      const T Xk = Xn[k];
-      if constexpr (LVL0) {
-        const int64_t o = R.offset + base;
-#pragma unroll
-        for (int j = 0; j < C; ++j)
-          if (j <= je) {
-            const T delta = tfma(-ch[j], Xk, tfma(-ah[j], L, v[j]));
-            T l0 = T(0);
-            if constexpr (Kahan<T>::on) l0 = lo[o + j];
-            dst[o + j] = comp_add(src[o + j], delta, l0);
-            if constexpr (Kahan<T>::on) lo[o + j] = l0;
-          }
-      } else {
-        T* out = ws + R.x[level];
-#pragma unroll
-        for (int j = 0; j < C; ++j)
-          if (j <= je) out[base + j] = tfma(-ch[j], Xk, tfma(-ah[j], L, v[j]));
-      }
-    }
   }
 }
 
 // ---------------------------------------------------------------------------
 // Level-0 sweeps with staged tiles. A CTA's tile of NT*C nodes and its two
-// halo nodes (and, for the recover sweep in FP32, the tile's Kahan terms) are
-// copied into shared memory with cp.async while the previous tile is being
+// halo nodes are copied into shared memory with cp.async while the previous tile is being
 // eliminated (two buffers), so the sweep streams instead of waiting on each
 // thread's strided loads. Rows whose start is 16-byte aligned move in 16-byte
 // vectors (the last one zero-filled past the row end); others move element
@@ -292,11 +201,10 @@ struct Sweep0Smem {
   static constexpr int GRP = 128 / int(sizeof(T));
   __device__ __host__ static constexpr int idx(int L) { return L + VE * (L / GRP); }
   static constexpr int SSK = (idx(TILE + VE) / VE + 1) * VE;  // one buffer, elements
-  // buffers: the state, its Kahan terms (FP32 recover sweeps) and the
-  // iterate's e (Picard, Newton), two of each
+  // buffers: the state and the iterate's e (Picard, Newton), two of each
   static constexpr size_t bytes(bool recover, bool iterating = false) {
-    return sizeof(T) * size_t(SSK) * 2 *
-           (1 + ((recover && Kahan<T>::on) ? 1 : 0) + (iterating ? 1 : 0));
+    (void)recover;
+    return sizeof(T) * size_t(SSK) * 2 * (1 + (iterating ? 1 : 0));
   }
 };
 
@@ -432,8 +340,11 @@ __global__ void __launch_bounds__(NT, ((sizeof(T) == 4 && VAR < 2) ? 768 : 512) 
   if constexpr (!STAGE_E) { (void)ecur; (void)enext; }
   using SM = Sweep0Smem<T, NT, C>;
   constexpr int TILE = SM::TILE, VE = SM::VE, SSK = SM::SSK;
+  // FP32 recover sweeps: the Kahan term of u lives in `lo` as one byte per
+  // node (lo8_encode against the value it compensates), read and written in
+  // place by each thread for its own nodes (16 contiguous bytes: no staging)
   constexpr bool KL = RECOVER && Kahan<T>::on;
-  constexpr int EBUF = KL ? 4 : 2;  // first buffer of e
+  constexpr int EBUF = 2;  // first buffer of e
   constexpr int RV = int(sizeof(MLRow) / 16);
   static_assert(sizeof(MLRow) % 16 == 0, "row record moves in 16-byte pieces");
   extern __shared__ __align__(16) unsigned char dsm[];
@@ -481,7 +392,6 @@ __global__ void __launch_bounds__(NT, ((sizeof(T) == 4 && VAR < 2) ? 768 : 512) 
     if (tid >= 32 && tid < 32 + RV)
       cp_async_vec(reinterpret_cast<char*>(&srow[b]) + 16 * (tid - 32),
                    reinterpret_cast<const char*>(rows + rowi) + 16 * (tid - 32), 16);
-    if constexpr (KL) stage_tile<T, NT, C>(sbase + (2 + b) * SSK, lo + coff[slot], t0, n);
     if constexpr (STAGE_E) {
       if (ecur) {  // e (lam) of the tile and of its two neighbours
         const T* erow = ecur + coff[slot];
@@ -517,7 +427,6 @@ __global__ void __launch_bounds__(NT, ((sizeof(T) == 4 && VAR < 2) ? 768 : 512) 
     const int64_t t0 = int64_t(stile[b]) * TILE;
     const int64_t base = t0 + int64_t(tid) * C;
     T* su = sbase + b * SSK;
-    T* sl = sbase + (2 + b) * SSK;
     const int lb = VE + tid * C;  // local index of this thread's first node
     using V = typename Vec16<T>::type;
     constexpr int NV = C / VE;
@@ -648,17 +557,34 @@ __global__ void __launch_bounds__(NT, ((sizeof(T) == 4 && VAR < 2) ? 768 : 512) 
         // add e + delta), one vector at a time, stored straight from
         // registers; rows already done are copied through
         T* drow = dst + R.offset + base;
-        T* lrow = lo + R.offset + base;
+        signed char* lrow = reinterpret_cast<signed char*>(lo) + R.offset + base;
         const int cnt = M - base < C ? int(M - base) : C;
-        const bool vec = cnt == C && (reinterpret_cast<uintptr_t>(drow) & 15) == 0 &&
-                         (!KL || (reinterpret_cast<uintptr_t>(lrow) & 15) == 0);
+        const bool vec = cnt == C && (reinterpret_cast<uintptr_t>(drow) & 15) == 0;
+        // the chunk's compensation bytes, four to a word (registers)
+        static_assert(C % 4 == 0, "whole words of compensation bytes");
+        unsigned lw[C / 4], nw[C / 4];
+#pragma unroll
+        for (int k = 0; k < C / 4; ++k) { lw[k] = 0u; nw[k] = 0u; }
+        const bool lvec = cnt == C && (reinterpret_cast<uintptr_t>(lrow) & 15) == 0 && C % 16 == 0;
+        if constexpr (KL) {
+          if (active) {
+            if (lvec) {
+#pragma unroll
+              for (int k = 0; k < C / 16; ++k) {
+                const uint4 w = reinterpret_cast<const uint4*>(lrow)[k];
+                lw[4 * k] = w.x; lw[4 * k + 1] = w.y; lw[4 * k + 2] = w.z; lw[4 * k + 3] = w.w;
+              }
+            } else {
+#pragma unroll
+              for (int j = 0; j < C; ++j)
+                if (j < cnt) lw[j >> 2] |= unsigned(static_cast<unsigned char>(lrow[j])) << (8 * (j & 3));
+            }
+          }
+        }
 #pragma unroll
         for (int q = 0; q < NV; ++q) {
           V w = lds_fresh(su + SM::idx(lb + q * VE));  // u^n again, not kept live
-          V wl;
-          if constexpr (KL) wl = lds_fresh(sl + SM::idx(lb + q * VE));
           T* wp = reinterpret_cast<T*>(&w);
-          T* wlp = reinterpret_cast<T*>(&wl);
           if (active) {
 #pragma unroll
             for (int e = 0; e < VE; ++e) {
@@ -669,7 +595,11 @@ __global__ void __launch_bounds__(NT, ((sizeof(T) == 4 && VAR < 2) ? 768 : 512) 
                   if (ecur) delta = ev[j + 1] + delta;
                 }
                 if constexpr (KL) {
-                  wp[e] = comp_add(wp[e], delta, wlp[e]);
+                  const signed char q0 = static_cast<signed char>(lw[j >> 2] >> (8 * (j & 3)));
+                  T l0 = T(lo8_decode(float(wp[e]), q0));
+                  wp[e] = comp_add(wp[e], delta, l0);
+                  nw[j >> 2] |= unsigned(static_cast<unsigned char>(lo8_encode(float(wp[e]), float(l0))))
+                                << (8 * (j & 3));
                 } else {
                   wp[e] = wp[e] + delta;
                 }
@@ -678,14 +608,24 @@ __global__ void __launch_bounds__(NT, ((sizeof(T) == 4 && VAR < 2) ? 768 : 512) 
           }
           if (vec) {
             *reinterpret_cast<V*>(drow + q * VE) = w;
-            if constexpr (KL) *reinterpret_cast<V*>(lrow + q * VE) = wl;
           } else {
 #pragma unroll
             for (int e = 0; e < VE; ++e)
-              if (q * VE + e < cnt) {
-                drow[q * VE + e] = wp[e];
-                if constexpr (KL) lrow[q * VE + e] = wlp[e];
-              }
+              if (q * VE + e < cnt) drow[q * VE + e] = wp[e];
+          }
+        }
+        if constexpr (KL) {  // rows already done keep their terms
+          if (active) {
+            if (lvec) {
+#pragma unroll
+              for (int k = 0; k < C / 16; ++k)
+                reinterpret_cast<uint4*>(lrow)[k] =
+                    make_uint4(nw[4 * k], nw[4 * k + 1], nw[4 * k + 2], nw[4 * k + 3]);
+            } else {
+#pragma unroll
+              for (int j = 0; j < C; ++j)
+                if (j < cnt) lrow[j] = static_cast<signed char>(nw[j >> 2] >> (8 * (j & 3)));
+            }
           }
         }
       }
@@ -924,7 +864,8 @@ burgers_status plan_multilevel(burgers_ctx* ctx, const burgers_batch* batch,
   for (const MLRow& R : mrows) span = std::max<int64_t>(span, R.offset + R.n);
   span = (span + 63) & ~int64_t(63);  // aligned start of the Kahan buffer
   p->ml_span = span;
-  // ping-pong copy of the rows (+ the Kahan terms for FP32), then for the
+  // ping-pong copy of the rows (+ the Kahan terms for FP32, one byte a node in
+  // a region of span elements), then for the
   // iterating variants two planes of e = w - u^n (read by one iteration,
   // written by it for the next)
   p->ml_e_off = dtype == 0 ? 2 * span : span;
