@@ -1186,6 +1186,12 @@ def serve_bench(ctx, dev, duration: float, rate: float = 20000.0, plain_seconds:
     lag = {}
     order = []
     th = threading.Thread(target=collector, args=(len(trace),), daemon=True)
+    # the client's own pauses are not the server's: no cyclic garbage
+    # collection (which would walk the trace's objects) while it submits
+    import gc
+    gc.collect()
+    gc.freeze()
+    gc.disable()
     start = time.perf_counter()
     th.start()
     late = 0.0
@@ -1200,6 +1206,8 @@ def serve_bench(ctx, dev, duration: float, rate: float = 20000.0, plain_seconds:
         lag[tk] = max(0.0, time.perf_counter() - (start + q.t_arrive))
         order.append(tk)
     finished.wait(duration + 600)
+    gc.enable()
+    gc.unfreeze()
     stats = sv.stats()
     sv.close()
     # latency from the request's scheduled arrival: server time from submission
