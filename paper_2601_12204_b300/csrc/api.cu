@@ -111,8 +111,8 @@ static const std::vector<Shape>& resident_shapes(int kind, int dtype) {
                                           {64, 32},  {128, 32}, {256, 16}, {256, 32}};
   if (kind == K_EXPLICIT_RESIDENT) return dtype == 0 ? ex32 : ex64;
   if (kind == K_RK4_RESIDENT) return dtype == 0 ? rk32 : rk64;
-  if (kind == K_CN_RESIDENT || kind == K_PICARD_RESIDENT) return dtype == 0 ? cp32 : im64;
-  if (kind == K_NEWTON_RESIDENT) return dtype == 0 ? im32 : im64;
+  if (kind == K_CN_RESIDENT || kind == K_PICARD_RESIDENT || kind == K_NEWTON_RESIDENT)
+    return dtype == 0 ? cp32 : im64;
   return dtype == 0 ? bt32 : bt64;
 }
 
@@ -189,9 +189,10 @@ static Shape pick_resident(const burgers_ctx* ctx, int kind, int dtype, int64_t 
   // ragged FP32 BTCS rows of up to 2048 nodes: the packed kernel at 64 x 32
   // (longer chains, a 64-row reduced system) measured 6.5e11 against 5.4e11
   // cell-updates/s at 128 x 16 on 2000-node rows (100 steps at 10x the CFL
-  // step); Crank-Nicolson and Picard take the same shape (one Picard
+  // step); Crank-Nicolson, Picard and Newton take the same shape (one Picard
   // iteration is then bitwise the BTCS step)
-  if ((kind == K_BTCS_RESIDENT || kind == K_CN_RESIDENT || kind == K_PICARD_RESIDENT) &&
+  if ((kind == K_BTCS_RESIDENT || kind == K_CN_RESIDENT || kind == K_PICARD_RESIDENT ||
+       kind == K_NEWTON_RESIDENT) &&
       dtype == 0 && cap == 2048 && n < cap)
     return Shape{64, 32};
   return best;
@@ -410,7 +411,8 @@ static burgers_status build_plan(burgers_ctx* ctx, int scheme, const burgers_bat
     // row of its capacity class; a tuning table could name another shape)
     if (!exact && dtype == 0 && sh.c >= 4 && sh.c % 2 == 0 &&
         (rkind == K_EXPLICIT_RESIDENT || rkind == K_BTCS_RESIDENT || rkind == K_CN_RESIDENT ||
-         rkind == K_PICARD_RESIDENT || (rkind == K_RK4_RESIDENT && sh.c >= 16))) {
+         rkind == K_PICARD_RESIDENT || rkind == K_NEWTON_RESIDENT ||
+         (rkind == K_RK4_RESIDENT && sh.c >= 16))) {
       const int64_t t = (int64_t(in.n) + sh.c - 1) / sh.c;
       if (t * sh.c - in.n > t || t > sh.nt)
         return set_error(BURGERS_EINVAL, "row length has no split into chunks of C or C - 1 "

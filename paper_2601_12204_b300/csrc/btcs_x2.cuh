@@ -1,6 +1,6 @@
 // btcs_x2.cuh -- the FP32 resident implicit-step kernel on packed f32x2
-// arithmetic (lagged BTCS, Crank-Nicolson and Picard; the algebra of each
-// variant is that of btcs_kernel.cuh), for rows of exactly NT*C nodes and for
+// arithmetic (lagged BTCS, Crank-Nicolson, Picard and Newton; the algebra of
+// each variant is that of btcs_kernel.cuh), for rows of exactly NT*C nodes and for
 // ragged rows of its capacity class (chunks of C or C - 1 nodes, below).
 //
 // Each thread's chunk of C nodes is two half-chunks, A = nodes [0, C/2) and
@@ -39,7 +39,8 @@ struct X2Shared {
 
 template <int NT, int C, int VAR>
 constexpr size_t btcs_x2_dsm() {
-  return sizeof(float2) * size_t(NT) * size_t(C / 2) * (2 + (VAR == VAR_PICARD ? 1 : 0));
+  return sizeof(float2) * size_t(NT) * size_t(C / 2) *
+         (2 + ((VAR == VAR_PICARD || VAR == VAR_NEWTON) ? 1 : 0));
 }
 
 // Thread 0's reduced row coefficients A_0, B_0 from its published values and
@@ -59,11 +60,15 @@ __device__ __forceinline__ void btcs_steps_x2(int64_t nsteps, int iters, float r
                                               float2* es, int solver, int tl_, bool shrt,
                                               bool padwarp) {
   static_assert(C % 2 == 0 && C >= 2, "two half-chunks");
-  static_assert(VAR != VAR_NEWTON, "Newton takes its neighbours directly (scalar kernel)");
   constexpr int H = C / 2;
-  constexpr bool ITER = VAR == VAR_PICARD;
+  constexpr bool ITER = VAR == VAR_PICARD || VAR == VAR_NEWTON;
+  // Newton's Jacobian diagonal holds w_{i+1} - w_{i-1}, so its sweeps take
+  // the neighbours' values directly (published by their owners in the
+  // previous back-substitution, one more CTA barrier per iteration) instead
+  // of deferring them to the reduced rows: no deferred terms (kappa = 0)
+  constexpr bool DEFER = VAR != VAR_NEWTON;
   constexpr bool PER = BCT == BC_PERIODIC;
-  const float kap = VAR == VAR_CN ? 2.f : 1.f;
+  const float kap = VAR == VAR_CN ? 2.f : (DEFER ? 1.f : 0.f);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   // last chunk holding nodes (ragged rows: chunks past it hold none, and the
   // short chunks end one pair early in their second half)
@@ -73,6 +78,8 @@ __device__ __forceinline__ void btcs_steps_x2(int64_t nsteps, int iters, float r
   const float2 RM2 = make_float2(rm, rm), SM2 = make_float2(smat, smat);
   const float ds1 = 1.f + 2.f * smat;
   const float2 DS1 = make_float2(ds1, ds1);
+  const float hr = 0.5f * rm;  // Newton: r/2
+  const float2 HR2 = make_float2(hr, hr), NS2 = make_float2(-smat, -smat);
   const int nit = ITER ? iters : 1;
   auto W = [&](int k) -> float2 {
     if constexpr (ITER) return add2(us[k * NT + tid], es[k * NT + tid]);
@@ -94,29 +101,49 @@ __device__ __forceinline__ void btcs_steps_x2(int64_t nsteps, int iters, float r
     // branch around the sweep spilled): nothing reads what they publish.
     float eBc = 0.f, eBa = 0.f, eBd = 0.f, pa = 0.f, pc = 0.f, pd0 = 0.f;
     if (EXACT || C > 16 || !padwarp) {
+    // Newton: the current iterate's values left of the chunk and right of it
+    float nleft = 0.f, nright = 0.f;
+    if constexpr (!DEFER) {
+      nleft = tid > 0 ? hlast[tid - 1] : (PER ? hlast[tl] : 0.f);
+      nright = tid < tl ? hfirst[tid + 1] : (PER ? hfirst[0] : 0.f);
+    }
     float2 a = W(0);
-    float2 DL = sub2(a, make_float2(a.x, W(H - 1).x));  // a - u_l
+    float2 ul = make_float2(DEFER ? a.x : nleft, W(H - 1).x);
+    float2 DL = sub2(a, ul);  // a - u_l
     float2 chp = make_float2(0.f, 0.f), ahp = make_float2(-1.f, -1.f), ndhp = make_float2(0.f, 0.f);
 #pragma unroll
     for (int k = 0; k < H; ++k) {
-      float2 an = (k + 1 < H) ? W(k + 1) : make_float2(W(0).y, a.y);
+      float2 an = (k + 1 < H) ? W(k + 1) : make_float2(W(0).y, DEFER ? a.y : nright);
       // a short chunk's second half ends at pair H - 2 and stands in for its
       // own right neighbour there (its pair H - 1 is padding)
       if constexpr (!EXACT) {
-        if (k == H - 2 && shrt) an.y = a.y;
+        if (k == H - 2 && shrt) an.y = DEFER ? a.y : nright;
       }
       const float2 ER = sub2(an, a);  // u_r - a
-      const float2 ra = mul2(RM2, a);
-      const float2 M = make_float2(fmaxf(ra.x, 0.f), fmaxf(ra.y, 0.f));
-      const float2 m = make_float2(fminf(ra.x, 0.f), fminf(ra.y, 0.f));
-      float2 nl = add2(SM2, M);       // -l
-      float2 c = sub2(m, SM2);        // c
-      float2 nc = sub2(SM2, m);       // -c
-      float2 d = add2(DS1, sub2(M, m));
-      // -rhs = -(l (a - u_l) - c (u_r - a)) of the increment form
-      float2 nrhs = fma2(nl, DL, mul2(c, ER));
-      if constexpr (VAR == VAR_CN) nrhs = mul2(make_float2(2.f, 2.f), nrhs);
-      if constexpr (ITER) nrhs = add2(nrhs, es[k * NT + tid]);
+      float2 nl, c, nc, d, nrhs;      // -l, c, -c, d, -rhs
+      if constexpr (VAR == VAR_NEWTON) {
+        // J rows l = -(r/2) w - s, d = 1 + (r/2)(w_r - w_l) + 2s, c = (r/2) w - s;
+        // -rhs = F = e + (r/2) w (w_r - w_l) - s (w_r - 2 w + w_l)
+        const float2 ha = mul2(HR2, a);
+        const float2 cdf = sub2(an, ul);
+        nl = add2(ha, SM2);
+        c = sub2(ha, SM2);
+        nc = sub2(SM2, ha);
+        d = fma2(HR2, cdf, DS1);
+        nrhs = fma2(NS2, sub2(ER, DL), fma2(ha, cdf, es[k * NT + tid]));
+      } else {
+        const float2 ra = mul2(RM2, a);
+        const float2 M = make_float2(fmaxf(ra.x, 0.f), fmaxf(ra.y, 0.f));
+        const float2 m = make_float2(fminf(ra.x, 0.f), fminf(ra.y, 0.f));
+        nl = add2(SM2, M);
+        c = sub2(m, SM2);
+        nc = sub2(SM2, m);
+        d = add2(DS1, sub2(M, m));
+        // -rhs = -(l (a - u_l) - c (u_r - a)) of the increment form
+        nrhs = fma2(nl, DL, mul2(c, ER));
+        if constexpr (VAR == VAR_CN) nrhs = mul2(make_float2(2.f, 2.f), nrhs);
+        if constexpr (ITER) nrhs = add2(nrhs, es[k * NT + tid]);
+      }
       if constexpr (BCT == BC_DIRICHLET) {  // the row's end nodes are identity rows
         if (k == 0 && tid == 0) { nl.x = 0.f; c.x = 0.f; nc.x = 0.f; d.x = 1.f; nrhs.x = 0.f; }
         // (ragged rows: the last node only zeroes its chunk's end relation, below)
@@ -134,6 +161,7 @@ __device__ __forceinline__ void btcs_steps_x2(int64_t nsteps, int iters, float r
       AH[k] = ahp;
       ND[k] = ndhp;
       DL = ER;
+      ul = a;
       a = an;
     }
     // end rows of both halves: x_e = dh - ah L - ch x_next
@@ -273,6 +301,8 @@ __device__ __forceinline__ void btcs_steps_x2(int64_t nsteps, int iters, float r
         }
       }
     }
+    // Newton: the next sweep reads its neighbours' new edge values
+    if constexpr (!DEFER) __syncthreads();
   }  // iterations
   }  // steps
 }
