@@ -429,6 +429,20 @@ burgers_status burgers_serve_create(burgers_ctx* ctx, const burgers_serve_cfg* c
 burgers_status burgers_serve_submit(burgers_server* sv, const burgers_request* rq,
                                     uint64_t* ticket);
 
+/* Blocking: a client that replays a trace of `count` requests from the
+ * calling thread (no interpreter between the requests and the server): request
+ * i is submitted as burgers_serve_submit does, once t_arrive[i] seconds have
+ * passed since the call began (at once if that time is already past), and
+ * late_s[i] receives how late its submission returned against that time, so
+ * a caller can measure latency from each request's scheduled arrival.
+ * rqs, t_arrive, tickets and late_s are host arrays of `count` elements owned
+ * by the caller (u0 of each request is copied during its submission).
+ * Stops at the first submission that fails and returns its status; tickets
+ * of requests not submitted are 0. count < 0 or a NULL array: EINVAL. */
+burgers_status burgers_serve_submit_timed(burgers_server* sv, const burgers_request* rqs,
+                                          const double* t_arrive, int64_t count,
+                                          uint64_t* tickets, double* late_s);
+
 /* Non-blocking: EAGAIN while the request is pending or running; otherwise
  * copies the result (n values) to out_host (may be NULL), fills *stats (may
  * be NULL), forgets the ticket and returns the request's status (OK,

@@ -130,6 +130,7 @@ class burgers_serve_stats(ctypes.Structure):
 SIGNATURES.update({
     "burgers_serve_create": (_ST, [_P, _P, ctypes.POINTER(_P)]),
     "burgers_serve_submit": (_ST, [_P, _P, ctypes.POINTER(ctypes.c_uint64)]),
+    "burgers_serve_submit_timed": (_ST, [_P, _P, _P, ctypes.c_int64, _P, _P]),
     "burgers_serve_poll": (_ST, [_P, ctypes.c_uint64, _P, _P]),
     "burgers_serve_wait": (_ST, [_P, ctypes.c_uint64, _D, _P, _P]),
     "burgers_serve_cancel": (_ST, [_P, ctypes.c_uint64]),

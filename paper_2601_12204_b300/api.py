@@ -324,6 +324,22 @@ class Server:
                 "burgers_serve_submit")
         return int(t.value)
 
+    def submit_timed(self, reqs, t_arrive):
+        """Replays a trace from native code: reqs is a ctypes array of
+        burgers_request, t_arrive the arrival times in seconds after the call
+        (float64). Blocks until every request is submitted; returns the
+        tickets (uint64) and each submission's lateness in seconds."""
+        n = len(reqs)
+        ta = np.ascontiguousarray(t_arrive, dtype=np.float64)
+        if ta.size != n:
+            raise ValueError("one arrival time per request")
+        tickets = np.zeros(n, dtype=np.uint64)
+        late = np.zeros(n, dtype=np.float64)
+        L.check(self._lib.burgers_serve_submit_timed(
+            self.h, ctypes.cast(reqs, ctypes.c_void_p), ta.ctypes.data, ctypes.c_int64(n),
+            tickets.ctypes.data, late.ctypes.data), "burgers_serve_submit_timed")
+        return tickets, late
+
     def _result(self, fn, ticket, n, *extra):
         out = np.empty(n, dtype=self.np_dtype)
         st = L.burgers_req_stats()

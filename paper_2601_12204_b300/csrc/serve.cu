@@ -761,6 +761,32 @@ static burgers_status take_result(burgers_server* sv, Req* q, void* out_host,
   return BURGERS_OK;
 }
 
+burgers_status burgers_serve_submit_timed(burgers_server* sv, const burgers_request* rqs,
+                                          const double* t_arrive, int64_t count,
+                                          uint64_t* tickets, double* late_s) {
+  if (!sv || count < 0 || (count > 0 && (!rqs || !t_arrive || !tickets || !late_s)))
+    return set_error(BURGERS_EINVAL, "NULL argument or negative count");
+  for (int64_t i = 0; i < count; ++i) {
+    tickets[i] = 0;
+    late_s[i] = 0.0;
+  }
+  using clk = std::chrono::steady_clock;
+  const clk::time_point t0 = clk::now();
+  for (int64_t i = 0; i < count; ++i) {
+    const clk::time_point due =
+        t0 + std::chrono::duration_cast<clk::duration>(std::chrono::duration<double>(t_arrive[i]));
+    if (clk::now() < due) std::this_thread::sleep_until(due);
+    const burgers_status st = burgers_serve_submit(sv, &rqs[i], &tickets[i]);
+    if (st != BURGERS_OK) {
+      tickets[i] = 0;
+      return st;
+    }
+    // how late the request reached the server against its arrival time
+    late_s[i] = std::max(0.0, std::chrono::duration<double>(clk::now() - due).count());
+  }
+  return BURGERS_OK;
+}
+
 burgers_status burgers_serve_poll(burgers_server* sv, uint64_t ticket, void* out_host,
                                   burgers_req_stats* rs) {
   if (!sv) return set_error(BURGERS_EINVAL, "NULL server");

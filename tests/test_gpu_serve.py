@@ -173,3 +173,33 @@ def test_serve_concurrent_submitters(ctx):
                     (q.scheme, q.bc, q.n, q.nsteps)
     finally:
         sv.close()
+
+
+def test_serve_submit_timed_replays_a_trace(ctx):
+    """burgers_serve_submit_timed submits each request once its arrival time
+    has passed, from native code: every request completes (oracle parity),
+    the server saw the submissions spread over the trace's 50 ms, each
+    lateness is non-negative, and a NULL array is EINVAL."""
+    import ctypes
+    from paper_2601_12204_b300.api import Server
+    sv = Server(ctx, F32, hbm_budget=512 << 20, slice_steps=64)
+    reqs = _requests(24, seed=9, nmax=5000)
+    u0s = [np.ascontiguousarray(q.u0, dtype=np.float32) for q, _ in reqs]
+    arr = (L.burgers_request * len(reqs))()
+    for i, ((q, dt), u) in enumerate(zip(reqs, u0s)):
+        arr[i] = L.burgers_request(int(q.scheme), int(q.bc), int(q.n), 0, float(q.dx),
+                                   float(q.nu), float(dt), int(q.nsteps), u.ctypes.data)
+    t_arr = np.linspace(0.0, 0.05, len(reqs))
+    tickets, late = sv.submit_timed(arr, t_arr)
+    assert len(set(tickets.tolist())) == len(reqs) and np.all(tickets > 0)
+    assert np.all(late >= 0.0)
+    subs = []
+    for (q, dt), t in zip(reqs, tickets.tolist()):
+        rc, out, st = sv.wait(t, q.n, timeout_s=120)
+        assert rc == L.BURGERS_OK, L.last_error()
+        assert oracle.rel_l2(out.astype(np.float64), _oracle(q, dt)) <= 1e-5
+        subs.append(st.t_submit)
+    assert max(subs) - min(subs) >= 0.045
+    rc = sv._lib.burgers_serve_submit_timed(sv.h, None, None, ctypes.c_int64(1), None, None)
+    assert rc == L.BURGERS_EINVAL
+    assert sv.close() == 0
